@@ -1,0 +1,166 @@
+"""Pin checks of the oracle: each returns the largest deviation from something the
+paper or the mathematics fixes (brute force, closed forms, invariants, library
+routines). ``test_oracle_pins`` asserts they are small; ``test_oracle_mutations``
+plants mistakes in the oracle and asserts that some pin then fails.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.spatial.distance import cdist
+
+import closed_forms as cf
+from oracle import circuit, gram, mps
+from paper_2602_01330_gb300 import synthetic
+
+
+def statevector_vs_product(reps: int, c: float = 2.0, n: int = 6, seed: int = 11) -> float:
+    """Statevector kernel with entanglers off vs the product closed forms (forms 1, 2)."""
+    x = synthetic.uniform_angles(5, n, seed)
+    k = circuit.kernel_matrix(x, x, reps, angle_scale=c, entangle=False)
+    err = 0.0
+    for i in range(5):
+        for j in range(5):
+            if reps == 1:
+                ref = cf.product_kernel_r1(x[i], x[j], c)
+            else:
+                ref = float(np.prod(np.abs(cf.product_amplitudes_r2(x[i], x[j], c)) ** 2))
+            err = max(err, abs(k[i, j] - ref))
+    return err
+
+
+def statevector_vs_ising(n: int = 7, c: float = 2.0, seed: int = 12) -> float:
+    """Statevector kernel with entanglers, one repetition, vs the Ising form (form 3)."""
+    x = synthetic.uniform_angles(5, n, seed)
+    k = circuit.kernel_matrix(x, x, 1, angle_scale=c, entangle=True)
+    err = 0.0
+    for i in range(5):
+        for j in range(5):
+            err = max(err, abs(k[i, j] - np.exp(cf.ising_log_kernel(x[i], x[j], c))))
+    return err
+
+
+def statevector_vs_dense(n: int = 4, reps: int = 2, c: float = 2.0, seed: int = 18) -> float:
+    """Oracle statevector kernel vs dense expm/Kronecker unitaries (form 5), any reps."""
+    x = synthetic.uniform_angles(4, n, seed)
+    k = circuit.kernel_matrix(x, x, reps, angle_scale=c, entangle=True)
+    states = [cf.dense_state(row, reps, c) for row in x]
+    err = 0.0
+    for i in range(4):
+        for j in range(4):
+            err = max(err, abs(k[i, j] - abs(np.vdot(states[i], states[j])) ** 2))
+    return err
+
+
+def mps_vs_statevector(n: int, reps: int, entangle: bool = True, c: float = 2.0, seed: int = 13) -> float:
+    """Oracle MPS + transfer Gram vs brute-force statevector overlaps (n <= 12)."""
+    x = synthetic.uniform_angles(6, n, seed)
+    ref = circuit.kernel_matrix(x, x, reps, angle_scale=c, entangle=entangle)
+    sites, _ = mps.build_mps(x, reps, angle_scale=c, entangle=entangle)
+    kq, _ = gram.gram_from_mps(sites, sites)
+    return float(np.max(np.abs(kq - ref)))
+
+
+def mps_statevector_amplitudes(n: int, reps: int, seed: int = 14) -> float:
+    """Each sample's contracted MPS equals its statevector up to a global phase."""
+    x = synthetic.uniform_angles(3, n, seed)
+    sites, _ = mps.build_mps(x, reps)
+    err = 0.0
+    for i in range(3):
+        v = mps.to_statevector(sites, i)
+        s = circuit.statevector(x[i], reps)
+        ph = np.vdot(v, s)
+        ph = ph / abs(ph) if abs(ph) > 0 else 1.0
+        err = max(err, float(np.max(np.abs(v * ph - s))))
+    return err
+
+
+def large_n_ising(n: int = 784, seed: int = 21) -> float:
+    """Oracle log K_q at large n, one repetition, vs the Ising recursion; relative in log."""
+    d = synthetic.fmnist_like(6, 0, n)["x_train"].astype(np.float64)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    near = np.clip(d[:2] + rng.normal(0, 1e-3, size=d[:2].shape), 0, np.pi)
+    x = np.concatenate([d, near])
+    sites, _ = mps.build_mps(x, 1)
+    pairs = [(0, 1), (0, 2), (3, 5), (0, 6), (1, 7), (4, 4)]
+    i_idx = [p[0] for p in pairs]
+    j_idx = [p[1] for p in pairs]
+    _, lkq = gram.pair_values(sites, sites, i_idx, j_idx)
+    err = 0.0
+    for (i, j), got in zip(pairs, lkq):
+        ref = cf.ising_log_kernel(x[i], x[j])
+        err = max(err, abs(got - ref) / max(1.0, abs(ref)))
+    return err
+
+
+def large_n_product(n: int = 784, reps: int = 2, seed: int = 22) -> float:
+    """Entanglers off at large n vs the product closed forms, relative in log."""
+    x = synthetic.uniform_angles(4, n, seed)
+    x[3] = np.clip(x[0] + 1e-3, 0, np.pi)
+    sites, _ = mps.build_mps(x, reps, entangle=False)
+    pairs = [(0, 1), (1, 2), (0, 3), (2, 2)]
+    _, lkq = gram.pair_values(sites, sites, [p[0] for p in pairs], [p[1] for p in pairs])
+    err = 0.0
+    for (i, j), got in zip(pairs, lkq):
+        ref = cf.product_log_kernel_r1(x[i], x[j]) if reps == 1 else cf.product_log_kernel_r2(x[i], x[j])
+        err = max(err, abs(got - ref) / max(1.0, abs(ref)))
+    return err
+
+
+def near_duplicate_abs(n: int = 784, seed: int = 23) -> float:
+    """|K_q - closed form| for a near-duplicate pair at large n (K_q close to 1)."""
+    x = synthetic.uniform_angles(1, n, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    y = np.clip(x + rng.normal(0, 2e-3, size=x.shape), 0, np.pi)
+    both = np.concatenate([x, y])
+    sites, _ = mps.build_mps(both, 1)
+    kq, _ = gram.pair_values(sites, sites, [0], [1])
+    return float(abs(kq[0] - np.exp(cf.ising_log_kernel(x[0], y[0]))))
+
+
+def bond_ranks(n: int = 9, reps: int = 2, seed: int = 15) -> int:
+    """Number of bonds whose oracle-MPS dimension or statevector Schmidt rank differs from
+    min(2^k, 2^(n-k), 2^reps)."""
+    x = synthetic.uniform_angles(2, n, seed)
+    sites, _ = mps.build_mps(x, reps)
+    dims = mps.bond_dims(sites)
+    bad = 0
+    for k in range(1, n):
+        want = cf.exact_bond_rank(n, reps, k)
+        psi = circuit.statevector(x[0], reps)
+        sv = np.linalg.svd(psi.reshape(2 ** k, 2 ** (n - k)), compute_uv=False)
+        rank = int(np.sum(sv > 1e-12 * sv[0]))
+        bad += int(dims[k] != want) + int(rank != want)
+    return bad
+
+
+def invariants(n: int = 64, m: int = 40, reps: int = 2) -> float:
+    """Diagonal = 1, symmetry, 0 <= K <= 1, PSD, chain reversal, on Fashion-MNIST-shaped data."""
+    x = synthetic.fmnist_like(m, 0, n)["x_train"].astype(np.float64)
+    sites, _ = mps.build_mps(x, reps)
+    kq, _ = gram.gram_from_mps(sites, sites)
+    err = float(np.max(np.abs(np.diag(kq) - 1.0)))
+    err = max(err, float(np.max(np.abs(kq - kq.T))))
+    err = max(err, float(max(0.0, -kq.min())), float(max(0.0, kq.max() - 1.0 - 1e-12)))
+    lam = np.linalg.eigvalsh(0.5 * (kq + kq.T))
+    err = max(err, float(max(0.0, -lam.min())))
+    rev, _ = mps.build_mps(x[:, ::-1].copy(), reps)
+    kr, _ = gram.gram_from_mps(rev, rev)
+    err = max(err, float(np.max(np.abs(kr - kq))))
+    return err
+
+
+def rbf_vs_library(seed: int = 16) -> float:
+    x = synthetic.fmnist_like(30, 10, 64)
+    a, b = x["x_train"].astype(np.float64), x["x_test"].astype(np.float64)
+    gamma = 1.0 / 64
+    ref = np.exp(-gamma * cdist(a, b, "sqeuclidean"))
+    return float(np.max(np.abs(gram.rbf(a, b, gamma) - ref)))
+
+
+def mix_limits() -> float:
+    x = synthetic.uniform_angles(8, 5, 17)
+    kq, _ = gram.quantum_gram(x, reps=2)
+    kc = gram.rbf(x, x, 0.2)
+    e = float(np.max(np.abs(gram.dual_kernel(kq, kc, 1.0) - kq)))
+    e = max(e, float(np.max(np.abs(gram.dual_kernel(kq, kc, 0.0) - kc))))
+    return e
