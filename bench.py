@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark of the quantum-kernel Gram hot path: Gram entries x qubits per second.
+
+Workload (one step, all of the hot path): Fashion-MNIST-shaped synthetic data at d = 784
+features (raw pixels, one qubit per feature), 2000 training + 500 test samples, ZZ-chain
+map with reps = 2 (bond chi = 4), complex64 / FP32:
+  MPS build of the 2000 training and the 500 test samples (FP64 QR canonicalisation),
+  the symmetric 2000 x 2000 Gram with the fused RBF kernel and mix (w = 0.5; K, K_q,
+  K_c and log K_q written), and the 500 x 2000 dual-kernel rows.
+Unit of work: one entry x qubit (one pair through one site). Entries per step =
+2000*2001/2 + 500*2000 = 3,001,000; x 784 qubits = 2.353e9 entry-qubits.
+
+Default arm: our CUDA library (libdualk.so) through its Python binding. `--impl reference`
+times the FP64 CPU oracle on a bounded sample of the same workload.
+Multi-GPU (torchrun, one rank per GPU): each rank runs its own independent problem of the
+same size (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+WL = dict(workload="fmnist784_gram2000_rows500", d=784, n_train=2000, n_test=500, reps=2, chi=4, w=0.5)
+METRIC = "Gram entries*qubits/s (n=784,chi=4)"
+UNIT = "entry-qubits/s"
+
+
+def entries_per_step(n_train, n_test):
+    return n_train * (n_train + 1) // 2 + n_test * n_train
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.device_index = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_rate(n_train, n_test, d, reps, seed_train=1, seed_test=2):
+    """The FP64 oracle on a sample of the workload: MPS of n_train + n_test samples, the
+    unique pairs of the train Gram and the test x train rows. Returns (entry-qubits/s, seconds)."""
+    from oracle import gram, mps
+    from paper_2602_01330_gb300 import synthetic
+    data = synthetic.fmnist_like(n_train, n_test, d, seed_train=seed_train, seed_test=seed_test)
+    xtr = data["x_train"].astype(np.float64)
+    xte = data["x_test"].astype(np.float64)
+    t0 = time.perf_counter()
+    otr, _ = mps.build_mps(xtr, reps)
+    ote, _ = mps.build_mps(xte, reps)
+    iu, ju = np.triu_indices(n_train)
+    kq, _ = gram.pair_values(otr, otr, iu, ju)
+    kc = gram.rbf_pairs(xtr, xtr, iu, ju, 1.0 / d)
+    gram.dual_kernel(kq, kc, WL["w"])
+    ii, jj = np.meshgrid(np.arange(n_test), np.arange(n_train), indexing="ij")
+    kq2, _ = gram.pair_values(ote, otr, ii.ravel(), jj.ravel())
+    kc2 = gram.rbf_pairs(xte, xtr, ii.ravel(), jj.ravel(), 1.0 / d)
+    gram.dual_kernel(kq2, kc2, WL["w"])
+    dt = time.perf_counter() - t0
+    units = (n_train * (n_train + 1) // 2 + n_test * n_train) * d
+    return units / dt, dt
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    sample = dict(n_train=24, n_test=8)
+    for _ in range(args.warmup):
+        oracle_rate(sample["n_train"], sample["n_test"], WL["d"], WL["reps"])
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, s = oracle_rate(sample["n_train"], sample["n_test"], WL["d"], WL["reps"])
+        rates.append(r)
+        secs.append(s)
+    total_units = sum(r * s for r, s in zip(rates, secs))
+    value = total_units / sum(secs)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Fashion-MNIST-shaped, seeded)",
+        "config": {"workload": WL["workload"], "d": WL["d"], "reps": WL["reps"], "chi": WL["chi"],
+                   "sample_per_step": f"{sample['n_train']} train + {sample['n_test']} test samples"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step: MPS of {sample['n_train']}+{sample['n_test']} samples at n=784, "
+                                   f"{sample['n_train'] * (sample['n_train'] + 1) // 2} Gram + "
+                                   f"{sample['n_train'] * sample['n_test']} row entries"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as tdist
+
+    from paper_2602_01330_gb300 import build as libbuild
+    from paper_2602_01330_gb300 import dualk, synthetic, workload
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not os.path.exists(dualk.LIB_PATH):
+        libbuild.build()
+
+    n_tr, n_te, d, reps, chi, w = WL["n_train"], WL["n_test"], WL["d"], WL["reps"], WL["chi"], WL["w"]
+    data = synthetic.fmnist_like(n_tr, n_te, d, seed_train=1 + 100 * rank, seed_test=2 + 100 * rank)
+    ctx = dualk.Context(local)
+    fm = dualk.FeatureMap(reps=reps, chi_max=chi)
+    stream = torch.cuda.current_stream()
+
+    x_tr = torch.from_numpy(data["x_train"]).to(dev)
+    x_te = torch.from_numpy(data["x_test"]).to(dev)
+    mps_tr = torch.empty(dualk.mps_bytes(n_tr, d, chi), dtype=torch.uint8, device=dev)
+    mps_te = torch.empty(dualk.mps_bytes(n_te, d, chi), dtype=torch.uint8, device=dev)
+    g_out = {k: torch.empty((n_tr, n_tr), dtype=torch.float32, device=dev) for k in ("k", "kq", "kc", "logkq")}
+    r_out = {k: torch.empty((n_te, n_tr), dtype=torch.float32, device=dev) for k in ("k", "kq", "kc", "logkq")}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    gram_events = []
+
+    def step(record=False):
+        mtr = dualk.mps_build(ctx, x_tr, fm, out=mps_tr)
+        mte = dualk.mps_build(ctx, x_te, fm, out=mps_te)
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        dualk.gram_tile(ctx, mtr, mtr, symmetric=True, w=w, out=g_out, ld=n_tr)
+        if record:
+            e1.record(stream)
+            gram_events.append((e0, e1))
+        dualk.dual_kernel_rows(ctx, mte, mtr, w=w, out=r_out)
+
+    launches_per_step = 2 + 2 + 1 + 1  # (build + self-overlap) x 2, Gram, rows
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.sync_status()
+
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        step(record=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ctx.sync_status()
+    gram_ms = [a.elapsed_time(b) for a, b in gram_events]
+
+    units_step = entries_per_step(n_tr, n_te) * d
+    value = world * units_step * args.steps / (ms / 1e3)
+
+    # End to end through the public API: pinned host inputs in, K blocks out, every step.
+    h_xtr = torch.from_numpy(data["x_train"]).pin_memory()
+    h_xte = torch.from_numpy(data["x_test"]).pin_memory()
+    h_k = torch.empty((n_tr, n_tr), dtype=torch.float32).pin_memory()
+    h_r = torch.empty((n_te, n_tr), dtype=torch.float32).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        x_tr.copy_(h_xtr, non_blocking=True)
+        x_te.copy_(h_xte, non_blocking=True)
+        step()
+        h_k.copy_(g_out["k"], non_blocking=True)
+        h_r.copy_(r_out["k"], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = world * units_step * args.steps / (e2e_ms / 1e3)
+    h2d = h_xtr.numel() * 4 + h_xte.numel() * 4
+    d2h = h_k.numel() * 4 + h_r.numel() * 4
+
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = workload.fp32_peak_tflops(props.multi_processor_count, sm_max)
+    gram_flops = workload.gram_entries(n_tr) * workload.flops_per_pair(d, reps)
+    gram_avg_ms = statistics.mean(gram_ms)
+    achieved = gram_flops / (gram_avg_ms / 1e3) / 1e12
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s_tr, s_te = 48, 16
+        rate, secs = oracle_rate(s_tr, s_te, d, reps)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"MPS of {s_tr}+{s_te} samples at n=784 (TEBD), {s_tr * (s_tr + 1) // 2} Gram + "
+                         f"{s_tr * s_te} row entries, {secs:.1f} s, FP64 NumPy single thread"}
+
+    if world > 1:
+        tdist.destroy_process_group()
+    ctx.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (Fashion-MNIST-shaped, seeded; the real data set is not available)",
+        "config": {"workload": WL["workload"], "d": d, "n_train": n_tr, "n_test": n_te, "reps": reps, "chi": chi,
+                   "w": w, "mps_dtype": "complex64", "parallelism": f"independent problem per GPU x{world}",
+                   "l2": "256 MB buffer written before every timed step (inside the timed region)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "gram_kernel<float,chi=4> (symmetric 2000x2000 Gram)",
+                     "peak_source": f"FP32 FMA peak {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
+                     "avg_launch_ms": gram_avg_ms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

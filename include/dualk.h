@@ -1,0 +1,162 @@
+/*
+ * dualk -- C ABI of the GB300 (sm_103a) quantum-classical dual-kernel engine.
+ *
+ * Paper: "Scalable Tensor Network Simulation for Quantum-Classical Dual Kernel"
+ * (arXiv 2602.01330). The library computes, on one GPU,
+ *
+ *   K_q(x_i, x_j) = |<psi(x_i)|psi(x_j)>|^2                         (§II-C, Eqs. 6-10)
+ *   K_c(x_i, x_j) = exp(-gamma ||x_i - x_j||^2)                       (§II-B, Eq. 3)
+ *   K(x_i, x_j)   = w K_q + (1 - w) K_c                               (§II-D, Eq. 11)
+ *
+ * with |psi(x)> held as a matrix product state (MPS) and K_q evaluated by
+ * contracting the compute-uncompute overlap network as a chain of transfer
+ * matrices, E <- sum_s A_s(x_i)^dagger E A_s(x_j), tile by tile over blocks of
+ * (row, column) sample pairs (§II-C: exact tensor-network contraction; §II-D:
+ * blockwise construction of the kernel matrix).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named x, mps, log_norm, bond_dims, k_out, kq_out, kc_out, logkq_out
+ *   are DEVICE pointers, allocated and owned by the caller. The library never
+ *   allocates, frees or keeps them. `stream` is a cudaStream_t passed as void*
+ *   (NULL = the legacy default stream). Every call is asynchronous on `stream`;
+ *   inputs must stay valid and outputs untouched until the stream reaches the call.
+ * - Features x are float32, row-major m x n (sample-major): x[i*n + f].
+ * - MPS layout (written by dk_mps_build, read by the Gram calls), site-major:
+ *       A[k][i][s][r][l],  k < n sites, i < m samples, s in {0,1},
+ *       r < chi_max (right bond), l < chi_max (left bond), l fastest,
+ *   complex64 (float re, float im) for DK_C64 or complex128 for DK_C128.
+ *   Element (k,i,s,r,l) sits at index (((k*m + i)*2 + s)*chi_max + r)*chi_max + l.
+ *   Bonds narrower than chi_max are zero-padded. Base pointers must be 16-byte
+ *   aligned (cudaMalloc / torch allocations are).
+ * - Errors: every call returns a dk_status. Argument errors are detected on the
+ *   host before anything is launched (DK_ERR_ARG, DK_ERR_UNSUPPORTED). A failing
+ *   CUDA launch returns DK_ERR_CUDA. A device-side wait that exceeds its bound
+ *   (about two seconds) makes the kernel record DK_ERR_TIMEOUT in the context's
+ *   status word and return without finishing; dk_sync_status reads it. No call
+ *   aborts, asserts or traps.
+ */
+#ifndef DUALK_H
+#define DUALK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DK_OK = 0,
+  DK_ERR_ARG = 1,          /* invalid argument: NULL pointer, bad size, misaligned pointer */
+  DK_ERR_UNSUPPORTED = 2,  /* combination of chi_max / dtype / precision not built */
+  DK_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
+  DK_ERR_TIMEOUT = 4,      /* a device-side wait exceeded its bound (read via dk_sync_status) */
+  DK_ERR_WORKSPACE = 5,    /* caller-provided workspace too small */
+  DK_ERR_NO_DEVICE = 6     /* no usable sm_100-family device */
+} dk_status;
+
+typedef enum { DK_C64 = 0, DK_C128 = 1 } dk_dtype;
+
+/* Arithmetic of the transfer contraction. F32: complex64 tensors, FP32 FMA on CUDA
+ * cores. F64: complex128 tensors, FP64. */
+typedef enum {
+  DK_PREC_F32 = 0,
+  DK_PREC_F64 = 1
+} dk_precision;
+
+typedef struct dk_ctx dk_ctx;
+
+/* Feature map U(x) of §II-C (Eq. 6). The paper's circuit figure is not in its text;
+ * the map built here is the ZZ chain: per repetition, H on every qubit, then
+ * RZ(angle_scale * x_i) on qubit i, then (if entangle) RZZ(2 (pi - x_i)(pi - x_{i+1}))
+ * on every neighbouring pair of the open chain; the same x is re-uploaded by every
+ * repetition. */
+typedef struct {
+  int reps;           /* repetitions, 1..5 */
+  float angle_scale;  /* RZ angle = angle_scale * x_i (2 for the ZZ-chain map) */
+  int entangle;       /* 1: RZZ chain applied; 0: product state */
+  int chi_max;        /* padded bond dimension of the stored tensors: >= min(2^reps, 2^(n-1)) */
+} dk_fmap;
+
+/* Create a context on `device` (sets it current on the calling thread). The context
+ * holds the device status word and cached launch parameters; it never owns user
+ * buffers. Returns DK_ERR_NO_DEVICE if the device is not compute capability 10.x. */
+dk_status dk_create(dk_ctx** out, int device);
+void dk_destroy(dk_ctx* ctx);
+const char* dk_error_string(dk_status status);
+
+/* Wait for `stream`, then return and clear the device status word (DK_OK if no
+ * kernel recorded an error since the last call). */
+dk_status dk_sync_status(dk_ctx* ctx, void* stream);
+
+/* Bytes of an MPS buffer for m samples, n sites, padded bond chi_max. */
+size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
+
+/* |psi(x_i)> = U(x_i)|0>^n as an MPS (§II-C, Eq. 6), for i < m.
+ *
+ * Exact construction: every RZZ layer is a diagonal bond-2 operator, so after r
+ * repetitions the state is an MPS of bond 2^r whose site tensors have a closed form
+ * in (x_{k-1}, x_k). Each sample's chain is then brought to left-canonical form by
+ * Householder QR in FP64 (the only FP64 on the GPU), normalised, and rounded to
+ * `dtype`.
+ *   x          m x n float32 features (device)
+ *   fm         feature map (host pointer)
+ *   mps        dk_mps_bytes(m, n, fm->chi_max, dtype) bytes (device, written)
+ *   bond_dims  n + 1 int32 (device, written, may be NULL): stored left bond of site k,
+ *              and 1 at index n
+ *   log_norm   m floats (device, written, may be NULL): ln |<psi~_i|psi~_i>| of the
+ *              rounded tensors, evaluated by the same transfer arithmetic as the Gram
+ *              calls; passing it to them normalises K_q so that K_q(x, x) = 1.
+ * Errors: DK_ERR_ARG (m < 1, n < 1, NULL x/mps/fm, reps outside 1..5),
+ *         DK_ERR_UNSUPPORTED (chi_max too small for the exact bond, or a chi_max /
+ *         dtype pair without a Gram kernel: DK_C64 needs chi_max 4, DK_C128 chi_max 2 or 4). */
+dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm,
+                       dk_dtype dtype, void* mps, int32_t* bond_dims, float* log_norm,
+                       void* stream);
+
+/* One block of the Gram matrix (§II-D: block (i:i+B, j:j+B) contracted by a GPU
+ * worker), with the RBF kernel and the mix fused into the epilogue.
+ *
+ * Rows are samples row0 .. row0+nrows-1 of the MPS `mps_rows` (which holds m_rows
+ * samples) and columns are samples col0 .. col0+ncols-1 of `mps_cols` (m_cols
+ * samples); both were built with the same n, chi_max and dtype. For each pair,
+ *   a    = <psi(x_i)|psi(x_j)>  by the transfer chain with per-site power-of-two
+ *          rescaling (never underflows),
+ *   logkq = 2 ln|a| - log_norm_rows[i] - log_norm_cols[j]  (log_norm NULL => 0),
+ *   kq   = exp(logkq),  kc = exp(-gamma ||x_i - x_j||^2),  k = w kq + (1 - w) kc.
+ * Outputs (each may be NULL; all float32, device) are written at
+ * out[(i - row0) * ld + (j - col0)].
+ * symmetric = 1 requires mps_rows == mps_cols, row0 == col0, nrows == ncols; each
+ * unordered pair is then contracted once and written to both (i,j) and (j,i).
+ *   x_rows / x_cols: the m_rows x n / m_cols x n features the MPS were built from;
+ *   needed only when k_out or kc_out is requested.
+ * Errors: DK_ERR_ARG (ranges outside the MPS, ld < ncols, bad symmetric request,
+ *         NULL x when k/kc requested), DK_ERR_UNSUPPORTED (precision/dtype/chi). */
+dk_status dk_gram_tile(dk_ctx* ctx,
+                       const void* mps_rows, int m_rows, const void* mps_cols, int m_cols,
+                       int n, int chi_max, dk_dtype dtype,
+                       int row0, int nrows, int col0, int ncols,
+                       const float* log_norm_rows, const float* log_norm_cols,
+                       const float* x_rows, const float* x_cols,
+                       float gamma, float w, dk_precision prec,
+                       float* k_out, float* kq_out, float* kc_out, float* logkq_out,
+                       int64_t ld, int symmetric, void* stream);
+
+/* Dual-kernel rows for prediction (§II-B, Eq. 5 needs K(x_i, x) for every training
+ * sample x_i): the b x m block K(test, train), row-major with leading dimension m.
+ * Same arithmetic and output conventions as dk_gram_tile with rows = the b test
+ * samples and columns = the m training samples. */
+dk_status dk_dual_kernel_rows(dk_ctx* ctx,
+                              const void* mps_test, const float* x_test, const float* log_norm_test, int b,
+                              const void* mps_train, const float* x_train, const float* log_norm_train, int m,
+                              int n, int chi_max, dk_dtype dtype, float gamma, float w,
+                              dk_precision prec,
+                              float* k_out, float* kq_out, float* kc_out, float* logkq_out,
+                              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DUALK_H */

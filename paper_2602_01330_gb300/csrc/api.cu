@@ -1,0 +1,104 @@
+// Context, error strings, status word and tensor-map encoding of libdualk.so.
+#include <stdlib.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+DK_API dk_status dk_create(dk_ctx** out, int device) {
+  if (!out) return DK_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count <= 0) {
+    cudaGetLastError();
+    return DK_ERR_NO_DEVICE;
+  }
+  if (device < 0 || device >= count) return DK_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return DK_ERR_CUDA;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return DK_ERR_CUDA;
+  if (prop.major != 10) return DK_ERR_NO_DEVICE;  // kernels are built for sm_103a only
+
+  dk_ctx* ctx = static_cast<dk_ctx*>(calloc(1, sizeof(dk_ctx)));
+  if (!ctx) return DK_ERR_ARG;
+  ctx->device = device;
+  ctx->sm_count = prop.multiProcessorCount;
+  ctx->cc_major = prop.major;
+  ctx->cc_minor = prop.minor;
+
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    free(ctx);
+    return DK_ERR_CUDA;
+  }
+  ctx->encode_tiled = reinterpret_cast<dk_encode_tiled_fn>(fn);
+
+  if (cudaMalloc(&ctx->status, sizeof(unsigned)) != cudaSuccess) {
+    free(ctx);
+    return DK_ERR_CUDA;
+  }
+  if (cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess) {
+    cudaFree(ctx->status);
+    free(ctx);
+    return DK_ERR_CUDA;
+  }
+  *out = ctx;
+  return DK_OK;
+}
+
+DK_API void dk_destroy(dk_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaFree(ctx->status);
+  free(ctx);
+}
+
+DK_API const char* dk_error_string(dk_status s) {
+  switch (s) {
+    case DK_OK: return "ok";
+    case DK_ERR_ARG: return "invalid argument";
+    case DK_ERR_UNSUPPORTED: return "unsupported chi_max / dtype / precision combination";
+    case DK_ERR_CUDA: return "CUDA runtime error";
+    case DK_ERR_TIMEOUT: return "device-side wait exceeded its bound";
+    case DK_ERR_WORKSPACE: return "workspace too small";
+    case DK_ERR_NO_DEVICE: return "no sm_10x CUDA device";
+  }
+  return "unknown status";
+}
+
+DK_API dk_status dk_sync_status(dk_ctx* ctx, void* stream) {
+  if (!ctx) return DK_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return DK_ERR_CUDA;
+  unsigned host = 0;
+  if (cudaMemcpy(&host, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return DK_ERR_CUDA;
+  if (host) {
+    if (cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess) return DK_ERR_CUDA;
+  }
+  if (host & dk::DEV_TIMEOUT) return DK_ERR_TIMEOUT;
+  return DK_OK;
+}
+
+DK_API size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype) {
+  if (m <= 0 || n <= 0 || chi_max <= 0) return 0;
+  return size_t(m) * size_t(n) * dk::site_bytes(chi_max, dtype);
+}
+
+namespace dk {
+
+dk_status encode_mps_map(dk_ctx* ctx, CUtensorMap* map, const void* mps, int m, int n, size_t sbytes,
+                         int box_samples) {
+  if (sbytes % 128 != 0 || box_samples < 1 || box_samples > 256) return DK_ERR_UNSUPPORTED;
+  cuuint64_t dims[3] = {cuuint64_t(sbytes / 4), cuuint64_t(m), cuuint64_t(n)};
+  cuuint64_t strides[2] = {cuuint64_t(sbytes), cuuint64_t(sbytes) * cuuint64_t(m)};
+  cuuint32_t box[3] = {32u, cuuint32_t(box_samples), 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = ctx->encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(mps), dims, strides, box,
+                                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? DK_OK : DK_ERR_CUDA;
+}
+
+}  // namespace dk

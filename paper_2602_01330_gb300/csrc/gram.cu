@@ -1,0 +1,386 @@
+// Tiled quantum-kernel Gram with the RBF kernel and the dual-kernel mix fused in.
+//
+// Paper: §II-C (Eqs. 7-10: K_q = |<psi(x_i)|psi(x_j)>|^2 by exact tensor-network
+// contraction), §II-B (Eq. 3: RBF), §II-D (Eq. 11: K = w K_q + (1 - w) K_c; blocks of
+// (row, column) pairs contracted by a worker).
+//
+// Design (one GPU, persistent CTAs):
+//  * A CTA owns a TR x TC tile of pairs; each thread owns one pair and keeps its chi x chi
+//    transfer matrix E in registers for all n sites (transfer.cuh).
+//  * Per site the tile needs the site tensors of TR row samples and TC column samples.
+//    With the site-major MPS layout these are two contiguous runs of samples, fetched by
+//    TMA (cp.async.bulk.tensor, 128-byte swizzle) into a STAGES-deep shared-memory ring
+//    guarded by full/empty mbarriers. Thread 0 refills the stage released one site
+//    earlier, so the copy of site k+STAGES-1 overlaps the arithmetic of site k.
+//  * The swizzle puts the 16-byte chunk c of sample t's 128-byte row at c XOR (t & 7):
+//    the 8 distinct samples that a quarter-warp reads land in 8 different bank groups.
+//  * Tiles are handed out round-robin to a grid of (SMs x resident CTAs); the symmetric
+//    Gram enumerates only the upper-triangular tiles and writes each pair twice.
+//  * Epilogue per pair: log K_q from the rescaled amplitude and the per-sample
+//    log-norms, K_q = exp(log K_q), K_c = exp(-gamma ||x_i - x_j||^2) with a compensated
+//    FP32 sum over the features, K = w K_q + (1 - w) K_c.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "transfer.cuh"
+
+namespace dk {
+
+struct GramArgs {
+  int n;
+  int row0, nrows, col0, ncols;
+  int tiles_r, tiles_c, ntiles;
+  int symmetric;
+  const float* lnorm_r;
+  const float* lnorm_c;
+  const float* x_r;
+  const float* x_c;
+  float gamma, w;
+  float* k;
+  float* kq;
+  float* kc;
+  float* lkq;
+  long long ld;
+  unsigned* status;
+};
+
+template <typename real_, int CHI_, int WTR_, int WTC_, int WR_, int WC_, int STAGES_, int MINB_>
+struct GramCfg {
+  using real = real_;
+  static constexpr int CHI = CHI_, WTR = WTR_, WTC = WTC_, WR = WR_, WC = WC_, STAGES = STAGES_, MINB = MINB_;
+  static constexpr int NWARPS = WR * WC;
+  static constexpr int NTHREADS = NWARPS * 32;
+  static constexpr int TR = WTR * WR;
+  static constexpr int TC = WTC * WC;
+  static constexpr int SITE_BYTES = 2 * CHI * CHI * 2 * int(sizeof(real));
+  static constexpr int H = SITE_BYTES / 128;              // 128-byte rows per sample-site
+  static constexpr int HBUF_R = ((TR * 128 + 1023) / 1024) * 1024;  // bytes per row-sample half buffer
+  static constexpr int HBUF_C = ((TC * 128 + 1023) / 1024) * 1024;
+  static constexpr int ROW_BOX = H * HBUF_R;
+  static constexpr int COL_BOX = H * HBUF_C;
+  static constexpr int STAGE_BYTES = ROW_BOX + COL_BOX;
+  static constexpr int TX_BYTES = (TR + TC) * SITE_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16 + 1024;
+  static_assert(SITE_BYTES % 128 == 0, "site tensor must be a whole number of 128-byte rows");
+  static_assert(WTR * WTC == 32, "warp tile must hold 32 pairs");
+  static_assert(CHI * 2 * int(sizeof(real)) <= 128, "one bond column must fit a 128-byte row");
+};
+
+// Reads one right-bond column A_s[:, col] of sample t from a swizzled stage buffer.
+template <typename real, int CHI, int HBUF>
+struct SmemCol {
+  const uint8_t* buf;  // h = 0 buffer of this side
+  int t;
+  __device__ __forceinline__ void operator()(int s, int col, real (&re)[CHI], real (&im)[CHI]) const {
+    constexpr int CPLX = 2 * int(sizeof(real));
+    constexpr int NCH = CHI * CPLX / 16;
+    const int off = (s * CHI + col) * CHI * CPLX;
+    const int h = off >> 7;
+    const int c0 = (off & 127) >> 4;
+    const uint8_t* row = buf + h * HBUF + t * 128;
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) {
+      const uint8_t* p = row + (((c0 + q) ^ (t & 7)) << 4);
+      if constexpr (sizeof(real) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        re[2 * q] = v.x;
+        im[2 * q] = v.y;
+        re[2 * q + 1] = v.z;
+        im[2 * q + 1] = v.w;
+      } else {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        re[q] = v.x;
+        im[q] = v.y;
+      }
+    }
+  }
+};
+
+__device__ __forceinline__ void decode_tile(const GramArgs& p, int t, int& ti, int& tj) {
+  if (p.symmetric) {
+    const int T = p.tiles_r;
+    const double b = 2.0 * T + 1.0;
+    int r = int((b - sqrt(b * b - 8.0 * double(t))) * 0.5);
+    if (r < 0) r = 0;
+    if (r > T - 1) r = T - 1;
+    auto start = [T](int q) { return q * T - (q * (q - 1)) / 2; };
+    while (r + 1 < T && start(r + 1) <= t) ++r;
+    while (r > 0 && start(r) > t) --r;
+    ti = r;
+    tj = r + (t - start(r));
+  } else {
+    ti = t / p.tiles_c;
+    tj = t - ti * p.tiles_c;
+  }
+}
+
+// ||a - b||^2 over n features with a compensated (Kahan) FP32 sum.
+__device__ __forceinline__ float sq_dist(const float* __restrict__ a, const float* __restrict__ b, int n) {
+  float s = 0.0f, c = 0.0f;
+  int f = 0;
+  if (((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) == 0) {
+    for (; f + 4 <= n; f += 4) {
+      const float4 va = __ldg(reinterpret_cast<const float4*>(a + f));
+      const float4 vb = __ldg(reinterpret_cast<const float4*>(b + f));
+      const float d[4] = {va.x - vb.x, va.y - vb.y, va.z - vb.z, va.w - vb.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float y = fmaf(d[u], d[u], -c);
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+      }
+    }
+  }
+  for (; f < n; ++f) {
+    const float d = __ldg(a + f) - __ldg(b + f);
+    const float y = fmaf(d, d, -c);
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  return s;
+}
+
+template <class Cfg>
+__device__ __forceinline__ void write_pair(const GramArgs& p, float half_log, int i, int j) {
+  if (i >= p.row0 + p.nrows || j >= p.col0 + p.ncols) return;
+  if (p.symmetric && j < i) return;
+  const float lr = p.lnorm_r ? p.lnorm_r[i] : 0.0f;
+  const float lc = p.lnorm_c ? p.lnorm_c[j] : 0.0f;
+  const float lkq = 2.0f * half_log - lr - lc;
+  const float kq = expf(lkq);
+  float kc = 0.0f;
+  const bool need_kc = (p.k != nullptr && p.w != 1.0f) || p.kc != nullptr;
+  if (need_kc) kc = expf(-p.gamma * sq_dist(p.x_r + size_t(i) * p.n, p.x_c + size_t(j) * p.n, p.n));
+  const float k = p.w * kq + (1.0f - p.w) * kc;
+  const long long a = (long long)(i - p.row0) * p.ld + (j - p.col0);
+  if (p.k) p.k[a] = k;
+  if (p.kq) p.kq[a] = kq;
+  if (p.kc) p.kc[a] = kc;
+  if (p.lkq) p.lkq[a] = lkq;
+  if (p.symmetric && i != j) {
+    const long long b = (long long)(j - p.col0) * p.ld + (i - p.row0);
+    if (p.k) p.k[b] = k;
+    if (p.kq) p.kq[b] = kq;
+    if (p.kc) p.kc[b] = kc;
+    if (p.lkq) p.lkq[b] = lkq;
+  }
+}
+
+template <class Cfg>
+__global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
+    gram_kernel(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_c,
+                const GramArgs p) {
+  using real = typename Cfg::real;
+  constexpr int CHI = Cfg::CHI, STAGES = Cfg::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + STAGES);
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int tr = (warp / Cfg::WC) * Cfg::WTR + lane / Cfg::WTC;
+  const int tc = (warp % Cfg::WC) * Cfg::WTC + lane % Cfg::WTC;
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], Cfg::NWARPS);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+    prefetch_tensormap(&tm_r);
+    prefetch_tensormap(&tm_c);
+  }
+  __syncthreads();
+
+  const int my_tiles = (p.ntiles > int(blockIdx.x)) ? (p.ntiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+  const long long total = (long long)my_tiles * p.n;
+
+  auto tile_origin = [&](long long local, int& r0, int& c0) {
+    int ti, tj;
+    decode_tile(p, int(blockIdx.x) + int(local) * int(gridDim.x), ti, tj);
+    r0 = p.row0 + ti * Cfg::TR;
+    c0 = p.col0 + tj * Cfg::TC;
+  };
+  auto issue = [&](long long q) {
+    const int st = int(q % STAGES);
+    const int k = int(q % p.n);
+    int r0, c0;
+    tile_origin(q / p.n, r0, c0);
+    uint8_t* base = smem + st * Cfg::STAGE_BYTES;
+    mbar_arrive_expect_tx(&full[st], Cfg::TX_BYTES);
+#pragma unroll
+    for (int h = 0; h < Cfg::H; ++h) {
+      tma_load_3d(base + h * Cfg::HBUF_R, &tm_r, &full[st], h * 32, r0, k);
+      tma_load_3d(base + Cfg::ROW_BOX + h * Cfg::HBUF_C, &tm_c, &full[st], h * 32, c0, k);
+    }
+  };
+
+  long long issued = 0;
+  if (tid == 0) {
+    for (; issued < total && issued < STAGES; ++issued) issue(issued);
+  }
+
+  Chain<real, CHI> ch;
+  ch.init();
+  int r0 = 0, c0 = 0;
+  long long q = 0;
+  for (; q < total; ++q) {
+    const int st = int(q % STAGES);
+    const uint32_t ph = uint32_t((q / STAGES) & 1);
+    const int k = int(q % p.n);
+    if (k == 0) {
+      ch.init();
+      tile_origin(q / p.n, r0, c0);
+    }
+    if (!mbar_wait_bounded(&full[st], ph)) {
+      record_status(p.status, DEV_TIMEOUT);
+      *abort_flag = 1;
+      break;
+    }
+    const uint8_t* base = smem + st * Cfg::STAGE_BYTES;
+    const SmemCol<real, CHI, Cfg::HBUF_R> ldi{base, tr};
+    const SmemCol<real, CHI, Cfg::HBUF_C> ldj{base + Cfg::ROW_BOX, tc};
+    ch.step(ldi, ldj);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+    if (tid == 0 && q >= 1 && issued < total) {
+      const long long qq = q - 1;
+      if (!mbar_wait_bounded(&empty[qq % STAGES], uint32_t((qq / STAGES) & 1))) {
+        record_status(p.status, DEV_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      issue(issued);
+      ++issued;
+    }
+    if (k == p.n - 1) write_pair<Cfg>(p, ch.half_log_mod(), r0 + tr, c0 + tc);
+    if (*abort_flag) break;
+  }
+  // On an early exit, let the copies already issued land before the CTA leaves.
+  if (tid == 0) {
+    for (long long qq = q; qq < issued; ++qq) {
+      if (!mbar_wait_bounded(&full[qq % STAGES], uint32_t((qq / STAGES) & 1))) break;
+    }
+  }
+}
+
+template <class Cfg>
+struct GramLauncher {
+  static dk_status run(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, const GramArgs& a,
+                       cudaStream_t st) {
+    CUtensorMap tmr, tmc;
+    dk_status s = encode_mps_map(ctx, &tmr, mps_r, m_r, a.n, Cfg::SITE_BYTES, Cfg::TR);
+    if (s != DK_OK) return s;
+    s = encode_mps_map(ctx, &tmc, mps_c, m_c, a.n, Cfg::SITE_BYTES, Cfg::TC);
+    if (s != DK_OK) return s;
+    auto kern = gram_kernel<Cfg>;
+    static int occ = -1;  // resident CTAs per SM, per instantiation
+    if (occ < 0) {
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES) != cudaSuccess)
+        return DK_ERR_CUDA;
+      int o = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Cfg::NTHREADS, Cfg::SMEM_BYTES) != cudaSuccess)
+        return DK_ERR_CUDA;
+      occ = o > 0 ? o : 1;
+    }
+    long long grid = (long long)ctx->sm_count * occ;
+    if (grid > a.ntiles) grid = a.ntiles;
+    if (grid < 1) return DK_OK;
+    kern<<<int(grid), Cfg::NTHREADS, Cfg::SMEM_BYTES, st>>>(tmr, tmc, a);
+    return launch_status();
+  }
+};
+
+// Tile shapes: 4 x 8 pairs per warp, 4 x 2 warps -> 16 x 16 pairs per CTA.
+using CfgF32x4 = GramCfg<float, 4, 4, 8, 4, 2, 4, 1>;
+using CfgF64x2 = GramCfg<double, 2, 4, 8, 4, 2, 4, 1>;
+using CfgF64x4 = GramCfg<double, 4, 4, 8, 4, 2, 4, 1>;
+
+template <class Cfg>
+static dk_status launch_gram(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
+                             cudaStream_t st) {
+  a.tiles_r = (a.nrows + Cfg::TR - 1) / Cfg::TR;
+  a.tiles_c = (a.ncols + Cfg::TC - 1) / Cfg::TC;
+  if (a.symmetric) {
+    if (Cfg::TR != Cfg::TC) return DK_ERR_UNSUPPORTED;
+    a.ntiles = a.tiles_r * (a.tiles_r + 1) / 2;
+  } else {
+    a.ntiles = a.tiles_r * a.tiles_c;
+  }
+  return GramLauncher<Cfg>::run(ctx, mps_r, m_r, mps_c, m_c, a, st);
+}
+
+static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, int chi,
+                               dk_dtype dtype, dk_precision prec, const GramArgs& a, cudaStream_t st) {
+  if (dtype == DK_C64 && prec == DK_PREC_F32 && chi == 4)
+    return launch_gram<CfgF32x4>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+  if (dtype == DK_C128 && prec == DK_PREC_F64 && chi == 2)
+    return launch_gram<CfgF64x2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+  if (dtype == DK_C128 && prec == DK_PREC_F64 && chi == 4)
+    return launch_gram<CfgF64x4>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+  return DK_ERR_UNSUPPORTED;
+}
+
+}  // namespace dk
+
+DK_API dk_status dk_gram_tile(dk_ctx* ctx, const void* mps_rows, int m_rows, const void* mps_cols, int m_cols,
+                              int n, int chi_max, dk_dtype dtype, int row0, int nrows, int col0, int ncols,
+                              const float* log_norm_rows, const float* log_norm_cols, const float* x_rows,
+                              const float* x_cols, float gamma, float w, dk_precision prec, float* k_out,
+                              float* kq_out, float* kc_out, float* logkq_out, int64_t ld, int symmetric,
+                              void* stream) {
+  using namespace dk;
+  if (!ctx || !mps_rows || !mps_cols || n < 1 || m_rows < 1 || m_cols < 1) return DK_ERR_ARG;
+  if (row0 < 0 || nrows < 0 || col0 < 0 || ncols < 0) return DK_ERR_ARG;
+  if ((long long)row0 + nrows > m_rows || (long long)col0 + ncols > m_cols) return DK_ERR_ARG;
+  if (!aligned16(mps_rows) || !aligned16(mps_cols)) return DK_ERR_ARG;
+  const bool any_out = k_out || kq_out || kc_out || logkq_out;
+  if (any_out && ld < ncols) return DK_ERR_ARG;
+  if (symmetric) {
+    if (mps_rows != mps_cols || row0 != col0 || nrows != ncols || m_rows != m_cols) return DK_ERR_ARG;
+    if (x_rows != x_cols || log_norm_rows != log_norm_cols) return DK_ERR_ARG;
+    if (any_out && ld < nrows) return DK_ERR_ARG;
+  }
+  const bool need_x = kc_out != nullptr || (k_out != nullptr && w != 1.0f);
+  if (need_x && (!x_rows || !x_cols)) return DK_ERR_ARG;
+  if (!(w >= 0.0f && w <= 1.0f)) return DK_ERR_ARG;
+  if (nrows == 0 || ncols == 0 || !any_out) return DK_OK;
+
+  GramArgs a{};
+  a.n = n;
+  a.row0 = row0;
+  a.nrows = nrows;
+  a.col0 = col0;
+  a.ncols = ncols;
+  a.symmetric = symmetric ? 1 : 0;
+  a.lnorm_r = log_norm_rows;
+  a.lnorm_c = log_norm_cols;
+  a.x_r = x_rows;
+  a.x_c = x_cols;
+  a.gamma = gamma;
+  a.w = w;
+  a.k = k_out;
+  a.kq = kq_out;
+  a.kc = kc_out;
+  a.lkq = logkq_out;
+  a.ld = ld;
+  a.status = ctx->status;
+  return gram_dispatch(ctx, mps_rows, m_rows, mps_cols, m_cols, chi_max, dtype, prec, a,
+                       static_cast<cudaStream_t>(stream));
+}
+
+DK_API dk_status dk_dual_kernel_rows(dk_ctx* ctx, const void* mps_test, const float* x_test,
+                                     const float* log_norm_test, int b, const void* mps_train, const float* x_train,
+                                     const float* log_norm_train, int m, int n, int chi_max, dk_dtype dtype,
+                                     float gamma, float w, dk_precision prec, float* k_out, float* kq_out,
+                                     float* kc_out, float* logkq_out, void* stream) {
+  if (b == 0) return ctx ? DK_OK : DK_ERR_ARG;
+  return dk_gram_tile(ctx, mps_test, b, mps_train, m, n, chi_max, dtype, 0, b, 0, m, log_norm_test, log_norm_train,
+                      x_test, x_train, gamma, w, prec, k_out, kq_out, kc_out, logkq_out, m, 0, stream);
+}

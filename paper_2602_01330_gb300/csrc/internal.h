@@ -1,0 +1,42 @@
+// Host-side internals shared by the translation units of libdualk.so.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dualk.h"
+
+#define DK_API extern "C" __attribute__((visibility("default")))
+
+typedef CUresult (*dk_encode_tiled_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                       const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                       CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct dk_ctx {
+  int device;
+  int sm_count;
+  int cc_major, cc_minor;
+  unsigned* status;  // device word, bits of dk::DEV_*
+  dk_encode_tiled_fn encode_tiled;
+};
+
+namespace dk {
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline size_t site_bytes(int chi_max, dk_dtype dtype) {
+  return size_t(2) * chi_max * chi_max * (dtype == DK_C64 ? 8 : 16);
+}
+
+// Tensor map over an MPS buffer viewed as [n sites][m samples][site_bytes/4 floats]:
+// box = 32 floats (128 B) x `box_samples` samples x 1 site, 128-byte swizzle.
+dk_status encode_mps_map(dk_ctx* ctx, CUtensorMap* map, const void* mps, int m, int n, size_t site_bytes,
+                         int box_samples);
+
+inline dk_status launch_status() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DK_OK : DK_ERR_CUDA;
+}
+
+}  // namespace dk

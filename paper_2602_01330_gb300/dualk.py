@@ -1,0 +1,226 @@
+"""ctypes binding of libdualk.so (include/dualk.h), names matching the C ABI.
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels. Tensors are torch CUDA tensors (PyTorch provides device memory and streams);
+outputs are allocated here with torch when the caller does not pass them. If the
+library is not built, or no sm_10x device is visible, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdualk.so")
+
+DK_OK = 0
+DK_C64, DK_C128 = 0, 1
+DK_PREC_F32, DK_PREC_F64 = 0, 1
+
+_STATUS_NAMES = {0: "DK_OK", 1: "DK_ERR_ARG", 2: "DK_ERR_UNSUPPORTED", 3: "DK_ERR_CUDA",
+                 4: "DK_ERR_TIMEOUT", 5: "DK_ERR_WORKSPACE", 6: "DK_ERR_NO_DEVICE"}
+
+EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_mps_bytes",
+            "dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows")
+
+
+class DualKError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_STATUS_NAMES.get(status, status)} ({_lib().dk_error_string(status).decode()})")
+
+
+class _Fmap(ctypes.Structure):
+    _fields_ = [("reps", ctypes.c_int), ("angle_scale", ctypes.c_float),
+                ("entangle", ctypes.c_int), ("chi_max", ctypes.c_int)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2602_01330_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
+    lib.dk_create.argtypes = [ctypes.POINTER(vp), i32]
+    lib.dk_create.restype = i32
+    lib.dk_destroy.argtypes = [vp]
+    lib.dk_destroy.restype = None
+    lib.dk_error_string.argtypes = [i32]
+    lib.dk_error_string.restype = ctypes.c_char_p
+    lib.dk_sync_status.argtypes = [vp, vp]
+    lib.dk_sync_status.restype = i32
+    lib.dk_mps_bytes.argtypes = [i32, i32, i32, i32]
+    lib.dk_mps_bytes.restype = ctypes.c_size_t
+    lib.dk_mps_build.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, vp, vp, vp, vp]
+    lib.dk_mps_build.restype = i32
+    lib.dk_gram_tile.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, i32,
+                                 vp, vp, vp, vp, f32, f32, i32, vp, vp, vp, vp, i64, i32, vp]
+    lib.dk_gram_tile.restype = i32
+    lib.dk_dual_kernel_rows.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, i32, i32, i32, i32,
+                                        f32, f32, i32, vp, vp, vp, vp, vp]
+    lib.dk_dual_kernel_rows.restype = i32
+    _LIB = lib
+    return lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(status: int, what: str):
+    if status != DK_OK:
+        raise DualKError(status, what)
+
+
+def _need_cuda(t, name, dtype=None):
+    if t is None:
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}")
+
+
+@dataclass
+class FeatureMap:
+    """ZZ-chain feature map: reps x (H, RZ(angle_scale x_i), RZZ chain); see include/dualk.h."""
+    reps: int = 2
+    angle_scale: float = 2.0
+    entangle: bool = True
+    chi_max: int = 4
+
+    def _c(self):
+        return _Fmap(self.reps, self.angle_scale, 1 if self.entangle else 0, self.chi_max)
+
+
+@dataclass
+class MPS:
+    """Device MPS batch as written by mps_build (site-major, see include/dualk.h)."""
+    data: torch.Tensor        # uint8 bytes
+    m: int
+    n: int
+    chi_max: int
+    dtype: int                # DK_C64 / DK_C128
+    bond_dims: torch.Tensor   # int32, n + 1
+    log_norm: torch.Tensor    # float32, m
+    x: torch.Tensor           # float32 m x n features it was built from
+
+    def complex_view(self):
+        ct = torch.complex64 if self.dtype == DK_C64 else torch.complex128
+        return self.data.view(ct).view(self.n, self.m, 2, self.chi_max, self.chi_max)
+
+
+class Context:
+    """dk_ctx on one device."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib().dk_create(ctypes.byref(h), int(device)), "dk_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            _lib().dk_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync_status(self, stream=None):
+        _check(_lib().dk_sync_status(self.handle, _stream(stream)), "dk_sync_status")
+
+
+def mps_bytes(m: int, n: int, chi_max: int, dtype: int = DK_C64) -> int:
+    return int(_lib().dk_mps_bytes(m, n, chi_max, dtype))
+
+
+def mps_build(ctx: Context, x: torch.Tensor, fmap: FeatureMap, dtype: int = DK_C64,
+              out: torch.Tensor | None = None, stream=None) -> MPS:
+    """dk_mps_build: MPS of |psi(x_i)> for the rows of x (m x n float32, CUDA)."""
+    _need_cuda(x, "x", torch.float32)
+    m, n = x.shape
+    nbytes = mps_bytes(m, n, fmap.chi_max, dtype)
+    if out is None:
+        out = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
+    elif out.numel() * out.element_size() < nbytes:
+        raise ValueError("out is too small for the MPS")
+    bond = torch.empty(n + 1, dtype=torch.int32, device=x.device)
+    lnorm = torch.empty(m, dtype=torch.float32, device=x.device)
+    fm = fmap._c()
+    _check(_lib().dk_mps_build(ctx.handle, _ptr(x), m, n, ctypes.byref(fm), dtype, _ptr(out), _ptr(bond),
+                               _ptr(lnorm), _stream(stream)), "dk_mps_build")
+    return MPS(out, m, n, fmap.chi_max, dtype, bond, lnorm, x)
+
+
+def _outs(shape, device, want):
+    return {k: (torch.empty(shape, dtype=torch.float32, device=device) if k in want else None)
+            for k in ("k", "kq", "kc", "logkq")}
+
+
+def gram_tile(ctx: Context, rows: MPS, cols: MPS, row0: int = 0, nrows: int | None = None,
+              col0: int = 0, ncols: int | None = None, gamma: float | None = None, w: float = 0.5,
+              want=("k", "kq", "kc", "logkq"), symmetric: bool = False, out=None, ld: int | None = None,
+              stream=None):
+    """dk_gram_tile: the (nrows x ncols) block of K, K_q, K_c, log K_q (dict of tensors)."""
+    nrows = rows.m - row0 if nrows is None else nrows
+    ncols = cols.m - col0 if ncols is None else ncols
+    if rows.n != cols.n or rows.chi_max != cols.chi_max or rows.dtype != cols.dtype:
+        raise ValueError("row and column MPS differ in n, chi_max or dtype")
+    gamma = 1.0 / rows.n if gamma is None else gamma
+    if out is None:
+        out = _outs((nrows, ncols), rows.data.device, want)
+        ld = ncols
+    elif ld is None:
+        raise ValueError("ld is required with caller-provided outputs")
+    prec = DK_PREC_F32 if rows.dtype == DK_C64 else DK_PREC_F64
+    _check(_lib().dk_gram_tile(ctx.handle, _ptr(rows.data), rows.m, _ptr(cols.data), cols.m, rows.n,
+                               rows.chi_max, rows.dtype, row0, nrows, col0, ncols, _ptr(rows.log_norm),
+                               _ptr(cols.log_norm), _ptr(rows.x), _ptr(cols.x), float(gamma), float(w), prec,
+                               _ptr(out.get("k")), _ptr(out.get("kq")), _ptr(out.get("kc")),
+                               _ptr(out.get("logkq")), int(ld), 1 if symmetric else 0, _stream(stream)),
+           "dk_gram_tile")
+    return out
+
+
+def gram(ctx: Context, mps: MPS, gamma: float | None = None, w: float = 0.5,
+         want=("k", "kq", "kc", "logkq"), stream=None):
+    """Full symmetric m x m Gram of one MPS batch (each unordered pair contracted once)."""
+    return gram_tile(ctx, mps, mps, gamma=gamma, w=w, want=want, symmetric=True, stream=stream)
+
+
+def dual_kernel_rows(ctx: Context, test: MPS, train: MPS, gamma: float | None = None, w: float = 0.5,
+                     want=("k", "kq", "kc", "logkq"), out=None, stream=None):
+    """dk_dual_kernel_rows: the b x m block K(test, train)."""
+    if test.n != train.n or test.chi_max != train.chi_max or test.dtype != train.dtype:
+        raise ValueError("test and train MPS differ in n, chi_max or dtype")
+    gamma = 1.0 / train.n if gamma is None else gamma
+    if out is None:
+        out = _outs((test.m, train.m), train.data.device, want)
+    prec = DK_PREC_F32 if train.dtype == DK_C64 else DK_PREC_F64
+    _check(_lib().dk_dual_kernel_rows(ctx.handle, _ptr(test.data), _ptr(test.x), _ptr(test.log_norm), test.m,
+                                      _ptr(train.data), _ptr(train.x), _ptr(train.log_norm), train.m, train.n,
+                                      train.chi_max, train.dtype, float(gamma), float(w), prec,
+                                      _ptr(out.get("k")), _ptr(out.get("kq")), _ptr(out.get("kc")),
+                                      _ptr(out.get("logkq")), _stream(stream)),
+           "dk_dual_kernel_rows")
+    return out

@@ -1,0 +1,40 @@
+"""Work accounting for the transfer-chain Gram (units, algorithmic flops and bytes).
+
+Unit of work: one entry x qubit = one (row, column) pair advanced through one site of
+the transfer chain. For a pair the exact bond dimensions of the ZZ-chain MPS are
+D_k = min(2^k, 2^(n-k), 2^reps) (D_0 = D_n = 1), and site k costs
+4 D_{k-1} D_k (D_{k-1} + D_k) complex multiply-adds = 16 (D_{k-1}^2 D_k + D_{k-1} D_k^2)
+real flops (F = E A_s(x_j): D_{k-1}^2 D_k per s; E' += A_s(x_i)^dagger F: D_{k-1} D_k^2 per
+s; 4 real FMAs = 8 flops per complex multiply-add). At D = 4 that is 2048 flops.
+"""
+from __future__ import annotations
+
+from functools import lru_cache
+
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
+
+
+def exact_bonds(n: int, reps: int):
+    return [min(2 ** k, 2 ** (n - k), 2 ** reps) for k in range(n + 1)]
+
+
+@lru_cache(maxsize=None)
+def flops_per_pair(n: int, reps: int) -> int:
+    d = exact_bonds(n, reps)
+    return sum(16 * (d[k - 1] ** 2 * d[k] + d[k - 1] * d[k] ** 2) for k in range(1, n + 1))
+
+
+def gram_entries(m: int, symmetric: bool = True, b: int | None = None) -> int:
+    """Unique entries: m(m+1)/2 for a symmetric Gram, b*m for a row block."""
+    if symmetric:
+        return m * (m + 1) // 2
+    return int(b) * m
+
+
+def fp32_peak_tflops(sm_count: int, sm_mhz: float) -> float:
+    """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
+    return sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def mps_site_bytes(chi_max: int, complex_bytes: int = 8) -> int:
+    return 2 * chi_max * chi_max * complex_bytes

@@ -1,0 +1,87 @@
+"""The C-ABI library builds, loads and exports every symbol include/dualk.h declares.
+
+CPU only: no kernel is launched. Calls made here either fail argument validation on
+the host or find no device.
+"""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dualk.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dk_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2602_01330_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows"):
+        assert name in syms
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), f"{name} declared in dualk.h but not exported"
+
+
+def test_binding_names_match_header():
+    from paper_2602_01330_gb300 import dualk
+    assert sorted(dualk.EXPORTED) == declared_symbols()
+
+
+def test_only_dk_symbols_exported(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", os.path.join(ROOT, "paper_2602_01330_gb300", "libdualk.so")],
+                         capture_output=True, text=True).stdout
+    names = [ln.split()[-1] for ln in out.splitlines() if ln.strip() and ln.split()[1] in ("T", "t")]
+    assert names and all(n.startswith("dk_") for n in names if not n.startswith("_"))
+
+
+def test_error_strings_and_host_validation(lib):
+    lib.dk_error_string.restype = ctypes.c_char_p
+    assert lib.dk_error_string(0) == b"ok"
+    assert b"argument" in lib.dk_error_string(1)
+    lib.dk_mps_bytes.restype = ctypes.c_size_t
+    assert lib.dk_mps_bytes(10, 7, 4, 0) == 10 * 7 * 2 * 4 * 4 * 8
+    assert lib.dk_mps_bytes(10, 7, 2, 1) == 10 * 7 * 2 * 2 * 2 * 16
+    assert lib.dk_mps_bytes(0, 7, 4, 0) == 0
+    # NULL context / pointers are rejected on the host before any CUDA call.
+    assert lib.dk_mps_build(None, None, 1, 1, None, 0, None, None, None, None) == 1
+    assert lib.dk_gram_tile(None, None, 1, None, 1, 1, 4, 0, 0, 1, 0, 1, None, None, None, None,
+                            ctypes.c_float(1.0), ctypes.c_float(0.5), 0, None, None, None, None,
+                            ctypes.c_int64(1), 0, None) == 1
+
+
+def test_create_without_device_reports_no_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is visible")
+    h = ctypes.c_void_p()
+    assert lib.dk_create(ctypes.byref(h), 0) == 6  # DK_ERR_NO_DEVICE
+
+
+def test_workload_accounting():
+    from paper_2602_01330_gb300 import workload
+    assert workload.exact_bonds(6, 2) == [1, 2, 4, 4, 4, 2, 1]
+    # n = 3: D = 1, 2, 2, 1 -> 16 (1*2 + 1*4) + 16 (4*2 + 2*4) + 16 (4*1 + 2*1) = 448
+    assert workload.flops_per_pair(3, 5) == 448
+    # n = 784, reps = 2: 780 interior sites at D = 4 cost 2048 flops each
+    edge = 16 * (1 * 2 + 1 * 4) + 16 * (4 * 4 + 2 * 16) + 16 * (16 * 2 + 4 * 4) + 16 * (4 * 1 + 2 * 1)
+    assert workload.flops_per_pair(784, 2) == 780 * 2048 + edge
+    assert workload.gram_entries(4) == 10 and workload.gram_entries(4, False, 3) == 12

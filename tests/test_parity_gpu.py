@@ -1,0 +1,219 @@
+"""GPU parity: every C-ABI entry point against the FP64 oracle on the same seeded inputs.
+
+Tolerance (written here, used below): |dK| <= 1e-6 for K, K_q and K_c on the FP32
+path (complex64 MPS, FP32 transfer arithmetic, float32 outputs); log K_q within
+1e-3 * max(1, |log K_q|) wherever the oracle's log K_q > -700. The complex128 path
+also writes float32 outputs, so it is held to the same 1e-6.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL_K = 1e-6
+
+
+def _tol_log(ref):
+    return 1e-3 * np.maximum(1.0, np.abs(ref))
+
+
+@pytest.fixture(scope="module")
+def dk():
+    import torch
+    from paper_2602_01330_gb300 import build, dualk
+    build.build()
+    ctx = dualk.Context(0)
+    yield dualk, ctx, torch
+    ctx.close()
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _oracle_block(x_rows, x_cols, reps, entangle=True, angle_scale=2.0):
+    from oracle import gram, mps
+    r, _ = mps.build_mps(x_rows.astype(np.float64), reps, angle_scale, entangle)
+    c, _ = mps.build_mps(x_cols.astype(np.float64), reps, angle_scale, entangle)
+    return gram.gram_from_mps(r, c)
+
+
+def _check_block(out, kq_ref, lkq_ref, kc_ref, w):
+    kq = out["kq"].cpu().numpy().astype(np.float64)
+    kc = out["kc"].cpu().numpy().astype(np.float64)
+    k = out["k"].cpu().numpy().astype(np.float64)
+    lkq = out["logkq"].cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(kq - kq_ref)) <= TOL_K
+    assert np.max(np.abs(kc - kc_ref)) <= TOL_K
+    assert np.max(np.abs(k - (w * kq_ref + (1 - w) * kc_ref))) <= TOL_K
+    sel = lkq_ref > -700
+    assert np.all(np.abs(lkq[sel] - lkq_ref[sel]) <= _tol_log(lkq_ref[sel]))
+
+
+def test_tiny_case_complex128_vs_statevector(dk):
+    """n = 8, 64 samples uniform in [0, pi] (seed 0), reps = 1, complex128 chi <= 2:
+    the full 64 x 64 K_q against brute-force 256-amplitude statevectors."""
+    dualk, ctx, torch = dk
+    from oracle import circuit
+    from paper_2602_01330_gb300 import synthetic
+    x = synthetic.uniform_angles(64, 8, seed=0)
+    ref = circuit.kernel_matrix(x, x, 1)
+    m = dualk.mps_build(ctx, _dev(torch, x), dualk.FeatureMap(reps=1, chi_max=2), dtype=dualk.DK_C128)
+    out = dualk.gram(ctx, m, w=1.0)
+    torch.cuda.synchronize()
+    kq = out["kq"].cpu().numpy()
+    assert np.max(np.abs(kq - ref)) <= TOL_K
+    assert np.array_equal(kq, kq.T)
+    assert np.all(np.diag(kq) == 1.0)
+    stored = np.loadtxt(__import__("os").path.join(__import__("os").path.dirname(__file__), "golden", "cfg1_kq16.txt"))
+    assert np.max(np.abs(kq[:16, :16] - stored)) <= TOL_K
+    assert m.bond_dims.cpu().tolist() == [1, 2, 2, 2, 2, 2, 2, 2, 1]
+    ctx.sync_status()
+
+
+@pytest.mark.parametrize("reps,chi,dtype", [(1, 4, "c64"), (2, 4, "c64"), (1, 2, "c128"), (2, 4, "c128")])
+def test_small_n_vs_statevector(dk, reps, chi, dtype):
+    dualk, ctx, torch = dk
+    from oracle import circuit
+    from paper_2602_01330_gb300 import synthetic
+    x = synthetic.uniform_angles(37, 10, seed=5)
+    ref = circuit.kernel_matrix(x, x, reps)
+    dt = dualk.DK_C64 if dtype == "c64" else dualk.DK_C128
+    m = dualk.mps_build(ctx, _dev(torch, x), dualk.FeatureMap(reps=reps, chi_max=chi), dtype=dt)
+    out = dualk.gram(ctx, m, w=1.0)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(out["kq"].cpu().numpy() - ref)) <= TOL_K
+
+
+def test_fmnist_d64_reps2_all_mixes(dk):
+    """d = 64 Fashion-MNIST-shaped features, reps = 2 (chi = 4), complex64: Gram of 200
+    train samples (12 full 16-tiles + a ragged one) and 50 x 200 dual-kernel rows, at
+    w in {0, 0.25, 0.5, 0.75, 1}, element by element against the oracle."""
+    dualk, ctx, torch = dk
+    from oracle import gram as og
+    from paper_2602_01330_gb300 import synthetic
+    d = synthetic.fmnist_like(200, 50, 64)
+    xtr, xte = d["x_train"], d["x_test"]
+    kq_tr, lkq_tr = _oracle_block(xtr, xtr, 2)
+    kq_te, lkq_te = _oracle_block(xte, xtr, 2)
+    kc_tr = og.rbf(xtr, xtr, 1 / 64)
+    kc_te = og.rbf(xte, xtr, 1 / 64)
+    fm = dualk.FeatureMap(reps=2, chi_max=4)
+    mtr = dualk.mps_build(ctx, _dev(torch, xtr), fm)
+    mte = dualk.mps_build(ctx, _dev(torch, xte), fm)
+    for w in (0.0, 0.25, 0.5, 0.75, 1.0):
+        out = dualk.gram(ctx, mtr, w=w)
+        rows = dualk.dual_kernel_rows(ctx, mte, mtr, w=w)
+        torch.cuda.synchronize()
+        _check_block(out, kq_tr, lkq_tr, kc_tr, w)
+        _check_block(rows, kq_te, lkq_te, kc_te, w)
+    ctx.sync_status()
+
+
+def test_gram_invariants_and_determinism(dk):
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    x = synthetic.fmnist_like(150, 0, 64)["x_train"]
+    m = dualk.mps_build(ctx, _dev(torch, x), dualk.FeatureMap(reps=2, chi_max=4))
+    out = dualk.gram(ctx, m, w=1.0)
+    rows = dualk.dual_kernel_rows(ctx, m, m, w=1.0)
+    blk = dualk.gram_tile(ctx, m, m, row0=17, nrows=60, col0=40, ncols=77, w=1.0)
+    torch.cuda.synchronize()
+    kq = out["kq"].cpu().numpy()
+    assert np.array_equal(kq, kq.T)
+    assert np.all(np.diag(kq) == 1.0)
+    assert kq.min() >= 0.0 and kq.max() <= 1.0 + 1e-6
+    lam = np.linalg.eigvalsh(kq.astype(np.float64))
+    assert lam.min() >= -150 * 1e-6
+    # the same pair gives the same bits whatever tile or call computes it
+    r = rows["kq"].cpu().numpy()
+    iu = np.triu_indices(150)
+    assert np.array_equal(r[iu], kq[iu])
+    b = blk["kq"].cpu().numpy()
+    sub = kq[17:77, 40:117]
+    ii, jj = np.meshgrid(np.arange(17, 77), np.arange(40, 117), indexing="ij")
+    upper = ii <= jj
+    assert np.array_equal(b[upper], sub[upper])
+
+
+def test_edge_cases(dk):
+    dualk, ctx, torch = dk
+    from oracle import circuit, gram as og
+    from paper_2602_01330_gb300 import synthetic
+    fm = dualk.FeatureMap(reps=2, chi_max=4)
+    # n = 1 and n = 2 qubits, m = 1 sample, odd sizes
+    for n, msz in ((1, 5), (2, 3), (3, 1), (5, 19)):
+        x = synthetic.uniform_angles(msz, n, seed=n)
+        ref = circuit.kernel_matrix(x, x, 2)
+        m = dualk.mps_build(ctx, _dev(torch, x), fm)
+        out = dualk.gram(ctx, m, w=0.5)
+        torch.cuda.synchronize()
+        assert np.max(np.abs(out["kq"].cpu().numpy() - ref)) <= TOL_K
+        kc = og.rbf(x, x, 1.0 / n)
+        assert np.max(np.abs(out["kc"].cpu().numpy() - kc)) <= TOL_K
+    # entanglers off: product closed form
+    x = synthetic.uniform_angles(20, 30, seed=9)
+    m = dualk.mps_build(ctx, _dev(torch, x), dualk.FeatureMap(reps=1, entangle=False, chi_max=4))
+    out = dualk.gram(ctx, m, w=1.0, want=("kq",))
+    torch.cuda.synchronize()
+    xx = x.astype(np.float32).astype(np.float64)
+    ref = np.prod(np.cos(xx[:, None, :] - xx[None, :, :]) ** 2, axis=2)
+    assert np.max(np.abs(out["kq"].cpu().numpy() - ref)) <= TOL_K
+    # only one output requested, ld larger than the block, into a bigger buffer
+    x = synthetic.uniform_angles(40, 12, seed=10)
+    m = dualk.mps_build(ctx, _dev(torch, x), fm)
+    big = torch.full((50, 64), -7.0, device="cuda")
+    dualk.gram_tile(ctx, m, m, row0=3, nrows=20, col0=5, ncols=30, w=1.0, out={"kq": big}, ld=64)
+    full = dualk.gram(ctx, m, w=1.0, want=("kq",))
+    torch.cuda.synchronize()
+    bb = big.cpu().numpy()
+    assert np.all(bb[20:, :] == -7.0) and np.all(bb[:, 30:] == -7.0)
+    np.testing.assert_array_equal(bb[:20, :30], full["kq"].cpu().numpy()[3:23, 5:35])
+
+
+def test_host_errors(dk):
+    dualk, ctx, torch = dk
+    x = torch.rand(4, 6, device="cuda") * 3
+    with pytest.raises(dualk.DualKError) as e:
+        dualk.mps_build(ctx, x, dualk.FeatureMap(reps=3, chi_max=4))  # needs chi >= 8
+    assert e.value.status == 2
+    with pytest.raises(dualk.DualKError) as e:
+        dualk.mps_build(ctx, x, dualk.FeatureMap(reps=0, chi_max=4))
+    assert e.value.status == 1
+    m = dualk.mps_build(ctx, x, dualk.FeatureMap(reps=2, chi_max=4))
+    with pytest.raises(dualk.DualKError) as e:
+        dualk.gram_tile(ctx, m, m, row0=2, nrows=3)  # runs past the 4 samples
+    assert e.value.status == 1
+    ctx.sync_status()
+
+
+def test_n784_bench_shape_sampled(dk):
+    """The benchmarked workload: d = 784 raw pixels, 2000 train + 500 test, reps = 2,
+    chi = 4, in the bench launch configuration; 64 train samples (Gram block) and 16
+    test samples (rows) are checked element by element against the oracle."""
+    dualk, ctx, torch = dk
+    from oracle import gram as og
+    from paper_2602_01330_gb300 import synthetic
+    d = synthetic.fmnist_like(2000, 500, 784)
+    xtr, xte = d["x_train"], d["x_test"]
+    fm = dualk.FeatureMap(reps=2, chi_max=4)
+    mtr = dualk.mps_build(ctx, _dev(torch, xtr), fm)
+    mte = dualk.mps_build(ctx, _dev(torch, xte), fm)
+    out = dualk.gram(ctx, mtr, w=0.5)
+    rows = dualk.dual_kernel_rows(ctx, mte, mtr, w=0.5)
+    torch.cuda.synchronize()
+    rng = np.random.Generator(np.random.PCG64(7))
+    si = np.sort(rng.choice(2000, 64, replace=False))
+    ti = np.sort(rng.choice(500, 16, replace=False))
+    kq_ref, lkq_ref = _oracle_block(xtr[si], xtr[si], 2)
+    kc_ref = og.rbf(xtr[si], xtr[si], 1 / 784)
+    sub = {k: v[si][:, si] for k, v in out.items()}
+    _check_block(sub, kq_ref, lkq_ref, kc_ref, 0.5)
+    kq_ref, lkq_ref = _oracle_block(xte[ti], xtr[si], 2)
+    kc_ref = og.rbf(xte[ti], xtr[si], 1 / 784)
+    sub = {k: v[ti][:, si] for k, v in rows.items()}
+    _check_block(sub, kq_ref, lkq_ref, kc_ref, 0.5)
+    kq = out["kq"]
+    assert bool(torch.all(torch.diagonal(kq) == 1.0))
+    assert bool(torch.equal(kq, kq.T))
+    ctx.sync_status()
