@@ -162,6 +162,42 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def end_to_end(torch, tdist, args, world, stream, flush, x_tr, x_te, g_out, r_out, data, step, units_step,
+               barrier, dev):
+    """The same metric through the public API: pinned host inputs copied in and the K blocks
+    copied out inside the timed region, every step."""
+    n_tr, n_te = x_tr.shape[0], x_te.shape[0]
+    h_xtr = torch.from_numpy(data["x_train"]).pin_memory()
+    h_xte = torch.from_numpy(data["x_test"]).pin_memory()
+    h_k = torch.empty((n_tr, n_tr), dtype=torch.float32).pin_memory()
+    h_r = torch.empty((n_te, n_tr), dtype=torch.float32).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        x_tr.copy_(h_xtr, non_blocking=True)
+        x_te.copy_(h_xte, non_blocking=True)
+        step()
+        h_k.copy_(g_out["k"], non_blocking=True)
+        h_r.copy_(r_out["k"], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = world * units_step * args.steps / (e2e_ms / 1e3)
+    h2d = h_xtr.numel() * 4 + h_xte.numel() * 4
+    d2h = h_k.numel() * 4 + h_r.numel() * 4
+    return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+
 def run_ours(args):
     import torch
     import torch.distributed as tdist
@@ -191,20 +227,23 @@ def run_ours(args):
     r_out = {k: torch.empty((n_te, n_tr), dtype=torch.float32, device=dev) for k in ("k", "kq", "kc", "logkq")}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
-    gram_events = []
+    phase_events = []  # per timed step: events before build, Gram, rows, and after rows
 
     def step(record=False):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+        if record:
+            ev[0].record(stream)
         mtr = dualk.mps_build(ctx, x_tr, fm, out=mps_tr)
         mte = dualk.mps_build(ctx, x_te, fm, out=mps_te)
         if record:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            ev[1].record(stream)
         dualk.gram_tile(ctx, mtr, mtr, symmetric=True, w=w, out=g_out, ld=n_tr)
         if record:
-            e1.record(stream)
-            gram_events.append((e0, e1))
+            ev[2].record(stream)
         dualk.dual_kernel_rows(ctx, mte, mtr, w=w, out=r_out)
+        if record:
+            ev[3].record(stream)
+            phase_events.append(ev)
 
     launches_per_step = 2 + 2 + 1 + 1  # (build + self-overlap) x 2, Gram, rows
 
@@ -237,39 +276,18 @@ def run_ours(args):
         tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
         ms = float(tt.item())
     ctx.sync_status()
-    gram_ms = [a.elapsed_time(b) for a, b in gram_events]
+    gram_ms = [ev[1].elapsed_time(ev[2]) for ev in phase_events]
+    phases = {"mps_build_ms": statistics.mean(ev[0].elapsed_time(ev[1]) for ev in phase_events),
+              "gram_ms": statistics.mean(gram_ms),
+              "rows_ms": statistics.mean(ev[2].elapsed_time(ev[3]) for ev in phase_events)}
 
     units_step = entries_per_step(n_tr, n_te) * d
     value = world * units_step * args.steps / (ms / 1e3)
 
-    # End to end through the public API: pinned host inputs in, K blocks out, every step.
-    h_xtr = torch.from_numpy(data["x_train"]).pin_memory()
-    h_xte = torch.from_numpy(data["x_test"]).pin_memory()
-    h_k = torch.empty((n_tr, n_tr), dtype=torch.float32).pin_memory()
-    h_r = torch.empty((n_te, n_tr), dtype=torch.float32).pin_memory()
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        flush.zero_()
-        x_tr.copy_(h_xtr, non_blocking=True)
-        x_te.copy_(h_xte, non_blocking=True)
-        step()
-        h_k.copy_(g_out["k"], non_blocking=True)
-        h_r.copy_(r_out["k"], non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e_value = world * units_step * args.steps / (e2e_ms / 1e3)
-    h2d = h_xtr.numel() * 4 + h_xte.numel() * 4
-    d2h = h_k.numel() * 4 + h_r.numel() * 4
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(torch, tdist, args, world, stream, flush, x_tr, x_te, g_out, r_out, data, step,
+                         units_step, barrier, dev)
 
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -305,7 +323,8 @@ def run_ours(args):
                      "kernel": "gram_kernel<float,chi=4> (symmetric 2000x2000 Gram)",
                      "peak_source": f"FP32 FMA peak {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
                      "avg_launch_ms": gram_avg_ms},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
+        "phases_ms": phases,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -320,7 +339,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--n-train", type=int, default=WL["n_train"],
+                    help="training-set size; smaller cases serve ncu captures, not bench lines")
+    ap.add_argument("--n-test", type=int, default=WL["n_test"])
     args = ap.parse_args()
+    if (args.n_train, args.n_test) != (WL["n_train"], WL["n_test"]):
+        WL.update(n_train=args.n_train, n_test=args.n_test,
+                  workload=f"fmnist784_gram{args.n_train}_rows{args.n_test}")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -168,7 +168,12 @@ def test_edge_cases(dk):
     torch.cuda.synchronize()
     bb = big.cpu().numpy()
     assert np.all(bb[20:, :] == -7.0) and np.all(bb[:, 30:] == -7.0)
-    np.testing.assert_array_equal(bb[:20, :30], full["kq"].cpu().numpy()[3:23, 5:35])
+    ref = full["kq"].cpu().numpy()[3:23, 5:35]
+    gi, gj = np.meshgrid(np.arange(3, 23), np.arange(5, 35), indexing="ij")
+    # pairs with i <= j are contracted with the same operand roles as in the symmetric
+    # call, so they agree bit for bit; the others agree to rounding
+    np.testing.assert_array_equal(bb[:20, :30][gi <= gj], ref[gi <= gj])
+    assert np.max(np.abs(bb[:20, :30] - ref)) <= TOL_K
 
 
 def test_host_errors(dk):
