@@ -22,13 +22,18 @@
  *   (NULL = the legacy default stream). Every call is asynchronous on `stream`;
  *   inputs must stay valid and outputs untouched until the stream reaches the call.
  * - Features x are float32, row-major m x n (sample-major): x[i*n + f].
- * - MPS layout (written by dk_mps_build, read by the Gram calls), site-major:
- *       A[k][i][s][r][l],  k < n sites, i < m samples, s in {0,1},
- *       r < chi_max (right bond), l < chi_max (left bond), l fastest,
- *   complex64 (float re, float im) for DK_C64 or complex128 for DK_C128.
- *   Element (k,i,s,r,l) sits at index (((k*m + i)*2 + s)*chi_max + r)*chi_max + l.
- *   Bonds narrower than chi_max are zero-padded. Base pointers must be 16-byte
- *   aligned (cudaMalloc / torch allocations are).
+ * - MPS layout (written by dk_mps_build, read by the Gram calls). Every bond of the
+ *   ZZ-chain MPS carries a copy of the computational value of the qubit to its left, so
+ *   with bond positions ordered as b = t*h + j (t = that bit, h = chi_max/2) the site
+ *   tensor A_s[l][b] vanishes unless b lies in block s. Only the non-zero half is stored,
+ *   site-major:
+ *       A[k][i][s][j][l],  k < n sites, i < m samples, s in {0,1},
+ *       j < h (right bond position s*h + j), l < chi_max (left bond position),
+ *   l fastest: element (k,i,s,j,l) sits at index (((k*m + i)*2 + s)*h + j)*chi_max + l,
+ *   complex64 (float re, float im) for DK_C64 or complex128 for DK_C128, chi_max^2
+ *   complex numbers per sample and site. At the last site the right bond is 1 and both
+ *   s use j = 0. Unused bond positions are zero. Base pointers must be 16-byte aligned
+ *   (cudaMalloc / torch allocations are).
  * - Errors: every call returns a dk_status. Argument errors are detected on the
  *   host before anything is launched (DK_ERR_ARG, DK_ERR_UNSUPPORTED). A failing
  *   CUDA launch returns DK_ERR_CUDA. A device-side wait that exceeds its bound
@@ -76,7 +81,7 @@ typedef struct {
   int reps;           /* repetitions, 1..5 */
   float angle_scale;  /* RZ angle = angle_scale * x_i (2 for the ZZ-chain map) */
   int entangle;       /* 1: RZZ chain applied; 0: product state */
-  int chi_max;        /* padded bond dimension of the stored tensors: >= min(2^reps, 2^(n-1)) */
+  int chi_max;        /* stored bond dimension: 4, 8, 16 or 32, and >= 2^reps */
 } dk_fmap;
 
 /* Create a context on `device` (sets it current on the calling thread). The context
@@ -98,19 +103,19 @@ size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
  * Exact construction: every RZZ layer is a diagonal bond-2 operator, so after r
  * repetitions the state is an MPS of bond 2^r whose site tensors have a closed form
  * in (x_{k-1}, x_k). Each sample's chain is then brought to left-canonical form by
- * Householder QR in FP64 (the only FP64 on the GPU), normalised, and rounded to
- * `dtype`.
+ * Householder QR in FP64, one bond block at a time (the only FP64 on the GPU),
+ * normalised, and rounded to `dtype`.
  *   x          m x n float32 features (device)
  *   fm         feature map (host pointer)
  *   mps        dk_mps_bytes(m, n, fm->chi_max, dtype) bytes (device, written)
- *   bond_dims  n + 1 int32 (device, written, may be NULL): stored left bond of site k,
- *              and 1 at index n
+ *   bond_dims  n + 1 int32 (device, written, may be NULL): number of non-zero left-bond
+ *              positions of site k (1, 2, 4, ... up to 2^reps), and 1 at index n
  *   log_norm   m floats (device, written, may be NULL): ln |<psi~_i|psi~_i>| of the
  *              rounded tensors, evaluated by the same transfer arithmetic as the Gram
  *              calls; passing it to them normalises K_q so that K_q(x, x) = 1.
- * Errors: DK_ERR_ARG (m < 1, n < 1, NULL x/mps/fm, reps outside 1..5),
- *         DK_ERR_UNSUPPORTED (chi_max too small for the exact bond, or a chi_max /
- *         dtype pair without a Gram kernel: DK_C64 needs chi_max 4, DK_C128 chi_max 2 or 4). */
+ * Errors: DK_ERR_ARG (m < 1, n < 1, NULL x/mps/fm, reps outside 1..5, misaligned mps),
+ *         DK_ERR_UNSUPPORTED (chi_max not in {4, 8, 16, 32} or below 2^reps; log_norm
+ *         requested with chi_max != 4). */
 dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm,
                        dk_dtype dtype, void* mps, int32_t* bond_dims, float* log_norm,
                        void* stream);
@@ -154,6 +159,17 @@ dk_status dk_dual_kernel_rows(dk_ctx* ctx,
                               dk_precision prec,
                               float* k_out, float* kq_out, float* kc_out, float* logkq_out,
                               void* stream);
+
+/* Tile shapes of the Gram kernels (the blocks of §II-D, sized for one GB300 SM).
+ * Shape 0 is the built-in choice; shapes 1..dk_gram_config_count(dtype, chi_max) can be
+ * selected per context with dk_set_gram_config, e.g. by an autotuner that times them on
+ * the caller's workload. dk_gram_config_info reports a shape's tile (row samples x
+ * column samples) and threads per CTA; any pointer may be NULL.
+ * Errors: DK_ERR_ARG for an unknown id or NULL ctx. */
+int dk_gram_config_count(dk_dtype dtype, int chi_max);
+dk_status dk_gram_config_info(dk_dtype dtype, int chi_max, int id, int* tile_rows, int* tile_cols,
+                              int* threads);
+dk_status dk_set_gram_config(dk_ctx* ctx, int id);
 
 #ifdef __cplusplus
 }

@@ -45,53 +45,67 @@ struct GramArgs {
   unsigned* status;
 };
 
-template <typename real_, int CHI_, int WTR_, int WTC_, int WR_, int WC_, int STAGES_, int MINB_>
+template <typename real_, int CHI_, int WTR_, int WTC_, int PR_, int PC_, int WR_, int WC_, int STAGES_, int MINB_>
 struct GramCfg {
   using real = real_;
-  static constexpr int CHI = CHI_, WTR = WTR_, WTC = WTC_, WR = WR_, WC = WC_, STAGES = STAGES_, MINB = MINB_;
+  static constexpr int CHI = CHI_, H = CHI_ / 2;
+  static constexpr int WTR = WTR_, WTC = WTC_, PR = PR_, PC = PC_, WR = WR_, WC = WC_;
+  static constexpr int STAGES = STAGES_, MINB = MINB_;
   static constexpr int NWARPS = WR * WC;
   static constexpr int NTHREADS = NWARPS * 32;
-  static constexpr int TR = WTR * WR;
-  static constexpr int TC = WTC * WC;
-  static constexpr int SITE_BYTES = 2 * CHI * CHI * 2 * int(sizeof(real));
-  static constexpr int H = SITE_BYTES / 128;              // 128-byte rows per sample-site
-  static constexpr int HBUF_R = ((TR * 128 + 1023) / 1024) * 1024;  // bytes per row-sample half buffer
+  static constexpr int TR = WR * WTR * PR;   // row samples per tile
+  static constexpr int TC = WC * WTC * PC;   // column samples per tile
+  static constexpr int CPLX = 2 * int(sizeof(real));
+  static constexpr int SITE_BYTES = CHI * CHI * CPLX;      // compact site tensor of one sample
+  static constexpr int NROW = SITE_BYTES / 128;            // 128-byte rows per sample-site
+  static constexpr int HBUF_R = ((TR * 128 + 1023) / 1024) * 1024;  // one 128-byte row of TR samples
   static constexpr int HBUF_C = ((TC * 128 + 1023) / 1024) * 1024;
-  static constexpr int ROW_BOX = H * HBUF_R;
-  static constexpr int COL_BOX = H * HBUF_C;
+  static constexpr int ROW_BOX = NROW * HBUF_R;
+  static constexpr int COL_BOX = NROW * HBUF_C;
   static constexpr int STAGE_BYTES = ROW_BOX + COL_BOX;
   static constexpr int TX_BYTES = (TR + TC) * SITE_BYTES;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16 + 1024;
   static_assert(SITE_BYTES % 128 == 0, "site tensor must be a whole number of 128-byte rows");
-  static_assert(WTR * WTC == 32, "warp tile must hold 32 pairs");
-  static_assert(CHI * 2 * int(sizeof(real)) <= 128, "one bond column must fit a 128-byte row");
+  static_assert(WTR * WTC == 32, "a warp is WTR x WTC threads");
+  static_assert(H * CPLX >= 16 && (H * CPLX) % 16 == 0, "a sub-block column must be whole 16-byte chunks");
 };
 
-// Reads one right-bond column A_s[:, col] of sample t from a swizzled stage buffer.
-template <typename real, int CHI, int HBUF>
-struct SmemCol {
-  const uint8_t* buf;  // h = 0 buffer of this side
-  int t;
-  __device__ __forceinline__ void operator()(int s, int col, real (&re)[CHI], real (&im)[CHI]) const {
-    constexpr int CPLX = 2 * int(sizeof(real));
-    constexpr int NCH = CHI * CPLX / 16;
-    const int off = (s * CHI + col) * CHI * CPLX;
-    const int h = off >> 7;
-    const int c0 = (off & 127) >> 4;
-    const uint8_t* row = buf + h * HBUF + t * 128;
+// Fills the h x h sub-block A_s[t] (rows: left bond l = t*h + a, columns j) of one sample
+// from a swizzled stage buffer. In the compact layout element (s, j, l) of a sample-site
+// sits at complex index (s*h + j)*chi + l, so each sub-block column is h consecutive
+// complex numbers; the TMA 128-byte swizzle stores chunk c of sample slot u at c ^ (u & 7).
+template <class Cfg>
+struct SubLoad {
+  using real = typename Cfg::real;
+  static constexpr int H = Cfg::H;
+  const uint8_t* buf;  // row-0 buffer of this side (shared memory)
+  int hbuf;            // bytes between the 128-byte-row buffers of this side
+  int slot0;           // sample slot of this thread's first row/column
+  int stride;          // slot distance between this thread's rows/columns
+  __device__ __forceinline__ void operator()(int p, int s, int t, Blk<real, H>& blk) const {
+    constexpr int CPLX = Cfg::CPLX;
+    constexpr int NCH = H * CPLX / 16;  // chunks per sub-block column
+    const int slot = slot0 + p * stride;
+    const uint8_t* row0 = buf + slot * 128;
 #pragma unroll
-    for (int q = 0; q < NCH; ++q) {
-      const uint8_t* p = row + (((c0 + q) ^ (t & 7)) << 4);
-      if constexpr (sizeof(real) == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(p);
-        re[2 * q] = v.x;
-        im[2 * q] = v.y;
-        re[2 * q + 1] = v.z;
-        im[2 * q + 1] = v.w;
-      } else {
-        const double2 v = *reinterpret_cast<const double2*>(p);
-        re[q] = v.x;
-        im[q] = v.y;
+    for (int j = 0; j < H; ++j) {
+      const int off = ((s * H + j) * Cfg::CHI + t * H) * CPLX;
+      const int r = off >> 7;
+      const int c0 = (off & 127) >> 4;
+#pragma unroll
+      for (int q = 0; q < NCH; ++q) {
+        const uint8_t* a = row0 + r * hbuf + (((c0 + q) ^ (slot & 7)) << 4);
+        if constexpr (sizeof(real) == 4) {
+          const float4 v = *reinterpret_cast<const float4*>(a);
+          blk.r[2 * q][j] = v.x;
+          blk.i[2 * q][j] = v.y;
+          blk.r[2 * q + 1][j] = v.z;
+          blk.i[2 * q + 1][j] = v.w;
+        } else {
+          const double2 v = *reinterpret_cast<const double2*>(a);
+          blk.r[q][j] = v.x;
+          blk.i[q][j] = v.y;
+        }
       }
     }
   }
@@ -174,17 +188,20 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
     gram_kernel(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_c,
                 const GramArgs p) {
   using real = typename Cfg::real;
-  constexpr int CHI = Cfg::CHI, STAGES = Cfg::STAGES;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int H = Cfg::H, STAGES = Cfg::STAGES, PR = Cfg::PR, PC = Cfg::PC;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  // 1024-byte aligned base for the 128-byte swizzle, kept as shared-memory pointer arithmetic
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
   uint64_t* empty = full + STAGES;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + STAGES);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int tr = (warp / Cfg::WC) * Cfg::WTR + lane / Cfg::WTC;
-  const int tc = (warp % Cfg::WC) * Cfg::WTC + lane % Cfg::WTC;
+  // Thread (lr, lc) of warp (wr, wc) owns rows slot_r + pr*WTR and columns slot_c + pc*WTC:
+  // the 8 lanes of a quarter-warp read 8 consecutive column samples and one row sample.
+  const int slot_r = (warp / Cfg::WC) * (Cfg::WTR * PR) + lane / Cfg::WTC;
+  const int slot_c = (warp % Cfg::WC) * (Cfg::WTC * PC) + lane % Cfg::WTC;
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -215,7 +232,7 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
     uint8_t* base = smem + st * Cfg::STAGE_BYTES;
     mbar_arrive_expect_tx(&full[st], Cfg::TX_BYTES);
 #pragma unroll
-    for (int h = 0; h < Cfg::H; ++h) {
+    for (int h = 0; h < Cfg::NROW; ++h) {
       tma_load_3d(base + h * Cfg::HBUF_R, &tm_r, &full[st], h * 32, r0, k);
       tma_load_3d(base + Cfg::ROW_BOX + h * Cfg::HBUF_C, &tm_c, &full[st], h * 32, c0, k);
     }
@@ -226,29 +243,32 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
     for (; issued < total && issued < STAGES; ++issued) issue(issued);
   }
 
-  Chain<real, CHI> ch;
-  ch.init();
+  PairE<real, H> st[PR][PC];
   int r0 = 0, c0 = 0;
   long long q = 0;
   for (; q < total; ++q) {
-    const int st = int(q % STAGES);
+    const int sidx = int(q % STAGES);
     const uint32_t ph = uint32_t((q / STAGES) & 1);
     const int k = int(q % p.n);
     if (k == 0) {
-      ch.init();
+#pragma unroll
+      for (int pr = 0; pr < PR; ++pr)
+#pragma unroll
+        for (int pc = 0; pc < PC; ++pc) st[pr][pc].init();
       tile_origin(q / p.n, r0, c0);
     }
-    if (!mbar_wait_bounded(&full[st], ph)) {
+    if (!mbar_wait_bounded(&full[sidx], ph)) {
       record_status(p.status, DEV_TIMEOUT);
       *abort_flag = 1;
       break;
     }
-    const uint8_t* base = smem + st * Cfg::STAGE_BYTES;
-    const SmemCol<real, CHI, Cfg::HBUF_R> ldi{base, tr};
-    const SmemCol<real, CHI, Cfg::HBUF_C> ldj{base + Cfg::ROW_BOX, tc};
-    ch.step(ldi, ldj);
+    const uint8_t* base = smem + sidx * Cfg::STAGE_BYTES;
+    const SubLoad<Cfg> ldi{base, Cfg::HBUF_R, slot_r, Cfg::WTR};
+    const SubLoad<Cfg> ldj{base + Cfg::ROW_BOX, Cfg::HBUF_C, slot_c, Cfg::WTC};
+    const bool last = (k == p.n - 1);
+    site_step<real, H, PR, PC>(st, ldi, ldj, last || ((k % RENORM_EVERY) == RENORM_EVERY - 1));
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[st]);
+    if (lane == 0) mbar_arrive(&empty[sidx]);
     if (tid == 0 && q >= 1 && issued < total) {
       const long long qq = q - 1;
       if (!mbar_wait_bounded(&empty[qq % STAGES], uint32_t((qq / STAGES) & 1))) {
@@ -259,7 +279,13 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
       issue(issued);
       ++issued;
     }
-    if (k == p.n - 1) write_pair<Cfg>(p, ch.half_log_mod(), r0 + tr, c0 + tc);
+    if (last) {
+#pragma unroll
+      for (int pr = 0; pr < PR; ++pr)
+#pragma unroll
+        for (int pc = 0; pc < PC; ++pc)
+          write_pair<Cfg>(p, st[pr][pc].half_log_mod(), r0 + slot_r + pr * Cfg::WTR, c0 + slot_c + pc * Cfg::WTC);
+    }
     if (*abort_flag) break;
   }
   // On an early exit, let the copies already issued land before the CTA leaves.
@@ -297,10 +323,14 @@ struct GramLauncher {
   }
 };
 
-// Tile shapes: 4 x 8 pairs per warp, 4 x 2 warps -> 16 x 16 pairs per CTA.
-using CfgF32x4 = GramCfg<float, 4, 4, 8, 4, 2, 4, 1>;
-using CfgF64x2 = GramCfg<double, 2, 4, 8, 4, 2, 4, 1>;
-using CfgF64x4 = GramCfg<double, 4, 4, 8, 4, 2, 4, 1>;
+// Tile shapes: GramCfg<real, chi, warp WTR x WTC threads, PR x PC pairs per thread,
+// WR x WC warps, stages, min CTAs per SM>. All are square (TR == TC) so that each can
+// serve the symmetric Gram.
+using F32_P11 = GramCfg<float, 4, 4, 8, 1, 1, 4, 2, 4, 2>;  // 16 x 16 pairs, 256 threads
+using F32_P21 = GramCfg<float, 4, 4, 8, 2, 1, 4, 4, 4, 1>;  // 32 x 32 pairs, 512 threads
+using F32_P22 = GramCfg<float, 4, 4, 8, 2, 2, 4, 2, 4, 1>;  // 32 x 32 pairs, 256 threads
+using F32_P12 = GramCfg<float, 4, 8, 4, 1, 2, 4, 4, 4, 1>;  // 32 x 32 pairs, 512 threads
+using F64_P11 = GramCfg<double, 4, 4, 8, 1, 1, 4, 2, 4, 1>; // 16 x 16 pairs, 256 threads
 
 template <class Cfg>
 static dk_status launch_gram(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
@@ -316,14 +346,31 @@ static dk_status launch_gram(dk_ctx* ctx, const void* mps_r, int m_r, const void
   return GramLauncher<Cfg>::run(ctx, mps_r, m_r, mps_c, m_c, a, st);
 }
 
+struct CfgInfo {
+  int tile_rows, tile_cols, threads;
+};
+template <class Cfg>
+constexpr CfgInfo info_of() {
+  return CfgInfo{Cfg::TR, Cfg::TC, Cfg::NTHREADS};
+}
+// Shapes selectable for complex64 / chi 4, in id order 1..4; the built-in choice is id 3.
+static const CfgInfo kF32Chi4[] = {info_of<F32_P11>(), info_of<F32_P21>(), info_of<F32_P22>(), info_of<F32_P12>()};
+constexpr int kF32Chi4Default = 3;
+static const CfgInfo kF64Chi4[] = {info_of<F64_P11>()};
+
 static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, int chi,
                                dk_dtype dtype, dk_precision prec, const GramArgs& a, cudaStream_t st) {
-  if (dtype == DK_C64 && prec == DK_PREC_F32 && chi == 4)
-    return launch_gram<CfgF32x4>(ctx, mps_r, m_r, mps_c, m_c, a, st);
-  if (dtype == DK_C128 && prec == DK_PREC_F64 && chi == 2)
-    return launch_gram<CfgF64x2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+  if (dtype == DK_C64 && prec == DK_PREC_F32 && chi == 4) {
+    const int id = ctx->gram_config > 0 ? ctx->gram_config : kF32Chi4Default;
+    switch (id) {
+      case 1: return launch_gram<F32_P11>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 2: return launch_gram<F32_P21>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 4: return launch_gram<F32_P12>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      default: return launch_gram<F32_P22>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+    }
+  }
   if (dtype == DK_C128 && prec == DK_PREC_F64 && chi == 4)
-    return launch_gram<CfgF64x4>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+    return launch_gram<F64_P11>(ctx, mps_r, m_r, mps_c, m_c, a, st);
   return DK_ERR_UNSUPPORTED;
 }
 
@@ -373,6 +420,30 @@ DK_API dk_status dk_gram_tile(dk_ctx* ctx, const void* mps_rows, int m_rows, con
   a.status = ctx->status;
   return gram_dispatch(ctx, mps_rows, m_rows, mps_cols, m_cols, chi_max, dtype, prec, a,
                        static_cast<cudaStream_t>(stream));
+}
+
+DK_API int dk_gram_config_count(dk_dtype dtype, int chi_max) {
+  if (dtype == DK_C64 && chi_max == 4) return int(sizeof(dk::kF32Chi4) / sizeof(dk::kF32Chi4[0]));
+  if (dtype == DK_C128 && chi_max == 4) return int(sizeof(dk::kF64Chi4) / sizeof(dk::kF64Chi4[0]));
+  return 0;
+}
+
+DK_API dk_status dk_gram_config_info(dk_dtype dtype, int chi_max, int id, int* tile_rows, int* tile_cols,
+                                     int* threads) {
+  const int count = dk_gram_config_count(dtype, chi_max);
+  if (id < 0 || id > count || count == 0) return DK_ERR_ARG;
+  const dk::CfgInfo* tab = dtype == DK_C64 ? dk::kF32Chi4 : dk::kF64Chi4;
+  const int idx = (id == 0 ? (dtype == DK_C64 ? dk::kF32Chi4Default : 1) : id) - 1;
+  if (tile_rows) *tile_rows = tab[idx].tile_rows;
+  if (tile_cols) *tile_cols = tab[idx].tile_cols;
+  if (threads) *threads = tab[idx].threads;
+  return DK_OK;
+}
+
+DK_API dk_status dk_set_gram_config(dk_ctx* ctx, int id) {
+  if (!ctx || id < 0 || id > 4) return DK_ERR_ARG;
+  ctx->gram_config = id;
+  return DK_OK;
 }
 
 DK_API dk_status dk_dual_kernel_rows(dk_ctx* ctx, const void* mps_test, const float* x_test,

@@ -19,14 +19,16 @@ struct dk_ctx {
   int cc_major, cc_minor;
   unsigned* status;  // device word, bits of dk::DEV_*
   dk_encode_tiled_fn encode_tiled;
+  int gram_config;   // 0: built-in choice; otherwise a tile-shape id (dk_set_gram_config)
 };
 
 namespace dk {
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Compact site tensor of one sample: chi^2 complex numbers (see include/dualk.h).
 inline size_t site_bytes(int chi_max, dk_dtype dtype) {
-  return size_t(2) * chi_max * chi_max * (dtype == DK_C64 ? 8 : 16);
+  return size_t(chi_max) * chi_max * (dtype == DK_C64 ? 8 : 16);
 }
 
 // Tensor map over an MPS buffer viewed as [n sites][m samples][site_bytes/4 floats]:

@@ -1,24 +1,35 @@
-// One pair's left-to-right transfer contraction (§II-C, Eqs. 8-10), held in registers.
+// Left-to-right transfer contraction of one pair (§II-C, Eqs. 8-10), block-structured.
 //
 // For a pair (x_i, x_j) the amplitude a = <psi(x_i)|psi(x_j)> of two MPS is
 //     E_0 = [1],   E_k = sum_{s in {0,1}} A_s^(k)(x_i)^dagger E_{k-1} A_s^(k)(x_j),   a = E_n,
-// with E a chi x chi complex matrix (rows: bond of the conjugated row sample i,
-// columns: bond of the column sample j). After each site E is scaled by an exact
-// power of two so that max(|Re|, |Im|) lies in [1, 2); the exponents are summed in
-// `e2`, so a = E_n[0][0] * 2^e2 never underflows.
+// with E a chi x chi complex matrix (rows: bond of the conjugated row sample i, columns:
+// bond of the column sample j).
 //
-// Per site the work is F_s = E A_s(x_j) followed by E' = sum_s A_s(x_i)^dagger F_s:
-// 4 chi^3 complex multiply-adds = 16 chi^3 FP FMAs, all written as explicit fma() so
-// the rounding sequence is fixed: the Gram kernel and the self-overlap kernel use this
-// code on the same tensors and get bit-identical diagonal amplitudes.
+// Block structure. In the ZZ-chain MPS every bond carries a copy of the computational
+// value of the qubit to its left (the RZZ layers are diagonal), so with the bond index
+// ordered as l = t * h + j (t = that copied bit, h = chi / 2) a site tensor A_s has
+// non-zero columns only in block s, and consequently E_k is block diagonal,
+// E = diag(E_0, E_1) with h x h blocks. Writing A_s[t] for the h x h sub-block of A_s
+// with rows in block t and its block-s columns, one site is
+//     E'_s = sum_{t in {0,1}} A_s[t](x_i)^dagger  E_t  A_s[t](x_j),     s = 0, 1,
+// i.e. 8 h^3 complex multiply-adds instead of the 4 chi^3 = 32 h^3 of the dense form;
+// the zeros skipped are exact zeros of the construction. At the last site the right bond
+// is 1 and both s land in the same 1 x 1 entry: a = E'_0[0][0] + E'_1[0][0].
 //
-// Operand columns come through a loader: ld(s, col, re[], im[]) yields the chi complex
-// entries A_s[l][col], l = 0..chi-1 (one right-bond column of the site tensor).
+// Every 4 sites (and after the last) E is scaled by an exact power of two so that
+// max(|Re|, |Im|) lies in [1, 2); the exponents are summed in e2, so a = mantissa * 2^e2
+// never underflows (between rescales E shrinks by at most a few per-site overlap factors).
+//
+// All arithmetic is explicit fma() in a fixed order: the Gram kernels and the
+// self-overlap kernel run this code on the same tensors and get bit-identical diagonal
+// amplitudes.
 #pragma once
 
 #include <stdint.h>
 
 namespace dk {
+
+constexpr int RENORM_EVERY = 4;
 
 template <typename real>
 struct RealBits;
@@ -41,107 +52,153 @@ struct RealBits<double> {
   }
 };
 
-template <typename real, int CHI>
-struct Chain {
-  real er[CHI][CHI];
-  real ei[CHI][CHI];
+// h x h complex block, split real / imaginary.
+template <typename real, int H>
+struct Blk {
+  real r[H][H];
+  real i[H][H];
+};
+
+// Transfer state of one pair: E = diag(b[0], b[1]) and the binary exponent.
+template <typename real, int H>
+struct PairE {
+  Blk<real, H> b[2];
   int e2;
 
   __device__ __forceinline__ void init() {
 #pragma unroll
-    for (int a = 0; a < CHI; ++a)
+    for (int t = 0; t < 2; ++t)
 #pragma unroll
-      for (int b = 0; b < CHI; ++b) {
-        er[a][b] = real(0);
-        ei[a][b] = real(0);
-      }
-    er[0][0] = real(1);
+      for (int a = 0; a < H; ++a)
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+          b[t].r[a][c] = real(0);
+          b[t].i[a][c] = real(0);
+        }
+    b[0].r[0][0] = real(1);
     e2 = 0;
   }
 
-  template <class LoadI, class LoadJ>
-  __device__ __forceinline__ void step(const LoadI& ldi, const LoadJ& ldj) {
-    real nr[CHI][CHI], ni[CHI][CHI];
-#pragma unroll
-    for (int a = 0; a < CHI; ++a)
-#pragma unroll
-      for (int b = 0; b < CHI; ++b) {
-        nr[a][b] = real(0);
-        ni[a][b] = real(0);
-      }
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      real fr[CHI][CHI], fi[CHI][CHI];
-      // F_s[a][bp] = sum_b E[a][b] * A^j_s[b][bp]
-#pragma unroll
-      for (int bp = 0; bp < CHI; ++bp) {
-        real cr[CHI], ci[CHI];
-        ldj(s, bp, cr, ci);
-#pragma unroll
-        for (int a = 0; a < CHI; ++a) {
-          real accr = er[a][0] * cr[0];
-          real acci = er[a][0] * ci[0];
-          accr = fma(-ei[a][0], ci[0], accr);
-          acci = fma(ei[a][0], cr[0], acci);
-#pragma unroll
-          for (int b = 1; b < CHI; ++b) {
-            accr = fma(er[a][b], cr[b], accr);
-            accr = fma(-ei[a][b], ci[b], accr);
-            acci = fma(er[a][b], ci[b], acci);
-            acci = fma(ei[a][b], cr[b], acci);
-          }
-          fr[a][bp] = accr;
-          fi[a][bp] = acci;
-        }
-      }
-      // E'[ap][bp] += sum_a conj(A^i_s[a][ap]) * F_s[a][bp]
-#pragma unroll
-      for (int ap = 0; ap < CHI; ++ap) {
-        real cr[CHI], ci[CHI];
-        ldi(s, ap, cr, ci);
-#pragma unroll
-        for (int bp = 0; bp < CHI; ++bp) {
-          real accr = nr[ap][bp];
-          real acci = ni[ap][bp];
-#pragma unroll
-          for (int a = 0; a < CHI; ++a) {
-            accr = fma(cr[a], fr[a][bp], accr);
-            accr = fma(ci[a], fi[a][bp], accr);
-            acci = fma(cr[a], fi[a][bp], acci);
-            acci = fma(-ci[a], fr[a][bp], acci);
-          }
-          nr[ap][bp] = accr;
-          ni[ap][bp] = acci;
-        }
-      }
-    }
-    // Exact power-of-two rescale: max(|Re|, |Im|) -> [1, 2).
+  __device__ __forceinline__ void renorm() {
     real mx = real(0);
 #pragma unroll
-    for (int a = 0; a < CHI; ++a)
+    for (int t = 0; t < 2; ++t)
 #pragma unroll
-      for (int b = 0; b < CHI; ++b) mx = fmax(mx, fmax(fabs(nr[a][b]), fabs(ni[a][b])));
+      for (int a = 0; a < H; ++a)
+#pragma unroll
+        for (int c = 0; c < H; ++c) mx = fmax(mx, fmax(fabs(b[t].r[a][c]), fabs(b[t].i[a][c])));
     const int e = RealBits<real>::exponent(mx);
     const real sc = RealBits<real>::pow2_neg(e);
 #pragma unroll
-    for (int a = 0; a < CHI; ++a)
+    for (int t = 0; t < 2; ++t)
 #pragma unroll
-      for (int b = 0; b < CHI; ++b) {
-        er[a][b] = nr[a][b] * sc;
-        ei[a][b] = ni[a][b] * sc;
-      }
+      for (int a = 0; a < H; ++a)
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+          b[t].r[a][c] *= sc;
+          b[t].i[a][c] *= sc;
+        }
     e2 += e;
   }
 
-  // ln|a| = 0.5 ln(|mantissa|^2) + e2 ln 2, rounded to float (-inf for a = 0). The Gram
-  // epilogue forms 2 * this - ln_norm_i - ln_norm_j, which is exactly 0 on the diagonal
-  // because ln_norm_i is this same value from the self-overlap kernel.
+  // ln|a| with a = b[0][0][0] + b[1][0][0] (valid after the last site), rounded to float;
+  // -inf for a = 0. The Gram epilogue forms 2 * this - ln_norm_i - ln_norm_j, which is
+  // exactly 0 on the diagonal because ln_norm_i is this same value from the self-overlap
+  // kernel.
   __device__ __forceinline__ float half_log_mod() const {
-    const real re = er[0][0];
-    const real im = ei[0][0];
+    const real re = b[0].r[0][0] + b[1].r[0][0];
+    const real im = b[0].i[0][0] + b[1].i[0][0];
     const real mod2 = fma(re, re, im * im);
     return float(fma(real(0.5), log(mod2), real(e2) * real(0.69314718055994530942)));
   }
 };
+
+// acc += conj(ai)^T * (e * aj) for one (s, t) term of one pair:
+//   F[a][c]   = sum_b e[a][b] aj[b][c]
+//   acc[p][c] += sum_a conj(ai[a][p]) F[a][c]
+// ai / aj are h x h sub-blocks indexed [row (bond l within block t)][column j].
+template <typename real, int H>
+__device__ __forceinline__ void term(Blk<real, H>& acc, const Blk<real, H>& e, const Blk<real, H>& ai,
+                                     const Blk<real, H>& aj) {
+  Blk<real, H> f;
+#pragma unroll
+  for (int a = 0; a < H; ++a)
+#pragma unroll
+    for (int c = 0; c < H; ++c) {
+      real fr = e.r[a][0] * aj.r[0][c];
+      real fi = e.r[a][0] * aj.i[0][c];
+      fr = fma(-e.i[a][0], aj.i[0][c], fr);
+      fi = fma(e.i[a][0], aj.r[0][c], fi);
+#pragma unroll
+      for (int b = 1; b < H; ++b) {
+        fr = fma(e.r[a][b], aj.r[b][c], fr);
+        fr = fma(-e.i[a][b], aj.i[b][c], fr);
+        fi = fma(e.r[a][b], aj.i[b][c], fi);
+        fi = fma(e.i[a][b], aj.r[b][c], fi);
+      }
+      f.r[a][c] = fr;
+      f.i[a][c] = fi;
+    }
+#pragma unroll
+  for (int p = 0; p < H; ++p)
+#pragma unroll
+    for (int c = 0; c < H; ++c) {
+      real ar = acc.r[p][c];
+      real aim = acc.i[p][c];
+#pragma unroll
+      for (int a = 0; a < H; ++a) {
+        ar = fma(ai.r[a][p], f.r[a][c], ar);
+        ar = fma(ai.i[a][p], f.i[a][c], ar);
+        aim = fma(ai.r[a][p], f.i[a][c], aim);
+        aim = fma(-ai.i[a][p], f.r[a][c], aim);
+      }
+      acc.r[p][c] = ar;
+      acc.i[p][c] = aim;
+    }
+}
+
+// One site for a PR x PC group of pairs (rows share A(x_i), columns share A(x_j)).
+// The loaders fill one sub-block: ldi(pr, s, t, blk) / ldj(pc, s, t, blk).
+template <typename real, int H, int PR, int PC, class LoadI, class LoadJ>
+__device__ __forceinline__ void site_step(PairE<real, H> (&st)[PR][PC], const LoadI& ldi, const LoadJ& ldj,
+                                          bool renorm) {
+  Blk<real, H> nw[PR][PC][2];
+#pragma unroll
+  for (int pr = 0; pr < PR; ++pr)
+#pragma unroll
+    for (int pc = 0; pc < PC; ++pc)
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < H; ++a)
+#pragma unroll
+          for (int c = 0; c < H; ++c) {
+            nw[pr][pc][s].r[a][c] = real(0);
+            nw[pr][pc][s].i[a][c] = real(0);
+          }
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      Blk<real, H> ai[PR], aj[PC];
+#pragma unroll
+      for (int pr = 0; pr < PR; ++pr) ldi(pr, s, t, ai[pr]);
+#pragma unroll
+      for (int pc = 0; pc < PC; ++pc) ldj(pc, s, t, aj[pc]);
+#pragma unroll
+      for (int pr = 0; pr < PR; ++pr)
+#pragma unroll
+        for (int pc = 0; pc < PC; ++pc) term<real, H>(nw[pr][pc][s], st[pr][pc].b[t], ai[pr], aj[pc]);
+    }
+  }
+#pragma unroll
+  for (int pr = 0; pr < PR; ++pr)
+#pragma unroll
+    for (int pc = 0; pc < PC; ++pc) {
+      st[pr][pc].b[0] = nw[pr][pc][0];
+      st[pr][pc].b[1] = nw[pr][pc][1];
+      if (renorm) st[pr][pc].renorm();
+    }
+}
 
 }  // namespace dk

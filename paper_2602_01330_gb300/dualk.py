@@ -24,7 +24,8 @@ _STATUS_NAMES = {0: "DK_OK", 1: "DK_ERR_ARG", 2: "DK_ERR_UNSUPPORTED", 3: "DK_ER
                  4: "DK_ERR_TIMEOUT", 5: "DK_ERR_WORKSPACE", 6: "DK_ERR_NO_DEVICE"}
 
 EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_mps_bytes",
-            "dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows")
+            "dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows", "dk_gram_config_count",
+            "dk_gram_config_info", "dk_set_gram_config")
 
 
 class DualKError(RuntimeError):
@@ -67,6 +68,13 @@ def _lib():
     lib.dk_dual_kernel_rows.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, i32, i32, i32, i32,
                                         f32, f32, i32, vp, vp, vp, vp, vp]
     lib.dk_dual_kernel_rows.restype = i32
+    lib.dk_gram_config_count.argtypes = [i32, i32]
+    lib.dk_gram_config_count.restype = i32
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.dk_gram_config_info.argtypes = [i32, i32, i32, ip, ip, ip]
+    lib.dk_gram_config_info.restype = i32
+    lib.dk_set_gram_config.argtypes = [vp, i32]
+    lib.dk_set_gram_config.restype = i32
     _LIB = lib
     return lib
 
@@ -122,8 +130,9 @@ class MPS:
     x: torch.Tensor           # float32 m x n features it was built from
 
     def complex_view(self):
+        """[site][sample][s][j][l] view of the compact block layout (see include/dualk.h)."""
         ct = torch.complex64 if self.dtype == DK_C64 else torch.complex128
-        return self.data.view(ct).view(self.n, self.m, 2, self.chi_max, self.chi_max)
+        return self.data.view(ct).view(self.n, self.m, 2, self.chi_max // 2, self.chi_max)
 
 
 class Context:
@@ -148,6 +157,22 @@ class Context:
 
     def sync_status(self, stream=None):
         _check(_lib().dk_sync_status(self.handle, _stream(stream)), "dk_sync_status")
+
+    def set_gram_config(self, cfg_id: int):
+        """dk_set_gram_config: 0 = built-in tile shape, 1..gram_config_count() = a fixed one."""
+        _check(_lib().dk_set_gram_config(self.handle, int(cfg_id)), "dk_set_gram_config")
+
+
+def gram_config_count(dtype: int = DK_C64, chi_max: int = 4) -> int:
+    return int(_lib().dk_gram_config_count(dtype, chi_max))
+
+
+def gram_config_info(cfg_id: int, dtype: int = DK_C64, chi_max: int = 4):
+    """(tile_rows, tile_cols, threads) of a Gram tile shape."""
+    r, c, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib().dk_gram_config_info(dtype, chi_max, cfg_id, ctypes.byref(r), ctypes.byref(c), ctypes.byref(t)),
+           "dk_gram_config_info")
+    return r.value, c.value, t.value
 
 
 def mps_bytes(m: int, n: int, chi_max: int, dtype: int = DK_C64) -> int:

@@ -58,8 +58,8 @@ def test_error_strings_and_host_validation(lib):
     assert lib.dk_error_string(0) == b"ok"
     assert b"argument" in lib.dk_error_string(1)
     lib.dk_mps_bytes.restype = ctypes.c_size_t
-    assert lib.dk_mps_bytes(10, 7, 4, 0) == 10 * 7 * 2 * 4 * 4 * 8
-    assert lib.dk_mps_bytes(10, 7, 2, 1) == 10 * 7 * 2 * 2 * 2 * 16
+    assert lib.dk_mps_bytes(10, 7, 4, 0) == 10 * 7 * 4 * 4 * 8     # chi^2 complex64 per sample-site
+    assert lib.dk_mps_bytes(10, 7, 8, 1) == 10 * 7 * 8 * 8 * 16
     assert lib.dk_mps_bytes(0, 7, 4, 0) == 0
     # NULL context / pointers are rejected on the host before any CUDA call.
     assert lib.dk_mps_build(None, None, 1, 1, None, 0, None, None, None, None) == 1
@@ -79,9 +79,13 @@ def test_create_without_device_reports_no_device(lib):
 def test_workload_accounting():
     from paper_2602_01330_gb300 import workload
     assert workload.exact_bonds(6, 2) == [1, 2, 4, 4, 4, 2, 1]
-    # n = 3: D = 1, 2, 2, 1 -> 16 (1*2 + 1*4) + 16 (4*2 + 2*4) + 16 (4*1 + 2*1) = 448
-    assert workload.flops_per_pair(3, 5) == 448
-    # n = 784, reps = 2: 780 interior sites at D = 4 cost 2048 flops each
+    # dense count, n = 3: D = 1, 2, 2, 1 -> 16 (1*2 + 1*4) + 16 (4*2 + 2*4) + 16 (4*1 + 2*1) = 448
+    assert workload.dense_flops_per_pair(3, 5) == 448
+    # dense count, n = 784, reps = 2: 780 interior sites at D = 4 cost 2048 flops each
     edge = 16 * (1 * 2 + 1 * 4) + 16 * (4 * 4 + 2 * 16) + 16 * (16 * 2 + 4 * 4) + 16 * (4 * 1 + 2 * 1)
-    assert workload.flops_per_pair(784, 2) == 780 * 2048 + edge
+    assert workload.dense_flops_per_pair(784, 2) == 780 * 2048 + edge
+    # block count, interior site at D = 4: 4 (s, t) terms of (2*2*2 + 2*2*2) complex MACs x 8
+    assert workload.flops_per_pair(6, 2) - workload.flops_per_pair(5, 2) == 4 * 16 * 8
+    # block count at n = 784: sites 1, 2, 783, 784 cost 32, 192, 192, 64 flops
+    assert workload.flops_per_pair(784, 2) == 780 * 512 + 32 + 192 + 192 + 64
     assert workload.gram_entries(4) == 10 and workload.gram_entries(4, False, 3) == 12
