@@ -64,7 +64,7 @@ struct GramCfg {
   static constexpr int COL_BOX = NROW * HBUF_C;
   static constexpr int STAGE_BYTES = ROW_BOX + COL_BOX;
   static constexpr int TX_BYTES = (TR + TC) * SITE_BYTES;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16 + 1024;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STAGES * 8 + 2 * STAGES * 4 + 16 + 1024;
   static_assert(SITE_BYTES % 128 == 0, "site tensor must be a whole number of 128-byte rows");
   static_assert(WTR * WTC == 32, "a warp is WTR x WTC threads");
   static_assert(H * CPLX >= 16 && (H * CPLX) % 16 == 0, "a sub-block column must be whole 16-byte chunks");
@@ -111,18 +111,25 @@ struct SubLoad {
   }
 };
 
-__device__ __forceinline__ void decode_tile(const GramArgs& p, int t, int& ti, int& tj) {
+// First column tile of row tile ti that holds a pair with j >= i (symmetric Gram): the
+// tile (ti, tj) covers rows from ti*TR and columns up to (tj+1)*TC - 1.
+__host__ __device__ __forceinline__ int first_upper_tile(int ti, int tr, int tc) { return (ti * tr) / tc; }
+
+// Tile index t (row-major over the tiles that are computed) -> (row tile, column tile).
+__device__ __forceinline__ void decode_tile(const GramArgs& p, int tr, int tc, int t, int& ti, int& tj) {
   if (p.symmetric) {
-    const int T = p.tiles_r;
-    const double b = 2.0 * T + 1.0;
-    int r = int((b - sqrt(b * b - 8.0 * double(t))) * 0.5);
-    if (r < 0) r = 0;
-    if (r > T - 1) r = T - 1;
-    auto start = [T](int q) { return q * T - (q * (q - 1)) / 2; };
-    while (r + 1 < T && start(r + 1) <= t) ++r;
-    while (r > 0 && start(r) > t) --r;
-    ti = r;
-    tj = r + (t - start(r));
+    int r = 0;
+    while (true) {
+      const int first = first_upper_tile(r, tr, tc);
+      const int cnt = first < p.tiles_c ? p.tiles_c - first : 0;
+      if (t < cnt || r + 1 >= p.tiles_r) {
+        ti = r;
+        tj = first + t;
+        return;
+      }
+      t -= cnt;
+      ++r;
+    }
   } else {
     ti = t / p.tiles_c;
     tj = t - ti * p.tiles_c;
@@ -193,8 +200,9 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
   // 1024-byte aligned base for the 128-byte swizzle, kept as shared-memory pointer arithmetic
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + STAGES);
+  int* released = reinterpret_cast<int*>(full + STAGES);  // warps done with each stage
+  int* inflight = released + STAGES;                       // parity + 1 of the last load per stage
+  volatile int* abort_flag = inflight + STAGES;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -206,7 +214,8 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], Cfg::NWARPS);
+      released[s] = 0;
+      inflight[s] = 0;
     }
     *abort_flag = 0;
     fence_mbar_init();
@@ -218,18 +227,16 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
   const int my_tiles = (p.ntiles > int(blockIdx.x)) ? (p.ntiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
   const long long total = (long long)my_tiles * p.n;
 
-  auto tile_origin = [&](long long local, int& r0, int& c0) {
+  auto tile_origin = [&](int local, int& r0, int& c0) {
     int ti, tj;
-    decode_tile(p, int(blockIdx.x) + int(local) * int(gridDim.x), ti, tj);
+    decode_tile(p, Cfg::TR, Cfg::TC, int(blockIdx.x) + local * int(gridDim.x), ti, tj);
     r0 = p.row0 + ti * Cfg::TR;
     c0 = p.col0 + tj * Cfg::TC;
   };
-  auto issue = [&](long long q) {
-    const int st = int(q % STAGES);
-    const int k = int(q % p.n);
-    int r0, c0;
-    tile_origin(q / p.n, r0, c0);
+  // Load site k of the tile at (r0, c0) into stage `st` (one thread).
+  auto issue = [&](int st, uint32_t parity, int r0, int c0, int k) {
     uint8_t* base = smem + st * Cfg::STAGE_BYTES;
+    inflight[st] = int(parity) + 1;
     mbar_arrive_expect_tx(&full[st], Cfg::TX_BYTES);
 #pragma unroll
     for (int h = 0; h < Cfg::NROW; ++h) {
@@ -238,24 +245,30 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
     }
   };
 
-  long long issued = 0;
   if (tid == 0) {
-    for (; issued < total && issued < STAGES; ++issued) issue(issued);
+    int tile = 0, k = 0, r0 = 0, c0 = 0;
+    for (int q = 0; q < STAGES && q < total; ++q) {
+      if (k == 0) tile_origin(tile, r0, c0);
+      issue(q, 0u, r0, c0, k);
+      if (++k == p.n) {
+        k = 0;
+        ++tile;
+      }
+    }
   }
 
   PairE<real, H> st[PR][PC];
   int r0 = 0, c0 = 0;
+  int sidx = 0, k = 0, tile = 0;
+  uint32_t ph = 0;
   long long q = 0;
   for (; q < total; ++q) {
-    const int sidx = int(q % STAGES);
-    const uint32_t ph = uint32_t((q / STAGES) & 1);
-    const int k = int(q % p.n);
     if (k == 0) {
 #pragma unroll
       for (int pr = 0; pr < PR; ++pr)
 #pragma unroll
         for (int pc = 0; pc < PC; ++pc) st[pr][pc].init();
-      tile_origin(q / p.n, r0, c0);
+      tile_origin(tile, r0, c0);
     }
     if (!mbar_wait_bounded(&full[sidx], ph)) {
       record_status(p.status, DEV_TIMEOUT);
@@ -266,18 +279,27 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
     const SubLoad<Cfg> ldi{base, Cfg::HBUF_R, slot_r, Cfg::WTR};
     const SubLoad<Cfg> ldj{base + Cfg::ROW_BOX, Cfg::HBUF_C, slot_c, Cfg::WTC};
     const bool last = (k == p.n - 1);
-    site_step<real, H, PR, PC>(st, ldi, ldj, last || ((k % RENORM_EVERY) == RENORM_EVERY - 1));
+    site_step<real, H, PR, PC>(st, ldi, ldj, last || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1));
+    // Release the stage; the last warp to do so refills it with the site STAGES ahead, so
+    // no thread ever waits for the others to free a buffer.
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[sidx]);
-    if (tid == 0 && q >= 1 && issued < total) {
-      const long long qq = q - 1;
-      if (!mbar_wait_bounded(&empty[qq % STAGES], uint32_t((qq / STAGES) & 1))) {
-        record_status(p.status, DEV_TIMEOUT);
-        *abort_flag = 1;
-        break;
+    if (lane == 0) {
+      __threadfence_block();
+      if (atomicAdd(&released[sidx], 1) == Cfg::NWARPS - 1) {
+        released[sidx] = 0;
+        __threadfence_block();
+        if (q + STAGES < total) {
+          int kk = k + STAGES, tt = tile;
+          while (kk >= p.n) {
+            kk -= p.n;
+            ++tt;
+          }
+          int rr = r0, cc = c0;
+          if (tt != tile) tile_origin(tt, rr, cc);  // once per tile, not per site
+          fence_proxy_async_smem();
+          issue(sidx, ph ^ 1u, rr, cc, kk);
+        }
       }
-      issue(issued);
-      ++issued;
     }
     if (last) {
 #pragma unroll
@@ -287,12 +309,20 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
           write_pair<Cfg>(p, st[pr][pc].half_log_mod(), r0 + slot_r + pr * Cfg::WTR, c0 + slot_c + pc * Cfg::WTC);
     }
     if (*abort_flag) break;
-  }
-  // On an early exit, let the copies already issued land before the CTA leaves.
-  if (tid == 0) {
-    for (long long qq = q; qq < issued; ++qq) {
-      if (!mbar_wait_bounded(&full[qq % STAGES], uint32_t((qq / STAGES) & 1))) break;
+    if (++sidx == STAGES) {
+      sidx = 0;
+      ph ^= 1u;
     }
+    if (++k == p.n) {
+      k = 0;
+      ++tile;
+    }
+  }
+  // After a timeout, let the copies still in flight land before the CTA leaves.
+  __syncthreads();
+  if (tid == 0 && *abort_flag) {
+    for (int s = 0; s < STAGES; ++s)
+      if (inflight[s] > 0 && !mbar_wait_bounded(&full[s], uint32_t(inflight[s] - 1))) break;
   }
 }
 
@@ -324,13 +354,15 @@ struct GramLauncher {
 };
 
 // Tile shapes: GramCfg<real, chi, warp WTR x WTC threads, PR x PC pairs per thread,
-// WR x WC warps, stages, min CTAs per SM>. All are square (TR == TC) so that each can
-// serve the symmetric Gram.
-using F32_P11 = GramCfg<float, 4, 4, 8, 1, 1, 4, 2, 4, 2>;  // 16 x 16 pairs, 256 threads
-using F32_P21 = GramCfg<float, 4, 4, 8, 2, 1, 4, 4, 4, 1>;  // 32 x 32 pairs, 512 threads
-using F32_P22 = GramCfg<float, 4, 4, 8, 2, 2, 4, 2, 4, 1>;  // 32 x 32 pairs, 256 threads
-using F32_P12 = GramCfg<float, 4, 8, 4, 1, 2, 4, 4, 4, 1>;  // 32 x 32 pairs, 512 threads
-using F64_P11 = GramCfg<double, 4, 4, 8, 1, 1, 4, 2, 4, 1>; // 16 x 16 pairs, 256 threads
+// WR x WC warps, stages, min CTAs per SM>.
+using F32_P11 = GramCfg<float, 4, 4, 8, 1, 1, 4, 2, 4, 2>;     // 16 x 16 pairs, 256 threads
+using F32_P21 = GramCfg<float, 4, 4, 8, 2, 1, 4, 4, 4, 1>;     // 32 x 32 pairs, 512 threads
+using F32_P22 = GramCfg<float, 4, 4, 8, 2, 2, 4, 2, 4, 1>;     // 32 x 32 pairs, 256 threads
+using F32_P12 = GramCfg<float, 4, 8, 4, 1, 2, 4, 4, 4, 1>;     // 32 x 32 pairs, 512 threads
+using F32_P22w = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 4, 1>;    // 48 x 32 pairs, 384 threads
+using F32_P21w = GramCfg<float, 4, 4, 8, 2, 1, 4, 3, 4, 1>;    // 32 x 24 pairs, 384 threads
+using F32_P14 = GramCfg<float, 4, 8, 4, 1, 4, 4, 2, 4, 1>;     // 32 x 32 pairs, 256 threads
+using F64_P11 = GramCfg<double, 4, 4, 8, 1, 1, 4, 2, 4, 1>;    // 16 x 16 pairs, 256 threads
 
 template <class Cfg>
 static dk_status launch_gram(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
@@ -338,8 +370,12 @@ static dk_status launch_gram(dk_ctx* ctx, const void* mps_r, int m_r, const void
   a.tiles_r = (a.nrows + Cfg::TR - 1) / Cfg::TR;
   a.tiles_c = (a.ncols + Cfg::TC - 1) / Cfg::TC;
   if (a.symmetric) {
-    if (Cfg::TR != Cfg::TC) return DK_ERR_UNSUPPORTED;
-    a.ntiles = a.tiles_r * (a.tiles_r + 1) / 2;
+    long long cnt = 0;
+    for (int ti = 0; ti < a.tiles_r; ++ti) {
+      const int first = first_upper_tile(ti, Cfg::TR, Cfg::TC);
+      if (first < a.tiles_c) cnt += a.tiles_c - first;
+    }
+    a.ntiles = int(cnt);
   } else {
     a.ntiles = a.tiles_r * a.tiles_c;
   }
@@ -353,9 +389,10 @@ template <class Cfg>
 constexpr CfgInfo info_of() {
   return CfgInfo{Cfg::TR, Cfg::TC, Cfg::NTHREADS};
 }
-// Shapes selectable for complex64 / chi 4, in id order 1..4; the built-in choice is id 3.
-static const CfgInfo kF32Chi4[] = {info_of<F32_P11>(), info_of<F32_P21>(), info_of<F32_P22>(), info_of<F32_P12>()};
-constexpr int kF32Chi4Default = 3;
+// Shapes selectable for complex64 / chi 4, in id order 1..7; the built-in choice is id 5.
+static const CfgInfo kF32Chi4[] = {info_of<F32_P11>(),  info_of<F32_P21>(),  info_of<F32_P22>(), info_of<F32_P12>(),
+                                   info_of<F32_P22w>(), info_of<F32_P21w>(), info_of<F32_P14>()};
+constexpr int kF32Chi4Default = 5;
 static const CfgInfo kF64Chi4[] = {info_of<F64_P11>()};
 
 static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, int chi,
@@ -366,7 +403,11 @@ static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const vo
       case 1: return launch_gram<F32_P11>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 2: return launch_gram<F32_P21>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 4: return launch_gram<F32_P12>(ctx, mps_r, m_r, mps_c, m_c, a, st);
-      default: return launch_gram<F32_P22>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 5: return launch_gram<F32_P22w>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 6: return launch_gram<F32_P21w>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 7: return launch_gram<F32_P14>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 3: return launch_gram<F32_P22>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      default: return launch_gram<F32_P22w>(ctx, mps_r, m_r, mps_c, m_c, a, st);
     }
   }
   if (dtype == DK_C128 && prec == DK_PREC_F64 && chi == 4)
@@ -441,7 +482,7 @@ DK_API dk_status dk_gram_config_info(dk_dtype dtype, int chi_max, int id, int* t
 }
 
 DK_API dk_status dk_set_gram_config(dk_ctx* ctx, int id) {
-  if (!ctx || id < 0 || id > 4) return DK_ERR_ARG;
+  if (!ctx || id < 0 || id > dk_gram_config_count(DK_C64, 4)) return DK_ERR_ARG;
   ctx->gram_config = id;
   return DK_OK;
 }

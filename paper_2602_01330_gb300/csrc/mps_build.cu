@@ -50,121 +50,116 @@ __device__ __forceinline__ double cabs2(cd a) { return fma(a.x, a.x, a.y * a.y);
 
 constexpr double PI_D = 3.14159265358979323846;
 
-// Closed-form factors of one site: u^e and w^e for e in [-r, r], u = exp(-i phi/2),
-// w = exp(-i theta/2) (both unit modulus, so u^-e = conj(u^e)).
+// Closed-form factors of one site for RP repetitions: u^e and w^e for e in [-RP, RP],
+// u = exp(-i phi/2), w = exp(-i theta/2) (unit modulus, so u^-e = conj(u^e)).
+template <int RP>
 struct SiteFactors {
-  cd up[6];
-  cd wp[6];
-  double amp;
-  int reps;
-  __device__ __forceinline__ void make(double phi, double theta, int r) {
-    reps = r;
-    amp = exp2(-0.5 * r);
+  cd up[RP + 1];
+  cd wp[RP + 1];
+  __device__ __forceinline__ void make(double phi, double theta) {
     double sn, cs;
     sincos(-0.5 * phi, &sn, &cs);
     const cd u = mk(cs, sn);
     sincos(-0.5 * theta, &sn, &cs);
-    const cd w = mk(cs, sn);
+    make_from(u, mk(cs, sn));
+  }
+  __device__ __forceinline__ void make_from(cd u, cd w) {
     up[0] = mk(1.0, 0.0);
     wp[0] = mk(1.0, 0.0);
 #pragma unroll
-    for (int q = 1; q < 6; ++q) {
+    for (int q = 1; q <= RP; ++q) {
       up[q] = cmul(up[q - 1], u);
       wp[q] = cmul(wp[q - 1], w);
     }
   }
   __device__ __forceinline__ cd upow(int e) const { return e >= 0 ? up[e] : cconj(up[-e]); }
   __device__ __forceinline__ cd wpow(int e) const { return e >= 0 ? wp[e] : cconj(wp[-e]); }
-  // L_k(c)
+  // L_k(c) = 2^(-r/2) (-1)^popc(c & c>>1) u^(r - 2 popc(c))
   __device__ __forceinline__ cd local(int c) const {
+    constexpr double amp = RP == 1 ? 0.70710678118654752440 : RP == 2 ? 0.5 : RP == 3 ? 0.35355339059327376220
+                         : RP == 4 ? 0.25 : 0.17677669529663688110;
     const double sign = (__popc(c & (c >> 1)) & 1) ? -amp : amp;
-    return cscale(upow(reps - 2 * __popc(c)), sign);
+    return cscale(upow(RP - 2 * __popc(c)), sign);
   }
   // bond phase between closed-form left index cp and right index c
-  __device__ __forceinline__ cd bond(int cp, int c) const { return wpow(reps - 2 * __popc(cp ^ c)); }
+  __device__ __forceinline__ cd bond(int cp, int c) const { return wpow(RP - 2 * __popc(cp ^ c)); }
 };
-
-// Householder QR of a P x C complex matrix (static sizes, registers), nref <= C reflectors.
-// On return Q holds the first nref columns of Q (others zero) and R the nref x C upper
-// trapezoidal factor (rows >= nref zero).
-template <int P, int C>
-__device__ __forceinline__ void householder_qr(cd (&M)[P][C], int nref, cd (&Q)[P][C], cd (&R)[C][C]) {
-  double beta[C];
-  cd alpha[C];
-#pragma unroll
-  for (int j = 0; j < C; ++j) {
-    beta[j] = 0.0;
-    alpha[j] = mk(0.0, 0.0);
-    if (j < nref && j < P) {
-      double sigma2 = 0.0;
-#pragma unroll
-      for (int i = j; i < P; ++i) sigma2 += cabs2(M[i][j]);
-      const cd x0 = M[j][j];
-      const double ax0 = sqrt(cabs2(x0));
-      const double sigma = sqrt(sigma2);
-      if (sigma > 0.0) {
-        const cd u = ax0 > 0.0 ? cscale(x0, 1.0 / ax0) : mk(1.0, 0.0);
-        alpha[j] = cscale(u, -sigma);
-        M[j][j] = cscale(u, ax0 + sigma);  // v_0; v_i = M[i][j] below
-        beta[j] = 1.0 / (sigma * (sigma + ax0));
-#pragma unroll
-        for (int c = j + 1; c < C; ++c) {
-          cd w = mk(0.0, 0.0);
-#pragma unroll
-          for (int i = j; i < P; ++i) w = cadd(w, cconjmul(M[i][j], M[i][c]));
-          w = cscale(w, beta[j]);
-#pragma unroll
-          for (int i = j; i < P; ++i) M[i][c] = csub(M[i][c], cmul(M[i][j], w));
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < C; ++r)
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      cd v = mk(0.0, 0.0);
-      if (r < nref) {
-        if (c == r) v = alpha[r];
-        else if (c > r) v = M[r][c];
-      }
-      R[r][c] = v;
-    }
-#pragma unroll
-  for (int c = 0; c < C; ++c) {
-    cd col[P];
-#pragma unroll
-    for (int i = 0; i < P; ++i) col[i] = mk((i == c && c < nref) ? 1.0 : 0.0, 0.0);
-#pragma unroll
-    for (int j = C - 1; j >= 0; --j) {
-      if (j < nref && j < P && beta[j] != 0.0 && c < nref) {
-        cd w = mk(0.0, 0.0);
-#pragma unroll
-        for (int i = j; i < P; ++i) w = cadd(w, cconjmul(M[i][j], col[i]));
-        w = cscale(w, beta[j]);
-#pragma unroll
-        for (int i = j; i < P; ++i) col[i] = csub(col[i], cmul(M[i][j], w));
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < P; ++i) Q[i][c] = col[i];
-  }
-}
 
 __device__ __forceinline__ void store_cplx(void* out, size_t idx, cd v, int c128) {
   if (c128) reinterpret_cast<double2*>(out)[idx] = make_double2(v.x, v.y);
   else reinterpret_cast<float2*>(out)[idx] = make_float2(float(v.x), float(v.y));
 }
 
-// One thread per sample; HS = stored block size chi/2, HA = closed-form block size 2^(r-1).
-template <int HS, int HA>
-__global__ void __launch_bounds__(128) mps_build_thread_kernel(const float* __restrict__ x, int m, int n, int reps,
-                                                               double angle_scale, int entangle, int out_c128,
-                                                               void* __restrict__ out, int32_t* __restrict__ bond) {
-  constexpr int P = 2 * HS;   // stored left-bond positions
+// QR of a P x C complex matrix (C <= 2) by classical Gram-Schmidt with one
+// re-orthogonalisation pass, in registers. nref <= C columns are orthonormalised; R is
+// nref x C (rows >= nref zero), Q's columns >= nref are zero. A column whose residual
+// vanishes gets a zero Q column and a zero R diagonal (the product Q R is still M).
+template <int P, int C>
+__device__ __forceinline__ void qr_cgs2(const cd (&M)[P][C], int nref, cd (&Q)[P][C], cd (&R)[C][C]) {
+#pragma unroll
+  for (int r = 0; r < C; ++r)
+#pragma unroll
+    for (int c = 0; c < C; ++c) R[r][c] = mk(0.0, 0.0);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    cd v[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) v[i] = M[i][c];
+    if (c < nref) {
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+        for (int q = 0; q < c; ++q) {
+          cd r = mk(0.0, 0.0);
+#pragma unroll
+          for (int i = 0; i < P; ++i) r = cadd(r, cconjmul(Q[i][q], v[i]));
+          R[q][c] = cadd(R[q][c], r);
+#pragma unroll
+          for (int i = 0; i < P; ++i) v[i] = csub(v[i], cmul(Q[i][q], r));
+        }
+      double n2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < P; ++i) n2 += cabs2(v[i]);
+      const double nrm = sqrt(n2);
+      const double inv = nrm > 1e-300 ? 1.0 / nrm : 0.0;
+      R[c][c] = mk(nrm, 0.0);
+#pragma unroll
+      for (int i = 0; i < P; ++i) Q[i][c] = cscale(v[i], inv);
+    } else {
+#pragma unroll
+      for (int q = 0; q < C; ++q) {
+        if (q < nref) {
+          cd r = mk(0.0, 0.0);
+#pragma unroll
+          for (int i = 0; i < P; ++i) r = cadd(r, cconjmul(Q[i][q], v[i]));
+          R[q][c] = r;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < P; ++i) Q[i][c] = mk(0.0, 0.0);
+    }
+  }
+}
+
+__device__ __forceinline__ cd shfl_cd(unsigned mask, cd v, int lane_mask) {
+  return mk(__shfl_xor_sync(mask, v.x, lane_mask), __shfl_xor_sync(mask, v.y, lane_mask));
+}
+
+// Two threads per sample, one per bond block s; HS = stored block size chi/2, HA =
+// closed-form block size 2^(r-1) <= 2. A CTA is one (possibly partial) warp holding
+// blockDim.x / 2 samples; the launch picks the width so that the FP64 work spreads over
+// all SMs.
+template <int HS, int HA, int RP>
+__global__ void __launch_bounds__(32) mps_build_pair_kernel(const float* __restrict__ x, int m, int n,
+                                                            double angle_scale, int entangle, int out_c128,
+                                                            void* __restrict__ out, int32_t* __restrict__ bond) {
+  constexpr int P = 2 * HS;  // stored left-bond positions
   constexpr int CHI = 2 * HS;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
+  const int s = threadIdx.x & 1;
+  const int i0 = blockIdx.x * (blockDim.x >> 1) + (threadIdx.x >> 1);
+  const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+  const bool live = i0 < m;
+  const int i = live ? i0 : m - 1;  // dead lanes shadow the last sample and store nothing
   const float* xs = x + size_t(i) * n;
   cd R[2][HS][HA];
 #pragma unroll
@@ -177,80 +172,84 @@ __global__ void __launch_bounds__(128) mps_build_thread_kernel(const float* __re
   int act = 1;  // active left-bond positions (pk_0 + pk_1 of the previous site)
   double xprev = 0.0;
   const size_t per = size_t(CHI) * CHI;  // complex entries per sample-site
-  SiteFactors f;
+  SiteFactors<RP> f;
   for (int k = 0; k < n; ++k) {
     const double xk = double(xs[k]);
-    f.make(angle_scale * xk, (entangle && k > 0) ? 2.0 * (PI_D - xprev) * (PI_D - xk) : 0.0, reps);
-    const size_t base = (size_t(k) * m + i) * per;
-    if (bond && i == 0) bond[k] = act;
+    {
+      // the two threads of a sample evaluate one exponential each and swap
+      const double arg = s == 0 ? -0.5 * angle_scale * xk
+                                : ((entangle && k > 0) ? -(PI_D - xprev) * (PI_D - xk) : 0.0);
+      double sn, cs;
+      sincos(arg, &sn, &cs);
+      const cd mine = mk(cs, sn);
+      const cd other = shfl_cd(mask, mine, 1);
+      f.make_from(s == 0 ? mine : other, s == 0 ? other : mine);
+    }
+    const size_t base = (size_t(k) * m + i) * per + size_t(s) * HS * CHI;
+    if (bond && i0 == 0 && s == 0) bond[k] = act;
     if (k < n - 1) {
-      cd Rn[2][HS][HA];
-      int pk = 0;
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        cd M[P][HA];
-#pragma unroll
-        for (int t = 0; t < 2; ++t)
-#pragma unroll
-          for (int j = 0; j < HS; ++j)
-#pragma unroll
-            for (int cc = 0; cc < HA; ++cc) {
-              const int c = s * HA + cc;
-              cd acc = mk(0.0, 0.0);
-#pragma unroll
-              for (int cp = 0; cp < HA; ++cp) acc = cadd(acc, cmul(R[t][j][cp], f.bond(t * HA + cp, c)));
-              M[t * HS + j][cc] = cmul(f.local(c), acc);
-            }
-        const int nref = act < HA ? act : HA;
-        cd Q[P][HA], Rr[HA][HA];
-        householder_qr<P, HA>(M, nref, Q, Rr);
-#pragma unroll
-        for (int j = 0; j < HS; ++j)
-#pragma unroll
-          for (int l = 0; l < P; ++l) store_cplx(out, base + (s * HS + j) * CHI + l, j < HA ? Q[l][j] : mk(0.0, 0.0), out_c128);
-#pragma unroll
-        for (int j = 0; j < HS; ++j)
-#pragma unroll
-          for (int cc = 0; cc < HA; ++cc) Rn[s][j][cc] = j < HA ? Rr[j][cc] : mk(0.0, 0.0);
-        pk += nref;
-      }
+      cd M[P][HA];
 #pragma unroll
       for (int t = 0; t < 2; ++t)
 #pragma unroll
         for (int j = 0; j < HS; ++j)
 #pragma unroll
-          for (int c = 0; c < HA; ++c) R[t][j][c] = Rn[t][j][c];
-      act = pk;
-    } else {
-      cd v[2][P];
-      double nrm2 = 0.0;
-#pragma unroll
-      for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int t = 0; t < 2; ++t)
-#pragma unroll
-          for (int j = 0; j < HS; ++j) {
+          for (int cc = 0; cc < HA; ++cc) {
+            const int c = s * HA + cc;
             cd acc = mk(0.0, 0.0);
 #pragma unroll
-            for (int cc = 0; cc < HA; ++cc) {
-              const int c = s * HA + cc;
-              cd inner = mk(0.0, 0.0);
-#pragma unroll
-              for (int cp = 0; cp < HA; ++cp) inner = cadd(inner, cmul(R[t][j][cp], f.bond(t * HA + cp, c)));
-              acc = cadd(acc, cmul(f.local(c), inner));
-            }
-            v[s][t * HS + j] = acc;
-            nrm2 += cabs2(acc);
+            for (int cp = 0; cp < HA; ++cp) acc = cadd(acc, cmul(R[t][j][cp], f.bond(t * HA + cp, c)));
+            M[t * HS + j][cc] = cmul(f.local(c), acc);
           }
-      const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+      const int nref = act < HA ? act : HA;
+      cd Q[P][HA], Rr[HA][HA];
+      qr_cgs2<P, HA>(M, nref, Q, Rr);
+      if (live) {
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
+        for (int j = 0; j < HS; ++j)
+#pragma unroll
+          for (int l = 0; l < P; ++l) store_cplx(out, base + j * CHI + l, j < HA ? Q[l][j] : mk(0.0, 0.0), out_c128);
+      }
+      // R <- diag(R_0, R_1): keep this block, take the other from the partner lane
+#pragma unroll
+      for (int j = 0; j < HS; ++j)
+#pragma unroll
+        for (int cc = 0; cc < HA; ++cc) {
+          const cd mine = j < HA ? Rr[j][cc] : mk(0.0, 0.0);
+          const cd other = shfl_cd(mask, mine, 1);
+          R[s][j][cc] = mine;
+          R[1 - s][j][cc] = other;
+        }
+      act = 2 * nref;
+    } else {
+      cd v[P];
+      double nrm2 = 0.0;
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int j = 0; j < HS; ++j) {
+          cd acc = mk(0.0, 0.0);
+#pragma unroll
+          for (int cc = 0; cc < HA; ++cc) {
+            const int c = s * HA + cc;
+            cd inner = mk(0.0, 0.0);
+#pragma unroll
+            for (int cp = 0; cp < HA; ++cp) inner = cadd(inner, cmul(R[t][j][cp], f.bond(t * HA + cp, c)));
+            acc = cadd(acc, cmul(f.local(c), inner));
+          }
+          v[t * HS + j] = acc;
+          nrm2 += cabs2(acc);
+        }
+      nrm2 += __shfl_xor_sync(mask, nrm2, 1);
+      const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+      if (live) {
 #pragma unroll
         for (int j = 0; j < HS; ++j)
 #pragma unroll
           for (int l = 0; l < P; ++l)
-            store_cplx(out, base + (s * HS + j) * CHI + l, j == 0 ? cscale(v[s][l], inv) : mk(0.0, 0.0), out_c128);
-      if (bond && i == 0) bond[n] = 1;
+            store_cplx(out, base + j * CHI + l, j == 0 ? cscale(v[l], inv) : mk(0.0, 0.0), out_c128);
+      }
+      if (bond && i0 == 0 && s == 0) bond[n] = 1;
     }
     xprev = xk;
   }
@@ -270,8 +269,8 @@ struct WarpQr {
   double part[32];
 };
 
-template <int HS, int HA>
-__global__ void __launch_bounds__(32) mps_build_warp_kernel(const float* __restrict__ x, int m, int n, int reps,
+template <int HS, int HA, int RP>
+__global__ void __launch_bounds__(32) mps_build_warp_kernel(const float* __restrict__ x, int m, int n,
                                                             double angle_scale, int entangle, int out_c128,
                                                             void* __restrict__ out, int32_t* __restrict__ bond) {
   constexpr int P = 2 * HS;
@@ -288,10 +287,10 @@ __global__ void __launch_bounds__(32) mps_build_warp_kernel(const float* __restr
   int act = 1;
   double xprev = 0.0;
   const size_t per = size_t(CHI) * CHI;
-  SiteFactors f;
+  SiteFactors<RP> f;
   for (int k = 0; k < n; ++k) {
     const double xk = double(xs[k]);
-    f.make(angle_scale * xk, (entangle && k > 0) ? 2.0 * (PI_D - xprev) * (PI_D - xk) : 0.0, reps);
+    f.make(angle_scale * xk, (entangle && k > 0) ? 2.0 * (PI_D - xprev) * (PI_D - xk) : 0.0);
     for (int c = lane; c < 2 * HA; c += 32) S.L[c] = f.local(c);
     __syncwarp();
     const size_t base = (size_t(k) * m + i) * per;
@@ -439,20 +438,32 @@ __global__ void __launch_bounds__(128) self_overlap_kernel(const real* __restric
   log_norm[i] = st[0][0].half_log_mod();
 }
 
+// Threads per CTA of the pair kernel: full warps while there are enough samples to give
+// every SM one, narrower CTAs (fewer samples each) otherwise, so that more SMs share the
+// FP64 work.
+static int pair_kernel_lanes(int m, int sm_count) {
+  int lanes = 32;
+  while (lanes > 8 && (2 * m + lanes - 1) / lanes < sm_count) lanes >>= 1;
+  return lanes;
+}
+
 template <int HS, int HA>
 static dk_status launch_build(const float* x, int m, int n, const dk_fmap* fm, int c128, void* mps, int32_t* bond,
-                              cudaStream_t st) {
+                              int sm_count, cudaStream_t st) {
   if constexpr (HA <= 2) {
-    mps_build_thread_kernel<HS, HA><<<(m + 127) / 128, 128, 0, st>>>(x, m, n, fm->reps, double(fm->angle_scale),
-                                                                    fm->entangle, c128, mps, bond);
+    constexpr int RP = HA == 1 ? 1 : 2;
+    const int lanes = pair_kernel_lanes(m, sm_count);
+    mps_build_pair_kernel<HS, HA, RP><<<(2 * m + lanes - 1) / lanes, lanes, 0, st>>>(
+        x, m, n, double(fm->angle_scale), fm->entangle, c128, mps, bond);
   } else {
     const size_t smem = sizeof(WarpQr<HS, HA>);
-    auto kern = mps_build_warp_kernel<HS, HA>;
+    constexpr int RP = HA == 4 ? 3 : HA == 8 ? 4 : 5;
+    auto kern = mps_build_warp_kernel<HS, HA, RP>;
     if (smem > 48 * 1024) {
       if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
         return DK_ERR_CUDA;
     }
-    kern<<<m, 32, smem, st>>>(x, m, n, fm->reps, double(fm->angle_scale), fm->entangle, c128, mps, bond);
+    kern<<<m, 32, smem, st>>>(x, m, n, double(fm->angle_scale), fm->entangle, c128, mps, bond);
   }
   return launch_status();
 }
@@ -474,13 +485,13 @@ DK_API dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const d
   const int c128 = dtype == DK_C128 ? 1 : 0;
   dk_status s = DK_ERR_UNSUPPORTED;
   // (stored block HS = chi/2, closed-form block HA = 2^(reps-1))
-  if (chi == 4 && fm->reps == 1) s = launch_build<2, 1>(x, m, n, fm, c128, mps, bond_dims, st);
-  else if (chi == 4 && fm->reps == 2) s = launch_build<2, 2>(x, m, n, fm, c128, mps, bond_dims, st);
-  else if (chi == 8 && fm->reps == 1) s = launch_build<4, 1>(x, m, n, fm, c128, mps, bond_dims, st);
-  else if (chi == 8 && fm->reps == 2) s = launch_build<4, 2>(x, m, n, fm, c128, mps, bond_dims, st);
-  else if (chi == 8 && fm->reps == 3) s = launch_build<4, 4>(x, m, n, fm, c128, mps, bond_dims, st);
-  else if (chi == 16 && fm->reps == 4) s = launch_build<8, 8>(x, m, n, fm, c128, mps, bond_dims, st);
-  else if (chi == 32 && fm->reps == 5) s = launch_build<16, 16>(x, m, n, fm, c128, mps, bond_dims, st);
+  if (chi == 4 && fm->reps == 1) s = launch_build<2, 1>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
+  else if (chi == 4 && fm->reps == 2) s = launch_build<2, 2>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
+  else if (chi == 8 && fm->reps == 1) s = launch_build<4, 1>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
+  else if (chi == 8 && fm->reps == 2) s = launch_build<4, 2>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
+  else if (chi == 8 && fm->reps == 3) s = launch_build<4, 4>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
+  else if (chi == 16 && fm->reps == 4) s = launch_build<8, 8>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
+  else if (chi == 32 && fm->reps == 5) s = launch_build<16, 16>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
   if (s != DK_OK || !log_norm) return s;
   const int grid = (m + 127) / 128;
   if (dtype == DK_C64) {

@@ -30,6 +30,7 @@
 namespace dk {
 
 constexpr int RENORM_EVERY = 4;
+static_assert((RENORM_EVERY & (RENORM_EVERY - 1)) == 0, "rescale interval must be a power of two");
 
 template <typename real>
 struct RealBits;

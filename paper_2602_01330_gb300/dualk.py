@@ -180,8 +180,11 @@ def mps_bytes(m: int, n: int, chi_max: int, dtype: int = DK_C64) -> int:
 
 
 def mps_build(ctx: Context, x: torch.Tensor, fmap: FeatureMap, dtype: int = DK_C64,
-              out: torch.Tensor | None = None, stream=None) -> MPS:
-    """dk_mps_build: MPS of |psi(x_i)> for the rows of x (m x n float32, CUDA)."""
+              out: torch.Tensor | None = None, stream=None, bond: torch.Tensor | None = None,
+              log_norm: torch.Tensor | None = None) -> MPS:
+    """dk_mps_build: MPS of |psi(x_i)> for the rows of x (m x n float32, CUDA).
+
+    out / bond / log_norm may be preallocated (bytes, n + 1 int32, m float32)."""
     _need_cuda(x, "x", torch.float32)
     m, n = x.shape
     nbytes = mps_bytes(m, n, fmap.chi_max, dtype)
@@ -189,8 +192,13 @@ def mps_build(ctx: Context, x: torch.Tensor, fmap: FeatureMap, dtype: int = DK_C
         out = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
     elif out.numel() * out.element_size() < nbytes:
         raise ValueError("out is too small for the MPS")
-    bond = torch.empty(n + 1, dtype=torch.int32, device=x.device)
-    lnorm = torch.empty(m, dtype=torch.float32, device=x.device)
+    if bond is None:
+        bond = torch.empty(n + 1, dtype=torch.int32, device=x.device)
+    if log_norm is None:
+        log_norm = torch.empty(m, dtype=torch.float32, device=x.device)
+    _need_cuda(bond, "bond", torch.int32)
+    _need_cuda(log_norm, "log_norm", torch.float32)
+    lnorm = log_norm
     fm = fmap._c()
     _check(_lib().dk_mps_build(ctx.handle, _ptr(x), m, n, ctypes.byref(fm), dtype, _ptr(out), _ptr(bond),
                                _ptr(lnorm), _stream(stream)), "dk_mps_build")
