@@ -259,6 +259,7 @@ def run_ours(args):
             tdist.barrier()
 
     for _ in range(args.warmup):
+        flush.zero_()
         step()
     torch.cuda.synchronize()
     ctx.sync_status()

@@ -89,11 +89,12 @@ DK_API size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype) {
 namespace dk {
 
 dk_status encode_mps_map(dk_ctx* ctx, CUtensorMap* map, const void* mps, int m, int n, size_t sbytes,
-                         int box_samples) {
-  if (sbytes % 128 != 0 || box_samples < 1 || box_samples > 256) return DK_ERR_UNSUPPORTED;
+                         int box_samples, int box_sites) {
+  if (sbytes % 128 != 0 || box_samples < 1 || box_samples > 256 || box_sites < 1 || box_sites > 8)
+    return DK_ERR_UNSUPPORTED;
   cuuint64_t dims[3] = {cuuint64_t(sbytes / 4), cuuint64_t(m), cuuint64_t(n)};
   cuuint64_t strides[2] = {cuuint64_t(sbytes), cuuint64_t(sbytes) * cuuint64_t(m)};
-  cuuint32_t box[3] = {32u, cuuint32_t(box_samples), 1u};
+  cuuint32_t box[3] = {32u, cuuint32_t(box_samples), cuuint32_t(box_sites)};
   cuuint32_t estr[3] = {1u, 1u, 1u};
   CUresult r = ctx->encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(mps), dims, strides, box,
                                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,

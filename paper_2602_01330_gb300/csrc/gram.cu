@@ -43,14 +43,17 @@ struct GramArgs {
   float* lkq;
   long long ld;
   unsigned* status;
+  int need_kc;  // K_c is needed (k_out with w != 1, or kc_out)
 };
 
-template <typename real_, int CHI_, int WTR_, int WTC_, int PR_, int PC_, int WR_, int WC_, int STAGES_, int MINB_>
+template <typename real_, int CHI_, int WTR_, int WTC_, int PR_, int PC_, int WR_, int WC_, int STAGES_, int MINB_,
+          int SPS_ = 1>
 struct GramCfg {
   using real = real_;
   static constexpr int CHI = CHI_, H = CHI_ / 2;
   static constexpr int WTR = WTR_, WTC = WTC_, PR = PR_, PC = PC_, WR = WR_, WC = WC_;
   static constexpr int STAGES = STAGES_, MINB = MINB_;
+  static constexpr int SPS = SPS_;  // sites per pipeline stage (one barrier wait per stage)
   static constexpr int NWARPS = WR * WC;
   static constexpr int NTHREADS = NWARPS * 32;
   static constexpr int TR = WR * WTR * PR;   // row samples per tile
@@ -58,16 +61,21 @@ struct GramCfg {
   static constexpr int CPLX = 2 * int(sizeof(real));
   static constexpr int SITE_BYTES = CHI * CHI * CPLX;      // compact site tensor of one sample
   static constexpr int NROW = SITE_BYTES / 128;            // 128-byte rows per sample-site
-  static constexpr int HBUF_R = ((TR * 128 + 1023) / 1024) * 1024;  // one 128-byte row of TR samples
-  static constexpr int HBUF_C = ((TC * 128 + 1023) / 1024) * 1024;
+  // Per side and stage: [128-byte row r][site u][sample slot][128 B]; one (r, u) plane of
+  // T samples is T * 128 bytes and starts on a 1024-byte boundary (the swizzle period).
+  static constexpr int PLANE_R = ((TR * 128 + 1023) / 1024) * 1024;
+  static constexpr int PLANE_C = ((TC * 128 + 1023) / 1024) * 1024;
+  static constexpr int HBUF_R = SPS * PLANE_R;  // one 128-byte row of TR samples, SPS sites
+  static constexpr int HBUF_C = SPS * PLANE_C;
   static constexpr int ROW_BOX = NROW * HBUF_R;
   static constexpr int COL_BOX = NROW * HBUF_C;
   static constexpr int STAGE_BYTES = ROW_BOX + COL_BOX;
-  static constexpr int TX_BYTES = (TR + TC) * SITE_BYTES;
+  static constexpr int TX_BYTES = SPS * (TR + TC) * SITE_BYTES;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STAGES * 8 + 2 * STAGES * 4 + 16 + 1024;
   static_assert(SITE_BYTES % 128 == 0, "site tensor must be a whole number of 128-byte rows");
   static_assert(WTR * WTC == 32, "a warp is WTR x WTC threads");
   static_assert(H * CPLX >= 16 && (H * CPLX) % 16 == 0, "a sub-block column must be whole 16-byte chunks");
+  static_assert(SPS == 1 || (TR % 8 == 0 && TC % 8 == 0), "multi-site stages need 1024-byte planes");
 };
 
 // Fills the h x h sub-block A_s[t] (rows: left bond l = t*h + a, columns j) of one sample
@@ -78,7 +86,7 @@ template <class Cfg>
 struct SubLoad {
   using real = typename Cfg::real;
   static constexpr int H = Cfg::H;
-  const uint8_t* buf;  // row-0 buffer of this side (shared memory)
+  const uint8_t* buf;  // row-0 buffer of this side at the current site (shared memory)
   int hbuf;            // bytes between the 128-byte-row buffers of this side
   int slot0;           // sample slot of this thread's first row/column
   int stride;          // slot distance between this thread's rows/columns
@@ -136,45 +144,23 @@ __device__ __forceinline__ void decode_tile(const GramArgs& p, int tr, int tc, i
   }
 }
 
-// ||a - b||^2 over n features with a compensated (Kahan) FP32 sum.
-__device__ __forceinline__ float sq_dist(const float* __restrict__ a, const float* __restrict__ b, int n) {
-  float s = 0.0f, c = 0.0f;
-  int f = 0;
-  if (((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) == 0) {
-    for (; f + 4 <= n; f += 4) {
-      const float4 va = __ldg(reinterpret_cast<const float4*>(a + f));
-      const float4 vb = __ldg(reinterpret_cast<const float4*>(b + f));
-      const float d[4] = {va.x - vb.x, va.y - vb.y, va.z - vb.z, va.w - vb.w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float y = fmaf(d[u], d[u], -c);
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-      }
-    }
-  }
-  for (; f < n; ++f) {
-    const float d = __ldg(a + f) - __ldg(b + f);
-    const float y = fmaf(d, d, -c);
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-  return s;
+// Compensated (Kahan) FP32 accumulation of one squared feature difference.
+__device__ __forceinline__ void kahan_add_sq(float& sum, float& comp, float d) {
+  const float y = fmaf(d, d, -comp);
+  const float t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
 }
 
 template <class Cfg>
-__device__ __forceinline__ void write_pair(const GramArgs& p, float half_log, int i, int j) {
+__device__ __forceinline__ void write_pair(const GramArgs& p, float half_log, float d2, int i, int j) {
   if (i >= p.row0 + p.nrows || j >= p.col0 + p.ncols) return;
   if (p.symmetric && j < i) return;
   const float lr = p.lnorm_r ? p.lnorm_r[i] : 0.0f;
   const float lc = p.lnorm_c ? p.lnorm_c[j] : 0.0f;
   const float lkq = 2.0f * half_log - lr - lc;
   const float kq = expf(lkq);
-  float kc = 0.0f;
-  const bool need_kc = (p.k != nullptr && p.w != 1.0f) || p.kc != nullptr;
-  if (need_kc) kc = expf(-p.gamma * sq_dist(p.x_r + size_t(i) * p.n, p.x_c + size_t(j) * p.n, p.n));
+  const float kc = p.need_kc ? expf(-p.gamma * d2) : 0.0f;
   const float k = p.w * kq + (1.0f - p.w) * kc;
   const long long a = (long long)(i - p.row0) * p.ld + (j - p.col0);
   if (p.k) p.k[a] = k;
@@ -195,7 +181,7 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
     gram_kernel(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_c,
                 const GramArgs p) {
   using real = typename Cfg::real;
-  constexpr int H = Cfg::H, STAGES = Cfg::STAGES, PR = Cfg::PR, PC = Cfg::PC;
+  constexpr int H = Cfg::H, STAGES = Cfg::STAGES, PR = Cfg::PR, PC = Cfg::PC, SPS = Cfg::SPS;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   // 1024-byte aligned base for the 128-byte swizzle, kept as shared-memory pointer arithmetic
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -224,8 +210,9 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
   }
   __syncthreads();
 
+  const int steps = (p.n + SPS - 1) / SPS;  // pipeline stages per tile
   const int my_tiles = (p.ntiles > int(blockIdx.x)) ? (p.ntiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
-  const long long total = (long long)my_tiles * p.n;
+  const long long total = (long long)my_tiles * steps;
 
   auto tile_origin = [&](int local, int& r0, int& c0) {
     int ti, tj;
@@ -233,25 +220,26 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
     r0 = p.row0 + ti * Cfg::TR;
     c0 = p.col0 + tj * Cfg::TC;
   };
-  // Load site k of the tile at (r0, c0) into stage `st` (one thread).
-  auto issue = [&](int st, uint32_t parity, int r0, int c0, int k) {
+  // Load sites js*SPS .. js*SPS+SPS-1 of the tile at (r0, c0) into stage `st` (one thread);
+  // sites past n arrive as zeros and are skipped.
+  auto issue = [&](int st, uint32_t parity, int r0, int c0, int js) {
     uint8_t* base = smem + st * Cfg::STAGE_BYTES;
     inflight[st] = int(parity) + 1;
     mbar_arrive_expect_tx(&full[st], Cfg::TX_BYTES);
 #pragma unroll
     for (int h = 0; h < Cfg::NROW; ++h) {
-      tma_load_3d(base + h * Cfg::HBUF_R, &tm_r, &full[st], h * 32, r0, k);
-      tma_load_3d(base + Cfg::ROW_BOX + h * Cfg::HBUF_C, &tm_c, &full[st], h * 32, c0, k);
+      tma_load_3d(base + h * Cfg::HBUF_R, &tm_r, &full[st], h * 32, r0, js * SPS);
+      tma_load_3d(base + Cfg::ROW_BOX + h * Cfg::HBUF_C, &tm_c, &full[st], h * 32, c0, js * SPS);
     }
   };
 
   if (tid == 0) {
-    int tile = 0, k = 0, r0 = 0, c0 = 0;
+    int tile = 0, js = 0, r0 = 0, c0 = 0;
     for (int q = 0; q < STAGES && q < total; ++q) {
-      if (k == 0) tile_origin(tile, r0, c0);
-      issue(q, 0u, r0, c0, k);
-      if (++k == p.n) {
-        k = 0;
+      if (js == 0) tile_origin(tile, r0, c0);
+      issue(q, 0u, r0, c0, js);
+      if (++js == steps) {
+        js = 0;
         ++tile;
       }
     }
@@ -259,11 +247,11 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
 
   PairE<real, H> st[PR][PC];
   int r0 = 0, c0 = 0;
-  int sidx = 0, k = 0, tile = 0;
+  int sidx = 0, js = 0, tile = 0;
   uint32_t ph = 0;
   long long q = 0;
   for (; q < total; ++q) {
-    if (k == 0) {
+    if (js == 0) {
 #pragma unroll
       for (int pr = 0; pr < PR; ++pr)
 #pragma unroll
@@ -276,11 +264,15 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
       break;
     }
     const uint8_t* base = smem + sidx * Cfg::STAGE_BYTES;
-    const SubLoad<Cfg> ldi{base, Cfg::HBUF_R, slot_r, Cfg::WTR};
-    const SubLoad<Cfg> ldj{base + Cfg::ROW_BOX, Cfg::HBUF_C, slot_c, Cfg::WTC};
-    const bool last = (k == p.n - 1);
-    site_step<real, H, PR, PC>(st, ldi, ldj, last || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1));
-    // Release the stage; the last warp to do so refills it with the site STAGES ahead, so
+#pragma unroll
+    for (int u = 0; u < SPS; ++u) {
+      const int k = js * SPS + u;
+      if (SPS > 1 && k >= p.n) break;
+      const SubLoad<Cfg> ldi{base + u * Cfg::PLANE_R, Cfg::HBUF_R, slot_r, Cfg::WTR};
+      const SubLoad<Cfg> ldj{base + Cfg::ROW_BOX + u * Cfg::PLANE_C, Cfg::HBUF_C, slot_c, Cfg::WTC};
+      site_step<real, H, PR, PC>(st, ldi, ldj, k == p.n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1));
+    }
+    // Release the stage; the last warp to do so refills it with the stage STAGES ahead, so
     // no thread ever waits for the others to free a buffer.
     __syncwarp();
     if (lane == 0) {
@@ -289,32 +281,65 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
         released[sidx] = 0;
         __threadfence_block();
         if (q + STAGES < total) {
-          int kk = k + STAGES, tt = tile;
-          while (kk >= p.n) {
-            kk -= p.n;
+          int jj = js + STAGES, tt = tile;
+          while (jj >= steps) {
+            jj -= steps;
             ++tt;
           }
           int rr = r0, cc = c0;
-          if (tt != tile) tile_origin(tt, rr, cc);  // once per tile, not per site
+          if (tt != tile) tile_origin(tt, rr, cc);  // once per tile, not per stage
           fence_proxy_async_smem();
-          issue(sidx, ph ^ 1u, rr, cc, kk);
+          issue(sidx, ph ^ 1u, rr, cc, jj);
         }
       }
     }
-    if (last) {
+    if (js == steps - 1) {
+      // ||x_i - x_j||^2 of this thread's pairs, Kahan sums over the features, all pairs
+      // interleaved; rows / columns past the block read the last valid sample and are dropped.
+      float d2s[PR][PC], d2c[PR][PC];
+#pragma unroll
+      for (int pr = 0; pr < PR; ++pr)
+#pragma unroll
+        for (int pc = 0; pc < PC; ++pc) {
+          d2s[pr][pc] = 0.0f;
+          d2c[pr][pc] = 0.0f;
+        }
+      if (p.need_kc) {
+        const float* xr[PR];
+        const float* xc[PC];
+#pragma unroll
+        for (int pr = 0; pr < PR; ++pr)
+          xr[pr] = p.x_r + size_t(min(r0 + slot_r + pr * Cfg::WTR, p.row0 + p.nrows - 1)) * p.n;
+#pragma unroll
+        for (int pc = 0; pc < PC; ++pc)
+          xc[pc] = p.x_c + size_t(min(c0 + slot_c + pc * Cfg::WTC, p.col0 + p.ncols - 1)) * p.n;
+#pragma unroll 4
+        for (int f = 0; f < p.n; ++f) {
+          float a[PR], b[PC];
+#pragma unroll
+          for (int pr = 0; pr < PR; ++pr) a[pr] = __ldg(xr[pr] + f);
+#pragma unroll
+          for (int pc = 0; pc < PC; ++pc) b[pc] = __ldg(xc[pc] + f);
+#pragma unroll
+          for (int pr = 0; pr < PR; ++pr)
+#pragma unroll
+            for (int pc = 0; pc < PC; ++pc) kahan_add_sq(d2s[pr][pc], d2c[pr][pc], a[pr] - b[pc]);
+        }
+      }
 #pragma unroll
       for (int pr = 0; pr < PR; ++pr)
 #pragma unroll
         for (int pc = 0; pc < PC; ++pc)
-          write_pair<Cfg>(p, st[pr][pc].half_log_mod(), r0 + slot_r + pr * Cfg::WTR, c0 + slot_c + pc * Cfg::WTC);
+          write_pair<Cfg>(p, st[pr][pc].half_log_mod(), d2s[pr][pc], r0 + slot_r + pr * Cfg::WTR,
+                          c0 + slot_c + pc * Cfg::WTC);
     }
     if (*abort_flag) break;
     if (++sidx == STAGES) {
       sidx = 0;
       ph ^= 1u;
     }
-    if (++k == p.n) {
-      k = 0;
+    if (++js == steps) {
+      js = 0;
       ++tile;
     }
   }
@@ -331,9 +356,9 @@ struct GramLauncher {
   static dk_status run(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, const GramArgs& a,
                        cudaStream_t st) {
     CUtensorMap tmr, tmc;
-    dk_status s = encode_mps_map(ctx, &tmr, mps_r, m_r, a.n, Cfg::SITE_BYTES, Cfg::TR);
+    dk_status s = encode_mps_map(ctx, &tmr, mps_r, m_r, a.n, Cfg::SITE_BYTES, Cfg::TR, Cfg::SPS);
     if (s != DK_OK) return s;
-    s = encode_mps_map(ctx, &tmc, mps_c, m_c, a.n, Cfg::SITE_BYTES, Cfg::TC);
+    s = encode_mps_map(ctx, &tmc, mps_c, m_c, a.n, Cfg::SITE_BYTES, Cfg::TC, Cfg::SPS);
     if (s != DK_OK) return s;
     auto kern = gram_kernel<Cfg>;
     static int occ = -1;  // resident CTAs per SM, per instantiation
@@ -362,6 +387,8 @@ using F32_P12 = GramCfg<float, 4, 8, 4, 1, 2, 4, 4, 4, 1>;     // 32 x 32 pairs,
 using F32_P22w = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 4, 1>;    // 48 x 32 pairs, 384 threads
 using F32_P21w = GramCfg<float, 4, 4, 8, 2, 1, 4, 3, 4, 1>;    // 32 x 24 pairs, 384 threads
 using F32_P14 = GramCfg<float, 4, 8, 4, 1, 4, 4, 2, 4, 1>;     // 32 x 32 pairs, 256 threads
+using F32_P22wS2 = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 3, 1, 2>;  // 48 x 32 pairs, 384 threads, 2 sites/stage
+using F32_P22S2 = GramCfg<float, 4, 4, 8, 2, 2, 4, 2, 3, 1, 2>;   // 32 x 32 pairs, 256 threads, 2 sites/stage
 using F64_P11 = GramCfg<double, 4, 4, 8, 1, 1, 4, 2, 4, 1>;    // 16 x 16 pairs, 256 threads
 
 template <class Cfg>
@@ -389,10 +416,11 @@ template <class Cfg>
 constexpr CfgInfo info_of() {
   return CfgInfo{Cfg::TR, Cfg::TC, Cfg::NTHREADS};
 }
-// Shapes selectable for complex64 / chi 4, in id order 1..7; the built-in choice is id 5.
+// Shapes selectable for complex64 / chi 4, in id order 1..9; the built-in choice is id 8.
 static const CfgInfo kF32Chi4[] = {info_of<F32_P11>(),  info_of<F32_P21>(),  info_of<F32_P22>(), info_of<F32_P12>(),
-                                   info_of<F32_P22w>(), info_of<F32_P21w>(), info_of<F32_P14>()};
-constexpr int kF32Chi4Default = 5;
+                                   info_of<F32_P22w>(), info_of<F32_P21w>(), info_of<F32_P14>(),
+                                   info_of<F32_P22wS2>(), info_of<F32_P22S2>()};
+constexpr int kF32Chi4Default = 8;
 static const CfgInfo kF64Chi4[] = {info_of<F64_P11>()};
 
 static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, int chi,
@@ -406,8 +434,10 @@ static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const vo
       case 5: return launch_gram<F32_P22w>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 6: return launch_gram<F32_P21w>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 7: return launch_gram<F32_P14>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 8: return launch_gram<F32_P22wS2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 9: return launch_gram<F32_P22S2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 3: return launch_gram<F32_P22>(ctx, mps_r, m_r, mps_c, m_c, a, st);
-      default: return launch_gram<F32_P22w>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      default: return launch_gram<F32_P22wS2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
     }
   }
   if (dtype == DK_C128 && prec == DK_PREC_F64 && chi == 4)
@@ -459,6 +489,7 @@ DK_API dk_status dk_gram_tile(dk_ctx* ctx, const void* mps_rows, int m_rows, con
   a.lkq = logkq_out;
   a.ld = ld;
   a.status = ctx->status;
+  a.need_kc = need_x ? 1 : 0;
   return gram_dispatch(ctx, mps_rows, m_rows, mps_cols, m_cols, chi_max, dtype, prec, a,
                        static_cast<cudaStream_t>(stream));
 }

@@ -32,9 +32,9 @@ inline size_t site_bytes(int chi_max, dk_dtype dtype) {
 }
 
 // Tensor map over an MPS buffer viewed as [n sites][m samples][site_bytes/4 floats]:
-// box = 32 floats (128 B) x `box_samples` samples x 1 site, 128-byte swizzle.
+// box = 32 floats (128 B) x `box_samples` samples x `box_sites` sites, 128-byte swizzle.
 dk_status encode_mps_map(dk_ctx* ctx, CUtensorMap* map, const void* mps, int m, int n, size_t site_bytes,
-                         int box_samples);
+                         int box_samples, int box_sites);
 
 inline dk_status launch_status() {
   cudaError_t e = cudaGetLastError();

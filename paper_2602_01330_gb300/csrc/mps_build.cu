@@ -423,7 +423,7 @@ struct GlobalSub {
 };
 
 template <typename real, int H>
-__global__ void __launch_bounds__(128) self_overlap_kernel(const real* __restrict__ mps, int m, int n,
+__global__ void __launch_bounds__(32) self_overlap_kernel(const real* __restrict__ mps, int m, int n,
                                                            float* __restrict__ log_norm) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
@@ -493,11 +493,12 @@ DK_API dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const d
   else if (chi == 16 && fm->reps == 4) s = launch_build<8, 8>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
   else if (chi == 32 && fm->reps == 5) s = launch_build<16, 16>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
   if (s != DK_OK || !log_norm) return s;
-  const int grid = (m + 127) / 128;
+  // one warp per CTA: each thread runs a whole n-site chain, so spread the chains over SMs
+  const int grid = (m + 31) / 32;
   if (dtype == DK_C64) {
-    self_overlap_kernel<float, 2><<<grid, 128, 0, st>>>(static_cast<const float*>(mps), m, n, log_norm);
+    self_overlap_kernel<float, 2><<<grid, 32, 0, st>>>(static_cast<const float*>(mps), m, n, log_norm);
   } else {
-    self_overlap_kernel<double, 2><<<grid, 128, 0, st>>>(static_cast<const double*>(mps), m, n, log_norm);
+    self_overlap_kernel<double, 2><<<grid, 32, 0, st>>>(static_cast<const double*>(mps), m, n, log_norm);
   }
   return launch_status();
 }

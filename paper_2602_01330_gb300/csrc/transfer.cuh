@@ -126,6 +126,7 @@ __device__ __forceinline__ void term(Blk<real, H>& acc, const Blk<real, H>& e, c
   for (int a = 0; a < H; ++a)
 #pragma unroll
     for (int c = 0; c < H; ++c) {
+      // operand order keeps each register in two consecutive FMAs (operand reuse)
       real fr = e.r[a][0] * aj.r[0][c];
       real fi = e.r[a][0] * aj.i[0][c];
       fr = fma(-e.i[a][0], aj.i[0][c], fr);
@@ -133,8 +134,8 @@ __device__ __forceinline__ void term(Blk<real, H>& acc, const Blk<real, H>& e, c
 #pragma unroll
       for (int b = 1; b < H; ++b) {
         fr = fma(e.r[a][b], aj.r[b][c], fr);
-        fr = fma(-e.i[a][b], aj.i[b][c], fr);
         fi = fma(e.r[a][b], aj.i[b][c], fi);
+        fr = fma(-e.i[a][b], aj.i[b][c], fr);
         fi = fma(e.i[a][b], aj.r[b][c], fi);
       }
       f.r[a][c] = fr;
@@ -149,8 +150,8 @@ __device__ __forceinline__ void term(Blk<real, H>& acc, const Blk<real, H>& e, c
 #pragma unroll
       for (int a = 0; a < H; ++a) {
         ar = fma(ai.r[a][p], f.r[a][c], ar);
-        ar = fma(ai.i[a][p], f.i[a][c], ar);
         aim = fma(ai.r[a][p], f.i[a][c], aim);
+        ar = fma(ai.i[a][p], f.i[a][c], ar);
         aim = fma(-ai.i[a][p], f.r[a][c], aim);
       }
       acc.r[p][c] = ar;
