@@ -95,6 +95,14 @@ const char* dk_error_string(dk_status status);
  * kernel recorded an error since the last call). */
 dk_status dk_sync_status(dk_ctx* ctx, void* stream);
 
+/* Failure-detection self test: launches a kernel whose wait can never be satisfied (an
+ * mbarrier that nothing arrives on), bounded by limit_ns (1 .. 2e9). The kernel gives up,
+ * records DK_ERR_TIMEOUT in the status word and returns, so the next dk_sync_status
+ * reports DK_ERR_TIMEOUT and the context stays usable. This exercises the same bounded
+ * wait and status path as the Gram kernels without faulting or hanging the GPU.
+ * Errors: DK_ERR_ARG for NULL ctx or limit_ns outside 1 .. 2e9; DK_ERR_CUDA. */
+dk_status dk_selftest_wait_timeout(dk_ctx* ctx, unsigned long long limit_ns, void* stream);
+
 /* Bytes of an MPS buffer for m samples, n sites, padded bond chi_max. */
 size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
 
@@ -115,7 +123,8 @@ size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
  *              calls; passing it to them normalises K_q so that K_q(x, x) = 1.
  * Errors: DK_ERR_ARG (m < 1, n < 1, NULL x/mps/fm, reps outside 1..5, misaligned mps),
  *         DK_ERR_UNSUPPORTED (chi_max not in {4, 8, 16, 32} or below 2^reps; log_norm
- *         requested with chi_max != 4). */
+ *         requested for a chi_max / dtype without a Gram kernel: complex64 has chi_max 4
+ *         and 8, complex128 chi_max 4). */
 dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm,
                        dk_dtype dtype, void* mps, int32_t* bond_dims, float* log_norm,
                        void* stream);

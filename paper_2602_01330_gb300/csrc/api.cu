@@ -88,6 +88,21 @@ DK_API size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype) {
 
 namespace dk {
 
+// A wait that nothing will ever satisfy: an mbarrier expecting one arrival that never comes.
+// The bounded wait gives up after limit_ns and records DEV_TIMEOUT, exactly as the Gram
+// kernels do when a copy fails to land.
+__global__ void __launch_bounds__(32) wait_timeout_kernel(unsigned* status, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  if (!mbar_wait_bounded(&bar, 0u, limit_ns)) {
+    if (threadIdx.x == 0) record_status(status, DEV_TIMEOUT);
+  }
+}
+
 dk_status encode_mps_map(dk_ctx* ctx, CUtensorMap* map, const void* mps, int m, int n, size_t sbytes,
                          int box_samples, int box_sites) {
   if (sbytes % 128 != 0 || box_samples < 1 || box_samples > 256 || box_sites < 1 || box_sites > 8)
@@ -103,3 +118,9 @@ dk_status encode_mps_map(dk_ctx* ctx, CUtensorMap* map, const void* mps, int m, 
 }
 
 }  // namespace dk
+
+DK_API dk_status dk_selftest_wait_timeout(dk_ctx* ctx, unsigned long long limit_ns, void* stream) {
+  if (!ctx || limit_ns == 0 || limit_ns > dk::WAIT_LIMIT_NS) return DK_ERR_ARG;
+  dk::wait_timeout_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(ctx->status, limit_ns);
+  return dk::launch_status();
+}

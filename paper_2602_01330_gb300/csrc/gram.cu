@@ -390,6 +390,7 @@ using F32_P14 = GramCfg<float, 4, 8, 4, 1, 4, 4, 2, 4, 1>;     // 32 x 32 pairs,
 using F32_P22wS2 = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 3, 1, 2>;  // 48 x 32 pairs, 384 threads, 2 sites/stage
 using F32_P22S2 = GramCfg<float, 4, 4, 8, 2, 2, 4, 2, 3, 1, 2>;   // 32 x 32 pairs, 256 threads, 2 sites/stage
 using F64_P11 = GramCfg<double, 4, 4, 8, 1, 1, 4, 2, 4, 1>;    // 16 x 16 pairs, 256 threads
+using F32X8_P11 = GramCfg<float, 8, 4, 8, 1, 1, 4, 2, 4, 1>;   // chi = 8: 16 x 16 pairs, 256 threads
 
 template <class Cfg>
 static dk_status launch_gram(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
@@ -422,6 +423,7 @@ static const CfgInfo kF32Chi4[] = {info_of<F32_P11>(),  info_of<F32_P21>(),  inf
                                    info_of<F32_P22wS2>(), info_of<F32_P22S2>()};
 constexpr int kF32Chi4Default = 8;
 static const CfgInfo kF64Chi4[] = {info_of<F64_P11>()};
+static const CfgInfo kF32Chi8[] = {info_of<F32X8_P11>()};
 
 static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, int chi,
                                dk_dtype dtype, dk_precision prec, const GramArgs& a, cudaStream_t st) {
@@ -442,6 +444,8 @@ static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const vo
   }
   if (dtype == DK_C128 && prec == DK_PREC_F64 && chi == 4)
     return launch_gram<F64_P11>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+  if (dtype == DK_C64 && prec == DK_PREC_F32 && chi == 8)
+    return launch_gram<F32X8_P11>(ctx, mps_r, m_r, mps_c, m_c, a, st);
   return DK_ERR_UNSUPPORTED;
 }
 
@@ -497,6 +501,7 @@ DK_API dk_status dk_gram_tile(dk_ctx* ctx, const void* mps_rows, int m_rows, con
 DK_API int dk_gram_config_count(dk_dtype dtype, int chi_max) {
   if (dtype == DK_C64 && chi_max == 4) return int(sizeof(dk::kF32Chi4) / sizeof(dk::kF32Chi4[0]));
   if (dtype == DK_C128 && chi_max == 4) return int(sizeof(dk::kF64Chi4) / sizeof(dk::kF64Chi4[0]));
+  if (dtype == DK_C64 && chi_max == 8) return int(sizeof(dk::kF32Chi8) / sizeof(dk::kF32Chi8[0]));
   return 0;
 }
 
@@ -504,8 +509,8 @@ DK_API dk_status dk_gram_config_info(dk_dtype dtype, int chi_max, int id, int* t
                                      int* threads) {
   const int count = dk_gram_config_count(dtype, chi_max);
   if (id < 0 || id > count || count == 0) return DK_ERR_ARG;
-  const dk::CfgInfo* tab = dtype == DK_C64 ? dk::kF32Chi4 : dk::kF64Chi4;
-  const int idx = (id == 0 ? (dtype == DK_C64 ? dk::kF32Chi4Default : 1) : id) - 1;
+  const dk::CfgInfo* tab = dtype == DK_C64 ? (chi_max == 4 ? dk::kF32Chi4 : dk::kF32Chi8) : dk::kF64Chi4;
+  const int idx = (id == 0 ? ((dtype == DK_C64 && chi_max == 4) ? dk::kF32Chi4Default : 1) : id) - 1;
   if (tile_rows) *tile_rows = tab[idx].tile_rows;
   if (tile_cols) *tile_cols = tab[idx].tile_cols;
   if (threads) *threads = tab[idx].threads;

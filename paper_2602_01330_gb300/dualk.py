@@ -25,7 +25,7 @@ _STATUS_NAMES = {0: "DK_OK", 1: "DK_ERR_ARG", 2: "DK_ERR_UNSUPPORTED", 3: "DK_ER
 
 EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_mps_bytes",
             "dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows", "dk_gram_config_count",
-            "dk_gram_config_info", "dk_set_gram_config")
+            "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout")
 
 
 class DualKError(RuntimeError):
@@ -75,6 +75,8 @@ def _lib():
     lib.dk_gram_config_info.restype = i32
     lib.dk_set_gram_config.argtypes = [vp, i32]
     lib.dk_set_gram_config.restype = i32
+    lib.dk_selftest_wait_timeout.argtypes = [vp, ctypes.c_ulonglong, vp]
+    lib.dk_selftest_wait_timeout.restype = i32
     _LIB = lib
     return lib
 
@@ -157,6 +159,11 @@ class Context:
 
     def sync_status(self, stream=None):
         _check(_lib().dk_sync_status(self.handle, _stream(stream)), "dk_sync_status")
+
+    def selftest_wait_timeout(self, limit_ns: int = 50_000_000, stream=None):
+        """dk_selftest_wait_timeout: a bounded wait that must time out (see include/dualk.h)."""
+        _check(_lib().dk_selftest_wait_timeout(self.handle, int(limit_ns), _stream(stream)),
+               "dk_selftest_wait_timeout")
 
     def set_gram_config(self, cfg_id: int):
         """dk_set_gram_config: 0 = built-in tile shape, 1..gram_config_count() = a fixed one."""

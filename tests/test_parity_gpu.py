@@ -222,3 +222,58 @@ def test_n784_bench_shape_sampled(dk):
     assert bool(torch.all(torch.diagonal(kq) == 1.0))
     assert bool(torch.equal(kq, kq.T))
     ctx.sync_status()
+
+
+@pytest.mark.parametrize("n,reps", [(8, 3), (11, 3)])
+def test_chi8_fp32_vs_statevector(dk, n, reps):
+    """reps = 3 keeps the exact bond 8: the chi = 8 FP32 kernels against brute force."""
+    dualk, ctx, torch = dk
+    from oracle import circuit
+    from paper_2602_01330_gb300 import synthetic
+    x = synthetic.uniform_angles(21, n, seed=n)
+    ref = circuit.kernel_matrix(x, x, reps)
+    m = dualk.mps_build(ctx, _dev(torch, x), dualk.FeatureMap(reps=reps, chi_max=8))
+    out = dualk.gram(ctx, m, w=1.0)
+    torch.cuda.synchronize()
+    kq = out["kq"].cpu().numpy()
+    assert np.max(np.abs(kq - ref)) <= TOL_K
+    assert np.all(np.diag(kq) == 1.0)
+    assert m.bond_dims.cpu().tolist()[:5] == [1, 2, 4, 8, 8][:5]
+
+
+def test_chi8_fmnist_d256_sampled(dk):
+    """reps = 3 at d = 256 (the precision-form data, exact bond 8): 40 train x 40 train and
+    10 test rows against the oracle, element by element."""
+    dualk, ctx, torch = dk
+    from oracle import gram as og
+    from paper_2602_01330_gb300 import synthetic
+    d = synthetic.fmnist_like(40, 10, 256)
+    xtr, xte = d["x_train"], d["x_test"]
+    fm = dualk.FeatureMap(reps=3, chi_max=8)
+    mtr = dualk.mps_build(ctx, _dev(torch, xtr), fm)
+    mte = dualk.mps_build(ctx, _dev(torch, xte), fm)
+    out = dualk.gram(ctx, mtr, w=0.5)
+    rows = dualk.dual_kernel_rows(ctx, mte, mtr, w=0.5)
+    torch.cuda.synchronize()
+    kq, lkq = _oracle_block(xtr, xtr, 3)
+    _check_block(out, kq, lkq, og.rbf(xtr, xtr, 1 / 256), 0.5)
+    kq, lkq = _oracle_block(xte, xtr, 3)
+    _check_block(rows, kq, lkq, og.rbf(xte, xtr, 1 / 256), 0.5)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(dk):
+    """A device wait that nothing satisfies gives up after its bound, the status word says
+    DK_ERR_TIMEOUT, and the same context then runs a Gram normally."""
+    dualk, ctx, torch = dk
+    ctx.sync_status()
+    ctx.selftest_wait_timeout(50_000_000)
+    with pytest.raises(dualk.DualKError) as e:
+        ctx.sync_status()
+    assert e.value.status == 4
+    ctx.sync_status()  # cleared
+    x = torch.rand(9, 6, device="cuda") * 3
+    m = dualk.mps_build(ctx, x, dualk.FeatureMap(reps=2, chi_max=4))
+    out = dualk.gram(ctx, m, w=1.0, want=("kq",))
+    torch.cuda.synchronize()
+    assert bool(torch.all(torch.diagonal(out["kq"]) == 1.0))
+    ctx.sync_status()
