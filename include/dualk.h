@@ -123,8 +123,8 @@ size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
  *              calls; passing it to them normalises K_q so that K_q(x, x) = 1.
  * Errors: DK_ERR_ARG (m < 1, n < 1, NULL x/mps/fm, reps outside 1..5, misaligned mps),
  *         DK_ERR_UNSUPPORTED (chi_max not in {4, 8, 16, 32} or below 2^reps; log_norm
- *         requested for a chi_max / dtype without a Gram kernel: complex64 has chi_max 4
- *         and 8, complex128 chi_max 4). */
+ *         requested for a chi_max / dtype without a Gram kernel: complex64 has chi_max 4,
+ *         8 and 32, complex128 chi_max 4). */
 dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm,
                        dk_dtype dtype, void* mps, int32_t* bond_dims, float* log_norm,
                        void* stream);

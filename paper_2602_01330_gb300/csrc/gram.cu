@@ -23,28 +23,10 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "gram_common.cuh"
 #include "transfer.cuh"
 
 namespace dk {
-
-struct GramArgs {
-  int n;
-  int row0, nrows, col0, ncols;
-  int tiles_r, tiles_c, ntiles;
-  int symmetric;
-  const float* lnorm_r;
-  const float* lnorm_c;
-  const float* x_r;
-  const float* x_c;
-  float gamma, w;
-  float* k;
-  float* kq;
-  float* kc;
-  float* lkq;
-  long long ld;
-  unsigned* status;
-  int need_kc;  // K_c is needed (k_out with w != 1, or kc_out)
-};
 
 template <typename real_, int CHI_, int WTR_, int WTC_, int PR_, int PC_, int WR_, int WC_, int STAGES_, int MINB_,
           int SPS_ = 1>
@@ -118,63 +100,6 @@ struct SubLoad {
     }
   }
 };
-
-// First column tile of row tile ti that holds a pair with j >= i (symmetric Gram): the
-// tile (ti, tj) covers rows from ti*TR and columns up to (tj+1)*TC - 1.
-__host__ __device__ __forceinline__ int first_upper_tile(int ti, int tr, int tc) { return (ti * tr) / tc; }
-
-// Tile index t (row-major over the tiles that are computed) -> (row tile, column tile).
-__device__ __forceinline__ void decode_tile(const GramArgs& p, int tr, int tc, int t, int& ti, int& tj) {
-  if (p.symmetric) {
-    int r = 0;
-    while (true) {
-      const int first = first_upper_tile(r, tr, tc);
-      const int cnt = first < p.tiles_c ? p.tiles_c - first : 0;
-      if (t < cnt || r + 1 >= p.tiles_r) {
-        ti = r;
-        tj = first + t;
-        return;
-      }
-      t -= cnt;
-      ++r;
-    }
-  } else {
-    ti = t / p.tiles_c;
-    tj = t - ti * p.tiles_c;
-  }
-}
-
-// Compensated (Kahan) FP32 accumulation of one squared feature difference.
-__device__ __forceinline__ void kahan_add_sq(float& sum, float& comp, float d) {
-  const float y = fmaf(d, d, -comp);
-  const float t = sum + y;
-  comp = (t - sum) - y;
-  sum = t;
-}
-
-template <class Cfg>
-__device__ __forceinline__ void write_pair(const GramArgs& p, float half_log, float d2, int i, int j) {
-  if (i >= p.row0 + p.nrows || j >= p.col0 + p.ncols) return;
-  if (p.symmetric && j < i) return;
-  const float lr = p.lnorm_r ? p.lnorm_r[i] : 0.0f;
-  const float lc = p.lnorm_c ? p.lnorm_c[j] : 0.0f;
-  const float lkq = 2.0f * half_log - lr - lc;
-  const float kq = expf(lkq);
-  const float kc = p.need_kc ? expf(-p.gamma * d2) : 0.0f;
-  const float k = p.w * kq + (1.0f - p.w) * kc;
-  const long long a = (long long)(i - p.row0) * p.ld + (j - p.col0);
-  if (p.k) p.k[a] = k;
-  if (p.kq) p.kq[a] = kq;
-  if (p.kc) p.kc[a] = kc;
-  if (p.lkq) p.lkq[a] = lkq;
-  if (p.symmetric && i != j) {
-    const long long b = (long long)(j - p.col0) * p.ld + (i - p.row0);
-    if (p.k) p.k[b] = k;
-    if (p.kq) p.kq[b] = kq;
-    if (p.kc) p.kc[b] = kc;
-    if (p.lkq) p.lkq[b] = lkq;
-  }
-}
 
 template <class Cfg>
 __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
@@ -330,7 +255,7 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
       for (int pr = 0; pr < PR; ++pr)
 #pragma unroll
         for (int pc = 0; pc < PC; ++pc)
-          write_pair<Cfg>(p, st[pr][pc].half_log_mod(), d2s[pr][pc], r0 + slot_r + pr * Cfg::WTR,
+          write_pair(p, st[pr][pc].half_log_mod(), d2s[pr][pc], r0 + slot_r + pr * Cfg::WTR,
                           c0 + slot_c + pc * Cfg::WTC);
     }
     if (*abort_flag) break;
@@ -395,18 +320,7 @@ using F32X8_P11 = GramCfg<float, 8, 4, 8, 1, 1, 4, 2, 4, 1>;   // chi = 8: 16 x 
 template <class Cfg>
 static dk_status launch_gram(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
                              cudaStream_t st) {
-  a.tiles_r = (a.nrows + Cfg::TR - 1) / Cfg::TR;
-  a.tiles_c = (a.ncols + Cfg::TC - 1) / Cfg::TC;
-  if (a.symmetric) {
-    long long cnt = 0;
-    for (int ti = 0; ti < a.tiles_r; ++ti) {
-      const int first = first_upper_tile(ti, Cfg::TR, Cfg::TC);
-      if (first < a.tiles_c) cnt += a.tiles_c - first;
-    }
-    a.ntiles = int(cnt);
-  } else {
-    a.ntiles = a.tiles_r * a.tiles_c;
-  }
+  a.ntiles = count_tiles(a, Cfg::TR, Cfg::TC);
   return GramLauncher<Cfg>::run(ctx, mps_r, m_r, mps_c, m_c, a, st);
 }
 
@@ -446,6 +360,7 @@ static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const vo
     return launch_gram<F64_P11>(ctx, mps_r, m_r, mps_c, m_c, a, st);
   if (dtype == DK_C64 && prec == DK_PREC_F32 && chi == 8)
     return launch_gram<F32X8_P11>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+  if (dtype == DK_C64 && prec == DK_PREC_F32 && chi == 32) return gram32_launch(ctx, mps_r, m_r, mps_c, m_c, a, st);
   return DK_ERR_UNSUPPORTED;
 }
 

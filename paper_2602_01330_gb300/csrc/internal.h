@@ -36,6 +36,12 @@ inline size_t site_bytes(int chi_max, dk_dtype dtype) {
 dk_status encode_mps_map(dk_ctx* ctx, CUtensorMap* map, const void* mps, int m, int n, size_t site_bytes,
                          int box_samples, int box_sites);
 
+struct GramArgs;
+// Bond-32 kernels (gram32.cu): the FP32 Gram and the matching self-overlap.
+dk_status gram32_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
+                        cudaStream_t st);
+dk_status self_overlap32_launch(const void* mps, int m, int n, float* log_norm, cudaStream_t st);
+
 inline dk_status launch_status() {
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? DK_OK : DK_ERR_CUDA;

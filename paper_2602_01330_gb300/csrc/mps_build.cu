@@ -480,7 +480,7 @@ DK_API dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const d
   if (chi != 4 && chi != 8 && chi != 16 && chi != 32) return DK_ERR_UNSUPPORTED;
   if (chi < (1 << fm->reps)) return DK_ERR_UNSUPPORTED;
   if (!aligned16(mps)) return DK_ERR_ARG;
-  if (log_norm && !(chi == 4 || (chi == 8 && dtype == DK_C64))) return DK_ERR_UNSUPPORTED;
+  if (log_norm && !(chi == 4 || (dtype == DK_C64 && (chi == 8 || chi == 32)))) return DK_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int c128 = dtype == DK_C128 ? 1 : 0;
   dk_status s = DK_ERR_UNSUPPORTED;
@@ -495,6 +495,7 @@ DK_API dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const d
   if (s != DK_OK || !log_norm) return s;
   // one warp per CTA: each thread runs a whole n-site chain, so spread the chains over SMs
   const int grid = (m + 31) / 32;
+  if (dtype == DK_C64 && chi == 32) return self_overlap32_launch(mps, m, n, log_norm, st);
   if (dtype == DK_C64 && chi == 8) {
     self_overlap_kernel<float, 4><<<grid, 32, 0, st>>>(static_cast<const float*>(mps), m, n, log_norm);
   } else if (dtype == DK_C64) {

@@ -277,3 +277,42 @@ def test_bounded_wait_reports_timeout_and_context_survives(dk):
     torch.cuda.synchronize()
     assert bool(torch.all(torch.diagonal(out["kq"]) == 1.0))
     ctx.sync_status()
+
+
+def test_chi32_fp32_vs_statevector(dk):
+    """reps = 5 reaches bond 32 at n = 12: the bond-32 FP32 kernels against brute force."""
+    dualk, ctx, torch = dk
+    from oracle import circuit
+    from paper_2602_01330_gb300 import synthetic
+    x = synthetic.uniform_angles(11, 12, seed=12)
+    ref = circuit.kernel_matrix(x, x, 5)
+    m = dualk.mps_build(ctx, _dev(torch, x), dualk.FeatureMap(reps=5, chi_max=32))
+    out = dualk.gram(ctx, m, w=1.0)
+    torch.cuda.synchronize()
+    kq = out["kq"].cpu().numpy()
+    assert np.max(np.abs(kq - ref)) <= TOL_K
+    assert np.all(np.diag(kq) == 1.0)
+    assert np.array_equal(kq, kq.T)
+    assert m.bond_dims.cpu().tolist() == [1, 2, 4, 8, 16, 32, 32, 32, 32, 32, 32, 32, 1]
+    ctx.sync_status()
+
+
+def test_chi32_fmnist_d256_sampled(dk):
+    """The precision-form data (d = 256) at reps = 5 (bond 32): 8 train x 8 train and
+    4 test rows against the oracle (TEBD, untruncated), element by element."""
+    dualk, ctx, torch = dk
+    from oracle import gram as og
+    from paper_2602_01330_gb300 import synthetic
+    d = synthetic.fmnist_like(8, 4, 256)
+    xtr, xte = d["x_train"], d["x_test"]
+    fm = dualk.FeatureMap(reps=5, chi_max=32)
+    mtr = dualk.mps_build(ctx, _dev(torch, xtr), fm)
+    mte = dualk.mps_build(ctx, _dev(torch, xte), fm)
+    out = dualk.gram(ctx, mtr, w=0.5)
+    rows = dualk.dual_kernel_rows(ctx, mte, mtr, w=0.5)
+    torch.cuda.synchronize()
+    kq, lkq = _oracle_block(xtr, xtr, 5)
+    _check_block(out, kq, lkq, og.rbf(xtr, xtr, 1 / 256), 0.5)
+    kq, lkq = _oracle_block(xte, xtr, 5)
+    _check_block(rows, kq, lkq, og.rbf(xte, xtr, 1 / 256), 0.5)
+    ctx.sync_status()
