@@ -64,10 +64,14 @@ typedef enum {
 typedef enum { DK_C64 = 0, DK_C128 = 1 } dk_dtype;
 
 /* Arithmetic of the transfer contraction. F32: complex64 tensors, FP32 FMA on CUDA
- * cores. F64: complex128 tensors, FP64. */
+ * cores (chi_max 4, 8, 32). F64: complex128 tensors, FP64 (chi_max 4). BF16X3: complex64
+ * tensors at chi_max 32 on tensor cores, each FP32 operand split into two BF16 halves
+ * (hi + lo) and each product formed as hi.hi + hi.lo + lo.hi with FP32 accumulation
+ * (about 16 significant bits per product). */
 typedef enum {
   DK_PREC_F32 = 0,
-  DK_PREC_F64 = 1
+  DK_PREC_F64 = 1,
+  DK_PREC_BF16X3 = 2
 } dk_precision;
 
 typedef struct dk_ctx dk_ctx;
@@ -128,6 +132,17 @@ size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
 dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm,
                        dk_dtype dtype, void* mps, int32_t* bond_dims, float* log_norm,
                        void* stream);
+
+/* ln|<psi~_i|psi~_i>| of the stored (rounded) MPS of m samples, computed with the
+ * arithmetic of precision `prec`, so that a Gram call with the same precision and these
+ * normalisers gives K_q(x, x) = 1 exactly (§II-C, Eq. 7 for unit-norm states).
+ * dk_mps_build already writes the F32 (complex64) / F64 (complex128) normalisers; this
+ * call provides them for another precision (BF16X3).
+ *   mps: device MPS (dk_mps_build layout); log_norm: m floats (device, written).
+ * Errors: DK_ERR_ARG (NULL pointers, m or n < 1), DK_ERR_UNSUPPORTED (no kernel for
+ *         chi_max / dtype / prec). */
+dk_status dk_self_overlap(dk_ctx* ctx, const void* mps, int m, int n, int chi_max, dk_dtype dtype,
+                          dk_precision prec, float* log_norm, void* stream);
 
 /* One block of the Gram matrix (§II-D: block (i:i+B, j:j+B) contracted by a GPU
  * worker), with the RBF kernel and the mix fused into the epilogue.

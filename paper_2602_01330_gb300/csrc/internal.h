@@ -41,6 +41,13 @@ struct GramArgs;
 dk_status gram32_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
                         cudaStream_t st);
 dk_status self_overlap32_launch(const void* mps, int m, int n, float* log_norm, cudaStream_t st);
+// Bond-32 tensor-core kernels (gram32_tc.cu): split-BF16 Gram and self-overlap.
+dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
+                           cudaStream_t st);
+dk_status self_overlap32_tc_launch(const void* mps, int m, int n, float* log_norm, cudaStream_t st);
+// Self-overlap normalisers of the chi_max 4 / 8 kernels (mps_build.cu).
+dk_status self_overlap_launch(const void* mps, int m, int n, int chi, dk_dtype dtype, float* log_norm,
+                              cudaStream_t st);
 
 inline dk_status launch_status() {
   cudaError_t e = cudaGetLastError();

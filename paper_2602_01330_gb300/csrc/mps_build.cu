@@ -468,6 +468,20 @@ static dk_status launch_build(const float* x, int m, int n, const dk_fmap* fm, i
   return launch_status();
 }
 
+DK_API dk_status dk_self_overlap(dk_ctx* ctx, const void* mps, int m, int n, int chi_max, dk_dtype dtype,
+                                 dk_precision prec, float* log_norm, void* stream) {
+  using namespace dk;
+  if (!ctx || !mps || !log_norm || m < 1 || n < 1) return DK_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == DK_PREC_BF16X3) {
+    if (dtype != DK_C64 || chi_max != 32) return DK_ERR_UNSUPPORTED;
+    return self_overlap32_tc_launch(mps, m, n, log_norm, st);
+  }
+  if ((prec == DK_PREC_F32 && dtype != DK_C64) || (prec == DK_PREC_F64 && dtype != DK_C128)) return DK_ERR_UNSUPPORTED;
+  if (prec != DK_PREC_F32 && prec != DK_PREC_F64) return DK_ERR_UNSUPPORTED;
+  return self_overlap_launch(mps, m, n, chi_max, dtype, log_norm, st);
+}
+
 }  // namespace dk
 
 DK_API dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm, dk_dtype dtype,
@@ -493,15 +507,23 @@ DK_API dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const d
   else if (chi == 16 && fm->reps == 4) s = launch_build<8, 8>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
   else if (chi == 32 && fm->reps == 5) s = launch_build<16, 16>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
   if (s != DK_OK || !log_norm) return s;
+  return self_overlap_launch(mps, m, n, chi, dtype, log_norm, st);
+}
+
+dk_status dk::self_overlap_launch(const void* mps, int m, int n, int chi, dk_dtype dtype, float* log_norm,
+                                  cudaStream_t st) {
+  using namespace dk;
   // one warp per CTA: each thread runs a whole n-site chain, so spread the chains over SMs
   const int grid = (m + 31) / 32;
   if (dtype == DK_C64 && chi == 32) return self_overlap32_launch(mps, m, n, log_norm, st);
   if (dtype == DK_C64 && chi == 8) {
     self_overlap_kernel<float, 4><<<grid, 32, 0, st>>>(static_cast<const float*>(mps), m, n, log_norm);
-  } else if (dtype == DK_C64) {
+  } else if (dtype == DK_C64 && chi == 4) {
     self_overlap_kernel<float, 2><<<grid, 32, 0, st>>>(static_cast<const float*>(mps), m, n, log_norm);
-  } else {
+  } else if (dtype == DK_C128 && chi == 4) {
     self_overlap_kernel<double, 2><<<grid, 32, 0, st>>>(static_cast<const double*>(mps), m, n, log_norm);
+  } else {
+    return DK_ERR_UNSUPPORTED;
   }
   return launch_status();
 }

@@ -18,14 +18,14 @@ LIB_PATH = os.path.join(_HERE, "libdualk.so")
 
 DK_OK = 0
 DK_C64, DK_C128 = 0, 1
-DK_PREC_F32, DK_PREC_F64 = 0, 1
+DK_PREC_F32, DK_PREC_F64, DK_PREC_BF16X3 = 0, 1, 2
 
 _STATUS_NAMES = {0: "DK_OK", 1: "DK_ERR_ARG", 2: "DK_ERR_UNSUPPORTED", 3: "DK_ERR_CUDA",
                  4: "DK_ERR_TIMEOUT", 5: "DK_ERR_WORKSPACE", 6: "DK_ERR_NO_DEVICE"}
 
 EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_mps_bytes",
             "dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows", "dk_gram_config_count",
-            "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout")
+            "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout", "dk_self_overlap")
 
 
 class DualKError(RuntimeError):
@@ -75,6 +75,8 @@ def _lib():
     lib.dk_gram_config_info.restype = i32
     lib.dk_set_gram_config.argtypes = [vp, i32]
     lib.dk_set_gram_config.restype = i32
+    lib.dk_self_overlap.argtypes = [vp, vp, i32, i32, i32, i32, i32, vp, vp]
+    lib.dk_self_overlap.restype = i32
     lib.dk_selftest_wait_timeout.argtypes = [vp, ctypes.c_ulonglong, vp]
     lib.dk_selftest_wait_timeout.restype = i32
     _LIB = lib
@@ -130,6 +132,18 @@ class MPS:
     bond_dims: torch.Tensor   # int32, n + 1
     log_norm: torch.Tensor    # float32, m
     x: torch.Tensor           # float32 m x n features it was built from
+    norms: dict | None = None  # precision -> log_norm computed with that arithmetic
+
+    def log_norm_for(self, ctx: "Context", prec: int, stream=None) -> torch.Tensor:
+        """ln-norms matching the Gram precision `prec` (dk_self_overlap when not built in)."""
+        native = DK_PREC_F32 if self.dtype == DK_C64 else DK_PREC_F64
+        if prec == native:
+            return self.log_norm
+        if self.norms is None:
+            self.norms = {}
+        if prec not in self.norms:
+            self.norms[prec] = self_overlap(ctx, self, prec, stream=stream)
+        return self.norms[prec]
 
     def complex_view(self):
         """[site][sample][s][j][l] view of the compact block layout (see include/dualk.h)."""
@@ -212,6 +226,19 @@ def mps_build(ctx: Context, x: torch.Tensor, fmap: FeatureMap, dtype: int = DK_C
     return MPS(out, m, n, fmap.chi_max, dtype, bond, lnorm, x)
 
 
+def self_overlap(ctx: Context, mps: "MPS", prec: int, out: torch.Tensor | None = None, stream=None):
+    """dk_self_overlap: ln|<psi~|psi~>| per sample with the arithmetic of precision `prec`."""
+    if out is None:
+        out = torch.empty(mps.m, dtype=torch.float32, device=mps.data.device)
+    _check(_lib().dk_self_overlap(ctx.handle, _ptr(mps.data), mps.m, mps.n, mps.chi_max, mps.dtype, int(prec),
+                                  _ptr(out), _stream(stream)), "dk_self_overlap")
+    return out
+
+
+def _default_prec(mps):
+    return DK_PREC_F32 if mps.dtype == DK_C64 else DK_PREC_F64
+
+
 def _outs(shape, device, want):
     return {k: (torch.empty(shape, dtype=torch.float32, device=device) if k in want else None)
             for k in ("k", "kq", "kc", "logkq")}
@@ -220,7 +247,7 @@ def _outs(shape, device, want):
 def gram_tile(ctx: Context, rows: MPS, cols: MPS, row0: int = 0, nrows: int | None = None,
               col0: int = 0, ncols: int | None = None, gamma: float | None = None, w: float = 0.5,
               want=("k", "kq", "kc", "logkq"), symmetric: bool = False, out=None, ld: int | None = None,
-              stream=None):
+              stream=None, prec: int | None = None):
     """dk_gram_tile: the (nrows x ncols) block of K, K_q, K_c, log K_q (dict of tensors)."""
     nrows = rows.m - row0 if nrows is None else nrows
     ncols = cols.m - col0 if ncols is None else ncols
@@ -232,10 +259,12 @@ def gram_tile(ctx: Context, rows: MPS, cols: MPS, row0: int = 0, nrows: int | No
         ld = ncols
     elif ld is None:
         raise ValueError("ld is required with caller-provided outputs")
-    prec = DK_PREC_F32 if rows.dtype == DK_C64 else DK_PREC_F64
+    prec = _default_prec(rows) if prec is None else prec
+    ln_r = rows.log_norm_for(ctx, prec, stream)
+    ln_c = ln_r if cols is rows else cols.log_norm_for(ctx, prec, stream)
     _check(_lib().dk_gram_tile(ctx.handle, _ptr(rows.data), rows.m, _ptr(cols.data), cols.m, rows.n,
-                               rows.chi_max, rows.dtype, row0, nrows, col0, ncols, _ptr(rows.log_norm),
-                               _ptr(cols.log_norm), _ptr(rows.x), _ptr(cols.x), float(gamma), float(w), prec,
+                               rows.chi_max, rows.dtype, row0, nrows, col0, ncols, _ptr(ln_r),
+                               _ptr(ln_c), _ptr(rows.x), _ptr(cols.x), float(gamma), float(w), prec,
                                _ptr(out.get("k")), _ptr(out.get("kq")), _ptr(out.get("kc")),
                                _ptr(out.get("logkq")), int(ld), 1 if symmetric else 0, _stream(stream)),
            "dk_gram_tile")
@@ -243,22 +272,24 @@ def gram_tile(ctx: Context, rows: MPS, cols: MPS, row0: int = 0, nrows: int | No
 
 
 def gram(ctx: Context, mps: MPS, gamma: float | None = None, w: float = 0.5,
-         want=("k", "kq", "kc", "logkq"), stream=None):
+         want=("k", "kq", "kc", "logkq"), stream=None, prec: int | None = None):
     """Full symmetric m x m Gram of one MPS batch (each unordered pair contracted once)."""
-    return gram_tile(ctx, mps, mps, gamma=gamma, w=w, want=want, symmetric=True, stream=stream)
+    return gram_tile(ctx, mps, mps, gamma=gamma, w=w, want=want, symmetric=True, stream=stream, prec=prec)
 
 
 def dual_kernel_rows(ctx: Context, test: MPS, train: MPS, gamma: float | None = None, w: float = 0.5,
-                     want=("k", "kq", "kc", "logkq"), out=None, stream=None):
+                     want=("k", "kq", "kc", "logkq"), out=None, stream=None, prec: int | None = None):
     """dk_dual_kernel_rows: the b x m block K(test, train)."""
     if test.n != train.n or test.chi_max != train.chi_max or test.dtype != train.dtype:
         raise ValueError("test and train MPS differ in n, chi_max or dtype")
     gamma = 1.0 / train.n if gamma is None else gamma
     if out is None:
         out = _outs((test.m, train.m), train.data.device, want)
-    prec = DK_PREC_F32 if train.dtype == DK_C64 else DK_PREC_F64
-    _check(_lib().dk_dual_kernel_rows(ctx.handle, _ptr(test.data), _ptr(test.x), _ptr(test.log_norm), test.m,
-                                      _ptr(train.data), _ptr(train.x), _ptr(train.log_norm), train.m, train.n,
+    prec = _default_prec(train) if prec is None else prec
+    ln_te = test.log_norm_for(ctx, prec, stream)
+    ln_tr = train.log_norm_for(ctx, prec, stream)
+    _check(_lib().dk_dual_kernel_rows(ctx.handle, _ptr(test.data), _ptr(test.x), _ptr(ln_te), test.m,
+                                      _ptr(train.data), _ptr(train.x), _ptr(ln_tr), train.m, train.n,
                                       train.chi_max, train.dtype, float(gamma), float(w), prec,
                                       _ptr(out.get("k")), _ptr(out.get("kq")), _ptr(out.get("kc")),
                                       _ptr(out.get("logkq")), _stream(stream)),

@@ -316,3 +316,45 @@ def test_chi32_fmnist_d256_sampled(dk):
     kq, lkq = _oracle_block(xte, xtr, 5)
     _check_block(rows, kq, lkq, og.rbf(xte, xtr, 1 / 256), 0.5)
     ctx.sync_status()
+
+
+TOL_MIXED = 1e-4  # split-BF16 (bf16x3) tensor-core path
+
+
+def test_chi32_bf16x3_vs_statevector_and_fp32(dk):
+    """Tensor-core bond-32 path: within 1e-4 of brute force at n = 12, exact diagonal, and
+    within 1e-4 of the FP32 bond-32 path on the same tensors."""
+    dualk, ctx, torch = dk
+    from oracle import circuit
+    from paper_2602_01330_gb300 import synthetic
+    x = synthetic.uniform_angles(11, 12, seed=12)
+    ref = circuit.kernel_matrix(x, x, 5)
+    m = dualk.mps_build(ctx, _dev(torch, x), dualk.FeatureMap(reps=5, chi_max=32))
+    mixed = dualk.gram(ctx, m, w=1.0, prec=dualk.DK_PREC_BF16X3)
+    fp32 = dualk.gram(ctx, m, w=1.0)
+    torch.cuda.synchronize()
+    kq = mixed["kq"].cpu().numpy()
+    assert np.max(np.abs(kq - ref)) <= TOL_MIXED
+    assert np.all(np.diag(kq) == 1.0)
+    assert np.max(np.abs(kq - fp32["kq"].cpu().numpy())) <= TOL_MIXED
+    ctx.sync_status()
+
+
+def test_chi32_bf16x3_fmnist_d256(dk):
+    dualk, ctx, torch = dk
+    from oracle import gram as og
+    from paper_2602_01330_gb300 import synthetic
+    d = synthetic.fmnist_like(8, 4, 256)
+    xtr, xte = d["x_train"], d["x_test"]
+    fm = dualk.FeatureMap(reps=5, chi_max=32)
+    mtr = dualk.mps_build(ctx, _dev(torch, xtr), fm)
+    mte = dualk.mps_build(ctx, _dev(torch, xte), fm)
+    out = dualk.gram(ctx, mtr, w=0.5, prec=dualk.DK_PREC_BF16X3)
+    rows = dualk.dual_kernel_rows(ctx, mte, mtr, w=0.5, prec=dualk.DK_PREC_BF16X3)
+    torch.cuda.synchronize()
+    for got, xa, xb in ((out, xtr, xtr), (rows, xte, xtr)):
+        kq, lkq = _oracle_block(xa, xb, 5)
+        assert np.max(np.abs(got["kq"].cpu().numpy() - kq)) <= TOL_MIXED
+        k_ref = og.dual_kernel(kq, og.rbf(xa, xb, 1 / 256), 0.5)
+        assert np.max(np.abs(got["k"].cpu().numpy() - k_ref)) <= TOL_MIXED
+    ctx.sync_status()
