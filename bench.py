@@ -313,6 +313,15 @@ def run_ours(args):
                "sample": f"MPS of {s_tr}+{s_te} samples at n=784 (TEBD), {s_tr * (s_tr + 1) // 2} Gram + "
                          f"{s_tr * s_te} row entries, {secs:.1f} s, FP64 NumPy single thread"}
 
+    # The other two parts of the metric, measured after the timed region (rank 0, one GPU):
+    # the split-BF16 tensor-core Gram against the FP32 one at bond 32 (d = 256, reps = 5),
+    # and the continuous-batching server's latency.
+    mixed = serving_stats = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        from paper_2602_01330_gb300 import precision, serving
+        mixed = precision.compare(m=512, pool=128, n_uniform=40, n_near=20, n_diag=10, ctx=ctx)
+        serving_stats = serving.run_benchmark(ctx, m=8000, requests=150, rho=0.8, slots=8)
+
     if world > 1:
         tdist.destroy_process_group()
     ctx.close()
@@ -336,6 +345,8 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "mixed_precision": mixed,
+        "serving": serving_stats,
     }
     print(json.dumps(line), flush=True)
 
@@ -348,6 +359,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mixed-precision and serving measurements after the timed region")
     ap.add_argument("--n-train", type=int, default=WL["n_train"],
                     help="training-set size; smaller cases serve ncu captures, not bench lines")
     ap.add_argument("--n-test", type=int, default=WL["n_test"])

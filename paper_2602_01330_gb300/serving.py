@@ -187,12 +187,36 @@ def poisson_requests(rng: np.random.Generator, count: int, rate_per_s: float, di
     return reqs
 
 
+def run_benchmark(ctx: dualk.Context, m: int = 8000, requests: int = 300, rho: float = 0.8, slots: int = 8,
+                  seed: int = 4, dims=(16, 128, 784), b_max: int = 256) -> dict:
+    """Resident training sets of m samples per qubit count, a saturating burst to measure the
+    peak rows/s, then Poisson arrivals at rho times that rate; p50/p99 latency, rows/s,
+    admissions, and whether a few results are bit-identical when run alone."""
+    from . import synthetic
+
+    fm = dualk.FeatureMap(reps=2, chi_max=4)
+    train = {n: synthetic.fmnist_like(m, 0, n)["x_train"] for n in dims}
+    test_pool = {n: synthetic.fmnist_like(16, 512, n)["x_test"] for n in dims}
+    srv = KernelServer(ctx, train, fm, slots=slots)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    burst = poisson_requests(rng, 32, 1e9, dims, test_pool, b_max)
+    t0 = time.perf_counter()
+    srv.run(burst)
+    sat_rows = sum(r.x.shape[0] for r in burst) / (time.perf_counter() - t0)
+    rate = rho * sat_rows / ((1 + b_max) / 2)
+    reqs = poisson_requests(rng, requests, rate, dims, test_pool, b_max)
+    srv.run(reqs)
+    stats = latency_stats(reqs)
+    same = all(np.array_equal(srv.solve_alone(r), r.result) for r in reqs[:5] if r.result is not None)
+    return {"workload": f"serving m={m} n={tuple(dims)} slots={slots} rho={rho} requests={requests}",
+            "saturated_rows_per_s": sat_rows, "offered_requests_per_s": rate, **stats,
+            "admitted": srv.admitted, "same_alone_and_in_mix": same}
+
+
 def main():
     """Serving run: 8000-sample training sets at n in {16, 128, 784}, Poisson arrivals."""
     import argparse
     import json
-
-    from . import synthetic
 
     ap = argparse.ArgumentParser(description=main.__doc__)
     ap.add_argument("--m", type=int, default=8000)
@@ -201,28 +225,8 @@ def main():
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--seed", type=int, default=4)
     args = ap.parse_args()
-    dims = (16, 128, 784)
     ctx = dualk.Context(0)
-    fm = dualk.FeatureMap(reps=2, chi_max=4)
-    train = {n: synthetic.fmnist_like(args.m, 0, n)["x_train"] for n in dims}
-    test_pool = {n: synthetic.fmnist_like(16, 512, n)["x_test"] for n in dims}
-    srv = KernelServer(ctx, train, fm, slots=args.slots)
-    rng = np.random.Generator(np.random.PCG64(args.seed))
-    # saturated rate: a closed burst of requests all admitted at t = 0
-    burst = poisson_requests(rng, 32, 1e9, dims, test_pool)
-    t0 = time.perf_counter()
-    srv.run(burst)
-    sat_rows = sum(r.x.shape[0] for r in burst) / (time.perf_counter() - t0)
-    mean_b = 128.5
-    rate = args.rho * sat_rows / mean_b
-    reqs = poisson_requests(rng, args.requests, rate, dims, test_pool)
-    srv.run(reqs)
-    stats = latency_stats(reqs)
-    # determinism: a few requests again, alone, must give the same bits
-    same = all(np.array_equal(srv.solve_alone(r), r.result) for r in reqs[:5] if r.result is not None)
-    print(json.dumps({"workload": f"serving m={args.m} n={dims} slots={args.slots} rho={args.rho}",
-                      "saturated_rows_per_s": sat_rows, "offered_requests_per_s": rate, **stats,
-                      "admitted": srv.admitted, "same_alone_and_in_mix": same}))
+    print(json.dumps(run_benchmark(ctx, args.m, args.requests, args.rho, args.slots, args.seed)))
     ctx.close()
 
 
