@@ -96,6 +96,10 @@ __device__ __forceinline__ void put_row_chunk(u16* rbuf, int chunk, float4 v) {
 
 // Column sample, block (s, t): B[b][c] = compact (s, j = c, l = 16 t + b); the operand is
 // [[Br, Bi], [-Bi, Br]] (32 x 32). A chunk holds b, b+1 of compact row r = 16 s + c.
+// Work item w of a column sample handles chunk col_chunk(w): consecutive items walk the 32
+// compact rows (consecutive columns c of the operand) first, so a warp's 16-bit stores
+// land in consecutive banks.
+__device__ __forceinline__ int col_chunk(int w) { return (w & 31) * 16 + (w >> 5); }
 __device__ __forceinline__ void put_col_chunk(u16* cbuf, int chunk, float4 v) {
   const int r = chunk >> 4, q = chunk & 15;
   const int s = r >> 4, c = r & 15;
@@ -127,28 +131,29 @@ struct Frag {
 };
 
 // acc += X . Yop with X given as 16 x 32 A fragments (hi/lo per k-step) and Yop a 32 x 32
-// row-major BF16 operand in shared memory (hi, lo), for the 4 n-tiles.
+// row-major BF16 operand in shared memory (hi, lo), for the 4 n-tiles. The MMAs are issued
+// term-major over the four independent n-tile accumulators, so consecutive MMAs never wait
+// on each other.
 __device__ __forceinline__ void gemm_16x32x32(float (&acc)[4][4], const u32 (&ahi)[2][4], const u32 (&alo)[2][4],
                                               const u16* yhi, const u16* ylo, int lane) {
-  // ldmatrix.trans lane address: tile (k half kh, n tile) rows = 16 kk + 8 kh + (lane & 7)
+  // ldmatrix.trans lane address: tile (k half, n tile) rows = 16 kk + 8 (sel & 1) + (lane & 7)
   const int lr = lane & 7, sel = lane >> 3;  // sel: 0 (k 0-7, nt), 1 (k 8-15, nt), 2 (k 0-7, nt+1), 3
 #pragma unroll
   for (int kk = 0; kk < 2; ++kk) {
+    u32 bh[2][4], bl[2][4];
 #pragma unroll
     for (int np = 0; np < 2; ++np) {  // pairs of n-tiles (2np, 2np+1)
       const int krow = 16 * kk + 8 * (sel & 1) + lr;
       const int ncol = 16 * np + 8 * (sel >> 1);
-      u32 bh[4], bl[4];
-      ldsm_x4_t(bh, yhi + krow * ROW + ncol);
-      ldsm_x4_t(bl, ylo + krow * ROW + ncol);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int nt = 2 * np + h;
-        mma16816(acc[nt], alo[kk], bh[2 * h], bh[2 * h + 1]);
-        mma16816(acc[nt], ahi[kk], bl[2 * h], bl[2 * h + 1]);
-        mma16816(acc[nt], ahi[kk], bh[2 * h], bh[2 * h + 1]);
-      }
+      ldsm_x4_t(bh[np], yhi + krow * ROW + ncol);
+      ldsm_x4_t(bl[np], ylo + krow * ROW + ncol);
     }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], alo[kk], bh[nt >> 1][2 * (nt & 1)], bh[nt >> 1][2 * (nt & 1) + 1]);
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], ahi[kk], bl[nt >> 1][2 * (nt & 1)], bl[nt >> 1][2 * (nt & 1) + 1]);
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], ahi[kk], bh[nt >> 1][2 * (nt & 1)], bh[nt >> 1][2 * (nt & 1) + 1]);
   }
 }
 
@@ -293,8 +298,9 @@ __global__ void __launch_bounds__(TR * TC * 32, 1)
     for (int q = 0; q < C::PER_THREAD; ++q) {
       const int ch = threadIdx.x + q * C::NT;
       if (ch < C::CH) {
-        const int smp = ch / CHUNKS, part = ch % CHUNKS;
+        const int smp = ch / CHUNKS, w = ch % CHUNKS;
         const bool is_row = smp < TR;
+        const int part = is_row ? w : col_chunk(w);
         const int idx = is_row ? min(r0 + smp, m_r - 1) : min(c0 + smp - TR, m_c - 1);
         const float* src = (is_row ? mps_r + (size_t(k) * m_r + idx) * SAMPLE_FLOATS
                                    : mps_c + (size_t(k) * m_c + idx) * SAMPLE_FLOATS) + part * 4;
@@ -307,9 +313,9 @@ __global__ void __launch_bounds__(TR * TC * 32, 1)
     for (int q = 0; q < C::PER_THREAD; ++q) {
       const int ch = threadIdx.x + q * C::NT;
       if (ch < C::CH) {
-        const int smp = ch / CHUNKS, part = ch % CHUNKS;
-        if (smp < TR) put_row_chunk(st + smp * RBUF, part, pre[q]);
-        else put_col_chunk(st + TR * RBUF + (smp - TR) * CBUF, part, pre[q]);
+        const int smp = ch / CHUNKS, w = ch % CHUNKS;
+        if (smp < TR) put_row_chunk(st + smp * RBUF, w, pre[q]);
+        else put_col_chunk(st + TR * RBUF + (smp - TR) * CBUF, col_chunk(w), pre[q]);
       }
     }
   };
@@ -362,10 +368,11 @@ __global__ void __launch_bounds__(32) self_overlap32_tc_kernel(const float* __re
   int e2 = 0;
   for (int k = 0; k < n; ++k) {
     const float* src = mps + (size_t(k) * m + i) * SAMPLE_FLOATS;
-    for (int ch = lane; ch < CHUNKS; ch += 32) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(src) + ch);
-      put_row_chunk(rbuf, ch, v);
-      put_col_chunk(cbuf, ch, v);
+    for (int w = lane; w < CHUNKS; w += 32) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(src) + w);
+      put_row_chunk(rbuf, w, v);
+      const int cw = col_chunk(w);
+      put_col_chunk(cbuf, cw, __ldg(reinterpret_cast<const float4*>(src) + cw));
     }
     __syncwarp();
     pair_site(E, rbuf, cbuf, gbuf, lane);

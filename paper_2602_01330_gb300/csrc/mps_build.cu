@@ -120,9 +120,8 @@ __device__ __forceinline__ void qr_cgs2(const cd (&M)[P][C], int nref, cd (&Q)[P
       double n2 = 0.0;
 #pragma unroll
       for (int i = 0; i < P; ++i) n2 += cabs2(v[i]);
-      const double nrm = sqrt(n2);
-      const double inv = nrm > 1e-300 ? 1.0 / nrm : 0.0;
-      R[c][c] = mk(nrm, 0.0);
+      const double inv = n2 > 1e-300 ? rsqrt(n2) : 0.0;
+      R[c][c] = mk(n2 * inv, 0.0);
 #pragma unroll
       for (int i = 0; i < P; ++i) Q[i][c] = cscale(v[i], inv);
     } else {
@@ -148,13 +147,19 @@ __device__ __forceinline__ cd shfl_cd(unsigned mask, cd v, int lane_mask) {
 // Two threads per sample, one per bond block s; HS = stored block size chi/2, HA =
 // closed-form block size 2^(r-1) <= 2. A CTA is one (possibly partial) warp holding
 // blockDim.x / 2 samples; the launch picks the width so that the FP64 work spreads over
-// all SMs.
-template <int HS, int HA, int RP>
+// all SMs. The exponentials of site k+1 are evaluated while site k is factorised, so they
+// stay off the chain's dependency path. With log_norm set, the kernel also runs the Gram's
+// transfer arithmetic (transfer.cuh, in `real`, on the FMA pipes) on each sample's own
+// rounded tensors as they are produced, giving ln|<psi~|psi~>| bit-identical to the Gram
+// diagonal without a second pass.
+template <int HS, int HA, int RP, typename real>
 __global__ void __launch_bounds__(32) mps_build_pair_kernel(const float* __restrict__ x, int m, int n,
-                                                            double angle_scale, int entangle, int out_c128,
-                                                            void* __restrict__ out, int32_t* __restrict__ bond) {
+                                                            double angle_scale, int entangle,
+                                                            void* __restrict__ out, int32_t* __restrict__ bond,
+                                                            float* __restrict__ log_norm) {
   constexpr int P = 2 * HS;  // stored left-bond positions
   constexpr int CHI = 2 * HS;
+  constexpr int c128 = sizeof(real) == 8 ? 1 : 0;
   const int s = threadIdx.x & 1;
   const int i0 = blockIdx.x * (blockDim.x >> 1) + (threadIdx.x >> 1);
   const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
@@ -170,23 +175,30 @@ __global__ void __launch_bounds__(32) mps_build_pair_kernel(const float* __restr
       for (int c = 0; c < HA; ++c) R[t][j][c] = mk(0.0, 0.0);
   R[0][0][0] = mk(1.0, 0.0);
   int act = 1;  // active left-bond positions (pk_0 + pk_1 of the previous site)
-  double xprev = 0.0;
   const size_t per = size_t(CHI) * CHI;  // complex entries per sample-site
-  SiteFactors<RP> f;
-  for (int k = 0; k < n; ++k) {
+  // this thread's exponential for site k: s = 0 -> exp(-i angle_scale x_k / 2),
+  // s = 1 -> exp(-i theta_{k-1} / 2), theta_{k-1} = 2 (pi - x_{k-1})(pi - x_k)
+  auto expo = [&](int k) {
     const double xk = double(xs[k]);
+    const double xp = k > 0 ? double(xs[k - 1]) : 0.0;
+    const double arg = s == 0 ? -0.5 * angle_scale * xk : ((entangle && k > 0) ? -(PI_D - xp) * (PI_D - xk) : 0.0);
+    double sn, cs;
+    sincos(arg, &sn, &cs);
+    return mk(cs, sn);
+  };
+  PairE<real, HS> chain[1][1];
+  chain[0][0].init();
+  cd e_cur = expo(0);
+  for (int k = 0; k < n; ++k) {
+    const cd e_next = (k + 1 < n) ? expo(k + 1) : mk(1.0, 0.0);  // independent of this site's chain
+    SiteFactors<RP> f;
     {
-      // the two threads of a sample evaluate one exponential each and swap
-      const double arg = s == 0 ? -0.5 * angle_scale * xk
-                                : ((entangle && k > 0) ? -(PI_D - xprev) * (PI_D - xk) : 0.0);
-      double sn, cs;
-      sincos(arg, &sn, &cs);
-      const cd mine = mk(cs, sn);
-      const cd other = shfl_cd(mask, mine, 1);
-      f.make_from(s == 0 ? mine : other, s == 0 ? other : mine);
+      const cd other = shfl_cd(mask, e_cur, 1);
+      f.make_from(s == 0 ? e_cur : other, s == 0 ? other : e_cur);
     }
     const size_t base = (size_t(k) * m + i) * per + size_t(s) * HS * CHI;
     if (bond && i0 == 0 && s == 0) bond[k] = act;
+    cd Qs[P][HS];  // this thread's block of the stored tensor, columns j >= the active ones zero
     if (k < n - 1) {
       cd M[P][HA];
 #pragma unroll
@@ -204,12 +216,10 @@ __global__ void __launch_bounds__(32) mps_build_pair_kernel(const float* __restr
       const int nref = act < HA ? act : HA;
       cd Q[P][HA], Rr[HA][HA];
       qr_cgs2<P, HA>(M, nref, Q, Rr);
-      if (live) {
 #pragma unroll
-        for (int j = 0; j < HS; ++j)
+      for (int j = 0; j < HS; ++j)
 #pragma unroll
-          for (int l = 0; l < P; ++l) store_cplx(out, base + j * CHI + l, j < HA ? Q[l][j] : mk(0.0, 0.0), out_c128);
-      }
+        for (int l = 0; l < P; ++l) Qs[l][j] = j < HA ? Q[l][j] : mk(0.0, 0.0);
       // R <- diag(R_0, R_1): keep this block, take the other from the partner lane
 #pragma unroll
       for (int j = 0; j < HS; ++j)
@@ -241,18 +251,57 @@ __global__ void __launch_bounds__(32) mps_build_pair_kernel(const float* __restr
           nrm2 += cabs2(acc);
         }
       nrm2 += __shfl_xor_sync(mask, nrm2, 1);
-      const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
-      if (live) {
+      const double inv = nrm2 > 0.0 ? rsqrt(nrm2) : 0.0;
+#pragma unroll
+      for (int j = 0; j < HS; ++j)
+#pragma unroll
+        for (int l = 0; l < P; ++l) Qs[l][j] = j == 0 ? cscale(v[l], inv) : mk(0.0, 0.0);
+      if (bond && i0 == 0 && s == 0) bond[n] = 1;
+    }
+    // the stored values, rounded once: to memory and, for the self-overlap, to registers
+    real qr[HS][P], qi[HS][P];
+#pragma unroll
+    for (int j = 0; j < HS; ++j)
+#pragma unroll
+      for (int l = 0; l < P; ++l) {
+        qr[j][l] = real(Qs[l][j].x);
+        qi[j][l] = real(Qs[l][j].y);
+      }
+    if (live) {
+#pragma unroll
+      for (int j = 0; j < HS; ++j)
+#pragma unroll
+        for (int l = 0; l < P; ++l) store_cplx(out, base + j * CHI + l, Qs[l][j], c128);
+    }
+    if (log_norm) {
+      // both threads of the sample hold the full site tensor after the swap
+      real ar[2][HS][P], ai[2][HS][P];
+#pragma unroll
+      for (int j = 0; j < HS; ++j)
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+          const real orr = __shfl_xor_sync(mask, qr[j][l], 1);
+          const real oi = __shfl_xor_sync(mask, qi[j][l], 1);
+          ar[s][j][l] = qr[j][l];
+          ai[s][j][l] = qi[j][l];
+          ar[1 - s][j][l] = orr;
+          ai[1 - s][j][l] = oi;
+        }
+      // sub-block A_s[t]: rows l = t*HS + a, columns j (as in the Gram kernels' loaders)
+      auto ld = [&](int, int ss, int t, Blk<real, HS>& blk) {
 #pragma unroll
         for (int j = 0; j < HS; ++j)
 #pragma unroll
-          for (int l = 0; l < P; ++l)
-            store_cplx(out, base + j * CHI + l, j == 0 ? cscale(v[l], inv) : mk(0.0, 0.0), out_c128);
-      }
-      if (bond && i0 == 0 && s == 0) bond[n] = 1;
+          for (int a = 0; a < HS; ++a) {
+            blk.r[a][j] = ar[ss][j][t * HS + a];
+            blk.i[a][j] = ai[ss][j][t * HS + a];
+          }
+      };
+      site_step<real, HS, 1, 1>(chain, ld, ld, k == n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1));
     }
-    xprev = xk;
+    e_cur = e_next;
   }
+  if (log_norm && live && s == 0) log_norm[i] = chain[0][0].half_log_mod();
 }
 
 // One warp per sample for wide bonds (closed-form block HA >= 4): the same sweep with the
@@ -449,12 +498,22 @@ static int pair_kernel_lanes(int m, int sm_count) {
 
 template <int HS, int HA>
 static dk_status launch_build(const float* x, int m, int n, const dk_fmap* fm, int c128, void* mps, int32_t* bond,
-                              int sm_count, cudaStream_t st) {
+                              float* log_norm, int sm_count, cudaStream_t st, bool* fused_norm) {
+  *fused_norm = false;
   if constexpr (HA <= 2) {
     constexpr int RP = HA == 1 ? 1 : 2;
     const int lanes = pair_kernel_lanes(m, sm_count);
-    mps_build_pair_kernel<HS, HA, RP><<<(2 * m + lanes - 1) / lanes, lanes, 0, st>>>(
-        x, m, n, double(fm->angle_scale), fm->entangle, c128, mps, bond);
+    const int grid = (2 * m + lanes - 1) / lanes;
+    // the fused self-overlap covers the bond-4 tensors (the Gram kernels' HS = 2)
+    float* ln = HS == 2 ? log_norm : nullptr;
+    if (c128) {
+      mps_build_pair_kernel<HS, HA, RP, double><<<grid, lanes, 0, st>>>(x, m, n, double(fm->angle_scale),
+                                                                       fm->entangle, mps, bond, ln);
+    } else {
+      mps_build_pair_kernel<HS, HA, RP, float><<<grid, lanes, 0, st>>>(x, m, n, double(fm->angle_scale),
+                                                                      fm->entangle, mps, bond, ln);
+    }
+    *fused_norm = ln != nullptr;
   } else {
     const size_t smem = sizeof(WarpQr<HS, HA>);
     constexpr int RP = HA == 4 ? 3 : HA == 8 ? 4 : 5;
@@ -498,15 +557,16 @@ DK_API dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const d
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int c128 = dtype == DK_C128 ? 1 : 0;
   dk_status s = DK_ERR_UNSUPPORTED;
+  bool fused = false;
   // (stored block HS = chi/2, closed-form block HA = 2^(reps-1))
-  if (chi == 4 && fm->reps == 1) s = launch_build<2, 1>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
-  else if (chi == 4 && fm->reps == 2) s = launch_build<2, 2>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
-  else if (chi == 8 && fm->reps == 1) s = launch_build<4, 1>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
-  else if (chi == 8 && fm->reps == 2) s = launch_build<4, 2>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
-  else if (chi == 8 && fm->reps == 3) s = launch_build<4, 4>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
-  else if (chi == 16 && fm->reps == 4) s = launch_build<8, 8>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
-  else if (chi == 32 && fm->reps == 5) s = launch_build<16, 16>(x, m, n, fm, c128, mps, bond_dims, ctx->sm_count, st);
-  if (s != DK_OK || !log_norm) return s;
+  if (chi == 4 && fm->reps == 1) s = launch_build<2, 1>(x, m, n, fm, c128, mps, bond_dims, log_norm, ctx->sm_count, st, &fused);
+  else if (chi == 4 && fm->reps == 2) s = launch_build<2, 2>(x, m, n, fm, c128, mps, bond_dims, log_norm, ctx->sm_count, st, &fused);
+  else if (chi == 8 && fm->reps == 1) s = launch_build<4, 1>(x, m, n, fm, c128, mps, bond_dims, log_norm, ctx->sm_count, st, &fused);
+  else if (chi == 8 && fm->reps == 2) s = launch_build<4, 2>(x, m, n, fm, c128, mps, bond_dims, log_norm, ctx->sm_count, st, &fused);
+  else if (chi == 8 && fm->reps == 3) s = launch_build<4, 4>(x, m, n, fm, c128, mps, bond_dims, log_norm, ctx->sm_count, st, &fused);
+  else if (chi == 16 && fm->reps == 4) s = launch_build<8, 8>(x, m, n, fm, c128, mps, bond_dims, log_norm, ctx->sm_count, st, &fused);
+  else if (chi == 32 && fm->reps == 5) s = launch_build<16, 16>(x, m, n, fm, c128, mps, bond_dims, log_norm, ctx->sm_count, st, &fused);
+  if (s != DK_OK || !log_norm || fused) return s;
   return self_overlap_launch(mps, m, n, chi, dtype, log_norm, st);
 }
 
