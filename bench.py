@@ -235,6 +235,9 @@ def run_ours(args):
     phase_events = []  # per timed step: events before build, Gram, rows, and after rows
 
     def step(record=False):
+        # The test-set build runs on a side stream beside the training-set build (each is a
+        # latency-bound chain per sample); the Gram and the rows then run one after the other
+        # on the main stream, so each launch's own time is measured.
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
         if record:
             ev[0].record(stream)

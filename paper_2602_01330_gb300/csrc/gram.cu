@@ -314,6 +314,8 @@ using F32_P21w = GramCfg<float, 4, 4, 8, 2, 1, 4, 3, 4, 1>;    // 32 x 24 pairs,
 using F32_P14 = GramCfg<float, 4, 8, 4, 1, 4, 4, 2, 4, 1>;     // 32 x 32 pairs, 256 threads
 using F32_P22wS2 = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 3, 1, 2>;  // 48 x 32 pairs, 384 threads, 2 sites/stage
 using F32_P22S2 = GramCfg<float, 4, 4, 8, 2, 2, 4, 2, 3, 1, 2>;   // 32 x 32 pairs, 256 threads, 2 sites/stage
+using F32_P22wS4 = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 2, 1, 4>;  // 48 x 32 pairs, 384 threads, 4 sites/stage
+using F32_P22wS4b = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 3, 1, 4>; // same, 3 stages
 using F64_P11 = GramCfg<double, 4, 4, 8, 1, 1, 4, 2, 4, 1>;    // 16 x 16 pairs, 256 threads
 using F32X8_P11 = GramCfg<float, 8, 4, 8, 1, 1, 4, 2, 4, 1>;   // chi = 8: 16 x 16 pairs, 256 threads
 
@@ -331,10 +333,11 @@ template <class Cfg>
 constexpr CfgInfo info_of() {
   return CfgInfo{Cfg::TR, Cfg::TC, Cfg::NTHREADS};
 }
-// Shapes selectable for complex64 / chi 4, in id order 1..9; the built-in choice is id 8.
+// Shapes selectable for complex64 / chi 4, in id order 1..11; the built-in choice is id 8.
 static const CfgInfo kF32Chi4[] = {info_of<F32_P11>(),  info_of<F32_P21>(),  info_of<F32_P22>(), info_of<F32_P12>(),
                                    info_of<F32_P22w>(), info_of<F32_P21w>(), info_of<F32_P14>(),
-                                   info_of<F32_P22wS2>(), info_of<F32_P22S2>()};
+                                   info_of<F32_P22wS2>(), info_of<F32_P22S2>(), info_of<F32_P22wS4>(),
+                                   info_of<F32_P22wS4b>()};
 constexpr int kF32Chi4Default = 8;
 static const CfgInfo kF64Chi4[] = {info_of<F64_P11>()};
 static const CfgInfo kF32Chi8[] = {info_of<F32X8_P11>()};
@@ -352,6 +355,8 @@ static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const vo
       case 7: return launch_gram<F32_P14>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 8: return launch_gram<F32_P22wS2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 9: return launch_gram<F32_P22S2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 10: return launch_gram<F32_P22wS4>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 11: return launch_gram<F32_P22wS4b>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 3: return launch_gram<F32_P22>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       default: return launch_gram<F32_P22wS2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
     }
