@@ -72,8 +72,17 @@ struct SiteFactors {
       wp[q] = cmul(wp[q - 1], w);
     }
   }
-  __device__ __forceinline__ cd upow(int e) const { return e >= 0 ? up[e] : cconj(up[-e]); }
-  __device__ __forceinline__ cd wpow(int e) const { return e >= 0 ? wp[e] : cconj(wp[-e]); }
+  // powers by exponent in -RP..RP, picked with selects so that a run-time exponent does
+  // not send the tables to local memory
+  __device__ __forceinline__ static cd pick(const cd (&tab)[RP + 1], int e) {
+    const int a = e >= 0 ? e : -e;
+    cd r = tab[0];
+#pragma unroll
+    for (int q = 1; q <= RP; ++q) r = a == q ? tab[q] : r;
+    return e >= 0 ? r : cconj(r);
+  }
+  __device__ __forceinline__ cd upow(int e) const { return pick(up, e); }
+  __device__ __forceinline__ cd wpow(int e) const { return pick(wp, e); }
   // L_k(c) = 2^(-r/2) (-1)^popc(c & c>>1) u^(r - 2 popc(c))
   __device__ __forceinline__ cd local(int c) const {
     constexpr double amp = RP == 1 ? 0.70710678118654752440 : RP == 2 ? 0.5 : RP == 3 ? 0.35355339059327376220
@@ -227,8 +236,8 @@ __global__ void __launch_bounds__(32) mps_build_pair_kernel(const float* __restr
         for (int cc = 0; cc < HA; ++cc) {
           const cd mine = j < HA ? Rr[j][cc] : mk(0.0, 0.0);
           const cd other = shfl_cd(mask, mine, 1);
-          R[s][j][cc] = mine;
-          R[1 - s][j][cc] = other;
+          R[0][j][cc] = s == 0 ? mine : other;  // selects keep R in registers
+          R[1][j][cc] = s == 0 ? other : mine;
         }
       act = 2 * nref;
     } else {
@@ -282,10 +291,10 @@ __global__ void __launch_bounds__(32) mps_build_pair_kernel(const float* __restr
         for (int l = 0; l < P; ++l) {
           const real orr = __shfl_xor_sync(mask, qr[j][l], 1);
           const real oi = __shfl_xor_sync(mask, qi[j][l], 1);
-          ar[s][j][l] = qr[j][l];
-          ai[s][j][l] = qi[j][l];
-          ar[1 - s][j][l] = orr;
-          ai[1 - s][j][l] = oi;
+          ar[0][j][l] = s == 0 ? qr[j][l] : orr;
+          ai[0][j][l] = s == 0 ? qi[j][l] : oi;
+          ar[1][j][l] = s == 0 ? orr : qr[j][l];
+          ai[1][j][l] = s == 0 ? oi : qi[j][l];
         }
       // sub-block A_s[t]: rows l = t*HS + a, columns j (as in the Gram kernels' loaders)
       auto ld = [&](int, int ss, int t, Blk<real, HS>& blk) {
@@ -302,6 +311,177 @@ __global__ void __launch_bounds__(32) mps_build_pair_kernel(const float* __restr
     e_cur = e_next;
   }
   if (log_norm && live && s == 0) log_norm[i] = chain[0][0].half_log_mod();
+}
+
+// Eight threads per sample for the bond-4 tensors (chi_max = 4, reps <= 2): thread q of a
+// sample's group handles block s = q >> 2 and row (t, j) = ((q >> 1) & 1, q & 1) of that
+// block's 4 x HA matrix M_s, and the Gram-Schmidt sums over the 4 rows are shuffle
+// reductions inside the group. Every FP64 warp instruction costs the same issue time on
+// GB300 whatever its active lanes, so spreading one sample over 8 threads shortens the
+// per-site dependency chain about 2.5x against two threads per sample. The exponentials of
+// site k+1 are evaluated while site k is factorised; with log_norm set, every thread also
+// runs the Gram's transfer arithmetic on the sample's rounded tensors (gathered by shuffles)
+// so that ln|<psi~|psi~>| is bit-identical to the Gram diagonal.
+template <int HA, int RP, typename real>
+__global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restrict__ x, int m, int n,
+                                                           double angle_scale, int entangle,
+                                                           void* __restrict__ out, int32_t* __restrict__ bond,
+                                                           float* __restrict__ log_norm) {
+  constexpr int HS = 2, CHI = 4;
+  constexpr int c128 = sizeof(real) == 8 ? 1 : 0;
+  const int q = threadIdx.x & 7;
+  const int s = q >> 2, t = (q >> 1) & 1, j = q & 1;
+  const int row = t * HS + j;  // this thread's left-bond position
+  const int i0 = blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
+  const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+  const bool live = i0 < m;
+  const int i = live ? i0 : m - 1;
+  const float* xs = x + size_t(i) * n;
+  // Rrow[cp] = R_t[j][cp]: row j of the previous site's block-t factor (HA columns)
+  cd Rrow[HA];
+#pragma unroll
+  for (int c = 0; c < HA; ++c) Rrow[c] = mk(0.0, 0.0);
+  if (t == 0 && j == 0) Rrow[0] = mk(1.0, 0.0);
+  int act = 1;
+  auto expo = [&](int k) {  // thread q & 1 == 0: u_k, q & 1 == 1: w_k (see mps_build_pair_kernel)
+    const double xk = double(xs[k]);
+    const double xp = k > 0 ? double(xs[k - 1]) : 0.0;
+    const double arg = (q & 1) == 0 ? -0.5 * angle_scale * xk : ((entangle && k > 0) ? -(PI_D - xp) * (PI_D - xk) : 0.0);
+    double sn, cs;
+    sincos(arg, &sn, &cs);
+    return mk(cs, sn);
+  };
+  auto gsum = [&](double v) {  // sum over the 4 threads of this block
+    v += __shfl_xor_sync(mask, v, 1);
+    v += __shfl_xor_sync(mask, v, 2);
+    return v;
+  };
+  auto gsumc = [&](cd v) { return mk(gsum(v.x), gsum(v.y)); };
+  PairE<real, HS> chain[1][1];
+  chain[0][0].init();
+  cd e_cur = expo(0);
+  for (int k = 0; k < n; ++k) {
+    const cd e_next = (k + 1 < n) ? expo(k + 1) : mk(1.0, 0.0);
+    SiteFactors<RP> f;
+    {
+      const int base_lane = (threadIdx.x & ~7);
+      const cd u = mk(__shfl_sync(mask, e_cur.x, base_lane), __shfl_sync(mask, e_cur.y, base_lane));
+      const cd w = mk(__shfl_sync(mask, e_cur.x, base_lane + 1), __shfl_sync(mask, e_cur.y, base_lane + 1));
+      f.make_from(u, w);
+    }
+    if (bond && i0 == 0 && q == 0) bond[k] = act;
+    cd qv[HS];  // this thread's row of Q_s: stored element (s, jc, l = row) for jc < HS
+    if (k < n - 1) {
+      cd mrow[HA];
+#pragma unroll
+      for (int cc = 0; cc < HA; ++cc) {
+        const int c = s * HA + cc;
+        cd acc = mk(0.0, 0.0);
+#pragma unroll
+        for (int cp = 0; cp < HA; ++cp) acc = cadd(acc, cmul(Rrow[cp], f.bond(t * HA + cp, c)));
+        mrow[cc] = cmul(f.local(c), acc);
+      }
+      const int nref = act < HA ? act : HA;
+      // classical Gram-Schmidt with one re-orthogonalisation pass over the 4 rows
+      cd qrow[HA], rcol[HA][HA];
+#pragma unroll
+      for (int a = 0; a < HA; ++a)
+#pragma unroll
+        for (int b = 0; b < HA; ++b) rcol[a][b] = mk(0.0, 0.0);
+#pragma unroll
+      for (int c = 0; c < HA; ++c) {
+        cd v = mrow[c];
+        if (c < nref) {
+#pragma unroll
+          for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+            for (int pq = 0; pq < c; ++pq) {
+              const cd r = gsumc(cconjmul(qrow[pq], v));
+              rcol[pq][c] = cadd(rcol[pq][c], r);
+              v = csub(v, cmul(qrow[pq], r));
+            }
+          const double n2 = gsum(cabs2(v));
+          const double inv = n2 > 1e-300 ? rsqrt(n2) : 0.0;
+          rcol[c][c] = mk(n2 * inv, 0.0);
+          qrow[c] = cscale(v, inv);
+        } else {
+#pragma unroll
+          for (int pq = 0; pq < HA; ++pq)
+            if (pq < nref) rcol[pq][c] = gsumc(cconjmul(qrow[pq], v));
+          qrow[c] = mk(0.0, 0.0);
+        }
+      }
+#pragma unroll
+      for (int jc = 0; jc < HS; ++jc) qv[jc] = jc < HA ? qrow[jc] : mk(0.0, 0.0);
+      // next R row for this thread: row j of block t's factor, which every thread of block t
+      // holds after the reductions
+      // (thread 4 t + j holds block t and the same j, so its row-j pick is the one wanted)
+      const int src = (threadIdx.x & ~7) + 4 * t + j;
+#pragma unroll
+      for (int cp = 0; cp < HA; ++cp) {
+        cd mine = rcol[0][cp];
+        if constexpr (HA > 1) mine = j == 1 ? rcol[1][cp] : mine;
+        else mine = j == 1 ? mk(0.0, 0.0) : mine;
+        Rrow[cp] = mk(__shfl_sync(mask, mine.x, src), __shfl_sync(mask, mine.y, src));
+      }
+      act = 2 * nref;
+    } else {
+      cd acc = mk(0.0, 0.0);
+#pragma unroll
+      for (int cc = 0; cc < HA; ++cc) {
+        const int c = s * HA + cc;
+        cd inner = mk(0.0, 0.0);
+#pragma unroll
+        for (int cp = 0; cp < HA; ++cp) inner = cadd(inner, cmul(Rrow[cp], f.bond(t * HA + cp, c)));
+        acc = cadd(acc, cmul(f.local(c), inner));
+      }
+      double n2 = cabs2(acc);
+      n2 += __shfl_xor_sync(mask, n2, 1);
+      n2 += __shfl_xor_sync(mask, n2, 2);
+      n2 += __shfl_xor_sync(mask, n2, 4);
+      const double inv = n2 > 0.0 ? rsqrt(n2) : 0.0;
+      qv[0] = cscale(acc, inv);
+      qv[1] = mk(0.0, 0.0);
+      if (bond && i0 == 0 && q == 0) bond[n] = 1;
+    }
+    real vr[HS], vi[HS];
+#pragma unroll
+    for (int jc = 0; jc < HS; ++jc) {
+      vr[jc] = real(qv[jc].x);
+      vi[jc] = real(qv[jc].y);
+    }
+    if (live) {
+      const size_t base = (size_t(k) * m + i) * (CHI * CHI);
+#pragma unroll
+      for (int jc = 0; jc < HS; ++jc) store_cplx(out, base + (s * HS + jc) * CHI + row, qv[jc], c128);
+    }
+    if (log_norm) {
+      // gather the sample's 16 stored values: element (s', jc, l) from thread 4 s' + l
+      real ar[2][HS][CHI], ai[2][HS][CHI];
+      const int base_lane = threadIdx.x & ~7;
+#pragma unroll
+      for (int ss = 0; ss < 2; ++ss)
+#pragma unroll
+        for (int l = 0; l < CHI; ++l)
+#pragma unroll
+          for (int jc = 0; jc < HS; ++jc) {
+            ar[ss][jc][l] = __shfl_sync(mask, vr[jc], base_lane + 4 * ss + l);
+            ai[ss][jc][l] = __shfl_sync(mask, vi[jc], base_lane + 4 * ss + l);
+          }
+      auto ld = [&](int, int ss, int tt, Blk<real, HS>& blk) {
+#pragma unroll
+        for (int jc = 0; jc < HS; ++jc)
+#pragma unroll
+          for (int a = 0; a < HS; ++a) {
+            blk.r[a][jc] = ar[ss][jc][tt * HS + a];
+            blk.i[a][jc] = ai[ss][jc][tt * HS + a];
+          }
+      };
+      site_step<real, HS, 1, 1>(chain, ld, ld, k == n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1));
+    }
+    e_cur = e_next;
+  }
+  if (log_norm && live && q == 0) log_norm[i] = chain[0][0].half_log_mod();
 }
 
 // One warp per sample for wide bonds (closed-form block HA >= 4): the same sweep with the
@@ -502,10 +682,28 @@ static dk_status launch_build(const float* x, int m, int n, const dk_fmap* fm, i
   *fused_norm = false;
   if constexpr (HA <= 2) {
     constexpr int RP = HA == 1 ? 1 : 2;
-    const int lanes = pair_kernel_lanes(m, sm_count);
-    const int grid = (2 * m + lanes - 1) / lanes;
     // the fused self-overlap covers the bond-4 tensors (the Gram kernels' HS = 2)
     float* ln = HS == 2 ? log_norm : nullptr;
+    // Bond 4: 8 threads per sample while the set is small enough that the per-sample
+    // chain latency, not the FP64 issue rate, sets the time (up to about 2.5 warps per SM
+    // sub-partition); two threads per sample beyond that, where the 8-thread form's extra
+    // reduction instructions cost more than its shorter chain saves.
+    if (HS == 2 && (m + 3) / 4 <= 10 * sm_count) {
+      // 4 samples per warp-sized CTA; fewer per CTA when that would leave SMs idle
+      const int spc = (m + 3) / 4 >= sm_count ? 4 : ((m + 1) / 2 >= sm_count ? 2 : 1);
+      const int grid = (m + spc - 1) / spc;
+      if (c128) {
+        mps_build_oct_kernel<HA, RP, double><<<grid, 8 * spc, 0, st>>>(x, m, n, double(fm->angle_scale),
+                                                                     fm->entangle, mps, bond, ln);
+      } else {
+        mps_build_oct_kernel<HA, RP, float><<<grid, 8 * spc, 0, st>>>(x, m, n, double(fm->angle_scale),
+                                                                    fm->entangle, mps, bond, ln);
+      }
+      *fused_norm = ln != nullptr;
+      return launch_status();
+    }
+    const int lanes = pair_kernel_lanes(m, sm_count);
+    const int grid = (2 * m + lanes - 1) / lanes;
     if (c128) {
       mps_build_pair_kernel<HS, HA, RP, double><<<grid, lanes, 0, st>>>(x, m, n, double(fm->angle_scale),
                                                                        fm->entangle, mps, bond, ln);

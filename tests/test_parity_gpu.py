@@ -224,6 +224,45 @@ def test_n784_bench_shape_sampled(dk):
     ctx.sync_status()
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_bond4_build_kernels_agree_small_and_large_sets(dk, dtype):
+    """The bond-4 MPS build has two launch forms chosen by the sample count: 8 threads per
+    sample for sets up to 40 samples per SM, 2 threads per sample above. 6400 samples
+    (the 2-thread form), d = 40, reps = 2: the Gram block between the first 48 and the
+    last 48 samples against the oracle, the same 96 samples built as a small set (the
+    8-thread form) giving the same block, and for both forms the fused ln-norms close to
+    the self-overlap entry point's and a unit Gram diagonal (exact in FP32)."""
+    dualk, ctx, torch = dk
+    from oracle import gram as og
+    from paper_2602_01330_gb300 import synthetic
+    dt = dualk.DK_C64 if dtype == "c64" else dualk.DK_C128
+    m, n = 6400, 40
+    x = synthetic.fmnist_like(m, 0, n)["x_train"]
+    fm = dualk.FeatureMap(reps=2, chi_max=4)
+    big = dualk.mps_build(ctx, _dev(torch, x), fm, dtype=dt)
+    out = dualk.gram_tile(ctx, big, big, 0, 48, m - 48, 48, w=0.5)
+    sel = np.r_[0:48, m - 48:m]
+    small = dualk.mps_build(ctx, _dev(torch, x[sel]), fm, dtype=dt)
+    out_s = dualk.gram_tile(ctx, small, small, 0, 48, 48, 48, w=0.5)
+    torch.cuda.synchronize()
+    kq_ref, lkq_ref = _oracle_block(x[:48], x[m - 48:], 2)
+    kc_ref = og.rbf(x[:48], x[m - 48:], 1 / n)
+    _check_block(out, kq_ref, lkq_ref, kc_ref, 0.5)
+    _check_block(out_s, kq_ref, lkq_ref, kc_ref, 0.5)
+    prec = dualk.DK_PREC_F32 if dtype == "c64" else dualk.DK_PREC_F64
+    for mp in (big, small):
+        fused = mp.log_norm.clone()
+        sep = dualk.self_overlap(ctx, mp, prec)
+        diag = dualk.gram_tile(ctx, mp, mp, 0, 48, 0, 48, w=1.0, want=("kq",))["kq"]
+        torch.cuda.synchronize()
+        assert torch.max(torch.abs(fused - sep)).item() <= 1e-5
+        if dtype == "c64":
+            assert bool(torch.all(torch.diagonal(diag) == 1.0))
+        else:
+            assert torch.max(torch.abs(torch.diagonal(diag) - 1.0)).item() <= TOL_K
+    ctx.sync_status()
+
+
 @pytest.mark.parametrize("n,reps", [(8, 3), (11, 3)])
 def test_chi8_fp32_vs_statevector(dk, n, reps):
     """reps = 3 keeps the exact bond 8: the chi = 8 FP32 kernels against brute force."""
