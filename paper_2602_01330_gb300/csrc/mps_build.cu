@@ -36,26 +36,40 @@
 
 namespace dk {
 
-struct cd {
-  double x, y;
+template <typename T>
+struct cx {
+  T x, y;
 };
+using cd = cx<double>;
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ cd mk(double x, double y) { return cd{x, y}; }
-__device__ __forceinline__ cd cmul(cd a, cd b) { return mk(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)); }
-__device__ __forceinline__ cd cconjmul(cd a, cd b) { return mk(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x)); }
-__device__ __forceinline__ cd cadd(cd a, cd b) { return mk(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ cd csub(cd a, cd b) { return mk(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ cd cscale(cd a, double s) { return mk(a.x * s, a.y * s); }
-__device__ __forceinline__ cd cconj(cd a) { return mk(a.x, -a.y); }
-__device__ __forceinline__ double cabs2(cd a) { return fma(a.x, a.x, a.y * a.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> mkc(T x, T y) { return cx<T>{x, y}; }
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) { return mkc(fmx(a.x, b.x, -a.y * b.y), fmx(a.x, b.y, a.y * b.x)); }
+template <typename T>
+__device__ __forceinline__ cx<T> cconjmul(cx<T> a, cx<T> b) { return mkc(fmx(a.x, b.x, a.y * b.y), fmx(a.x, b.y, -a.y * b.x)); }
+template <typename T>
+__device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return mkc(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return mkc(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return mkc(a.x * s, a.y * s); }
+template <typename T>
+__device__ __forceinline__ cx<T> cconj(cx<T> a) { return mkc(a.x, -a.y); }
+template <typename T>
+__device__ __forceinline__ T cabs2(cx<T> a) { return fmx(a.x, a.x, a.y * a.y); }
 
 constexpr double PI_D = 3.14159265358979323846;
 
 // Closed-form factors of one site for RP repetitions: u^e and w^e for e in [-RP, RP],
 // u = exp(-i phi/2), w = exp(-i theta/2) (unit modulus, so u^-e = conj(u^e)).
-template <int RP>
+template <int RP, typename T = double>
 struct SiteFactors {
-  cd up[RP + 1];
-  cd wp[RP + 1];
+  using C = cx<T>;
+  C up[RP + 1];
+  C wp[RP + 1];
   __device__ __forceinline__ void make(double phi, double theta) {
     double sn, cs;
     sincos(-0.5 * phi, &sn, &cs);
@@ -63,9 +77,9 @@ struct SiteFactors {
     sincos(-0.5 * theta, &sn, &cs);
     make_from(u, mk(cs, sn));
   }
-  __device__ __forceinline__ void make_from(cd u, cd w) {
-    up[0] = mk(1.0, 0.0);
-    wp[0] = mk(1.0, 0.0);
+  __device__ __forceinline__ void make_from(C u, C w) {
+    up[0] = mkc(T(1), T(0));
+    wp[0] = mkc(T(1), T(0));
 #pragma unroll
     for (int q = 1; q <= RP; ++q) {
       up[q] = cmul(up[q - 1], u);
@@ -74,24 +88,24 @@ struct SiteFactors {
   }
   // powers by exponent in -RP..RP, picked with selects so that a run-time exponent does
   // not send the tables to local memory
-  __device__ __forceinline__ static cd pick(const cd (&tab)[RP + 1], int e) {
+  __device__ __forceinline__ static C pick(const C (&tab)[RP + 1], int e) {
     const int a = e >= 0 ? e : -e;
-    cd r = tab[0];
+    C r = tab[0];
 #pragma unroll
     for (int q = 1; q <= RP; ++q) r = a == q ? tab[q] : r;
     return e >= 0 ? r : cconj(r);
   }
-  __device__ __forceinline__ cd upow(int e) const { return pick(up, e); }
-  __device__ __forceinline__ cd wpow(int e) const { return pick(wp, e); }
+  __device__ __forceinline__ C upow(int e) const { return pick(up, e); }
+  __device__ __forceinline__ C wpow(int e) const { return pick(wp, e); }
   // L_k(c) = 2^(-r/2) (-1)^popc(c & c>>1) u^(r - 2 popc(c))
-  __device__ __forceinline__ cd local(int c) const {
+  __device__ __forceinline__ C local(int c) const {
     constexpr double amp = RP == 1 ? 0.70710678118654752440 : RP == 2 ? 0.5 : RP == 3 ? 0.35355339059327376220
                          : RP == 4 ? 0.25 : 0.17677669529663688110;
-    const double sign = (__popc(c & (c >> 1)) & 1) ? -amp : amp;
+    const T sign = (__popc(c & (c >> 1)) & 1) ? T(-amp) : T(amp);
     return cscale(upow(RP - 2 * __popc(c)), sign);
   }
   // bond phase between closed-form left index cp and right index c
-  __device__ __forceinline__ cd bond(int cp, int c) const { return wpow(RP - 2 * __popc(cp ^ c)); }
+  __device__ __forceinline__ C bond(int cp, int c) const { return wpow(RP - 2 * __popc(cp ^ c)); }
 };
 
 __device__ __forceinline__ void store_cplx(void* out, size_t idx, cd v, int c128) {
@@ -313,22 +327,43 @@ __global__ void __launch_bounds__(32) mps_build_pair_kernel(const float* __restr
   if (log_norm && live && s == 0) log_norm[i] = chain[0][0].half_log_mod();
 }
 
+// Phase exp(i a) for an angle given as an unevaluated sum a = hi + lo, |lo| <= 2^-22 |hi|:
+// sincosf of hi, then the first-order correction by lo (the neglected term is lo^2 / 2).
+__device__ __forceinline__ cx<float> expi_split(float hi, float lo) {
+  float sn, cs;
+  sincosf(hi, &sn, &cs);
+  return mkc(fmaf(-lo, sn, cs), fmaf(lo, cs, sn));
+}
+
+// pi - v as hi + lo for a float v in [0, pi] (Fast2Sum of the float pi against v, plus the
+// float pi's own error); the pair carries pi - v to about 2^-48 relative
+__device__ __forceinline__ void pi_minus(float v, float& hi, float& lo) {
+  constexpr float PI_HI = 3.14159274101257324219f;   // pi rounded to float
+  constexpr float PI_LO = -8.74227800037248e-8f;     // pi - PI_HI
+  hi = PI_HI - v;
+  lo = ((PI_HI - hi) - v) + PI_LO;
+}
+
 // Eight threads per sample for the bond-4 tensors (chi_max = 4, reps <= 2): thread q of a
 // sample's group handles block s = q >> 2 and row (t, j) = ((q >> 1) & 1, q & 1) of that
 // block's 4 x HA matrix M_s, and the Gram-Schmidt sums over the 4 rows are shuffle
-// reductions inside the group. Every FP64 warp instruction costs the same issue time on
-// GB300 whatever its active lanes, so spreading one sample over 8 threads shortens the
-// per-site dependency chain about 2.5x against two threads per sample. The exponentials of
-// site k+1 are evaluated while site k is factorised; with log_norm set, every thread also
-// runs the Gram's transfer arithmetic on the sample's rounded tensors (gathered by shuffles)
-// so that ln|<psi~|psi~>| is bit-identical to the Gram diagonal.
+// reductions inside the group. The arithmetic runs in the stored precision `real`:
+// complex128 tensors are factorised in FP64, complex64 ones in FP32 (FP64 issues at a
+// small fraction of the FP32 rate on GB300, and every FP32 result is rounded to the stored
+// FP32 anyway). In FP32 the rotation angles are formed exactly enough by error-free
+// transforms (pi - x and the products as float pairs), so the only FP32 error in a phase
+// is sincosf's. The exponentials of site k+1 are evaluated while site k is factorised;
+// with log_norm set, every thread also runs the Gram's transfer arithmetic on the
+// sample's stored tensors (gathered by shuffles) so that ln|<psi~|psi~>| is bit-identical
+// to the Gram diagonal.
 template <int HA, int RP, typename real>
 __global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restrict__ x, int m, int n,
                                                            double angle_scale, int entangle,
                                                            void* __restrict__ out, int32_t* __restrict__ bond,
                                                            float* __restrict__ log_norm) {
+  using C = cx<real>;
   constexpr int HS = 2, CHI = 4;
-  constexpr int c128 = sizeof(real) == 8 ? 1 : 0;
+  constexpr bool c128 = sizeof(real) == 8;
   const int q = threadIdx.x & 7;
   const int s = q >> 2, t = (q >> 1) & 1, j = q & 1;
   const int row = t * HS + j;  // this thread's left-bond position
@@ -336,137 +371,167 @@ __global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restri
   const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
   const bool live = i0 < m;
   const int i = live ? i0 : m - 1;
+  const int base_lane = threadIdx.x & ~7;
   const float* xs = x + size_t(i) * n;
+  const C zero = mkc(real(0), real(0));
   // Rrow[cp] = R_t[j][cp]: row j of the previous site's block-t factor (HA columns)
-  cd Rrow[HA];
+  C Rrow[HA];
 #pragma unroll
-  for (int c = 0; c < HA; ++c) Rrow[c] = mk(0.0, 0.0);
-  if (t == 0 && j == 0) Rrow[0] = mk(1.0, 0.0);
+  for (int c = 0; c < HA; ++c) Rrow[c] = zero;
+  if (t == 0 && j == 0) Rrow[0] = mkc(real(1), real(0));
   int act = 1;
-  auto expo = [&](int k) {  // thread q & 1 == 0: u_k, q & 1 == 1: w_k (see mps_build_pair_kernel)
-    const double xk = double(xs[k]);
-    const double xp = k > 0 ? double(xs[k - 1]) : 0.0;
-    const double arg = (q & 1) == 0 ? -0.5 * angle_scale * xk : ((entangle && k > 0) ? -(PI_D - xp) * (PI_D - xk) : 0.0);
-    double sn, cs;
-    sincos(arg, &sn, &cs);
-    return mk(cs, sn);
+  // -angle_scale / 2 as a float pair (FP32 form)
+  const float g_hi = float(-0.5 * angle_scale);
+  const float g_lo = float(-0.5 * angle_scale - double(g_hi));
+  // thread q & 1 == 0: u_k = exp(-i angle_scale x_k / 2); q & 1 == 1: w_k =
+  // exp(-i (pi - x_{k-1})(pi - x_k)) (one factor of the RZZ phase, see mps_build_pair_kernel)
+  auto expo = [&](int k) -> C {
+    const float xk = xs[k];
+    const float xp = k > 0 ? xs[k - 1] : 0.0f;
+    const bool ent = entangle && k > 0;
+    if constexpr (c128) {
+      const double arg = (q & 1) == 0 ? -0.5 * angle_scale * double(xk)
+                                      : (ent ? -(PI_D - double(xp)) * (PI_D - double(xk)) : 0.0);
+      double sn, cs;
+      sincos(arg, &sn, &cs);
+      return mkc(cs, sn);
+    } else {
+      float hi, lo;
+      if ((q & 1) == 0) {
+        hi = g_hi * xk;
+        lo = fmaf(g_hi, xk, -hi) + g_lo * xk;
+      } else if (ent) {
+        float ah, al, bh, bl;
+        pi_minus(xp, ah, al);
+        pi_minus(xk, bh, bl);
+        const float ph = ah * bh;
+        const float pl = fmaf(ah, bh, -ph) + fmaf(ah, bl, al * bh);
+        hi = -ph;
+        lo = -pl;
+      } else {
+        hi = 0.0f;
+        lo = 0.0f;
+      }
+      return expi_split(hi, lo);
+    }
   };
-  auto gsum = [&](double v) {  // sum over the 4 threads of this block
+  auto gsum = [&](real v) {  // sum over the 4 threads of this block
     v += __shfl_xor_sync(mask, v, 1);
     v += __shfl_xor_sync(mask, v, 2);
     return v;
   };
-  auto gsumc = [&](cd v) { return mk(gsum(v.x), gsum(v.y)); };
+  auto gsumc = [&](C v) { return mkc(gsum(v.x), gsum(v.y)); };
+  auto inv_sqrt = [](real v) -> real {
+    if constexpr (c128) return rsqrt(v);
+    else return __frsqrt_rn(v);
+  };
+  constexpr real TINY = c128 ? real(1e-300) : real(1e-30);
   PairE<real, HS> chain[1][1];
   chain[0][0].init();
-  cd e_cur = expo(0);
+  C e_cur = expo(0);
   for (int k = 0; k < n; ++k) {
-    const cd e_next = (k + 1 < n) ? expo(k + 1) : mk(1.0, 0.0);
-    SiteFactors<RP> f;
+    const C e_next = (k + 1 < n) ? expo(k + 1) : mkc(real(1), real(0));
+    SiteFactors<RP, real> f;
     {
-      const int base_lane = (threadIdx.x & ~7);
-      const cd u = mk(__shfl_sync(mask, e_cur.x, base_lane), __shfl_sync(mask, e_cur.y, base_lane));
-      const cd w = mk(__shfl_sync(mask, e_cur.x, base_lane + 1), __shfl_sync(mask, e_cur.y, base_lane + 1));
+      const C u = mkc(__shfl_sync(mask, e_cur.x, base_lane), __shfl_sync(mask, e_cur.y, base_lane));
+      const C w = mkc(__shfl_sync(mask, e_cur.x, base_lane + 1), __shfl_sync(mask, e_cur.y, base_lane + 1));
       f.make_from(u, w);
     }
     if (bond && i0 == 0 && q == 0) bond[k] = act;
-    cd qv[HS];  // this thread's row of Q_s: stored element (s, jc, l = row) for jc < HS
+    C qv[HS];  // this thread's row of Q_s: stored element (s, jc, l = row) for jc < HS
     if (k < n - 1) {
-      cd mrow[HA];
+      C mrow[HA];
 #pragma unroll
       for (int cc = 0; cc < HA; ++cc) {
         const int c = s * HA + cc;
-        cd acc = mk(0.0, 0.0);
+        C acc = zero;
 #pragma unroll
         for (int cp = 0; cp < HA; ++cp) acc = cadd(acc, cmul(Rrow[cp], f.bond(t * HA + cp, c)));
         mrow[cc] = cmul(f.local(c), acc);
       }
       const int nref = act < HA ? act : HA;
       // classical Gram-Schmidt with one re-orthogonalisation pass over the 4 rows
-      cd qrow[HA], rcol[HA][HA];
+      C qrow[HA], rcol[HA][HA];
 #pragma unroll
       for (int a = 0; a < HA; ++a)
 #pragma unroll
-        for (int b = 0; b < HA; ++b) rcol[a][b] = mk(0.0, 0.0);
+        for (int b = 0; b < HA; ++b) rcol[a][b] = zero;
 #pragma unroll
       for (int c = 0; c < HA; ++c) {
-        cd v = mrow[c];
+        C v = mrow[c];
         if (c < nref) {
 #pragma unroll
           for (int pass = 0; pass < 2; ++pass)
 #pragma unroll
             for (int pq = 0; pq < c; ++pq) {
-              const cd r = gsumc(cconjmul(qrow[pq], v));
+              const C r = gsumc(cconjmul(qrow[pq], v));
               rcol[pq][c] = cadd(rcol[pq][c], r);
               v = csub(v, cmul(qrow[pq], r));
             }
-          const double n2 = gsum(cabs2(v));
-          const double inv = n2 > 1e-300 ? rsqrt(n2) : 0.0;
-          rcol[c][c] = mk(n2 * inv, 0.0);
+          const real n2 = gsum(cabs2(v));
+          const real inv = n2 > TINY ? inv_sqrt(n2) : real(0);
+          rcol[c][c] = mkc(n2 * inv, real(0));
           qrow[c] = cscale(v, inv);
         } else {
 #pragma unroll
           for (int pq = 0; pq < HA; ++pq)
             if (pq < nref) rcol[pq][c] = gsumc(cconjmul(qrow[pq], v));
-          qrow[c] = mk(0.0, 0.0);
+          qrow[c] = zero;
         }
       }
 #pragma unroll
-      for (int jc = 0; jc < HS; ++jc) qv[jc] = jc < HA ? qrow[jc] : mk(0.0, 0.0);
+      for (int jc = 0; jc < HS; ++jc) qv[jc] = jc < HA ? qrow[jc < HA ? jc : 0] : zero;
       // next R row for this thread: row j of block t's factor, which every thread of block t
-      // holds after the reductions
-      // (thread 4 t + j holds block t and the same j, so its row-j pick is the one wanted)
-      const int src = (threadIdx.x & ~7) + 4 * t + j;
+      // holds after the reductions (thread 4 t + j holds block t and the same j, so its
+      // row-j pick is the one wanted)
+      const int src = base_lane + 4 * t + j;
 #pragma unroll
       for (int cp = 0; cp < HA; ++cp) {
-        cd mine = rcol[0][cp];
+        C mine = rcol[0][cp];
         if constexpr (HA > 1) mine = j == 1 ? rcol[1][cp] : mine;
-        else mine = j == 1 ? mk(0.0, 0.0) : mine;
-        Rrow[cp] = mk(__shfl_sync(mask, mine.x, src), __shfl_sync(mask, mine.y, src));
+        else mine = j == 1 ? zero : mine;
+        Rrow[cp] = mkc(__shfl_sync(mask, mine.x, src), __shfl_sync(mask, mine.y, src));
       }
       act = 2 * nref;
     } else {
-      cd acc = mk(0.0, 0.0);
+      C acc = zero;
 #pragma unroll
       for (int cc = 0; cc < HA; ++cc) {
         const int c = s * HA + cc;
-        cd inner = mk(0.0, 0.0);
+        C inner = zero;
 #pragma unroll
         for (int cp = 0; cp < HA; ++cp) inner = cadd(inner, cmul(Rrow[cp], f.bond(t * HA + cp, c)));
         acc = cadd(acc, cmul(f.local(c), inner));
       }
-      double n2 = cabs2(acc);
+      real n2 = cabs2(acc);
       n2 += __shfl_xor_sync(mask, n2, 1);
       n2 += __shfl_xor_sync(mask, n2, 2);
       n2 += __shfl_xor_sync(mask, n2, 4);
-      const double inv = n2 > 0.0 ? rsqrt(n2) : 0.0;
+      const real inv = n2 > real(0) ? inv_sqrt(n2) : real(0);
       qv[0] = cscale(acc, inv);
-      qv[1] = mk(0.0, 0.0);
+      qv[1] = zero;
       if (bond && i0 == 0 && q == 0) bond[n] = 1;
-    }
-    real vr[HS], vi[HS];
-#pragma unroll
-    for (int jc = 0; jc < HS; ++jc) {
-      vr[jc] = real(qv[jc].x);
-      vi[jc] = real(qv[jc].y);
     }
     if (live) {
       const size_t base = (size_t(k) * m + i) * (CHI * CHI);
 #pragma unroll
-      for (int jc = 0; jc < HS; ++jc) store_cplx(out, base + (s * HS + jc) * CHI + row, qv[jc], c128);
+      for (int jc = 0; jc < HS; ++jc) {
+        const size_t idx = base + (s * HS + jc) * CHI + row;
+        if constexpr (c128) reinterpret_cast<double2*>(out)[idx] = make_double2(qv[jc].x, qv[jc].y);
+        else reinterpret_cast<float2*>(out)[idx] = make_float2(qv[jc].x, qv[jc].y);
+      }
     }
     if (log_norm) {
       // gather the sample's 16 stored values: element (s', jc, l) from thread 4 s' + l
       real ar[2][HS][CHI], ai[2][HS][CHI];
-      const int base_lane = threadIdx.x & ~7;
 #pragma unroll
       for (int ss = 0; ss < 2; ++ss)
 #pragma unroll
         for (int l = 0; l < CHI; ++l)
 #pragma unroll
           for (int jc = 0; jc < HS; ++jc) {
-            ar[ss][jc][l] = __shfl_sync(mask, vr[jc], base_lane + 4 * ss + l);
-            ai[ss][jc][l] = __shfl_sync(mask, vi[jc], base_lane + 4 * ss + l);
+            ar[ss][jc][l] = __shfl_sync(mask, qv[jc].x, base_lane + 4 * ss + l);
+            ai[ss][jc][l] = __shfl_sync(mask, qv[jc].y, base_lane + 4 * ss + l);
           }
       auto ld = [&](int, int ss, int tt, Blk<real, HS>& blk) {
 #pragma unroll
@@ -684,11 +749,12 @@ static dk_status launch_build(const float* x, int m, int n, const dk_fmap* fm, i
     constexpr int RP = HA == 1 ? 1 : 2;
     // the fused self-overlap covers the bond-4 tensors (the Gram kernels' HS = 2)
     float* ln = HS == 2 ? log_norm : nullptr;
-    // Bond 4: 8 threads per sample while the set is small enough that the per-sample
-    // chain latency, not the FP64 issue rate, sets the time (up to about 2.5 warps per SM
-    // sub-partition); two threads per sample beyond that, where the 8-thread form's extra
-    // reduction instructions cost more than its shorter chain saves.
-    if (HS == 2 && (m + 3) / 4 <= 10 * sm_count) {
+    // Bond 4: 8 threads per sample, in FP32 for complex64 at every size; for complex128
+    // (FP64) while the set is small enough that the per-sample chain latency, not the FP64
+    // issue rate, sets the time (up to about 2.5 warps per SM sub-partition), and two threads
+    // per sample beyond that, where the 8-thread form's extra reduction instructions cost
+    // more than its shorter chain saves.
+    if (HS == 2 && (!c128 || (m + 3) / 4 <= 10 * sm_count)) {
       // 4 samples per warp-sized CTA; fewer per CTA when that would leave SMs idle
       const int spc = (m + 3) / 4 >= sm_count ? 4 : ((m + 1) / 2 >= sm_count ? 2 : 1);
       const int grid = (m + spc - 1) / spc;
