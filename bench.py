@@ -43,6 +43,32 @@ def entries_per_step(n_train, n_test):
     return n_train * (n_train + 1) // 2 + n_test * n_train
 
 
+# DRAM bytes (read + write) of one Gram launch of the benchmarked workload, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass) of this bench's own launch;
+# the command and figures are in profiles/gram_kernel_dram_traffic_fmnist784_gram2000.md.
+# Reported only while the kernel sources hash to the value they had when it was taken.
+GRAM_TRAFFIC = {"n_train": 2000, "bytes": 1.11e9 + 20.07e6,
+                "sources_sha256": "1e1fb95938c62f72e2c891552f4be1cb66cdc289a8f7ef4205ab860b8dfdfa53"}
+GRAM_SOURCES = ["gram.cu", "gram_common.cuh", "transfer.cuh", "common.cuh"]
+
+
+def gram_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2602_01330_gb300", "csrc")
+    for f in GRAM_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def gram_traffic(n_train: int):
+    """Measured DRAM bytes per Gram launch, or None if the kernel or the workload differs."""
+    if GRAM_TRAFFIC["bytes"] is None or n_train != GRAM_TRAFFIC["n_train"]:
+        return None
+    return GRAM_TRAFFIC["bytes"] if gram_sources_sha256() == GRAM_TRAFFIC["sources_sha256"] else None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
@@ -255,7 +281,9 @@ def run_ours(args):
             ev[3].record(stream)
             phase_events.append(ev)
 
-    launches_per_step = 2 + 2 + 1 + 1  # (build + self-overlap) x 2, Gram, rows
+    # MPS build x 2 (the ln-norms are fused into the build at bond 4), Gram, rows: the ncu launch
+    # list of this command shows exactly these four libdualk kernels per step
+    launches_per_step = 2 + 1 + 1
 
     def barrier():
         if world > 1:
@@ -339,8 +367,8 @@ def run_ours(args):
                    "w": w, "mps_dtype": "complex64", "parallelism": f"independent problem per GPU x{world}",
                    "l2": "256 MB buffer written before every timed step (inside the timed region)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None,
-                     "kernel": "gram_kernel<float,chi=4> (symmetric 2000x2000 Gram)",
+                     "frac": achieved / peak_tflops, "traffic": gram_traffic(n_tr),
+                     "kernel": f"gram_kernel<float,chi=4> (symmetric {n_tr}x{n_tr} Gram)",
                      "peak_source": f"FP32 FMA peak {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
                      "avg_launch_ms": gram_avg_ms},
         "e2e": e2e,

@@ -54,6 +54,11 @@ __device__ __forceinline__ void decode_tile(const GramArgs& p, int tr, int tc, i
   }
 }
 
+// Component c (compile-time after unrolling) of a float4.
+__device__ __forceinline__ float f4_get(const float4& v, int c) {
+  return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+
 // Compensated (Kahan) FP32 accumulation of one squared feature difference.
 __device__ __forceinline__ void kahan_add_sq(float& sum, float& comp, float d) {
   const float y = fmaf(d, d, -comp);

@@ -121,11 +121,13 @@ struct PairE {
 template <typename real, int H>
 __device__ __forceinline__ void term(Blk<real, H>& acc, const Blk<real, H>& e, const Blk<real, H>& ai,
                                      const Blk<real, H>& aj) {
-  Blk<real, H> f;
+  // one column of F at a time: each acc entry sees the same additions in the same order as
+  // with the whole F formed first, with a quarter of the temporaries live
 #pragma unroll
-  for (int a = 0; a < H; ++a)
+  for (int c = 0; c < H; ++c) {
+    real fr_c[H], fi_c[H];
 #pragma unroll
-    for (int c = 0; c < H; ++c) {
+    for (int a = 0; a < H; ++a) {
       // operand order keeps each register in two consecutive FMAs (operand reuse)
       real fr = e.r[a][0] * aj.r[0][c];
       real fi = e.r[a][0] * aj.i[0][c];
@@ -138,25 +140,24 @@ __device__ __forceinline__ void term(Blk<real, H>& acc, const Blk<real, H>& e, c
         fr = fma(-e.i[a][b], aj.i[b][c], fr);
         fi = fma(e.i[a][b], aj.r[b][c], fi);
       }
-      f.r[a][c] = fr;
-      f.i[a][c] = fi;
+      fr_c[a] = fr;
+      fi_c[a] = fi;
     }
 #pragma unroll
-  for (int p = 0; p < H; ++p)
-#pragma unroll
-    for (int c = 0; c < H; ++c) {
+    for (int p = 0; p < H; ++p) {
       real ar = acc.r[p][c];
       real aim = acc.i[p][c];
 #pragma unroll
       for (int a = 0; a < H; ++a) {
-        ar = fma(ai.r[a][p], f.r[a][c], ar);
-        aim = fma(ai.r[a][p], f.i[a][c], aim);
-        ar = fma(ai.i[a][p], f.i[a][c], ar);
-        aim = fma(-ai.i[a][p], f.r[a][c], aim);
+        ar = fma(ai.r[a][p], fr_c[a], ar);
+        aim = fma(ai.r[a][p], fi_c[a], aim);
+        ar = fma(ai.i[a][p], fi_c[a], ar);
+        aim = fma(-ai.i[a][p], fr_c[a], aim);
       }
       acc.r[p][c] = ar;
       acc.i[p][c] = aim;
     }
+  }
 }
 
 // One site for a PR x PC group of pairs (rows share A(x_i), columns share A(x_j)).

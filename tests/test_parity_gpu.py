@@ -263,6 +263,25 @@ def test_bond4_build_kernels_agree_small_and_large_sets(dk, dtype):
     ctx.sync_status()
 
 
+@pytest.mark.parametrize("d", [8, 16])
+def test_bond4_fp32_build_relative_accuracy(dk, d):
+    """The complex64 build factorises in FP32. On 96 uniform-angle samples (seed 5),
+    reps = 2, where many K_q are O(1): |dK| <= 1e-6 everywhere and the relative error of
+    every K_q > 1e-3 within 2e-5 of the oracle (an FP64 factorisation rounded to complex64
+    storage reaches about 2e-6 here; the FP32 one about 4e-6)."""
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    x = synthetic.uniform_angles(96, d, seed=5).astype(np.float32)
+    m = dualk.mps_build(ctx, _dev(torch, x), dualk.FeatureMap(reps=2, chi_max=4))
+    kq = dualk.gram(ctx, m, w=1.0, want=("kq",))["kq"].cpu().numpy().astype(np.float64)
+    kq_ref, _ = _oracle_block(x, x, 2)
+    assert np.max(np.abs(kq - kq_ref)) <= TOL_K
+    big = kq_ref > 1e-3
+    assert big.sum() > 96
+    assert np.max(np.abs(kq - kq_ref)[big] / kq_ref[big]) <= 2e-5
+    ctx.sync_status()
+
+
 @pytest.mark.parametrize("n,reps", [(8, 3), (11, 3)])
 def test_chi8_fp32_vs_statevector(dk, n, reps):
     """reps = 3 keeps the exact bond 8: the chi = 8 FP32 kernels against brute force."""
