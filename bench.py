@@ -345,12 +345,15 @@ def run_ours(args):
                          f"{s_tr * s_te} row entries, {secs:.1f} s, FP64 NumPy single thread"}
 
     # The other two parts of the metric, measured after the timed region (rank 0, one GPU):
-    # the split-BF16 tensor-core Gram against the FP32 one at bond 32 (d = 256, reps = 5),
-    # and the continuous-batching server's latency.
+    # the split-BF16 tensor-core Gram against the FP32 one at bond 32 (reps = 5; d = 256,
+    # where every off-diagonal K_q is tiny, and d = 16, where many are not), the FP32 against
+    # the FP64 QR sweep of the bond-4 build, and the continuous-batching server's latency.
     mixed = serving_stats = None
     if rank == 0 and world == 1 and not args.no_extras:
         from paper_2602_01330_gb300 import precision, serving
-        mixed = precision.compare(m=512, pool=128, n_uniform=40, n_near=20, n_diag=10, ctx=ctx)
+        mixed = {"d256": precision.compare(m=512, pool=128, n_uniform=40, n_near=20, n_diag=10, ctx=ctx),
+                 "d16": precision.compare(m=512, d=16, pool=128, n_uniform=40, n_near=20, n_diag=10, ctx=ctx),
+                 "mps_build_qr": precision.compare_build_qr(ctx=ctx)}
         serving_stats = serving.run_benchmark(ctx, m=8000, requests=150, rho=0.8, slots=8)
 
     if world > 1:

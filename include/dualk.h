@@ -86,6 +86,9 @@ typedef struct {
   float angle_scale;  /* RZ angle = angle_scale * x_i (2 for the ZZ-chain map) */
   int entangle;       /* 1: RZZ chain applied; 0: product state */
   int chi_max;        /* stored bond dimension: 4, 8, 16 or 32, and >= 2^reps */
+  int qr_prec;        /* arithmetic of the left-canonical QR sweep for complex64 output at
+                         chi_max 4: DK_PREC_F32 (0, default) or DK_PREC_F64. complex128
+                         output and wider bonds always use FP64. */
 } dk_fmap;
 
 /* Create a context on `device` (sets it current on the calling thread). The context
@@ -114,9 +117,11 @@ size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
  *
  * Exact construction: every RZZ layer is a diagonal bond-2 operator, so after r
  * repetitions the state is an MPS of bond 2^r whose site tensors have a closed form
- * in (x_{k-1}, x_k). Each sample's chain is then brought to left-canonical form by
- * Householder QR in FP64, one bond block at a time (the only FP64 on the GPU),
- * normalised, and rounded to `dtype`.
+ * in (x_{k-1}, x_k). Each sample's chain is then brought to left-canonical form by QR,
+ * one bond block at a time (Gram-Schmidt with re-orthogonalisation at bond 4, Householder
+ * for wider bonds), normalised, and rounded to `dtype`. The QR arithmetic is FP64, except
+ * for complex64 output at chi_max 4 with fm->qr_prec = DK_PREC_F32 (the default), where it
+ * is FP32; no bond is truncated in either case.
  *   x          m x n float32 features (device)
  *   fm         feature map (host pointer)
  *   mps        dk_mps_bytes(m, n, fm->chi_max, dtype) bytes (device, written)
@@ -125,7 +130,8 @@ size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
  *   log_norm   m floats (device, written, may be NULL): ln |<psi~_i|psi~_i>| of the
  *              rounded tensors, evaluated by the same transfer arithmetic as the Gram
  *              calls; passing it to them normalises K_q so that K_q(x, x) = 1.
- * Errors: DK_ERR_ARG (m < 1, n < 1, NULL x/mps/fm, reps outside 1..5, misaligned mps),
+ * Errors: DK_ERR_ARG (m < 1, n < 1, NULL x/mps/fm, reps outside 1..5, qr_prec neither
+ *         DK_PREC_F32 nor DK_PREC_F64, misaligned mps),
  *         DK_ERR_UNSUPPORTED (chi_max not in {4, 8, 16, 32} or below 2^reps; log_norm
  *         requested for a chi_max / dtype without a Gram kernel: complex64 has chi_max 4,
  *         8 and 32, complex128 chi_max 4). */

@@ -347,23 +347,25 @@ __device__ __forceinline__ void pi_minus(float v, float& hi, float& lo) {
 // Eight threads per sample for the bond-4 tensors (chi_max = 4, reps <= 2): thread q of a
 // sample's group handles block s = q >> 2 and row (t, j) = ((q >> 1) & 1, q & 1) of that
 // block's 4 x HA matrix M_s, and the Gram-Schmidt sums over the 4 rows are shuffle
-// reductions inside the group. The arithmetic runs in the stored precision `real`:
-// complex128 tensors are factorised in FP64, complex64 ones in FP32 (FP64 issues at a
-// small fraction of the FP32 rate on GB300, and every FP32 result is rounded to the stored
-// FP32 anyway). In FP32 the rotation angles are formed exactly enough by error-free
-// transforms (pi - x and the products as float pairs), so the only FP32 error in a phase
-// is sincosf's. The exponentials of site k+1 are evaluated while site k is factorised;
+// reductions inside the group. The arithmetic runs in `creal`: FP64 for complex128
+// output, and for complex64 output FP32 by default or FP64 on request (dk_fmap.qr_prec).
+// FP64 issues at a small fraction of the FP32 rate on GB300, and the gauge QR of the exact
+// bond-4 chain truncates nothing, so the FP32 sweep only adds rounding of the size of the
+// complex64 storage's own. In FP32 the rotation angles are formed exactly enough by
+// error-free transforms (pi - x and the products as float pairs), so the only FP32 error
+// in a phase is sincosf's. The exponentials of site k+1 are evaluated while site k is factorised;
 // with log_norm set, every thread also runs the Gram's transfer arithmetic on the
 // sample's stored tensors (gathered by shuffles) so that ln|<psi~|psi~>| is bit-identical
 // to the Gram diagonal.
-template <int HA, int RP, typename real>
+template <int HA, int RP, typename real, typename creal>
 __global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restrict__ x, int m, int n,
                                                            double angle_scale, int entangle,
                                                            void* __restrict__ out, int32_t* __restrict__ bond,
                                                            float* __restrict__ log_norm) {
-  using C = cx<real>;
+  using C = cx<creal>;
   constexpr int HS = 2, CHI = 4;
-  constexpr bool c128 = sizeof(real) == 8;
+  constexpr bool c128 = sizeof(real) == 8;   // stored precision
+  constexpr bool f64 = sizeof(creal) == 8;   // arithmetic precision
   const int q = threadIdx.x & 7;
   const int s = q >> 2, t = (q >> 1) & 1, j = q & 1;
   const int row = t * HS + j;  // this thread's left-bond position
@@ -373,12 +375,12 @@ __global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restri
   const int i = live ? i0 : m - 1;
   const int base_lane = threadIdx.x & ~7;
   const float* xs = x + size_t(i) * n;
-  const C zero = mkc(real(0), real(0));
+  const C zero = mkc(creal(0), creal(0));
   // Rrow[cp] = R_t[j][cp]: row j of the previous site's block-t factor (HA columns)
   C Rrow[HA];
 #pragma unroll
   for (int c = 0; c < HA; ++c) Rrow[c] = zero;
-  if (t == 0 && j == 0) Rrow[0] = mkc(real(1), real(0));
+  if (t == 0 && j == 0) Rrow[0] = mkc(creal(1), creal(0));
   int act = 1;
   // -angle_scale / 2 as a float pair (FP32 form)
   const float g_hi = float(-0.5 * angle_scale);
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restri
     const float xk = xs[k];
     const float xp = k > 0 ? xs[k - 1] : 0.0f;
     const bool ent = entangle && k > 0;
-    if constexpr (c128) {
+    if constexpr (f64) {
       const double arg = (q & 1) == 0 ? -0.5 * angle_scale * double(xk)
                                       : (ent ? -(PI_D - double(xp)) * (PI_D - double(xk)) : 0.0);
       double sn, cs;
@@ -415,23 +417,23 @@ __global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restri
       return expi_split(hi, lo);
     }
   };
-  auto gsum = [&](real v) {  // sum over the 4 threads of this block
+  auto gsum = [&](creal v) {  // sum over the 4 threads of this block
     v += __shfl_xor_sync(mask, v, 1);
     v += __shfl_xor_sync(mask, v, 2);
     return v;
   };
   auto gsumc = [&](C v) { return mkc(gsum(v.x), gsum(v.y)); };
-  auto inv_sqrt = [](real v) -> real {
-    if constexpr (c128) return rsqrt(v);
+  auto inv_sqrt = [](creal v) -> creal {
+    if constexpr (f64) return rsqrt(v);
     else return __frsqrt_rn(v);
   };
-  constexpr real TINY = c128 ? real(1e-300) : real(1e-30);
+  constexpr creal TINY = f64 ? creal(1e-300) : creal(1e-30);
   PairE<real, HS> chain[1][1];
   chain[0][0].init();
   C e_cur = expo(0);
   for (int k = 0; k < n; ++k) {
-    const C e_next = (k + 1 < n) ? expo(k + 1) : mkc(real(1), real(0));
-    SiteFactors<RP, real> f;
+    const C e_next = (k + 1 < n) ? expo(k + 1) : mkc(creal(1), creal(0));
+    SiteFactors<RP, creal> f;
     {
       const C u = mkc(__shfl_sync(mask, e_cur.x, base_lane), __shfl_sync(mask, e_cur.y, base_lane));
       const C w = mkc(__shfl_sync(mask, e_cur.x, base_lane + 1), __shfl_sync(mask, e_cur.y, base_lane + 1));
@@ -468,9 +470,9 @@ __global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restri
               rcol[pq][c] = cadd(rcol[pq][c], r);
               v = csub(v, cmul(qrow[pq], r));
             }
-          const real n2 = gsum(cabs2(v));
-          const real inv = n2 > TINY ? inv_sqrt(n2) : real(0);
-          rcol[c][c] = mkc(n2 * inv, real(0));
+          const creal n2 = gsum(cabs2(v));
+          const creal inv = n2 > TINY ? inv_sqrt(n2) : creal(0);
+          rcol[c][c] = mkc(n2 * inv, creal(0));
           qrow[c] = cscale(v, inv);
         } else {
 #pragma unroll
@@ -503,22 +505,29 @@ __global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restri
         for (int cp = 0; cp < HA; ++cp) inner = cadd(inner, cmul(Rrow[cp], f.bond(t * HA + cp, c)));
         acc = cadd(acc, cmul(f.local(c), inner));
       }
-      real n2 = cabs2(acc);
+      creal n2 = cabs2(acc);
       n2 += __shfl_xor_sync(mask, n2, 1);
       n2 += __shfl_xor_sync(mask, n2, 2);
       n2 += __shfl_xor_sync(mask, n2, 4);
-      const real inv = n2 > real(0) ? inv_sqrt(n2) : real(0);
+      const creal inv = n2 > creal(0) ? inv_sqrt(n2) : creal(0);
       qv[0] = cscale(acc, inv);
       qv[1] = zero;
       if (bond && i0 == 0 && q == 0) bond[n] = 1;
+    }
+    // the stored values, rounded once: to memory and, for the self-overlap, to registers
+    real vr[HS], vi[HS];
+#pragma unroll
+    for (int jc = 0; jc < HS; ++jc) {
+      vr[jc] = real(qv[jc].x);
+      vi[jc] = real(qv[jc].y);
     }
     if (live) {
       const size_t base = (size_t(k) * m + i) * (CHI * CHI);
 #pragma unroll
       for (int jc = 0; jc < HS; ++jc) {
         const size_t idx = base + (s * HS + jc) * CHI + row;
-        if constexpr (c128) reinterpret_cast<double2*>(out)[idx] = make_double2(qv[jc].x, qv[jc].y);
-        else reinterpret_cast<float2*>(out)[idx] = make_float2(qv[jc].x, qv[jc].y);
+        if constexpr (c128) reinterpret_cast<double2*>(out)[idx] = make_double2(vr[jc], vi[jc]);
+        else reinterpret_cast<float2*>(out)[idx] = make_float2(vr[jc], vi[jc]);
       }
     }
     if (log_norm) {
@@ -530,8 +539,8 @@ __global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restri
         for (int l = 0; l < CHI; ++l)
 #pragma unroll
           for (int jc = 0; jc < HS; ++jc) {
-            ar[ss][jc][l] = __shfl_sync(mask, qv[jc].x, base_lane + 4 * ss + l);
-            ai[ss][jc][l] = __shfl_sync(mask, qv[jc].y, base_lane + 4 * ss + l);
+            ar[ss][jc][l] = __shfl_sync(mask, vr[jc], base_lane + 4 * ss + l);
+            ai[ss][jc][l] = __shfl_sync(mask, vi[jc], base_lane + 4 * ss + l);
           }
       auto ld = [&](int, int ss, int tt, Blk<real, HS>& blk) {
 #pragma unroll
@@ -744,26 +753,29 @@ static int pair_kernel_lanes(int m, int sm_count) {
 template <int HS, int HA>
 static dk_status launch_build(const float* x, int m, int n, const dk_fmap* fm, int c128, void* mps, int32_t* bond,
                               float* log_norm, int sm_count, cudaStream_t st, bool* fused_norm) {
+  const bool fp64_qr = c128 || fm->qr_prec == DK_PREC_F64;
   *fused_norm = false;
   if constexpr (HA <= 2) {
     constexpr int RP = HA == 1 ? 1 : 2;
     // the fused self-overlap covers the bond-4 tensors (the Gram kernels' HS = 2)
     float* ln = HS == 2 ? log_norm : nullptr;
-    // Bond 4: 8 threads per sample, in FP32 for complex64 at every size; for complex128
-    // (FP64) while the set is small enough that the per-sample chain latency, not the FP64
-    // issue rate, sets the time (up to about 2.5 warps per SM sub-partition), and two threads
-    // per sample beyond that, where the 8-thread form's extra reduction instructions cost
-    // more than its shorter chain saves.
-    if (HS == 2 && (!c128 || (m + 3) / 4 <= 10 * sm_count)) {
+    // Bond 4: 8 threads per sample. FP32 arithmetic (complex64 output, qr_prec F32) at
+    // every size; FP64 arithmetic while the set is small enough that the per-sample chain
+    // latency, not the FP64 issue rate, sets the time (up to about 2.5 warps per SM
+    // sub-partition), and two threads per sample beyond that, where the 8-thread form's
+    // extra reduction instructions cost more than its shorter chain saves.
+    const bool small = (m + 3) / 4 <= 10 * sm_count;
+    if (HS == 2 && (!fp64_qr || small)) {
       // 4 samples per warp-sized CTA; fewer per CTA when that would leave SMs idle
       const int spc = (m + 3) / 4 >= sm_count ? 4 : ((m + 1) / 2 >= sm_count ? 2 : 1);
       const int grid = (m + spc - 1) / spc;
+      const double as = double(fm->angle_scale);
       if (c128) {
-        mps_build_oct_kernel<HA, RP, double><<<grid, 8 * spc, 0, st>>>(x, m, n, double(fm->angle_scale),
-                                                                     fm->entangle, mps, bond, ln);
+        mps_build_oct_kernel<HA, RP, double, double><<<grid, 8 * spc, 0, st>>>(x, m, n, as, fm->entangle, mps, bond, ln);
+      } else if (fp64_qr) {
+        mps_build_oct_kernel<HA, RP, float, double><<<grid, 8 * spc, 0, st>>>(x, m, n, as, fm->entangle, mps, bond, ln);
       } else {
-        mps_build_oct_kernel<HA, RP, float><<<grid, 8 * spc, 0, st>>>(x, m, n, double(fm->angle_scale),
-                                                                    fm->entangle, mps, bond, ln);
+        mps_build_oct_kernel<HA, RP, float, float><<<grid, 8 * spc, 0, st>>>(x, m, n, as, fm->entangle, mps, bond, ln);
       }
       *fused_norm = ln != nullptr;
       return launch_status();
@@ -812,6 +824,7 @@ DK_API dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const d
   using namespace dk;
   if (!ctx || !x || !fm || !mps || m < 1 || n < 1) return DK_ERR_ARG;
   if (fm->reps < 1 || fm->reps > 5) return DK_ERR_ARG;
+  if (fm->qr_prec != DK_PREC_F32 && fm->qr_prec != DK_PREC_F64) return DK_ERR_ARG;
   if (dtype != DK_C64 && dtype != DK_C128) return DK_ERR_ARG;
   const int chi = fm->chi_max;
   if (chi != 4 && chi != 8 && chi != 16 && chi != 32) return DK_ERR_UNSUPPORTED;

@@ -36,7 +36,7 @@ class DualKError(RuntimeError):
 
 class _Fmap(ctypes.Structure):
     _fields_ = [("reps", ctypes.c_int), ("angle_scale", ctypes.c_float),
-                ("entangle", ctypes.c_int), ("chi_max", ctypes.c_int)]
+                ("entangle", ctypes.c_int), ("chi_max", ctypes.c_int), ("qr_prec", ctypes.c_int)]
 
 
 _LIB = None
@@ -116,9 +116,10 @@ class FeatureMap:
     angle_scale: float = 2.0
     entangle: bool = True
     chi_max: int = 4
+    qr_prec: int = 0  # DK_PREC_F32 / DK_PREC_F64: QR arithmetic of complex64 bond-4 builds
 
     def _c(self):
-        return _Fmap(self.reps, self.angle_scale, 1 if self.entangle else 0, self.chi_max)
+        return _Fmap(self.reps, self.angle_scale, 1 if self.entangle else 0, self.chi_max, self.qr_prec)
 
 
 @dataclass
@@ -133,6 +134,7 @@ class MPS:
     log_norm: torch.Tensor    # float32, m
     x: torch.Tensor           # float32 m x n features it was built from
     norms: dict | None = None  # precision -> log_norm computed with that arithmetic
+    fmap: "FeatureMap | None" = None  # the feature map it was built with
 
     def log_norm_for(self, ctx: "Context", prec: int, stream=None) -> torch.Tensor:
         """ln-norms matching the Gram precision `prec` (dk_self_overlap when not built in)."""
@@ -223,7 +225,7 @@ def mps_build(ctx: Context, x: torch.Tensor, fmap: FeatureMap, dtype: int = DK_C
     fm = fmap._c()
     _check(_lib().dk_mps_build(ctx.handle, _ptr(x), m, n, ctypes.byref(fm), dtype, _ptr(out), _ptr(bond),
                                _ptr(lnorm), _stream(stream)), "dk_mps_build")
-    return MPS(out, m, n, fmap.chi_max, dtype, bond, lnorm, x)
+    return MPS(out, m, n, fmap.chi_max, dtype, bond, lnorm, x, fmap=fmap)
 
 
 def self_overlap(ctx: Context, mps: "MPS", prec: int, out: torch.Tensor | None = None, stream=None):

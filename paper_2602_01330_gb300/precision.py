@@ -1,5 +1,6 @@
 """Precision form: the same Gram in FP32 on CUDA cores and in split-BF16 (bf16x3) on
-tensor cores, timed and compared with each other (§II-C Eqs. 7-10).
+tensor cores, timed and compared with each other (§II-C Eqs. 7-10); and the bond-4 MPS
+build with its QR sweep in FP32 against FP64 (``compare_build_qr``).
 
 Data: the Fashion-MNIST-shaped generator at d = 256. reps = 3 gives the exact bond 8
 (FP32 only: the tensor-core path needs bond 32); reps = 5 reaches bond 32, where the
@@ -81,11 +82,47 @@ def compare(m: int = 512, d: int = 256, pool: int = 128, n_uniform: int = 40, n_
     diff = np.abs(kq_block[(32, "fp32")] - kq_block[(32, "bf16x3")])
     res["chi32_max_abs_dK_bf16x3_vs_fp32_block"] = float(diff.max())
     res["chi32_max_abs_dK_bf16x3_vs_fp32_sampled"] = float(max(diff[i, j] for i, j in pairs))
+    off = ~np.eye(m, dtype=bool)
+    res["chi32_offdiag_entries_with_K>1e-3"] = int((kq_block[(32, "fp32")][off] > 1e-3).sum())
     ctx.sync_status()
     if own:
         ctx.close()
     if return_blocks:
         return res, pairs, kq_block, x
+    return res
+
+
+def compare_build_qr(m: int = 2000, d: int = 784, block: int = 256, ctx: dualk.Context | None = None):
+    """The bond-4 MPS build with its QR sweep in FP32 (default) and in FP64, both stored as
+    complex64: build time for m samples at d features, and the largest |dK| and |d log K|
+    between the two Gram blocks of the first `block` samples; plus the same on 96
+    uniform-angle samples at d = 8, where many K_q are O(1) (largest relative dK there)."""
+    own = ctx is None
+    ctx = ctx or dualk.Context(0)
+    res = {"workload": f"fmnist d={d} m={m} (build timing), Gram of the first {block}; uniform d=8 m=96"}
+    cases = {"fmnist": torch.from_numpy(synthetic.fmnist_like(m, 0, d)["x_train"]).cuda(),
+             "uniform8": torch.from_numpy(synthetic.uniform_angles(96, 8, seed=5).astype(np.float32)).cuda()}
+    out = {}
+    for name, prec in (("fp32_qr", dualk.DK_PREC_F32), ("fp64_qr", dualk.DK_PREC_F64)):
+        fm = dualk.FeatureMap(reps=2, chi_max=4, qr_prec=prec)
+        x = cases["fmnist"]
+        buf = torch.empty(dualk.mps_bytes(m, d, 4), dtype=torch.uint8, device="cuda")
+        res[f"build_ms_{name}"] = _time(lambda: dualk.mps_build(ctx, x, fm, out=buf), reps=3)
+        mp = dualk.mps_build(ctx, x[:block].contiguous(), fm)
+        g = dualk.gram(ctx, mp, w=1.0, want=("kq", "logkq"))
+        mu = dualk.mps_build(ctx, cases["uniform8"], fm)
+        gu = dualk.gram(ctx, mu, w=1.0, want=("kq",))
+        out[name] = ({k: v.cpu().numpy().astype(np.float64) for k, v in g.items() if v is not None},
+                     gu["kq"].cpu().numpy().astype(np.float64))
+    a, b = out["fp32_qr"], out["fp64_qr"]
+    res["max_abs_dK_fmnist"] = float(np.abs(a[0]["kq"] - b[0]["kq"]).max())
+    res["max_abs_dlogK_fmnist"] = float(np.abs(a[0]["logkq"] - b[0]["logkq"]).max())
+    big = b[1] > 1e-3
+    res["max_abs_dK_uniform8"] = float(np.abs(a[1] - b[1]).max())
+    res["max_rel_dK_uniform8_K>1e-3"] = float((np.abs(a[1] - b[1])[big] / b[1][big]).max())
+    ctx.sync_status()
+    if own:
+        ctx.close()
     return res
 
 

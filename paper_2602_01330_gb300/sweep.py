@@ -71,7 +71,8 @@ class Autotuner:
             return 0
         sites = min(mps.n, self.probe_sites)
         xs = mps.x[:, :sites].contiguous()
-        probe = dualk.mps_build(self.ctx, xs, dualk.FeatureMap(reps=2, chi_max=mps.chi_max), dtype=mps.dtype)
+        fm = mps.fmap if mps.fmap is not None else dualk.FeatureMap(chi_max=mps.chi_max)
+        probe = dualk.mps_build(self.ctx, xs, fm, dtype=mps.dtype)
         rows = mps.m
         out = {"kq": torch.empty((rows, rows), dtype=torch.float32, device=mps.data.device)}
         times = {}

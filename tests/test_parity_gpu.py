@@ -185,6 +185,9 @@ def test_host_errors(dk):
     with pytest.raises(dualk.DualKError) as e:
         dualk.mps_build(ctx, x, dualk.FeatureMap(reps=0, chi_max=4))
     assert e.value.status == 1
+    with pytest.raises(dualk.DualKError) as e:
+        dualk.mps_build(ctx, x, dualk.FeatureMap(reps=2, chi_max=4, qr_prec=2))  # neither F32 nor F64
+    assert e.value.status == 1
     m = dualk.mps_build(ctx, x, dualk.FeatureMap(reps=2, chi_max=4))
     with pytest.raises(dualk.DualKError) as e:
         dualk.gram_tile(ctx, m, m, row0=2, nrows=3)  # runs past the 4 samples
@@ -224,21 +227,22 @@ def test_n784_bench_shape_sampled(dk):
     ctx.sync_status()
 
 
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_bond4_build_kernels_agree_small_and_large_sets(dk, dtype):
-    """The bond-4 MPS build has two launch forms chosen by the sample count: 8 threads per
-    sample for sets up to 40 samples per SM, 2 threads per sample above. 6400 samples
-    (the 2-thread form), d = 40, reps = 2: the Gram block between the first 48 and the
-    last 48 samples against the oracle, the same 96 samples built as a small set (the
-    8-thread form) giving the same block, and for both forms the fused ln-norms close to
-    the self-overlap entry point's and a unit Gram diagonal (exact in FP32)."""
+@pytest.mark.parametrize("dtype,qr", [("c64", "f32"), ("c64", "f64"), ("c128", "f64")])
+def test_bond4_build_kernels_agree_small_and_large_sets(dk, dtype, qr):
+    """The bond-4 MPS build runs its QR in FP32 (complex64, the default) or FP64 (complex64
+    on request, complex128 always). The FP64 form has two launches chosen by the sample
+    count: 8 threads per sample up to 40 samples per SM, 2 threads per sample above; the
+    FP32 form uses 8 threads at every size. 6400 samples, d = 40, reps = 2: the Gram block
+    between the first 48 and the last 48 samples against the oracle, the same 96 samples
+    built as a small set giving the same block, and for both sets the fused ln-norms close
+    to the self-overlap entry point's and a unit Gram diagonal (exact in FP32)."""
     dualk, ctx, torch = dk
     from oracle import gram as og
     from paper_2602_01330_gb300 import synthetic
     dt = dualk.DK_C64 if dtype == "c64" else dualk.DK_C128
     m, n = 6400, 40
     x = synthetic.fmnist_like(m, 0, n)["x_train"]
-    fm = dualk.FeatureMap(reps=2, chi_max=4)
+    fm = dualk.FeatureMap(reps=2, chi_max=4, qr_prec=dualk.DK_PREC_F32 if qr == "f32" else dualk.DK_PREC_F64)
     big = dualk.mps_build(ctx, _dev(torch, x), fm, dtype=dt)
     out = dualk.gram_tile(ctx, big, big, 0, 48, m - 48, 48, w=0.5)
     sel = np.r_[0:48, m - 48:m]
