@@ -189,7 +189,9 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
       break;
     }
     const uint8_t* base = smem + sidx * Cfg::STAGE_BYTES;
-#pragma unroll
+    // Not unrolled: one site's code (~1200 instructions) is reused for every site of the
+    // stage; unrolled stages of 4 or 8 sites overflow the instruction cache.
+#pragma unroll 1
     for (int u = 0; u < SPS; ++u) {
       const int k = js * SPS + u;
       if (SPS > 1 && k >= p.n) break;
@@ -343,7 +345,7 @@ using F32_P14 = GramCfg<float, 4, 8, 4, 1, 4, 4, 2, 4, 1>;     // 32 x 32 pairs,
 using F32_P22wS2 = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 3, 1, 2>;  // 48 x 32 pairs, 384 threads, 2 sites/stage
 using F32_P22S2 = GramCfg<float, 4, 4, 8, 2, 2, 4, 2, 3, 1, 2>;   // 32 x 32 pairs, 256 threads, 2 sites/stage
 using F32_P22wS4 = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 2, 1, 4>;  // 48 x 32 pairs, 384 threads, 4 sites/stage
-using F32_P22wS4b = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 3, 1, 4>; // same, 3 stages
+using F32_P22wS8 = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 2, 1, 8>;  // 48 x 32 pairs, 384 threads, 8 sites/stage
 using F64_P11 = GramCfg<double, 4, 4, 8, 1, 1, 4, 2, 4, 1>;    // 16 x 16 pairs, 256 threads
 using F32X8_P11 = GramCfg<float, 8, 4, 8, 1, 1, 4, 2, 4, 1>;   // chi = 8: 16 x 16 pairs, 256 threads
 
@@ -365,8 +367,8 @@ constexpr CfgInfo info_of() {
 static const CfgInfo kF32Chi4[] = {info_of<F32_P11>(),  info_of<F32_P21>(),  info_of<F32_P22>(), info_of<F32_P12>(),
                                    info_of<F32_P22w>(), info_of<F32_P21w>(), info_of<F32_P14>(),
                                    info_of<F32_P22wS2>(), info_of<F32_P22S2>(), info_of<F32_P22wS4>(),
-                                   info_of<F32_P22wS4b>()};
-constexpr int kF32Chi4Default = 10;  // 48 x 32 pairs, 4 sites per stage: fastest on the n = 784 Gram and rows
+                                   info_of<F32_P22wS8>()};
+constexpr int kF32Chi4Default = 11;  // 48 x 32 pairs, 8 sites per stage: fastest on the n = 784 Gram and rows
 static const CfgInfo kF64Chi4[] = {info_of<F64_P11>()};
 static const CfgInfo kF32Chi8[] = {info_of<F32X8_P11>()};
 
@@ -384,9 +386,9 @@ static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const vo
       case 8: return launch_gram<F32_P22wS2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 9: return launch_gram<F32_P22S2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 10: return launch_gram<F32_P22wS4>(ctx, mps_r, m_r, mps_c, m_c, a, st);
-      case 11: return launch_gram<F32_P22wS4b>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 11: return launch_gram<F32_P22wS8>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 3: return launch_gram<F32_P22>(ctx, mps_r, m_r, mps_c, m_c, a, st);
-      default: return launch_gram<F32_P22wS4>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      default: return launch_gram<F32_P22wS8>(ctx, mps_r, m_r, mps_c, m_c, a, st);
     }
   }
   if (dtype == DK_C128 && prec == DK_PREC_F64 && chi == 4)
