@@ -47,8 +47,8 @@ def entries_per_step(n_train, n_test):
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass) of this bench's own launch;
 # the command and figures are in profiles/gram_kernel_dram_traffic_fmnist784_gram2000.md.
 # Reported only while the kernel sources hash to the value they had when it was taken.
-GRAM_TRAFFIC = {"n_train": 2000, "bytes": 1107528192 + 18022144,
-                "sources_sha256": "038f372942dbffdfeb98dbf0406829de58163c78f7dd8efb7aca219d8fdf86af"}
+GRAM_TRAFFIC = {"n_train": 2000, "tile_shape_id": 12, "bytes": 1890982656 + 59853824,
+                "sources_sha256": "bfdcd285b808d3b359f305e8e9f01ebe6f23796c9c69a8649a5a18f503f18888"}
 GRAM_SOURCES = ["gram.cu", "gram_common.cuh", "transfer.cuh", "common.cuh"]
 
 
@@ -62,9 +62,12 @@ def gram_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def gram_traffic(n_train: int):
-    """Measured DRAM bytes per Gram launch, or None if the kernel or the workload differs."""
+def gram_traffic(n_train: int, tile_shape_id: int):
+    """Measured DRAM bytes per Gram launch, or None if the kernel, its tile shape or the
+    workload differs."""
     if GRAM_TRAFFIC["bytes"] is None or n_train != GRAM_TRAFFIC["n_train"]:
+        return None
+    if tile_shape_id != GRAM_TRAFFIC["tile_shape_id"]:
         return None
     return GRAM_TRAFFIC["bytes"] if gram_sources_sha256() == GRAM_TRAFFIC["sources_sha256"] else None
 
@@ -258,6 +261,20 @@ def run_ours(args):
     ln_te = torch.empty(n_te, dtype=torch.float32, device=dev)
     side = torch.cuda.Stream(device=dev)  # the test-set build runs beside the training-set build
 
+    # Tile shapes for the two Gram launches, picked by the library's autotuner (sweep.py) on a
+    # 48-site probe of the same sample sets, before anything is timed.
+    # --tile-shapes G,R fixes them instead (profiling runs, where the tuner's launches would
+    # shift the launch indices).
+    if args.tile_shapes:
+        cfg_gram, cfg_rows = (int(v) for v in args.tile_shapes.split(","))
+    else:
+        from paper_2602_01330_gb300.sweep import Autotuner
+        tuner = Autotuner(ctx)
+        mtr0 = dualk.mps_build(ctx, x_tr, fm, out=mps_tr, bond=bond_tr, log_norm=ln_tr)
+        mte0 = dualk.mps_build(ctx, x_te, fm, out=mps_te, bond=bond_te, log_norm=ln_te)
+        cfg_gram = tuner.best(mtr0, symmetric=True)
+        cfg_rows = tuner.best(mte0, symmetric=False, cols=mtr0)
+
     phase_events = []  # per timed step: events before build, Gram, rows, and after rows
 
     def step(record=False):
@@ -272,10 +289,12 @@ def run_ours(args):
         mte = dualk.mps_build(ctx, x_te, fm, out=mps_te, bond=bond_te, log_norm=ln_te, stream=side)
         if record:
             ev[1].record(stream)
+        ctx.set_gram_config(cfg_gram)
         dualk.gram_tile(ctx, mtr, mtr, symmetric=True, w=w, out=g_out, ld=n_tr)
         if record:
             ev[2].record(stream)
         stream.wait_stream(side)
+        ctx.set_gram_config(cfg_rows)
         dualk.dual_kernel_rows(ctx, mte, mtr, w=w, out=r_out)
         if record:
             ev[3].record(stream)
@@ -328,6 +347,7 @@ def run_ours(args):
         e2e = end_to_end(torch, tdist, args, world, stream, flush, x_tr, x_te, g_out, r_out, data, step,
                          units_step, barrier, dev)
 
+    tile_gram = dualk.gram_config_info(cfg_gram)
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -370,8 +390,10 @@ def run_ours(args):
                    "w": w, "mps_dtype": "complex64", "parallelism": f"independent problem per GPU x{world}",
                    "l2": "256 MB buffer written before every timed step (inside the timed region)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": gram_traffic(n_tr),
-                     "kernel": f"gram_kernel<float,chi=4> (symmetric {n_tr}x{n_tr} Gram)",
+                     "frac": achieved / peak_tflops, "traffic": gram_traffic(n_tr, cfg_gram),
+                     "kernel": f"gram_kernel<float,chi=4> (symmetric {n_tr}x{n_tr} Gram), "
+                               f"{tile_gram[0]}x{tile_gram[1]} tiles, {tile_gram[2]} threads",
+                     "tile_shape_ids": {"gram": cfg_gram, "rows": cfg_rows},
                      "peak_source": f"FP32 FMA peak {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
                      "avg_launch_ms": gram_avg_ms},
         "e2e": e2e,
@@ -389,6 +411,7 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--tile-shapes", default="", help="G,R: Gram and rows tile-shape ids (default: autotuned)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -241,11 +241,11 @@ __global__ void __launch_bounds__(Cfg::NTHREADS, Cfg::MINB)
         for (int pc = 0; pc < PC; ++pc)
           xc[pc] = p.x_c + size_t(min(c0 + slot_c + pc * Cfg::WTC, p.col0 + p.ncols - 1)) * p.n;
         // Features 8 at a time as float4 pairs when every row is 16-byte aligned (n a multiple
-        // of 8): the loads of a tile's epilogue then take an eighth of the L2 round trips
-        // of the scalar loop. Same additions in the same order as the scalar loop.
+        // of 8), two groups in flight: the loads of a tile's epilogue then take a sixteenth of
+        // the L2 round trips of the scalar loop. Same additions in the same order.
         const bool vec8 = (p.n & 7) == 0 && ((reinterpret_cast<uintptr_t>(p.x_r) | reinterpret_cast<uintptr_t>(p.x_c)) & 15) == 0;
         if (vec8) {
-#pragma unroll 1
+#pragma unroll 2
           for (int f = 0; f < p.n; f += 8) {
             float4 a[PR][2], b[PC][2];
 #pragma unroll
@@ -346,6 +346,9 @@ using F32_P22wS2 = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 3, 1, 2>;  // 48 x 32 pai
 using F32_P22S2 = GramCfg<float, 4, 4, 8, 2, 2, 4, 2, 3, 1, 2>;   // 32 x 32 pairs, 256 threads, 2 sites/stage
 using F32_P22wS4 = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 2, 1, 4>;  // 48 x 32 pairs, 384 threads, 4 sites/stage
 using F32_P22wS8 = GramCfg<float, 4, 4, 8, 2, 2, 6, 2, 2, 1, 8>;  // 48 x 32 pairs, 384 threads, 8 sites/stage
+using F32_P22S8 = GramCfg<float, 4, 4, 8, 2, 2, 4, 2, 2, 1, 8>;   // 32 x 32 pairs, 256 threads, 8 sites/stage
+using F32_P22hS8 = GramCfg<float, 4, 4, 8, 2, 2, 2, 2, 2, 2, 8>;  // 16 x 32 pairs, 128 threads, 2 CTAs per SM
+using F32_P22vS8 = GramCfg<float, 4, 4, 8, 2, 2, 4, 1, 2, 2, 8>;  // 32 x 16 pairs, 128 threads, 2 CTAs per SM
 using F64_P11 = GramCfg<double, 4, 4, 8, 1, 1, 4, 2, 4, 1>;    // 16 x 16 pairs, 256 threads
 using F32X8_P11 = GramCfg<float, 8, 4, 8, 1, 1, 4, 2, 4, 1>;   // chi = 8: 16 x 16 pairs, 256 threads
 
@@ -367,8 +370,9 @@ constexpr CfgInfo info_of() {
 static const CfgInfo kF32Chi4[] = {info_of<F32_P11>(),  info_of<F32_P21>(),  info_of<F32_P22>(), info_of<F32_P12>(),
                                    info_of<F32_P22w>(), info_of<F32_P21w>(), info_of<F32_P14>(),
                                    info_of<F32_P22wS2>(), info_of<F32_P22S2>(), info_of<F32_P22wS4>(),
-                                   info_of<F32_P22wS8>()};
-constexpr int kF32Chi4Default = 11;  // 48 x 32 pairs, 8 sites per stage: fastest on the n = 784 Gram and rows
+                                   info_of<F32_P22wS8>(), info_of<F32_P22S8>(),
+                                   info_of<F32_P22hS8>(), info_of<F32_P22vS8>()};
+constexpr int kF32Chi4Default = 12;  // 32 x 32 pairs, 8 sites per stage: fastest on the n = 784 Gram and rows
 static const CfgInfo kF64Chi4[] = {info_of<F64_P11>()};
 static const CfgInfo kF32Chi8[] = {info_of<F32X8_P11>()};
 
@@ -387,8 +391,11 @@ static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const vo
       case 9: return launch_gram<F32_P22S2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 10: return launch_gram<F32_P22wS4>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 11: return launch_gram<F32_P22wS8>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 12: return launch_gram<F32_P22S8>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 13: return launch_gram<F32_P22hS8>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 14: return launch_gram<F32_P22vS8>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 3: return launch_gram<F32_P22>(ctx, mps_r, m_r, mps_c, m_c, a, st);
-      default: return launch_gram<F32_P22wS8>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      default: return launch_gram<F32_P22S8>(ctx, mps_r, m_r, mps_c, m_c, a, st);
     }
   }
   if (dtype == DK_C128 && prec == DK_PREC_F64 && chi == 4)

@@ -58,28 +58,33 @@ class Autotuner:
                 self.cache = {k: int(v) for k, v in json.load(f).items()}
 
     @staticmethod
-    def key(mps: dualk.MPS, symmetric: bool, m_cols: int | None = None) -> str:
-        return f"dtype{mps.dtype}-chi{mps.chi_max}-n{mps.n}-m{mps.m}-c{m_cols or mps.m}-sym{int(symmetric)}"
+    def key(mps: dualk.MPS, symmetric: bool, cols: dualk.MPS | None = None) -> str:
+        m_cols = mps.m if cols is None else cols.m
+        return f"dtype{mps.dtype}-chi{mps.chi_max}-n{mps.n}-m{mps.m}-c{m_cols}-sym{int(symmetric)}"
 
-    def best(self, mps: dualk.MPS, symmetric: bool = True) -> int:
-        k = self.key(mps, symmetric)
+    def _probe(self, mps: dualk.MPS) -> dualk.MPS:
+        sites = min(mps.n, self.probe_sites)
+        fm = mps.fmap if mps.fmap is not None else dualk.FeatureMap(chi_max=mps.chi_max)
+        return dualk.mps_build(self.ctx, mps.x[:, :sites].contiguous(), fm, dtype=mps.dtype)
+
+    def best(self, mps: dualk.MPS, symmetric: bool = True, cols: dualk.MPS | None = None) -> int:
+        """Fastest tile shape for the Gram of `mps` (symmetric) or its block against `cols`."""
+        k = self.key(mps, symmetric, cols)
         if k in self.cache:
             return self.cache[k]
         count = dualk.gram_config_count(mps.dtype, mps.chi_max)
         if count <= 1:
             self.cache[k] = 0
             return 0
-        sites = min(mps.n, self.probe_sites)
-        xs = mps.x[:, :sites].contiguous()
-        fm = mps.fmap if mps.fmap is not None else dualk.FeatureMap(chi_max=mps.chi_max)
-        probe = dualk.mps_build(self.ctx, xs, fm, dtype=mps.dtype)
-        rows = mps.m
-        out = {"kq": torch.empty((rows, rows), dtype=torch.float32, device=mps.data.device)}
+        prow = self._probe(mps)
+        pcol = prow if cols is None else self._probe(cols)
+        rows, ncols = prow.m, pcol.m
+        out = {"kq": torch.empty((rows, ncols), dtype=torch.float32, device=mps.data.device)}
         times = {}
         for cid in range(1, count + 1):
             self.ctx.set_gram_config(cid)
-            times[cid] = _time_ms(lambda: dualk.gram_tile(self.ctx, probe, probe, 0, rows, 0, rows, w=1.0, out=out,
-                                                          ld=rows, symmetric=symmetric), self.reps)
+            times[cid] = _time_ms(lambda: dualk.gram_tile(self.ctx, prow, pcol, 0, rows, 0, ncols, w=1.0, out=out,
+                                                          ld=ncols, symmetric=symmetric), self.reps)
         self.ctx.set_gram_config(0)
         choice = min(times, key=times.get)
         self.cache[k] = choice
