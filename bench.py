@@ -47,8 +47,8 @@ def entries_per_step(n_train, n_test):
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass) of this bench's own launch;
 # the command and figures are in profiles/gram_kernel_dram_traffic_fmnist784_gram2000.md.
 # Reported only while the kernel sources hash to the value they had when it was taken.
-GRAM_TRAFFIC = {"n_train": 2000, "tile_shape_id": 12, "bytes": 1890982656 + 59853824,
-                "sources_sha256": "bfdcd285b808d3b359f305e8e9f01ebe6f23796c9c69a8649a5a18f503f18888"}
+GRAM_TRAFFIC = {"n_train": 2000, "sources_sha256": "89b2a9d438938a07a0b8b2a80f9dd52dd0da9b4fa1356eedde09a0cb49af4480",
+                "bytes_by_tile_shape": {14: 1878100480 + 60251648, 15: 1949647616 + 60267520}}
 GRAM_SOURCES = ["gram.cu", "gram_common.cuh", "transfer.cuh", "common.cuh"]
 
 
@@ -65,11 +65,11 @@ def gram_sources_sha256() -> str:
 def gram_traffic(n_train: int, tile_shape_id: int):
     """Measured DRAM bytes per Gram launch, or None if the kernel, its tile shape or the
     workload differs."""
-    if GRAM_TRAFFIC["bytes"] is None or n_train != GRAM_TRAFFIC["n_train"]:
+    if n_train != GRAM_TRAFFIC["n_train"] or tile_shape_id not in GRAM_TRAFFIC["bytes_by_tile_shape"]:
         return None
-    if tile_shape_id != GRAM_TRAFFIC["tile_shape_id"]:
+    if gram_sources_sha256() != GRAM_TRAFFIC["sources_sha256"]:
         return None
-    return GRAM_TRAFFIC["bytes"] if gram_sources_sha256() == GRAM_TRAFFIC["sources_sha256"] else None
+    return GRAM_TRAFFIC["bytes_by_tile_shape"][tile_shape_id]
 
 
 def measured_peaks():
