@@ -14,7 +14,10 @@ What it computes, in plain NumPy float64 / complex128 and in the paper's order:
   two-site SVD splits (time-evolving block decimation), for any n;
 * ``gram``     -- the quantum kernel K_q = |<psi(x_i)|psi(x_j)>|^2 (§II-C, Eqs. 7-10)
   from the MPS by a left-to-right transfer contraction with power-of-two rescaling,
-  the RBF kernel (§II-B, Eq. 3) and the linear mix (§II-D, Eq. 11).
+  the RBF kernel (§II-B, Eq. 3) and the linear mix (§II-D, Eq. 11);
+* ``svm``      -- the SVM that consumes the kernel matrices: the dual problem of §II-B
+  (Eqs. 1-2) by sequential minimal optimisation, the decision function (Eq. 5) and
+  one-against-one voting.
 
 Feature map. The paper's circuit figure (Fig. 1(B)) is not part of its text; §II-C
 only says that Hadamards and data-dependent rotations alternate with local
