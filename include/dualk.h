@@ -38,8 +38,9 @@
  *   host before anything is launched (DK_ERR_ARG, DK_ERR_UNSUPPORTED). A failing
  *   CUDA launch returns DK_ERR_CUDA. A device-side wait that exceeds its bound
  *   (about two seconds) makes the kernel record DK_ERR_TIMEOUT in the context's
- *   status word and return without finishing; dk_sync_status reads it. No call
- *   aborts, asserts or traps.
+ *   status word and return without finishing; an index out of range in a device-side
+ *   list (SVM calls) is skipped and recorded the same way; dk_sync_status reads it. No
+ *   call aborts, asserts or traps.
  */
 #ifndef DUALK_H
 #define DUALK_H
@@ -99,7 +100,8 @@ void dk_destroy(dk_ctx* ctx);
 const char* dk_error_string(dk_status status);
 
 /* Wait for `stream`, then return and clear the device status word (DK_OK if no
- * kernel recorded an error since the last call). */
+ * kernel recorded an error since the last call): DK_ERR_TIMEOUT for an expired bounded
+ * wait, else DK_ERR_ARG for an out-of-range index found in a device array (SVM calls). */
 dk_status dk_sync_status(dk_ctx* ctx, void* stream);
 
 /* Failure-detection self test: launches a kernel whose wait can never be satisfied (an
@@ -200,6 +202,71 @@ int dk_gram_config_count(dk_dtype dtype, int chi_max);
 dk_status dk_gram_config_info(dk_dtype dtype, int chi_max, int id, int* tile_rows, int* tile_cols,
                               int* threads);
 dk_status dk_set_gram_config(dk_ctx* ctx, int id);
+
+/* Largest training list (m_max) of the SVM calls below. */
+#define DK_SVM_MAX_SAMPLES 4096
+
+/* One-against-one SVM training on precomputed kernel values (§II-B, Eqs. 1-2: the dual
+ * problem min 1/2 sum a_i a_j y_i y_j K_ij - sum a_i, sum a_i y_i = 0, 0 <= a_i <= C;
+ * §II-D, Eq. 11: the mixed kernel), for n_jobs independent jobs in one launch, e.g. the
+ * folds x C x w grid of a cross-validation.
+ *   kq, kc     n x n kernel matrices over the samples (device, float32, row stride ld >= n);
+ *              the job uses K(r, c) = w[job] kq[r*ld + c] + (1 - w[job]) kc[r*ld + c]. Either
+ *              may be NULL (its term is dropped). Only entries between samples of a job are
+ *              read.
+ *   w, C       n_jobs floats each (device): mixing weight and box bound per job
+ *   idx        n_jobs x m_max int32 (device): job j trains on the samples idx[j*m_max + k],
+ *              k < count[j] (indices 0..n-1 into the kernel matrix), in this order; an index
+ *              outside 0..n-1 is skipped and makes the next dk_sync_status return DK_ERR_ARG
+ *   count      n_jobs int32 (device), each in 0..m_max (larger values act as m_max)
+ *   labels     class of every sample, indexed like the kernel matrix (device int32,
+ *              0..n_class-1)
+ *   tol        stop when the largest KKT violation (max over the upper set minus min over the
+ *              lower set of -y_t grad_t) is below tol
+ *   max_iter   steps per binary problem at most
+ * For class pair p = (c1, c2), c1 < c2, numbered (0,1), (0,2), ..., (1,2), ..., one binary
+ * problem on the job's samples of those two classes with y = +1 for c1, solved by
+ * sequential minimal optimisation with second-order working-set selection.
+ *   coef       n_jobs x P x m_max floats, P = n_class (n_class - 1) / 2 (device, written):
+ *              a_k y_k of the sample at position k of the job's list; 0 for samples outside
+ *              the pair and for k >= count[j]
+ *   bias       n_jobs x P floats (device, written): b of the decision function (Eq. 5)
+ *   iters      n_jobs x P int32 (device, written, may be NULL): steps taken, -1 if max_iter
+ *              was reached before tol; 0 when a class of the pair is absent from the job
+ *              (coef and bias are then 0)
+ * Errors: DK_ERR_ARG (NULL ctx / w / C / idx / count / labels / coef / bias, both kq and kc
+ *         NULL, n_jobs outside 1..65535, m_max < 2, n < 1, ld < n, tol <= 0, max_iter < 1),
+ *         DK_ERR_UNSUPPORTED (n_class outside 2..32, m_max > DK_SVM_MAX_SAMPLES). */
+dk_status dk_svm_ovo_train(dk_ctx* ctx, const float* kq, const float* kc, long long ld, int n, int n_jobs,
+                           const float* w, const float* C, const int32_t* idx, const int32_t* count,
+                           int m_max, const int32_t* labels, int n_class, float tol, int max_iter,
+                           float* coef, float* bias, int32_t* iters, void* stream);
+
+/* Decision values and one-against-one votes (§II-B, Eqs. 4-5) for rows of a kernel matrix,
+ * per job of dk_svm_ovo_train.
+ *   kq, kc, ld, w  as for dk_svm_ovo_train, but n_rows x n_cols (n_cols <= ld): K(r, c) is
+ *              read at row r of the classified samples and column c of the training samples
+ *              (for test samples: the output of dk_dual_kernel_rows)
+ *   rows       n_jobs x r_max int32 (device) row indices 0..n_rows-1 of the samples to
+ *              classify, or NULL for rows 0..r_max-1; row_count n_jobs int32 (device) or NULL
+ *              for r_max. A row index out of range is not classified and makes the next
+ *              dk_sync_status return DK_ERR_ARG, as does a training index outside 0..n_cols-1
+ *              (that sample then contributes nothing).
+ *   idx, count the training lists of the jobs (device), or NULL for columns 0..m_max-1
+ *   coef, bias the outputs of dk_svm_ovo_train for the same jobs and m_max
+ *   decision   n_jobs x r_max x P floats (device, written, may be NULL): f_p(x) of Eq. 5
+ *   pred       n_jobs x r_max int32 (device, written, may be NULL): the class with the most
+ *              votes (pair (c1, c2) votes c1 if f > 0, else c2), the smallest index on ties
+ * Entries of rows past row_count[j] are not written.
+ * Errors: DK_ERR_ARG (NULL ctx / w / coef / bias, both kq and kc NULL, both decision and
+ *         pred NULL, n_jobs outside 1..65535, r_max < 1, m_max < 1, n_rows < 1, n_cols < 1,
+ *         ld < n_cols, rows NULL with r_max > n_rows, idx NULL with m_max > n_cols),
+ *         DK_ERR_UNSUPPORTED (n_class outside 2..32, m_max > DK_SVM_MAX_SAMPLES). */
+dk_status dk_svm_ovo_predict(dk_ctx* ctx, const float* kq, const float* kc, long long ld, int n_rows,
+                             int n_cols, int n_jobs, const float* w, const int32_t* rows,
+                             const int32_t* row_count, int r_max, const int32_t* idx, const int32_t* count,
+                             int m_max, const float* coef, const float* bias, int n_class, float* decision,
+                             int32_t* pred, void* stream);
 
 #ifdef __cplusplus
 }

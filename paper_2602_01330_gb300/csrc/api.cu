@@ -78,6 +78,7 @@ DK_API dk_status dk_sync_status(dk_ctx* ctx, void* stream) {
     if (cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess) return DK_ERR_CUDA;
   }
   if (host & dk::DEV_TIMEOUT) return DK_ERR_TIMEOUT;
+  if (host & dk::DEV_BAD_INDEX) return DK_ERR_ARG;
   return DK_OK;
 }
 

@@ -10,7 +10,7 @@
 namespace dk {
 
 // Bits of the device status word (ctx-owned, 4 bytes).
-enum : unsigned { DEV_TIMEOUT = 1u };
+enum : unsigned { DEV_TIMEOUT = 1u, DEV_BAD_INDEX = 2u };
 
 // Upper bound of every device-side wait, in globaltimer nanoseconds.
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;

@@ -25,7 +25,9 @@ _STATUS_NAMES = {0: "DK_OK", 1: "DK_ERR_ARG", 2: "DK_ERR_UNSUPPORTED", 3: "DK_ER
 
 EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_mps_bytes",
             "dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows", "dk_gram_config_count",
-            "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout", "dk_self_overlap")
+            "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout", "dk_self_overlap",
+            "dk_svm_ovo_train", "dk_svm_ovo_predict")
+SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 
 
 class DualKError(RuntimeError):
@@ -79,6 +81,12 @@ def _lib():
     lib.dk_self_overlap.restype = i32
     lib.dk_selftest_wait_timeout.argtypes = [vp, ctypes.c_ulonglong, vp]
     lib.dk_selftest_wait_timeout.restype = i32
+    lib.dk_svm_ovo_train.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, i32, vp, i32, f32, i32, vp, vp, vp,
+                                     vp]
+    lib.dk_svm_ovo_train.restype = i32
+    lib.dk_svm_ovo_predict.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp, vp, vp, i32, vp, vp, i32, vp, vp, i32, vp,
+                                       vp, vp]
+    lib.dk_svm_ovo_predict.restype = i32
     _LIB = lib
     return lib
 
@@ -297,3 +305,64 @@ def dual_kernel_rows(ctx: Context, test: MPS, train: MPS, gamma: float | None = 
                                       _ptr(out.get("logkq")), _stream(stream)),
            "dk_dual_kernel_rows")
     return out
+
+
+def svm_ovo_train(ctx: Context, kq: torch.Tensor | None, kc: torch.Tensor | None, w: torch.Tensor,
+                  C: torch.Tensor, idx: torch.Tensor, count: torch.Tensor, labels: torch.Tensor, n_class: int,
+                  tol: float = 1e-3, max_iter: int = 1_000_000, out=None, stream=None):
+    """dk_svm_ovo_train: one-against-one SVMs for n_jobs jobs (see include/dualk.h).
+
+    kq / kc: kernel matrices (float32, row-major, same leading dimension); w, C: (n_jobs,)
+    float32; idx: (n_jobs, m_max) int32; count: (n_jobs,) int32; labels: int32 per kernel row.
+    Returns a dict with coef (n_jobs, P, m_max), bias (n_jobs, P) and iters (n_jobs, P)."""
+    ref = kq if kq is not None else kc
+    for t, name, dt in ((kq, "kq", torch.float32), (kc, "kc", torch.float32), (w, "w", torch.float32),
+                        (C, "C", torch.float32), (idx, "idx", torch.int32), (count, "count", torch.int32),
+                        (labels, "labels", torch.int32)):
+        _need_cuda(t, name, dt)
+    if kq is not None and kc is not None and kq.shape != kc.shape:
+        raise ValueError("kq and kc differ in shape")
+    n_jobs, m_max = idx.shape
+    P = n_class * (n_class - 1) // 2
+    if out is None:
+        out = {"coef": torch.empty((n_jobs, P, m_max), dtype=torch.float32, device=ref.device),
+               "bias": torch.empty((n_jobs, P), dtype=torch.float32, device=ref.device),
+               "iters": torch.empty((n_jobs, P), dtype=torch.int32, device=ref.device)}
+    if ref.dim() != 2 or ref.shape[0] != ref.shape[1]:
+        raise ValueError("the training kernel must be a square matrix")
+    _check(_lib().dk_svm_ovo_train(ctx.handle, _ptr(kq), _ptr(kc), int(ref.stride(0)), int(ref.shape[0]), n_jobs,
+                                   _ptr(w), _ptr(C),
+                                   _ptr(idx), _ptr(count), m_max, _ptr(labels), int(n_class), float(tol),
+                                   int(max_iter), _ptr(out["coef"]), _ptr(out["bias"]), _ptr(out.get("iters")),
+                                   _stream(stream)), "dk_svm_ovo_train")
+    return out
+
+
+def svm_ovo_predict(ctx: Context, kq: torch.Tensor | None, kc: torch.Tensor | None, w: torch.Tensor,
+                    model: dict, n_class: int, rows: torch.Tensor | None = None,
+                    row_count: torch.Tensor | None = None, r_max: int | None = None,
+                    idx: torch.Tensor | None = None, count: torch.Tensor | None = None,
+                    want_decision: bool = True, stream=None):
+    """dk_svm_ovo_predict: decision values (n_jobs, r_max, P) and votes (n_jobs, r_max).
+
+    rows (n_jobs, r_max) int32 or None (rows 0..r_max-1 of kq / kc); idx / count: the jobs'
+    training lists as given to svm_ovo_train, or None for columns 0..m_max-1."""
+    ref = kq if kq is not None else kc
+    for t, name, dt in ((kq, "kq", torch.float32), (kc, "kc", torch.float32), (w, "w", torch.float32),
+                        (rows, "rows", torch.int32), (row_count, "row_count", torch.int32),
+                        (idx, "idx", torch.int32), (count, "count", torch.int32)):
+        _need_cuda(t, name, dt)
+    coef, bias = model["coef"], model["bias"]
+    n_jobs, P, m_max = coef.shape
+    if r_max is None:
+        r_max = rows.shape[1] if rows is not None else ref.shape[0]
+    dec = torch.empty((n_jobs, r_max, P), dtype=torch.float32, device=ref.device) if want_decision else None
+    pred = torch.full((n_jobs, r_max), -1, dtype=torch.int32, device=ref.device)
+    if kq is not None and kc is not None and kq.shape != kc.shape:
+        raise ValueError("kq and kc differ in shape")
+    _check(_lib().dk_svm_ovo_predict(ctx.handle, _ptr(kq), _ptr(kc), int(ref.stride(0)), int(ref.shape[0]),
+                                     int(ref.shape[1]), n_jobs, _ptr(w),
+                                     _ptr(rows), _ptr(row_count), int(r_max), _ptr(idx), _ptr(count), m_max,
+                                     _ptr(coef), _ptr(bias), int(n_class), _ptr(dec), _ptr(pred), _stream(stream)),
+           "dk_svm_ovo_predict")
+    return {"decision": dec, "pred": pred}
