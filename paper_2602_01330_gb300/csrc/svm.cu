@@ -10,9 +10,9 @@
 // Lin (JMLR 6, 2005): per step a block-wide argmax picks i, the kernel row of i is gathered
 // from the Gram in global memory (L2-resident), a block-wide argmin of the guaranteed
 // decrease picks j, one thread solves the two-variable problem, and the gradient is updated
-// with rows i and j. Multipliers and gradient are FP64 in shared memory (the kernel values
-// are the FP32 Gram outputs); nothing else is written until the end, so no global scratch is
-// used. The loop ends when the largest KKT violation is below tol, or after max_iter steps.
+// with rows i and j. Multipliers and gradient are FP64 in shared memory, the working-set
+// choice compares FP32 copies (the kernel values are the FP32 Gram outputs); nothing else is
+// written until the end, so no global scratch is used. The loop ends when the largest KKT violation is below tol, or after max_iter steps.
 //
 // Prediction: one CTA per (job, row): the row's kernel values against the job's training
 // samples are staged in shared memory, each class pair's decision value is one warp-wide dot
@@ -110,24 +110,93 @@ struct TrainArgs {
   int32_t* iters;
 };
 
-// Shared memory (dynamic): alpha, grad (double, m_max each), kd, krow_i, krow_j (float),
-// gi (kernel index), pos (position in the job's list), y (int8) of the pair's samples.
+struct ArgF {
+  float v;
+  int i;
+};
+
+__device__ __forceinline__ bool better_f(const ArgF& x, const ArgF& y, bool want_max) {
+  if (x.i < 0) return false;
+  if (y.i < 0) return true;
+  if (x.v != y.v) return want_max ? x.v > y.v : x.v < y.v;
+  return x.i < y.i;
+}
+
+__device__ __forceinline__ void warp_arg_f(ArgF& x, bool want_max) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ArgF b{__shfl_xor_sync(0xffffffffu, x.v, o), __shfl_xor_sync(0xffffffffu, x.i, o)};
+    if (better_f(b, x, want_max)) x = b;
+  }
+}
+
+// block-wide (argmax of x, argmin of y) in one pass; ties to the smaller index, i = -1 if empty
+__device__ void block_argmax_argmin(ArgF& x, ArgF& y, ArgF* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_arg_f(x, true);
+  warp_arg_f(y, false);
+  __syncthreads();
+  if (lane == 0) {
+    red[warp] = x;
+    red[NW + warp] = y;
+  }
+  __syncthreads();
+  x = red[0];
+  y = red[NW];
+  for (int w2 = 1; w2 < NW; ++w2) {
+    if (better_f(red[w2], x, true)) x = red[w2];
+    if (better_f(red[NW + w2], y, false)) y = red[NW + w2];
+  }
+}
+
+__device__ ArgF block_argmin(ArgF x, ArgF* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_arg_f(x, false);
+  __syncthreads();
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  ArgF r = red[0];
+  for (int w2 = 1; w2 < NW; ++w2)
+    if (better_f(red[w2], r, false)) r = red[w2];
+  return r;
+}
+
+constexpr unsigned char IN_UP = 1, IN_LOW = 2;
+
+// membership of one multiplier in the upper / lower index sets
+__device__ __forceinline__ unsigned char set_flags(double alpha, double C, int y) {
+  unsigned char f = 0;
+  if ((y > 0 && alpha < C) || (y < 0 && alpha > 0.0)) f |= IN_UP;
+  if ((y > 0 && alpha > 0.0) || (y < 0 && alpha < C)) f |= IN_LOW;
+  return f;
+}
+
+// Shared memory (dynamic), per sample of the pair: alpha, grad (FP64), v = -y grad (FP32
+// copy for the working-set choice), kd, krow_i, krow_j (FP32 kernel values), gi (kernel
+// index), pos (position in the job's list), y (int8) and the set flags (uint8).
+// Arithmetic: the gradient and the multipliers are FP64; the choice of the working pair
+// compares FP32 copies (FP64 issues at a small fraction of the FP32 rate on GB300, and the
+// choice is a heuristic: any violating pair makes progress); the stopping test re-reads the
+// two chosen gradients in FP64.
 __global__ void __launch_bounds__(NT) ovo_train_kernel(const TrainArgs a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int p = blockIdx.x, job = blockIdx.y;
   const int mm = a.m_max;
   double* alpha = reinterpret_cast<double*>(sm_raw);
   double* grad = alpha + mm;
-  float* kd = reinterpret_cast<float*>(grad + mm);
+  float* vf = reinterpret_cast<float*>(grad + mm);
+  float* kd = vf + mm;
   float* ki = kd + mm;
   float* kj = ki + mm;
   int* gi = reinterpret_cast<int*>(kj + mm);
   int* pos = gi + mm;
   signed char* ys = reinterpret_cast<signed char*>(pos + mm);
+  unsigned char* fl = reinterpret_cast<unsigned char*>(ys + mm);
+  __shared__ ArgF red_f[2 * NW];
   __shared__ ArgBest red_a[NW];
   __shared__ double red_d[NW];
   __shared__ int s_np, s_n1, s_warp_base[NW + 1];
-  __shared__ double s_da_i, s_da_j;
+  __shared__ double s_ci, s_cj;
 
   int c1, c2;
   pair_of(p, a.n_class, c1, c2);
@@ -186,6 +255,8 @@ __global__ void __launch_bounds__(NT) ovo_train_kernel(const TrainArgs a) {
   for (int t = tid; t < np; t += NT) {
     alpha[t] = 0.0;
     grad[t] = -1.0;
+    vf[t] = float(ys[t]);  // -y (-1)
+    fl[t] = set_flags(0.0, C, ys[t]);
     kd[t] = kval(a.kq, a.kc, a.ld, w, gi[t], gi[t]);
   }
   __syncthreads();
@@ -194,41 +265,41 @@ __global__ void __launch_bounds__(NT) ovo_train_kernel(const TrainArgs a) {
   int it = 0;
   bool converged = false;
   for (; it < a.max_iter; ++it) {
-    ArgBest up{0.0, -1}, low{0.0, -1};
+    ArgF up{0.0f, -1}, low{0.0f, -1};
     for (int t = tid; t < np; t += NT) {
-      const double yt = ys[t];
-      const double v = -yt * grad[t];
-      const bool in_up = (yt > 0 && alpha[t] < C) || (yt < 0 && alpha[t] > 0.0);
-      const bool in_low = (yt > 0 && alpha[t] > 0.0) || (yt < 0 && alpha[t] < C);
-      if (in_up && (up.i < 0 || v > up.v)) up = ArgBest{v, t};
-      if (in_low && (low.i < 0 || v < low.v)) low = ArgBest{v, t};
+      const float v = vf[t];
+      const unsigned char f = fl[t];
+      if ((f & IN_UP) && (up.i < 0 || v > up.v)) up = ArgF{v, t};
+      if ((f & IN_LOW) && (low.i < 0 || v < low.v)) low = ArgF{v, t};
     }
-    const ArgBest bi = block_arg(up, true, red_a);
-    const ArgBest bl = block_arg(low, false, red_a);
-    if (bi.i < 0 || bl.i < 0 || bi.v - bl.v < a.tol) {
+    block_argmax_argmin(up, low, red_f);
+    if (up.i < 0 || low.i < 0) {
       converged = true;
       break;
     }
-    const int i = bi.i;
-    const double vmax = bi.v;
+    const int i = up.i;
+    const double vmax = -double(ys[i]) * grad[i];
+    if (vmax - (-double(ys[low.i]) * grad[low.i]) < a.tol) {
+      converged = true;
+      break;
+    }
     // kernel row of i over the pair's samples
     for (int t = tid; t < np; t += NT) ki[t] = kval(a.kq, a.kc, a.ld, w, gi[i], gi[t]);
     __syncthreads();
     // j: the lower-set index with the largest guaranteed decrease (vmax - v_t)^2 / curvature
-    ArgBest jb{0.0, -1};
+    const float vmax_f = up.v, kdi = kd[i];
+    ArgF jb{0.0f, -1};
     for (int t = tid; t < np; t += NT) {
-      const double yt = ys[t];
-      const double v = -yt * grad[t];
-      const bool in_low = (yt > 0 && alpha[t] > 0.0) || (yt < 0 && alpha[t] < C);
-      if (in_low && v < vmax) {
-        const double gap = vmax - v;
-        double curv = double(kd[i]) + double(kd[t]) - 2.0 * double(ki[t]);
-        if (!(curv > 0.0)) curv = 1e-12;
-        const double obj = -(gap * gap) / curv;
-        if (jb.i < 0 || obj < jb.v) jb = ArgBest{obj, t};
+      const float v = vf[t];
+      if ((fl[t] & IN_LOW) && v < vmax_f) {
+        const float gap = vmax_f - v;
+        float curv = kdi + kd[t] - 2.0f * ki[t];
+        if (!(curv > 0.0f)) curv = 1e-12f;
+        const float obj = -(gap * gap) / curv;
+        if (jb.i < 0 || obj < jb.v) jb = ArgF{obj, t};
       }
     }
-    const ArgBest bj = block_arg(jb, false, red_a);
+    const ArgF bj = block_argmin(jb, red_f);
     if (bj.i < 0) {
       converged = true;
       break;
@@ -260,15 +331,23 @@ __global__ void __launch_bounds__(NT) ovo_train_kernel(const TrainArgs a) {
         hi = fmin(hi, aj);
       }
       step = fmin(fmax(step, lo), hi);
-      s_da_i = yi * step;
-      s_da_j = -yj * step;
-      alpha[i] = ai + s_da_i;
-      alpha[j] = aj + s_da_j;
+      const double da_i = yi * step, da_j = -yj * step;
+      alpha[i] = ai + da_i;
+      alpha[j] = aj + da_j;
+      fl[i] = set_flags(alpha[i], C, ys[i]);
+      fl[j] = set_flags(alpha[j], C, ys[j]);
+      s_ci = yi * da_i;
+      s_cj = yj * da_j;
     }
     for (int t = tid; t < np; t += NT) kj[t] = kval(a.kq, a.kc, a.ld, w, gi[j], gi[t]);
     __syncthreads();
-    const double ci = double(ys[i]) * s_da_i, cj = double(ys[j]) * s_da_j;
-    for (int t = tid; t < np; t += NT) grad[t] += double(ys[t]) * (ci * double(ki[t]) + cj * double(kj[t]));
+    const double ci = s_ci, cj = s_cj;
+    for (int t = tid; t < np; t += NT) {
+      const double yt = ys[t];
+      const double g = grad[t] + yt * (ci * double(ki[t]) + cj * double(kj[t]));
+      grad[t] = g;
+      vf[t] = float(-yt * g);
+    }
     __syncthreads();
   }
 
@@ -381,7 +460,7 @@ __global__ void __launch_bounds__(NT) ovo_predict_kernel(const PredictArgs a) {
 }
 
 size_t train_smem(int m_max) {
-  return size_t(m_max) * (2 * sizeof(double) + 3 * sizeof(float) + 2 * sizeof(int) + 1) + 16;
+  return size_t(m_max) * (2 * sizeof(double) + 4 * sizeof(float) + 2 * sizeof(int) + 2) + 16;
 }
 
 }  // namespace svm
