@@ -203,6 +203,21 @@ dk_status dk_gram_config_info(dk_dtype dtype, int chi_max, int id, int* tile_row
                               int* threads);
 dk_status dk_set_gram_config(dk_ctx* ctx, int id);
 
+/* Concentration diagnostics of a kernel block (§I: exponential concentration of quantum
+ * kernels; the conclusion's kernel diagnostics): over the entries of an nrows x ncols block
+ * (symmetric = 1: the strict upper triangle of a square Gram, each pair of distinct samples
+ * once), in FP64:
+ *   out[0] = entries of kq counted, out[1] = sum K_q, out[2] = sum K_q^2,
+ *   out[3] = entries of logkq with a finite value, out[4] = sum log K_q, out[5] = sum (log K_q)^2
+ * (mean and variance follow; log K_q stays informative where K_q underflows to 0).
+ *   kq, logkq  float32 blocks with row stride ld >= ncols (device); either may be NULL (its
+ *              three sums stay 0)
+ *   out        6 doubles (device, written; cleared by the call first)
+ * Errors: DK_ERR_ARG (NULL ctx / out, both kq and logkq NULL, nrows or ncols < 1, ld < ncols,
+ *         symmetric with nrows != ncols), DK_ERR_CUDA. */
+dk_status dk_gram_stats(dk_ctx* ctx, const float* kq, const float* logkq, long long ld, int nrows, int ncols,
+                        int symmetric, double* out, void* stream);
+
 /* Largest training list (m_max) of the SVM calls below. */
 #define DK_SVM_MAX_SAMPLES 4096
 

@@ -26,7 +26,7 @@ _STATUS_NAMES = {0: "DK_OK", 1: "DK_ERR_ARG", 2: "DK_ERR_UNSUPPORTED", 3: "DK_ER
 EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_mps_bytes",
             "dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows", "dk_gram_config_count",
             "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout", "dk_self_overlap",
-            "dk_svm_ovo_train", "dk_svm_ovo_predict")
+            "dk_svm_ovo_train", "dk_svm_ovo_predict", "dk_gram_stats")
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 
 
@@ -81,6 +81,8 @@ def _lib():
     lib.dk_self_overlap.restype = i32
     lib.dk_selftest_wait_timeout.argtypes = [vp, ctypes.c_ulonglong, vp]
     lib.dk_selftest_wait_timeout.restype = i32
+    lib.dk_gram_stats.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp, vp]
+    lib.dk_gram_stats.restype = i32
     lib.dk_svm_ovo_train.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, i32, vp, i32, f32, i32, vp, vp, vp,
                                      vp]
     lib.dk_svm_ovo_train.restype = i32
@@ -366,3 +368,25 @@ def svm_ovo_predict(ctx: Context, kq: torch.Tensor | None, kc: torch.Tensor | No
                                      _ptr(coef), _ptr(bias), int(n_class), _ptr(dec), _ptr(pred), _stream(stream)),
            "dk_svm_ovo_predict")
     return {"decision": dec, "pred": pred}
+
+
+def gram_stats(ctx: Context, kq: torch.Tensor | None, logkq: torch.Tensor | None = None,
+               symmetric: bool = True, stream=None) -> dict:
+    """dk_gram_stats: mean and variance of the off-diagonal K_q and log K_q of a Gram block
+    (the strict upper triangle when symmetric). Reads back six numbers."""
+    ref = kq if kq is not None else logkq
+    _need_cuda(kq, "kq", torch.float32)
+    _need_cuda(logkq, "logkq", torch.float32)
+    out = torch.empty(6, dtype=torch.float64, device=ref.device)
+    _check(_lib().dk_gram_stats(ctx.handle, _ptr(kq), _ptr(logkq), int(ref.stride(0)), int(ref.shape[0]),
+                                int(ref.shape[1]), 1 if symmetric else 0, _ptr(out), _stream(stream)),
+           "dk_gram_stats")
+    c, s1, s2, cl, l1, l2 = out.cpu().tolist()
+    res = {"pairs": int(c), "finite_log_pairs": int(cl)}
+    if c > 0:
+        res["kq_mean"] = s1 / c
+        res["kq_var"] = max(s2 / c - (s1 / c) ** 2, 0.0)
+    if cl > 0:
+        res["logkq_mean"] = l1 / cl
+        res["logkq_var"] = max(l2 / cl - (l1 / cl) ** 2, 0.0)
+    return res

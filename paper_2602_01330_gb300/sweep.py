@@ -167,6 +167,15 @@ class GramSweep:
             self.capture()
         self.graph.replay()
 
+    def concentration(self) -> dict:
+        """Per qubit count: mean and variance of the off-diagonal K_q and log K_q of the last
+        pass (dk_gram_stats), the concentration of the quantum kernel as n grows."""
+        res = {}
+        for mt in self.mats:
+            if "kq" in mt.out and "logkq" in mt.out:
+                res[mt.d] = dualk.gram_stats(self.ctx, mt.out["kq"], mt.out["logkq"], symmetric=True)
+        return res
+
     def entries_qubits(self) -> int:
         return sum(mt.x.shape[0] * (mt.x.shape[0] + 1) // 2 * mt.d for mt in self.mats)
 
@@ -199,6 +208,8 @@ def main():
         "eager_ms": eager, "graph_ms": graph,
         "eager_entry_qubits_per_s": units / (eager / 1e3), "graph_entry_qubits_per_s": units / (graph / 1e3),
         "tile_shapes": {mt.d: (mt.cfg, dualk.gram_config_info(mt.cfg) if mt.cfg else None) for mt in sw.mats},
+        "concentration": {d: {k: s[k] for k in ("kq_mean", "kq_var", "logkq_mean", "logkq_var")}
+                          for d, s in sw.concentration().items()},
         "autotune_ms": (tuner.timings if tuner else None),
     }, default=str))
     ctx.close()
