@@ -353,6 +353,10 @@ using F32_P22qS4 = GramCfg<float, 4, 4, 8, 2, 2, 2, 1, 2, 4, 4>;  // 16 x 16 pai
 using F32_P22tS4 = GramCfg<float, 4, 4, 8, 2, 2, 4, 1, 2, 3, 4>;  // 32 x 16 pairs, 128 threads, 3 CTAs per SM
 using F64_P11 = GramCfg<double, 4, 4, 8, 1, 1, 4, 2, 4, 1>;    // 16 x 16 pairs, 256 threads
 using F32X8_P11 = GramCfg<float, 8, 4, 8, 1, 1, 4, 2, 4, 1>;   // chi = 8: 16 x 16 pairs, 256 threads
+using F32X8_S4 = GramCfg<float, 8, 4, 8, 1, 1, 4, 2, 2, 1, 4>;    // chi = 8: 16 x 16, 2 stages of 4 sites
+using F32X8_S2 = GramCfg<float, 8, 4, 8, 1, 1, 4, 2, 3, 1, 2>;    // chi = 8: 16 x 16, 3 stages of 2 sites
+using F32X8_h = GramCfg<float, 8, 4, 8, 1, 1, 2, 2, 2, 2, 4>;     // chi = 8: 8 x 16, 128 threads, 2 CTAs per SM
+using F32X8_q = GramCfg<float, 8, 4, 8, 1, 1, 2, 1, 2, 4, 2>;     // chi = 8: 8 x 8, 64 threads, 4 CTAs per SM
 
 template <class Cfg>
 static dk_status launch_gram(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
@@ -377,7 +381,9 @@ static const CfgInfo kF32Chi4[] = {info_of<F32_P11>(),  info_of<F32_P21>(),  inf
                                    info_of<F32_P22tS4>()};
 constexpr int kF32Chi4Default = 14;  // 32 x 16 pairs, 2 CTAs per SM: among the fastest on the n = 784 Gram and rows
 static const CfgInfo kF64Chi4[] = {info_of<F64_P11>()};
-static const CfgInfo kF32Chi8[] = {info_of<F32X8_P11>()};
+constexpr int kF32Chi8Default = 2;  // 16 x 16 pairs, 2 stages of 4 sites: fastest at d = 256
+static const CfgInfo kF32Chi8[] = {info_of<F32X8_P11>(), info_of<F32X8_S4>(), info_of<F32X8_S2>(),
+                                   info_of<F32X8_h>(), info_of<F32X8_q>()};
 
 static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, int chi,
                                dk_dtype dtype, dk_precision prec, const GramArgs& a, cudaStream_t st) {
@@ -405,8 +411,17 @@ static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const vo
   }
   if (dtype == DK_C128 && prec == DK_PREC_F64 && chi == 4)
     return launch_gram<F64_P11>(ctx, mps_r, m_r, mps_c, m_c, a, st);
-  if (dtype == DK_C64 && prec == DK_PREC_F32 && chi == 8)
-    return launch_gram<F32X8_P11>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+  if (dtype == DK_C64 && prec == DK_PREC_F32 && chi == 8) {
+    // shape ids index the bond-8 table; an id beyond it (e.g. one chosen for bond 4) gives
+    // the default
+    switch (ctx->gram_config) {
+      case 1: return launch_gram<F32X8_P11>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 3: return launch_gram<F32X8_S2>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 4: return launch_gram<F32X8_h>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 5: return launch_gram<F32X8_q>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      default: return launch_gram<F32X8_S4>(ctx, mps_r, m_r, mps_c, m_c, a, st);  // kF32Chi8Default
+    }
+  }
   if (dtype == DK_C64 && prec == DK_PREC_F32 && chi == 32) return gram32_launch(ctx, mps_r, m_r, mps_c, m_c, a, st);
   if (dtype == DK_C64 && prec == DK_PREC_BF16X3 && chi == 32)
     return gram32_tc_launch(ctx, mps_r, m_r, mps_c, m_c, a, st);
@@ -474,7 +489,8 @@ DK_API dk_status dk_gram_config_info(dk_dtype dtype, int chi_max, int id, int* t
   const int count = dk_gram_config_count(dtype, chi_max);
   if (id < 0 || id > count || count == 0) return DK_ERR_ARG;
   const dk::CfgInfo* tab = dtype == DK_C64 ? (chi_max == 4 ? dk::kF32Chi4 : dk::kF32Chi8) : dk::kF64Chi4;
-  const int idx = (id == 0 ? ((dtype == DK_C64 && chi_max == 4) ? dk::kF32Chi4Default : 1) : id) - 1;
+  const int dflt = dtype == DK_C64 ? (chi_max == 4 ? dk::kF32Chi4Default : dk::kF32Chi8Default) : 1;
+  const int idx = (id == 0 ? dflt : id) - 1;
   if (tile_rows) *tile_rows = tab[idx].tile_rows;
   if (tile_cols) *tile_cols = tab[idx].tile_cols;
   if (threads) *threads = tab[idx].threads;

@@ -323,6 +323,34 @@ def test_chi8_fmnist_d256_sampled(dk):
     _check_block(rows, kq, lkq, og.rbf(xte, xtr, 1 / 256), 0.5)
 
 
+def test_chi8_every_tile_shape_bit_identical(dk):
+    """Every bond-8 tile shape (reps = 3, d = 40) gives bit-identical K_q, log K_q and K_c for
+    a symmetric Gram with ragged tiles (150 samples) and a rectangular block: each pair is
+    contracted by the same arithmetic whatever tile, stage depth or CTA count it lands in."""
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    d = synthetic.fmnist_like(150, 37, 40)
+    fm = dualk.FeatureMap(reps=3, chi_max=8)
+    mtr = dualk.mps_build(ctx, _dev(torch, d["x_train"]), fm)
+    mte = dualk.mps_build(ctx, _dev(torch, d["x_test"]), fm)
+    ref = None
+    try:
+        for cid in range(1, dualk.gram_config_count(dualk.DK_C64, 8) + 1):
+            ctx.set_gram_config(cid)
+            g = dualk.gram(ctx, mtr, w=0.5)
+            r = dualk.dual_kernel_rows(ctx, mte, mtr, w=0.5)
+            got = [t.cpu() for t in (g["kq"], g["logkq"], g["kc"], r["kq"], r["logkq"])]
+            if ref is None:
+                ref = got
+            else:
+                for a, b in zip(ref, got):
+                    assert torch.equal(a, b)
+    finally:
+        ctx.set_gram_config(0)
+    assert dualk.gram_config_count(dualk.DK_C64, 8) >= 5
+    ctx.sync_status()
+
+
 def test_bounded_wait_reports_timeout_and_context_survives(dk):
     """A device wait that nothing satisfies gives up after its bound, the status word says
     DK_ERR_TIMEOUT, and the same context then runs a Gram normally."""
