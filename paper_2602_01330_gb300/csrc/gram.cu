@@ -351,6 +351,9 @@ using F32_P22hS8 = GramCfg<float, 4, 4, 8, 2, 2, 2, 2, 2, 2, 8>;  // 16 x 32 pai
 using F32_P22vS8 = GramCfg<float, 4, 4, 8, 2, 2, 4, 1, 2, 2, 8>;  // 32 x 16 pairs, 128 threads, 2 CTAs per SM
 using F32_P22qS4 = GramCfg<float, 4, 4, 8, 2, 2, 2, 1, 2, 4, 4>;  // 16 x 16 pairs, 64 threads, 4 CTAs per SM
 using F32_P22tS4 = GramCfg<float, 4, 4, 8, 2, 2, 4, 1, 2, 3, 4>;  // 32 x 16 pairs, 128 threads, 3 CTAs per SM
+using F32_P22qS6 = GramCfg<float, 4, 4, 8, 2, 2, 2, 1, 2, 4, 6>;  // 16 x 16 pairs, 4 CTAs per SM, 6 sites/stage
+using F32_P22vS5 = GramCfg<float, 4, 4, 8, 2, 2, 4, 1, 3, 2, 5>;  // 32 x 16 pairs, 2 CTAs per SM, 3 stages of 5
+using F32_P22oS4 = GramCfg<float, 4, 4, 8, 2, 2, 1, 1, 2, 8, 4>;  // 8 x 16 pairs, one warp, 8 CTAs per SM
 using F64_P11 = GramCfg<double, 4, 4, 8, 1, 1, 4, 2, 4, 1>;    // 16 x 16 pairs, 256 threads
 using F32X8_P11 = GramCfg<float, 8, 4, 8, 1, 1, 4, 2, 4, 1>;   // chi = 8: 16 x 16 pairs, 256 threads
 using F32X8_S4 = GramCfg<float, 8, 4, 8, 1, 1, 4, 2, 2, 1, 4>;    // chi = 8: 16 x 16, 2 stages of 4 sites
@@ -378,8 +381,9 @@ static const CfgInfo kF32Chi4[] = {info_of<F32_P11>(),  info_of<F32_P21>(),  inf
                                    info_of<F32_P22wS2>(), info_of<F32_P22S2>(), info_of<F32_P22wS4>(),
                                    info_of<F32_P22wS8>(), info_of<F32_P22S8>(),
                                    info_of<F32_P22hS8>(), info_of<F32_P22vS8>(), info_of<F32_P22qS4>(),
-                                   info_of<F32_P22tS4>()};
-constexpr int kF32Chi4Default = 14;  // 32 x 16 pairs, 2 CTAs per SM: among the fastest on the n = 784 Gram and rows
+                                   info_of<F32_P22tS4>(), info_of<F32_P22qS6>(), info_of<F32_P22vS5>(),
+                                   info_of<F32_P22oS4>()};
+constexpr int kF32Chi4Default = 17;  // 16 x 16 pairs, 4 CTAs per SM, 6-site stages: fastest on the n = 784 Gram and rows
 static const CfgInfo kF64Chi4[] = {info_of<F64_P11>()};
 constexpr int kF32Chi8Default = 2;  // 16 x 16 pairs, 2 stages of 4 sites: fastest at d = 256
 static const CfgInfo kF32Chi8[] = {info_of<F32X8_P11>(), info_of<F32X8_S4>(), info_of<F32X8_S2>(),
@@ -405,8 +409,11 @@ static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const vo
       case 14: return launch_gram<F32_P22vS8>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 15: return launch_gram<F32_P22qS4>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 16: return launch_gram<F32_P22tS4>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 17: return launch_gram<F32_P22qS6>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 18: return launch_gram<F32_P22vS5>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      case 19: return launch_gram<F32_P22oS4>(ctx, mps_r, m_r, mps_c, m_c, a, st);
       case 3: return launch_gram<F32_P22>(ctx, mps_r, m_r, mps_c, m_c, a, st);
-      default: return launch_gram<F32_P22vS8>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+      default: return launch_gram<F32_P22qS6>(ctx, mps_r, m_r, mps_c, m_c, a, st);
     }
   }
   if (dtype == DK_C128 && prec == DK_PREC_F64 && chi == 4)
