@@ -15,6 +15,8 @@ What it computes, in plain NumPy float64 / complex128 and in the paper's order:
 * ``gram``     -- the quantum kernel K_q = |<psi(x_i)|psi(x_j)>|^2 (§II-C, Eqs. 7-10)
   from the MPS by a left-to-right transfer contraction with power-of-two rescaling,
   the RBF kernel (§II-B, Eq. 3) and the linear mix (§II-D, Eq. 11);
+* ``preprocess`` -- the data pre-processing of §II-A: standardisation, PCA (eigh of the
+  covariance), min-max scaling;
 * ``svm``      -- the SVM that consumes the kernel matrices: the dual problem of §II-B
   (Eqs. 1-2) by sequential minimal optimisation, the decision function (Eq. 5) and
   one-against-one voting.
