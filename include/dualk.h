@@ -218,6 +218,46 @@ dk_status dk_set_gram_config(dk_ctx* ctx, int id);
 dk_status dk_gram_stats(dk_ctx* ctx, const float* kq, const float* logkq, long long ld, int nrows, int ncols,
                         int symmetric, double* out, void* stream);
 
+/* Largest feature count p of the PCA calls below. */
+#define DK_PCA_MAX_FEATURES 4096
+
+/* Bytes of the caller-provided workspace of dk_pca_fit for p features (2 p^2 floats and a
+ * table of p / 2 rotations, 256-byte aligned parts); 0 for p outside 2..DK_PCA_MAX_FEATURES. */
+size_t dk_pca_workspace_bytes(int p);
+
+/* Data pre-processing of §II-A, fit on the training rows: standardisation (zero mean, unit
+ * population variance per feature; scale 1 for a constant feature) and PCA (the eigenvectors
+ * of the covariance Z^T Z / (m - 1) of the standardised rows, by parallel cyclic Jacobi in
+ * FP32, `sweeps` sweeps of p - 1 rounds each, no host synchronisation).
+ *   x            m x p float32, row-major (device), m >= 2
+ *   k            components kept, 1..p
+ *   workspace    dk_pca_workspace_bytes(p) bytes (device, 256-byte aligned), overwritten
+ *   mean, scale  p floats each (device, written)
+ *   components   k x p floats (device, written): orthonormal rows in order of decreasing
+ *                eigenvalue, each with its entry of largest magnitude positive
+ *   eigenvalues  k floats (device, written)
+ *   off_norm     1 float (device, written, may be NULL): sqrt(off-diagonal / total sum of
+ *                squares) of the rotated covariance after the last sweep (about 1e-7 when
+ *                the sweeps sufficed)
+ * Errors: DK_ERR_ARG (NULL pointers, m < 2, p < 2, k outside 1..p, sweeps outside 1..100),
+ *         DK_ERR_UNSUPPORTED (p > DK_PCA_MAX_FEATURES), DK_ERR_WORKSPACE (workspace too small
+ *         or misaligned). */
+dk_status dk_pca_fit(dk_ctx* ctx, const float* x, int m, int p, int k, int sweeps, void* workspace,
+                     size_t workspace_bytes, float* mean, float* scale, float* components, float* eigenvalues,
+                     float* off_norm, void* stream);
+
+/* Projection onto the leading k components and min-max scaling (§II-A): y = ((x - mean) /
+ * scale) components^T, then out = range_max (y - lo) / (hi - lo) clipped to [0, range_max]
+ * (0 where hi == lo). fit_range = 1 (training rows): lo / hi are the per-feature minimum and
+ * maximum of y over these rows (written); fit_range = 0 (test rows): lo / hi are read.
+ *   x            m x p float32 (device); mean, scale, components from dk_pca_fit
+ *   lo, hi       k floats each (device)
+ *   out          m x k floats (device, written)
+ * Errors: DK_ERR_ARG (NULL pointers, m < 1, p < 1, k outside 1..p, range_max <= 0). */
+dk_status dk_pca_transform(dk_ctx* ctx, const float* x, int m, int p, const float* mean, const float* scale,
+                           const float* components, int k, int fit_range, float range_max, float* lo, float* hi,
+                           float* out, void* stream);
+
 /* Largest training list (m_max) of the SVM calls below. */
 #define DK_SVM_MAX_SAMPLES 4096
 

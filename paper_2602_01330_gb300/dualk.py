@@ -26,8 +26,10 @@ _STATUS_NAMES = {0: "DK_OK", 1: "DK_ERR_ARG", 2: "DK_ERR_UNSUPPORTED", 3: "DK_ER
 EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_mps_bytes",
             "dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows", "dk_gram_config_count",
             "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout", "dk_self_overlap",
-            "dk_svm_ovo_train", "dk_svm_ovo_predict", "dk_gram_stats")
+            "dk_svm_ovo_train", "dk_svm_ovo_predict", "dk_gram_stats", "dk_pca_workspace_bytes", "dk_pca_fit",
+            "dk_pca_transform")
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
+PCA_MAX_FEATURES = 4096  # DK_PCA_MAX_FEATURES
 
 
 class DualKError(RuntimeError):
@@ -81,6 +83,12 @@ def _lib():
     lib.dk_self_overlap.restype = i32
     lib.dk_selftest_wait_timeout.argtypes = [vp, ctypes.c_ulonglong, vp]
     lib.dk_selftest_wait_timeout.restype = i32
+    lib.dk_pca_workspace_bytes.argtypes = [i32]
+    lib.dk_pca_workspace_bytes.restype = ctypes.c_size_t
+    lib.dk_pca_fit.argtypes = [vp, vp, i32, i32, i32, i32, vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp]
+    lib.dk_pca_fit.restype = i32
+    lib.dk_pca_transform.argtypes = [vp, vp, i32, i32, vp, vp, vp, i32, i32, f32, vp, vp, vp, vp]
+    lib.dk_pca_transform.restype = i32
     lib.dk_gram_stats.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp, vp]
     lib.dk_gram_stats.restype = i32
     lib.dk_svm_ovo_train.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, i32, vp, i32, f32, i32, vp, vp, vp,
@@ -390,3 +398,41 @@ def gram_stats(ctx: Context, kq: torch.Tensor | None, logkq: torch.Tensor | None
         res["logkq_mean"] = l1 / cl
         res["logkq_var"] = max(l2 / cl - (l1 / cl) ** 2, 0.0)
     return res
+
+
+def pca_fit(ctx: Context, x: torch.Tensor, k: int, sweeps: int = 10, stream=None) -> dict:
+    """dk_pca_fit on the training rows x (m x p float32, CUDA): mean, scale, components
+    (k x p), eigenvalues (k) and the remaining off-diagonal norm (a 1-element tensor)."""
+    _need_cuda(x, "x", torch.float32)
+    m, p = x.shape
+    nbytes = int(_lib().dk_pca_workspace_bytes(int(p)))
+    if nbytes == 0:
+        raise ValueError(f"{p} features are outside the supported range")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
+    out = {"mean": torch.empty(p, dtype=torch.float32, device=x.device),
+           "scale": torch.empty(p, dtype=torch.float32, device=x.device),
+           "components": torch.empty((k, p), dtype=torch.float32, device=x.device),
+           "eigenvalues": torch.empty(k, dtype=torch.float32, device=x.device),
+           "off_norm": torch.empty(1, dtype=torch.float32, device=x.device)}
+    _check(_lib().dk_pca_fit(ctx.handle, _ptr(x), int(m), int(p), int(k), int(sweeps), _ptr(ws), nbytes,
+                             _ptr(out["mean"]), _ptr(out["scale"]), _ptr(out["components"]),
+                             _ptr(out["eigenvalues"]), _ptr(out["off_norm"]), _stream(stream)), "dk_pca_fit")
+    return out
+
+
+def pca_transform(ctx: Context, x: torch.Tensor, model: dict, fit_range: bool, range_max: float = 3.141592653589793,
+                  stream=None) -> torch.Tensor:
+    """dk_pca_transform: m x k features in [0, range_max]. With fit_range the per-feature
+    range is taken from these rows and stored in model["lo"] / model["hi"]; otherwise read."""
+    _need_cuda(x, "x", torch.float32)
+    m, p = x.shape
+    k = model["components"].shape[0]
+    if fit_range:
+        model["lo"] = torch.empty(k, dtype=torch.float32, device=x.device)
+        model["hi"] = torch.empty(k, dtype=torch.float32, device=x.device)
+    out = torch.empty((m, k), dtype=torch.float32, device=x.device)
+    _check(_lib().dk_pca_transform(ctx.handle, _ptr(x), int(m), int(p), _ptr(model["mean"]), _ptr(model["scale"]),
+                                   _ptr(model["components"]), int(k), 1 if fit_range else 0, float(range_max),
+                                   _ptr(model["lo"]), _ptr(model["hi"]), _ptr(out), _stream(stream)),
+           "dk_pca_transform")
+    return out
