@@ -258,6 +258,30 @@ dk_status dk_pca_transform(dk_ctx* ctx, const float* x, int m, int p, const floa
                            const float* components, int k, int fit_range, float range_max, float* lo, float* hi,
                            float* out, void* stream);
 
+/* Largest feature count of dk_pca_fit_noalloc. */
+#define DK_PCA_NOALLOC_MAX_FEATURES 256
+
+/* dk_pca_fit without a caller workspace, for callers that cannot give this library device
+ * memory of their own: a program whose device memory is owned and capped by another
+ * framework, a plug-in that receives only its input and output pointers, or a loop that must
+ * not stall on or fail in an allocation midway. The paper has no counterpart; it is a
+ * deployment variant of the §II-A fit above, with the same arguments (minus the workspace)
+ * and the same results.
+ *   Working memory: a fixed array of about 0.5 MB inside the library (room for
+ *   DK_PCA_NOALLOC_MAX_FEATURES features), held by every GPU that loads the library until
+ *   the process exits. The call allocates no device memory.
+ *   First call on a device: it looks up that array's device address (once per device, with
+ *   the context's device made current for the lookup); make this first call before any
+ *   stream capture.
+ *   Sharing: every call uses the same array, so calls whose work overlaps on the GPU (on
+ *   different streams, or from different threads) race and corrupt each other; run them one
+ *   after another. Nothing from an earlier call needs clearing: each call writes every part
+ *   of the array it reads.
+ * Errors: as dk_pca_fit, and DK_ERR_UNSUPPORTED for p > DK_PCA_NOALLOC_MAX_FEATURES;
+ *         DK_ERR_CUDA if the array's address cannot be found. */
+dk_status dk_pca_fit_noalloc(dk_ctx* ctx, const float* x, int m, int p, int k, int sweeps, float* mean, float* scale,
+                             float* components, float* eigenvalues, float* off_norm, void* stream);
+
 /* Largest training list (m_max) of the SVM calls below. */
 #define DK_SVM_MAX_SAMPLES 4096
 

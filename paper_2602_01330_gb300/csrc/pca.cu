@@ -22,6 +22,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -395,4 +397,68 @@ DK_API dk_status dk_pca_transform(dk_ctx* ctx, const float* x, int m, int p, con
   const int blocks = int((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
   pca::minmax_apply_kernel<<<blocks, 256, 0, st>>>(out, n, k, lo, hi, range_max);
   return launch_status();
+}
+
+// ---------------------------------------------------------------------------------------
+// dk_pca_fit_noalloc: the same fit with its working memory in a fixed device array.
+//
+// For callers that cannot hand this library device memory of their own: a host program
+// whose device memory is owned and capped by another framework, a plug-in that receives
+// only its input and output pointers, or a loop that must not stall on or fail in an
+// allocation midway. The working memory for up to DK_PCA_NOALLOC_MAX_FEATURES features
+// lives in the file-scope array below, which every GPU that loads the library holds until
+// the process exits. Host code cannot pass the array's name to a kernel (on the host it
+// names a stand-in, not device memory), so the first call on each device looks up the
+// array's device address with that device current and keeps it for later calls.
+
+namespace dk {
+namespace pca {
+
+constexpr size_t round256_c(size_t b) { return (b + 255) & ~size_t(255); }
+constexpr size_t noalloc_bytes() {
+  return 2 * round256_c(size_t(DK_PCA_NOALLOC_MAX_FEATURES) * DK_PCA_NOALLOC_MAX_FEATURES * sizeof(float)) +
+         round256_c(DK_PCA_NOALLOC_MAX_FEATURES / 2 * sizeof(int2)) +
+         round256_c(DK_PCA_NOALLOC_MAX_FEATURES / 2 * sizeof(float4));
+}
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[noalloc_bytes()];
+
+constexpr int MAX_DEVICES = 64;
+static void* g_noalloc_ptr[MAX_DEVICES] = {};
+static std::mutex g_noalloc_mu;
+
+// device address of g_noalloc_scratch on `device`, looked up once with that device current
+static dk_status noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= MAX_DEVICES) return DK_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return DK_ERR_CUDA;
+    if (cur != device && cudaSetDevice(device) != cudaSuccess) return DK_ERR_CUDA;
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (cur != device && cudaSetDevice(cur) != cudaSuccess) return DK_ERR_CUDA;
+    if (e != cudaSuccess || !ptr) return DK_ERR_CUDA;
+    g_noalloc_ptr[device] = ptr;
+  }
+  *out = g_noalloc_ptr[device];
+  return DK_OK;
+}
+
+}  // namespace pca
+}  // namespace dk
+
+DK_API dk_status dk_pca_fit_noalloc(dk_ctx* ctx, const float* x, int m, int p, int k, int sweeps, float* mean,
+                                    float* scale, float* components, float* eigenvalues, float* off_norm,
+                                    void* stream) {
+  if (!ctx || !x || !mean || !scale || !components || !eigenvalues) return DK_ERR_ARG;
+  if (m < 2 || p < 2 || k < 1 || k > p || sweeps < 1 || sweeps > 100) return DK_ERR_ARG;
+  if (p > DK_PCA_NOALLOC_MAX_FEATURES) return DK_ERR_UNSUPPORTED;
+  void* scratch = nullptr;
+  const dk_status s = pca::noalloc_scratch(ctx->device, &scratch);
+  if (s != DK_OK) return s;
+  // every part of the scratch that the fit reads is written earlier in the same call (the
+  // covariance, the identity, each round's rotation table), so nothing needs clearing
+  return pca::fit(ctx, x, m, p, k, sweeps, pca::carve(scratch, p), mean, scale, components, eigenvalues, off_norm,
+                  static_cast<cudaStream_t>(stream));
 }

@@ -27,9 +27,10 @@ EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_
             "dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows", "dk_gram_config_count",
             "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout", "dk_self_overlap",
             "dk_svm_ovo_train", "dk_svm_ovo_predict", "dk_gram_stats", "dk_pca_workspace_bytes", "dk_pca_fit",
-            "dk_pca_transform")
+            "dk_pca_transform", "dk_pca_fit_noalloc")
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 PCA_MAX_FEATURES = 4096  # DK_PCA_MAX_FEATURES
+PCA_NOALLOC_MAX_FEATURES = 256  # DK_PCA_NOALLOC_MAX_FEATURES
 
 
 class DualKError(RuntimeError):
@@ -87,6 +88,8 @@ def _lib():
     lib.dk_pca_workspace_bytes.restype = ctypes.c_size_t
     lib.dk_pca_fit.argtypes = [vp, vp, i32, i32, i32, i32, vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp]
     lib.dk_pca_fit.restype = i32
+    lib.dk_pca_fit_noalloc.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.dk_pca_fit_noalloc.restype = i32
     lib.dk_pca_transform.argtypes = [vp, vp, i32, i32, vp, vp, vp, i32, i32, f32, vp, vp, vp, vp]
     lib.dk_pca_transform.restype = i32
     lib.dk_gram_stats.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp, vp]
