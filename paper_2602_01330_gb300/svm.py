@@ -124,19 +124,40 @@ class DualKernelSVM:
 
 def run_pipeline(ctx: dualk.Context, n_train: int = 2000, n_test: int = 500, d: int = 784, reps: int = 2,
                  Cs=(0.1, 1.0, 10.0, 100.0), ws=(0.0, 0.25, 0.5, 0.75, 1.0), seed: int = 0,
-                 gram=None) -> dict:
+                 gram=None, features: str = "projection") -> dict:
     """The §II-D workflow on synthetic Fashion-MNIST-shaped data: Gram + rows (or the given
     `gram` = (kq, kc, kq_rows, kc_rows) tensors), 5-fold CV over C x w, final fit, test
-    accuracy. Accuracies on synthetic data are a consistency check, not the paper's results."""
+    accuracy. features = "projection": the generator's seeded projection and scaling;
+    "pca": the raw images through the GPU pre-processing of §II-A (standardise, PCA to d,
+    min-max to [0, pi]). Accuracies on synthetic data are a consistency check, not the
+    paper's results."""
     from . import synthetic
-    data = synthetic.fmnist_like(n_train, n_test, d)
-    ytr, yte = np.asarray(data["y_train"]), np.asarray(data["y_test"])
+    pre_ms = None
+    if features == "pca":
+        from .preprocess import PCAPreprocessor
+        xr, ytr = synthetic.images(n_train, synthetic.SEED_TRAIN)
+        xs, yte = synthetic.images(n_test, synthetic.SEED_TEST)
+        xr = torch.from_numpy(xr.astype(np.float32)).cuda()
+        xs = torch.from_numpy(xs.astype(np.float32)).cuda()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        pre = PCAPreprocessor(ctx, k_max=d).fit(xr)
+        ftr, fte = pre.features(xr, xs, d)
+        ev[1].record()
+        torch.cuda.synchronize()
+        pre_ms = ev[0].elapsed_time(ev[1])
+        data = {"x_train": ftr, "x_test": fte}
+    else:
+        data = synthetic.fmnist_like(n_train, n_test, d)
+        ytr, yte = data["y_train"], data["y_test"]
+        data = {"x_train": torch.from_numpy(data["x_train"]).cuda(), "x_test": torch.from_numpy(data["x_test"]).cuda()}
+    ytr, yte = np.asarray(ytr), np.asarray(yte)
     n_class = int(max(ytr.max(), yte.max())) + 1
     t0 = time.perf_counter()
     if gram is None:
         fm = dualk.FeatureMap(reps=reps, chi_max=4)
-        mtr = dualk.mps_build(ctx, torch.from_numpy(data["x_train"]).cuda(), fm)
-        mte = dualk.mps_build(ctx, torch.from_numpy(data["x_test"]).cuda(), fm)
+        mtr = dualk.mps_build(ctx, data["x_train"], fm)
+        mte = dualk.mps_build(ctx, data["x_test"], fm)
         g = dualk.gram(ctx, mtr, w=1.0, want=("kq", "kc"))
         r = dualk.dual_kernel_rows(ctx, mte, mtr, w=1.0, want=("kq", "kc"))
         kq, kc, kqr, kcr = g["kq"], g["kc"], r["kq"], r["kc"]
@@ -156,8 +177,9 @@ def run_pipeline(ctx: dualk.Context, n_train: int = 2000, n_test: int = 500, d: 
     pred = pred.cpu().numpy()
     ctx.sync_status()
     return {
-        "workload": f"fmnist-shaped d={d} train={n_train} test={n_test} classes={n_class}, "
+        "workload": f"fmnist-shaped d={d} train={n_train} test={n_test} classes={n_class}, features={features}, "
                     f"{len(cv.grid)} (C, w) points x 5 folds",
+        "preprocess_ms": pre_ms,
         "gram_and_rows_s": t_gram,
         "cv_jobs": cv.jobs, "cv_binary_problems": cv.binary_problems,
         "cv_train_ms": cv.train_ms, "cv_predict_ms": cv.predict_ms,
@@ -177,9 +199,10 @@ def main():
     ap.add_argument("--n-train", type=int, default=2000)
     ap.add_argument("--n-test", type=int, default=500)
     ap.add_argument("--d", type=int, default=784)
+    ap.add_argument("--features", choices=("projection", "pca"), default="projection")
     args = ap.parse_args()
     ctx = dualk.Context(0)
-    print(json.dumps(run_pipeline(ctx, args.n_train, args.n_test, args.d)))
+    print(json.dumps(run_pipeline(ctx, args.n_train, args.n_test, args.d, features=args.features)))
     ctx.close()
 
 

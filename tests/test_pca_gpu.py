@@ -89,3 +89,51 @@ def test_pca_workspace_checked(dk):
     assert st == 5  # DK_ERR_WORKSPACE
     assert dualk._lib().dk_pca_workspace_bytes(1) == 0
     assert dualk._lib().dk_pca_workspace_bytes(dualk.PCA_MAX_FEATURES + 1) == 0
+
+
+def test_preprocessor_leading_features(dk):
+    """One fit to 32 components serves every n <= 32: the leading 8 of it give exactly the
+    features of a fit to 8 (the Jacobi sweeps diagonalise the whole matrix either way), the
+    training columns span [0, pi], and against the oracle every feature agrees within the
+    bound its component's error implies: |dy| <= max|z| * |v - v_ref| rescaled to [0, pi],
+    with |v - v_ref| = sqrt(2 (1 - <v, v_ref>)), plus 2e-3 of rounding."""
+    dualk, ctx, torch = dk
+    from oracle import preprocess as pp
+    from paper_2602_01330_gb300 import synthetic
+    from paper_2602_01330_gb300.preprocess import PCAPreprocessor
+    xr, _ = synthetic.images(500, synthetic.SEED_TRAIN)
+    xs, _ = synthetic.images(100, synthetic.SEED_TEST)
+    xr, xs = xr.astype(np.float32), xs.astype(np.float32)
+    gr, gs = torch.from_numpy(xr).cuda(), torch.from_numpy(xs).cuda()
+    pre = PCAPreprocessor(ctx, k_max=32).fit(gr)
+    ftr, fte = pre.features(gr, gs, 8)
+    direct = dualk.pca_fit(ctx, gr, 8, sweeps=10)
+    dtr = dualk.pca_transform(ctx, gr, direct, fit_range=True)
+    torch.cuda.synchronize()
+    assert torch.equal(ftr, dtr)
+    f = ftr.cpu().numpy()
+    np.testing.assert_allclose(f.min(axis=0), 0.0, atol=1e-6)
+    np.testing.assert_allclose(f.max(axis=0), np.pi, rtol=1e-6)
+    mean, scale, comps, _ = pp.pca_fit(xr, 8)
+    y = pp.project(xr, mean, scale, comps)
+    lo, hi = pp.minmax_fit(y)
+    v = pre.model["components"][:8].cpu().numpy().astype(np.float64)
+    dv = np.sqrt(np.maximum(2.0 * (1.0 - np.sum(v * comps, axis=1)), 0.0))
+    znorm = max(np.linalg.norm((xr - mean) / scale, axis=1).max(), np.linalg.norm((xs - mean) / scale, axis=1).max())
+    tol = znorm * dv * np.pi / (hi - lo) + 2e-3
+    assert np.all(np.abs(f - pp.minmax_apply(y, lo, hi)) <= tol)
+    ref_te = pp.minmax_apply(pp.project(xs, mean, scale, comps), lo, hi)
+    assert np.all(np.abs(fte.cpu().numpy() - ref_te) <= tol)
+    ctx.sync_status()
+
+
+def test_pipeline_on_pca_features(dk):
+    """The §II-D workflow from raw images: GPU pre-processing to 16 components, MPS, Gram,
+    cross-validation, fit, test predictions. On the synthetic classes it must beat chance
+    (0.1) by far; the paper's accuracies are not a target on synthetic data."""
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import svm
+    out = svm.run_pipeline(ctx, n_train=300, n_test=100, d=16, Cs=(1.0, 10.0), ws=(0.5, 1.0), features="pca")
+    assert out["preprocess_ms"] is not None and out["preprocess_ms"] > 0
+    assert out["test_accuracy"] > 0.5
+    ctx.sync_status()
