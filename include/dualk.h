@@ -81,7 +81,10 @@ typedef struct dk_ctx dk_ctx;
  * the map built here is the ZZ chain: per repetition, H on every qubit, then
  * RZ(angle_scale * x_i) on qubit i, then (if entangle) RZZ(2 (pi - x_i)(pi - x_{i+1}))
  * on every neighbouring pair of the open chain; the same x is re-uploaded by every
- * repetition. */
+ * repetition. With block = b >= 1 the entanglers are block-structured (the block product
+ * state form §II-C describes): the qubits form blocks of b consecutive qubits (the last
+ * may be shorter) and only pairs inside a block get an RZZ, so the state is a product of
+ * the blocks' own chain states and K_q a product of per-block kernels. */
 typedef struct {
   int reps;           /* repetitions, 1..5 */
   float angle_scale;  /* RZ angle = angle_scale * x_i (2 for the ZZ-chain map) */
@@ -90,6 +93,8 @@ typedef struct {
   int qr_prec;        /* arithmetic of the left-canonical QR sweep for complex64 output at
                          chi_max 4: DK_PREC_F32 (0, default) or DK_PREC_F64. complex128
                          output and wider bonds always use FP64. */
+  int block;          /* 0: one block (the whole chain); b >= 1: entanglers only inside
+                         blocks of b consecutive qubits (b = 1: none, b >= n: the chain) */
 } dk_fmap;
 
 /* Create a context on `device` (sets it current on the calling thread). The context
@@ -128,12 +133,14 @@ size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
  *   fm         feature map (host pointer)
  *   mps        dk_mps_bytes(m, n, fm->chi_max, dtype) bytes (device, written)
  *   bond_dims  n + 1 int32 (device, written, may be NULL): number of non-zero left-bond
- *              positions of site k (1, 2, 4, ... up to 2^reps), and 1 at index n
+ *              positions of site k (1, 2, 4, ... up to 2^reps), and 1 at index n. With
+ *              block >= 1 the stored bond at a block boundary keeps the chain's size
+ *              (its exact rank is 1; the extra positions hold rounding-level columns).
  *   log_norm   m floats (device, written, may be NULL): ln |<psi~_i|psi~_i>| of the
  *              rounded tensors, evaluated by the same transfer arithmetic as the Gram
  *              calls; passing it to them normalises K_q so that K_q(x, x) = 1.
  * Errors: DK_ERR_ARG (m < 1, n < 1, NULL x/mps/fm, reps outside 1..5, qr_prec neither
- *         DK_PREC_F32 nor DK_PREC_F64, misaligned mps),
+ *         DK_PREC_F32 nor DK_PREC_F64, block < 0, misaligned mps),
  *         DK_ERR_UNSUPPORTED (chi_max not in {4, 8, 16, 32} or below 2^reps; log_norm
  *         requested for a chi_max / dtype without a Gram kernel: complex64 has chi_max 4,
  *         8 and 32, complex128 chi_max 4). */

@@ -36,6 +36,20 @@ def entangler_angles(x: np.ndarray) -> np.ndarray:
     return 2.0 * (np.pi - x[:-1]) * (np.pi - x[1:])
 
 
+def entangled_bonds(n: int, block: int = 0) -> np.ndarray:
+    """Which neighbouring pairs (i, i+1), i = 0 .. n-2, carry an RZZ.
+
+    block = 0 (or >= n): every pair, the open chain. block = b >= 1: the block product
+    (BPS) structure of §II-C, qubits grouped into blocks of b consecutive qubits with
+    entanglers only inside a block, so pair (i, i+1) is entangled when i and i+1 fall in
+    the same block (the last block may be shorter).
+    """
+    i = np.arange(max(n - 1, 0))
+    if block <= 0:
+        return np.ones(i.shape, dtype=bool)
+    return (i // block) == ((i + 1) // block)
+
+
 def _apply_1q(psi: np.ndarray, gate: np.ndarray, q: int) -> np.ndarray:
     out = np.tensordot(gate, psi, axes=([1], [q]))
     return np.moveaxis(out, 0, q)
@@ -49,10 +63,11 @@ def _apply_zz(psi: np.ndarray, theta: float, q: int) -> np.ndarray:
     return psi * rzz_phases(theta).reshape(shape)
 
 
-def statevector(x, reps: int, angle_scale: float = 2.0, entangle: bool = True) -> np.ndarray:
+def statevector(x, reps: int, angle_scale: float = 2.0, entangle: bool = True, block: int = 0) -> np.ndarray:
     """|psi(x)> = [U_ZZ(x) . (x)_i RZ(angle_scale x_i) . H^(x)n]^reps |0...0>, flattened.
 
-    Qubit 0 is the most significant bit of the flattened index.
+    U_ZZ holds the RZZ of every pair that ``entangled_bonds(n, block)`` lists. Qubit 0 is
+    the most significant bit of the flattened index.
     """
     x = np.asarray(x, dtype=np.float64)
     n = x.shape[0]
@@ -63,6 +78,7 @@ def statevector(x, reps: int, angle_scale: float = 2.0, entangle: bool = True) -
     h = hadamard()
     phis = single_qubit_angles(x, angle_scale)
     thetas = entangler_angles(x)
+    bonds = entangled_bonds(n, block)
     for _ in range(reps):
         for q in range(n):
             psi = _apply_1q(psi, h, q)
@@ -70,13 +86,15 @@ def statevector(x, reps: int, angle_scale: float = 2.0, entangle: bool = True) -
             psi = _apply_1q(psi, rz(phis[q]), q)
         if entangle:
             for q in range(n - 1):
-                psi = _apply_zz(psi, thetas[q], q)
+                if bonds[q]:
+                    psi = _apply_zz(psi, thetas[q], q)
     return psi.reshape(-1)
 
 
-def kernel_matrix(x_rows, x_cols, reps: int, angle_scale: float = 2.0, entangle: bool = True) -> np.ndarray:
+def kernel_matrix(x_rows, x_cols, reps: int, angle_scale: float = 2.0, entangle: bool = True,
+                  block: int = 0) -> np.ndarray:
     """K_q[i, j] = |<psi(x_i)|psi(x_j)>|^2 (Eq. 7) by brute-force statevectors."""
-    a = np.stack([statevector(x, reps, angle_scale, entangle) for x in np.asarray(x_rows)])
-    b = np.stack([statevector(x, reps, angle_scale, entangle) for x in np.asarray(x_cols)])
+    a = np.stack([statevector(x, reps, angle_scale, entangle, block) for x in np.asarray(x_rows)])
+    b = np.stack([statevector(x, reps, angle_scale, entangle, block) for x in np.asarray(x_cols)])
     amp = a.conj() @ b.T
     return np.abs(amp) ** 2

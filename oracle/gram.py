@@ -78,10 +78,11 @@ def gram_from_mps(rows, cols, chunk: int = 8192):
 
 
 def quantum_gram(x_rows, x_cols=None, reps: int = 2, angle_scale: float = 2.0,
-                 entangle: bool = True, chi_cap=None, cutoff: float = 1e-14):
-    """K_q and log K_q for all pairs of rows of x_rows and x_cols (x_cols defaults to x_rows)."""
-    rows, _ = build_mps(x_rows, reps, angle_scale, entangle, chi_cap, cutoff)
-    cols = rows if x_cols is None else build_mps(x_cols, reps, angle_scale, entangle, chi_cap, cutoff)[0]
+                 entangle: bool = True, chi_cap=None, cutoff: float = 1e-14, block: int = 0):
+    """K_q and log K_q for all pairs of rows of x_rows and x_cols (x_cols defaults to x_rows).
+    block: 0 for the open ZZ chain, b >= 1 for blocks of b qubits (``circuit.entangled_bonds``)."""
+    rows, _ = build_mps(x_rows, reps, angle_scale, entangle, chi_cap, cutoff, block)
+    cols = rows if x_cols is None else build_mps(x_cols, reps, angle_scale, entangle, chi_cap, cutoff, block)[0]
     return gram_from_mps(rows, cols)
 
 

@@ -10,10 +10,14 @@ circuit is applied in order (time-evolving block decimation):
 2. per repetition: H, then RZ(angle_scale * x_k), on every site (single-site
    contraction on the physical leg);
 3. per repetition, if entanglers are on: bring the MPS to right-canonical form
-   (orthogonality centre on site 0), then apply RZZ(2 (pi - x_k)(pi - x_{k+1})) to
-   k = 0 .. n-2 in order, each time splitting the two-site block by SVD, keeping the
+   (orthogonality centre on site 0), then for k = 0 .. n-2 in order apply
+   RZZ(2 (pi - x_k)(pi - x_{k+1})) where the pair (k, k+1) is entangled (every pair of
+   the chain, or only pairs inside a block for the block product structure, see
+   ``circuit.entangled_bonds``), and split the two-site block by SVD, keeping the
    singular values s > cutoff * s_0 (at most chi_cap of them), rescaling the kept ones
-   to the norm of the full spectrum, and moving the centre one site right.
+   to the norm of the full spectrum, and moving the centre one site right. Across a
+   block boundary no gate acts and the split only moves the centre (the bond there
+   falls to 1).
 
 With the default cutoff (1e-14) nothing but numerically zero singular values is
 dropped, so the MPS equals the statevector to rounding. All samples of one call share
@@ -24,7 +28,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .circuit import entangler_angles, hadamard, rz, rzz_phases, single_qubit_angles
+from .circuit import entangled_bonds, entangler_angles, hadamard, rz, rzz_phases, single_qubit_angles
 
 
 def _product_zero(m: int, n: int):
@@ -57,7 +61,7 @@ def _right_canonicalize(sites) -> None:
 
 
 def build_mps(x, reps: int, angle_scale: float = 2.0, entangle: bool = True,
-              chi_cap: int | None = None, cutoff: float = 1e-14):
+              chi_cap: int | None = None, cutoff: float = 1e-14, block: int = 0):
     """Return (sites, discarded) for the samples in x (shape m x n).
 
     sites[k] has shape (m, D_{k}, 2, D_{k+1}); discarded[m] is the squared weight of the
@@ -70,6 +74,7 @@ def build_mps(x, reps: int, angle_scale: float = 2.0, entangle: bool = True,
     h = hadamard()
     phis = single_qubit_angles(x, angle_scale)          # (m, n)
     thetas = np.stack([entangler_angles(row) for row in x]) if n > 1 else np.zeros((m, 0))
+    bonds = entangled_bonds(n, block)
     for _ in range(reps):
         for k in range(n):
             gates = np.stack([rz(phis[i, k]) @ h for i in range(m)])
@@ -80,10 +85,11 @@ def build_mps(x, reps: int, angle_scale: float = 2.0, entangle: bool = True,
         for k in range(n - 1):
             a, b = sites[k], sites[k + 1]
             dl, dr = a.shape[1], b.shape[3]
-            block = np.einsum("mlsa,matr->mlstr", a, b)
-            phase = np.stack([rzz_phases(thetas[i, k]) for i in range(m)])  # (m, 2, 2)
-            block = block * phase[:, None, :, :, None]
-            mat = block.reshape(m, dl * 2, 2 * dr)
+            pair = np.einsum("mlsa,matr->mlstr", a, b)
+            if bonds[k]:
+                phase = np.stack([rzz_phases(thetas[i, k]) for i in range(m)])  # (m, 2, 2)
+                pair = pair * phase[:, None, :, :, None]
+            mat = pair.reshape(m, dl * 2, 2 * dr)
             u, s, vh = np.linalg.svd(mat, full_matrices=False)
             s0 = s[:, :1]
             keep = s > cutoff * np.where(s0 > 0, s0, 1.0)

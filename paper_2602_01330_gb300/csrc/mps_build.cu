@@ -25,6 +25,11 @@
 // Stored layout (compact, see include/dualk.h): A[k][i][s][j][l], j < h = chi/2 the
 // column inside block s (bond position s*h + j), l < chi the left bond position.
 //
+// Block-structured entanglers (dk_fmap.block = b): the RZZ of the pair (k-1, k) is applied
+// only when k is not a multiple of b, i.e. both qubits lie in one block; elsewhere theta = 0
+// and the bond phase is 1, so the same closed form holds with the chain cut at the block
+// boundaries (the stored bond there keeps its size; QR leaves rounding-level columns).
+//
 // The self-overlap kernel then runs the Gram transfer arithmetic (transfer.cuh) on each
 // sample's own rounded tensors and stores ln|<psi~|psi~>|, the normaliser that makes the
 // Gram diagonal exactly 1.
@@ -62,6 +67,12 @@ template <typename T>
 __device__ __forceinline__ T cabs2(cx<T> a) { return fmx(a.x, a.x, a.y * a.y); }
 
 constexpr double PI_D = 3.14159265358979323846;
+
+// RZZ on the pair (k-1, k)? ent_block = 0: no entanglers; b >= 1: only inside blocks of b
+// (the open chain is b = n).
+__host__ __device__ __forceinline__ bool entangled(int ent_block, int k) {
+  return ent_block > 0 && k % ent_block != 0;
+}
 
 // Closed-form factors of one site for RP repetitions: u^e and w^e for e in [-RP, RP],
 // u = exp(-i phi/2), w = exp(-i theta/2) (unit modulus, so u^-e = conj(u^e)).
@@ -177,7 +188,7 @@ __device__ __forceinline__ cd shfl_cd(unsigned mask, cd v, int lane_mask) {
 // diagonal without a second pass.
 template <int HS, int HA, int RP, typename real>
 __global__ void __launch_bounds__(32) mps_build_pair_kernel(const float* __restrict__ x, int m, int n,
-                                                            double angle_scale, int entangle,
+                                                            double angle_scale, int ent_block,
                                                             void* __restrict__ out, int32_t* __restrict__ bond,
                                                             float* __restrict__ log_norm) {
   constexpr int P = 2 * HS;  // stored left-bond positions
@@ -204,7 +215,7 @@ __global__ void __launch_bounds__(32) mps_build_pair_kernel(const float* __restr
   auto expo = [&](int k) {
     const double xk = double(xs[k]);
     const double xp = k > 0 ? double(xs[k - 1]) : 0.0;
-    const double arg = s == 0 ? -0.5 * angle_scale * xk : ((entangle && k > 0) ? -(PI_D - xp) * (PI_D - xk) : 0.0);
+    const double arg = s == 0 ? -0.5 * angle_scale * xk : (entangled(ent_block, k) ? -(PI_D - xp) * (PI_D - xk) : 0.0);
     double sn, cs;
     sincos(arg, &sn, &cs);
     return mk(cs, sn);
@@ -359,7 +370,7 @@ __device__ __forceinline__ void pi_minus(float v, float& hi, float& lo) {
 // to the Gram diagonal.
 template <int HA, int RP, typename real, typename creal>
 __global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restrict__ x, int m, int n,
-                                                           double angle_scale, int entangle,
+                                                           double angle_scale, int ent_block,
                                                            void* __restrict__ out, int32_t* __restrict__ bond,
                                                            float* __restrict__ log_norm) {
   using C = cx<creal>;
@@ -390,7 +401,7 @@ __global__ void __launch_bounds__(32) mps_build_oct_kernel(const float* __restri
   auto expo = [&](int k) -> C {
     const float xk = xs[k];
     const float xp = k > 0 ? xs[k - 1] : 0.0f;
-    const bool ent = entangle && k > 0;
+    const bool ent = entangled(ent_block, k);
     if constexpr (f64) {
       const double arg = (q & 1) == 0 ? -0.5 * angle_scale * double(xk)
                                       : (ent ? -(PI_D - double(xp)) * (PI_D - double(xk)) : 0.0);
@@ -574,7 +585,7 @@ struct WarpQr {
 
 template <int HS, int HA, int RP>
 __global__ void __launch_bounds__(32) mps_build_warp_kernel(const float* __restrict__ x, int m, int n,
-                                                            double angle_scale, int entangle, int out_c128,
+                                                            double angle_scale, int ent_block, int out_c128,
                                                             void* __restrict__ out, int32_t* __restrict__ bond) {
   constexpr int P = 2 * HS;
   constexpr int CHI = 2 * HS;
@@ -593,7 +604,7 @@ __global__ void __launch_bounds__(32) mps_build_warp_kernel(const float* __restr
   SiteFactors<RP> f;
   for (int k = 0; k < n; ++k) {
     const double xk = double(xs[k]);
-    f.make(angle_scale * xk, (entangle && k > 0) ? 2.0 * (PI_D - xprev) * (PI_D - xk) : 0.0);
+    f.make(angle_scale * xk, entangled(ent_block, k) ? 2.0 * (PI_D - xprev) * (PI_D - xk) : 0.0);
     for (int c = lane; c < 2 * HA; c += 32) S.L[c] = f.local(c);
     __syncwarp();
     const size_t base = (size_t(k) * m + i) * per;
@@ -754,6 +765,7 @@ template <int HS, int HA>
 static dk_status launch_build(const float* x, int m, int n, const dk_fmap* fm, int c128, void* mps, int32_t* bond,
                               float* log_norm, int sm_count, cudaStream_t st, bool* fused_norm) {
   const bool fp64_qr = c128 || fm->qr_prec == DK_PREC_F64;
+  const int eb = !fm->entangle ? 0 : ((fm->block >= 1 && fm->block < n) ? fm->block : n);
   *fused_norm = false;
   if constexpr (HA <= 2) {
     constexpr int RP = HA == 1 ? 1 : 2;
@@ -771,11 +783,11 @@ static dk_status launch_build(const float* x, int m, int n, const dk_fmap* fm, i
       const int grid = (m + spc - 1) / spc;
       const double as = double(fm->angle_scale);
       if (c128) {
-        mps_build_oct_kernel<HA, RP, double, double><<<grid, 8 * spc, 0, st>>>(x, m, n, as, fm->entangle, mps, bond, ln);
+        mps_build_oct_kernel<HA, RP, double, double><<<grid, 8 * spc, 0, st>>>(x, m, n, as, eb, mps, bond, ln);
       } else if (fp64_qr) {
-        mps_build_oct_kernel<HA, RP, float, double><<<grid, 8 * spc, 0, st>>>(x, m, n, as, fm->entangle, mps, bond, ln);
+        mps_build_oct_kernel<HA, RP, float, double><<<grid, 8 * spc, 0, st>>>(x, m, n, as, eb, mps, bond, ln);
       } else {
-        mps_build_oct_kernel<HA, RP, float, float><<<grid, 8 * spc, 0, st>>>(x, m, n, as, fm->entangle, mps, bond, ln);
+        mps_build_oct_kernel<HA, RP, float, float><<<grid, 8 * spc, 0, st>>>(x, m, n, as, eb, mps, bond, ln);
       }
       *fused_norm = ln != nullptr;
       return launch_status();
@@ -784,10 +796,10 @@ static dk_status launch_build(const float* x, int m, int n, const dk_fmap* fm, i
     const int grid = (2 * m + lanes - 1) / lanes;
     if (c128) {
       mps_build_pair_kernel<HS, HA, RP, double><<<grid, lanes, 0, st>>>(x, m, n, double(fm->angle_scale),
-                                                                       fm->entangle, mps, bond, ln);
+                                                                       eb, mps, bond, ln);
     } else {
       mps_build_pair_kernel<HS, HA, RP, float><<<grid, lanes, 0, st>>>(x, m, n, double(fm->angle_scale),
-                                                                      fm->entangle, mps, bond, ln);
+                                                                      eb, mps, bond, ln);
     }
     *fused_norm = ln != nullptr;
   } else {
@@ -798,7 +810,7 @@ static dk_status launch_build(const float* x, int m, int n, const dk_fmap* fm, i
       if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
         return DK_ERR_CUDA;
     }
-    kern<<<m, 32, smem, st>>>(x, m, n, double(fm->angle_scale), fm->entangle, c128, mps, bond);
+    kern<<<m, 32, smem, st>>>(x, m, n, double(fm->angle_scale), eb, c128, mps, bond);
   }
   return launch_status();
 }
@@ -825,6 +837,7 @@ DK_API dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const d
   if (!ctx || !x || !fm || !mps || m < 1 || n < 1) return DK_ERR_ARG;
   if (fm->reps < 1 || fm->reps > 5) return DK_ERR_ARG;
   if (fm->qr_prec != DK_PREC_F32 && fm->qr_prec != DK_PREC_F64) return DK_ERR_ARG;
+  if (fm->block < 0) return DK_ERR_ARG;
   if (dtype != DK_C64 && dtype != DK_C128) return DK_ERR_ARG;
   const int chi = fm->chi_max;
   if (chi != 4 && chi != 8 && chi != 16 && chi != 32) return DK_ERR_UNSUPPORTED;

@@ -41,7 +41,8 @@ class DualKError(RuntimeError):
 
 class _Fmap(ctypes.Structure):
     _fields_ = [("reps", ctypes.c_int), ("angle_scale", ctypes.c_float),
-                ("entangle", ctypes.c_int), ("chi_max", ctypes.c_int), ("qr_prec", ctypes.c_int)]
+                ("entangle", ctypes.c_int), ("chi_max", ctypes.c_int), ("qr_prec", ctypes.c_int),
+                ("block", ctypes.c_int)]
 
 
 _LIB = None
@@ -132,15 +133,18 @@ def _need_cuda(t, name, dtype=None):
 
 @dataclass
 class FeatureMap:
-    """ZZ-chain feature map: reps x (H, RZ(angle_scale x_i), RZZ chain); see include/dualk.h."""
+    """ZZ-chain feature map: reps x (H, RZ(angle_scale x_i), RZZ chain); see include/dualk.h.
+    block = b >= 1 keeps only the RZZ inside blocks of b consecutive qubits (block product form)."""
     reps: int = 2
     angle_scale: float = 2.0
     entangle: bool = True
     chi_max: int = 4
     qr_prec: int = 0  # DK_PREC_F32 / DK_PREC_F64: QR arithmetic of complex64 bond-4 builds
+    block: int = 0
 
     def _c(self):
-        return _Fmap(self.reps, self.angle_scale, 1 if self.entangle else 0, self.chi_max, self.qr_prec)
+        return _Fmap(self.reps, self.angle_scale, 1 if self.entangle else 0, self.chi_max, self.qr_prec,
+                     self.block)
 
 
 @dataclass

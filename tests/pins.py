@@ -164,3 +164,54 @@ def mix_limits() -> float:
     e = float(np.max(np.abs(gram.dual_kernel(kq, kc, 1.0) - kq)))
     e = max(e, float(np.max(np.abs(gram.dual_kernel(kq, kc, 0.0) - kc))))
     return e
+
+
+def _blocks(n: int, b: int):
+    return [(s, min(s + b, n)) for s in range(0, n, b)]
+
+
+def bps_statevector_vs_kron(n: int = 11, reps: int = 2, b: int = 4, seed: int = 21) -> float:
+    """Block product structure (§II-C): the oracle statevector with blocks of b qubits vs
+    the Kronecker product of the blocks' own chain states from dense unitaries (form 5)."""
+    from functools import reduce
+    x = synthetic.uniform_angles(3, n, seed)
+    err = 0.0
+    for row in x:
+        got = circuit.statevector(row, reps, block=b)
+        ref = reduce(np.kron, [cf.dense_state(row[s:e], reps) for s, e in _blocks(n, b)])
+        err = max(err, float(np.max(np.abs(got - ref))))
+    return err
+
+
+def bps_log_kernel_vs_block_products(n: int = 40, reps: int = 2, b: int = 6, seed: int = 22) -> float:
+    """Oracle MPS + transfer log K_q with blocks of b qubits vs the sum over blocks of
+    log |<psi_B(x)|psi_B(y)>|^2, each block state from dense unitaries (form 5). Exact at
+    any n, so it pins the oracle's long-chain path at reps >= 2 (largest relative error)."""
+    x = synthetic.uniform_angles(4, n, seed)
+    sites, _ = mps.build_mps(x, reps, block=b)
+    ii, jj = np.triu_indices(4, 1)
+    _, lkq = gram.pair_values(sites, sites, ii, jj)
+    err = 0.0
+    for p, (i, j) in enumerate(zip(ii, jj)):
+        ref = 0.0
+        for s, e in _blocks(n, b):
+            a = np.vdot(cf.dense_state(x[i, s:e], reps), cf.dense_state(x[j, s:e], reps))
+            ref += np.log(abs(a) ** 2)
+        err = max(err, abs(lkq[p] - ref) / max(1.0, abs(ref)))
+    return err
+
+
+def bps_bond_ranks(n: int = 17, reps: int = 2, b: int = 5) -> int:
+    """Bond dimensions of the oracle MPS with blocks of b qubits vs the exact Schmidt ranks:
+    1 at a block boundary, min(2^(k - start), 2^(end - k), 2^reps) inside a block. Returns
+    the number of mismatching bonds."""
+    x = synthetic.uniform_angles(3, n, 23)
+    sites, _ = mps.build_mps(x, reps, block=b)
+    dims = mps.bond_dims(sites)
+    bad = 0
+    for k in range(1, n):
+        s = (k // b) * b
+        e = min(s + b, n)
+        ref = 1 if k == s else min(2 ** (k - s), 2 ** (e - k), 2 ** reps)
+        bad += int(dims[k] != ref)
+    return bad

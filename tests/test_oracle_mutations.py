@@ -44,6 +44,8 @@ PIN_SUITE = [
     ("mps vs sv r3", lambda: pins.mps_vs_statevector(7, 3), 1e-11),
     ("ranks", lambda: float(pins.bond_ranks(7, 2)), 0.5),
     ("deep underflow", deep_underflow, 1e-9),
+    ("bps kron", lambda: pins.bps_statevector_vs_kron(9, 2, 4), 1e-12),
+    ("bps blocks", lambda: pins.bps_log_kernel_vs_block_products(20, 2, 6), 1e-10),
     ("rbf", pins.rbf_vs_library, 1e-12),
     ("mix", pins.mix_limits, 1e-12),
 ]
@@ -123,7 +125,18 @@ def _mut_hadamard_sign(mp):
     mp.setattr(mps, "hadamard", lambda: h)
 
 
+def _mut_block_boundary_shifted(mp):
+    def bonds(n, block=0):
+        i = real_np.arange(max(n - 1, 0))
+        if block <= 0:
+            return real_np.ones(i.shape, dtype=bool)
+        return ((i + 1) // block) == ((i + 2) // block)
+    mp.setattr(circuit, "entangled_bonds", bonds)
+    mp.setattr(mps, "entangled_bonds", bonds)
+
+
 MUTATIONS = {
+    "block boundary shifted by one": _mut_block_boundary_shifted,
     "rz angle halved": _mut_rz_half,
     "rzz sign flipped": _mut_rzz_sign,
     "entangler uses wrong neighbour": _mut_entangler_index,

@@ -65,6 +65,33 @@ def test_bond_dimensions_are_exact_ranks(reps):
     assert pins.bond_ranks(9, reps) == 0
 
 
+@pytest.mark.parametrize("n,reps,b", [(11, 2, 4), (12, 3, 6), (9, 2, 3), (7, 2, 7), (6, 2, 1)])
+def test_bps_statevector_is_kron_of_blocks(n, reps, b):
+    # b = n is the plain chain and b = 1 has no entanglers (cross-checks both ends)
+    assert pins.bps_statevector_vs_kron(n, reps, b) < 1e-12
+
+
+@pytest.mark.parametrize("n,reps,b", [(40, 2, 6), (784, 2, 6), (100, 3, 5)])
+def test_bps_log_kernel_is_sum_over_blocks(n, reps, b):
+    # n = 784 at two repetitions: the long-chain path (rescaling, log domain) exactly pinned
+    assert pins.bps_log_kernel_vs_block_products(n, reps, b) < 1e-10
+
+
+@pytest.mark.parametrize("reps", [1, 2, 3])
+def test_bps_bond_dimensions(reps):
+    assert pins.bps_bond_ranks(17, reps, 5) == 0
+
+
+def test_block_limits():
+    x = synthetic.uniform_angles(2, 9, 24)
+    for row in x:
+        np.testing.assert_allclose(circuit.statevector(row, 2, block=9), circuit.statevector(row, 2), atol=1e-15)
+        np.testing.assert_allclose(circuit.statevector(row, 2, block=1),
+                                   circuit.statevector(row, 2, entangle=False), atol=1e-15)
+    assert circuit.entangled_bonds(7, 3).tolist() == [True, True, False, True, True, False]
+    assert circuit.entangled_bonds(4, 0).tolist() == [True, True, True]
+
+
 def test_large_n_ising_log_domain():
     # n = 784, one repetition with entanglers: off-diagonal K_q far below 1e-300.
     assert pins.large_n_ising(784) < 1e-10
