@@ -12,6 +12,9 @@ What it computes, in plain NumPy float64 / complex128 and in the paper's order:
   statevector simulation, for n <= 14;
 * ``mps``      -- the same state as a matrix product state, built gate by gate with
   two-site SVD splits (time-evolving block decimation), for any n;
+* ``blocks``   -- the MPS of a block-structured map (entanglers only inside blocks of b
+  qubits, chain or all-to-all inside) from its dense block states by SVD sweeps with the
+  cutoff / cap truncation and the discarded weight;
 * ``gram``     -- the quantum kernel K_q = |<psi(x_i)|psi(x_j)>|^2 (§II-C, Eqs. 7-10)
   from the MPS by a left-to-right transfer contraction with power-of-two rescaling,
   the RBF kernel (§II-B, Eq. 3) and the linear mix (§II-D, Eq. 11);

@@ -50,24 +50,43 @@ def entangled_bonds(n: int, block: int = 0) -> np.ndarray:
     return (i // block) == ((i + 1) // block)
 
 
+def entangled_pairs(n: int, block: int = 0, entangler: str = "chain"):
+    """The qubit pairs (i, j), i < j, that carry an RZZ(2 (pi - x_i)(pi - x_j)).
+
+    entangler = "chain": neighbouring pairs (i, i+1) inside a block (``entangled_bonds``).
+    entangler = "full": every pair inside a block (all-to-all two-local ZZ within each block;
+    block = 0 makes the whole register one block).
+    """
+    if entangler == "chain":
+        return [(i, i + 1) for i in np.flatnonzero(entangled_bonds(n, block))]
+    if entangler != "full":
+        raise ValueError(f"unknown entangler {entangler!r}")
+    b = n if block <= 0 else block
+    return [(i, j) for i in range(n) for j in range(i + 1, n) if i // b == j // b]
+
+
 def _apply_1q(psi: np.ndarray, gate: np.ndarray, q: int) -> np.ndarray:
     out = np.tensordot(gate, psi, axes=([1], [q]))
     return np.moveaxis(out, 0, q)
 
 
-def _apply_zz(psi: np.ndarray, theta: float, q: int) -> np.ndarray:
+def _apply_zz(psi: np.ndarray, theta: float, q: int, r: int | None = None) -> np.ndarray:
+    """RZZ(theta) on qubits q and r (default q + 1)."""
+    r = q + 1 if r is None else r
     n = psi.ndim
     shape = [1] * n
     shape[q] = 2
-    shape[q + 1] = 2
+    shape[r] = 2
     return psi * rzz_phases(theta).reshape(shape)
 
 
-def statevector(x, reps: int, angle_scale: float = 2.0, entangle: bool = True, block: int = 0) -> np.ndarray:
+def statevector(x, reps: int, angle_scale: float = 2.0, entangle: bool = True, block: int = 0,
+                entangler: str = "chain") -> np.ndarray:
     """|psi(x)> = [U_ZZ(x) . (x)_i RZ(angle_scale x_i) . H^(x)n]^reps |0...0>, flattened.
 
-    U_ZZ holds the RZZ of every pair that ``entangled_bonds(n, block)`` lists. Qubit 0 is
-    the most significant bit of the flattened index.
+    U_ZZ holds the RZZ of every pair that ``entangled_pairs(n, block, entangler)`` lists
+    (the gates are diagonal and commute). Qubit 0 is the most significant bit of the
+    flattened index.
     """
     x = np.asarray(x, dtype=np.float64)
     n = x.shape[0]
@@ -77,24 +96,22 @@ def statevector(x, reps: int, angle_scale: float = 2.0, entangle: bool = True, b
     psi[(0,) * n] = 1.0
     h = hadamard()
     phis = single_qubit_angles(x, angle_scale)
-    thetas = entangler_angles(x)
-    bonds = entangled_bonds(n, block)
+    pairs = entangled_pairs(n, block, entangler)
     for _ in range(reps):
         for q in range(n):
             psi = _apply_1q(psi, h, q)
         for q in range(n):
             psi = _apply_1q(psi, rz(phis[q]), q)
         if entangle:
-            for q in range(n - 1):
-                if bonds[q]:
-                    psi = _apply_zz(psi, thetas[q], q)
+            for q, r in pairs:
+                psi = _apply_zz(psi, 2.0 * (np.pi - x[q]) * (np.pi - x[r]), q, r)
     return psi.reshape(-1)
 
 
 def kernel_matrix(x_rows, x_cols, reps: int, angle_scale: float = 2.0, entangle: bool = True,
-                  block: int = 0) -> np.ndarray:
+                  block: int = 0, entangler: str = "chain") -> np.ndarray:
     """K_q[i, j] = |<psi(x_i)|psi(x_j)>|^2 (Eq. 7) by brute-force statevectors."""
-    a = np.stack([statevector(x, reps, angle_scale, entangle, block) for x in np.asarray(x_rows)])
-    b = np.stack([statevector(x, reps, angle_scale, entangle, block) for x in np.asarray(x_cols)])
+    a = np.stack([statevector(x, reps, angle_scale, entangle, block, entangler) for x in np.asarray(x_rows)])
+    b = np.stack([statevector(x, reps, angle_scale, entangle, block, entangler) for x in np.asarray(x_cols)])
     amp = a.conj() @ b.T
     return np.abs(amp) ** 2

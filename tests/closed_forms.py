@@ -85,8 +85,9 @@ def two_qubit_amplitude(x, y, c=2.0):
     return 0.5 * (np.exp(1j * h1) * np.cos(h2 + j1) + np.exp(-1j * h1) * np.cos(h2 - j1))
 
 
-def dense_state(x, reps, c=2.0, entangle=True):
-    """Form 5: U(x)|0...0> from Kronecker products of expm'd Pauli generators (n <= 6)."""
+def dense_state(x, reps, c=2.0, entangle=True, all_pairs=False):
+    """Form 5: U(x)|0...0> from Kronecker products of expm'd Pauli generators (n <= 8);
+    all_pairs puts the ZZ generator on every pair (q, r), q < r, not just neighbours."""
     from functools import reduce
     from scipy.linalg import expm
 
@@ -107,9 +108,11 @@ def dense_state(x, reps, c=2.0, entangle=True):
         for q in range(n):
             u = expm(-0.5j * c * x[q] * place({q: pauli_z})) @ u
         if entangle:
-            for q in range(n - 1):
-                t = 2.0 * (np.pi - x[q]) * (np.pi - x[q + 1])
-                u = expm(-0.5j * t * place({q: pauli_z, q + 1: pauli_z})) @ u
+            pairs = [(q, r) for q in range(n) for r in range(q + 1, n)] if all_pairs else \
+                [(q, q + 1) for q in range(n - 1)]
+            for q, r in pairs:
+                t = 2.0 * (np.pi - x[q]) * (np.pi - x[r])
+                u = expm(-0.5j * t * place({q: pauli_z, r: pauli_z})) @ u
     return u[:, 0]
 
 

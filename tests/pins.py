@@ -215,3 +215,70 @@ def bps_bond_ranks(n: int = 17, reps: int = 2, b: int = 5) -> int:
         ref = 1 if k == s else min(2 ** (k - s), 2 ** (e - k), 2 ** reps)
         bad += int(dims[k] != ref)
     return bad
+
+
+def full_statevector_vs_dense(n: int = 6, reps: int = 2, b: int = 4, seed: int = 25) -> float:
+    """All-to-all ZZ inside blocks: the oracle statevector vs the Kronecker product of dense
+    expm unitaries with the ZZ generator on every pair of each block (form 5)."""
+    from functools import reduce
+    x = synthetic.uniform_angles(3, n, seed)
+    err = 0.0
+    for row in x:
+        got = circuit.statevector(row, reps, block=b, entangler="full")
+        ref = reduce(np.kron, [cf.dense_state(row[s:e], reps, all_pairs=True) for s, e in _blocks(n, b)])
+        err = max(err, float(np.max(np.abs(got - ref))))
+    return err
+
+
+def block_mps_vs_products(n: int = 30, reps: int = 2, b: int = 6, entangler: str = "full", seed: int = 26) -> float:
+    """Untruncated MPS from block states + the transfer Gram vs the sum over blocks of log
+    overlaps of dense block states (form 5), largest relative error of log K_q."""
+    from oracle import blocks
+    x = synthetic.uniform_angles(4, n, seed)
+    sites, disc = blocks.mps_from_block_states(x, reps, b, entangler, cutoff=1e-14)
+    ii, jj = np.triu_indices(4, 1)
+    _, lkq = gram.pair_values(sites, sites, ii, jj)
+    err = float(np.max(disc))
+    for p, (i, j) in enumerate(zip(ii, jj)):
+        ref = 0.0
+        for s, e in _blocks(n, b):
+            a = np.vdot(cf.dense_state(x[i, s:e], reps, all_pairs=entangler == "full"),
+                        cf.dense_state(x[j, s:e], reps, all_pairs=entangler == "full"))
+            ref += np.log(abs(a) ** 2)
+        err = max(err, abs(lkq[p] - ref) / max(1.0, abs(ref)))
+    return err
+
+
+def block_mps_ranks(b: int = 7, reps: int = 2, seed: int = 27) -> int:
+    """Bond dimensions of the untruncated block MPS vs the numerical Schmidt ranks of the
+    dense block state (form 5) at every cut; number of mismatches."""
+    from oracle import blocks, mps as omps
+    x = synthetic.uniform_angles(1, b, seed)
+    sites, _ = blocks.mps_from_block_states(x, reps, b, "full", cutoff=1e-10)
+    dims = omps.bond_dims(sites)
+    psi = cf.dense_state(x[0], reps, all_pairs=True)
+    bad = 0
+    for k in range(1, b):
+        s = np.linalg.svd(psi.reshape(2 ** k, -1), compute_uv=False)
+        bad += int(dims[k] != int(np.sum(s > 1e-10 * s[0])))
+    return bad
+
+
+def single_cut_truncation(reps: int = 2, seed: int = 28) -> float:
+    """A 6-qubit all-to-all block capped at bond 4: only the middle cut (rank 8) truncates.
+    Eckart-Young: the discarded weight is the squared tail of that cut's singular values of
+    the dense state, and the renormalised result has |<psi_t|psi>|^2 = 1 - discarded.
+    Returns the larger deviation of the two."""
+    from oracle import blocks, mps as omps
+    x = synthetic.uniform_angles(2, 6, seed)
+    sites, disc = blocks.mps_from_block_states(x, reps, 6, "full", chi_cap=4)
+    err = 0.0
+    for i in range(2):
+        psi = cf.dense_state(x[i], reps, all_pairs=True)
+        s = np.linalg.svd(psi.reshape(8, 8), compute_uv=False)
+        tail = float(np.sum(s[4:] ** 2) / np.sum(s ** 2))
+        fid = abs(np.vdot(omps.to_statevector(sites, i), psi)) ** 2
+        err = max(err, abs(disc[i] - tail), abs(fid - (1.0 - tail)))
+        if tail < 1e-6:  # the pin needs a truncation that bites
+            return 1.0
+    return err

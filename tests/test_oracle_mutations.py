@@ -9,7 +9,7 @@ import pytest
 
 import closed_forms as cf
 import pins
-from oracle import circuit, gram, mps
+from oracle import blocks, circuit, gram, mps
 from paper_2602_01330_gb300 import synthetic
 
 
@@ -46,6 +46,9 @@ PIN_SUITE = [
     ("deep underflow", deep_underflow, 1e-9),
     ("bps kron", lambda: pins.bps_statevector_vs_kron(9, 2, 4), 1e-12),
     ("bps blocks", lambda: pins.bps_log_kernel_vs_block_products(20, 2, 6), 1e-10),
+    ("full sv", lambda: pins.full_statevector_vs_dense(5, 2, 4), 1e-12),
+    ("block mps", lambda: pins.block_mps_vs_products(12, 2, 6), 1e-10),
+    ("single cut", pins.single_cut_truncation, 1e-12),
     ("rbf", pins.rbf_vs_library, 1e-12),
     ("mix", pins.mix_limits, 1e-12),
 ]
@@ -135,7 +138,29 @@ def _mut_block_boundary_shifted(mp):
     mp.setattr(mps, "entangled_bonds", bonds)
 
 
+def _mut_full_pairs_short_range(mp):
+    good = circuit.entangled_pairs
+
+    def pairs(n, block=0, entangler="chain"):
+        return [(i, j) for i, j in good(n, block, entangler) if j - i <= 2]
+    mp.setattr(circuit, "entangled_pairs", pairs)
+
+
+def _mut_keeps_smallest(mp):
+    def svd(a, full_matrices=True):
+        u, s, vh = real_np.linalg.svd(a, full_matrices=full_matrices)
+        return u[..., ::-1], s[..., ::-1], vh[..., ::-1, :]
+    mp.setattr(blocks, "np", _Proxy(real_np, linalg=_Proxy(real_np.linalg, svd=svd)))
+
+
+def _mut_no_renormalisation(mp):
+    mp.setattr(blocks, "np", _Proxy(real_np, sqrt=lambda a: real_np.ones_like(a)))
+
+
 MUTATIONS = {
+    "full entangler skips long-range pairs": _mut_full_pairs_short_range,
+    "truncation keeps the smallest singular values": _mut_keeps_smallest,
+    "truncation not renormalised": _mut_no_renormalisation,
     "block boundary shifted by one": _mut_block_boundary_shifted,
     "rz angle halved": _mut_rz_half,
     "rzz sign flipped": _mut_rzz_sign,

@@ -92,6 +92,41 @@ def test_block_limits():
     assert circuit.entangled_bonds(4, 0).tolist() == [True, True, True]
 
 
+@pytest.mark.parametrize("n,reps,b", [(6, 2, 4), (8, 2, 8), (7, 3, 3)])
+def test_full_entangler_statevector_vs_dense(n, reps, b):
+    assert pins.full_statevector_vs_dense(n, reps, b) < 1e-12
+
+
+@pytest.mark.parametrize("n,reps,b,ent", [(30, 2, 6, "full"), (23, 3, 5, "full"), (20, 2, 5, "chain"),
+                                          (96, 2, 8, "full")])
+def test_block_mps_untruncated_vs_block_products(n, reps, b, ent):
+    assert pins.block_mps_vs_products(n, reps, b, ent) < 1e-10
+
+
+@pytest.mark.parametrize("b,reps", [(7, 2), (8, 3), (6, 1)])
+def test_block_mps_ranks_are_schmidt_ranks(b, reps):
+    assert pins.block_mps_ranks(b, reps) == 0
+
+
+@pytest.mark.parametrize("reps", [2, 3])
+def test_single_cut_truncation_eckart_young(reps):
+    assert pins.single_cut_truncation(reps) < 1e-12
+
+
+def test_block_mps_chain_matches_tebd():
+    """The chain entangler through block states + SVD equals the gate-by-gate TEBD MPS with
+    the same blocks: same log K_q and the same bond dimensions (cutoff removes the exact zeros)."""
+    from oracle import blocks
+    x = synthetic.uniform_angles(4, 26, 29)
+    a, _ = blocks.mps_from_block_states(x, 2, 7, "chain")
+    t, _ = mps.build_mps(x, 2, block=7)
+    ii, jj = np.triu_indices(4, 1)
+    la = gram.pair_values(a, a, ii, jj)[1]
+    lt = gram.pair_values(t, t, ii, jj)[1]
+    np.testing.assert_allclose(la, lt, rtol=1e-11)
+    assert mps.bond_dims(a) == mps.bond_dims(t)
+
+
 def test_large_n_ising_log_domain():
     # n = 784, one repetition with entanglers: off-diagonal K_q far below 1e-300.
     assert pins.large_n_ising(784) < 1e-10
