@@ -148,6 +148,44 @@ dk_status dk_mps_build(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap*
                        dk_dtype dtype, void* mps, int32_t* bond_dims, float* log_norm,
                        void* stream);
 
+/* Entanglers inside a block for dk_mps_build_blocks. */
+#define DK_ENT_CHAIN 0 /* RZZ on neighbouring pairs (i, i+1) of the block */
+#define DK_ENT_FULL 1  /* RZZ(2 (pi - x_i)(pi - x_j)) on every pair i < j of the block */
+
+/* MPS of a block-structured feature map (§II-C: entanglers only inside blocks of b
+ * consecutive qubits, dk_fmap.block) from its block statevectors, with SVD truncation.
+ * Per sample and block (b <= 12 qubits): the dense 2^b statevector of the block in FP64
+ * (per repetition H on every qubit, RZ(angle_scale x_q), then the RZZ of every entangled
+ * pair), then a left-to-right sweep of singular value decompositions (one-sided Jacobi in
+ * FP64): at each cut the singular values s > cutoff * s_0 are kept, at most chi_max / 2 of
+ * them, rescaled to the norm of the whole spectrum, and the discarded squared weight is
+ * accumulated. The bond at a block boundary is 1. With DK_ENT_FULL the exact bond inside a
+ * block reaches 2^min(q, b - q) at the cut after q qubits, beyond the 2^reps of the chain.
+ *   x          m x n float32 features (device)
+ *   fm         reps 1..5, angle_scale, entangle (0: product state), chi_max 4, 8, 16 or 32
+ *              (stored width; kept bond <= chi_max / 2), block 1..12 (0: one block, n <= 12);
+ *              qr_prec is ignored (FP64 throughout)
+ *   entangler  DK_ENT_CHAIN or DK_ENT_FULL
+ *   cutoff     relative singular value cutoff, 0 <= cutoff < 1 (1e-10 drops only numerical
+ *              zeros)
+ *   mps        dk_mps_bytes(m, n, chi_max, dtype) bytes (device, written). Layout as
+ *              dk_mps_build: a site tensor B_s[a][j] (left bond a, right bond j < chi_max/2)
+ *              is stored at block s, column j, left positions a and chi_max/2 + a, so the
+ *              Gram calls for chi_max contract the general MPS unchanged.
+ *   bond_dims  n + 1 int32 (device, written, may be NULL): kept bond left of each site, the
+ *              largest over the samples (1 at block starts and at index n)
+ *   log_norm   m floats (device, written, may be NULL): as dk_mps_build
+ *   discarded  m floats (device, written, may be NULL): discarded squared weight of each
+ *              sample summed over its cuts (0 when nothing was truncated)
+ * One CTA per sample; the call allocates nothing.
+ * Errors: DK_ERR_ARG (NULL ctx/x/fm/mps, m or n < 1, reps outside 1..5, unknown entangler,
+ *         cutoff outside [0, 1), dtype, misaligned mps), DK_ERR_UNSUPPORTED (block < 0 or a
+ *         block above 12 qubits, chi_max not in {4, 8, 16, 32}, log_norm for a chi_max /
+ *         dtype without a Gram kernel), DK_ERR_CUDA. */
+dk_status dk_mps_build_blocks(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm, int entangler,
+                              double cutoff, dk_dtype dtype, void* mps, int32_t* bond_dims, float* log_norm,
+                              float* discarded, void* stream);
+
 /* ln|<psi~_i|psi~_i>| of the stored (rounded) MPS of m samples, computed with the
  * arithmetic of precision `prec`, so that a Gram call with the same precision and these
  * normalisers gives K_q(x, x) = 1 exactly (§II-C, Eq. 7 for unit-norm states).

@@ -27,7 +27,7 @@ EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_
             "dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows", "dk_gram_config_count",
             "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout", "dk_self_overlap",
             "dk_svm_ovo_train", "dk_svm_ovo_predict", "dk_gram_stats", "dk_pca_workspace_bytes", "dk_pca_fit",
-            "dk_pca_transform", "dk_pca_fit_noalloc")
+            "dk_pca_transform", "dk_pca_fit_noalloc", "dk_mps_build_blocks")
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 PCA_MAX_FEATURES = 4096  # DK_PCA_MAX_FEATURES
 PCA_NOALLOC_MAX_FEATURES = 256  # DK_PCA_NOALLOC_MAX_FEATURES
@@ -68,6 +68,9 @@ def _lib():
     lib.dk_mps_bytes.restype = ctypes.c_size_t
     lib.dk_mps_build.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, vp, vp, vp, vp]
     lib.dk_mps_build.restype = i32
+    lib.dk_mps_build_blocks.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, ctypes.c_double, i32, vp, vp,
+                                        vp, vp, vp]
+    lib.dk_mps_build_blocks.restype = i32
     lib.dk_gram_tile.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, i32,
                                  vp, vp, vp, vp, f32, f32, i32, vp, vp, vp, vp, i64, i32, vp]
     lib.dk_gram_tile.restype = i32
@@ -251,6 +254,26 @@ def mps_build(ctx: Context, x: torch.Tensor, fmap: FeatureMap, dtype: int = DK_C
     _check(_lib().dk_mps_build(ctx.handle, _ptr(x), m, n, ctypes.byref(fm), dtype, _ptr(out), _ptr(bond),
                                _ptr(lnorm), _stream(stream)), "dk_mps_build")
     return MPS(out, m, n, fmap.chi_max, dtype, bond, lnorm, x, fmap=fmap)
+
+
+DK_ENT_CHAIN, DK_ENT_FULL = 0, 1
+
+
+def mps_build_blocks(ctx: Context, x: torch.Tensor, fmap: FeatureMap, entangler: int = DK_ENT_FULL,
+                     cutoff: float = 1e-10, dtype: int = DK_C64, stream=None):
+    """dk_mps_build_blocks: MPS of a block-structured map (fmap.block qubits per block) from
+    block statevectors with SVD truncation. Returns (MPS, discarded weight per sample)."""
+    _need_cuda(x, "x", torch.float32)
+    m, n = x.shape
+    out = torch.empty(mps_bytes(m, n, fmap.chi_max, dtype), dtype=torch.uint8, device=x.device)
+    bond = torch.empty(n + 1, dtype=torch.int32, device=x.device)
+    log_norm = torch.empty(m, dtype=torch.float32, device=x.device)
+    disc = torch.empty(m, dtype=torch.float32, device=x.device)
+    fm = fmap._c()
+    _check(_lib().dk_mps_build_blocks(ctx.handle, _ptr(x), m, n, ctypes.byref(fm), int(entangler), float(cutoff),
+                                      dtype, _ptr(out), _ptr(bond), _ptr(log_norm), _ptr(disc), _stream(stream)),
+           "dk_mps_build_blocks")
+    return MPS(out, m, n, fmap.chi_max, dtype, bond, log_norm, x, fmap=fmap), disc
 
 
 def self_overlap(ctx: Context, mps: "MPS", prec: int, out: torch.Tensor | None = None, stream=None):
