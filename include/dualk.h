@@ -186,6 +186,51 @@ dk_status dk_mps_build_blocks(dk_ctx* ctx, const float* x, int m, int n, const d
                               double cutoff, dk_dtype dtype, void* mps, int32_t* bond_dims, float* log_norm,
                               float* discarded, void* stream);
 
+/* Block statevectors of a block-structured feature map (§II-C: entanglers only inside
+ * blocks of b consecutive qubits, chain or all-to-all as for dk_mps_build_blocks). The state
+ * is the Kronecker product of its blocks' states, so the overlap of Eq. 9 factorises over
+ * the blocks and dk_gram_blocks contracts it exactly, block by block, with no MPS bond.
+ * Bytes: nb * m * dpad * 8, nb = ceil(n / b) blocks, dpad = max(2^b, 16) complex64
+ * amplitudes per (block, sample); 0 if block is outside 0..12 (0: one block, n <= 12). */
+size_t dk_block_states_bytes(int m, int n, int block);
+
+/*   x         m x n float32 features (device)
+ *   fm        reps 1..5, angle_scale, entangle (0: product state), block (see above);
+ *             chi_max and qr_prec are ignored
+ *   entangler DK_ENT_CHAIN or DK_ENT_FULL
+ *   states    dk_block_states_bytes(m, n, fm->block) bytes (device, written), layout
+ *             [block][sample][dpad] complex64: the block's 2^b amplitudes (qubit 0 of the
+ *             block most significant), computed in FP64 and rounded once; zeros beyond
+ *             2^b and beyond the 2^(n mod b) amplitudes of a short last block
+ *   log_norm  m floats (device, written, may be NULL): ln|<psi~_i|psi~_i>| of the rounded
+ *             states by the arithmetic of dk_gram_blocks, so that K_q(x, x) = 1 exactly
+ * Errors: DK_ERR_ARG (NULL pointers, m or n < 1, reps, entangler, misaligned states),
+ *         DK_ERR_UNSUPPORTED (block outside 0..12 or above 12 qubits, m > 65535),
+ *         DK_ERR_CUDA. */
+dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm, int entangler,
+                          void* states, float* log_norm, void* stream);
+
+/* A block of the Gram matrix of a block-structured map from block statevectors, outputs
+ * and epilogue as dk_gram_tile (§II-C Eqs. 8-10 factorised over blocks; §II-B Eq. 3;
+ * §II-D Eq. 11): for each pair, a = prod_B <psi_B(x_i)|psi_B(x_j)> with each factor a
+ * complex dot product of 2^b amplitudes in FP32 (CUDA cores), ln|a| accumulated as a
+ * mantissa and binary exponent (never underflows); log K_q = 2 ln|a| - ln N_i - ln N_j,
+ * K_q, K_c = exp(-gamma ||x_i - x_j||^2), K = w K_q + (1 - w) K_c.
+ *   states_rows / states_cols  dk_block_states output for m_rows / m_cols samples, same n
+ *                              and block; lnorm_rows / lnorm_cols their log_norm
+ *   x_rows / x_cols            features (needed for K_c: kc_out, or k_out with w != 1)
+ *   k_out, kq_out, kc_out, logkq_out  nrows x ncols float32 (device, any may be NULL, not
+ *                              all), row stride ld; symmetric (rows == cols, same range)
+ *                              computes each unordered pair once and writes both entries
+ * Errors: DK_ERR_ARG (NULL inputs, ranges outside the sample counts, ld < ncols, no
+ *         output, symmetric with different rows and columns, K_c needed without x),
+ *         DK_ERR_UNSUPPORTED (block), DK_ERR_CUDA. */
+dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows, const void* states_cols, int m_cols,
+                         int n, int block, int row0, int nrows, int col0, int ncols, const float* lnorm_rows,
+                         const float* lnorm_cols, const float* x_rows, const float* x_cols, float gamma, float w,
+                         float* k_out, float* kq_out, float* kc_out, float* logkq_out, long long ld, int symmetric,
+                         void* stream);
+
 /* ln|<psi~_i|psi~_i>| of the stored (rounded) MPS of m samples, computed with the
  * arithmetic of precision `prec`, so that a Gram call with the same precision and these
  * normalisers gives K_q(x, x) = 1 exactly (§II-C, Eq. 7 for unit-norm states).

@@ -29,6 +29,7 @@
 // chi_max Gram kernels unchanged.
 #include <math.h>
 
+#include "block_state.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -36,10 +37,9 @@ namespace dk {
 namespace bsvd {
 
 constexpr int NT = 128;         // threads per CTA
-constexpr int MAXB = 12;        // qubits per block
+constexpr int MAXB = blockstate::MAXB;
 constexpr int MAXR = 32;        // rows of M: 2 x kept bond <= chi_max <= 32
 constexpr int MAX_SWEEPS = 40;  // Jacobi sweeps per cut (quadratic convergence needs ~6-10)
-constexpr double PI_D = 3.14159265358979323846;
 constexpr double ORTH_TOL = 1e-14;  // rotate while |<p,q>| > tol sqrt(|p|^2 |q|^2)
 // The remainder always has unit Frobenius norm (the left factors are isometries and the kept
 // spectrum is rescaled to the whole), so a row with squared norm below FLOOR2 is rounding
@@ -62,8 +62,7 @@ struct Shared {
   int rowbase[MAXR];      // offset of each row of M in the state buffer
   int nextbase[MAXR];
   int perm[MAXR];         // rows by decreasing norm
-  double hq[MAXB];        // scale x_q / 2
-  double jq[MAXB][MAXB];  // (pi - x_q)(pi - x_r) for entangled q < r, else 0
+  blockstate::Coeffs coef;
   double scale;           // renormalisation of the kept rows
   int keep;               // kept bond of the current cut
 };
@@ -100,40 +99,7 @@ __global__ void __launch_bounds__(NT) block_svd_kernel(const float* __restrict__
     const int bl = min(b, n - start);
     const int dim = 1 << bl;
     // ---- 1. block statevector ----
-    if (tid < bl) S.hq[tid] = 0.5 * angle_scale * double(xs[start + tid]);
-    for (int e = tid; e < MAXB * MAXB; e += NT) {
-      const int q = e / MAXB, r = e % MAXB;
-      const bool on = q < bl && r < bl && q < r && (pairs_kind == DK_ENT_FULL ? true : (pairs_kind == DK_ENT_CHAIN && r == q + 1));
-      S.jq[q][r] = on ? (PI_D - double(xs[start + q])) * (PI_D - double(xs[start + r])) : 0.0;
-    }
-    for (int e = tid; e < dim; e += NT) psi[e] = make_double2(e == 0 ? 1.0 : 0.0, 0.0);
-    __syncthreads();
-    for (int rep = 0; rep < reps; ++rep) {
-      for (int q = 0; q < bl; ++q) {
-        const int bit = 1 << (bl - 1 - q);
-        for (int e = tid; e < dim / 2; e += NT) {
-          const int lo = ((e & ~(bit - 1)) << 1) | (e & (bit - 1));
-          const int hi = lo | bit;
-          const double2 u = psi[lo], v = psi[hi];
-          psi[lo] = make_double2((u.x + v.x) * M_SQRT1_2, (u.y + v.y) * M_SQRT1_2);
-          psi[hi] = make_double2((u.x - v.x) * M_SQRT1_2, (u.y - v.y) * M_SQRT1_2);
-        }
-        __syncthreads();
-      }
-      for (int e = tid; e < dim; e += NT) {
-        double phi = 0.0;
-        for (int q = 0; q < bl; ++q) {
-          const double zq = ((e >> (bl - 1 - q)) & 1) ? -1.0 : 1.0;
-          double pair = 0.0;
-          for (int r = q + 1; r < bl; ++r) pair += ((e >> (bl - 1 - r)) & 1) ? -S.jq[q][r] : S.jq[q][r];
-          phi += zq * (S.hq[q] + pair);
-        }
-        double sn, cs;
-        sincos(-phi, &sn, &cs);
-        psi[e] = cmul(psi[e], make_double2(cs, sn));
-      }
-      __syncthreads();
-    }
+    blockstate::build(psi, S.coef, xs + start, bl, reps, angle_scale, pairs_kind, tid, NT);
     // ---- 2. SVD sweep over the block's cuts ----
     int r = 2, c = dim / 2;
     if (tid < 2) S.rowbase[tid] = tid * c;

@@ -1,0 +1,273 @@
+// Gram matrix of a block-structured feature map from its block statevectors (§II-C).
+//
+// With entanglers only inside blocks of b consecutive qubits, |psi(x)> is the Kronecker
+// product of the blocks' states |psi_B(x_B)>, so the overlap of Eq. 9 factorises,
+//     a(x_i, x_j) = prod_B <psi_B(x_i)|psi_B(x_j)>,    log K_q = sum_B ln |G_B(i, j)|^2,
+// and each G_B is a dense complex matrix product over the 2^b amplitudes of block B: the
+// exact tensor-network contraction of a block product state, with no bond truncation.
+//
+//   * block_states_kernel: one CTA per (block, sample) builds the block's statevector in
+//     FP64 (block_state.cuh) and stores it rounded to complex64, layout
+//     states[B][i][k], k < dpad = max(2^b, KC) (a short last block is zero-padded, which
+//     leaves every overlap unchanged).
+//   * gram_blocks_kernel: 64 x 64 pair tiles, 256 threads, each 4 x 4 pairs; per block the
+//     K = dpad contraction runs in 16-amplitude chunks staged through shared memory
+//     (register prefetch of the next chunk, double buffer), FP32 FMAs on CUDA cores. After a
+//     block, each pair multiplies |G_B|^2 into a running product kept as mantissa and binary
+//     exponent (no logarithm per block, no underflow). The epilogue is the one of every Gram
+//     kernel: log K_q = 2 ln|a| - ln N_i - ln N_j, the RBF kernel (Kahan FP32 distance) and
+//     the mix.
+//   * block_selfnorm_kernel: ln N_i = ln|a(x_i, x_i)| with exactly the per-pair arithmetic of
+//     gram_blocks_kernel (same chunk order, same FMA sequence), so K_q(x, x) = 1 exactly.
+#include <math.h>
+
+#include "block_state.cuh"
+#include "common.cuh"
+#include "gram_common.cuh"
+#include "internal.h"
+
+namespace dk {
+namespace gblk {
+
+constexpr int KC = 16;           // amplitudes per chunk
+constexpr int TILE = 64;         // pairs per tile side
+constexpr int NT = 256;          // threads: 16 x 16, 4 x 4 pairs each
+constexpr int SROW = TILE + 2;   // shared row stride in complex (bank spread)
+constexpr int BUILD_NT = 128;
+
+__host__ __device__ inline int dpad_of(int b) { return (1 << b) > KC ? (1 << b) : KC; }
+
+// acc += conj(a) b, the one complex multiply-accumulate of every overlap here
+__device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
+// running product of |G_B|^2 as mantissa * 2^e
+__device__ __forceinline__ void mul_renorm(float& prod, int& e, float2 g) {
+  prod *= fmaf(g.x, g.x, g.y * g.y);
+  int ex;
+  prod = frexpf(prod, &ex);
+  e += ex;
+}
+
+__device__ __forceinline__ float half_log(float prod, int e) {
+  return 0.5f * fmaf(float(e), 0.69314718055994530942f, logf(prod));
+}
+
+__global__ void __launch_bounds__(BUILD_NT) block_states_kernel(const float* __restrict__ x, int m, int n, int b,
+                                                                int reps, double angle_scale, int pairs_kind,
+                                                                float2* __restrict__ states) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  blockstate::Coeffs& C = *reinterpret_cast<blockstate::Coeffs*>(raw);
+  double2* psi = reinterpret_cast<double2*>(raw + ((sizeof(blockstate::Coeffs) + 15) & ~size_t(15)));
+  const int blk = blockIdx.x, i = blockIdx.y;
+  const int start = blk * b;
+  const int bl = min(b, n - start);
+  const int dp = dpad_of(b);
+  blockstate::build(psi, C, x + size_t(i) * n + start, bl, reps, angle_scale, pairs_kind, threadIdx.x, BUILD_NT);
+  float2* out = states + (size_t(blk) * m + i) * dp;
+  const int dim = 1 << bl;
+  for (int k = threadIdx.x; k < dp; k += BUILD_NT)
+    out[k] = k < dim ? make_float2(float(psi[k].x), float(psi[k].y)) : make_float2(0.0f, 0.0f);
+}
+
+__global__ void __launch_bounds__(128) block_selfnorm_kernel(const float2* __restrict__ states, int m, int nb,
+                                                             int dp, float* __restrict__ log_norm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  float prod = 1.0f;
+  int e = 0;
+  for (int blk = 0; blk < nb; ++blk) {
+    const float2* a = states + (size_t(blk) * m + i) * dp;
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int k = 0; k < dp; ++k) {
+      const float2 v = a[k];
+      cmac(acc, v, v);
+    }
+    mul_renorm(prod, e, acc);
+  }
+  log_norm[i] = half_log(prod, e);
+}
+
+__global__ void __launch_bounds__(NT, 2) gram_blocks_kernel(const float2* __restrict__ sr, int m_r,
+                                                            const float2* __restrict__ sc, int m_c, int nb, int dp,
+                                                            const GramArgs p) {
+  __shared__ __align__(16) float2 As[2][KC][SROW];
+  __shared__ __align__(16) float2 Bs[2][KC][SROW];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // loader: thread -> (row lr = tid / 4, float4 q = tid % 4 and q + 4 of the row's chunk)
+  const int lr = tid >> 2, lq = tid & 3;
+  const int cpb = dp / KC;          // chunks per block
+  const int total = nb * cpb;
+  const int my_tiles = (p.ntiles > int(blockIdx.x)) ? (p.ntiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+  for (int lt = 0; lt < my_tiles; ++lt) {
+    int ti, tj;
+    decode_tile(p, TILE, TILE, int(blockIdx.x) + lt * int(gridDim.x), ti, tj);
+    const int r0 = p.row0 + ti * TILE, c0 = p.col0 + tj * TILE;
+    const int ar = min(r0 + lr, m_r - 1), bc = min(c0 + lr, m_c - 1);
+    float4 pa[2], pb[2];
+    auto fetch = [&](int c) {
+      const int blk = c / cpb, k0 = (c - blk * cpb) * KC;
+      const float4* a = reinterpret_cast<const float4*>(sr + (size_t(blk) * m_r + ar) * dp + k0);
+      const float4* bb = reinterpret_cast<const float4*>(sc + (size_t(blk) * m_c + bc) * dp + k0);
+      pa[0] = __ldg(a + lq);
+      pa[1] = __ldg(a + lq + 4);
+      pb[0] = __ldg(bb + lq);
+      pb[1] = __ldg(bb + lq + 4);
+    };
+    auto commit = [&](int buf) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * (lq + 4 * h);
+        As[buf][k][lr] = make_float2(pa[h].x, pa[h].y);
+        As[buf][k + 1][lr] = make_float2(pa[h].z, pa[h].w);
+        Bs[buf][k][lr] = make_float2(pb[h].x, pb[h].y);
+        Bs[buf][k + 1][lr] = make_float2(pb[h].z, pb[h].w);
+      }
+    };
+    float2 acc[4][4];
+    float prod[4][4];
+    int ex[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        acc[u][v] = make_float2(0.0f, 0.0f);
+        prod[u][v] = 1.0f;
+        ex[u][v] = 0;
+      }
+    fetch(0);
+    commit(0);
+    __syncthreads();
+    for (int c = 0; c < total; ++c) {
+      const int buf = c & 1;
+      if (c + 1 < total) fetch(c + 1);
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk) {
+        const float4 a01 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+        const float4 a23 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4 + 2]);
+        const float4 b01 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+        const float4 b23 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4 + 2]);
+        const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
+                              make_float2(a23.z, a23.w)};
+        const float2 bv[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w), make_float2(b23.x, b23.y),
+                              make_float2(b23.z, b23.w)};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) cmac(acc[u][v], av[u], bv[v]);
+      }
+      if ((c + 1) % cpb == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            mul_renorm(prod[u][v], ex[u][v], acc[u][v]);
+            acc[u][v] = make_float2(0.0f, 0.0f);
+          }
+      }
+      if (c + 1 < total) commit(buf ^ 1);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = r0 + ty * 4 + u, j = c0 + tx * 4 + v;
+        float d2 = 0.0f, comp = 0.0f;
+        if (p.need_kc && i < p.row0 + p.nrows && j < p.col0 + p.ncols && !(p.symmetric && j < i)) {
+          const float* xa = p.x_r + size_t(i) * p.n;
+          const float* xb = p.x_c + size_t(j) * p.n;
+          for (int f = 0; f < p.n; ++f) kahan_add_sq(d2, comp, __ldg(xa + f) - __ldg(xb + f));
+        }
+        write_pair(p, half_log(prod[u][v], ex[u][v]), d2, i, j);
+      }
+  }
+}
+
+}  // namespace gblk
+}  // namespace dk
+
+DK_API size_t dk_block_states_bytes(int m, int n, int block) {
+  if (m < 1 || n < 1 || block < 0 || block > dk::blockstate::MAXB) return 0;
+  const int b = block > 0 ? block : n;
+  if (b > dk::blockstate::MAXB) return 0;
+  const int nb = (n + b - 1) / b;
+  return size_t(nb) * m * dk::gblk::dpad_of(b) * sizeof(float2);
+}
+
+DK_API dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm, int entangler,
+                                 void* states, float* log_norm, void* stream) {
+  using namespace dk;
+  if (!ctx || !x || !fm || !states || m < 1 || n < 1) return DK_ERR_ARG;
+  if (fm->reps < 1 || fm->reps > 5) return DK_ERR_ARG;
+  if (entangler != DK_ENT_CHAIN && entangler != DK_ENT_FULL) return DK_ERR_ARG;
+  if (!aligned16(states)) return DK_ERR_ARG;
+  if (dk_block_states_bytes(m, n, fm->block) == 0) return DK_ERR_UNSUPPORTED;
+  if (m > 65535) return DK_ERR_UNSUPPORTED;  // grid y
+  const int b = fm->block > 0 ? fm->block : n;
+  const int nb = (n + b - 1) / b;
+  const int kind = fm->entangle ? entangler : -1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t smem = ((sizeof(blockstate::Coeffs) + 15) & ~size_t(15)) + (size_t(1) << b) * sizeof(double2);
+  if (cudaFuncSetAttribute(gblk::block_states_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+      cudaSuccess)
+    return DK_ERR_CUDA;
+  gblk::block_states_kernel<<<dim3(nb, m), gblk::BUILD_NT, smem, st>>>(x, m, n, b, fm->reps, double(fm->angle_scale),
+                                                                      kind, static_cast<float2*>(states));
+  if (log_norm)
+    gblk::block_selfnorm_kernel<<<(m + 127) / 128, 128, 0, st>>>(static_cast<const float2*>(states), m, nb,
+                                                                 gblk::dpad_of(b), log_norm);
+  return launch_status();
+}
+
+DK_API dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows, const void* states_cols, int m_cols,
+                                int n, int block, int row0, int nrows, int col0, int ncols, const float* lnorm_rows,
+                                const float* lnorm_cols, const float* x_rows, const float* x_cols, float gamma,
+                                float w, float* k_out, float* kq_out, float* kc_out, float* logkq_out, long long ld,
+                                int symmetric, void* stream) {
+  using namespace dk;
+  if (!ctx || !states_rows || !states_cols || !lnorm_rows || !lnorm_cols) return DK_ERR_ARG;
+  if (m_rows < 1 || m_cols < 1 || n < 1 || nrows < 0 || ncols < 0 || row0 < 0 || col0 < 0) return DK_ERR_ARG;
+  if (row0 + nrows > m_rows || col0 + ncols > m_cols) return DK_ERR_ARG;
+  if (dk_block_states_bytes(1, n, block) == 0) return DK_ERR_UNSUPPORTED;
+  if (!aligned16(states_rows) || !aligned16(states_cols)) return DK_ERR_ARG;
+  if (!k_out && !kq_out && !kc_out && !logkq_out) return DK_ERR_ARG;
+  if (ld < ncols) return DK_ERR_ARG;
+  if (symmetric && (row0 != col0 || nrows != ncols || states_rows != states_cols)) return DK_ERR_ARG;
+  const bool need_kc = kc_out || (k_out && w != 1.0f);
+  if (need_kc && (!x_rows || !x_cols)) return DK_ERR_ARG;
+  if (nrows == 0 || ncols == 0) return DK_OK;
+  const int b = block > 0 ? block : n;
+  GramArgs a{};
+  a.n = n;
+  a.row0 = row0;
+  a.nrows = nrows;
+  a.col0 = col0;
+  a.ncols = ncols;
+  a.symmetric = symmetric ? 1 : 0;
+  a.lnorm_r = lnorm_rows;
+  a.lnorm_c = lnorm_cols;
+  a.x_r = x_rows;
+  a.x_c = x_cols;
+  a.gamma = gamma;
+  a.w = w;
+  a.k = k_out;
+  a.kq = kq_out;
+  a.kc = kc_out;
+  a.lkq = logkq_out;
+  a.ld = ld;
+  a.status = ctx->status;
+  a.need_kc = need_kc ? 1 : 0;
+  a.ntiles = count_tiles(a, gblk::TILE, gblk::TILE);
+  long long grid = 2LL * ctx->sm_count;
+  if (grid > a.ntiles) grid = a.ntiles;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gblk::gram_blocks_kernel<<<int(grid), gblk::NT, 0, st>>>(static_cast<const float2*>(states_rows), m_rows,
+                                                           static_cast<const float2*>(states_cols), m_cols,
+                                                           (n + b - 1) / b, gblk::dpad_of(b), a);
+  return launch_status();
+}

@@ -27,7 +27,8 @@ EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_
             "dk_mps_build", "dk_gram_tile", "dk_dual_kernel_rows", "dk_gram_config_count",
             "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout", "dk_self_overlap",
             "dk_svm_ovo_train", "dk_svm_ovo_predict", "dk_gram_stats", "dk_pca_workspace_bytes", "dk_pca_fit",
-            "dk_pca_transform", "dk_pca_fit_noalloc", "dk_mps_build_blocks")
+            "dk_pca_transform", "dk_pca_fit_noalloc", "dk_mps_build_blocks", "dk_block_states_bytes",
+            "dk_block_states", "dk_gram_blocks")
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 PCA_MAX_FEATURES = 4096  # DK_PCA_MAX_FEATURES
 PCA_NOALLOC_MAX_FEATURES = 256  # DK_PCA_NOALLOC_MAX_FEATURES
@@ -71,6 +72,13 @@ def _lib():
     lib.dk_mps_build_blocks.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, ctypes.c_double, i32, vp, vp,
                                         vp, vp, vp]
     lib.dk_mps_build_blocks.restype = i32
+    lib.dk_block_states_bytes.argtypes = [i32, i32, i32]
+    lib.dk_block_states_bytes.restype = ctypes.c_size_t
+    lib.dk_block_states.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, vp, vp, vp]
+    lib.dk_block_states.restype = i32
+    lib.dk_gram_blocks.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, f32, f32,
+                                   vp, vp, vp, vp, i64, i32, vp]
+    lib.dk_gram_blocks.restype = i32
     lib.dk_gram_tile.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, i32,
                                  vp, vp, vp, vp, f32, f32, i32, vp, vp, vp, vp, i64, i32, vp]
     lib.dk_gram_tile.restype = i32
@@ -274,6 +282,50 @@ def mps_build_blocks(ctx: Context, x: torch.Tensor, fmap: FeatureMap, entangler:
                                       dtype, _ptr(out), _ptr(bond), _ptr(log_norm), _ptr(disc), _stream(stream)),
            "dk_mps_build_blocks")
     return MPS(out, m, n, fmap.chi_max, dtype, bond, log_norm, x, fmap=fmap), disc
+
+
+@dataclass
+class BlockStates:
+    """Block statevectors written by dk_block_states ([block][sample][dpad] complex64)."""
+    data: torch.Tensor      # uint8 bytes
+    m: int
+    n: int
+    block: int
+    log_norm: torch.Tensor  # float32, m
+    x: torch.Tensor         # float32 m x n features
+
+
+def block_states(ctx: Context, x: torch.Tensor, fmap: FeatureMap, entangler: int = DK_ENT_FULL,
+                 stream=None) -> BlockStates:
+    """dk_block_states: per-block statevectors of a block-structured map (fmap.block qubits)."""
+    _need_cuda(x, "x", torch.float32)
+    m, n = x.shape
+    nbytes = int(_lib().dk_block_states_bytes(m, n, int(fmap.block)))
+    if nbytes == 0:
+        raise ValueError(f"block {fmap.block} is outside the supported range for n = {n}")
+    out = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
+    log_norm = torch.empty(m, dtype=torch.float32, device=x.device)
+    fm = fmap._c()
+    _check(_lib().dk_block_states(ctx.handle, _ptr(x), m, n, ctypes.byref(fm), int(entangler), _ptr(out),
+                                  _ptr(log_norm), _stream(stream)), "dk_block_states")
+    return BlockStates(out, m, n, fmap.block, log_norm, x)
+
+
+def gram_blocks(ctx: Context, rows: BlockStates, cols: BlockStates | None = None, gamma: float | None = None,
+                w: float = 0.5, want=("k", "kq", "kc", "logkq"), stream=None) -> dict:
+    """dk_gram_blocks: K, K_q, K_c, log K_q of rows x cols (symmetric when cols is None)."""
+    symmetric = cols is None
+    cols = rows if cols is None else cols
+    if rows.n != cols.n or rows.block != cols.block:
+        raise ValueError("row and column states differ in n or block")
+    gamma = 1.0 / rows.n if gamma is None else gamma
+    out = _outs((rows.m, cols.m), rows.data.device, want)
+    _check(_lib().dk_gram_blocks(ctx.handle, _ptr(rows.data), rows.m, _ptr(cols.data), cols.m, rows.n, rows.block,
+                                 0, rows.m, 0, cols.m, _ptr(rows.log_norm), _ptr(cols.log_norm), _ptr(rows.x),
+                                 _ptr(cols.x), float(gamma), float(w), _ptr(out.get("k")), _ptr(out.get("kq")),
+                                 _ptr(out.get("kc")), _ptr(out.get("logkq")), int(cols.m), 1 if symmetric else 0,
+                                 _stream(stream)), "dk_gram_blocks")
+    return out
 
 
 def self_overlap(ctx: Context, mps: "MPS", prec: int, out: torch.Tensor | None = None, stream=None):

@@ -1,0 +1,138 @@
+"""GPU parity of the block-statevector Gram (dk_block_states + dk_gram_blocks) for
+block-structured feature maps (§II-C): K_q = prod_B |<psi_B(x_i)|psi_B(x_j)>|^2, exact at any
+n, with the RBF kernel and the mix fused as in every Gram call.
+
+Reference: the oracle's dense statevector of every block (``oracle.circuit.statevector``),
+summed in log domain. Tolerances as for the MPS Gram: |dK| <= 1e-6 on K, K_q and K_c (FP32
+dot products, float32 outputs); log K_q within 1e-3 * max(1, |log K_q|) where the reference
+is above -700, and 1e-4 relative at n = 784. The MPS paths for the same maps (closed-form
+chain build with blocks, and the SVD build of all-to-all blocks) must agree to 1e-6."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dk():
+    import torch
+    from paper_2602_01330_gb300 import build, dualk
+    build.build()
+    ctx = dualk.Context(0)
+    yield dualk, ctx, torch
+    ctx.close()
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _ref_log(xr, xc, reps, b, entangler):
+    from oracle import circuit
+    n = xr.shape[1]
+    out = np.zeros((xr.shape[0], xc.shape[0]))
+    for s in range(0, n, b):
+        e = min(s + b, n)
+        a = np.stack([circuit.statevector(r[s:e].astype(np.float64), reps, entangler=entangler) for r in xr])
+        c = np.stack([circuit.statevector(r[s:e].astype(np.float64), reps, entangler=entangler) for r in xc])
+        with np.errstate(divide="ignore"):
+            out += np.log(np.abs(a.conj() @ c.T) ** 2)
+    return out
+
+
+def _check(out, lref, kc_ref, w):
+    kq = out["kq"].cpu().numpy().astype(np.float64)
+    lkq = out["logkq"].cpu().numpy().astype(np.float64)
+    kc = out["kc"].cpu().numpy().astype(np.float64)
+    k = out["k"].cpu().numpy().astype(np.float64)
+    kq_ref = np.exp(lref)
+    assert np.max(np.abs(kq - kq_ref)) <= 1e-6
+    assert np.max(np.abs(kc - kc_ref)) <= 1e-6
+    assert np.max(np.abs(k - (w * kq_ref + (1 - w) * kc_ref))) <= 1e-6
+    sel = lref > -700
+    assert np.all(np.abs(lkq[sel] - lref[sel]) <= 1e-3 * np.maximum(1.0, np.abs(lref[sel])))
+
+
+@pytest.mark.parametrize("n,b,reps,ent", [(40, 8, 2, "full"), (50, 7, 2, "chain"), (36, 12, 2, "full"),
+                                          (9, 2, 3, "full"), (7, 1, 2, "full"), (30, 5, 1, "chain")])
+def test_gram_blocks_vs_block_statevectors(dk, n, b, reps, ent):
+    """Symmetric Gram of 70 samples (a full and a ragged tile) and 20 x 70 rows, element by
+    element; blocks of 1, 2 (below the 16-amplitude chunk), 5, 7, 8 and 12 qubits, short
+    last blocks (n = 50, 9, 7)."""
+    dualk, ctx, torch = dk
+    from oracle import gram as og
+    from paper_2602_01330_gb300 import synthetic
+    d = synthetic.fmnist_like(70, 20, n)
+    xtr, xte = d["x_train"], d["x_test"]
+    fm = dualk.FeatureMap(reps=reps, block=b)
+    e = dualk.DK_ENT_FULL if ent == "full" else dualk.DK_ENT_CHAIN
+    str_, ste = dualk.block_states(ctx, _dev(torch, xtr), fm, e), dualk.block_states(ctx, _dev(torch, xte), fm, e)
+    g = dualk.gram_blocks(ctx, str_, w=0.5)
+    r = dualk.gram_blocks(ctx, ste, str_, w=0.5)
+    torch.cuda.synchronize()
+    _check(g, _ref_log(xtr, xtr, reps, b, ent), og.rbf(xtr, xtr, 1.0 / n), 0.5)
+    _check(r, _ref_log(xte, xtr, reps, b, ent), og.rbf(xte, xtr, 1.0 / n), 0.5)
+    kq = g["kq"].cpu().numpy()
+    assert np.all(np.diag(kq) == 1.0)
+    assert np.array_equal(kq, kq.T)
+    ctx.sync_status()
+
+
+def test_gram_blocks_n784_log_kernel(dk):
+    """All 784 pixels in blocks of 10 with all-to-all ZZ (exact bond up to 32 inside a block,
+    beyond any bond-16 MPS): 48 images, every pair's log K_q against the oracle."""
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    x = synthetic.fmnist_like(48, 0, 784)["x_train"]
+    st = dualk.block_states(ctx, _dev(torch, x), dualk.FeatureMap(reps=2, block=10), dualk.DK_ENT_FULL)
+    g = dualk.gram_blocks(ctx, st, w=1.0, want=("kq", "logkq"))
+    torch.cuda.synchronize()
+    ref = _ref_log(x, x, 2, 10, "full")
+    lkq = g["logkq"].cpu().numpy().astype(np.float64)
+    off = ~np.eye(48, dtype=bool)
+    assert np.all(ref[off] < -100)
+    assert np.max(np.abs(lkq[off] - ref[off]) / np.abs(ref[off])) <= 1e-4
+    assert np.all(np.diag(g["kq"].cpu().numpy()) == 1.0)
+    ctx.sync_status()
+
+
+def test_gram_blocks_agrees_with_mps_paths(dk):
+    """The same block-structured states through the MPS Gram: the closed-form chain build with
+    blocks (bond 4) and the SVD build of all-to-all blocks of 8 (bond 16, exact at chi_max 32)."""
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    x = _dev(torch, synthetic.fmnist_like(60, 0, 48)["x_train"])
+    chain = dualk.gram_blocks(ctx, dualk.block_states(ctx, x, dualk.FeatureMap(reps=2, block=8), dualk.DK_ENT_CHAIN),
+                              w=0.5)
+    mchain = dualk.gram(ctx, dualk.mps_build(ctx, x, dualk.FeatureMap(reps=2, chi_max=4, block=8)), w=0.5)
+    full = dualk.gram_blocks(ctx, dualk.block_states(ctx, x, dualk.FeatureMap(reps=2, block=8), dualk.DK_ENT_FULL),
+                             w=0.5)
+    mfull, _ = dualk.mps_build_blocks(ctx, x, dualk.FeatureMap(reps=2, chi_max=32, block=8), dualk.DK_ENT_FULL)
+    gfull = dualk.gram(ctx, mfull, w=0.5)
+    torch.cuda.synchronize()
+    for a, b in ((chain, mchain), (full, gfull)):
+        assert torch.max(torch.abs(a["kq"] - b["kq"])).item() <= 1e-6
+        assert torch.max(torch.abs(a["k"] - b["k"])).item() <= 1e-6
+        assert torch.equal(a["kc"], b["kc"])
+    ctx.sync_status()
+
+
+def test_gram_blocks_errors(dk):
+    dualk, ctx, torch = dk
+    x = torch.rand(8, 30, device="cuda")
+    with pytest.raises(ValueError):
+        dualk.block_states(ctx, x, dualk.FeatureMap(reps=2, block=13))
+    with pytest.raises(ValueError):
+        dualk.block_states(ctx, x, dualk.FeatureMap(reps=2, block=0))  # one block of 30 qubits
+    st = dualk.block_states(ctx, x, dualk.FeatureMap(reps=2, block=6))
+    lib = dualk._lib()
+    out = torch.empty(8, 8, device="cuda")
+    # symmetric with different row and column ranges
+    assert lib.dk_gram_blocks(ctx.handle, dualk._ptr(st.data), 8, dualk._ptr(st.data), 8, 30, 6, 0, 4, 2, 4,
+                              dualk._ptr(st.log_norm), dualk._ptr(st.log_norm), dualk._ptr(x), dualk._ptr(x),
+                              0.1, 1.0, None, dualk._ptr(out), None, None, 8, 1, dualk._stream(None)) == 1
+    # ld below ncols
+    assert lib.dk_gram_blocks(ctx.handle, dualk._ptr(st.data), 8, dualk._ptr(st.data), 8, 30, 6, 0, 8, 0, 8,
+                              dualk._ptr(st.log_norm), dualk._ptr(st.log_norm), dualk._ptr(x), dualk._ptr(x),
+                              0.1, 1.0, None, dualk._ptr(out), None, None, 4, 0, dualk._stream(None)) == 1
+    ctx.sync_status()
