@@ -368,9 +368,9 @@ def run_ours(args):
     # the split-BF16 tensor-core Gram against the FP32 one at bond 32 (reps = 5; d = 256,
     # where every off-diagonal K_q is tiny, and d = 16, where many are not), the FP32 against
     # the FP64 QR sweep of the bond-4 build, and the continuous-batching server's latency.
-    mixed = serving_stats = svm_stats = None
+    mixed = serving_stats = svm_stats = block_stats = None
     if rank == 0 and world == 1 and not args.no_extras:
-        from paper_2602_01330_gb300 import precision, serving, svm
+        from paper_2602_01330_gb300 import blockmap, precision, serving, svm
         mixed = {"d256": precision.compare(m=512, pool=128, n_uniform=40, n_near=20, n_diag=10, ctx=ctx),
                  "d16": precision.compare(m=512, d=16, pool=128, n_uniform=40, n_near=20, n_diag=10, ctx=ctx),
                  "mps_build_qr": precision.compare_build_qr(ctx=ctx)}
@@ -378,6 +378,9 @@ def run_ours(args):
         # the SVM that consumes this step's Gram and rows: 5-fold CV over C x w, fit, test votes
         svm_stats = svm.run_pipeline(ctx, n_tr, n_te, d, reps,
                                      gram=(g_out["kq"], g_out["kc"], r_out["kq"], r_out["kc"]))
+        # the same data through a block-structured map (all-to-all ZZ in blocks of 10 qubits),
+        # contracted exactly by per-block statevector overlaps
+        block_stats = blockmap.run_benchmark(ctx, n_tr, n_te, d, block=10, reps=reps)
 
     if world > 1:
         tdist.destroy_process_group()
@@ -407,6 +410,7 @@ def run_ours(args):
         "mixed_precision": mixed,
         "serving": serving_stats,
         "svm": svm_stats,
+        "block_product_map": block_stats,
     }
     print(json.dumps(line), flush=True)
 

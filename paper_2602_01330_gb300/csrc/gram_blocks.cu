@@ -32,8 +32,14 @@ namespace gblk {
 constexpr int KC = 16;           // amplitudes per chunk
 constexpr int TILE = 64;         // pairs per tile side
 constexpr int NT = 256;          // threads: 16 x 16, 4 x 4 pairs each
-constexpr int SROW = TILE + 2;   // shared row stride in complex (bank spread)
+// Shared operand rows: column c of a tile sits at swz(c) = c + 2 (c / 16), i.e. 16 bytes of
+// padding after every 16 complex values, so the 8 column groups a warp reads at one k (each
+// 4 consecutive complex values, 32 B) fall in distinct banks; row stride 74 (= 72 + 2) also
+// spreads the transposed stores of the loader.
+constexpr int SROW = 74;
+__device__ __forceinline__ int swz(int c) { return c + 2 * (c >> 4); }
 constexpr int BUILD_NT = 128;
+constexpr size_t GRAM_SMEM = 4 * KC * SROW * sizeof(float2) + 16 * NT * (sizeof(float) + sizeof(int));
 
 __host__ __device__ inline int dpad_of(int b) { return (1 << b) > KC ? (1 << b) : KC; }
 
@@ -95,9 +101,17 @@ __global__ void __launch_bounds__(128) block_selfnorm_kernel(const float2* __res
 __global__ void __launch_bounds__(NT, 2) gram_blocks_kernel(const float2* __restrict__ sr, int m_r,
                                                             const float2* __restrict__ sc, int m_c, int nb, int dp,
                                                             const GramArgs p) {
-  __shared__ __align__(16) float2 As[2][KC][SROW];
-  __shared__ __align__(16) float2 Bs[2][KC][SROW];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // dynamic shared memory: the double-buffered operand tiles, then the running products of
+  // the 16 pairs of each thread (touched once per block: kept here, not in registers, which
+  // go to the accumulators and the operand loads)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto As = reinterpret_cast<float2(*)[KC][SROW]>(smem_raw);
+  auto Bs = reinterpret_cast<float2(*)[KC][SROW]>(smem_raw + 2 * KC * SROW * sizeof(float2));
+  auto s_prod = reinterpret_cast<float(*)[NT]>(smem_raw + 4 * KC * SROW * sizeof(float2));
+  auto s_ex = reinterpret_cast<int(*)[NT]>(smem_raw + 4 * KC * SROW * sizeof(float2) + 16 * NT * sizeof(float));
+  // a warp covers 4 x 8 threads (16 x 32 pairs): lane -> (ty % 4, tx % 8), warp -> (ty / 4, tx / 8)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ty = (warp >> 1) * 4 + (lane >> 3), tx = (warp & 1) * 8 + (lane & 7);
   // loader: thread -> (row lr = tid / 4, float4 q = tid % 4 and q + 4 of the row's chunk)
   const int lr = tid >> 2, lq = tid & 3;
   const int cpb = dp / KC;          // chunks per block
@@ -122,22 +136,20 @@ __global__ void __launch_bounds__(NT, 2) gram_blocks_kernel(const float2* __rest
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int k = 2 * (lq + 4 * h);
-        As[buf][k][lr] = make_float2(pa[h].x, pa[h].y);
-        As[buf][k + 1][lr] = make_float2(pa[h].z, pa[h].w);
-        Bs[buf][k][lr] = make_float2(pb[h].x, pb[h].y);
-        Bs[buf][k + 1][lr] = make_float2(pb[h].z, pb[h].w);
+        As[buf][k][swz(lr)] = make_float2(pa[h].x, pa[h].y);
+        As[buf][k + 1][swz(lr)] = make_float2(pa[h].z, pa[h].w);
+        Bs[buf][k][swz(lr)] = make_float2(pb[h].x, pb[h].y);
+        Bs[buf][k + 1][swz(lr)] = make_float2(pb[h].z, pb[h].w);
       }
     };
     float2 acc[4][4];
-    float prod[4][4];
-    int ex[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         acc[u][v] = make_float2(0.0f, 0.0f);
-        prod[u][v] = 1.0f;
-        ex[u][v] = 0;
+        s_prod[u * 4 + v][tid] = 1.0f;
+        s_ex[u * 4 + v][tid] = 0;
       }
     fetch(0);
     commit(0);
@@ -147,10 +159,10 @@ __global__ void __launch_bounds__(NT, 2) gram_blocks_kernel(const float2* __rest
       if (c + 1 < total) fetch(c + 1);
 #pragma unroll
       for (int kk = 0; kk < KC; ++kk) {
-        const float4 a01 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
-        const float4 a23 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4 + 2]);
-        const float4 b01 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
-        const float4 b23 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4 + 2]);
+        const float4 a01 = *reinterpret_cast<const float4*>(&As[buf][kk][swz(ty * 4)]);
+        const float4 a23 = *reinterpret_cast<const float4*>(&As[buf][kk][swz(ty * 4) + 2]);
+        const float4 b01 = *reinterpret_cast<const float4*>(&Bs[buf][kk][swz(tx * 4)]);
+        const float4 b23 = *reinterpret_cast<const float4*>(&Bs[buf][kk][swz(tx * 4) + 2]);
         const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
                               make_float2(a23.z, a23.w)};
         const float2 bv[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w), make_float2(b23.x, b23.y),
@@ -165,7 +177,11 @@ __global__ void __launch_bounds__(NT, 2) gram_blocks_kernel(const float2* __rest
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
-            mul_renorm(prod[u][v], ex[u][v], acc[u][v]);
+            float pr = s_prod[u * 4 + v][tid];
+            int e = s_ex[u * 4 + v][tid];
+            mul_renorm(pr, e, acc[u][v]);
+            s_prod[u * 4 + v][tid] = pr;
+            s_ex[u * 4 + v][tid] = e;
             acc[u][v] = make_float2(0.0f, 0.0f);
           }
       }
@@ -183,7 +199,7 @@ __global__ void __launch_bounds__(NT, 2) gram_blocks_kernel(const float2* __rest
           const float* xb = p.x_c + size_t(j) * p.n;
           for (int f = 0; f < p.n; ++f) kahan_add_sq(d2, comp, __ldg(xa + f) - __ldg(xb + f));
         }
-        write_pair(p, half_log(prod[u][v], ex[u][v]), d2, i, j);
+        write_pair(p, half_log(s_prod[u * 4 + v][tid], s_ex[u * 4 + v][tid]), d2, i, j);
       }
   }
 }
@@ -266,7 +282,10 @@ DK_API dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows
   long long grid = 2LL * ctx->sm_count;
   if (grid > a.ntiles) grid = a.ntiles;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  gblk::gram_blocks_kernel<<<int(grid), gblk::NT, 0, st>>>(static_cast<const float2*>(states_rows), m_rows,
+  if (cudaFuncSetAttribute(gblk::gram_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(gblk::GRAM_SMEM)) != cudaSuccess)
+    return DK_ERR_CUDA;
+  gblk::gram_blocks_kernel<<<int(grid), gblk::NT, gblk::GRAM_SMEM, st>>>(static_cast<const float2*>(states_rows), m_rows,
                                                            static_cast<const float2*>(states_cols), m_cols,
                                                            (n + b - 1) / b, gblk::dpad_of(b), a);
   return launch_status();
