@@ -205,8 +205,8 @@ size_t dk_block_states_bytes(int m, int n, int block);
  *   log_norm  m floats (device, written, may be NULL): ln|<psi~_i|psi~_i>| of the rounded
  *             states by the arithmetic of dk_gram_blocks, so that K_q(x, x) = 1 exactly
  * Errors: DK_ERR_ARG (NULL pointers, m or n < 1, reps, entangler, misaligned states),
- *         DK_ERR_UNSUPPORTED (block outside 0..12 or above 12 qubits, m > 65535),
- *         DK_ERR_CUDA. */
+ *         DK_ERR_UNSUPPORTED (block outside 0..12 or above 12 qubits, m > 65535, more than
+ *         6144 blocks), DK_ERR_CUDA. */
 dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm, int entangler,
                           void* states, float* log_norm, void* stream);
 

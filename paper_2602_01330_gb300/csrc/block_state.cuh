@@ -1,11 +1,19 @@
 // Dense statevector of one block of a block-structured feature map (§II-C, Eq. 6 restricted
 // to the block's qubits), computed by a whole CTA in FP64 shared memory.
 //
-// Per repetition: H on every qubit (one Walsh-Hadamard butterfly pass per qubit), then the
-// diagonal layer exp(-i Phi(z)) with
+// Per repetition: H on every qubit, then the diagonal layer exp(-i Phi(z)) with
 //   Phi(z) = sum_q (angle_scale x_q / 2) z_q + sum_{(q,r) entangled} (pi - x_q)(pi - x_r) z_q z_r,
 // z_q = +1 / -1 for bit value 0 / 1 (RZ(angle_scale x_q) and RZZ(2 (pi - x_q)(pi - x_r)) are
 // diagonal and commute). Qubit 0 of the block is the most significant bit of the index.
+//
+// Work saved against the plain gate sequence, all in FP64:
+//   * the first H layer acts on |0...0> and gives the uniform state, so the first repetition
+//     is psi(z) = 2^(-b/2) exp(-i Phi(z)) directly; later ones run one Walsh-Hadamard
+//     butterfly pass per qubit;
+//   * the phase factors exp(-i Phi(z)) are computed once and reused by every repetition;
+//   * Phi is evaluated from split tables: with z = (zH, zL) the high and low halves of the
+//     bits, Phi = A(zH) + B(zL) + sum_{q in H} z_q V_q(zL), V_q(zL) = sum_{r in L} J_qr z_r,
+//     a handful of additions per amplitude instead of one term per entangled pair.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,23 +24,34 @@
 namespace dk {
 namespace blockstate {
 
-constexpr int MAXB = 12;  // qubits per block
+constexpr int MAXB = 12;           // qubits per block
+constexpr int MAXH = MAXB / 2;     // bits of each half
 constexpr double PI_D = 3.14159265358979323846;
 
 struct Coeffs {
-  double hq[MAXB];        // angle_scale x_q / 2
-  double jq[MAXB][MAXB];  // (pi - x_q)(pi - x_r) for entangled q < r, else 0
+  double hq[MAXB];               // angle_scale x_q / 2
+  double jq[MAXB][MAXB];         // (pi - x_q)(pi - x_r) for entangled q < r, else 0
+  double ta[1 << MAXH];          // A(zH): the terms inside the high half
+  double tb[1 << MAXH];          // B(zL): the terms inside the low half
+  double tv[1 << MAXH][MAXH];    // V_q(zL) for the high qubits q
 };
+
+// Shared memory a block of bl <= b qubits needs: Coeffs, then psi and the phase factors.
+__host__ __device__ inline size_t smem_bytes(int b) {
+  return ((sizeof(Coeffs) + 15) & ~size_t(15)) + 2 * (size_t(1) << b) * sizeof(double2);
+}
 
 __device__ __forceinline__ double2 cmul64(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
-// psi[0 .. 2^bl) of the block whose features are xb[0 .. bl); pairs_kind DK_ENT_CHAIN,
-// DK_ENT_FULL, or anything else for no entanglers. Ends with __syncthreads().
-__device__ inline void build(double2* psi, Coeffs& C, const float* xb, int bl, int reps, double angle_scale,
-                             int pairs_kind, int tid, int nt) {
+// psi[0 .. 2^bl) of the block whose features are xb[0 .. bl); ph[0 .. 2^bl) receives the
+// phase factors. pairs_kind: DK_ENT_CHAIN, DK_ENT_FULL, or anything else for no entanglers.
+// Ends with __syncthreads().
+__device__ inline void build(double2* psi, double2* ph, Coeffs& C, const float* xb, int bl, int reps,
+                             double angle_scale, int pairs_kind, int tid, int nt) {
   const int dim = 1 << bl;
+  const int hb = bl >> 1, lb = bl - hb;  // high half: qubits 0 .. hb-1
   if (tid < bl) C.hq[tid] = 0.5 * angle_scale * double(xb[tid]);
   for (int e = tid; e < MAXB * MAXB; e += nt) {
     const int q = e / MAXB, r = e % MAXB;
@@ -40,9 +59,47 @@ __device__ inline void build(double2* psi, Coeffs& C, const float* xb, int bl, i
                     (pairs_kind == DK_ENT_FULL || (pairs_kind == DK_ENT_CHAIN && r == q + 1));
     C.jq[q][r] = on ? (PI_D - double(xb[q])) * (PI_D - double(xb[r])) : 0.0;
   }
-  for (int e = tid; e < dim; e += nt) psi[e] = make_double2(e == 0 ? 1.0 : 0.0, 0.0);
   __syncthreads();
-  for (int rep = 0; rep < reps; ++rep) {
+  // tables: z of qubit q (q < hb) is bit hb-1-q of zH; of qubit hb+t is bit lb-1-t of zL
+  for (int e = tid; e < (1 << hb); e += nt) {
+    double a = 0.0;
+    for (int q = 0; q < hb; ++q) {
+      const double zq = ((e >> (hb - 1 - q)) & 1) ? -1.0 : 1.0;
+      double s = C.hq[q];
+      for (int r = q + 1; r < hb; ++r) s += ((e >> (hb - 1 - r)) & 1) ? -C.jq[q][r] : C.jq[q][r];
+      a += zq * s;
+    }
+    C.ta[e] = a;
+  }
+  for (int e = tid; e < (1 << lb); e += nt) {
+    double bsum = 0.0;
+    for (int t = 0; t < lb; ++t) {
+      const int q = hb + t;
+      const double zq = ((e >> (lb - 1 - t)) & 1) ? -1.0 : 1.0;
+      double s = C.hq[q];
+      for (int u = t + 1; u < lb; ++u) s += ((e >> (lb - 1 - u)) & 1) ? -C.jq[q][hb + u] : C.jq[q][hb + u];
+      bsum += zq * s;
+    }
+    C.tb[e] = bsum;
+    for (int q = 0; q < hb; ++q) {
+      double v = 0.0;
+      for (int t = 0; t < lb; ++t) v += ((e >> (lb - 1 - t)) & 1) ? -C.jq[q][hb + t] : C.jq[q][hb + t];
+      C.tv[e][q] = v;
+    }
+  }
+  __syncthreads();
+  const double amp = exp2(-0.5 * double(bl));
+  for (int e = tid; e < dim; e += nt) {
+    const int zh = e >> lb, zl = e & ((1 << lb) - 1);
+    double phi = C.ta[zh] + C.tb[zl];
+    for (int q = 0; q < hb; ++q) phi += ((zh >> (hb - 1 - q)) & 1) ? -C.tv[zl][q] : C.tv[zl][q];
+    double sn, cs;
+    sincos(-phi, &sn, &cs);
+    ph[e] = make_double2(cs, sn);
+    psi[e] = make_double2(amp * cs, amp * sn);  // first repetition: uniform state times the phases
+  }
+  __syncthreads();
+  for (int rep = 1; rep < reps; ++rep) {
     for (int q = 0; q < bl; ++q) {
       const int bit = 1 << (bl - 1 - q);
       for (int e = tid; e < dim / 2; e += nt) {
@@ -54,18 +111,7 @@ __device__ inline void build(double2* psi, Coeffs& C, const float* xb, int bl, i
       }
       __syncthreads();
     }
-    for (int e = tid; e < dim; e += nt) {
-      double phi = 0.0;
-      for (int q = 0; q < bl; ++q) {
-        const double zq = ((e >> (bl - 1 - q)) & 1) ? -1.0 : 1.0;
-        double pair = 0.0;
-        for (int r = q + 1; r < bl; ++r) pair += ((e >> (bl - 1 - r)) & 1) ? -C.jq[q][r] : C.jq[q][r];
-        phi += zq * (C.hq[q] + pair);
-      }
-      double sn, cs;
-      sincos(-phi, &sn, &cs);
-      psi[e] = cmul64(psi[e], make_double2(cs, sn));
-    }
+    for (int e = tid; e < dim; e += nt) psi[e] = cmul64(psi[e], ph[e]);
     __syncthreads();
   }
 }

@@ -67,7 +67,8 @@ struct Shared {
   int keep;               // kept bond of the current cut
 };
 
-inline size_t smem_bytes(int b) { return ((sizeof(Shared) + 15) & ~size_t(15)) + (size_t(1) << b) * sizeof(double2); }
+// Shared, then the state and its phase factors (2^b amplitudes each)
+inline size_t smem_bytes(int b) { return ((sizeof(Shared) + 15) & ~size_t(15)) + 2 * (size_t(1) << b) * sizeof(double2); }
 
 // (k, round t) -> row of the round-robin pairing of r rows (r even): row 0 stays, the rest rotate
 __device__ __forceinline__ int rr_row(int k, int t, int r) { return k == 0 ? 0 : ((k - 1 + t) % (r - 1)) + 1; }
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(NT) block_svd_kernel(const float* __restrict__
   extern __shared__ __align__(16) unsigned char raw[];
   Shared& S = *reinterpret_cast<Shared*>(raw);
   double2* psi = reinterpret_cast<double2*>(raw + ((sizeof(Shared) + 15) & ~size_t(15)));
+  double2* ph = psi + (1 << b);
   const int i = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
   const float* xs = x + size_t(i) * n;
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(NT) block_svd_kernel(const float* __restrict__
     const int bl = min(b, n - start);
     const int dim = 1 << bl;
     // ---- 1. block statevector ----
-    blockstate::build(psi, S.coef, xs + start, bl, reps, angle_scale, pairs_kind, tid, NT);
+    blockstate::build(psi, ph, S.coef, xs + start, bl, reps, angle_scale, pairs_kind, tid, NT);
     // ---- 2. SVD sweep over the block's cuts ----
     int r = 2, c = dim / 2;
     if (tid < 2) S.rowbase[tid] = tid * c;

@@ -69,33 +69,42 @@ __global__ void __launch_bounds__(BUILD_NT) block_states_kernel(const float* __r
   extern __shared__ __align__(16) unsigned char raw[];
   blockstate::Coeffs& C = *reinterpret_cast<blockstate::Coeffs*>(raw);
   double2* psi = reinterpret_cast<double2*>(raw + ((sizeof(blockstate::Coeffs) + 15) & ~size_t(15)));
+  double2* ph = psi + (1 << b);
   const int blk = blockIdx.x, i = blockIdx.y;
   const int start = blk * b;
   const int bl = min(b, n - start);
   const int dp = dpad_of(b);
-  blockstate::build(psi, C, x + size_t(i) * n + start, bl, reps, angle_scale, pairs_kind, threadIdx.x, BUILD_NT);
+  blockstate::build(psi, ph, C, x + size_t(i) * n + start, bl, reps, angle_scale, pairs_kind, threadIdx.x, BUILD_NT);
   float2* out = states + (size_t(blk) * m + i) * dp;
   const int dim = 1 << bl;
   for (int k = threadIdx.x; k < dp; k += BUILD_NT)
     out[k] = k < dim ? make_float2(float(psi[k].x), float(psi[k].y)) : make_float2(0.0f, 0.0f);
 }
 
-__global__ void __launch_bounds__(128) block_selfnorm_kernel(const float2* __restrict__ states, int m, int nb,
-                                                             int dp, float* __restrict__ log_norm) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  float prod = 1.0f;
-  int e = 0;
-  for (int blk = 0; blk < nb; ++blk) {
-    const float2* a = states + (size_t(blk) * m + i) * dp;
+// One CTA per sample: thread B forms <psi_B|psi_B> with the Gram kernel's sequential
+// per-pair FMA order, then thread 0 multiplies the blocks in order as the Gram kernel does.
+constexpr int NORM_NT = 128;
+__global__ void __launch_bounds__(NORM_NT) block_selfnorm_kernel(const float2* __restrict__ states, int m, int nb,
+                                                                 int dp, float* __restrict__ log_norm) {
+  extern __shared__ float2 s_g[];  // nb overlaps
+  const int i = blockIdx.x;
+  for (int blk = threadIdx.x; blk < nb; blk += NORM_NT) {
+    const float4* a = reinterpret_cast<const float4*>(states + (size_t(blk) * m + i) * dp);
     float2 acc = make_float2(0.0f, 0.0f);
-    for (int k = 0; k < dp; ++k) {
-      const float2 v = a[k];
-      cmac(acc, v, v);
+    for (int k = 0; k < dp / 2; ++k) {
+      const float4 v = __ldg(a + k);
+      cmac(acc, make_float2(v.x, v.y), make_float2(v.x, v.y));
+      cmac(acc, make_float2(v.z, v.w), make_float2(v.z, v.w));
     }
-    mul_renorm(prod, e, acc);
+    s_g[blk] = acc;
   }
-  log_norm[i] = half_log(prod, e);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float prod = 1.0f;
+    int e = 0;
+    for (int blk = 0; blk < nb; ++blk) mul_renorm(prod, e, s_g[blk]);
+    log_norm[i] = half_log(prod, e);
+  }
 }
 
 __global__ void __launch_bounds__(NT, 2) gram_blocks_kernel(const float2* __restrict__ sr, int m_r,
@@ -226,17 +235,18 @@ DK_API dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, cons
   if (m > 65535) return DK_ERR_UNSUPPORTED;  // grid y
   const int b = fm->block > 0 ? fm->block : n;
   const int nb = (n + b - 1) / b;
+  if (size_t(nb) * sizeof(float2) > 48 * 1024) return DK_ERR_UNSUPPORTED;  // self-norm staging
   const int kind = fm->entangle ? entangler : -1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t smem = ((sizeof(blockstate::Coeffs) + 15) & ~size_t(15)) + (size_t(1) << b) * sizeof(double2);
+  const size_t smem = blockstate::smem_bytes(b);
   if (cudaFuncSetAttribute(gblk::block_states_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
       cudaSuccess)
     return DK_ERR_CUDA;
   gblk::block_states_kernel<<<dim3(nb, m), gblk::BUILD_NT, smem, st>>>(x, m, n, b, fm->reps, double(fm->angle_scale),
                                                                       kind, static_cast<float2*>(states));
   if (log_norm)
-    gblk::block_selfnorm_kernel<<<(m + 127) / 128, 128, 0, st>>>(static_cast<const float2*>(states), m, nb,
-                                                                 gblk::dpad_of(b), log_norm);
+    gblk::block_selfnorm_kernel<<<m, gblk::NORM_NT, nb * sizeof(float2), st>>>(static_cast<const float2*>(states), m,
+                                                                             nb, gblk::dpad_of(b), log_norm);
   return launch_status();
 }
 
