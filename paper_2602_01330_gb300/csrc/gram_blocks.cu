@@ -10,13 +10,14 @@
 //     FP64 (block_state.cuh) and stores it rounded to complex64, layout
 //     states[B][i][k], k < dpad = max(2^b, KC) (a short last block is zero-padded, which
 //     leaves every overlap unchanged).
-//   * gram_blocks_kernel: 64 x 64 pair tiles, 256 threads, each 4 x 4 pairs; per block the
-//     K = dpad contraction runs in 16-amplitude chunks staged through shared memory
-//     (register prefetch of the next chunk, double buffer), FP32 FMAs on CUDA cores. After a
-//     block, each pair multiplies |G_B|^2 into a running product kept as mantissa and binary
-//     exponent (no logarithm per block, no underflow). The epilogue is the one of every Gram
-//     kernel: log K_q = 2 ln|a| - ln N_i - ln N_j, the RBF kernel (Kahan FP32 distance) and
-//     the mix.
+//   * gram_blocks_kernel<RU>: (16 RU) x 64 pair tiles (RU = 8: 128 x 64, or 4: 64 x 64 when
+//     that fills the GPU better), 256 threads with RU x 4 pairs each; per block the K = dpad
+//     contraction runs in 16-amplitude chunks staged through shared memory (register prefetch
+//     of the next chunk, double buffer, rows swizzled so a warp's operand reads are
+//     conflict-free), FP32 FMAs on CUDA cores. After a block each pair adds log2 |G_B|^2 to
+//     a running sum kept in shared memory (no underflow however many blocks). The epilogue is
+//     the one of every Gram kernel: log K_q = 2 ln|a| - ln N_i - ln N_j, the RBF kernel
+//     (Kahan FP32 distance) and the mix.
 //   * block_selfnorm_kernel: ln N_i = ln|a(x_i, x_i)| with exactly the per-pair arithmetic of
 //     gram_blocks_kernel (same chunk order, same FMA sequence), so K_q(x, x) = 1 exactly.
 #include <math.h>
@@ -30,16 +31,21 @@ namespace dk {
 namespace gblk {
 
 constexpr int KC = 16;           // amplitudes per chunk
-constexpr int TILE = 64;         // pairs per tile side
-constexpr int NT = 256;          // threads: 16 x 16, 4 x 4 pairs each
+constexpr int TC = 64;           // pair tile: (16 RU) rows x TC columns, RU = 4 or 8 rows per thread
+constexpr int NT = 256;          // threads: 16 x 16
 // Shared operand rows: column c of a tile sits at swz(c) = c + 2 (c / 16), i.e. 16 bytes of
 // padding after every 16 complex values, so the 8 column groups a warp reads at one k (each
 // 4 consecutive complex values, 32 B) fall in distinct banks; row stride 74 (= 72 + 2) also
 // spreads the transposed stores of the loader.
-constexpr int SROW = 74;
+constexpr int SROW = 74;     // column tile row stride (64 + 2 x 4 pad + 2)
+template <int RU>
+struct RowTile {
+  static constexpr int TR = 16 * RU;
+  static constexpr int SROW_A = TR + 2 * (TR / 16) + 2;
+  static constexpr size_t SMEM = 2 * KC * (SROW_A + SROW) * sizeof(float2) + RU * 4 * NT * sizeof(float);
+};
 __device__ __forceinline__ int swz(int c) { return c + 2 * (c >> 4); }
 constexpr int BUILD_NT = 128;
-constexpr size_t GRAM_SMEM = 4 * KC * SROW * sizeof(float2) + 16 * NT * (sizeof(float) + sizeof(int));
 
 __host__ __device__ inline int dpad_of(int b) { return (1 << b) > KC ? (1 << b) : KC; }
 
@@ -51,17 +57,11 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(-a.y, b.x, acc.y);
 }
 
-// running product of |G_B|^2 as mantissa * 2^e
-__device__ __forceinline__ void mul_renorm(float& prod, int& e, float2 g) {
-  prod *= fmaf(g.x, g.x, g.y * g.y);
-  int ex;
-  prod = frexpf(prod, &ex);
-  e += ex;
-}
+// running sum of log2 |G_B|^2 over the blocks (one float per pair; never underflows)
+__device__ __forceinline__ void lg_add(float& lg, float2 g) { lg += log2f(fmaf(g.x, g.x, g.y * g.y)); }
 
-__device__ __forceinline__ float half_log(float prod, int e) {
-  return 0.5f * fmaf(float(e), 0.69314718055994530942f, logf(prod));
-}
+// ln|a| from the log2 sum of |a|^2
+__device__ __forceinline__ float half_log_lg(float lg) { return lg * (0.5f * 0.69314718055994530942f); }
 
 __global__ void __launch_bounds__(BUILD_NT) block_states_kernel(const float* __restrict__ x, int m, int n, int b,
                                                                 int reps, double angle_scale, int pairs_kind,
@@ -100,44 +100,49 @@ __global__ void __launch_bounds__(NORM_NT) block_selfnorm_kernel(const float2* _
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float prod = 1.0f;
-    int e = 0;
-    for (int blk = 0; blk < nb; ++blk) mul_renorm(prod, e, s_g[blk]);
-    log_norm[i] = half_log(prod, e);
+    float lg = 0.0f;
+    for (int blk = 0; blk < nb; ++blk) lg_add(lg, s_g[blk]);
+    log_norm[i] = half_log_lg(lg);
   }
 }
 
+template <int RU>
 __global__ void __launch_bounds__(NT, 2) gram_blocks_kernel(const float2* __restrict__ sr, int m_r,
                                                             const float2* __restrict__ sc, int m_c, int nb, int dp,
                                                             const GramArgs p) {
-  // dynamic shared memory: the double-buffered operand tiles, then the running products of
-  // the 16 pairs of each thread (touched once per block: kept here, not in registers, which
-  // go to the accumulators and the operand loads)
+  // dynamic shared memory: the double-buffered operand tiles (rows: TR x KC, columns: TC x KC,
+  // stored k-major), then the running log2 sums of each thread's pairs (touched once per
+  // block: kept here, not in registers, which go to the accumulators and the operand loads)
+  constexpr int TR = RowTile<RU>::TR, SROW_A = RowTile<RU>::SROW_A;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto As = reinterpret_cast<float2(*)[KC][SROW]>(smem_raw);
-  auto Bs = reinterpret_cast<float2(*)[KC][SROW]>(smem_raw + 2 * KC * SROW * sizeof(float2));
-  auto s_prod = reinterpret_cast<float(*)[NT]>(smem_raw + 4 * KC * SROW * sizeof(float2));
-  auto s_ex = reinterpret_cast<int(*)[NT]>(smem_raw + 4 * KC * SROW * sizeof(float2) + 16 * NT * sizeof(float));
-  // a warp covers 4 x 8 threads (16 x 32 pairs): lane -> (ty % 4, tx % 8), warp -> (ty / 4, tx / 8)
+  auto As = reinterpret_cast<float2(*)[KC][SROW_A]>(smem_raw);
+  auto Bs = reinterpret_cast<float2(*)[KC][SROW]>(smem_raw + 2 * KC * SROW_A * sizeof(float2));
+  auto s_lg = reinterpret_cast<float(*)[NT]>(smem_raw + 2 * KC * (SROW_A + SROW) * sizeof(float2));
+  // a warp covers 4 x 8 threads (32 x 32 pairs): lane -> (ty % 4, tx % 8), warp -> (ty / 4, tx / 8)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ty = (warp >> 1) * 4 + (lane >> 3), tx = (warp & 1) * 8 + (lane & 7);
-  // loader: thread -> (row lr = tid / 4, float4 q = tid % 4 and q + 4 of the row's chunk)
+  // loader: thread -> (rows lr and, for RU = 8, lr + 64; float4 lq and lq + 4 of each row's chunk)
   const int lr = tid >> 2, lq = tid & 3;
-  const int cpb = dp / KC;          // chunks per block
+  const int cpb = dp / KC;  // chunks per block
   const int total = nb * cpb;
   const int my_tiles = (p.ntiles > int(blockIdx.x)) ? (p.ntiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
   for (int lt = 0; lt < my_tiles; ++lt) {
     int ti, tj;
-    decode_tile(p, TILE, TILE, int(blockIdx.x) + lt * int(gridDim.x), ti, tj);
-    const int r0 = p.row0 + ti * TILE, c0 = p.col0 + tj * TILE;
-    const int ar = min(r0 + lr, m_r - 1), bc = min(c0 + lr, m_c - 1);
-    float4 pa[2], pb[2];
+    decode_tile(p, TR, TC, int(blockIdx.x) + lt * int(gridDim.x), ti, tj);
+    const int r0 = p.row0 + ti * TR, c0 = p.col0 + tj * TC;
+    const int ar0 = min(r0 + lr, m_r - 1), ar1 = min(r0 + 64 + lr, m_r - 1), bc = min(c0 + lr, m_c - 1);
+    float4 pa[RU / 2], pb[2];
     auto fetch = [&](int c) {
       const int blk = c / cpb, k0 = (c - blk * cpb) * KC;
-      const float4* a = reinterpret_cast<const float4*>(sr + (size_t(blk) * m_r + ar) * dp + k0);
+      const float4* a0 = reinterpret_cast<const float4*>(sr + (size_t(blk) * m_r + ar0) * dp + k0);
+      const float4* a1 = reinterpret_cast<const float4*>(sr + (size_t(blk) * m_r + ar1) * dp + k0);
       const float4* bb = reinterpret_cast<const float4*>(sc + (size_t(blk) * m_c + bc) * dp + k0);
-      pa[0] = __ldg(a + lq);
-      pa[1] = __ldg(a + lq + 4);
+      pa[0] = __ldg(a0 + lq);
+      pa[1] = __ldg(a0 + lq + 4);
+      if constexpr (RU == 8) {
+        pa[2] = __ldg(a1 + lq);
+        pa[3] = __ldg(a1 + lq + 4);
+      }
       pb[0] = __ldg(bb + lq);
       pb[1] = __ldg(bb + lq + 4);
     };
@@ -147,18 +152,21 @@ __global__ void __launch_bounds__(NT, 2) gram_blocks_kernel(const float2* __rest
         const int k = 2 * (lq + 4 * h);
         As[buf][k][swz(lr)] = make_float2(pa[h].x, pa[h].y);
         As[buf][k + 1][swz(lr)] = make_float2(pa[h].z, pa[h].w);
+        if constexpr (RU == 8) {
+          As[buf][k][swz(lr + 64)] = make_float2(pa[2 + h].x, pa[2 + h].y);
+          As[buf][k + 1][swz(lr + 64)] = make_float2(pa[2 + h].z, pa[2 + h].w);
+        }
         Bs[buf][k][swz(lr)] = make_float2(pb[h].x, pb[h].y);
         Bs[buf][k + 1][swz(lr)] = make_float2(pb[h].z, pb[h].w);
       }
     };
-    float2 acc[4][4];
+    float2 acc[RU][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < RU; ++u)
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         acc[u][v] = make_float2(0.0f, 0.0f);
-        s_prod[u * 4 + v][tid] = 1.0f;
-        s_ex[u * 4 + v][tid] = 0;
+        s_lg[u * 4 + v][tid] = 0.0f;
       }
     fetch(0);
     commit(0);
@@ -168,48 +176,52 @@ __global__ void __launch_bounds__(NT, 2) gram_blocks_kernel(const float2* __rest
       if (c + 1 < total) fetch(c + 1);
 #pragma unroll
       for (int kk = 0; kk < KC; ++kk) {
-        const float4 a01 = *reinterpret_cast<const float4*>(&As[buf][kk][swz(ty * 4)]);
-        const float4 a23 = *reinterpret_cast<const float4*>(&As[buf][kk][swz(ty * 4) + 2]);
-        const float4 b01 = *reinterpret_cast<const float4*>(&Bs[buf][kk][swz(tx * 4)]);
-        const float4 b23 = *reinterpret_cast<const float4*>(&Bs[buf][kk][swz(tx * 4) + 2]);
-        const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
-                              make_float2(a23.z, a23.w)};
-        const float2 bv[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w), make_float2(b23.x, b23.y),
-                              make_float2(b23.z, b23.w)};
+        float2 av[RU], bv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int h = 0; h < RU / 2; ++h) {
+          const float4 a = *reinterpret_cast<const float4*>(&As[buf][kk][swz(ty * RU) + 2 * h]);
+          av[2 * h] = make_float2(a.x, a.y);
+          av[2 * h + 1] = make_float2(a.z, a.w);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][swz(tx * 4) + 2 * h]);
+          bv[2 * h] = make_float2(b.x, b.y);
+          bv[2 * h + 1] = make_float2(b.z, b.w);
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) cmac(acc[u][v], av[u], bv[v]);
       }
       if ((c + 1) % cpb == 0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < RU; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
-            float pr = s_prod[u * 4 + v][tid];
-            int e = s_ex[u * 4 + v][tid];
-            mul_renorm(pr, e, acc[u][v]);
-            s_prod[u * 4 + v][tid] = pr;
-            s_ex[u * 4 + v][tid] = e;
+            float lg = s_lg[u * 4 + v][tid];
+            lg_add(lg, acc[u][v]);
+            s_lg[u * 4 + v][tid] = lg;
             acc[u][v] = make_float2(0.0f, 0.0f);
           }
       }
       if (c + 1 < total) commit(buf ^ 1);
       __syncthreads();
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
+#pragma unroll 1
+    for (int u = 0; u < RU; ++u)
+#pragma unroll 1
       for (int v = 0; v < 4; ++v) {
-        const int i = r0 + ty * 4 + u, j = c0 + tx * 4 + v;
+        const int i = r0 + ty * RU + u, j = c0 + tx * 4 + v;
         float d2 = 0.0f, comp = 0.0f;
         if (p.need_kc && i < p.row0 + p.nrows && j < p.col0 + p.ncols && !(p.symmetric && j < i)) {
           const float* xa = p.x_r + size_t(i) * p.n;
           const float* xb = p.x_c + size_t(j) * p.n;
           for (int f = 0; f < p.n; ++f) kahan_add_sq(d2, comp, __ldg(xa + f) - __ldg(xb + f));
         }
-        write_pair(p, half_log(s_prod[u * 4 + v][tid], s_ex[u * 4 + v][tid]), d2, i, j);
+        write_pair(p, half_log_lg(s_lg[u * 4 + v][tid]), d2, i, j);
       }
+    __syncthreads();  // s_lg is reset by the next tile
   }
 }
 
@@ -288,15 +300,33 @@ DK_API dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows
   a.ld = ld;
   a.status = ctx->status;
   a.need_kc = need_kc ? 1 : 0;
-  a.ntiles = count_tiles(a, gblk::TILE, gblk::TILE);
-  long long grid = 2LL * ctx->sm_count;
-  if (grid > a.ntiles) grid = a.ntiles;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (cudaFuncSetAttribute(gblk::gram_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(gblk::GRAM_SMEM)) != cudaSuccess)
-    return DK_ERR_CUDA;
-  gblk::gram_blocks_kernel<<<int(grid), gblk::NT, gblk::GRAM_SMEM, st>>>(static_cast<const float2*>(states_rows), m_rows,
-                                                           static_cast<const float2*>(states_cols), m_cols,
-                                                           (n + b - 1) / b, gblk::dpad_of(b), a);
+  // tile shape: estimated time = waves x tile area / per-pair efficiency (the 128 x 64 tile
+  // runs about 15 % more pairs per second than 64 x 64, which fills the GPU better when
+  // there are few tiles, e.g. a batch of decision rows)
+  const long long slots = 2LL * ctx->sm_count;
+  GramArgs a8 = a, a4 = a;
+  a8.ntiles = count_tiles(a8, gblk::RowTile<8>::TR, gblk::TC);
+  a4.ntiles = count_tiles(a4, gblk::RowTile<4>::TR, gblk::TC);
+  const double cost8 = double((a8.ntiles + slots - 1) / slots) * 2.0 / 1.15;
+  const double cost4 = double((a4.ntiles + slots - 1) / slots);
+  const int nbk = (n + b - 1) / b, dp = gblk::dpad_of(b);
+  const float2* srp = static_cast<const float2*>(states_rows);
+  const float2* scp = static_cast<const float2*>(states_cols);
+  if (cost8 <= cost4) {
+    auto kern = gblk::gram_blocks_kernel<8>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gblk::RowTile<8>::SMEM)) !=
+        cudaSuccess)
+      return DK_ERR_CUDA;
+    const int grid = int(a8.ntiles < slots ? a8.ntiles : slots);
+    kern<<<grid, gblk::NT, gblk::RowTile<8>::SMEM, st>>>(srp, m_rows, scp, m_cols, nbk, dp, a8);
+  } else {
+    auto kern = gblk::gram_blocks_kernel<4>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gblk::RowTile<4>::SMEM)) !=
+        cudaSuccess)
+      return DK_ERR_CUDA;
+    const int grid = int(a4.ntiles < slots ? a4.ntiles : slots);
+    kern<<<grid, gblk::NT, gblk::RowTile<4>::SMEM, st>>>(srp, m_rows, scp, m_cols, nbk, dp, a4);
+  }
   return launch_status();
 }

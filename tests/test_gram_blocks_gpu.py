@@ -78,6 +78,29 @@ def test_gram_blocks_vs_block_statevectors(dk, n, b, reps, ent):
     ctx.sync_status()
 
 
+def test_gram_blocks_large_tiles(dk):
+    """2000 samples, so that the 128 x 64 pair tile is the one chosen (2000 = 15 x 128 + 80
+    leaves a ragged last row tile): the full 2000 x 2000 Gram of two all-to-all blocks of 8
+    and 300 x 2000 rows (64 x 64 tiles), element by element."""
+    dualk, ctx, torch = dk
+    from oracle import gram as og
+    from paper_2602_01330_gb300 import synthetic
+    d = synthetic.fmnist_like(2000, 300, 16)
+    xtr, xte = d["x_train"], d["x_test"]
+    fm = dualk.FeatureMap(reps=2, block=8)
+    st = dualk.block_states(ctx, _dev(torch, xtr), fm, dualk.DK_ENT_FULL)
+    se = dualk.block_states(ctx, _dev(torch, xte), fm, dualk.DK_ENT_FULL)
+    g = dualk.gram_blocks(ctx, st, w=0.5)
+    r = dualk.gram_blocks(ctx, se, st, w=0.5)
+    torch.cuda.synchronize()
+    _check(g, _ref_log(xtr, xtr, 2, 8, "full"), og.rbf(xtr, xtr, 1.0 / 16), 0.5)
+    _check(r, _ref_log(xte, xtr, 2, 8, "full"), og.rbf(xte, xtr, 1.0 / 16), 0.5)
+    kq = g["kq"].cpu().numpy()
+    assert np.all(np.diag(kq) == 1.0)
+    assert np.array_equal(kq, kq.T)
+    ctx.sync_status()
+
+
 def test_gram_blocks_n784_log_kernel(dk):
     """All 784 pixels in blocks of 10 with all-to-all ZZ (exact bond up to 32 inside a block,
     beyond any bond-16 MPS): 48 images, every pair's log K_q against the oracle."""
