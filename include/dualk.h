@@ -186,6 +186,38 @@ dk_status dk_mps_build_blocks(dk_ctx* ctx, const float* x, int m, int n, const d
                               double cutoff, dk_dtype dtype, void* mps, int32_t* bond_dims, float* log_norm,
                               float* discarded, void* stream);
 
+/* One item of a feature-dimension sweep: the symmetric Gram of one MPS batch. */
+typedef struct {
+  const void* mps;        /* m samples, n sites (dk_mps_build layout, chi_max / dtype of the call) */
+  const float* log_norm;  /* m ln-norms in the arithmetic of the call's precision */
+  const float* x;         /* m x n features (needed for K_c: kc, or k with w != 1) */
+  float* k;               /* m x m outputs with row stride ld, any may be NULL but not all */
+  float* kq;
+  float* kc;
+  float* logkq;
+  long long ld;
+  int m, n;
+  int tile_shape;         /* 0: built-in tile shape; 1..dk_gram_config_count: a fixed one */
+} dk_sweep_item;
+
+/* The symmetric Gram matrices of a feature-dimension sweep (§II-D: a kernel matrix for
+ * every qubit count of a study, each filled block by block), each item as
+ * dk_gram_tile over all its samples with gamma = 1/n, mix weight w and precision prec,
+ * issued in order on `stream`.
+ * graph = 0: the launches are issued directly.
+ * graph = 1: the launches are recorded once into a CUDA graph that the context keeps
+ *   (keyed by the bytes of the item array and the other arguments, pointers included) and
+ *   replayed by every later call with the same key: one graph launch for the whole sweep.
+ *   The first call with a new key also computes the results (eagerly, before recording).
+ *   A replay reads the items' current buffer contents, so inputs may change between calls;
+ *   buffers must stay allocated while the context may replay them. At most 16 graphs are
+ *   kept (the oldest is destroyed); dk_destroy releases them. Needs a non-NULL stream.
+ * Errors: DK_ERR_ARG (NULL ctx/items, n_items < 1, an item with NULL mps or log_norm, m or
+ *         n < 1, no output, ld < m, tile_shape out of range; graph with the NULL stream),
+ *         and those of dk_gram_tile; DK_ERR_CUDA if recording or instantiation fails. */
+dk_status dk_gram_sweep(dk_ctx* ctx, const dk_sweep_item* items, int n_items, int chi_max, dk_dtype dtype,
+                        dk_precision prec, float w, int graph, void* stream);
+
 /* Block statevectors of a block-structured feature map (§II-C: entanglers only inside
  * blocks of b consecutive qubits, chain or all-to-all as for dk_mps_build_blocks). The state
  * is the Kronecker product of its blocks' states, so the overlap of Eq. 9 factorises over

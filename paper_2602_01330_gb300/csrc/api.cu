@@ -51,6 +51,7 @@ DK_API dk_status dk_create(dk_ctx** out, int device) {
 DK_API void dk_destroy(dk_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  dk::sweep_cache_free(ctx);
   cudaFree(ctx->status);
   free(ctx);
 }

@@ -20,6 +20,7 @@ struct dk_ctx {
   unsigned* status;  // device word, bits of dk::DEV_*
   dk_encode_tiled_fn encode_tiled;
   int gram_config;   // 0: built-in choice; otherwise a tile-shape id (dk_set_gram_config)
+  void* graphs;      // CUDA graphs recorded by dk_gram_sweep (sweep.cu), or NULL
 };
 
 namespace dk {
@@ -48,6 +49,9 @@ dk_status self_overlap32_tc_launch(const void* mps, int m, int n, float* log_nor
 // Self-overlap normalisers of the chi_max 4 / 8 kernels (mps_build.cu).
 dk_status self_overlap_launch(const void* mps, int m, int n, int chi, dk_dtype dtype, float* log_norm,
                               cudaStream_t st);
+
+// Destroys the graphs dk_gram_sweep recorded for this context (sweep.cu).
+void sweep_cache_free(dk_ctx* ctx);
 
 inline dk_status launch_status() {
   cudaError_t e = cudaGetLastError();

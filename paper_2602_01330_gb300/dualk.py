@@ -28,7 +28,7 @@ EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_
             "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout", "dk_self_overlap",
             "dk_svm_ovo_train", "dk_svm_ovo_predict", "dk_gram_stats", "dk_pca_workspace_bytes", "dk_pca_fit",
             "dk_pca_transform", "dk_pca_fit_noalloc", "dk_mps_build_blocks", "dk_block_states_bytes",
-            "dk_block_states", "dk_gram_blocks")
+            "dk_block_states", "dk_gram_blocks", "dk_gram_sweep")
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 PCA_MAX_FEATURES = 4096  # DK_PCA_MAX_FEATURES
 PCA_NOALLOC_MAX_FEATURES = 256  # DK_PCA_NOALLOC_MAX_FEATURES
@@ -72,6 +72,8 @@ def _lib():
     lib.dk_mps_build_blocks.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, ctypes.c_double, i32, vp, vp,
                                         vp, vp, vp]
     lib.dk_mps_build_blocks.restype = i32
+    lib.dk_gram_sweep.argtypes = [vp, ctypes.POINTER(_SweepItem), i32, i32, i32, i32, f32, i32, vp]
+    lib.dk_gram_sweep.restype = i32
     lib.dk_block_states_bytes.argtypes = [i32, i32, i32]
     lib.dk_block_states_bytes.restype = ctypes.c_size_t
     lib.dk_block_states.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, vp, vp, vp]
@@ -262,6 +264,29 @@ def mps_build(ctx: Context, x: torch.Tensor, fmap: FeatureMap, dtype: int = DK_C
     _check(_lib().dk_mps_build(ctx.handle, _ptr(x), m, n, ctypes.byref(fm), dtype, _ptr(out), _ptr(bond),
                                _ptr(lnorm), _stream(stream)), "dk_mps_build")
     return MPS(out, m, n, fmap.chi_max, dtype, bond, lnorm, x, fmap=fmap)
+
+
+class _SweepItem(ctypes.Structure):
+    _fields_ = [("mps", ctypes.c_void_p), ("log_norm", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("k", ctypes.c_void_p), ("kq", ctypes.c_void_p), ("kc", ctypes.c_void_p), ("logkq", ctypes.c_void_p),
+                ("ld", ctypes.c_longlong), ("m", ctypes.c_int), ("n", ctypes.c_int), ("tile_shape", ctypes.c_int)]
+
+
+def gram_sweep(ctx: "Context", items, w: float = 0.5, prec: int | None = None, graph: bool = False, stream=None):
+    """dk_gram_sweep over items = [(MPS, out dict of m x m tensors, tile_shape id)], all with
+    the same chi_max and dtype. graph=True records the launches once into a CUDA graph kept by
+    the context and replays it on later calls with the same items (needs a non-default stream)."""
+    first = items[0][0]
+    prec = _default_prec(first) if prec is None else prec
+    arr = (_SweepItem * len(items))()
+    for t, (mps, out, tile) in enumerate(items):
+        if mps.chi_max != first.chi_max or mps.dtype != first.dtype:
+            raise ValueError("sweep items differ in chi_max or dtype")
+        ln = mps.log_norm_for(ctx, prec, stream)
+        arr[t] = _SweepItem(_ptr(mps.data), _ptr(ln), _ptr(mps.x), _ptr(out.get("k")), _ptr(out.get("kq")),
+                            _ptr(out.get("kc")), _ptr(out.get("logkq")), mps.m, mps.m, mps.n, int(tile))
+    _check(_lib().dk_gram_sweep(ctx.handle, arr, len(items), first.chi_max, first.dtype, int(prec), float(w),
+                                1 if graph else 0, _stream(stream)), "dk_gram_sweep")
 
 
 DK_ENT_CHAIN, DK_ENT_FULL = 0, 1

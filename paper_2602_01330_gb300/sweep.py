@@ -169,6 +169,17 @@ class GramSweep:
             self.capture()
         self.graph.replay()
 
+    def run_native(self, graph: bool = True, stream=None):
+        """One pass through the library's own sweep call: the MPS builds, then every Gram by
+        dk_gram_sweep, which with graph=True records its launches once into a CUDA graph kept
+        by the context and replays it afterwards (a non-default stream is required)."""
+        items = []
+        for mt in self.mats:
+            mps = dualk.mps_build(self.ctx, mt.x, self.fmap, out=mt.mps, bond=mt.bond, log_norm=mt.log_norm,
+                                  stream=stream)
+            items.append((mps, mt.out, mt.cfg))
+        dualk.gram_sweep(self.ctx, items, w=self.w, graph=graph, stream=stream)
+
     def concentration(self) -> dict:
         """Per qubit count: mean and variance of the off-diagonal K_q and log K_q of the last
         pass (dk_gram_stats), the concentration of the quantum kernel as n grows."""
@@ -202,13 +213,23 @@ def main():
     eager = _time_ms(sw.run_eager, args.reps)
     sw.capture()
     graph = _time_ms(sw.replay, args.reps)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+
+    def native():
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            sw.run_native(graph=True, stream=side)
+        torch.cuda.current_stream().wait_stream(side)
+    native_ms = _time_ms(native, args.reps)
     ctx.sync_status()
     units = sw.entries_qubits()
     print(json.dumps({
         "workload": f"sweep d={dims} m={args.m} reps=2 chi=4",
         "entry_qubits": units,
-        "eager_ms": eager, "graph_ms": graph,
+        "eager_ms": eager, "graph_ms": graph, "native_sweep_graph_ms": native_ms,
         "eager_entry_qubits_per_s": units / (eager / 1e3), "graph_entry_qubits_per_s": units / (graph / 1e3),
+        "native_sweep_entry_qubits_per_s": units / (native_ms / 1e3),
         "tile_shapes": {mt.d: (mt.cfg, dualk.gram_config_info(mt.cfg) if mt.cfg else None) for mt in sw.mats},
         "concentration": {d: {k: s[k] for k in ("kq_mean", "kq_var", "logkq_mean", "logkq_var")}
                           for d, s in sw.concentration().items()},

@@ -42,6 +42,21 @@ def test_sweep_graph_equals_eager_and_oracle(env):
     for mt in sw.mats:
         for k in mt.out:
             assert torch.equal(mt.out[k], eager[mt.d][k]), (mt.d, k)
+    # the library's own sweep call (dk_gram_sweep), recorded into a graph and replayed
+    side = torch.cuda.Stream()
+    for rnd in range(2):
+        for mt in sw.mats:
+            for v in mt.out.values():
+                v.fill_(-1.0)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            sw.run_native(graph=True, stream=side)
+        side.synchronize()
+        for mt in sw.mats:
+            for k in mt.out:
+                assert torch.equal(mt.out[k], eager[mt.d][k]), (rnd, mt.d, k)
+    ctx.sync_status()
+    for mt in sw.mats:
         x = feats[mt.d].astype(np.float64)
         sites, _ = mps.build_mps(x, 2)
         kq, _ = gram.gram_from_mps(sites, sites)
