@@ -119,3 +119,52 @@ def dense_state(x, reps, c=2.0, entangle=True, all_pairs=False):
 def exact_bond_rank(n: int, reps: int, bond: int) -> int:
     """Schmidt rank bound across the cut left of site `bond` (1..n-1) for the ZZ chain."""
     return min(2 ** bond, 2 ** (n - bond), 2 ** reps)
+
+
+def chain_site_tensors(x, reps, c=2.0):
+    """Form 6: the ZZ-chain state as an MPS written down from the gate algebra, for any reps.
+
+    Expanding every H^(x)n layer over computational-basis states, the amplitude of the final
+    basis state is a sum over the intermediate bit strings b^(1..reps-1) (b^(0) = 0...0). Per
+    qubit q collect its bits across repetitions into c_q (bit rho-1 = b^(rho)_q, so the top bit
+    is the output bit). Each H contributes 2^(-1/2) (-1)^(b^(rho)_q b^(rho-1)_q), each RZ layer
+    exp(-i c x_q z/2) and each RZZ layer exp(-i (pi - x_q)(pi - x_{q+1}) z_q z_{q+1}), z = 1 - 2b.
+    Summed over rho these depend on c_q alone (site factor) and on (c_q, c_{q+1}) (bond
+    factor), so A^(q)_s[c_{q-1}][c_q] = [top bit of c_q = s] F_q(c_q) W_{q-1}(c_{q-1}, c_q).
+    Returns a list of arrays (2, D_left, D_right) with D = 2^reps (1 at the left end)."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    dim = 2 ** reps
+    cs = np.arange(dim)
+    bits = (cs[:, None] >> np.arange(reps)[None, :]) & 1          # [c, rho-1] = b^(rho)
+    z = 1 - 2 * bits
+    had = np.array([(-1.0) ** sum(bits[cc, r] * bits[cc, r - 1] for r in range(1, reps)) for cc in cs])
+    top = bits[:, reps - 1]
+    sites = []
+    for q in range(n):
+        f = 2.0 ** (-reps / 2) * had * np.exp(-0.5j * c * x[q] * z.sum(axis=1))
+        if q == 0:
+            w = np.ones((1, dim))
+        else:
+            j = (np.pi - x[q - 1]) * (np.pi - x[q])
+            w = np.exp(-1j * j * (z[:, None, :] * z[None, :, :]).sum(axis=2))   # [c_{q-1}, c_q]
+        a = np.zeros((2, w.shape[0], dim), dtype=np.complex128)
+        for s in (0, 1):
+            a[s] = w * (f * (top == s))[None, :]
+        sites.append(a)
+    return sites
+
+
+def chain_log_overlap(x, y, reps, c=2.0):
+    """ln|<psi(x)|psi(y)>| from the form-6 tensors by a left-to-right transfer contraction
+    with an exact power-of-two rescale after every site (the right end sums the bond)."""
+    ax, ay = chain_site_tensors(x, reps, c), chain_site_tensors(y, reps, c)
+    e = np.ones((1, 1), dtype=np.complex128)
+    exp2 = 0
+    for a, b in zip(ax, ay):
+        e = a[0].conj().T @ e @ b[0] + a[1].conj().T @ e @ b[1]
+        _, ex = np.frexp(np.max(np.abs(e)))
+        e = e * np.ldexp(1.0, -int(ex))  # an exact power of two
+        exp2 += int(ex)
+    amp = e.sum()
+    return float(np.log(abs(amp)) + exp2 * np.log(2.0))

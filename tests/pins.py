@@ -282,3 +282,24 @@ def single_cut_truncation(reps: int = 2, seed: int = 28) -> float:
         if tail < 1e-6:  # the pin needs a truncation that bites
             return 1.0
     return err
+
+
+def chain_closed_form_vs_statevector(n: int = 6, reps: int = 2, seed: int = 51) -> float:
+    """Form 6 (the chain MPS written from the gate algebra) against the oracle's brute-force
+    statevector overlaps: largest |ln|a| difference|."""
+    x = synthetic.uniform_angles(3, n, seed)
+    err = 0.0
+    for i in range(2):
+        a = np.vdot(circuit.statevector(x[i], reps), circuit.statevector(x[i + 1], reps))
+        err = max(err, abs(np.log(abs(a)) - cf.chain_log_overlap(x[i], x[i + 1], reps)))
+    return err
+
+
+def chain_large_n_vs_closed_form(n: int = 784, reps: int = 2, pairs: int = 3) -> float:
+    """The oracle's TEBD MPS + transfer log K_q of the chain at large n against form 6 (an
+    independent algorithm: closed-form tensors, no SVD), largest relative error."""
+    x = synthetic.fmnist_like(pairs + 1, 0, n)["x_train"].astype(np.float64)
+    sites, _ = mps.build_mps(x, reps)
+    _, lkq = gram.pair_values(sites, sites, list(range(pairs)), list(range(1, pairs + 1)))
+    ref = np.array([2.0 * cf.chain_log_overlap(x[i], x[i + 1], reps) for i in range(pairs)])
+    return float(np.max(np.abs(np.asarray(lkq) - ref) / np.maximum(1.0, np.abs(ref))))

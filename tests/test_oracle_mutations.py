@@ -44,6 +44,7 @@ PIN_SUITE = [
     ("mps vs sv r3", lambda: pins.mps_vs_statevector(7, 3), 1e-11),
     ("ranks", lambda: float(pins.bond_ranks(7, 2)), 0.5),
     ("deep underflow", deep_underflow, 1e-9),
+    ("chain form 6 large n", lambda: pins.chain_large_n_vs_closed_form(60, 2, 2), 1e-10),
     ("bps kron", lambda: pins.bps_statevector_vs_kron(9, 2, 4), 1e-12),
     ("bps blocks", lambda: pins.bps_log_kernel_vs_block_products(20, 2, 6), 1e-10),
     ("full sv", lambda: pins.full_statevector_vs_dense(5, 2, 4), 1e-12),

@@ -127,6 +127,18 @@ def test_block_mps_chain_matches_tebd():
     assert mps.bond_dims(a) == mps.bond_dims(t)
 
 
+@pytest.mark.parametrize("n,reps", [(5, 1), (6, 2), (7, 3), (4, 4), (3, 5)])
+def test_chain_closed_form_matches_statevector(n, reps):
+    assert pins.chain_closed_form_vs_statevector(n, reps) < 1e-12
+
+
+@pytest.mark.parametrize("n,reps", [(784, 2), (784, 3), (256, 5)])
+def test_oracle_chain_at_large_n_matches_closed_form(n, reps):
+    # the plain chain at two or more repetitions, where no product or Ising form exists:
+    # the oracle's gate-by-gate TEBD against the closed-form tensors, exact to rounding
+    assert pins.chain_large_n_vs_closed_form(n, reps) < 1e-10
+
+
 def test_large_n_ising_log_domain():
     # n = 784, one repetition with entanglers: off-diagonal K_q far below 1e-300.
     assert pins.large_n_ising(784) < 1e-10
