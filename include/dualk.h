@@ -230,24 +230,31 @@ size_t dk_block_states_bytes(int m, int n, int block);
  *   fm        reps 1..5, angle_scale, entangle (0: product state), block (see above);
  *             chi_max and qr_prec are ignored
  *   entangler DK_ENT_CHAIN or DK_ENT_FULL
+ *   prec      DK_PREC_F32: states for the FP32 CUDA-core Gram; DK_PREC_BF16X3: for the
+ *             split-BF16 tensor-core Gram (pass the same precision to dk_gram_blocks)
  *   states    dk_block_states_bytes(m, n, fm->block) bytes (device, written), layout
- *             [block][sample][dpad] complex64: the block's 2^b amplitudes (qubit 0 of the
- *             block most significant), computed in FP64 and rounded once; zeros beyond
- *             2^b and beyond the 2^(n mod b) amplitudes of a short last block
+ *             [block][sample][...] of dpad amplitudes (qubit 0 of the block most
+ *             significant), computed in FP64 and rounded once: F32 as complex64 values;
+ *             BF16X3 as four BF16 planes [hi(re) | hi(im) | lo(re) | lo(im)] with
+ *             v ~ hi + lo; zeros beyond 2^b and beyond the 2^(n mod b) amplitudes of a short
+ *             last block
  *   log_norm  m floats (device, written, may be NULL): ln|<psi~_i|psi~_i>| of the rounded
- *             states by the arithmetic of dk_gram_blocks, so that K_q(x, x) = 1 exactly
+ *             states by the arithmetic of dk_gram_blocks in `prec` (for BF16X3 the diagonal
+ *             tiles of that Gram), so that K_q(x, x) = 1 exactly
  * Errors: DK_ERR_ARG (NULL pointers, m or n < 1, reps, entangler, misaligned states),
  *         DK_ERR_UNSUPPORTED (block outside 0..12 or above 12 qubits, m > 65535, more than
- *         6144 blocks), DK_ERR_CUDA. */
+ *         6144 blocks, prec neither F32 nor BF16X3), DK_ERR_CUDA. */
 dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm, int entangler,
-                          void* states, float* log_norm, void* stream);
+                          dk_precision prec, void* states, float* log_norm, void* stream);
 
 /* A block of the Gram matrix of a block-structured map from block statevectors, outputs
  * and epilogue as dk_gram_tile (§II-C Eqs. 8-10 factorised over blocks; §II-B Eq. 3;
  * §II-D Eq. 11): for each pair, a = prod_B <psi_B(x_i)|psi_B(x_j)> with each factor a
- * complex dot product of 2^b amplitudes in FP32 (CUDA cores), ln|a| accumulated as a
- * mantissa and binary exponent (never underflows); log K_q = 2 ln|a| - ln N_i - ln N_j,
- * K_q, K_c = exp(-gamma ||x_i - x_j||^2), K = w K_q + (1 - w) K_c.
+ * complex dot product of 2^b amplitudes — prec DK_PREC_F32: FP32 FMAs on CUDA cores;
+ * DK_PREC_BF16X3: split-BF16 tensor-core products with FP32 accumulation (|dK| ~ 1e-5,
+ * the 1e-4 mixed-precision class) — and ln|a| accumulated as a sum of log2 |factor|^2
+ * (never underflows); log K_q = 2 ln|a| - ln N_i - ln N_j, K_q,
+ * K_c = exp(-gamma ||x_i - x_j||^2), K = w K_q + (1 - w) K_c.
  *   states_rows / states_cols  dk_block_states output for m_rows / m_cols samples, same n
  *                              and block; lnorm_rows / lnorm_cols their log_norm
  *   x_rows / x_cols            features (needed for K_c: kc_out, or k_out with w != 1)
@@ -256,12 +263,12 @@ dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, const dk_fm
  *                              computes each unordered pair once and writes both entries
  * Errors: DK_ERR_ARG (NULL inputs, ranges outside the sample counts, ld < ncols, no
  *         output, symmetric with different rows and columns, K_c needed without x),
- *         DK_ERR_UNSUPPORTED (block), DK_ERR_CUDA. */
+ *         DK_ERR_UNSUPPORTED (block, prec neither F32 nor BF16X3), DK_ERR_CUDA. */
 dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows, const void* states_cols, int m_cols,
                          int n, int block, int row0, int nrows, int col0, int ncols, const float* lnorm_rows,
                          const float* lnorm_cols, const float* x_rows, const float* x_cols, float gamma, float w,
-                         float* k_out, float* kq_out, float* kc_out, float* logkq_out, long long ld, int symmetric,
-                         void* stream);
+                         dk_precision prec, float* k_out, float* kq_out, float* kc_out, float* logkq_out,
+                         long long ld, int symmetric, void* stream);
 
 /* ln|<psi~_i|psi~_i>| of the stored (rounded) MPS of m samples, computed with the
  * arithmetic of precision `prec`, so that a Gram call with the same precision and these

@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import statistics
 
 import torch
@@ -25,8 +26,20 @@ def gram_flops(m_rows: int, m_cols: int, n: int, block: int, symmetric: bool) ->
     return pairs * nb * 8 * max(2 ** block, 16)
 
 
+def bf16_peak_tflops() -> tuple[float, str]:
+    """Dense BF16 tensor peak: the measured burst figure of this machine's GPUs when the
+    measurement file is present at the repository root, else 1900 (an earlier GB300 run)."""
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
 def run_benchmark(ctx: dualk.Context, m: int = 2000, m_test: int = 500, n: int = 784, block: int = 10,
-                  reps: int = 2, entangler: int = dualk.DK_ENT_FULL, w: float = 0.5, iters: int = 3) -> dict:
+                  reps: int = 2, entangler: int = dualk.DK_ENT_FULL, w: float = 0.5, iters: int = 3,
+                  prec: int = dualk.DK_PREC_F32) -> dict:
     d = synthetic.fmnist_like(m, m_test, n)
     xtr = torch.from_numpy(d["x_train"]).cuda()
     xte = torch.from_numpy(d["x_test"]).cuda()
@@ -36,8 +49,8 @@ def run_benchmark(ctx: dualk.Context, m: int = 2000, m_test: int = 500, n: int =
     for it in range(iters + 1):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(st)
-        tr = dualk.block_states(ctx, xtr, fm, entangler)
-        te = dualk.block_states(ctx, xte, fm, entangler) if m_test > 0 else None
+        tr = dualk.block_states(ctx, xtr, fm, entangler, prec=prec)
+        te = dualk.block_states(ctx, xte, fm, entangler, prec=prec) if m_test > 0 else None
         ev[1].record(st)
         g = dualk.gram_blocks(ctx, tr, w=w, want=("k", "kq", "kc", "logkq"))
         ev[2].record(st)
@@ -52,8 +65,18 @@ def run_benchmark(ctx: dualk.Context, m: int = 2000, m_test: int = 500, n: int =
     ctx.sync_status()
     t = {k: statistics.mean(v) for k, v in times.items()}
     props = torch.cuda.get_device_properties(0)
-    peak = workload.fp32_peak_tflops(props.multi_processor_count, 2070.0)
     achieved = gram_flops(m, m, n, block, True) / (t["gram_ms"] * 1e-3) / 1e12
+    if prec == dualk.DK_PREC_BF16X3:
+        bf16, src = bf16_peak_tflops()
+        roof = {"bound": "tensor", "kernel": "gram_blocks_tc_kernel (symmetric Gram, mma.sync bf16x3)",
+                "achieved": achieved, "peak": bf16 / 3, "unit": "TFLOP/s (FP32-equivalent)",
+                "frac": achieved / (bf16 / 3),
+                "peak_source": f"dense BF16 {bf16:.1f} TFLOP/s ({src}) / 3 products per FP32-equivalent product"}
+    else:
+        peak = workload.fp32_peak_tflops(props.multi_processor_count, 2070.0)
+        roof = {"bound": "alu", "kernel": "gram_blocks_kernel (symmetric Gram)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"FP32 FMA peak {props.multi_processor_count} SMs x 128 lanes x 2 x 2070 MHz"}
     entries = m * (m + 1) / 2 + m * m_test
     diag = torch.diagonal(g["kq"])
     return {
@@ -62,9 +85,8 @@ def run_benchmark(ctx: dualk.Context, m: int = 2000, m_test: int = 500, n: int =
                     f"{m} train (symmetric Gram) + {m_test} test rows",
         **t,
         "entry_qubits_per_s": entries * n / ((t["gram_ms"] + t["rows_ms"]) * 1e-3),
-        "roofline": {"bound": "alu", "kernel": "gram_blocks_kernel (symmetric Gram)", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": f"FP32 FMA peak {props.multi_processor_count} SMs x 128 lanes x 2 x 2070 MHz"},
+        "precision": "bf16x3" if prec == dualk.DK_PREC_BF16X3 else "f32",
+        "roofline": roof,
         "diag_kq_exactly_1": bool(torch.all(diag == 1.0).item()),
         "mean_offdiag_log_kq": float((g["logkq"].sum() - g["logkq"].diagonal().sum()).item() / (m * m - m)),
         "max_row_k": float(r["k"].max().item()) if r is not None else None,
@@ -80,10 +102,13 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--entangler", choices=("full", "chain"), default="full")
     ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--prec", choices=("f32", "bf16x3"), default="f32")
     args = ap.parse_args()
     ctx = dualk.Context(0)
     ent = dualk.DK_ENT_FULL if args.entangler == "full" else dualk.DK_ENT_CHAIN
-    print(json.dumps(run_benchmark(ctx, args.m, args.m_test, args.n, args.block, args.reps, ent, iters=args.iters)))
+    prec = dualk.DK_PREC_BF16X3 if args.prec == "bf16x3" else dualk.DK_PREC_F32
+    print(json.dumps(run_benchmark(ctx, args.m, args.m_test, args.n, args.block, args.reps, ent, iters=args.iters,
+                                   prec=prec)))
     ctx.close()
 
 

@@ -20,6 +20,7 @@
 //     (Kahan FP32 distance) and the mix.
 //   * block_selfnorm_kernel: ln N_i = ln|a(x_i, x_i)| with exactly the per-pair arithmetic of
 //     gram_blocks_kernel (same chunk order, same FMA sequence), so K_q(x, x) = 1 exactly.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "block_state.cuh"
@@ -63,9 +64,11 @@ __device__ __forceinline__ void lg_add(float& lg, float2 g) { lg += log2f(fmaf(g
 // ln|a| from the log2 sum of |a|^2
 __device__ __forceinline__ float half_log_lg(float lg) { return lg * (0.5f * 0.69314718055994530942f); }
 
+// split = 0: complex64 [dpad]; split = 1: BF16 planes [hi_re | hi_im | lo_re | lo_im] of dpad
+// values each (the operand form of the tensor-core Gram, same 8 bytes per amplitude)
 __global__ void __launch_bounds__(BUILD_NT) block_states_kernel(const float* __restrict__ x, int m, int n, int b,
                                                                 int reps, double angle_scale, int pairs_kind,
-                                                                float2* __restrict__ states) {
+                                                                int split, float2* __restrict__ states) {
   extern __shared__ __align__(16) unsigned char raw[];
   blockstate::Coeffs& C = *reinterpret_cast<blockstate::Coeffs*>(raw);
   double2* psi = reinterpret_cast<double2*>(raw + ((sizeof(blockstate::Coeffs) + 15) & ~size_t(15)));
@@ -77,8 +80,20 @@ __global__ void __launch_bounds__(BUILD_NT) block_states_kernel(const float* __r
   blockstate::build(psi, ph, C, x + size_t(i) * n + start, bl, reps, angle_scale, pairs_kind, threadIdx.x, BUILD_NT);
   float2* out = states + (size_t(blk) * m + i) * dp;
   const int dim = 1 << bl;
-  for (int k = threadIdx.x; k < dp; k += BUILD_NT)
-    out[k] = k < dim ? make_float2(float(psi[k].x), float(psi[k].y)) : make_float2(0.0f, 0.0f);
+  if (!split) {
+    for (int k = threadIdx.x; k < dp; k += BUILD_NT)
+      out[k] = k < dim ? make_float2(float(psi[k].x), float(psi[k].y)) : make_float2(0.0f, 0.0f);
+    return;
+  }
+  __nv_bfloat16* pl = reinterpret_cast<__nv_bfloat16*>(out);
+  for (int k = threadIdx.x; k < dp; k += BUILD_NT) {
+    const float vr = k < dim ? float(psi[k].x) : 0.0f, vi = k < dim ? float(psi[k].y) : 0.0f;
+    const __nv_bfloat16 hr = __float2bfloat16_rn(vr), hi = __float2bfloat16_rn(vi);
+    pl[k] = hr;
+    pl[dp + k] = hi;
+    pl[2 * dp + k] = __float2bfloat16_rn(vr - __bfloat162float(hr));
+    pl[3 * dp + k] = __float2bfloat16_rn(vi - __bfloat162float(hi));
+  }
 }
 
 // One CTA per sample: thread B forms <psi_B|psi_B> with the Gram kernel's sequential
@@ -237,9 +252,10 @@ DK_API size_t dk_block_states_bytes(int m, int n, int block) {
 }
 
 DK_API dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm, int entangler,
-                                 void* states, float* log_norm, void* stream) {
+                                 dk_precision prec, void* states, float* log_norm, void* stream) {
   using namespace dk;
   if (!ctx || !x || !fm || !states || m < 1 || n < 1) return DK_ERR_ARG;
+  if (prec != DK_PREC_F32 && prec != DK_PREC_BF16X3) return DK_ERR_UNSUPPORTED;
   if (fm->reps < 1 || fm->reps > 5) return DK_ERR_ARG;
   if (entangler != DK_ENT_CHAIN && entangler != DK_ENT_FULL) return DK_ERR_ARG;
   if (!aligned16(states)) return DK_ERR_ARG;
@@ -254,20 +270,24 @@ DK_API dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, cons
   if (cudaFuncSetAttribute(gblk::block_states_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
       cudaSuccess)
     return DK_ERR_CUDA;
+  const int split = prec == DK_PREC_BF16X3 ? 1 : 0;
   gblk::block_states_kernel<<<dim3(nb, m), gblk::BUILD_NT, smem, st>>>(x, m, n, b, fm->reps, double(fm->angle_scale),
-                                                                      kind, static_cast<float2*>(states));
-  if (log_norm)
-    gblk::block_selfnorm_kernel<<<m, gblk::NORM_NT, nb * sizeof(float2), st>>>(static_cast<const float2*>(states), m,
-                                                                             nb, gblk::dpad_of(b), log_norm);
+                                                                      kind, split, static_cast<float2*>(states));
+  dk_status s = launch_status();
+  if (s != DK_OK || !log_norm) return s;
+  if (split) return block_selfnorm_tc_launch(states, m, nb, gblk::dpad_of(b), log_norm, st);
+  gblk::block_selfnorm_kernel<<<m, gblk::NORM_NT, nb * sizeof(float2), st>>>(static_cast<const float2*>(states), m,
+                                                                           nb, gblk::dpad_of(b), log_norm);
   return launch_status();
 }
 
 DK_API dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows, const void* states_cols, int m_cols,
                                 int n, int block, int row0, int nrows, int col0, int ncols, const float* lnorm_rows,
                                 const float* lnorm_cols, const float* x_rows, const float* x_cols, float gamma,
-                                float w, float* k_out, float* kq_out, float* kc_out, float* logkq_out, long long ld,
-                                int symmetric, void* stream) {
+                                float w, dk_precision prec, float* k_out, float* kq_out, float* kc_out,
+                                float* logkq_out, long long ld, int symmetric, void* stream) {
   using namespace dk;
+  if (prec != DK_PREC_F32 && prec != DK_PREC_BF16X3) return DK_ERR_UNSUPPORTED;
   if (!ctx || !states_rows || !states_cols || !lnorm_rows || !lnorm_cols) return DK_ERR_ARG;
   if (m_rows < 1 || m_cols < 1 || n < 1 || nrows < 0 || ncols < 0 || row0 < 0 || col0 < 0) return DK_ERR_ARG;
   if (row0 + nrows > m_rows || col0 + ncols > m_cols) return DK_ERR_ARG;
@@ -301,6 +321,9 @@ DK_API dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows
   a.status = ctx->status;
   a.need_kc = need_kc ? 1 : 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == DK_PREC_BF16X3)
+    return gram_blocks_tc_launch(ctx, states_rows, m_rows, states_cols, m_cols, (n + b - 1) / b, gblk::dpad_of(b), a,
+                                 st);
   // tile shape: estimated time = waves x tile area / per-pair efficiency (the 128 x 64 tile
   // runs about 15 % more pairs per second than 64 x 64, which fills the GPU better when
   // there are few tiles, e.g. a batch of decision rows)

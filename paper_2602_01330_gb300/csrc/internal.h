@@ -50,6 +50,10 @@ dk_status self_overlap32_tc_launch(const void* mps, int m, int n, float* log_nor
 dk_status self_overlap_launch(const void* mps, int m, int n, int chi, dk_dtype dtype, float* log_norm,
                               cudaStream_t st);
 
+// Block-statevector Gram on tensor cores and its self-norms (gram_blocks_tc.cu).
+dk_status gram_blocks_tc_launch(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp,
+                                GramArgs a, cudaStream_t st);
+dk_status block_selfnorm_tc_launch(const void* states, int m, int nb, int dp, float* log_norm, cudaStream_t st);
 // Destroys the graphs dk_gram_sweep recorded for this context (sweep.cu).
 void sweep_cache_free(dk_ctx* ctx);
 

@@ -76,10 +76,10 @@ def _lib():
     lib.dk_gram_sweep.restype = i32
     lib.dk_block_states_bytes.argtypes = [i32, i32, i32]
     lib.dk_block_states_bytes.restype = ctypes.c_size_t
-    lib.dk_block_states.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, vp, vp, vp]
+    lib.dk_block_states.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, i32, vp, vp, vp]
     lib.dk_block_states.restype = i32
     lib.dk_gram_blocks.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, f32, f32,
-                                   vp, vp, vp, vp, i64, i32, vp]
+                                   i32, vp, vp, vp, vp, i64, i32, vp]
     lib.dk_gram_blocks.restype = i32
     lib.dk_gram_tile.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, i32,
                                  vp, vp, vp, vp, f32, f32, i32, vp, vp, vp, vp, i64, i32, vp]
@@ -318,11 +318,13 @@ class BlockStates:
     block: int
     log_norm: torch.Tensor  # float32, m
     x: torch.Tensor         # float32 m x n features
+    prec: int = 0           # DK_PREC_F32 (complex64) or DK_PREC_BF16X3 (split planes)
 
 
 def block_states(ctx: Context, x: torch.Tensor, fmap: FeatureMap, entangler: int = DK_ENT_FULL,
-                 stream=None) -> BlockStates:
-    """dk_block_states: per-block statevectors of a block-structured map (fmap.block qubits)."""
+                 prec: int = DK_PREC_F32, stream=None) -> BlockStates:
+    """dk_block_states: per-block statevectors of a block-structured map (fmap.block qubits),
+    laid out for the Gram precision `prec` (F32 CUDA cores or BF16X3 tensor cores)."""
     _need_cuda(x, "x", torch.float32)
     m, n = x.shape
     nbytes = int(_lib().dk_block_states_bytes(m, n, int(fmap.block)))
@@ -331,9 +333,9 @@ def block_states(ctx: Context, x: torch.Tensor, fmap: FeatureMap, entangler: int
     out = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
     log_norm = torch.empty(m, dtype=torch.float32, device=x.device)
     fm = fmap._c()
-    _check(_lib().dk_block_states(ctx.handle, _ptr(x), m, n, ctypes.byref(fm), int(entangler), _ptr(out),
+    _check(_lib().dk_block_states(ctx.handle, _ptr(x), m, n, ctypes.byref(fm), int(entangler), int(prec), _ptr(out),
                                   _ptr(log_norm), _stream(stream)), "dk_block_states")
-    return BlockStates(out, m, n, fmap.block, log_norm, x)
+    return BlockStates(out, m, n, fmap.block, log_norm, x, int(prec))
 
 
 def gram_blocks(ctx: Context, rows: BlockStates, cols: BlockStates | None = None, gamma: float | None = None,
@@ -341,13 +343,14 @@ def gram_blocks(ctx: Context, rows: BlockStates, cols: BlockStates | None = None
     """dk_gram_blocks: K, K_q, K_c, log K_q of rows x cols (symmetric when cols is None)."""
     symmetric = cols is None
     cols = rows if cols is None else cols
-    if rows.n != cols.n or rows.block != cols.block:
-        raise ValueError("row and column states differ in n or block")
+    if rows.n != cols.n or rows.block != cols.block or rows.prec != cols.prec:
+        raise ValueError("row and column states differ in n, block or precision")
     gamma = 1.0 / rows.n if gamma is None else gamma
     out = _outs((rows.m, cols.m), rows.data.device, want)
     _check(_lib().dk_gram_blocks(ctx.handle, _ptr(rows.data), rows.m, _ptr(cols.data), cols.m, rows.n, rows.block,
                                  0, rows.m, 0, cols.m, _ptr(rows.log_norm), _ptr(cols.log_norm), _ptr(rows.x),
-                                 _ptr(cols.x), float(gamma), float(w), _ptr(out.get("k")), _ptr(out.get("kq")),
+                                 _ptr(cols.x), float(gamma), float(w), rows.prec, _ptr(out.get("k")),
+                                 _ptr(out.get("kq")),
                                  _ptr(out.get("kc")), _ptr(out.get("logkq")), int(cols.m), 1 if symmetric else 0,
                                  _stream(stream)), "dk_gram_blocks")
     return out

@@ -140,6 +140,65 @@ def test_gram_blocks_agrees_with_mps_paths(dk):
     ctx.sync_status()
 
 
+def _check_tol(out, lref, kc_ref, w, tol):
+    kq = out["kq"].cpu().numpy().astype(np.float64)
+    kq_ref = np.exp(lref)
+    assert np.max(np.abs(kq - kq_ref)) <= tol
+    assert np.max(np.abs(out["kc"].cpu().numpy() - kc_ref)) <= 1e-6
+    assert np.max(np.abs(out["k"].cpu().numpy() - (w * kq_ref + (1 - w) * kc_ref))) <= tol
+    lkq = out["logkq"].cpu().numpy().astype(np.float64)
+    sel = lref > -700
+    assert np.all(np.abs(lkq[sel] - lref[sel]) <= 1e-3 * np.maximum(1.0, np.abs(lref[sel])))
+
+
+@pytest.mark.parametrize("m,n,b,reps,ent", [(70, 40, 8, 2, "full"), (70, 50, 7, 2, "chain"), (70, 36, 12, 2, "full"),
+                                            (70, 9, 2, 3, "full"), (300, 16, 8, 2, "full"), (2000, 16, 8, 2, "full")])
+def test_gram_blocks_bf16x3_tensor_cores(dk, m, n, b, reps, ent):
+    """Split-BF16 tensor-core form against the oracle with the mixed-precision tolerance
+    1e-4 on K_q and K (K_c stays FP32, 1e-6): one ragged 128 x 64 tile (70 samples), several
+    (300) and a full-size Gram (2000 = 15 x 128 + 80); short last blocks (n = 50, 9); rows;
+    exact unit diagonal from the self-norms of the same MMA sequence; exact symmetry."""
+    dualk, ctx, torch = dk
+    from oracle import gram as og
+    from paper_2602_01330_gb300 import synthetic
+    d = synthetic.fmnist_like(m, 20, n)
+    xtr, xte = d["x_train"], d["x_test"]
+    fm = dualk.FeatureMap(reps=reps, block=b)
+    e = dualk.DK_ENT_FULL if ent == "full" else dualk.DK_ENT_CHAIN
+    p = dualk.DK_PREC_BF16X3
+    str_ = dualk.block_states(ctx, _dev(torch, xtr), fm, e, prec=p)
+    ste = dualk.block_states(ctx, _dev(torch, xte), fm, e, prec=p)
+    g = dualk.gram_blocks(ctx, str_, w=0.5)
+    r = dualk.gram_blocks(ctx, ste, str_, w=0.5)
+    torch.cuda.synchronize()
+    _check_tol(g, _ref_log(xtr, xtr, reps, b, ent), og.rbf(xtr, xtr, 1.0 / n), 0.5, 1e-4)
+    _check_tol(r, _ref_log(xte, xtr, reps, b, ent), og.rbf(xte, xtr, 1.0 / n), 0.5, 1e-4)
+    kq = g["kq"].cpu().numpy()
+    assert np.all(np.diag(kq) == 1.0)
+    assert np.array_equal(kq, kq.T)
+    ctx.sync_status()
+
+
+def test_gram_blocks_bf16x3_n784_matches_fp32(dk):
+    """n = 784 in blocks of 10: the tensor-core log K_q against the FP32 form (and both
+    against the oracle on a sample) to 1e-4 relative."""
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    x = _dev(torch, synthetic.fmnist_like(200, 0, 784)["x_train"])
+    fm = dualk.FeatureMap(reps=2, block=10)
+    a = dualk.gram_blocks(ctx, dualk.block_states(ctx, x, fm, dualk.DK_ENT_FULL), w=1.0, want=("logkq",))
+    b = dualk.gram_blocks(ctx, dualk.block_states(ctx, x, fm, dualk.DK_ENT_FULL, prec=dualk.DK_PREC_BF16X3), w=1.0,
+                          want=("logkq",))
+    torch.cuda.synchronize()
+    la, lb = a["logkq"].cpu().numpy().astype(np.float64), b["logkq"].cpu().numpy().astype(np.float64)
+    off = ~np.eye(200, dtype=bool)
+    assert np.max(np.abs(la[off] - lb[off]) / np.abs(la[off])) <= 1e-4
+    ref = _ref_log(x[:12].cpu().numpy(), x[:12].cpu().numpy(), 2, 10, "full")
+    o12 = ~np.eye(12, dtype=bool)
+    assert np.max(np.abs(lb[:12, :12][o12] - ref[o12]) / np.abs(ref[o12])) <= 1e-4
+    ctx.sync_status()
+
+
 def test_gram_blocks_errors(dk):
     dualk, ctx, torch = dk
     x = torch.rand(8, 30, device="cuda")
@@ -153,9 +212,9 @@ def test_gram_blocks_errors(dk):
     # symmetric with different row and column ranges
     assert lib.dk_gram_blocks(ctx.handle, dualk._ptr(st.data), 8, dualk._ptr(st.data), 8, 30, 6, 0, 4, 2, 4,
                               dualk._ptr(st.log_norm), dualk._ptr(st.log_norm), dualk._ptr(x), dualk._ptr(x),
-                              0.1, 1.0, None, dualk._ptr(out), None, None, 8, 1, dualk._stream(None)) == 1
+                              0.1, 1.0, 0, None, dualk._ptr(out), None, None, 8, 1, dualk._stream(None)) == 1
     # ld below ncols
     assert lib.dk_gram_blocks(ctx.handle, dualk._ptr(st.data), 8, dualk._ptr(st.data), 8, 30, 6, 0, 8, 0, 8,
                               dualk._ptr(st.log_norm), dualk._ptr(st.log_norm), dualk._ptr(x), dualk._ptr(x),
-                              0.1, 1.0, None, dualk._ptr(out), None, None, 4, 0, dualk._stream(None)) == 1
+                              0.1, 1.0, 0, None, dualk._ptr(out), None, None, 4, 0, dualk._stream(None)) == 1
     ctx.sync_status()
