@@ -380,7 +380,9 @@ def run_ours(args):
                                      gram=(g_out["kq"], g_out["kc"], r_out["kq"], r_out["kc"]))
         # the same data through a block-structured map (all-to-all ZZ in blocks of 10 qubits),
         # contracted exactly by per-block statevector overlaps
-        block_stats = blockmap.run_benchmark(ctx, n_tr, n_te, d, block=10, reps=reps)
+        block_stats = {"f32": blockmap.run_benchmark(ctx, n_tr, n_te, d, block=10, reps=reps),
+                       "bf16x3": blockmap.run_benchmark(ctx, n_tr, n_te, d, block=10, reps=reps,
+                                                        prec=dualk.DK_PREC_BF16X3)}
 
     if world > 1:
         tdist.destroy_process_group()
