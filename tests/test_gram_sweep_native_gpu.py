@@ -29,6 +29,7 @@ def _items(dualk, torch, ctx, specs, fm, seed=0, tiles=None):
         mps = dualk.mps_build(ctx, x, fm)
         out = {k: torch.full((m, m), -7.0, device="cuda") for k in ("k", "kq", "kc", "logkq")}
         items.append((mps, out, 0 if tiles is None else tiles[t]))
+    torch.cuda.synchronize()  # the builds and fills ran on the current stream; sweeps may use another
     return items
 
 
@@ -100,8 +101,10 @@ def test_graph_cache_eviction_and_bond8(dk):
     dualk.gram_sweep(ctx, items, w=ws[-1], graph=True, stream=side)
     side.synchronize()
     _assert_same(torch, items, [_alone(dualk, ctx, items[0][0], 0, ws[-1])])
+    torch.cuda.synchronize()
     items8 = _items(dualk, torch, ctx, [(24, 9), (31, 20)], dualk.FeatureMap(reps=3, chi_max=8), seed=30)
     refs8 = [_alone(dualk, ctx, mps, 0, 0.5) for mps, _, _ in items8]
+    torch.cuda.synchronize()
     dualk.gram_sweep(ctx, items8, w=0.5, graph=True, stream=side)
     dualk.gram_sweep(ctx, items8, w=0.5, graph=True, stream=side)
     side.synchronize()
