@@ -218,3 +218,36 @@ def test_gram_blocks_errors(dk):
                               dualk._ptr(st.log_norm), dualk._ptr(st.log_norm), dualk._ptr(x), dualk._ptr(x),
                               0.1, 1.0, 0, None, dualk._ptr(out), None, None, 4, 0, dualk._stream(None)) == 1
     ctx.sync_status()
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16x3"])
+def test_gram_blocks_edge_cases(dk, prec):
+    """One sample (K = 1), one qubit (n = 1, block 1: the product form cos^2(x - y) at one
+    repetition), a single block of 12 qubits (block 0 with n = 12), and an empty row range."""
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    p = dualk.DK_PREC_BF16X3 if prec == "bf16x3" else dualk.DK_PREC_F32
+    tol = 1e-4 if prec == "bf16x3" else 1e-6
+    x1 = _dev(torch, synthetic.uniform_angles(1, 7, 60))
+    g1 = dualk.gram_blocks(ctx, dualk.block_states(ctx, x1, dualk.FeatureMap(reps=2, block=3), prec=p), w=0.5)
+    xs = synthetic.uniform_angles(9, 1, 61)
+    gs = dualk.gram_blocks(ctx, dualk.block_states(ctx, _dev(torch, xs), dualk.FeatureMap(reps=1, block=1), prec=p),
+                           w=1.0, want=("kq",))
+    x12 = synthetic.uniform_angles(10, 12, 62)
+    g12 = dualk.gram_blocks(ctx, dualk.block_states(ctx, _dev(torch, x12), dualk.FeatureMap(reps=2, block=0),
+                                                    dualk.DK_ENT_FULL, prec=p), w=1.0, want=("kq",))
+    torch.cuda.synchronize()
+    assert g1["k"].item() == 1.0 and g1["kq"].item() == 1.0
+    prod = np.cos(xs[:, None, 0] - xs[None, :, 0]) ** 2
+    assert np.max(np.abs(gs["kq"].cpu().numpy() - prod)) <= tol
+    ref = np.exp(_ref_log(x12, x12, 2, 12, "full"))
+    assert np.max(np.abs(g12["kq"].cpu().numpy() - ref)) <= tol
+    st = dualk.block_states(ctx, x1, dualk.FeatureMap(reps=2, block=3), prec=p)
+    out = torch.full((1, 1), -3.0, device="cuda")
+    assert dualk._lib().dk_gram_blocks(ctx.handle, dualk._ptr(st.data), 1, dualk._ptr(st.data), 1, 7, 3, 0, 0, 0, 1,
+                                       dualk._ptr(st.log_norm), dualk._ptr(st.log_norm), dualk._ptr(x1),
+                                       dualk._ptr(x1), 0.1, 1.0, p, None, dualk._ptr(out), None, None, 1, 0,
+                                       dualk._stream(None)) == 0
+    torch.cuda.synchronize()
+    assert out.item() == -3.0  # nothing to compute, nothing written
+    ctx.sync_status()
