@@ -2,18 +2,25 @@
 //
 // Same contraction as gram32.cu (§II-C, Eqs. 8-10, block-structured, h = 16): per site,
 // pair and (s, t), G = E_t B with B = A_s[t](x_j), then E'_s += C G with C = A_s[t](x_i)^dagger.
-// Each complex 16 x 16 x 16 product is one real GEMM of the block form
+// Each complex 16 x 16 x 16 product Z = X Y is one real GEMM of the block form
 //     [Xr | Xi] (16 x 32) . [[Yr, Yi], [-Yi, Yr]] (32 x 32) = [Zr | Zi] (16 x 32),
 // run as m16n8k16 BF16 MMAs with FP32 accumulation. Every FP32 operand v is split into
-// v = hi + lo (both BF16) and each product is hi.hi + hi.lo + lo.hi (bf16x3), which keeps
+// v = hi + lo (both BF16) and each product is lo.hi + hi.lo + hi.hi (bf16x3), which keeps
 // about 16 significant bits per product; the lo.lo term is dropped.
 //
-// Dataflow: one warp per pair. E (two 16 x 16 blocks) stays in MMA accumulator fragments
-// across sites; an accumulator tile converts directly into the A fragment of the next
-// product (the fragment layouts coincide), so step 1 needs no memory traffic for E. The
-// step-1 result G is the B operand of step 2 and goes through a per-warp shared buffer
-// (transposed by ldmatrix). The CTA stages, per site and double buffered, its row samples
-// as C operands and its column samples as B operands, both split into BF16 hi / lo.
+// Dataflow: one warp per pair, everything between sites in registers. An m16n8 accumulator
+// tile of a matrix X holds, lane by lane, exactly the B-operand fragment of X^T (lane 4g + t
+// has X[g][2t], X[g][2t+1] and the same for row g + 8; the B fragment wants Y[2t][g],
+// Y[2t+1][g]). So the step order is chosen to always consume an accumulator as the B
+// operand of a transposed product:
+//   step 1:  G^T = B^T E_t^T     (A operand B^T from shared memory, B operand from E_t's
+//                                  accumulators),
+//   step 2:  E'_s += C G          (A operand C from shared memory, B operand from G^T's
+//                                  accumulators),
+// and E'_s is again in accumulator form for the next site. No intermediate goes through
+// shared memory. The CTA stages, per site and double buffered, its row samples as C
+// operands and its column samples as B^T operands (the same 16 x 32 layout, without the
+// conjugation), split into BF16 hi / lo.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -33,12 +40,8 @@ constexpr int CHUNKS = SAMPLE_FLOATS / 4;    // 16-byte chunks per sample-site
 // Operand tiles are row-major BF16 with 80-byte rows (32 values + 8 pad), so that the 8
 // rows of an ldmatrix phase hit 8 different 16-byte bank groups.
 constexpr int ROW = 40;                      // u16 per padded row
-constexpr int COP = 16 * ROW;                // one C operand (16 x 32) in u16
-constexpr int BOP = 32 * ROW;                // one B operand (32 x 32) in u16
-// Row sample: C operands hi and lo for the 4 (s, t) blocks; column sample: B operands.
-constexpr int RBUF = 4 * 2 * COP;            // u16 per row sample
-constexpr int CBUF = 4 * 2 * BOP;            // u16 per column sample
-constexpr int GBUF = 2 * BOP;                // per-warp G operand, hi and lo
+constexpr int COP = 16 * ROW;                // one operand (16 x 32) in u16
+constexpr int SBUF = 4 * 2 * COP;            // one sample: 4 (s, t) blocks x hi / lo
 
 __device__ __forceinline__ void mma16816(float (&d)[4], const u32 (&a)[4], u32 b0, u32 b1) {
   asm volatile(
@@ -54,12 +57,6 @@ __device__ __forceinline__ void ldsm_x4(u32 (&r)[4], const u16* p) {
                : "r"(smem_u32(p)));
 }
 
-__device__ __forceinline__ void ldsm_x4_t(u32 (&r)[4], const u16* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
-
 // (x, y) -> packed BF16 pairs hi and lo with x ~ hi + lo (low half = x).
 __device__ __forceinline__ void split2(float x, float y, u32& hi, u32& lo) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
@@ -68,99 +65,85 @@ __device__ __forceinline__ void split2(float x, float y, u32& hi, u32& lo) {
   hi = *reinterpret_cast<const u32*>(&h);
   lo = *reinterpret_cast<const u32*>(&l);
 }
-__device__ __forceinline__ void split1(float x, u16& hi, u16& lo) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-  hi = *reinterpret_cast<const u16*>(&h);
-  lo = *reinterpret_cast<const u16*>(&l);
-}
 constexpr u32 NEG2 = 0x80008000u;  // flips the sign of both BF16 halves
 
-// Row sample, block (s, t): C[p][k] = Re A[k][p] (k < 16), -Im A[k-16][p] (k >= 16), where
-// A[a][p] is compact element (s, j = p, l = 16 t + a). A 16-byte chunk holds elements
-// l, l+1 of compact row r = 16 s + p.
-__device__ __forceinline__ void put_row_chunk(u16* rbuf, int chunk, float4 v) {
+// Operand of block (s, t) of a sample: X[p][k] = Re A[k][p] (k < 16), sign Im A[k-16][p]
+// (k >= 16), A[a][p] the compact element (s, j = p, l = 16 t + a). CONJ (sign -1): the C
+// operand of a row sample (conjugate transpose); otherwise the B^T operand of a column
+// sample (transpose). A 16-byte chunk holds elements l, l+1 of compact row r = 16 s + p.
+template <bool CONJ>
+__device__ __forceinline__ void put_chunk(u16* buf, int chunk, float4 v) {
   const int r = chunk >> 4, q = chunk & 15;
   const int s = r >> 4, p = r & 15;
   const int l = 2 * q, t = l >> 4, a = l & 15;
-  u16* hi = rbuf + (s * 2 + t) * 2 * COP;
+  u16* hi = buf + (s * 2 + t) * 2 * COP;
   u16* lo = hi + COP;
   u32 h, w;
   split2(v.x, v.z, h, w);  // Re at a, a+1
   *reinterpret_cast<u32*>(hi + p * ROW + a) = h;
   *reinterpret_cast<u32*>(lo + p * ROW + a) = w;
-  split2(v.y, v.w, h, w);  // Im at a, a+1 -> -Im
-  *reinterpret_cast<u32*>(hi + p * ROW + 16 + a) = h ^ NEG2;
-  *reinterpret_cast<u32*>(lo + p * ROW + 16 + a) = w ^ NEG2;
+  split2(v.y, v.w, h, w);  // Im at a, a+1
+  const u32 sg = CONJ ? NEG2 : 0u;
+  *reinterpret_cast<u32*>(hi + p * ROW + 16 + a) = h ^ sg;
+  *reinterpret_cast<u32*>(lo + p * ROW + 16 + a) = w ^ sg;
 }
 
-// Column sample, block (s, t): B[b][c] = compact (s, j = c, l = 16 t + b); the operand is
-// [[Br, Bi], [-Bi, Br]] (32 x 32). A chunk holds b, b+1 of compact row r = 16 s + c.
-// Work item w of a column sample handles chunk col_chunk(w): consecutive items walk the 32
-// compact rows (consecutive columns c of the operand) first, so a warp's 16-bit stores
-// land in consecutive banks.
-__device__ __forceinline__ int col_chunk(int w) { return (w & 31) * 16 + (w >> 5); }
-__device__ __forceinline__ void put_col_chunk(u16* cbuf, int chunk, float4 v) {
-  const int r = chunk >> 4, q = chunk & 15;
-  const int s = r >> 4, c = r & 15;
-  const int l = 2 * q, t = l >> 4, b = l & 15;
-  u16* hi = cbuf + (s * 2 + t) * 2 * BOP;
-  u16* lo = hi + BOP;
-  const float re[2] = {v.x, v.z}, im[2] = {v.y, v.w};
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    u16 rh, rl, ih, il;
-    split1(re[e], rh, rl);
-    split1(im[e], ih, il);
-    const int k = b + e;
-    hi[k * ROW + c] = rh;
-    lo[k * ROW + c] = rl;
-    hi[k * ROW + 16 + c] = ih;
-    lo[k * ROW + 16 + c] = il;
-    hi[(16 + k) * ROW + c] = ih ^ 0x8000u;
-    lo[(16 + k) * ROW + c] = il ^ 0x8000u;
-    hi[(16 + k) * ROW + 16 + c] = rh;
-    lo[(16 + k) * ROW + 16 + c] = rl;
-  }
-}
-
-// Fragment state of one pair: e[t][nt][4], nt 0..1 = real part columns 0-7 / 8-15,
-// nt 2..3 = imaginary part (m16n8 accumulator layout).
+// Accumulator state of one complex 16 x 16 matrix X: v[nt][4], nt 0..1 = real part columns
+// 0-7 / 8-15, nt 2..3 = imaginary part (m16n8 accumulator layout).
 struct Frag {
-  float v[2][4][4];
+  float v[2][4][4];  // two bond blocks
 };
 
-// acc += X . Yop with X given as 16 x 32 A fragments (hi/lo per k-step) and Yop a 32 x 32
-// row-major BF16 operand in shared memory (hi, lo), for the 4 n-tiles. The MMAs are issued
-// term-major over the four independent n-tile accumulators, so consecutive MMAs never wait
-// on each other.
-__device__ __forceinline__ void gemm_16x32x32(float (&acc)[4][4], const u32 (&ahi)[2][4], const u32 (&alo)[2][4],
-                                              const u16* yhi, const u16* ylo, int lane) {
-  // ldmatrix.trans lane address: tile (k half, n tile) rows = 16 kk + 8 (sel & 1) + (lane & 7)
-  const int lr = lane & 7, sel = lane >> 3;  // sel: 0 (k 0-7, nt), 1 (k 8-15, nt), 2 (k 0-7, nt+1), 3
+// B-operand words of Y = X^T (or of the block matrix built from it) taken from X's
+// accumulators: w[c][h][tile] = X component c (0 Re, 1 Im), rows g (h = 0) or g + 8 (h = 1),
+// columns 2t, 2t+1 of column tile `tile`, split into BF16 hi / lo.
+struct BFrag {
+  u32 hi[2][2][2], lo[2][2][2];
+};
+
+__device__ __forceinline__ void to_bfrag(const float (&x)[4][4], BFrag& f) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int tile = 0; tile < 2; ++tile)
+        split2(x[2 * c + tile][2 * h], x[2 * c + tile][2 * h + 1], f.hi[c][h][tile], f.lo[c][h][tile]);
+}
+
+// acc += [Xr | Xi] . [[Yr, Yi], [-Yi, Yr]] for X (16 x 16 complex) from shared memory
+// (xh: hi operand, lo operand COP further) and Y given by f (Y = the transpose of the matrix
+// whose accumulators made f). k-step kk = 0 takes the rows [Yr | Yi], kk = 1 [-Yi | Yr]; the
+// MMAs are issued term-major over the four independent n-tile accumulators.
+__device__ __forceinline__ void mma_block(float (&acc)[4][4], const u16* xh, const BFrag& f, int lane) {
 #pragma unroll
   for (int kk = 0; kk < 2; ++kk) {
-    u32 bh[2][4], bl[2][4];
+    u32 ahi[4], alo[4];
+    const u16* rowp = xh + (lane & 15) * ROW + 16 * kk + 8 * (lane >> 4);
+    ldsm_x4(ahi, rowp);
+    ldsm_x4(alo, rowp + COP);
+    u32 bh[4][2], bl[4][2];
 #pragma unroll
-    for (int np = 0; np < 2; ++np) {  // pairs of n-tiles (2np, 2np+1)
-      const int krow = 16 * kk + 8 * (sel & 1) + lr;
-      const int ncol = 16 * np + 8 * (sel >> 1);
-      ldsm_x4_t(bh[np], yhi + krow * ROW + ncol);
-      ldsm_x4_t(bl[np], ylo + krow * ROW + ncol);
+    for (int nt = 0; nt < 4; ++nt) {
+      const int c = (nt >> 1) ^ kk, h = nt & 1;
+      const u32 sg = (kk == 1 && nt < 2) ? NEG2 : 0u;
+      bh[nt][0] = f.hi[c][h][0] ^ sg;
+      bh[nt][1] = f.hi[c][h][1] ^ sg;
+      bl[nt][0] = f.lo[c][h][0] ^ sg;
+      bl[nt][1] = f.lo[c][h][1] ^ sg;
     }
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], alo[kk], bh[nt >> 1][2 * (nt & 1)], bh[nt >> 1][2 * (nt & 1) + 1]);
+    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], alo, bh[nt][0], bh[nt][1]);
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], ahi[kk], bl[nt >> 1][2 * (nt & 1)], bl[nt >> 1][2 * (nt & 1) + 1]);
+    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], ahi, bl[nt][0], bl[nt][1]);
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], ahi[kk], bh[nt >> 1][2 * (nt & 1)], bh[nt >> 1][2 * (nt & 1) + 1]);
+    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], ahi, bh[nt][0], bh[nt][1]);
   }
 }
 
-// One site of one pair (warp). rbuf: row-sample C operands; cbuf: column-sample B
-// operands; gbuf: this warp's G operand buffer. E is replaced by diag(acc_0, acc_1).
-__device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* cbuf, u16* gbuf, int lane) {
-  const int g = lane >> 2, tq = lane & 3;
+// One site of one pair (warp). rbuf: row-sample C operands; cbuf: column-sample B^T
+// operands. E is replaced by diag(acc_0, acc_1).
+__device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* cbuf, int lane) {
   float acc[2][4][4];
 #pragma unroll
   for (int s = 0; s < 2; ++s)
@@ -170,58 +153,21 @@ __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* c
       for (int c = 0; c < 4; ++c) acc[s][nt][c] = 0.0f;
 #pragma unroll
   for (int t = 0; t < 2; ++t) {
-    // A fragments of [Er | Ei] for E_t: k-step 0 = Er (n-tiles 0, 1), k-step 1 = Ei (2, 3)
-    u32 ahi[2][4], alo[2][4];
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      const float(&x0)[4] = E.v[t][2 * kk];
-      const float(&x1)[4] = E.v[t][2 * kk + 1];
-      split2(x0[0], x0[1], ahi[kk][0], alo[kk][0]);
-      split2(x0[2], x0[3], ahi[kk][1], alo[kk][1]);
-      split2(x1[0], x1[1], ahi[kk][2], alo[kk][2]);
-      split2(x1[2], x1[3], ahi[kk][3], alo[kk][3]);
-    }
+    BFrag fe;
+    to_bfrag(E.v[t], fe);  // B operand of E_t^T
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      // step 1: G = [Er | Ei] . [[Br, Bi], [-Bi, Br]]
-      float gacc[4][4];
+      // step 1: G^T = B^T . E_t^T
+      float g[4][4];
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) gacc[nt][c] = 0.0f;
-      const u16* bh = cbuf + (s * 2 + t) * 2 * BOP;
-      gemm_16x32x32(gacc, ahi, alo, bh, bh + BOP, lane);
-      // G operand [[Gr, Gi], [-Gi, Gr]] into the warp buffer (hi, lo)
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int col = 8 * nt + 2 * tq;
-        u32 h0, l0, h1, l1;
-        split2(gacc[nt][0], gacc[nt][1], h0, l0);  // row g
-        split2(gacc[nt][2], gacc[nt][3], h1, l1);  // row g + 8
-        *reinterpret_cast<u32*>(gbuf + g * ROW + col) = h0;
-        *reinterpret_cast<u32*>(gbuf + BOP + g * ROW + col) = l0;
-        *reinterpret_cast<u32*>(gbuf + (g + 8) * ROW + col) = h1;
-        *reinterpret_cast<u32*>(gbuf + BOP + (g + 8) * ROW + col) = l1;
-        // lower half: Gr block (nt 0,1) moves right, Gi block (nt 2,3) moves left negated
-        const int col2 = nt < 2 ? col + 16 : col - 16;
-        const u32 sg = nt < 2 ? 0u : NEG2;
-        *reinterpret_cast<u32*>(gbuf + (16 + g) * ROW + col2) = h0 ^ sg;
-        *reinterpret_cast<u32*>(gbuf + BOP + (16 + g) * ROW + col2) = l0 ^ sg;
-        *reinterpret_cast<u32*>(gbuf + (24 + g) * ROW + col2) = h1 ^ sg;
-        *reinterpret_cast<u32*>(gbuf + BOP + (24 + g) * ROW + col2) = l1 ^ sg;
-      }
-      __syncwarp();
-      // step 2: acc_s += [Cr | Ci] . [[Gr, Gi], [-Gi, Gr]]
-      u32 chi[2][4], clo[2][4];
-      const u16* ch = rbuf + (s * 2 + t) * 2 * COP;
-#pragma unroll
-      for (int kk = 0; kk < 2; ++kk) {
-        const u16* rowp = ch + (lane & 15) * ROW + 16 * kk + 8 * (lane >> 4);
-        ldsm_x4(chi[kk], rowp);
-        ldsm_x4(clo[kk], rowp + COP);
-      }
-      gemm_16x32x32(acc[s], chi, clo, gbuf, gbuf + BOP, lane);
-      __syncwarp();
+        for (int c = 0; c < 4; ++c) g[nt][c] = 0.0f;
+      mma_block(g, cbuf + (s * 2 + t) * 2 * COP, fe, lane);
+      // step 2: acc_s += C . G (B operand of G = (G^T)^T from G^T's accumulators)
+      BFrag fg;
+      to_bfrag(g, fg);
+      mma_block(acc[s], rbuf + (s * 2 + t) * 2 * COP, fg, lane);
     }
   }
 #pragma unroll
@@ -275,10 +221,10 @@ __device__ __forceinline__ float half_log_mod(const Frag& E, int e2) {
 template <int TR, int TC>
 struct CfgTc {
   static constexpr int NW = TR * TC, NT = NW * 32;
-  static constexpr int STAGE = TR * RBUF + TC * CBUF;  // u16 per stage
+  static constexpr int STAGE = (TR + TC) * SBUF;  // u16 per stage
   static constexpr int CH = (TR + TC) * CHUNKS;
   static constexpr int PER_THREAD = (CH + NT - 1) / NT;
-  static constexpr int SMEM = (2 * STAGE + NW * GBUF) * 2;
+  static constexpr int SMEM = 2 * STAGE * 2;
 };
 
 template <int TR, int TC>
@@ -289,7 +235,6 @@ __global__ void __launch_bounds__(TR * TC * 32, 1)
   extern __shared__ __align__(16) u16 smu[];
   u16* stage[2] = {smu, smu + C::STAGE};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  u16* gbuf = smu + 2 * C::STAGE + warp * GBUF;
   const int wr = warp / TC, wc = warp % TC;
 
   float4 pre[C::PER_THREAD];
@@ -300,10 +245,9 @@ __global__ void __launch_bounds__(TR * TC * 32, 1)
       if (ch < C::CH) {
         const int smp = ch / CHUNKS, w = ch % CHUNKS;
         const bool is_row = smp < TR;
-        const int part = is_row ? w : col_chunk(w);
         const int idx = is_row ? min(r0 + smp, m_r - 1) : min(c0 + smp - TR, m_c - 1);
         const float* src = (is_row ? mps_r + (size_t(k) * m_r + idx) * SAMPLE_FLOATS
-                                   : mps_c + (size_t(k) * m_c + idx) * SAMPLE_FLOATS) + part * 4;
+                                   : mps_c + (size_t(k) * m_c + idx) * SAMPLE_FLOATS) + w * 4;
         pre[q] = __ldg(reinterpret_cast<const float4*>(src));
       }
     }
@@ -314,8 +258,8 @@ __global__ void __launch_bounds__(TR * TC * 32, 1)
       const int ch = threadIdx.x + q * C::NT;
       if (ch < C::CH) {
         const int smp = ch / CHUNKS, w = ch % CHUNKS;
-        if (smp < TR) put_row_chunk(st + smp * RBUF, w, pre[q]);
-        else put_col_chunk(st + TR * RBUF + (smp - TR) * CBUF, col_chunk(w), pre[q]);
+        if (smp < TR) put_chunk<true>(st + smp * SBUF, w, pre[q]);
+        else put_chunk<false>(st + smp * SBUF, w, pre[q]);
       }
     }
   };
@@ -335,7 +279,7 @@ __global__ void __launch_bounds__(TR * TC * 32, 1)
     for (int k = 0; k < p.n; ++k) {
       u16* cur = stage[k & 1];
       if (k + 1 < p.n) fetch(r0, c0, k + 1);
-      pair_site(E, cur + wr * RBUF, cur + TR * RBUF + wc * CBUF, gbuf, lane);
+      pair_site(E, cur + wr * SBUF, cur + (TR + wc) * SBUF, lane);
       if (k == p.n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1)) e2 += renorm(E);
       if (k + 1 < p.n) commit(stage[(k + 1) & 1]);
       __syncthreads();
@@ -359,8 +303,7 @@ __global__ void __launch_bounds__(32) self_overlap32_tc_kernel(const float* __re
                                                                float* __restrict__ log_norm) {
   extern __shared__ __align__(16) u16 smu[];
   u16* rbuf = smu;
-  u16* cbuf = rbuf + RBUF;
-  u16* gbuf = cbuf + CBUF;
+  u16* cbuf = rbuf + SBUF;
   const int lane = threadIdx.x;
   const int i = blockIdx.x;
   Frag E;
@@ -370,12 +313,11 @@ __global__ void __launch_bounds__(32) self_overlap32_tc_kernel(const float* __re
     const float* src = mps + (size_t(k) * m + i) * SAMPLE_FLOATS;
     for (int w = lane; w < CHUNKS; w += 32) {
       const float4 v = __ldg(reinterpret_cast<const float4*>(src) + w);
-      put_row_chunk(rbuf, w, v);
-      const int cw = col_chunk(w);
-      put_col_chunk(cbuf, cw, __ldg(reinterpret_cast<const float4*>(src) + cw));
+      put_chunk<true>(rbuf, w, v);
+      put_chunk<false>(cbuf, w, v);
     }
     __syncwarp();
-    pair_site(E, rbuf, cbuf, gbuf, lane);
+    pair_site(E, rbuf, cbuf, lane);
     if (k == n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1)) e2 += renorm(E);
     __syncwarp();
   }
@@ -405,7 +347,7 @@ dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* 
 }
 
 dk_status self_overlap32_tc_launch(const void* mps, int m, int n, float* log_norm, cudaStream_t st) {
-  const int smem = (tc32::RBUF + tc32::CBUF + tc32::GBUF) * 2;
+  const int smem = 2 * tc32::SBUF * 2;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(tc32::self_overlap32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
