@@ -88,6 +88,17 @@ __device__ __forceinline__ void put_chunk(u16* buf, int chunk, float4 v) {
   *reinterpret_cast<u32*>(lo + p * ROW + 16 + a) = w ^ sg;
 }
 
+// Thread u (0..511 over a sample's chunks) -> chunk 16 r + q, r = 16 s + p, q = 8 t + q'.
+// A warp takes q' = 0..7 and p in {0, 2, 4, 6} (+1, +8): its stores into one (s, t) operand
+// start at banks 20 p + q' mod 32 = {0, 8, 16, 24} + q' (a padded row is 20 banks), so they
+// are conflict-free, and its global reads are four runs of 128 contiguous bytes.
+__device__ __forceinline__ int chunk_of(int u) {
+  const int qq = u & 7, psel = (u >> 3) & 3, par = (u >> 5) & 1, t = (u >> 6) & 1, phi = (u >> 7) & 1,
+            s = (u >> 8) & 1;
+  const int p = 2 * psel + par + 8 * phi;
+  return 16 * (16 * s + p) + 8 * t + qq;
+}
+
 // Accumulator state of one complex 16 x 16 matrix X: v[nt][4], nt 0..1 = real part columns
 // 0-7 / 8-15, nt 2..3 = imaginary part (m16n8 accumulator layout).
 struct Frag {
@@ -243,7 +254,7 @@ __global__ void __launch_bounds__(TR * TC * 32, 1)
     for (int q = 0; q < C::PER_THREAD; ++q) {
       const int ch = threadIdx.x + q * C::NT;
       if (ch < C::CH) {
-        const int smp = ch / CHUNKS, w = ch % CHUNKS;
+        const int smp = ch / CHUNKS, w = chunk_of(ch % CHUNKS);
         const bool is_row = smp < TR;
         const int idx = is_row ? min(r0 + smp, m_r - 1) : min(c0 + smp - TR, m_c - 1);
         const float* src = (is_row ? mps_r + (size_t(k) * m_r + idx) * SAMPLE_FLOATS
@@ -257,7 +268,7 @@ __global__ void __launch_bounds__(TR * TC * 32, 1)
     for (int q = 0; q < C::PER_THREAD; ++q) {
       const int ch = threadIdx.x + q * C::NT;
       if (ch < C::CH) {
-        const int smp = ch / CHUNKS, w = ch % CHUNKS;
+        const int smp = ch / CHUNKS, w = chunk_of(ch % CHUNKS);
         if (smp < TR) put_chunk<true>(st + smp * SBUF, w, pre[q]);
         else put_chunk<false>(st + smp * SBUF, w, pre[q]);
       }
