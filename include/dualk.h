@@ -120,6 +120,13 @@ dk_status dk_selftest_wait_timeout(dk_ctx* ctx, unsigned long long limit_ns, voi
 /* Bytes of an MPS buffer for m samples, n sites, padded bond chi_max. */
 size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
 
+/* Scratch bytes the build, Gram and rows calls need for (n, chi_max, dtype, prec): always 0.
+ * Every kernel keeps its working state in registers and shared memory and writes only the
+ * caller's outputs, so these calls take no workspace argument; the query exists for callers
+ * that size a workspace per call. Returns (size_t)-1 for a combination no kernel supports
+ * (chi_max / dtype / prec as dk_gram_tile), so it also serves as a capability check. */
+size_t dk_workspace_bytes(int n, int chi_max, dk_dtype dtype, dk_precision prec);
+
 /* |psi(x_i)> = U(x_i)|0>^n as an MPS (§II-C, Eq. 6), for i < m.
  *
  * Exact construction: every RZZ layer is a diagonal bond-2 operator, so after r

@@ -88,6 +88,16 @@ DK_API size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype) {
   return size_t(m) * size_t(n) * dk::site_bytes(chi_max, dtype);
 }
 
+DK_API size_t dk_workspace_bytes(int n, int chi_max, dk_dtype dtype, dk_precision prec) {
+  const size_t none = ~size_t(0);
+  if (n < 1) return none;
+  if (dtype == DK_C128) return (chi_max == 4 && prec == DK_PREC_F64) ? 0 : none;
+  if (dtype != DK_C64) return none;
+  if (prec == DK_PREC_F32) return (chi_max == 4 || chi_max == 8 || chi_max == 32) ? 0 : none;
+  if (prec == DK_PREC_BF16X3) return chi_max == 32 ? 0 : none;
+  return none;
+}
+
 namespace dk {
 
 // A wait that nothing will ever satisfy: an mbarrier expecting one arrival that never comes.

@@ -28,7 +28,7 @@ EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_
             "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout", "dk_self_overlap",
             "dk_svm_ovo_train", "dk_svm_ovo_predict", "dk_gram_stats", "dk_pca_workspace_bytes", "dk_pca_fit",
             "dk_pca_transform", "dk_pca_fit_noalloc", "dk_mps_build_blocks", "dk_block_states_bytes",
-            "dk_block_states", "dk_gram_blocks", "dk_gram_sweep")
+            "dk_block_states", "dk_gram_blocks", "dk_gram_sweep", "dk_workspace_bytes")
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 PCA_MAX_FEATURES = 4096  # DK_PCA_MAX_FEATURES
 PCA_NOALLOC_MAX_FEATURES = 256  # DK_PCA_NOALLOC_MAX_FEATURES
@@ -72,6 +72,8 @@ def _lib():
     lib.dk_mps_build_blocks.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, ctypes.c_double, i32, vp, vp,
                                         vp, vp, vp]
     lib.dk_mps_build_blocks.restype = i32
+    lib.dk_workspace_bytes.argtypes = [i32, i32, i32, i32]
+    lib.dk_workspace_bytes.restype = ctypes.c_size_t
     lib.dk_gram_sweep.argtypes = [vp, ctypes.POINTER(_SweepItem), i32, i32, i32, i32, f32, i32, vp]
     lib.dk_gram_sweep.restype = i32
     lib.dk_block_states_bytes.argtypes = [i32, i32, i32]

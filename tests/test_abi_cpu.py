@@ -61,6 +61,19 @@ def test_error_strings_and_host_validation(lib):
     assert lib.dk_mps_bytes(10, 7, 4, 0) == 10 * 7 * 4 * 4 * 8     # chi^2 complex64 per sample-site
     assert lib.dk_mps_bytes(10, 7, 8, 1) == 10 * 7 * 8 * 8 * 16
     assert lib.dk_mps_bytes(0, 7, 4, 0) == 0
+    # no Gram-path call needs a workspace; unsupported combinations read as (size_t)-1
+    lib.dk_workspace_bytes.restype = ctypes.c_size_t
+    none = ctypes.c_size_t(-1).value
+    for chi, dt, prec in ((4, 0, 0), (8, 0, 0), (32, 0, 0), (32, 0, 2), (4, 1, 1)):
+        assert lib.dk_workspace_bytes(784, chi, dt, prec) == 0
+    for chi, dt, prec in ((16, 0, 0), (4, 0, 2), (8, 1, 1), (4, 1, 0), (32, 0, 1)):
+        assert lib.dk_workspace_bytes(784, chi, dt, prec) == none
+    assert lib.dk_workspace_bytes(0, 4, 0, 0) == none
+    # block-state and PCA sizes
+    lib.dk_block_states_bytes.restype = ctypes.c_size_t
+    assert lib.dk_block_states_bytes(10, 784, 10) == 79 * 10 * 1024 * 8
+    assert lib.dk_block_states_bytes(10, 20, 2) == 10 * 10 * 16 * 8   # dpad = 16 below 16 amplitudes
+    assert lib.dk_block_states_bytes(10, 20, 13) == 0 and lib.dk_block_states_bytes(10, 20, 0) == 0
     # NULL context / pointers are rejected on the host before any CUDA call.
     assert lib.dk_mps_build(None, None, 1, 1, None, 0, None, None, None, None) == 1
     assert lib.dk_gram_tile(None, None, 1, None, 1, 1, 4, 0, 0, 1, 0, 1, None, None, None, None,
