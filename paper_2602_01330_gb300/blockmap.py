@@ -93,6 +93,28 @@ def run_benchmark(ctx: dualk.Context, m: int = 2000, m_test: int = 500, n: int =
     }
 
 
+def concentration(ctx: dualk.Context, dims=(8, 16, 32, 64, 128, 256, 784), m: int = 1000, reps: int = 2,
+                  blocks=(8,), entangler: int = dualk.DK_ENT_FULL) -> dict:
+    """Kernel concentration against the qubit count (§I; the diagnostics of §IV): per n, the
+    mean and variance of the off-diagonal K_q and log K_q of a symmetric Gram of m samples,
+    for the chain (MPS path) and for block-structured maps with the given block sizes
+    (block-statevector path). dk_gram_stats forms the FP64 sums."""
+    res = {}
+    for d in dims:
+        x = torch.from_numpy(synthetic.fmnist_like(m, 0, d)["x_train"]).cuda()
+        row = {}
+        g = dualk.gram(ctx, dualk.mps_build(ctx, x, dualk.FeatureMap(reps=reps, chi_max=4)), w=1.0,
+                       want=("kq", "logkq"))
+        row["chain"] = dualk.gram_stats(ctx, g["kq"], g["logkq"], symmetric=True)
+        for b in blocks:
+            st = dualk.block_states(ctx, x, dualk.FeatureMap(reps=reps, block=b), entangler)
+            gb = dualk.gram_blocks(ctx, st, w=1.0, want=("kq", "logkq"))
+            row[f"blocks_of_{b}"] = dualk.gram_stats(ctx, gb["kq"], gb["logkq"], symmetric=True)
+        res[d] = {k: {q: v[q] for q in ("kq_mean", "kq_var", "logkq_mean", "logkq_var")} for k, v in row.items()}
+    ctx.sync_status()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--m", type=int, default=2000)
@@ -103,8 +125,15 @@ def main():
     ap.add_argument("--entangler", choices=("full", "chain"), default="full")
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--prec", choices=("f32", "bf16x3"), default="f32")
+    ap.add_argument("--concentration", action="store_true",
+                    help="report kernel concentration against n for the chain and block maps instead")
     args = ap.parse_args()
     ctx = dualk.Context(0)
+    if args.concentration:
+        ent = dualk.DK_ENT_FULL if args.entangler == "full" else dualk.DK_ENT_CHAIN
+        print(json.dumps(concentration(ctx, m=1000, reps=args.reps, blocks=(4, 8, args.block), entangler=ent)))
+        ctx.close()
+        return
     ent = dualk.DK_ENT_FULL if args.entangler == "full" else dualk.DK_ENT_CHAIN
     prec = dualk.DK_PREC_BF16X3 if args.prec == "bf16x3" else dualk.DK_PREC_F32
     print(json.dumps(run_benchmark(ctx, args.m, args.m_test, args.n, args.block, args.reps, ent, iters=args.iters,
