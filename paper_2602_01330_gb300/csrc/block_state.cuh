@@ -1,5 +1,6 @@
 // Dense statevector of one block of a block-structured feature map (§II-C, Eq. 6 restricted
-// to the block's qubits), computed by a whole CTA in FP64 shared memory.
+// to the block's qubits), computed by the threads of a CTA or of one warp in FP64 shared
+// memory.
 //
 // Per repetition: H on every qubit, then the diagonal layer exp(-i Phi(z)) with
 //   Phi(z) = sum_q (angle_scale x_q / 2) z_q + sum_{(q,r) entangled} (pi - x_q)(pi - x_r) z_q z_r,
@@ -41,15 +42,24 @@ __host__ __device__ inline size_t smem_bytes(int b) {
   return ((sizeof(Coeffs) + 15) & ~size_t(15)) + 2 * (size_t(1) << b) * sizeof(double2);
 }
 
+// Barrier of the threads that build one block together: a whole CTA or one warp.
+struct CtaSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct WarpSync {
+  __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+
 __device__ __forceinline__ double2 cmul64(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
 // psi[0 .. 2^bl) of the block whose features are xb[0 .. bl); ph[0 .. 2^bl) receives the
 // phase factors. pairs_kind: DK_ENT_CHAIN, DK_ENT_FULL, or anything else for no entanglers.
-// Ends with __syncthreads().
+// Threads tid = 0 .. nt-1 work together and `sync` is their barrier; ends with a sync.
+template <class Sync = CtaSync>
 __device__ inline void build(double2* psi, double2* ph, Coeffs& C, const float* xb, int bl, int reps,
-                             double angle_scale, int pairs_kind, int tid, int nt) {
+                             double angle_scale, int pairs_kind, int tid, int nt, Sync sync = Sync()) {
   const int dim = 1 << bl;
   const int hb = bl >> 1, lb = bl - hb;  // high half: qubits 0 .. hb-1
   if (tid < bl) C.hq[tid] = 0.5 * angle_scale * double(xb[tid]);
@@ -59,7 +69,7 @@ __device__ inline void build(double2* psi, double2* ph, Coeffs& C, const float* 
                     (pairs_kind == DK_ENT_FULL || (pairs_kind == DK_ENT_CHAIN && r == q + 1));
     C.jq[q][r] = on ? (PI_D - double(xb[q])) * (PI_D - double(xb[r])) : 0.0;
   }
-  __syncthreads();
+  sync();
   // tables: z of qubit q (q < hb) is bit hb-1-q of zH; of qubit hb+t is bit lb-1-t of zL
   for (int e = tid; e < (1 << hb); e += nt) {
     double a = 0.0;
@@ -87,7 +97,7 @@ __device__ inline void build(double2* psi, double2* ph, Coeffs& C, const float* 
       C.tv[e][q] = v;
     }
   }
-  __syncthreads();
+  sync();
   const double amp = exp2(-0.5 * double(bl));
   for (int e = tid; e < dim; e += nt) {
     const int zh = e >> lb, zl = e & ((1 << lb) - 1);
@@ -98,7 +108,7 @@ __device__ inline void build(double2* psi, double2* ph, Coeffs& C, const float* 
     ph[e] = make_double2(cs, sn);
     psi[e] = make_double2(amp * cs, amp * sn);  // first repetition: uniform state times the phases
   }
-  __syncthreads();
+  sync();
   for (int rep = 1; rep < reps; ++rep) {
     for (int q = 0; q < bl; ++q) {
       const int bit = 1 << (bl - 1 - q);
@@ -109,10 +119,10 @@ __device__ inline void build(double2* psi, double2* ph, Coeffs& C, const float* 
         psi[lo] = make_double2((u.x + v.x) * M_SQRT1_2, (u.y + v.y) * M_SQRT1_2);
         psi[hi] = make_double2((u.x - v.x) * M_SQRT1_2, (u.y - v.y) * M_SQRT1_2);
       }
-      __syncthreads();
+      sync();
     }
     for (int e = tid; e < dim; e += nt) psi[e] = cmul64(psi[e], ph[e]);
-    __syncthreads();
+    sync();
   }
 }
 

@@ -7,7 +7,8 @@
 // exceeds the 2^reps of the nearest-neighbour closed form (all-to-all ZZ inside a block:
 // rank up to 2^(b/2)), where the bond cap and the singular value cutoff truncate.
 //
-// One CTA per sample walks its blocks. Per block, in FP64 shared memory:
+// One warp per (sample, block), up to four warps per CTA that never wait on each other. Per
+// block, in FP64 shared memory:
 //   1. the statevector: per repetition a Walsh-Hadamard pass per qubit, then the diagonal
 //      phase exp(-i Phi(z)), Phi(z) = sum_q (scale x_q / 2) z_q + sum_{(q,r)} (pi - x_q)(pi - x_r) z_q z_r
 //      over z in {+1, -1}^b (RZ and RZZ are diagonal and commute);
@@ -36,7 +37,6 @@
 namespace dk {
 namespace bsvd {
 
-constexpr int NT = 128;         // threads per CTA
 constexpr int MAXB = blockstate::MAXB;
 constexpr int MAXR = 32;        // rows of M: 2 x kept bond <= chi_max <= 32
 constexpr int MAX_SWEEPS = 40;  // Jacobi sweeps per cut (quadratic convergence needs ~6-10)
@@ -47,6 +47,8 @@ constexpr double ORTH_TOL = 1e-14;  // rotate while |<p,q>| > tol sqrt(|p|^2 |q|
 // drives them into underflow, so pairs involving one are left alone. Rows that the cutoff
 // can keep (s > 1e-10 s_0, s_0 >= 1/sqrt(32)) are far above it.
 constexpr double FLOOR2 = 1e-30;
+constexpr int MAX_WARPS = 4;    // warps (blocks) per CTA
+constexpr size_t SMEM_CAP = 227 * 1024;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -56,7 +58,8 @@ __device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {  // conj(a) 
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
-struct Shared {
+// Working memory of one warp (one block of one sample); the state and its phase factors follow.
+struct WarpShared {
   double2 J[MAXR][MAXR];  // accumulated row rotations of the current cut
   double nrm[MAXR];       // squared row norms
   int rowbase[MAXR];      // offset of each row of M in the state buffer
@@ -67,8 +70,14 @@ struct Shared {
   int keep;               // kept bond of the current cut
 };
 
-// Shared, then the state and its phase factors (2^b amplitudes each)
-inline size_t smem_bytes(int b) { return ((sizeof(Shared) + 15) & ~size_t(15)) + 2 * (size_t(1) << b) * sizeof(double2); }
+// Bytes per warp for blocks of b qubits, and warps per CTA
+inline size_t warp_bytes(int b) {
+  return ((sizeof(WarpShared) + 15) & ~size_t(15)) + 2 * (size_t(1) << b) * sizeof(double2);
+}
+inline int warps_per_cta(int b) {
+  const size_t w = SMEM_CAP / warp_bytes(b);
+  return int(w < 1 ? 1 : (w > size_t(MAX_WARPS) ? MAX_WARPS : w));
+}
 
 // (k, round t) -> row of the round-robin pairing of r rows (r even): row 0 stays, the rest rotate
 __device__ __forceinline__ int rr_row(int k, int t, int r) { return k == 0 ? 0 : ((k - 1 + t) % (r - 1)) + 1; }
@@ -78,177 +87,198 @@ __device__ __forceinline__ void store(void* out, size_t idx, double2 v, int c128
   else reinterpret_cast<float2*>(out)[idx] = make_float2(float(v.x), float(v.y));
 }
 
-__global__ void __launch_bounds__(NT) bond_init_kernel(int32_t* bond, int n) {
+__global__ void __launch_bounds__(128) bond_init_kernel(int32_t* bond, int n) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x) bond[k] = 1;
 }
 
-__global__ void __launch_bounds__(NT) block_svd_kernel(const float* __restrict__ x, int m, int n, int b, int reps,
-                                                       double angle_scale, int pairs_kind, double cutoff, int cap,
-                                                       int chi, int out_c128, void* __restrict__ out,
-                                                       int32_t* __restrict__ bond, float* __restrict__ discarded) {
+// UW warps per (sample, block) unit: u = sample * nb + block. UW = 1: several units per CTA,
+// each one warp with warp-level barriers only (units never wait on each other); UW = 4: one
+// unit per CTA (blocks whose state leaves room for one unit per SM).
+template <int UW>
+__device__ __forceinline__ void unit_sync() {
+  if constexpr (UW == 1) __syncwarp();
+  else __syncthreads();
+}
+
+template <int UW>
+__global__ void __launch_bounds__(MAX_WARPS * 32)
+    block_svd_kernel(const float* __restrict__ x, int m, int n, int b, int nb, int reps, double angle_scale,
+                     int pairs_kind, double cutoff, int cap, int chi, int out_c128, size_t wbytes,
+                     void* __restrict__ out, int32_t* __restrict__ bond, float* __restrict__ discarded) {
+  constexpr int NTU = 32 * UW;  // threads per unit
   extern __shared__ __align__(16) unsigned char raw[];
-  Shared& S = *reinterpret_cast<Shared*>(raw);
-  double2* psi = reinterpret_cast<double2*>(raw + ((sizeof(Shared) + 15) & ~size_t(15)));
+  const int slot = threadIdx.x / NTU, tid = threadIdx.x % NTU, lane = threadIdx.x & 31, wu = tid >> 5;
+  const long long unit = (long long)blockIdx.x * (blockDim.x / NTU) + slot;
+  if (unit >= (long long)m * nb) return;  // the whole unit (UW = 4: the whole CTA)
+  unsigned char* mine = raw + slot * wbytes;
+  WarpShared& S = *reinterpret_cast<WarpShared*>(mine);
+  double2* psi = reinterpret_cast<double2*>(mine + ((sizeof(WarpShared) + 15) & ~size_t(15)));
   double2* ph = psi + (1 << b);
-  const int i = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int i = int(unit / nb), blk = int(unit % nb);
+  const int start = blk * b;
+  const int bl = min(b, n - start);
+  const int dim = 1 << bl;
   const float* xs = x + size_t(i) * n;
   const int h = chi / 2;
   const size_t per = size_t(chi) * chi;  // complex entries per sample-site
-  double disc = 0.0;                     // thread 0: discarded weight over all cuts
+  double disc = 0.0;                     // thread 0: discarded weight over this block's cuts
 
-  for (int start = 0; start < n; start += b) {
-    const int bl = min(b, n - start);
-    const int dim = 1 << bl;
-    // ---- 1. block statevector ----
-    blockstate::build(psi, ph, S.coef, xs + start, bl, reps, angle_scale, pairs_kind, tid, NT);
-    // ---- 2. SVD sweep over the block's cuts ----
-    int r = 2, c = dim / 2;
-    if (tid < 2) S.rowbase[tid] = tid * c;
-    __syncthreads();
-    for (int q = 0; q < bl; ++q) {
-      const int site = start + q;
-      const size_t base = (size_t(site) * m + i) * per;
-      if (q == bl - 1) {
-        // last qubit: the remaining (r x 1) vector, normalised, is column 0 of each block s
-        double p = 0.0;
-        if (tid < r) {
-          const double2 v = psi[S.rowbase[tid]];
-          p = v.x * v.x + v.y * v.y;
-        }
-        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);  // r <= 32: warp 0 holds all
-        if (tid == 0) S.scale = p > 0.0 ? 1.0 / sqrt(p) : 0.0;
-        __syncthreads();
-        for (size_t e = tid; e < per; e += NT) {
-          const int s = int(e / (size_t(h) * chi)), j = int((e / chi) % h), l = int(e % chi);
-          const int a = l % h, row = 2 * a + s;
-          double2 v = make_double2(0.0, 0.0);
-          if (j == 0 && 2 * a < r) {
-            const double2 w = psi[S.rowbase[row]];
-            v = make_double2(w.x * S.scale, w.y * S.scale);
-          }
-          store(out, base + e, v, out_c128);
-        }
-        __syncthreads();
-        break;
+  // ---- 1. block statevector ----
+  if constexpr (UW == 1)
+    blockstate::build(psi, ph, S.coef, xs + start, bl, reps, angle_scale, pairs_kind, tid, NTU,
+                      blockstate::WarpSync());
+  else
+    blockstate::build(psi, ph, S.coef, xs + start, bl, reps, angle_scale, pairs_kind, tid, NTU,
+                      blockstate::CtaSync());
+  // ---- 2. SVD sweep over the block's cuts ----
+  int r = 2, c = dim / 2;
+  if (tid < 2) S.rowbase[tid] = tid * c;
+  unit_sync<UW>();
+  for (int q = 0; q < bl; ++q) {
+    const int site = start + q;
+    const size_t base = (size_t(site) * m + i) * per;
+    if (q == bl - 1) {
+      // last qubit: the remaining (r x 1) vector, normalised, is column 0 of each block s
+      double p = 0.0;
+      if (tid < r) {  // r <= 32: warp 0 holds every row
+        const double2 v = psi[S.rowbase[tid]];
+        p = v.x * v.x + v.y * v.y;
       }
-      for (int e = tid; e < r * r; e += NT) S.J[e / r][e % r] = make_double2(e / r == e % r ? 1.0 : 0.0, 0.0);
-      __syncthreads();
-      // one-sided Jacobi on the r rows (length c), r/2 disjoint pairs per round
-      const int npairs = r / 2;
-      int tpp = NT / npairs;
-      if (tpp > 32) tpp = 32;
-      tpp = 1 << (31 - __clz(tpp));  // power of two
-      const int g = tid / tpp, gl = tid % tpp;
-      for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
-        int rotated = 0;
-        for (int t = 0; t < r - 1; ++t) {
-          const bool act = g < npairs;
-          const int rp = act ? rr_row(g, t, r) : 0, rq = act ? rr_row(r - 1 - g, t, r) : 1;
-          const double2* P = psi + S.rowbase[rp];
-          const double2* Q = psi + S.rowbase[rq];
-          double al = 0.0, be = 0.0, gx = 0.0, gy = 0.0;
-          if (act)
-            for (int col = gl; col < c; col += tpp) {
-              const double2 u = P[col], v = Q[col];
-              al += u.x * u.x + u.y * u.y;
-              be += v.x * v.x + v.y * v.y;
-              const double2 w = cconjmul(u, v);
-              gx += w.x;
-              gy += w.y;
-            }
-          for (int o = tpp / 2; o > 0; o >>= 1) {
-            al += __shfl_xor_sync(0xffffffffu, al, o);
-            be += __shfl_xor_sync(0xffffffffu, be, o);
-            gx += __shfl_xor_sync(0xffffffffu, gx, o);
-            gy += __shfl_xor_sync(0xffffffffu, gy, o);
-          }
-          const double gm = sqrt(gx * gx + gy * gy);
-          if (act && fmin(al, be) > FLOOR2 && gm > ORTH_TOL * sqrt(al * be)) {
-            // rows p' = c p - s e^{-i phi} q, q' = s p + c e^{-i phi} q with gamma = |gamma| e^{i phi}
-            const double zeta = (be - al) / (2.0 * gm);
-            const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-            const double2 ph = make_double2(gx / gm, -gy / gm);  // e^{-i phi}
-            double2* Pw = psi + S.rowbase[rp];
-            double2* Qw = psi + S.rowbase[rq];
-            for (int col = gl; col < c; col += tpp) {
-              const double2 u = Pw[col], v = cmul(ph, Qw[col]);
-              Pw[col] = make_double2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
-              Qw[col] = make_double2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
-            }
-            for (int col = gl; col < r; col += tpp) {
-              const double2 u = S.J[rp][col], v = cmul(ph, S.J[rq][col]);
-              S.J[rp][col] = make_double2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
-              S.J[rq][col] = make_double2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
-            }
-            rotated = 1;
-          }
-          __syncthreads();
-        }
-        if (!__syncthreads_or(rotated)) break;
-      }
-      // squared row norms (one warp per row)
-      for (int row = tid >> 5; row < r; row += NT / 32) {
-        const double2* P = psi + S.rowbase[row];
-        double p = 0.0;
-        for (int col = lane; col < c; col += 32) p += P[col].x * P[col].x + P[col].y * P[col].y;
-        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-        if (lane == 0) S.nrm[row] = p;
-      }
-      __syncthreads();
-      if (tid < r) {
-        int rank = 0;
-        for (int j = 0; j < r; ++j) rank += (S.nrm[j] > S.nrm[tid] || (S.nrm[j] == S.nrm[tid] && j < tid)) ? 1 : 0;
-        S.perm[rank] = tid;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        const double top = S.nrm[S.perm[0]];
-        const double floor2 = cutoff * cutoff * top;
-        double total = 0.0, kept = 0.0;
-        int keep = 0;
-        for (int k = 0; k < r; ++k) {
-          const double v = S.nrm[S.perm[k]];
-          total += v;
-          if (keep < cap && v > floor2) {
-            ++keep;
-            kept += v;
-          }
-        }
-        if (keep == 0) {  // a zero remainder: keep one (zero) row so the chain stays defined
-          keep = 1;
-          kept = S.nrm[S.perm[0]];
-        }
-        disc += total > kept ? (total - kept) / total : 0.0;
-        S.scale = kept > 0.0 ? sqrt(total / kept) : 1.0;
-        S.keep = keep;
-        if (bond) atomicMax(bond + site + 1, keep);
-      }
-      __syncthreads();
-      const int keep = S.keep;
-      // site tensor: B_s[a][j] = conj(J[perm[j]][2 a + s]) for j < keep, lifted (both t)
-      for (size_t e = tid; e < per; e += NT) {
+      for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+      if (tid == 0) S.scale = p > 0.0 ? 1.0 / sqrt(p) : 0.0;
+      unit_sync<UW>();
+      const double inv = S.scale;
+      for (size_t e = tid; e < per; e += NTU) {
         const int s = int(e / (size_t(h) * chi)), j = int((e / chi) % h), l = int(e % chi);
         const int a = l % h, row = 2 * a + s;
         double2 v = make_double2(0.0, 0.0);
-        if (j < keep && row < r) v = cconj(S.J[S.perm[j]][row]);
+        if (j == 0 && 2 * a < r) {
+          const double2 w = psi[S.rowbase[row]];
+          v = make_double2(w.x * inv, w.y * inv);
+        }
         store(out, base + e, v, out_c128);
       }
-      // next remainder: kept rows rescaled, each split into its two halves
-      for (int k = tid >> 5; k < keep; k += NT / 32) {
-        double2* P = psi + S.rowbase[S.perm[k]];
-        for (int col = lane; col < c; col += 32) P[col] = make_double2(P[col].x * S.scale, P[col].y * S.scale);
-      }
-      if (tid < 2 * keep) S.nextbase[tid] = S.rowbase[S.perm[tid >> 1]] + (tid & 1) * (c / 2);
-      __syncthreads();
-      if (tid < 2 * keep) S.rowbase[tid] = S.nextbase[tid];
-      r = 2 * keep;
-      c /= 2;
-      __syncthreads();
+      break;
     }
+    for (int e = tid; e < r * r; e += NTU) S.J[e / r][e % r] = make_double2(e / r == e % r ? 1.0 : 0.0, 0.0);
+    unit_sync<UW>();
+    // one-sided Jacobi on the r rows (length c), r/2 disjoint pairs per round, a lane group each
+    const int npairs = r / 2;
+    int tpp = NTU / npairs;
+    if (tpp > 32) tpp = 32;
+    tpp = 1 << (31 - __clz(tpp));  // lanes per pair, a power of two within one warp
+    const int g = tid / tpp, gl = tid % tpp;
+    for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
+      int rotated = 0;
+      for (int t = 0; t < r - 1; ++t) {
+        const bool act = g < npairs;
+        const int rp = act ? rr_row(g, t, r) : 0, rq = act ? rr_row(r - 1 - g, t, r) : 1;
+        const double2* P = psi + S.rowbase[rp];
+        const double2* Q = psi + S.rowbase[rq];
+        double al = 0.0, be = 0.0, gx = 0.0, gy = 0.0;
+        if (act)
+          for (int col = gl; col < c; col += tpp) {
+            const double2 u = P[col], v = Q[col];
+            al += u.x * u.x + u.y * u.y;
+            be += v.x * v.x + v.y * v.y;
+            const double2 w = cconjmul(u, v);
+            gx += w.x;
+            gy += w.y;
+          }
+        for (int o = tpp / 2; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          gx += __shfl_xor_sync(0xffffffffu, gx, o);
+          gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        }
+        const double gm = sqrt(gx * gx + gy * gy);
+        if (act && fmin(al, be) > FLOOR2 && gm > ORTH_TOL * sqrt(al * be)) {
+          // rows p' = c p - s e^{-i phi} q, q' = s p + c e^{-i phi} q with gamma = |gamma| e^{i phi}
+          const double zeta = (be - al) / (2.0 * gm);
+          const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+          const double2 phs = make_double2(gx / gm, -gy / gm);  // e^{-i phi}
+          double2* Pw = psi + S.rowbase[rp];
+          double2* Qw = psi + S.rowbase[rq];
+          for (int col = gl; col < c; col += tpp) {
+            const double2 u = Pw[col], v = cmul(phs, Qw[col]);
+            Pw[col] = make_double2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
+            Qw[col] = make_double2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+          }
+          for (int col = gl; col < r; col += tpp) {
+            const double2 u = S.J[rp][col], v = cmul(phs, S.J[rq][col]);
+            S.J[rp][col] = make_double2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
+            S.J[rq][col] = make_double2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+          }
+          rotated = 1;
+        }
+        unit_sync<UW>();
+      }
+      int any;
+      if constexpr (UW == 1) any = __any_sync(0xffffffffu, rotated);
+      else any = __syncthreads_or(rotated);
+      if (!any) break;
+    }
+    // squared row norms: each warp sums rows in turn
+    for (int row = wu; row < r; row += UW) {
+      const double2* P = psi + S.rowbase[row];
+      double p = 0.0;
+      for (int col = lane; col < c; col += 32) p += P[col].x * P[col].x + P[col].y * P[col].y;
+      for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+      if (lane == 0) S.nrm[row] = p;
+    }
+    unit_sync<UW>();
+    if (tid < r) {
+      int rank = 0;
+      for (int j = 0; j < r; ++j) rank += (S.nrm[j] > S.nrm[tid] || (S.nrm[j] == S.nrm[tid] && j < tid)) ? 1 : 0;
+      S.perm[rank] = tid;
+    }
+    unit_sync<UW>();
+    if (tid == 0) {
+      const double top = S.nrm[S.perm[0]];
+      const double floor2 = cutoff * cutoff * top;
+      double total = 0.0, kept = 0.0;
+      int keep = 0;
+      for (int k = 0; k < r; ++k) {
+        const double v = S.nrm[S.perm[k]];
+        total += v;
+        if (keep < cap && v > floor2) {
+          ++keep;
+          kept += v;
+        }
+      }
+      if (keep == 0) {  // a zero remainder: keep one (zero) row so the chain stays defined
+        keep = 1;
+        kept = S.nrm[S.perm[0]];
+      }
+      disc += total > kept ? (total - kept) / total : 0.0;
+      S.scale = kept > 0.0 ? sqrt(total / kept) : 1.0;
+      S.keep = keep;
+      if (bond) atomicMax(bond + site + 1, keep);
+    }
+    unit_sync<UW>();
+    const int keep = S.keep;
+    // site tensor: B_s[a][j] = conj(J[perm[j]][2 a + s]) for j < keep, lifted (both t)
+    for (size_t e = tid; e < per; e += NTU) {
+      const int s = int(e / (size_t(h) * chi)), j = int((e / chi) % h), l = int(e % chi);
+      const int a = l % h, row = 2 * a + s;
+      double2 v = make_double2(0.0, 0.0);
+      if (j < keep && row < r) v = cconj(S.J[S.perm[j]][row]);
+      store(out, base + e, v, out_c128);
+    }
+    // next remainder: kept rows rescaled, each split into its two halves
+    for (int k = wu; k < keep; k += UW) {
+      double2* P = psi + S.rowbase[S.perm[k]];
+      for (int col = lane; col < c; col += 32) P[col] = make_double2(P[col].x * S.scale, P[col].y * S.scale);
+    }
+    if (tid < 2 * keep) S.nextbase[tid] = S.rowbase[S.perm[tid >> 1]] + (tid & 1) * (c / 2);
+    unit_sync<UW>();
+    if (tid < 2 * keep) S.rowbase[tid] = S.nextbase[tid];
+    r = 2 * keep;
+    c /= 2;
+    unit_sync<UW>();
   }
-  if (tid == 0 && discarded) discarded[i] = float(disc);
+  if (tid == 0 && discarded && disc > 0.0) atomicAdd(discarded + i, float(disc));
 }
 
 }  // namespace bsvd
@@ -271,13 +301,29 @@ DK_API dk_status dk_mps_build_blocks(dk_ctx* ctx, const float* x, int m, int n, 
   if (log_norm && !(chi == 4 || (dtype == DK_C64 && (chi == 8 || chi == 32)))) return DK_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int kind = fm->entangle ? entangler : -1;  // -1: no pair is entangled
-  const size_t smem = bsvd::smem_bytes(b);
-  if (cudaFuncSetAttribute(bsvd::block_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-      cudaSuccess)
-    return DK_ERR_CUDA;
-  if (bond_dims) bsvd::bond_init_kernel<<<1, bsvd::NT, 0, st>>>(bond_dims, n);
-  bsvd::block_svd_kernel<<<m, bsvd::NT, smem, st>>>(x, m, n, b, fm->reps, double(fm->angle_scale), kind, cutoff,
-                                                    chi / 2, chi, dtype == DK_C128 ? 1 : 0, mps, bond_dims, discarded);
+  const int nb = (n + b - 1) / b;
+  const int wpc = bsvd::warps_per_cta(b);  // units that fit in one CTA's shared memory
+  const size_t wbytes = bsvd::warp_bytes(b);
+  if (bond_dims) bsvd::bond_init_kernel<<<1, 128, 0, st>>>(bond_dims, n);
+  if (discarded && cudaMemsetAsync(discarded, 0, size_t(m) * sizeof(float), st) != cudaSuccess) return DK_ERR_CUDA;
+  const long long units = (long long)m * nb;
+  const int c128 = dtype == DK_C128 ? 1 : 0;
+  if (wpc >= 2) {  // a warp per unit, several units per CTA
+    const size_t smem = size_t(wpc) * wbytes;
+    if (cudaFuncSetAttribute(bsvd::block_svd_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+        cudaSuccess)
+      return DK_ERR_CUDA;
+    bsvd::block_svd_kernel<1><<<int((units + wpc - 1) / wpc), wpc * 32, smem, st>>>(
+        x, m, n, b, nb, fm->reps, double(fm->angle_scale), kind, cutoff, chi / 2, chi, c128, wbytes, mps, bond_dims,
+        discarded);
+  } else {  // large blocks: four warps per unit, one unit per CTA
+    if (cudaFuncSetAttribute(bsvd::block_svd_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wbytes)) !=
+        cudaSuccess)
+      return DK_ERR_CUDA;
+    bsvd::block_svd_kernel<4><<<int(units), 128, wbytes, st>>>(x, m, n, b, nb, fm->reps, double(fm->angle_scale), kind,
+                                                                cutoff, chi / 2, chi, c128, wbytes, mps, bond_dims,
+                                                                discarded);
+  }
   dk_status s = launch_status();
   if (s != DK_OK || !log_norm) return s;
   return self_overlap_launch(mps, m, n, chi, dtype, log_norm, st);
