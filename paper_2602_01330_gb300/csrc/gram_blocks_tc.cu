@@ -32,13 +32,20 @@ using u16 = uint16_t;
 using u32 = uint32_t;
 
 constexpr int KC = 16;                 // complex amplitudes per step (one k16 per plane)
-constexpr int TR = 128, TC = 64;       // pair tile
-constexpr int NT = 256;                // 8 warps: 4 (rows) x 2 (columns), warp tile 32 x 32
+constexpr int TC = 64;                 // pair tile: (32 WM) rows x 64 columns
 constexpr int ROWB = 144;              // staged sample row: 4 planes x 32 B + 16 B pad
-constexpr int STAGE_A = TR * ROWB;
-constexpr int STAGE = (TR + TC) * ROWB;
 constexpr int NSLOT = 32;              // pairs per thread
-constexpr size_t SMEM = 2 * STAGE + size_t(NSLOT) * NT * sizeof(float);
+// WM warps along the rows (4: 128 x 64 tiles, 8 warps; 2: 64 x 64 tiles, 4 warps), 2 along
+// the columns, each warp 32 x 32 pairs
+template <int WM>
+struct TileCfg {
+  static constexpr int TR = 32 * WM, NT = 64 * WM;
+  static constexpr int STAGE_A = TR * ROWB, STAGE = (TR + TC) * ROWB;
+  static constexpr int COPIES = (TR + TC) * 8 / NT;  // 16-byte copies per thread per stage
+  static constexpr size_t SMEM = 2 * STAGE + size_t(NSLOT) * NT * sizeof(float);
+};
+// self-norm kernel: 16 samples per warp
+constexpr int STAGE_N = 16 * ROWB;
 constexpr u32 NEG2 = 0x80008000u;      // flips the sign of both BF16 halves
 
 __device__ __forceinline__ void mma16816(float (&d)[4], const u32 (&a)[4], u32 b0, u32 b1) {
@@ -65,10 +72,13 @@ __device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_
 __device__ __forceinline__ void lg_add(float& lg, float re, float im) { lg += log2f(fmaf(re, re, im * im)); }
 __device__ __forceinline__ float half_log_lg(float lg) { return lg * (0.5f * 0.69314718055994530942f); }
 
-// The Gram block of p (symmetric or rectangular), p.ntiles tiles of 128 x 64 pairs.
-__global__ void __launch_bounds__(NT, 2)
+// The Gram block of p (symmetric or rectangular), p.ntiles tiles of TR x 64 pairs.
+template <int WM>
+__global__ void __launch_bounds__(64 * WM, 8 / WM)
     gram_blocks_tc_kernel(const unsigned char* __restrict__ sr, int m_r, const unsigned char* __restrict__ sc,
                           int m_c, int nb, int dp, const GramArgs p) {
+  using T = TileCfg<WM>;
+  constexpr int TR = T::TR, NT = T::NT, STAGE = T::STAGE, STAGE_A = T::STAGE_A;
   extern __shared__ __align__(128) unsigned char smem[];
   float* s_lg = reinterpret_cast<float*>(smem + 2 * STAGE);
   const u32 sbase = smem_u32(smem);
@@ -84,11 +94,11 @@ __global__ void __launch_bounds__(NT, 2)
     int ti, tj;
     decode_tile(p, TR, TC, t, ti, tj);
     const int r0 = p.row0 + ti * TR, c0 = p.col0 + tj * TC;
-    // stage loader: 6 copies of 16 B per thread (192 rows x 8 pieces)
+    // stage loader: (TR + 64) rows x 8 pieces of 16 B
     auto issue = [&](int c, int buf) {
       const int blk = c / cpb, k0 = (c - blk * cpb) * KC;
 #pragma unroll
-      for (int h = 0; h < 6; ++h) {
+      for (int h = 0; h < T::COPIES; ++h) {
         const int q = tid + NT * h;
         const int row = q >> 3, piece = q & 7, plane = piece >> 1, half = piece & 1;
         const bool is_a = row < TR;
@@ -301,22 +311,37 @@ dk_status block_selfnorm_tc_launch(const void* states, int m, int nb, int dp, fl
   return launch_status();
 }
 
-dk_status gram_blocks_tc_launch(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp,
-                                GramArgs a, cudaStream_t st) {
+template <int WM>
+static dk_status launch_tc(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp, GramArgs a,
+                           int ntiles, cudaStream_t st) {
+  using T = gbtc::TileCfg<WM>;
+  auto kern = gbtc::gram_blocks_tc_kernel<WM>;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(gbtc::gram_blocks_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(gbtc::SMEM)) != cudaSuccess)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(T::SMEM)) != cudaSuccess)
       return DK_ERR_CUDA;
     attr = true;
   }
-  a.ntiles = count_tiles(a, gbtc::TR, gbtc::TC);
-  long long grid = 2LL * ctx->sm_count;
-  if (grid > a.ntiles) grid = a.ntiles;
+  a.ntiles = ntiles;
+  long long grid = (long long)(8 / WM) * ctx->sm_count;
+  if (grid > ntiles) grid = ntiles;
   if (grid < 1) return DK_OK;
-  gbtc::gram_blocks_tc_kernel<<<int(grid), gbtc::NT, gbtc::SMEM, st>>>(
-      static_cast<const unsigned char*>(sr), m_r, static_cast<const unsigned char*>(sc), m_c, nb, dp, a);
+  kern<<<int(grid), T::NT, T::SMEM, st>>>(static_cast<const unsigned char*>(sr), m_r,
+                                          static_cast<const unsigned char*>(sc), m_c, nb, dp, a);
   return launch_status();
+}
+
+dk_status gram_blocks_tc_launch(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp,
+                                GramArgs a, cudaStream_t st) {
+  // tile rows 128 (2 CTAs of 8 warps per SM) or 64 (4 CTAs of 4 warps): the fewer waves x tile
+  // area, the larger tile on ties (its stages serve more pairs)
+  GramArgs a4 = a, a2 = a;
+  const int t4 = count_tiles(a4, gbtc::TileCfg<4>::TR, gbtc::TC);
+  const int t2 = count_tiles(a2, gbtc::TileCfg<2>::TR, gbtc::TC);
+  const long long s4 = 2LL * ctx->sm_count, s2 = 4LL * ctx->sm_count;
+  const long long cost4 = 2 * ((t4 + s4 - 1) / s4), cost2 = (t2 + s2 - 1) / s2;
+  if (cost4 <= cost2) return launch_tc<4>(ctx, sr, m_r, sc, m_c, nb, dp, a4, t4, st);
+  return launch_tc<2>(ctx, sr, m_r, sc, m_c, nb, dp, a2, t2, st);
 }
 
 }  // namespace dk
