@@ -126,5 +126,84 @@ __device__ inline void build(double2* psi, double2* ph, Coeffs& C, const float* 
   }
 }
 
+// The same state in FP32 for operands that are rounded to split BF16 afterwards (about 17
+// significant bits): the phase Phi(z), up to a few hundred radians, is still summed in FP64
+// from the tables and reduced to [-pi, pi] there, then sincosf of the reduced angle; the
+// butterflies and the phase multiplications run in FP32 (relative error ~1e-7 per amplitude,
+// far below the split's 2^-18 ~ 4e-6).
+template <class Sync = CtaSync>
+__device__ inline void build_f32(float2* psi, float2* ph, Coeffs& C, const float* xb, int bl, int reps,
+                                 double angle_scale, int pairs_kind, int tid, int nt, Sync sync = Sync()) {
+  const int dim = 1 << bl;
+  const int hb = bl >> 1, lb = bl - hb;
+  if (tid < bl) C.hq[tid] = 0.5 * angle_scale * double(xb[tid]);
+  for (int e = tid; e < MAXB * MAXB; e += nt) {
+    const int q = e / MAXB, r = e % MAXB;
+    const bool on = q < bl && r < bl && q < r &&
+                    (pairs_kind == DK_ENT_FULL || (pairs_kind == DK_ENT_CHAIN && r == q + 1));
+    C.jq[q][r] = on ? (PI_D - double(xb[q])) * (PI_D - double(xb[r])) : 0.0;
+  }
+  sync();
+  for (int e = tid; e < (1 << hb); e += nt) {
+    double a = 0.0;
+    for (int q = 0; q < hb; ++q) {
+      const double zq = ((e >> (hb - 1 - q)) & 1) ? -1.0 : 1.0;
+      double s = C.hq[q];
+      for (int r = q + 1; r < hb; ++r) s += ((e >> (hb - 1 - r)) & 1) ? -C.jq[q][r] : C.jq[q][r];
+      a += zq * s;
+    }
+    C.ta[e] = a;
+  }
+  for (int e = tid; e < (1 << lb); e += nt) {
+    double bsum = 0.0;
+    for (int t = 0; t < lb; ++t) {
+      const int q = hb + t;
+      const double zq = ((e >> (lb - 1 - t)) & 1) ? -1.0 : 1.0;
+      double s = C.hq[q];
+      for (int u = t + 1; u < lb; ++u) s += ((e >> (lb - 1 - u)) & 1) ? -C.jq[q][hb + u] : C.jq[q][hb + u];
+      bsum += zq * s;
+    }
+    C.tb[e] = bsum;
+    for (int q = 0; q < hb; ++q) {
+      double v = 0.0;
+      for (int t = 0; t < lb; ++t) v += ((e >> (lb - 1 - t)) & 1) ? -C.jq[q][hb + t] : C.jq[q][hb + t];
+      C.tv[e][q] = v;
+    }
+  }
+  sync();
+  const float amp = exp2f(-0.5f * float(bl));
+  constexpr double TWO_PI = 6.283185307179586476925;
+  for (int e = tid; e < dim; e += nt) {
+    const int zh = e >> lb, zl = e & ((1 << lb) - 1);
+    double phi = C.ta[zh] + C.tb[zl];
+    for (int q = 0; q < hb; ++q) phi += ((zh >> (hb - 1 - q)) & 1) ? -C.tv[zl][q] : C.tv[zl][q];
+    const float red = float(phi - TWO_PI * rint(phi * (1.0 / TWO_PI)));  // in [-pi, pi]
+    float sn, cs;
+    sincosf(-red, &sn, &cs);
+    ph[e] = make_float2(cs, sn);
+    psi[e] = make_float2(amp * cs, amp * sn);
+  }
+  sync();
+  constexpr float R2 = 0.70710678118654752440f;
+  for (int rep = 1; rep < reps; ++rep) {
+    for (int q = 0; q < bl; ++q) {
+      const int bit = 1 << (bl - 1 - q);
+      for (int e = tid; e < dim / 2; e += nt) {
+        const int lo = ((e & ~(bit - 1)) << 1) | (e & (bit - 1));
+        const int hi = lo | bit;
+        const float2 u = psi[lo], v = psi[hi];
+        psi[lo] = make_float2((u.x + v.x) * R2, (u.y + v.y) * R2);
+        psi[hi] = make_float2((u.x - v.x) * R2, (u.y - v.y) * R2);
+      }
+      sync();
+    }
+    for (int e = tid; e < dim; e += nt) {
+      const float2 a = psi[e], w = ph[e];
+      psi[e] = make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+    }
+    sync();
+  }
+}
+
 }  // namespace blockstate
 }  // namespace dk

@@ -77,17 +77,23 @@ __global__ void __launch_bounds__(BUILD_NT) block_states_kernel(const float* __r
   const int start = blk * b;
   const int bl = min(b, n - start);
   const int dp = dpad_of(b);
-  blockstate::build(psi, ph, C, x + size_t(i) * n + start, bl, reps, angle_scale, pairs_kind, threadIdx.x, BUILD_NT);
   float2* out = states + (size_t(blk) * m + i) * dp;
   const int dim = 1 << bl;
   if (!split) {
+    blockstate::build(psi, ph, C, x + size_t(i) * n + start, bl, reps, angle_scale, pairs_kind, threadIdx.x,
+                      BUILD_NT);
     for (int k = threadIdx.x; k < dp; k += BUILD_NT)
       out[k] = k < dim ? make_float2(float(psi[k].x), float(psi[k].y)) : make_float2(0.0f, 0.0f);
     return;
   }
+  // split-BF16 operands: the state in FP32 (see blockstate::build_f32), in the same buffer
+  float2* psf = reinterpret_cast<float2*>(psi);
+  float2* phf = psf + (1 << b);
+  blockstate::build_f32(psf, phf, C, x + size_t(i) * n + start, bl, reps, angle_scale, pairs_kind, threadIdx.x,
+                        BUILD_NT);
   __nv_bfloat16* pl = reinterpret_cast<__nv_bfloat16*>(out);
   for (int k = threadIdx.x; k < dp; k += BUILD_NT) {
-    const float vr = k < dim ? float(psi[k].x) : 0.0f, vi = k < dim ? float(psi[k].y) : 0.0f;
+    const float vr = k < dim ? psf[k].x : 0.0f, vi = k < dim ? psf[k].y : 0.0f;
     const __nv_bfloat16 hr = __float2bfloat16_rn(vr), hi = __float2bfloat16_rn(vi);
     pl[k] = hr;
     pl[dp + k] = hi;
