@@ -202,27 +202,28 @@ __global__ void __launch_bounds__(64 * WM, 8 / WM)
   }
 }
 
-// ln N_i for the states of m samples: one warp per 16 samples computes the 16 x 16 diagonal
-// block of their Gram with exactly the per-element MMA sequence of gram_blocks_tc_kernel
-// (same planes, same three products in the same order into re and im, same steps, same
-// per-block log2 sum). Every element of an m16n8k16 product is a function of its own row
-// and column only, and the diagonal element (i, i) sits at the same fragment position
-// (row i mod 16, column i mod 8) in both kernels, so the diagonal is bit-identical to the
-// Gram's and K_q(x, x) = 1 exactly.
-constexpr int NORM_WARPS = 4;
+// ln N_i for the states of m samples: a CTA per 16 samples, its warps taking the blocks in
+// turn (blk = warp, warp + NORM_WARPS, ...). A warp computes the 16 x 16 diagonal block of the
+// block's Gram with exactly the per-element MMA sequence of gram_blocks_tc_kernel (same
+// planes, same three products in the same order into re and im, same steps) and keeps
+// |G_B(i, i)|^2 in shared memory; then one thread per sample adds the log2 terms in block
+// order, as the Gram kernel does. Every element of an m16n8k16 product is a function of its
+// own row and column only, and the diagonal element (i, i) sits at the same fragment
+// position (row i mod 16, column i mod 8) in both kernels, so the diagonal is bit-identical
+// to the Gram's and K_q(x, x) = 1 exactly.
+constexpr int NORM_WARPS = 8;
 __global__ void __launch_bounds__(NORM_WARPS * 32)
     block_selfnorm_tc_kernel(const unsigned char* __restrict__ s, int m, int nb, int dp, float* __restrict__ log_norm) {
-  __shared__ __align__(128) unsigned char st[NORM_WARPS][2][16 * ROWB];
+  extern __shared__ __align__(128) unsigned char nsm[];
+  float* g2 = reinterpret_cast<float*>(nsm + NORM_WARPS * 2 * STAGE_N);  // [block][16 samples]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = (blockIdx.x * NORM_WARPS + warp) * 16;
-  if (i0 >= m) return;  // whole warp; the kernel uses no block-wide barrier
-  const int cpb = dp / KC, total = nb * cpb;
+  const int i0 = blockIdx.x * 16;
+  const int cpb = dp / KC;
   const size_t sample_bytes = size_t(dp) * 8;
   const int a_row = (lane & 7) + 8 * ((lane >> 3) & 1), a_k = 8 * (lane >> 4);
   const int b_row = (lane & 7) + 8 * (lane >> 4), b_k = 8 * ((lane >> 3) & 1);
-  const u32 sw = smem_u32(&st[warp][0][0]);
-  auto issue = [&](int c, int buf) {
-    const int blk = c / cpb, k0 = (c - blk * cpb) * KC;
+  const u32 sw = smem_u32(nsm + warp * 2 * STAGE_N);
+  auto issue = [&](int blk, int k0, int buf) {
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       const int q = lane + 32 * h;
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(NORM_WARPS * 32)
       const int smp = min(i0 + row, m - 1);
       const unsigned char* src =
           s + (size_t(blk) * m + smp) * sample_bytes + size_t(plane) * dp * 2 + size_t(k0) * 2 + half * 16;
-      cp_async16(sw + buf * 16 * ROWB + row * ROWB + plane * 32 + half * 16, src);
+      cp_async16(sw + buf * STAGE_N + row * ROWB + plane * 32 + half * 16, src);
     }
     cp_async_commit();
   };
@@ -239,74 +240,79 @@ __global__ void __launch_bounds__(NORM_WARPS * 32)
   const int g = lane >> 2, t4 = lane & 3;
   const bool holds = (g >> 1) == t4;
   const int e_lo = g & 1;  // accumulator index of (g, g) in tile 0; (g + 8, g + 8) is 2 + e_lo in tile 1
-  float re[2][4], im[2][4];
+  for (int blk = warp; blk < nb; blk += NORM_WARPS) {
+    float re[2][4], im[2][4];
 #pragma unroll
-  for (int v = 0; v < 2; ++v)
+    for (int v = 0; v < 2; ++v)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) re[v][e] = im[v][e] = 0.0f;
-  float lg0 = 0.0f, lg1 = 0.0f;
-  issue(0, 0);
-  for (int c = 0; c < total; ++c) {
-    const int buf = c & 1;
-    if (c + 1 < total) {
-      issue(c + 1, buf ^ 1);
-      cp_async_wait_1();
-    } else {
-      cp_async_wait_0();
-    }
-    __syncwarp();
-    const u32 sa = sw + buf * 16 * ROWB;
-    u32 bf[4][2][2];
-#pragma unroll
-    for (int pl = 0; pl < 4; ++pl) {
-      u32 r[4];
-      ldsm_x4(r, sa + b_row * ROWB + pl * 32 + b_k * 2);
-      bf[pl][0][0] = r[0];
-      bf[pl][0][1] = r[1];
-      bf[pl][1][0] = r[2];
-      bf[pl][1][1] = r[3];
-    }
-#pragma unroll
-    for (int part = 0; part < 2; ++part) {
-      u32 ahi[4], alo[4];
-      const u32 addr = sa + a_row * ROWB + a_k * 2;
-      ldsm_x4(ahi, addr + part * 32);
-      ldsm_x4(alo, addr + (2 + part) * 32);
-#pragma unroll
-      for (int v = 0; v < 2; ++v) {
-        const int pr_hi = part ? 1 : 0, pr_lo = part ? 3 : 2;
-        const int pi_hi = part ? 0 : 1, pi_lo = part ? 2 : 3;
-        const u32 sg = part ? NEG2 : 0u;
-        mma16816(re[v], alo, bf[pr_hi][v][0], bf[pr_hi][v][1]);
-        mma16816(re[v], ahi, bf[pr_lo][v][0], bf[pr_lo][v][1]);
-        mma16816(re[v], ahi, bf[pr_hi][v][0], bf[pr_hi][v][1]);
-        mma16816(im[v], alo, bf[pi_hi][v][0] ^ sg, bf[pi_hi][v][1] ^ sg);
-        mma16816(im[v], ahi, bf[pi_lo][v][0] ^ sg, bf[pi_lo][v][1] ^ sg);
-        mma16816(im[v], ahi, bf[pi_hi][v][0] ^ sg, bf[pi_hi][v][1] ^ sg);
+      for (int e = 0; e < 4; ++e) re[v][e] = im[v][e] = 0.0f;
+    issue(blk, 0, 0);
+    for (int c = 0; c < cpb; ++c) {
+      const int buf = c & 1;
+      if (c + 1 < cpb) {
+        issue(blk, (c + 1) * KC, buf ^ 1);
+        cp_async_wait_1();
+      } else {
+        cp_async_wait_0();
       }
+      __syncwarp();
+      const u32 sa = sw + buf * STAGE_N;
+      u32 bf[4][2][2];
+#pragma unroll
+      for (int pl = 0; pl < 4; ++pl) {
+        u32 r[4];
+        ldsm_x4(r, sa + b_row * ROWB + pl * 32 + b_k * 2);
+        bf[pl][0][0] = r[0];
+        bf[pl][0][1] = r[1];
+        bf[pl][1][0] = r[2];
+        bf[pl][1][1] = r[3];
+      }
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        u32 ahi[4], alo[4];
+        const u32 addr = sa + a_row * ROWB + a_k * 2;
+        ldsm_x4(ahi, addr + part * 32);
+        ldsm_x4(alo, addr + (2 + part) * 32);
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const int pr_hi = part ? 1 : 0, pr_lo = part ? 3 : 2;
+          const int pi_hi = part ? 0 : 1, pi_lo = part ? 2 : 3;
+          const u32 sg = part ? NEG2 : 0u;
+          mma16816(re[v], alo, bf[pr_hi][v][0], bf[pr_hi][v][1]);
+          mma16816(re[v], ahi, bf[pr_lo][v][0], bf[pr_lo][v][1]);
+          mma16816(re[v], ahi, bf[pr_hi][v][0], bf[pr_hi][v][1]);
+          mma16816(im[v], alo, bf[pi_hi][v][0] ^ sg, bf[pi_hi][v][1] ^ sg);
+          mma16816(im[v], ahi, bf[pi_lo][v][0] ^ sg, bf[pi_lo][v][1] ^ sg);
+          mma16816(im[v], ahi, bf[pi_hi][v][0] ^ sg, bf[pi_hi][v][1] ^ sg);
+        }
+      }
+      __syncwarp();  // the stage is overwritten by the copy issued next
     }
-    if ((c + 1) % cpb == 0) {
+    if (holds) {
       // (selects, not a run-time index, keep the accumulators in registers)
-      lg_add(lg0, e_lo ? re[0][1] : re[0][0], e_lo ? im[0][1] : im[0][0]);
-      lg_add(lg1, e_lo ? re[1][3] : re[1][2], e_lo ? im[1][3] : im[1][2]);
-#pragma unroll
-      for (int v = 0; v < 2; ++v)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) re[v][e] = im[v][e] = 0.0f;
+      const float r0 = e_lo ? re[0][1] : re[0][0], q0 = e_lo ? im[0][1] : im[0][0];
+      const float r1 = e_lo ? re[1][3] : re[1][2], q1 = e_lo ? im[1][3] : im[1][2];
+      g2[blk * 16 + g] = fmaf(r0, r0, q0 * q0);
+      g2[blk * 16 + g + 8] = fmaf(r1, r1, q1 * q1);
     }
-    __syncwarp();  // the stage is overwritten by the copy issued next
   }
-  if (holds) {
-    if (i0 + g < m) log_norm[i0 + g] = half_log_lg(lg0);
-    if (i0 + g + 8 < m) log_norm[i0 + g + 8] = half_log_lg(lg1);
+  __syncthreads();
+  if (threadIdx.x < 16 && i0 + int(threadIdx.x) < m) {
+    float lg = 0.0f;
+    for (int blk = 0; blk < nb; ++blk) lg += log2f(g2[blk * 16 + threadIdx.x]);  // lg_add's order
+    log_norm[i0 + threadIdx.x] = half_log_lg(lg);
   }
 }
 
 }  // namespace gbtc
 
 dk_status block_selfnorm_tc_launch(const void* states, int m, int nb, int dp, float* log_norm, cudaStream_t st) {
-  const int warps = (m + 15) / 16;
-  gbtc::block_selfnorm_tc_kernel<<<(warps + gbtc::NORM_WARPS - 1) / gbtc::NORM_WARPS, gbtc::NORM_WARPS * 32, 0, st>>>(
+  const size_t smem = size_t(gbtc::NORM_WARPS) * 2 * gbtc::STAGE_N + size_t(nb) * 16 * sizeof(float);
+  if (smem > 227 * 1024) return DK_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(gbtc::block_selfnorm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+      cudaSuccess)
+    return DK_ERR_CUDA;
+  gbtc::block_selfnorm_tc_kernel<<<(m + 15) / 16, gbtc::NORM_WARPS * 32, smem, st>>>(
       static_cast<const unsigned char*>(states), m, nb, dp, log_norm);
   return launch_status();
 }
