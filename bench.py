@@ -435,7 +435,10 @@ def run_ours(args):
         # contracted exactly by per-block statevector overlaps
         block_stats = {"f32": blockmap.run_benchmark(ctx, n_tr, n_te, d, block=10, reps=reps),
                        "bf16x3": blockmap.run_benchmark(ctx, n_tr, n_te, d, block=10, reps=reps,
-                                                        prec=dualk.DK_PREC_BF16X3)}
+                                                        prec=dualk.DK_PREC_BF16X3),
+                       "bf16x3_mma_sync": blockmap.run_benchmark(ctx, n_tr, n_te, d, block=10, reps=reps,
+                                                                 prec=dualk.DK_PREC_BF16X3,
+                                                                 form=dualk.DK_BLOCK_MMA_SYNC)}
 
     if world > 1:
         tdist.destroy_process_group()

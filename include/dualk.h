@@ -75,6 +75,12 @@ typedef enum {
   DK_PREC_BF16X3 = 2
 } dk_precision;
 
+/* Kernels of the split-BF16 block-statevector Gram (dk_set_block_gram_form). */
+typedef enum {
+  DK_BLOCK_TCGEN05 = 0,  /* tcgen05.mma, TMEM accumulators, TMA loads (default) */
+  DK_BLOCK_MMA_SYNC = 1  /* warp-level mma.sync m16n8k16 */
+} dk_block_form;
+
 typedef struct dk_ctx dk_ctx;
 
 /* Feature map U(x) of §II-C (Eq. 6). The paper's circuit figure is not in its text;
@@ -242,12 +248,15 @@ size_t dk_block_states_bytes(int m, int n, int block);
  *   states    dk_block_states_bytes(m, n, fm->block) bytes (device, written), layout
  *             [block][sample][...] of dpad amplitudes (qubit 0 of the block most
  *             significant), computed in FP64 and rounded once: F32 as complex64 values;
- *             BF16X3 as four BF16 planes [hi(re) | hi(im) | lo(re) | lo(im)] with
- *             v ~ hi + lo; zeros beyond 2^b and beyond the 2^(n mod b) amplitudes of a short
+ *             BF16X3 as split values v ~ hi + lo, per chunk of 16 amplitudes one
+ *             128-byte row of four BF16 planes [hi(re) | hi(im) | lo(re) | lo(im)] of 16
+ *             values each; zeros beyond 2^b and beyond the 2^(n mod b) amplitudes of a short
  *             last block
  *   log_norm  m floats (device, written, may be NULL): ln|<psi~_i|psi~_i>| of the rounded
  *             states by the arithmetic of dk_gram_blocks in `prec` (for BF16X3 the diagonal
- *             tiles of that Gram), so that K_q(x, x) = 1 exactly
+ *             tiles of that Gram, in the context's dk_set_block_gram_form form; the tcgen05
+ *             form takes nb * m * 4 bytes of stream-ordered scratch for it), so that
+ *             K_q(x, x) = 1 exactly
  * Errors: DK_ERR_ARG (NULL pointers, m or n < 1, reps, entangler, misaligned states),
  *         DK_ERR_UNSUPPORTED (block outside 0..12 or above 12 qubits, m > 65535, more than
  *         6144 blocks, prec neither F32 nor BF16X3), DK_ERR_CUDA. */
@@ -259,7 +268,8 @@ dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, const dk_fm
  * §II-D Eq. 11): for each pair, a = prod_B <psi_B(x_i)|psi_B(x_j)> with each factor a
  * complex dot product of 2^b amplitudes — prec DK_PREC_F32: FP32 FMAs on CUDA cores;
  * DK_PREC_BF16X3: split-BF16 tensor-core products with FP32 accumulation (|dK| ~ 1e-5,
- * the 1e-4 mixed-precision class) — and ln|a| accumulated as a sum of log2 |factor|^2
+ * the 1e-4 mixed-precision class; tcgen05 or mma.sync kernels as dk_set_block_gram_form
+ * selects) — and ln|a| accumulated as a sum of log2 |factor|^2
  * (never underflows); log K_q = 2 ln|a| - ln N_i - ln N_j, K_q,
  * K_c = exp(-gamma ||x_i - x_j||^2), K = w K_q + (1 - w) K_c.
  *   states_rows / states_cols  dk_block_states output for m_rows / m_cols samples, same n
@@ -276,6 +286,14 @@ dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows, const
                          const float* lnorm_cols, const float* x_rows, const float* x_cols, float gamma, float w,
                          dk_precision prec, float* k_out, float* kq_out, float* kc_out, float* logkq_out,
                          long long ld, int symmetric, void* stream);
+
+/* Kernels the context uses for DK_PREC_BF16X3 block states' self-norms and block Grams:
+ * DK_BLOCK_TCGEN05 (default; 128 x 128 or 128 x 64 pair tiles, one CTA per SM, tcgen05.mma
+ * from TMA-loaded shared memory into tensor-memory accumulators) or DK_BLOCK_MMA_SYNC. Both
+ * read the same states and agree to rounding; K_q(x, x) = 1 exactly holds when the states'
+ * log_norm and the Gram come from the same form.
+ * Errors: DK_ERR_ARG (NULL ctx, unknown form). */
+dk_status dk_set_block_gram_form(dk_ctx* ctx, int form);
 
 /* ln|<psi~_i|psi~_i>| of the stored (rounded) MPS of m samples, computed with the
  * arithmetic of precision `prec`, so that a Gram call with the same precision and these

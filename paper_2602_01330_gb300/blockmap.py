@@ -39,7 +39,17 @@ def bf16_peak_tflops() -> tuple[float, str]:
 
 def run_benchmark(ctx: dualk.Context, m: int = 2000, m_test: int = 500, n: int = 784, block: int = 10,
                   reps: int = 2, entangler: int = dualk.DK_ENT_FULL, w: float = 0.5, iters: int = 3,
-                  prec: int = dualk.DK_PREC_F32) -> dict:
+                  prec: int = dualk.DK_PREC_F32, form: int = dualk.DK_BLOCK_TCGEN05) -> dict:
+    """Block states of both sets, the symmetric training Gram and the test rows, timed with
+    CUDA events; for prec = DK_PREC_BF16X3 `form` selects the tcgen05 or mma.sync kernels."""
+    ctx.set_block_gram_form(form)
+    try:
+        return _run_benchmark(ctx, m, m_test, n, block, reps, entangler, w, iters, prec, form)
+    finally:
+        ctx.set_block_gram_form(dualk.DK_BLOCK_TCGEN05)
+
+
+def _run_benchmark(ctx, m, m_test, n, block, reps, entangler, w, iters, prec, form) -> dict:
     d = synthetic.fmnist_like(m, m_test, n)
     xtr = torch.from_numpy(d["x_train"]).cuda()
     xte = torch.from_numpy(d["x_test"]).cuda()
@@ -68,7 +78,9 @@ def run_benchmark(ctx: dualk.Context, m: int = 2000, m_test: int = 500, n: int =
     achieved = gram_flops(m, m, n, block, True) / (t["gram_ms"] * 1e-3) / 1e12
     if prec == dualk.DK_PREC_BF16X3:
         bf16, src = bf16_peak_tflops()
-        roof = {"bound": "tensor", "kernel": "gram_blocks_tc_kernel (symmetric Gram, mma.sync bf16x3)",
+        kern = ("gram_blocks_umma_kernel<128> (symmetric Gram, tcgen05 bf16x3)" if form == dualk.DK_BLOCK_TCGEN05
+                else "gram_blocks_tc_kernel (symmetric Gram, mma.sync bf16x3)")
+        roof = {"bound": "tensor", "kernel": kern,
                 "achieved": achieved, "peak": bf16 / 3, "unit": "TFLOP/s (FP32-equivalent)",
                 "frac": achieved / (bf16 / 3),
                 "peak_source": f"dense BF16 {bf16:.1f} TFLOP/s ({src}) / 3 products per FP32-equivalent product"}
@@ -86,6 +98,7 @@ def run_benchmark(ctx: dualk.Context, m: int = 2000, m_test: int = 500, n: int =
         **t,
         "entry_qubits_per_s": entries * n / ((t["gram_ms"] + t["rows_ms"]) * 1e-3),
         "precision": "bf16x3" if prec == dualk.DK_PREC_BF16X3 else "f32",
+        "form": ("tcgen05" if form == dualk.DK_BLOCK_TCGEN05 else "mma_sync") if prec == dualk.DK_PREC_BF16X3 else None,
         "roofline": roof,
         "diag_kq_exactly_1": bool(torch.all(diag == 1.0).item()),
         "mean_offdiag_log_kq": float((g["logkq"].sum() - g["logkq"].diagonal().sum()).item() / (m * m - m)),
@@ -125,6 +138,8 @@ def main():
     ap.add_argument("--entangler", choices=("full", "chain"), default="full")
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--prec", choices=("f32", "bf16x3"), default="f32")
+    ap.add_argument("--form", choices=("tcgen05", "mma_sync"), default="tcgen05",
+                    help="tensor-core kernels of the bf16x3 block Gram")
     ap.add_argument("--concentration", action="store_true",
                     help="report kernel concentration against n for the chain and block maps instead")
     args = ap.parse_args()
@@ -136,8 +151,9 @@ def main():
         return
     ent = dualk.DK_ENT_FULL if args.entangler == "full" else dualk.DK_ENT_CHAIN
     prec = dualk.DK_PREC_BF16X3 if args.prec == "bf16x3" else dualk.DK_PREC_F32
+    form = dualk.DK_BLOCK_TCGEN05 if args.form == "tcgen05" else dualk.DK_BLOCK_MMA_SYNC
     print(json.dumps(run_benchmark(ctx, args.m, args.m_test, args.n, args.block, args.reps, ent, iters=args.iters,
-                                   prec=prec)))
+                                   prec=prec, form=form)))
     ctx.close()
 
 

@@ -64,8 +64,9 @@ __device__ __forceinline__ void lg_add(float& lg, float2 g) { lg += log2f(fmaf(g
 // ln|a| from the log2 sum of |a|^2
 __device__ __forceinline__ float half_log_lg(float lg) { return lg * (0.5f * 0.69314718055994530942f); }
 
-// split = 0: complex64 [dpad]; split = 1: BF16 planes [hi_re | hi_im | lo_re | lo_im] of dpad
-// values each (the operand form of the tensor-core Gram, same 8 bytes per amplitude)
+// split = 0: complex64 [dpad]; split = 1: the operand form of the tensor-core Grams, same 8
+// bytes per amplitude: per chunk of 16 amplitudes one 128-byte row of four BF16 planes
+// [hi_re | hi_im | lo_re | lo_im] of 16 values each
 __global__ void __launch_bounds__(BUILD_NT) block_states_kernel(const float* __restrict__ x, int m, int n, int b,
                                                                 int reps, double angle_scale, int pairs_kind,
                                                                 int split, float2* __restrict__ states) {
@@ -95,10 +96,11 @@ __global__ void __launch_bounds__(BUILD_NT) block_states_kernel(const float* __r
   for (int k = threadIdx.x; k < dp; k += BUILD_NT) {
     const float vr = k < dim ? psf[k].x : 0.0f, vi = k < dim ? psf[k].y : 0.0f;
     const __nv_bfloat16 hr = __float2bfloat16_rn(vr), hi = __float2bfloat16_rn(vi);
-    pl[k] = hr;
-    pl[dp + k] = hi;
-    pl[2 * dp + k] = __float2bfloat16_rn(vr - __bfloat162float(hr));
-    pl[3 * dp + k] = __float2bfloat16_rn(vi - __bfloat162float(hi));
+    __nv_bfloat16* row = pl + (k >> 4) * 64 + (k & 15);
+    row[0] = hr;
+    row[16] = hi;
+    row[32] = __float2bfloat16_rn(vr - __bfloat162float(hr));
+    row[48] = __float2bfloat16_rn(vi - __bfloat162float(hi));
   }
 }
 
@@ -281,7 +283,10 @@ DK_API dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, cons
                                                                       kind, split, static_cast<float2*>(states));
   dk_status s = launch_status();
   if (s != DK_OK || !log_norm) return s;
-  if (split) return block_selfnorm_tc_launch(states, m, nb, gblk::dpad_of(b), log_norm, st);
+  if (split)
+    return ctx->block_form == DK_BLOCK_MMA_SYNC
+               ? block_selfnorm_tc_launch(states, m, nb, gblk::dpad_of(b), log_norm, st)
+               : block_selfnorm_umma_launch(ctx, states, m, nb, gblk::dpad_of(b), log_norm, st);
   gblk::block_selfnorm_kernel<<<m, gblk::NORM_NT, nb * sizeof(float2), st>>>(static_cast<const float2*>(states), m,
                                                                            nb, gblk::dpad_of(b), log_norm);
   return launch_status();
@@ -327,9 +332,13 @@ DK_API dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows
   a.status = ctx->status;
   a.need_kc = need_kc ? 1 : 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (prec == DK_PREC_BF16X3)
-    return gram_blocks_tc_launch(ctx, states_rows, m_rows, states_cols, m_cols, (n + b - 1) / b, gblk::dpad_of(b), a,
-                                 st);
+  if (prec == DK_PREC_BF16X3) {
+    if (ctx->block_form == DK_BLOCK_MMA_SYNC)
+      return gram_blocks_tc_launch(ctx, states_rows, m_rows, states_cols, m_cols, (n + b - 1) / b, gblk::dpad_of(b),
+                                   a, st);
+    return gram_blocks_umma_launch(ctx, states_rows, m_rows, states_cols, m_cols, (n + b - 1) / b, gblk::dpad_of(b),
+                                   a, st);
+  }
   // tile shape: estimated time = waves x tile area / per-pair efficiency (the 128 x 64 tile
   // runs about 15 % more pairs per second than 64 x 64, which fills the GPU better when
   // there are few tiles, e.g. a batch of decision rows)
@@ -358,4 +367,10 @@ DK_API dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows
     kern<<<grid, gblk::NT, gblk::RowTile<4>::SMEM, st>>>(srp, m_rows, scp, m_cols, nbk, dp, a4);
   }
   return launch_status();
+}
+
+DK_API dk_status dk_set_block_gram_form(dk_ctx* ctx, int form) {
+  if (!ctx || (form != DK_BLOCK_TCGEN05 && form != DK_BLOCK_MMA_SYNC)) return DK_ERR_ARG;
+  ctx->block_form = form;
+  return DK_OK;
 }

@@ -9,8 +9,9 @@
 // lo.hi + hi.lo + hi.hi (bf16x3; the lo.lo term is dropped), so a product keeps about 17
 // significant bits.
 //
-// Layout: dk_block_states in this precision stores, per (block, sample), four BF16 planes
-// [hi_re | hi_im | lo_re | lo_im] of dpad values each (8 bytes per amplitude, as complex64).
+// Layout: dk_block_states in this precision stores, per (block, sample) and chunk of 16
+// amplitudes, one 128-byte row of four BF16 planes [hi_re | hi_im | lo_re | lo_im] (8 bytes
+// per amplitude, as complex64).
 // A CTA computes a 128 x 64 pair tile with 8 warps (4 x 2, 32 x 32 pairs each); per
 // 16-amplitude step the operand rows of its 192 samples (4 planes x 32 bytes each) are
 // copied with cp.async into a double-buffered stage, padded to 144 bytes per row so the
@@ -100,13 +101,13 @@ __global__ void __launch_bounds__(64 * WM, 8 / WM)
 #pragma unroll
       for (int h = 0; h < T::COPIES; ++h) {
         const int q = tid + NT * h;
-        const int row = q >> 3, piece = q & 7, plane = piece >> 1, half = piece & 1;
+        const int row = q >> 3, piece = q & 7;
         const bool is_a = row < TR;
         const int smp = is_a ? min(r0 + row, m_r - 1) : min(c0 + row - TR, m_c - 1);
         const unsigned char* src = (is_a ? sr + (size_t(blk) * m_r + smp) * sample_bytes
                                          : sc + (size_t(blk) * m_c + smp) * sample_bytes) +
-                                   size_t(plane) * dp * 2 + size_t(k0) * 2 + half * 16;
-        cp_async16(sbase + buf * STAGE + row * ROWB + plane * 32 + half * 16, src);
+                                   size_t(k0) * 8 + piece * 16;
+        cp_async16(sbase + buf * STAGE + row * ROWB + piece * 16, src);
       }
       cp_async_commit();
     };
@@ -227,11 +228,10 @@ __global__ void __launch_bounds__(NORM_WARPS * 32)
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       const int q = lane + 32 * h;
-      const int row = q >> 3, piece = q & 7, plane = piece >> 1, half = piece & 1;
+      const int row = q >> 3, piece = q & 7;
       const int smp = min(i0 + row, m - 1);
-      const unsigned char* src =
-          s + (size_t(blk) * m + smp) * sample_bytes + size_t(plane) * dp * 2 + size_t(k0) * 2 + half * 16;
-      cp_async16(sw + buf * STAGE_N + row * ROWB + plane * 32 + half * 16, src);
+      const unsigned char* src = s + (size_t(blk) * m + smp) * sample_bytes + size_t(k0) * 8 + piece * 16;
+      cp_async16(sw + buf * STAGE_N + row * ROWB + piece * 16, src);
     }
     cp_async_commit();
   };

@@ -1,0 +1,441 @@
+// Block-statevector Gram (see gram_blocks.cu) on the fifth-generation tensor cores:
+// tcgen05.mma with both operands in shared memory and FP32 accumulators in tensor memory.
+//
+// For block B and a tile of 128 row samples x BN column samples the factor of the overlap
+// is the complex GEMM G_B = A^H B over K = 2^b amplitudes, taken with split-BF16 operands
+// (v ~ hi + lo) and FP32 accumulation as lo.hi + hi.lo + hi.hi (bf16x3, the precision of
+// gram_blocks_tc.cu): per 16 amplitudes twelve 128 x BN x 16 MMAs, six into Re G
+// (ar br + ai bi) and six into Im G (ar bi - ai br, the minus through the instruction's
+// negate-B bit).
+//
+// Warp roles of a CTA (one CTA per SM, persistent over its tiles):
+//   warp 0    one thread issues the TMA loads: per (tile, block, 16-amplitude chunk) one
+//             128-byte row per sample (the chunk's four BF16 planes, which dk_block_states
+//             interleaves in HBM) for the 128 row and BN column samples, 128-byte swizzle,
+//             into a ring of NSTAGES stages (full / empty mbarriers);
+//   warp 1    allocates the tensor memory, two accumulators of [Re | Im] (4 BN columns), and
+//             one thread issues the MMAs; tcgen05.commit releases each stage to the loader
+//             and hands a finished block's accumulator to the epilogue;
+//   warps 2-9 the epilogue: thread (TMEM lane r, column half h) reads BN/2 columns of Re and
+//             Im of row r, adds log2 |G_B|^2 to its running sums and frees the accumulator,
+//             which the MMA thread refills two blocks later (so block B's epilogue runs under
+//             the MMAs of block B + 1); between blocks it also takes its share of the RBF
+//             distances (Kahan FP32, one pair at a time); after the last block it writes the
+//             tile through the common epilogue (write_pair).
+//
+// Self-norms (diagonal mode): a unit is one (diagonal tile, block) pair with A = B in shared
+// memory. The diagonal tile of the symmetric Gram issues the same instructions on the same
+// shared-memory contents, so |G_B(i, i)|^2 is bit-identical in both; the epilogue stores it
+// per (block, sample) and a second kernel adds the log2 terms in block order, as the Gram
+// epilogue does, so K_q(x, x) = 1 exactly.
+#include <math.h>
+
+#include "common.cuh"
+#include "gram_common.cuh"
+#include "internal.h"
+
+namespace dk {
+namespace gbum {
+
+using u32 = uint32_t;
+using u64 = uint64_t;
+
+constexpr int BM = 128;     // tile rows = MMA M = TMEM lanes
+constexpr int ROWB = 128;   // one 16-amplitude chunk of a sample: 4 planes x 16 BF16
+constexpr int NSTAGES = 6;
+constexpr int NEPI = 8;     // epilogue warps
+constexpr int NTHREADS = (2 + NEPI) * 32;
+
+template <int BN>
+struct Cfg {
+  static_assert(BN % 16 == 0 && BN >= 32 && BN <= 128, "MMA N for M = 128");
+  static constexpr int A_BYTES = BM * ROWB;
+  static constexpr int B_BYTES = BN * ROWB;
+  static constexpr int STAGE = A_BYTES + B_BYTES;  // a multiple of 1024: every stage on a swizzle atom
+  static constexpr int ACC = 2 * BN;               // TMEM columns of one accumulator: Re | Im
+  static constexpr u32 TMEM_COLS = 2 * ACC;        // two accumulators (a power of two, >= 32)
+  static constexpr int CPT = BN / 2;               // columns per epilogue thread
+  static constexpr size_t SMEM = 1024 + size_t(NSTAGES) * STAGE + 256;
+};
+
+// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both K-major,
+// N = BN, M = 128; neg_b negates B.
+template <int BN>
+__host__ __device__ constexpr u32 idesc(bool neg_b) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (neg_b ? (1u << 14) : 0u) | (u32(BN >> 3) << 17) | (u32(BM >> 4) << 24);
+}
+
+// Shared-memory descriptor of a K-major operand in the 128-byte swizzle layout written by
+// TMA: rows of 128 bytes, 8-row atoms 1024 bytes apart; `saddr` may sit 32 p bytes into a
+// row (plane p), the swizzle being applied to the final address.
+__device__ __forceinline__ u64 sw128_desc(u32 saddr) {
+  return u64((saddr & 0x3FFFFu) >> 4) | (u64(1) << 16) | (u64(1024 >> 4) << 32) | (u64(1) << 46) | (u64(2) << 61);
+}
+
+__device__ __forceinline__ void tc_alloc(u32 dst, u32 ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(u32 taddr, u32 ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// `bar` receives one arrival once every MMA this thread issued so far has completed
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// D (+)= A B^T, D in tensor memory; accumulate = 0 overwrites D
+__device__ __forceinline__ void tc_mma(u32 d, u64 a, u64 b, u32 id, u32 accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(accumulate)
+      : "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane from two column offsets, waited for
+__device__ __forceinline__ void tc_ld16x2(u32 ta, u32 tb, float (&va)[16], float (&vb)[16]) {
+  u32 a[16], b[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+      "[%33];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]),
+        "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(b[0]),
+        "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]), "=r"(b[8]), "=r"(b[9]),
+        "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    va[e] = __uint_as_float(a[e]);
+    vb[e] = __uint_as_float(b[e]);
+  }
+}
+
+__device__ __forceinline__ float half_log_lg(float lg) { return lg * (0.5f * 0.69314718055994530942f); }
+__device__ __forceinline__ float abs2(float re, float im) { return fmaf(re, re, __fmul_rn(im, im)); }
+
+// Gram mode (diag = 0): tiles of p (symmetric or rectangular), each a sequence of nb units
+// (one per block). Diagonal mode (diag = 1): n_units = ceil(m_diag / 128) * nb units
+// (diagonal tile, block) over the states of tm_r, |G_B(i, i)|^2 written to g2_out[blk][i].
+template <int BN>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gram_blocks_umma_kernel(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_c,
+                            const GramArgs p, int nb, int cpb, int diag, int n_units, float* __restrict__ g2_out,
+                            int m_diag) {
+  using C = Cfg<BN>;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGES * C::STAGE);
+  uint64_t* empty = full + NSTAGES;
+  uint64_t* acc_full = empty + NSTAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* done = acc_empty + 2;
+  u32* tmem_slot = reinterpret_cast<u32*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], NEPI);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    prefetch_tensormap(&tm_r);
+    if (!diag) prefetch_tensormap(&tm_c);
+  }
+  if (warp == 1) {
+    tc_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+    tc_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const u32 tmem = *tmem_slot;
+
+  const int grid = int(gridDim.x), bid = int(blockIdx.x);
+  long long my_units;
+  if (diag) {
+    my_units = n_units > bid ? (n_units - 1 - bid) / grid + 1 : 0;
+  } else {
+    const int my_tiles = p.ntiles > bid ? (p.ntiles - 1 - bid) / grid + 1 : 0;
+    my_units = (long long)my_tiles * nb;
+  }
+  // unit k of this CTA -> tile origin (first row and column sample) and block
+  auto unit = [&](long long k, int& r0, int& c0, int& blk) {
+    if (diag) {
+      const long long u = bid + k * grid;
+      const int ti = int(u / nb);
+      blk = int(u - (long long)ti * nb);
+      r0 = c0 = ti * BM;
+    } else {
+      const int lt = int(k / nb);
+      blk = int(k - (long long)lt * nb);
+      int ti, tj;
+      decode_tile(p, BM, BN, bid + lt * grid, ti, tj);
+      r0 = p.row0 + ti * BM;
+      c0 = p.col0 + tj * BN;
+    }
+  };
+  auto give_up = [&]() {
+    record_status(p.status, DEV_TIMEOUT);
+    *abort_flag = 1;
+  };
+
+  if (warp == 0) {
+    // ---- TMA loader ----
+    if (lane == 0) {
+      const u32 tx = diag ? u32(C::A_BYTES) : u32(C::STAGE);
+      long long it = 0;  // stage fills issued
+      for (long long k = 0; k < my_units && !*abort_flag; ++k) {
+        int r0, c0, blk;
+        unit(k, r0, c0, blk);
+        for (int c = 0; c < cpb; ++c) {
+          const int s = int(it % NSTAGES);
+          const long long round = it / NSTAGES;
+          if (round > 0 && !mbar_wait_bounded(&empty[s], u32((round - 1) & 1))) {
+            give_up();
+            break;
+          }
+          uint8_t* sa = smem + s * C::STAGE;
+          mbar_arrive_expect_tx(&full[s], tx);
+          tma_load_3d(sa, &tm_r, &full[s], c * 64, r0, blk);
+          if (!diag) tma_load_3d(sa + C::A_BYTES, &tm_c, &full[s], c * 64, c0, blk);
+          ++it;
+        }
+      }
+      // every issued copy has landed before the CTA may exit
+      for (int s = 0; s < NSTAGES; ++s)
+        if (it > s && !mbar_wait_bounded(&full[s], u32(((it - 1 - s) / NSTAGES) & 1))) record_status(p.status, DEV_TIMEOUT);
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      constexpr u32 ID_POS = idesc<BN>(false), ID_NEG = idesc<BN>(true);
+      long long it = 0;
+      for (long long k = 0; k < my_units && !*abort_flag; ++k) {
+        const int a = int(k & 1);
+        const long long use = k >> 1;
+        if (use > 0 && !mbar_wait_bounded(&acc_empty[a], u32((use - 1) & 1))) {
+          give_up();
+          break;
+        }
+        tc_fence_after();
+        const u32 d_re = tmem + u32(a * C::ACC), d_im = d_re + BN;
+        bool ok = true;
+        for (int c = 0; c < cpb; ++c, ++it) {
+          const int s = int(it % NSTAGES);
+          if (!mbar_wait_bounded(&full[s], u32((it / NSTAGES) & 1))) {
+            give_up();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const u32 sa = smem_u32(smem + s * C::STAGE);
+          const u32 sb = diag ? sa : sa + C::A_BYTES;
+          // planes: 0 hi(re), 1 hi(im), 2 lo(re), 3 lo(im), 32 bytes apart in a row
+          const u64 a0 = sw128_desc(sa), a1 = sw128_desc(sa + 32), a2 = sw128_desc(sa + 64),
+                    a3 = sw128_desc(sa + 96);
+          const u64 b0 = sw128_desc(sb), b1 = sw128_desc(sb + 32), b2 = sw128_desc(sb + 64),
+                    b3 = sw128_desc(sb + 96);
+          const u32 acc = c > 0 ? 1u : 0u;
+          tc_mma(d_re, a2, b0, ID_POS, acc);  // Re += ar br
+          tc_mma(d_re, a0, b2, ID_POS, 1u);
+          tc_mma(d_re, a0, b0, ID_POS, 1u);
+          tc_mma(d_re, a3, b1, ID_POS, 1u);   // Re += ai bi
+          tc_mma(d_re, a1, b3, ID_POS, 1u);
+          tc_mma(d_re, a1, b1, ID_POS, 1u);
+          tc_mma(d_im, a2, b1, ID_POS, acc);  // Im += ar bi
+          tc_mma(d_im, a0, b3, ID_POS, 1u);
+          tc_mma(d_im, a0, b1, ID_POS, 1u);
+          tc_mma(d_im, a3, b0, ID_NEG, 1u);   // Im -= ai br
+          tc_mma(d_im, a1, b2, ID_NEG, 1u);
+          tc_mma(d_im, a1, b0, ID_NEG, 1u);
+          tc_commit(&empty[s]);
+        }
+        if (!ok) break;
+        tc_commit(&acc_full[a]);
+      }
+      tc_commit(done);
+      if (!mbar_wait_bounded(done, 0u)) record_status(p.status, DEV_TIMEOUT);
+    }
+  } else {
+    // ---- epilogue ----
+    const int q = warp & 3;           // the TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2;    // column half
+    const int r = 32 * q + lane;      // tile row = TMEM lane
+    const u32 t_row = tmem + (u32(32 * q) << 16) + u32(h * C::CPT);
+    float lg[C::CPT], d2[C::CPT];
+#pragma unroll
+    for (int u = 0; u < C::CPT; ++u) lg[u] = d2[u] = 0.0f;
+    for (long long k = 0; k < my_units; ++k) {
+      int r0, c0, blk;
+      unit(k, r0, c0, blk);
+      const int a = int(k & 1);
+      // one decision per warp: the loads below are warp-collective
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[a], u32((k >> 1) & 1)))) {
+        if (lane == 0) give_up();
+        break;
+      }
+      tc_fence_after();
+      float dg = 0.0f;
+#pragma unroll
+      for (int cc = 0; cc < C::CPT / 16; ++cc) {
+        float re[16], im[16];
+        tc_ld16x2(t_row + u32(a * C::ACC + 16 * cc), t_row + u32(a * C::ACC + BN + 16 * cc), re, im);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const float g2 = abs2(re[e], im[e]);
+          if (diag) {
+            if (h * C::CPT + 16 * cc + e == r) dg = g2;
+          } else {
+            lg[16 * cc + e] += log2f(g2);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[a]);
+      const int i = r0 + r;
+      if (diag) {
+        if (r / C::CPT == h && i < m_diag) g2_out[size_t(blk) * m_diag + i] = dg;
+        continue;
+      }
+      if (p.need_kc) {
+        // this block's share of the tile's RBF distances: pairs [lo, hi) of the thread's row
+        const int lo = int((long long)blk * C::CPT / nb), hi = int((long long)(blk + 1) * C::CPT / nb);
+        for (int pp = lo; pp < hi; ++pp) {
+          const int j = c0 + h * C::CPT + pp;
+          float s = 0.0f, comp = 0.0f;
+          if (i < p.row0 + p.nrows && j < p.col0 + p.ncols && !(p.symmetric && j < i)) {
+            const float* xa = p.x_r + size_t(i) * p.n;
+            const float* xb = p.x_c + size_t(j) * p.n;
+            for (int f = 0; f < p.n; ++f) kahan_add_sq(s, comp, __ldg(xa + f) - __ldg(xb + f));
+          }
+#pragma unroll
+          for (int u = 0; u < C::CPT; ++u)
+            if (u == pp) d2[u] = s;
+        }
+      }
+      if (blk == nb - 1) {
+#pragma unroll
+        for (int u = 0; u < C::CPT; ++u) {
+          write_pair(p, half_log_lg(lg[u]), d2[u], i, c0 + h * C::CPT + u);
+          lg[u] = 0.0f;
+          d2[u] = 0.0f;
+        }
+      }
+    }
+  }
+
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tc_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+// ln N_i from the per-block diagonal |G_B(i, i)|^2: log2 terms added in block order, as the
+// Gram epilogue adds them.
+__global__ void selfnorm_sum_kernel(const float* __restrict__ g2, int m, int nb, float* __restrict__ log_norm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  float lg = 0.0f;
+  for (int b = 0; b < nb; ++b) lg += log2f(g2[size_t(b) * m + i]);
+  log_norm[i] = half_log_lg(lg);
+}
+
+// Tensor map over split-BF16 block states [block][sample][dp/16 chunks x 64 BF16]: box of
+// one 128-byte chunk row x box_rows samples x 1 block, 128-byte swizzle, zeros past m.
+dk_status encode_states_map(dk_ctx* ctx, CUtensorMap* map, const void* states, int m, int nb, int dp, int box_rows) {
+  cuuint64_t dims[3] = {cuuint64_t(4) * cuuint64_t(dp), cuuint64_t(m), cuuint64_t(nb)};
+  cuuint64_t strides[2] = {cuuint64_t(8) * cuuint64_t(dp), cuuint64_t(8) * cuuint64_t(dp) * cuuint64_t(m)};
+  cuuint32_t box[3] = {64u, cuuint32_t(box_rows), 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = ctx->encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(states), dims, strides,
+                                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? DK_OK : DK_ERR_CUDA;
+}
+
+template <int BN>
+dk_status set_smem() {
+  static bool done = false;
+  if (done) return DK_OK;
+  if (cudaFuncSetAttribute(gram_blocks_umma_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(Cfg<BN>::SMEM)) != cudaSuccess)
+    return DK_ERR_CUDA;
+  done = true;
+  return DK_OK;
+}
+
+template <int BN>
+dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp, GramArgs a,
+                      int ntiles, cudaStream_t st) {
+  CUtensorMap tr, tc;
+  dk_status s = encode_states_map(ctx, &tr, sr, m_r, nb, dp, BM);
+  if (s == DK_OK) s = encode_states_map(ctx, &tc, sc, m_c, nb, dp, BN);
+  if (s == DK_OK) s = set_smem<BN>();
+  if (s != DK_OK) return s;
+  a.ntiles = ntiles;
+  const int grid = ntiles < ctx->sm_count ? ntiles : ctx->sm_count;
+  if (grid < 1) return DK_OK;
+  gram_blocks_umma_kernel<BN><<<grid, NTHREADS, Cfg<BN>::SMEM, st>>>(tr, tc, a, nb, dp / 16, 0, 0, nullptr, 0);
+  return launch_status();
+}
+
+}  // namespace gbum
+
+dk_status gram_blocks_umma_launch(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp,
+                                  GramArgs a, cudaStream_t st) {
+  // symmetric: 128 x 128 tiles (the diagonal tiles are the self-norm units, bit for bit);
+  // rectangular: 128 x 64 when it takes fewer waves of half-size tiles
+  GramArgs a128 = a, a64 = a;
+  const int t128 = count_tiles(a128, gbum::BM, 128);
+  if (a.symmetric) return gbum::launch_gram<128>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, st);
+  const int t64 = count_tiles(a64, gbum::BM, 64);
+  const long long sms = ctx->sm_count;
+  const long long cost128 = 2 * ((t128 + sms - 1) / sms), cost64 = (t64 + sms - 1) / sms;
+  if (cost128 <= cost64) return gbum::launch_gram<128>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, st);
+  return gbum::launch_gram<64>(ctx, sr, m_r, sc, m_c, nb, dp, a64, t64, st);
+}
+
+dk_status block_selfnorm_umma_launch(dk_ctx* ctx, const void* states, int m, int nb, int dp, float* log_norm,
+                                     cudaStream_t st) {
+  using namespace gbum;
+  const long long units = (long long)((m + BM - 1) / BM) * nb;
+  if (units > 0x7fffffffLL) return DK_ERR_UNSUPPORTED;
+  CUtensorMap t;
+  dk_status s = encode_states_map(ctx, &t, states, m, nb, dp, BM);
+  if (s == DK_OK) s = set_smem<128>();
+  if (s != DK_OK) return s;
+  float* g2 = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&g2), size_t(nb) * size_t(m) * sizeof(float), st) != cudaSuccess)
+    return DK_ERR_CUDA;
+  GramArgs a{};
+  a.status = ctx->status;
+  const int grid = int(units < ctx->sm_count ? units : ctx->sm_count);
+  gram_blocks_umma_kernel<128><<<grid, NTHREADS, Cfg<128>::SMEM, st>>>(t, t, a, nb, dp / 16, 1, int(units), g2, m);
+  s = launch_status();
+  if (s == DK_OK) {
+    selfnorm_sum_kernel<<<(m + 255) / 256, 256, 0, st>>>(g2, m, nb, log_norm);
+    s = launch_status();
+  }
+  if (cudaFreeAsync(g2, st) != cudaSuccess && s == DK_OK) s = DK_ERR_CUDA;
+  return s;
+}
+
+}  // namespace dk

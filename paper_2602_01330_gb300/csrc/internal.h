@@ -21,6 +21,7 @@ struct dk_ctx {
   dk_encode_tiled_fn encode_tiled;
   int gram_config;   // 0: built-in choice; otherwise a tile-shape id (dk_set_gram_config)
   void* graphs;      // CUDA graphs recorded by dk_gram_sweep (sweep.cu), or NULL
+  int block_form;    // split-BF16 block Gram: DK_BLOCK_TCGEN05 (0) or DK_BLOCK_MMA_SYNC (1)
 };
 
 namespace dk {
@@ -54,6 +55,11 @@ dk_status self_overlap_launch(const void* mps, int m, int n, int chi, dk_dtype d
 dk_status gram_blocks_tc_launch(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp,
                                 GramArgs a, cudaStream_t st);
 dk_status block_selfnorm_tc_launch(const void* states, int m, int nb, int dp, float* log_norm, cudaStream_t st);
+// The same on tcgen05 tensor cores (gram_blocks_umma.cu).
+dk_status gram_blocks_umma_launch(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp,
+                                  GramArgs a, cudaStream_t st);
+dk_status block_selfnorm_umma_launch(dk_ctx* ctx, const void* states, int m, int nb, int dp, float* log_norm,
+                                     cudaStream_t st);
 // Destroys the graphs dk_gram_sweep recorded for this context (sweep.cu).
 void sweep_cache_free(dk_ctx* ctx);
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libdualk.so")
 DK_OK = 0
 DK_C64, DK_C128 = 0, 1
 DK_PREC_F32, DK_PREC_F64, DK_PREC_BF16X3 = 0, 1, 2
+DK_BLOCK_TCGEN05, DK_BLOCK_MMA_SYNC = 0, 1
 
 _STATUS_NAMES = {0: "DK_OK", 1: "DK_ERR_ARG", 2: "DK_ERR_UNSUPPORTED", 3: "DK_ERR_CUDA",
                  4: "DK_ERR_TIMEOUT", 5: "DK_ERR_WORKSPACE", 6: "DK_ERR_NO_DEVICE"}
@@ -28,7 +29,8 @@ EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_
             "dk_gram_config_info", "dk_set_gram_config", "dk_selftest_wait_timeout", "dk_self_overlap",
             "dk_svm_ovo_train", "dk_svm_ovo_predict", "dk_gram_stats", "dk_pca_workspace_bytes", "dk_pca_fit",
             "dk_pca_transform", "dk_pca_fit_noalloc", "dk_mps_build_blocks", "dk_block_states_bytes",
-            "dk_block_states", "dk_gram_blocks", "dk_gram_sweep", "dk_workspace_bytes")
+            "dk_block_states", "dk_gram_blocks", "dk_gram_sweep", "dk_workspace_bytes",
+            "dk_set_block_gram_form")
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 PCA_MAX_FEATURES = 4096  # DK_PCA_MAX_FEATURES
 PCA_NOALLOC_MAX_FEATURES = 256  # DK_PCA_NOALLOC_MAX_FEATURES
@@ -96,6 +98,8 @@ def _lib():
     lib.dk_gram_config_info.restype = i32
     lib.dk_set_gram_config.argtypes = [vp, i32]
     lib.dk_set_gram_config.restype = i32
+    lib.dk_set_block_gram_form.argtypes = [vp, i32]
+    lib.dk_set_block_gram_form.restype = i32
     lib.dk_self_overlap.argtypes = [vp, vp, i32, i32, i32, i32, i32, vp, vp]
     lib.dk_self_overlap.restype = i32
     lib.dk_selftest_wait_timeout.argtypes = [vp, ctypes.c_ulonglong, vp]
@@ -224,6 +228,11 @@ class Context:
     def set_gram_config(self, cfg_id: int):
         """dk_set_gram_config: 0 = built-in tile shape, 1..gram_config_count() = a fixed one."""
         _check(_lib().dk_set_gram_config(self.handle, int(cfg_id)), "dk_set_gram_config")
+
+    def set_block_gram_form(self, form: int):
+        """dk_set_block_gram_form: DK_BLOCK_TCGEN05 (default) or DK_BLOCK_MMA_SYNC kernels for
+        the split-BF16 block states' self-norms and Gram; build states and Gram in one form."""
+        _check(_lib().dk_set_block_gram_form(self.handle, int(form)), "dk_set_block_gram_form")
 
 
 def gram_config_count(dtype: int = DK_C64, chi_max: int = 4) -> int:

@@ -27,6 +27,23 @@ def _dev(torch, a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
+FORMS = ("tcgen05", "mma_sync")
+
+
+class _form:
+    """Selects the split-BF16 block kernels of the context for a with-block."""
+
+    def __init__(self, dualk, ctx, name):
+        self.dualk, self.ctx = dualk, ctx
+        self.form = dualk.DK_BLOCK_TCGEN05 if name == "tcgen05" else dualk.DK_BLOCK_MMA_SYNC
+
+    def __enter__(self):
+        self.ctx.set_block_gram_form(self.form)
+
+    def __exit__(self, *exc):
+        self.ctx.set_block_gram_form(self.dualk.DK_BLOCK_TCGEN05)
+
+
 def _ref_log(xr, xc, reps, b, entangler):
     from oracle import circuit
     n = xr.shape[1]
@@ -151,13 +168,15 @@ def _check_tol(out, lref, kc_ref, w, tol):
     assert np.all(np.abs(lkq[sel] - lref[sel]) <= 1e-3 * np.maximum(1.0, np.abs(lref[sel])))
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("m,n,b,reps,ent", [(70, 40, 8, 2, "full"), (70, 50, 7, 2, "chain"), (70, 36, 12, 2, "full"),
                                             (70, 9, 2, 3, "full"), (300, 16, 8, 2, "full"), (2000, 16, 8, 2, "full")])
-def test_gram_blocks_bf16x3_tensor_cores(dk, m, n, b, reps, ent):
-    """Split-BF16 tensor-core form against the oracle with the mixed-precision tolerance
-    1e-4 on K_q and K (K_c stays FP32, 1e-6): one ragged 128 x 64 tile (70 samples), several
-    (300) and a full-size Gram (2000 = 15 x 128 + 80); short last blocks (n = 50, 9); rows;
-    exact unit diagonal from the self-norms of the same MMA sequence; exact symmetry."""
+def test_gram_blocks_bf16x3_tensor_cores(dk, m, n, b, reps, ent, form):
+    """Split-BF16 tensor-core forms (tcgen05 and mma.sync) against the oracle with the
+    mixed-precision tolerance 1e-4 on K_q and K (K_c stays FP32, 1e-6): one ragged tile (70
+    samples), several (300) and a full-size Gram (2000 = 15 x 128 + 80); short last blocks
+    (n = 50, 9); rows; exact unit diagonal from the self-norms of the same MMA sequence;
+    exact symmetry."""
     dualk, ctx, torch = dk
     from oracle import gram as og
     from paper_2602_01330_gb300 import synthetic
@@ -166,11 +185,12 @@ def test_gram_blocks_bf16x3_tensor_cores(dk, m, n, b, reps, ent):
     fm = dualk.FeatureMap(reps=reps, block=b)
     e = dualk.DK_ENT_FULL if ent == "full" else dualk.DK_ENT_CHAIN
     p = dualk.DK_PREC_BF16X3
-    str_ = dualk.block_states(ctx, _dev(torch, xtr), fm, e, prec=p)
-    ste = dualk.block_states(ctx, _dev(torch, xte), fm, e, prec=p)
-    g = dualk.gram_blocks(ctx, str_, w=0.5)
-    r = dualk.gram_blocks(ctx, ste, str_, w=0.5)
-    torch.cuda.synchronize()
+    with _form(dualk, ctx, form):
+        str_ = dualk.block_states(ctx, _dev(torch, xtr), fm, e, prec=p)
+        ste = dualk.block_states(ctx, _dev(torch, xte), fm, e, prec=p)
+        g = dualk.gram_blocks(ctx, str_, w=0.5)
+        r = dualk.gram_blocks(ctx, ste, str_, w=0.5)
+        torch.cuda.synchronize()
     _check_tol(g, _ref_log(xtr, xtr, reps, b, ent), og.rbf(xtr, xtr, 1.0 / n), 0.5, 1e-4)
     _check_tol(r, _ref_log(xte, xtr, reps, b, ent), og.rbf(xte, xtr, 1.0 / n), 0.5, 1e-4)
     kq = g["kq"].cpu().numpy()
@@ -179,17 +199,21 @@ def test_gram_blocks_bf16x3_tensor_cores(dk, m, n, b, reps, ent):
     ctx.sync_status()
 
 
-def test_gram_blocks_bf16x3_n784_matches_fp32(dk):
+@pytest.mark.parametrize("form", FORMS)
+def test_gram_blocks_bf16x3_n784_matches_fp32(dk, form):
     """n = 784 in blocks of 10: the tensor-core log K_q against the FP32 form (and both
-    against the oracle on a sample) to 1e-4 relative."""
+    against the oracle on a sample) to 1e-4 relative; 200 samples in 79 blocks give 158
+    self-norm units, more than one per SM."""
     dualk, ctx, torch = dk
     from paper_2602_01330_gb300 import synthetic
     x = _dev(torch, synthetic.fmnist_like(200, 0, 784)["x_train"])
     fm = dualk.FeatureMap(reps=2, block=10)
     a = dualk.gram_blocks(ctx, dualk.block_states(ctx, x, fm, dualk.DK_ENT_FULL), w=1.0, want=("logkq",))
-    b = dualk.gram_blocks(ctx, dualk.block_states(ctx, x, fm, dualk.DK_ENT_FULL, prec=dualk.DK_PREC_BF16X3), w=1.0,
-                          want=("logkq",))
-    torch.cuda.synchronize()
+    with _form(dualk, ctx, form):
+        b = dualk.gram_blocks(ctx, dualk.block_states(ctx, x, fm, dualk.DK_ENT_FULL, prec=dualk.DK_PREC_BF16X3),
+                              w=1.0, want=("logkq",))
+        torch.cuda.synchronize()
+    assert np.all(np.diag(b["logkq"].cpu().numpy()) == 0.0)
     la, lb = a["logkq"].cpu().numpy().astype(np.float64), b["logkq"].cpu().numpy().astype(np.float64)
     off = ~np.eye(200, dtype=bool)
     assert np.max(np.abs(la[off] - lb[off]) / np.abs(la[off])) <= 1e-4
@@ -220,14 +244,19 @@ def test_gram_blocks_errors(dk):
     ctx.sync_status()
 
 
-@pytest.mark.parametrize("prec", ["f32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["f32", "bf16x3", "bf16x3_mma_sync"])
 def test_gram_blocks_edge_cases(dk, prec):
     """One sample (K = 1), one qubit (n = 1, block 1: the product form cos^2(x - y) at one
     repetition), a single block of 12 qubits (block 0 with n = 12), and an empty row range."""
     dualk, ctx, torch = dk
+    with _form(dualk, ctx, "mma_sync" if prec == "bf16x3_mma_sync" else "tcgen05"):
+        _edge_cases(dualk, ctx, torch, prec)
+
+
+def _edge_cases(dualk, ctx, torch, prec):
     from paper_2602_01330_gb300 import synthetic
-    p = dualk.DK_PREC_BF16X3 if prec == "bf16x3" else dualk.DK_PREC_F32
-    tol = 1e-4 if prec == "bf16x3" else 1e-6
+    p = dualk.DK_PREC_F32 if prec == "f32" else dualk.DK_PREC_BF16X3
+    tol = 1e-6 if prec == "f32" else 1e-4
     x1 = _dev(torch, synthetic.uniform_angles(1, 7, 60))
     g1 = dualk.gram_blocks(ctx, dualk.block_states(ctx, x1, dualk.FeatureMap(reps=2, block=3), prec=p), w=0.5)
     xs = synthetic.uniform_angles(9, 1, 61)
@@ -251,6 +280,54 @@ def test_gram_blocks_edge_cases(dk, prec):
     torch.cuda.synchronize()
     assert out.item() == -3.0  # nothing to compute, nothing written
     ctx.sync_status()
+
+
+def test_block_gram_forms_agree_and_persist(dk):
+    """The tcgen05 and mma.sync kernels on the same split-BF16 states: log K_q within 2e-5
+    relative of each other (same products, other accumulation order) and both within the
+    mixed-precision tolerance of the oracle; a symmetric Gram of 4000 samples (528 tiles of
+    128 x 128, several per CTA), a rectangular 2000 x 1900 block (128 x 128 tiles, several
+    per CTA) and 500 rows (128 x 64 tiles); rows and columns offset into the sample range."""
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    n, b = 16, 8
+    fm = dualk.FeatureMap(reps=2, block=b)
+    p = dualk.DK_PREC_BF16X3
+    x4 = synthetic.fmnist_like(4000, 500, n)
+    xa, xt = x4["x_train"], x4["x_test"]
+    res = {}
+    for form in FORMS:
+        with _form(dualk, ctx, form):
+            sa = dualk.block_states(ctx, _dev(torch, xa), fm, dualk.DK_ENT_FULL, prec=p)
+            st = dualk.block_states(ctx, _dev(torch, xt), fm, dualk.DK_ENT_FULL, prec=p)
+            g = dualk.gram_blocks(ctx, sa, w=1.0, want=("logkq",))
+            rect = torch.empty(2000, 1900, device="cuda")
+            _check_call(dualk, dualk._lib().dk_gram_blocks(
+                ctx.handle, dualk._ptr(sa.data), 4000, dualk._ptr(sa.data), 4000, n, b, 100, 2000, 2100, 1900,
+                dualk._ptr(sa.log_norm), dualk._ptr(sa.log_norm), None, None, 0.0, 1.0, p, None, None, None,
+                dualk._ptr(rect), 1900, 0, dualk._stream(None)))
+            r = dualk.gram_blocks(ctx, st, sa, w=1.0, want=("logkq",))
+            torch.cuda.synchronize()
+            res[form] = (g["logkq"].cpu().numpy().astype(np.float64), rect.cpu().numpy().astype(np.float64),
+                         r["logkq"].cpu().numpy().astype(np.float64))
+            assert np.all(np.diag(res[form][0]) == 0.0)
+    for a, c in zip(res["tcgen05"], res["mma_sync"]):
+        assert np.max(np.abs(a - c) / np.maximum(1.0, np.abs(c))) <= 2e-5
+    def near(lg, ref):
+        assert np.max(np.abs(np.exp(lg) - np.exp(ref))) <= 1e-4
+        assert np.max(np.abs(lg - ref) / np.maximum(1.0, np.abs(ref))) <= 1e-3
+
+    gi, gj = np.arange(0, 4000, 97), np.arange(3, 4000, 89)
+    near(res["tcgen05"][0][np.ix_(gi, gj)], _ref_log(xa[gi], xa[gj], 2, b, "full"))
+    ri, rj = np.arange(100, 2100, 101), np.arange(2100, 4000, 93)
+    near(res["tcgen05"][1][np.ix_(ri - 100, rj - 2100)], _ref_log(xa[ri], xa[rj], 2, b, "full"))
+    ti = np.arange(0, 500, 25)
+    near(res["tcgen05"][2][np.ix_(ti, gj)], _ref_log(xt[ti], xa[gj], 2, b, "full"))
+    ctx.sync_status()
+
+
+def _check_call(dualk, status):
+    assert status == 0, status
 
 
 def test_svm_workflow_on_a_block_map(dk):
