@@ -19,9 +19,10 @@
 //   warps 2-9 the epilogue: thread (TMEM lane r, column half h) reads BN/2 columns of Re and
 //             Im of row r, adds log2 |G_B|^2 to its running sums and frees the accumulator,
 //             which the MMA thread refills two blocks later (so block B's epilogue runs under
-//             the MMAs of block B + 1); between blocks it also takes its share of the RBF
-//             distances (Kahan FP32, one pair at a time); after the last block it writes the
-//             tile through the common epilogue (write_pair).
+//             the MMAs of block B + 1); after the last block it writes the tile through the
+//             common epilogue (write_pair) with the squared distances of the RBF kernel, which
+//             rbf_d2_kernel computed beforehand (feature rows staged through shared memory, the
+//             per-pair Kahan FP32 sum of every Gram kernel).
 //
 // Self-norms (diagonal mode): a unit is one (diagonal tile, block) pair with A = B in shared
 // memory. The diagonal tile of the symmetric Gram issues the same instructions on the same
@@ -276,9 +277,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int h = (warp - 2) >> 2;    // column half
     const int r = 32 * q + lane;      // tile row = TMEM lane
     const u32 t_row = tmem + (u32(32 * q) << 16) + u32(h * C::CPT);
-    float lg[C::CPT], d2[C::CPT];
+    float lg[C::CPT];
 #pragma unroll
-    for (int u = 0; u < C::CPT; ++u) lg[u] = d2[u] = 0.0f;
+    for (int u = 0; u < C::CPT; ++u) lg[u] = 0.0f;
     for (long long k = 0; k < my_units; ++k) {
       int r0, c0, blk;
       unit(k, r0, c0, blk);
@@ -312,28 +313,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (r / C::CPT == h && i < m_diag) g2_out[size_t(blk) * m_diag + i] = dg;
         continue;
       }
-      if (p.need_kc) {
-        // this block's share of the tile's RBF distances: pairs [lo, hi) of the thread's row
-        const int lo = int((long long)blk * C::CPT / nb), hi = int((long long)(blk + 1) * C::CPT / nb);
-        for (int pp = lo; pp < hi; ++pp) {
-          const int j = c0 + h * C::CPT + pp;
-          float s = 0.0f, comp = 0.0f;
-          if (i < p.row0 + p.nrows && j < p.col0 + p.ncols && !(p.symmetric && j < i)) {
-            const float* xa = p.x_r + size_t(i) * p.n;
-            const float* xb = p.x_c + size_t(j) * p.n;
-            for (int f = 0; f < p.n; ++f) kahan_add_sq(s, comp, __ldg(xa + f) - __ldg(xb + f));
-          }
-#pragma unroll
-          for (int u = 0; u < C::CPT; ++u)
-            if (u == pp) d2[u] = s;
-        }
-      }
       if (blk == nb - 1) {
 #pragma unroll
         for (int u = 0; u < C::CPT; ++u) {
-          write_pair(p, half_log_lg(lg[u]), d2[u], i, c0 + h * C::CPT + u);
+          const int j = c0 + h * C::CPT + u;
+          float dd = 0.0f;
+          if (p.need_kc && i < p.row0 + p.nrows && j < p.col0 + p.ncols && !(p.symmetric && j < i))
+            dd = p.d2[size_t(i - p.row0) * size_t(p.ncols) + size_t(j - p.col0)];
+          write_pair(p, half_log_lg(lg[u]), dd, i, j);
           lg[u] = 0.0f;
-          d2[u] = 0.0f;
         }
       }
     }
@@ -345,6 +333,57 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     tc_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+// Squared feature distances of the pairs of a Gram block (RBF kernel, Eq. 3): 64 x 64 pairs
+// per tile, 256 threads with 4 x 4 pairs each, feature rows staged through shared memory 32
+// features at a time; per pair the Kahan FP32 sum of (x_i[f] - x_j[f])^2 over f = 0 .. n-1 in
+// order, the additions of every Gram kernel's epilogue. d2[(i - row0) ld2 + (j - col0)];
+// symmetric blocks get the pairs with j >= i.
+constexpr int RT = 64, RF = 32;
+__global__ void __launch_bounds__(256) rbf_d2_kernel(const GramArgs p, float* __restrict__ d2, int ld2) {
+  __shared__ float xr[RF][RT + 1], xc[RF][RT + 1];  // [feature][sample]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+    int ti, tj;
+    decode_tile(p, RT, RT, t, ti, tj);
+    const int r0 = p.row0 + ti * RT, c0 = p.col0 + tj * RT;
+    float s[4][4], cmp[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) s[a][b] = cmp[a][b] = 0.0f;
+    for (int f0 = 0; f0 < p.n; f0 += RF) {
+      const int nf = min(RF, p.n - f0);
+      __syncthreads();  // the previous chunk has been read
+      for (int e = threadIdx.x; e < RF * RT; e += 256) {
+        const int f = e & (RF - 1), r = e >> 5;
+        const int ir = min(r0 + r, p.row0 + p.nrows - 1), jc = min(c0 + r, p.col0 + p.ncols - 1);
+        xr[f][r] = f < nf ? __ldg(p.x_r + size_t(ir) * p.n + f0 + f) : 0.0f;
+        xc[f][r] = f < nf ? __ldg(p.x_c + size_t(jc) * p.n + f0 + f) : 0.0f;
+      }
+      __syncthreads();
+      for (int f = 0; f < nf; ++f) {
+        float va[4], vb[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) va[a] = xr[f][ty + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) vb[b] = xc[f][tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) kahan_add_sq(s[a][b], cmp[a][b], va[a] - vb[b]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = r0 + ty + 16 * a, j = c0 + tx + 16 * b;
+        if (i < p.row0 + p.nrows && j < p.col0 + p.ncols && !(p.symmetric && j < i))
+          d2[size_t(i - p.row0) * size_t(ld2) + size_t(j - p.col0)] = s[a][b];
+      }
   }
 }
 
@@ -393,8 +432,25 @@ dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int 
   a.ntiles = ntiles;
   const int grid = ntiles < ctx->sm_count ? ntiles : ctx->sm_count;
   if (grid < 1) return DK_OK;
-  gram_blocks_umma_kernel<BN><<<grid, NTHREADS, Cfg<BN>::SMEM, st>>>(tr, tc, a, nb, dp / 16, 0, 0, nullptr, 0);
-  return launch_status();
+  // squared distances of the RBF kernel first, into stream-ordered scratch
+  float* d2 = nullptr;
+  if (a.need_kc) {
+    if (cudaMallocAsync(reinterpret_cast<void**>(&d2), size_t(a.nrows) * size_t(a.ncols) * sizeof(float), st) !=
+        cudaSuccess)
+      return DK_ERR_CUDA;
+    GramArgs ar = a;
+    ar.ntiles = count_tiles(ar, RT, RT);
+    const int rgrid = ar.ntiles < 8 * ctx->sm_count ? ar.ntiles : 8 * ctx->sm_count;
+    rbf_d2_kernel<<<rgrid, 256, 0, st>>>(ar, d2, a.ncols);
+    s = launch_status();
+    a.d2 = d2;
+  }
+  if (s == DK_OK) {
+    gram_blocks_umma_kernel<BN><<<grid, NTHREADS, Cfg<BN>::SMEM, st>>>(tr, tc, a, nb, dp / 16, 0, 0, nullptr, 0);
+    s = launch_status();
+  }
+  if (d2 && cudaFreeAsync(d2, st) != cudaSuccess && s == DK_OK) s = DK_ERR_CUDA;
+  return s;
 }
 
 }  // namespace gbum

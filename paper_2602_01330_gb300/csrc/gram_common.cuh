@@ -27,6 +27,7 @@ struct GramArgs {
   long long ld;
   unsigned* status;
   int need_kc;  // K_c is needed (k_out with w != 1, or kc_out)
+  const float* d2;  // squared distances of the block's pairs, nrows x ncols (kernels that take them precomputed)
 };
 
 // First column tile of row tile ti that holds a pair with j >= i (symmetric Gram): the
