@@ -126,9 +126,22 @@ __device__ inline void build(double2* psi, double2* ph, Coeffs& C, const float* 
   }
 }
 
+// Two-float sum a + b of unevaluated pairs (hi, lo) (Knuth's two-sum of the high parts, the
+// low parts added to the error, then renormalised): about 44 significant bits.
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  float e = (a.x - (s - bb)) + (b.x - bb);
+  e += a.y + b.y;
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+
 // The same state in FP32 for operands that are rounded to split BF16 afterwards (about 17
-// significant bits): the phase Phi(z), up to a few hundred radians, is still summed in FP64
-// from the tables and reduced to [-pi, pi] there, then sincosf of the reduced angle; the
+// significant bits). The tables are built in FP64 as above, and each entry is then reduced to
+// [-pi, pi] and kept as a two-float pair; the phase of an amplitude, a sum of hb + 2 reduced
+// entries, is added in two-float arithmetic, reduced once more and passed to sincosf (angle
+// error ~1e-7 rad, as for an FP64 phase rounded to FP32, at a fraction of the FP64 work); the
 // butterflies and the phase multiplications run in FP32 (relative error ~1e-7 per amplitude,
 // far below the split's 2^-18 ~ 4e-6).
 template <class Sync = CtaSync>
@@ -144,6 +157,16 @@ __device__ inline void build_f32(float2* psi, float2* ph, Coeffs& C, const float
     C.jq[q][r] = on ? (PI_D - double(xb[q])) * (PI_D - double(xb[r])) : 0.0;
   }
   sync();
+  constexpr double TWO_PI = 6.283185307179586476925;
+  // an FP64 table entry reduced to [-pi, pi] as a two-float pair, stored in its own slot
+  auto reduced = [](double v) {
+    const double r = v - TWO_PI * rint(v * (1.0 / TWO_PI));
+    const float hi = float(r);
+    return make_float2(hi, float(r - double(hi)));
+  };
+  float2* ta2 = reinterpret_cast<float2*>(C.ta);
+  float2* tb2 = reinterpret_cast<float2*>(C.tb);
+  float2* tv2 = reinterpret_cast<float2*>(&C.tv[0][0]);
   for (int e = tid; e < (1 << hb); e += nt) {
     double a = 0.0;
     for (int q = 0; q < hb; ++q) {
@@ -152,7 +175,7 @@ __device__ inline void build_f32(float2* psi, float2* ph, Coeffs& C, const float
       for (int r = q + 1; r < hb; ++r) s += ((e >> (hb - 1 - r)) & 1) ? -C.jq[q][r] : C.jq[q][r];
       a += zq * s;
     }
-    C.ta[e] = a;
+    ta2[e] = reduced(a);
   }
   for (int e = tid; e < (1 << lb); e += nt) {
     double bsum = 0.0;
@@ -163,21 +186,27 @@ __device__ inline void build_f32(float2* psi, float2* ph, Coeffs& C, const float
       for (int u = t + 1; u < lb; ++u) s += ((e >> (lb - 1 - u)) & 1) ? -C.jq[q][hb + u] : C.jq[q][hb + u];
       bsum += zq * s;
     }
-    C.tb[e] = bsum;
+    tb2[e] = reduced(bsum);
     for (int q = 0; q < hb; ++q) {
       double v = 0.0;
       for (int t = 0; t < lb; ++t) v += ((e >> (lb - 1 - t)) & 1) ? -C.jq[q][hb + t] : C.jq[q][hb + t];
-      C.tv[e][q] = v;
+      tv2[e * MAXH + q] = reduced(v);
     }
   }
   sync();
   const float amp = exp2f(-0.5f * float(bl));
-  constexpr double TWO_PI = 6.283185307179586476925;
+  constexpr float TWO_PI_HI = 6.28318548202514648438f;             // float(2 pi)
+  constexpr float TWO_PI_LO = -1.74845553146951931e-07f;           // 2 pi - TWO_PI_HI
   for (int e = tid; e < dim; e += nt) {
     const int zh = e >> lb, zl = e & ((1 << lb) - 1);
-    double phi = C.ta[zh] + C.tb[zl];
-    for (int q = 0; q < hb; ++q) phi += ((zh >> (hb - 1 - q)) & 1) ? -C.tv[zl][q] : C.tv[zl][q];
-    const float red = float(phi - TWO_PI * rint(phi * (1.0 / TWO_PI)));  // in [-pi, pi]
+    float2 phi = ff_add(ta2[zh], tb2[zl]);
+    for (int q = 0; q < hb; ++q) {
+      const float2 v = tv2[zl * MAXH + q];
+      phi = ff_add(phi, ((zh >> (hb - 1 - q)) & 1) ? make_float2(-v.x, -v.y) : v);
+    }
+    // |phi| <= (hb + 2) pi: one more reduction, k = round(phi / 2 pi) <= 4 in magnitude
+    const float k = rintf(phi.x * 0.15915494309189533577f);
+    const float red = fmaf(-k, TWO_PI_LO, fmaf(-k, TWO_PI_HI, phi.x)) + phi.y;  // in [-pi, pi] up to rounding
     float sn, cs;
     sincosf(-red, &sn, &cs);
     ph[e] = make_float2(cs, sn);
