@@ -121,14 +121,16 @@ __device__ __forceinline__ void tc_ld16x2(u32 ta, u32 tb, float (&va)[16], float
 __device__ __forceinline__ float half_log_lg(float lg) { return lg * (0.5f * 0.69314718055994530942f); }
 __device__ __forceinline__ float abs2(float re, float im) { return fmaf(re, re, __fmul_rn(im, im)); }
 
-// Gram mode (diag = 0): tiles of p (symmetric or rectangular), each a sequence of nb units
-// (one per block). Diagonal mode (diag = 1): n_units = ceil(m_diag / 128) * nb units
-// (diagonal tile, block) over the states of tm_r, |G_B(i, i)|^2 written to g2_out[blk][i].
+// Gram mode (diag = 0): tiles of p (symmetric or rectangular); with ksplit > 1 (rectangular
+// only) each tile's blocks are split into ksplit ranges, each range a work item whose partial
+// log2 sums go to part[split][i - row0][j - col0] for split_finish_kernel. Diagonal mode
+// (diag = 1): n_units = ceil(m_diag / 128) * nb items (diagonal tile, block) over the states
+// of tm_r, |G_B(i, i)|^2 written to g2_out[blk][i].
 template <int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gram_blocks_umma_kernel(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_c,
                             const GramArgs p, int nb, int cpb, int diag, int n_units, float* __restrict__ g2_out,
-                            int m_diag) {
+                            int m_diag, int ksplit, float* __restrict__ part) {
   using C = Cfg<BN>;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -166,25 +168,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const u32 tmem = *tmem_slot;
 
   const int grid = int(gridDim.x), bid = int(blockIdx.x);
-  long long my_units;
-  if (diag) {
-    my_units = n_units > bid ? (n_units - 1 - bid) / grid + 1 : 0;
-  } else {
-    const int my_tiles = p.ntiles > bid ? (p.ntiles - 1 - bid) / grid + 1 : 0;
-    my_units = (long long)my_tiles * nb;
-  }
-  // unit k of this CTA -> tile origin (first row and column sample) and block
-  auto unit = [&](long long k, int& r0, int& c0, int& blk) {
+  // Work items of this CTA: w = bid, bid + grid, ... < n_items. Gram mode: tile w / ksplit,
+  // blocks [b0, b1) of its split w % ksplit; diagonal mode: diagonal tile w / nb, block w % nb.
+  // An item is a sequence of units (one per block); every role walks the same sequence.
+  const int n_items = diag ? n_units : p.ntiles * ksplit;
+  auto item = [&](int w, int& r0, int& c0, int& b0, int& b1, int& split) {
     if (diag) {
-      const long long u = bid + k * grid;
-      const int ti = int(u / nb);
-      blk = int(u - (long long)ti * nb);
+      const int ti = w / nb;
+      b0 = w - ti * nb;
+      b1 = b0 + 1;
       r0 = c0 = ti * BM;
+      split = 0;
     } else {
-      const int lt = int(k / nb);
-      blk = int(k - (long long)lt * nb);
+      const int t = w / ksplit;
+      split = w - t * ksplit;
+      b0 = int((long long)split * nb / ksplit);
+      b1 = int((long long)(split + 1) * nb / ksplit);
       int ti, tj;
-      decode_tile(p, BM, BN, bid + lt * grid, ti, tj);
+      decode_tile(p, BM, BN, t, ti, tj);
       r0 = p.row0 + ti * BM;
       c0 = p.col0 + tj * BN;
     }
@@ -199,21 +200,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       const u32 tx = diag ? u32(C::A_BYTES) : u32(C::STAGE);
       long long it = 0;  // stage fills issued
-      for (long long k = 0; k < my_units && !*abort_flag; ++k) {
-        int r0, c0, blk;
-        unit(k, r0, c0, blk);
-        for (int c = 0; c < cpb; ++c) {
-          const int s = int(it % NSTAGES);
-          const long long round = it / NSTAGES;
-          if (round > 0 && !mbar_wait_bounded(&empty[s], u32((round - 1) & 1))) {
-            give_up();
-            break;
+      bool stop = false;
+      for (int w = bid; w < n_items && !stop && !*abort_flag; w += grid) {
+        int r0, c0, b0, b1, split;
+        item(w, r0, c0, b0, b1, split);
+        for (int blk = b0; blk < b1 && !stop; ++blk) {
+          for (int c = 0; c < cpb; ++c) {
+            const int s = int(it % NSTAGES);
+            const long long round = it / NSTAGES;
+            if (round > 0 && !mbar_wait_bounded(&empty[s], u32((round - 1) & 1))) {
+              give_up();
+              stop = true;
+              break;
+            }
+            uint8_t* sa = smem + s * C::STAGE;
+            mbar_arrive_expect_tx(&full[s], tx);
+            tma_load_3d(sa, &tm_r, &full[s], c * 64, r0, blk);
+            if (!diag) tma_load_3d(sa + C::A_BYTES, &tm_c, &full[s], c * 64, c0, blk);
+            ++it;
           }
-          uint8_t* sa = smem + s * C::STAGE;
-          mbar_arrive_expect_tx(&full[s], tx);
-          tma_load_3d(sa, &tm_r, &full[s], c * 64, r0, blk);
-          if (!diag) tma_load_3d(sa + C::A_BYTES, &tm_c, &full[s], c * 64, c0, blk);
-          ++it;
         }
       }
       // every issued copy has landed before the CTA may exit
@@ -224,49 +229,53 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---- MMA issuer ----
     if (lane == 0) {
       constexpr u32 ID_POS = idesc<BN>(false), ID_NEG = idesc<BN>(true);
-      long long it = 0;
-      for (long long k = 0; k < my_units && !*abort_flag; ++k) {
-        const int a = int(k & 1);
-        const long long use = k >> 1;
-        if (use > 0 && !mbar_wait_bounded(&acc_empty[a], u32((use - 1) & 1))) {
-          give_up();
-          break;
-        }
-        tc_fence_after();
-        const u32 d_re = tmem + u32(a * C::ACC), d_im = d_re + BN;
-        bool ok = true;
-        for (int c = 0; c < cpb; ++c, ++it) {
-          const int s = int(it % NSTAGES);
-          if (!mbar_wait_bounded(&full[s], u32((it / NSTAGES) & 1))) {
+      long long it = 0, k = 0;  // stages consumed, units issued
+      bool stop = false;
+      for (int w = bid; w < n_items && !stop && !*abort_flag; w += grid) {
+        int r0, c0, b0, b1, split;
+        item(w, r0, c0, b0, b1, split);
+        for (int blk = b0; blk < b1 && !stop; ++blk, ++k) {
+          const int a = int(k & 1);
+          const long long use = k >> 1;
+          if (use > 0 && !mbar_wait_bounded(&acc_empty[a], u32((use - 1) & 1))) {
             give_up();
-            ok = false;
+            stop = true;
             break;
           }
           tc_fence_after();
-          const u32 sa = smem_u32(smem + s * C::STAGE);
-          const u32 sb = diag ? sa : sa + C::A_BYTES;
-          // planes: 0 hi(re), 1 hi(im), 2 lo(re), 3 lo(im), 32 bytes apart in a row
-          const u64 a0 = sw128_desc(sa), a1 = sw128_desc(sa + 32), a2 = sw128_desc(sa + 64),
-                    a3 = sw128_desc(sa + 96);
-          const u64 b0 = sw128_desc(sb), b1 = sw128_desc(sb + 32), b2 = sw128_desc(sb + 64),
-                    b3 = sw128_desc(sb + 96);
-          const u32 acc = c > 0 ? 1u : 0u;
-          tc_mma(d_re, a2, b0, ID_POS, acc);  // Re += ar br
-          tc_mma(d_re, a0, b2, ID_POS, 1u);
-          tc_mma(d_re, a0, b0, ID_POS, 1u);
-          tc_mma(d_re, a3, b1, ID_POS, 1u);   // Re += ai bi
-          tc_mma(d_re, a1, b3, ID_POS, 1u);
-          tc_mma(d_re, a1, b1, ID_POS, 1u);
-          tc_mma(d_im, a2, b1, ID_POS, acc);  // Im += ar bi
-          tc_mma(d_im, a0, b3, ID_POS, 1u);
-          tc_mma(d_im, a0, b1, ID_POS, 1u);
-          tc_mma(d_im, a3, b0, ID_NEG, 1u);   // Im -= ai br
-          tc_mma(d_im, a1, b2, ID_NEG, 1u);
-          tc_mma(d_im, a1, b0, ID_NEG, 1u);
-          tc_commit(&empty[s]);
+          const u32 d_re = tmem + u32(a * C::ACC), d_im = d_re + BN;
+          for (int c = 0; c < cpb; ++c, ++it) {
+            const int s = int(it % NSTAGES);
+            if (!mbar_wait_bounded(&full[s], u32((it / NSTAGES) & 1))) {
+              give_up();
+              stop = true;
+              break;
+            }
+            tc_fence_after();
+            const u32 sa = smem_u32(smem + s * C::STAGE);
+            const u32 sb = diag ? sa : sa + C::A_BYTES;
+            // planes: 0 hi(re), 1 hi(im), 2 lo(re), 3 lo(im), 32 bytes apart in a row
+            const u64 a0 = sw128_desc(sa), a1 = sw128_desc(sa + 32), a2 = sw128_desc(sa + 64),
+                      a3 = sw128_desc(sa + 96);
+            const u64 b0d = sw128_desc(sb), b1d = sw128_desc(sb + 32), b2d = sw128_desc(sb + 64),
+                      b3d = sw128_desc(sb + 96);
+            const u32 acc = c > 0 ? 1u : 0u;
+            tc_mma(d_re, a2, b0d, ID_POS, acc);  // Re += ar br
+            tc_mma(d_re, a0, b2d, ID_POS, 1u);
+            tc_mma(d_re, a0, b0d, ID_POS, 1u);
+            tc_mma(d_re, a3, b1d, ID_POS, 1u);   // Re += ai bi
+            tc_mma(d_re, a1, b3d, ID_POS, 1u);
+            tc_mma(d_re, a1, b1d, ID_POS, 1u);
+            tc_mma(d_im, a2, b1d, ID_POS, acc);  // Im += ar bi
+            tc_mma(d_im, a0, b3d, ID_POS, 1u);
+            tc_mma(d_im, a0, b1d, ID_POS, 1u);
+            tc_mma(d_im, a3, b0d, ID_NEG, 1u);   // Im -= ai br
+            tc_mma(d_im, a1, b2d, ID_NEG, 1u);
+            tc_mma(d_im, a1, b0d, ID_NEG, 1u);
+            tc_commit(&empty[s]);
+          }
+          if (!stop) tc_commit(&acc_full[a]);
         }
-        if (!ok) break;
-        tc_commit(&acc_full[a]);
       }
       tc_commit(done);
       if (!mbar_wait_bounded(done, 0u)) record_status(p.status, DEV_TIMEOUT);
@@ -280,49 +289,56 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float lg[C::CPT];
 #pragma unroll
     for (int u = 0; u < C::CPT; ++u) lg[u] = 0.0f;
-    for (long long k = 0; k < my_units; ++k) {
-      int r0, c0, blk;
-      unit(k, r0, c0, blk);
-      const int a = int(k & 1);
-      // one decision per warp: the loads below are warp-collective
-      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[a], u32((k >> 1) & 1)))) {
-        if (lane == 0) give_up();
-        break;
-      }
-      tc_fence_after();
-      float dg = 0.0f;
+    long long k = 0;
+    bool stop = false;
+    for (int w = bid; w < n_items && !stop; w += grid) {
+      int r0, c0, b0, b1, split;
+      item(w, r0, c0, b0, b1, split);
+      const int i = r0 + r;
+      for (int blk = b0; blk < b1; ++blk, ++k) {
+        const int a = int(k & 1);
+        // one decision per warp: the loads below are warp-collective
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[a], u32((k >> 1) & 1)))) {
+          if (lane == 0) give_up();
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        float dg = 0.0f;
 #pragma unroll
-      for (int cc = 0; cc < C::CPT / 16; ++cc) {
-        float re[16], im[16];
-        tc_ld16x2(t_row + u32(a * C::ACC + 16 * cc), t_row + u32(a * C::ACC + BN + 16 * cc), re, im);
+        for (int cc = 0; cc < C::CPT / 16; ++cc) {
+          float re[16], im[16];
+          tc_ld16x2(t_row + u32(a * C::ACC + 16 * cc), t_row + u32(a * C::ACC + BN + 16 * cc), re, im);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const float g2 = abs2(re[e], im[e]);
-          if (diag) {
-            if (h * C::CPT + 16 * cc + e == r) dg = g2;
-          } else {
-            lg[16 * cc + e] += log2f(g2);
+          for (int e = 0; e < 16; ++e) {
+            const float g2 = abs2(re[e], im[e]);
+            if (diag) {
+              if (h * C::CPT + 16 * cc + e == r) dg = g2;
+            } else {
+              lg[16 * cc + e] += log2f(g2);
+            }
           }
         }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[a]);
-      const int i = r0 + r;
-      if (diag) {
-        if (r / C::CPT == h && i < m_diag) g2_out[size_t(blk) * m_diag + i] = dg;
-        continue;
-      }
-      if (blk == nb - 1) {
-#pragma unroll
-        for (int u = 0; u < C::CPT; ++u) {
-          const int j = c0 + h * C::CPT + u;
-          float dd = 0.0f;
-          if (p.need_kc && i < p.row0 + p.nrows && j < p.col0 + p.ncols && !(p.symmetric && j < i))
-            dd = p.d2[size_t(i - p.row0) * size_t(p.ncols) + size_t(j - p.col0)];
-          write_pair(p, half_log_lg(lg[u]), dd, i, j);
-          lg[u] = 0.0f;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[a]);
+        if (diag) {
+          if (r / C::CPT == h && i < m_diag) g2_out[size_t(blk) * m_diag + i] = dg;
         }
+      }
+      if (diag || stop) continue;
+      // end of the item: the tile's outputs, or (split over the blocks) its partial log sums
+#pragma unroll
+      for (int u = 0; u < C::CPT; ++u) {
+        const int j = c0 + h * C::CPT + u;
+        const bool valid = i < p.row0 + p.nrows && j < p.col0 + p.ncols && !(p.symmetric && j < i);
+        const size_t at = size_t(i - p.row0) * size_t(p.ncols) + size_t(j - p.col0);
+        if (ksplit > 1) {
+          if (valid) part[size_t(split) * size_t(p.nrows) * size_t(p.ncols) + at] = lg[u];
+        } else {
+          write_pair(p, half_log_lg(lg[u]), (valid && p.need_kc) ? p.d2[at] : 0.0f, i, j);
+        }
+        lg[u] = 0.0f;
       }
     }
   }
@@ -387,6 +403,18 @@ __global__ void __launch_bounds__(256) rbf_d2_kernel(const GramArgs p, float* __
   }
 }
 
+// Outputs of a rectangular block computed with its blocks split over ksplit work items: the
+// partial log2 sums added in split order, then the common epilogue.
+__global__ void split_finish_kernel(const GramArgs p, const float* __restrict__ part, int ksplit) {
+  const long long np = (long long)p.nrows * p.ncols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < np; e += (long long)gridDim.x * blockDim.x) {
+    float lg = 0.0f;
+    for (int s = 0; s < ksplit; ++s) lg += part[size_t(s) * size_t(np) + size_t(e)];
+    const int i = p.row0 + int(e / p.ncols), j = p.col0 + int(e % p.ncols);
+    write_pair(p, half_log_lg(lg), p.need_kc ? p.d2[e] : 0.0f, i, j);
+  }
+}
+
 // ln N_i from the per-block diagonal |G_B(i, i)|^2: log2 terms added in block order, as the
 // Gram epilogue adds them.
 __global__ void selfnorm_sum_kernel(const float* __restrict__ g2, int m, int nb, float* __restrict__ log_norm) {
@@ -423,14 +451,15 @@ dk_status set_smem() {
 
 template <int BN>
 dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp, GramArgs a,
-                      int ntiles, cudaStream_t st) {
+                      int ntiles, int ksplit, cudaStream_t st) {
   CUtensorMap tr, tc;
   dk_status s = encode_states_map(ctx, &tr, sr, m_r, nb, dp, BM);
   if (s == DK_OK) s = encode_states_map(ctx, &tc, sc, m_c, nb, dp, BN);
   if (s == DK_OK) s = set_smem<BN>();
   if (s != DK_OK) return s;
   a.ntiles = ntiles;
-  const int grid = ntiles < ctx->sm_count ? ntiles : ctx->sm_count;
+  const long long items = (long long)ntiles * ksplit;
+  const int grid = int(items < ctx->sm_count ? items : ctx->sm_count);
   if (grid < 1) return DK_OK;
   // squared distances of the RBF kernel first, into stream-ordered scratch
   float* d2 = nullptr;
@@ -445,10 +474,23 @@ dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int 
     s = launch_status();
     a.d2 = d2;
   }
+  float* part = nullptr;
+  const size_t np = size_t(a.nrows) * size_t(a.ncols);
+  if (s == DK_OK && ksplit > 1 &&
+      cudaMallocAsync(reinterpret_cast<void**>(&part), size_t(ksplit) * np * sizeof(float), st) != cudaSuccess)
+    s = DK_ERR_CUDA;
   if (s == DK_OK) {
-    gram_blocks_umma_kernel<BN><<<grid, NTHREADS, Cfg<BN>::SMEM, st>>>(tr, tc, a, nb, dp / 16, 0, 0, nullptr, 0);
+    gram_blocks_umma_kernel<BN><<<grid, NTHREADS, Cfg<BN>::SMEM, st>>>(tr, tc, a, nb, dp / 16, 0, 0, nullptr, 0,
+                                                                       ksplit, part);
     s = launch_status();
   }
+  if (s == DK_OK && part) {
+    const long long fgrid = (long long)(np + 255) / 256;
+    split_finish_kernel<<<int(fgrid < 16LL * ctx->sm_count ? fgrid : 16LL * ctx->sm_count), 256, 0, st>>>(a, part,
+                                                                                                       ksplit);
+    s = launch_status();
+  }
+  if (part && cudaFreeAsync(part, st) != cudaSuccess && s == DK_OK) s = DK_ERR_CUDA;
   if (d2 && cudaFreeAsync(d2, st) != cudaSuccess && s == DK_OK) s = DK_ERR_CUDA;
   return s;
 }
@@ -457,16 +499,24 @@ dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int 
 
 dk_status gram_blocks_umma_launch(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp,
                                   GramArgs a, cudaStream_t st) {
-  // symmetric: 128 x 128 tiles (the diagonal tiles are the self-norm units, bit for bit);
-  // rectangular: 128 x 64 when it takes fewer waves of half-size tiles
+  // symmetric: 128 x 128 tiles, all blocks in one item (the diagonal tiles are then the
+  // self-norm units, bit for bit). Rectangular: 128 x 128 tiles with the blocks split over up
+  // to 8 items per tile when there are fewer tiles than SMs, or 128 x 64 tiles, whichever
+  // takes less time by waves x blocks per item (a 128 x 64 tile-block costs about 0.92 of a
+  // 128 x 128 one: its N = 64 MMAs are bound by shared-memory reads)
   GramArgs a128 = a, a64 = a;
   const int t128 = count_tiles(a128, gbum::BM, 128);
-  if (a.symmetric) return gbum::launch_gram<128>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, st);
+  if (a.symmetric) return gbum::launch_gram<128>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, 1, st);
   const int t64 = count_tiles(a64, gbum::BM, 64);
   const long long sms = ctx->sm_count;
-  const long long cost128 = 2 * ((t128 + sms - 1) / sms), cost64 = (t64 + sms - 1) / sms;
-  if (cost128 <= cost64) return gbum::launch_gram<128>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, st);
-  return gbum::launch_gram<64>(ctx, sr, m_r, sc, m_c, nb, dp, a64, t64, st);
+  long long ks = t128 < sms ? sms / t128 : 1;
+  if (ks > nb) ks = nb;
+  if (ks > 8) ks = 8;
+  if (ks < 1) ks = 1;
+  const double cost128 = double((t128 * ks + sms - 1) / sms) * double((nb + ks - 1) / ks);
+  const double cost64 = double((t64 + sms - 1) / sms) * double(nb) * 0.92;
+  if (cost128 <= cost64) return gbum::launch_gram<128>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, int(ks), st);
+  return gbum::launch_gram<64>(ctx, sr, m_r, sc, m_c, nb, dp, a64, t64, 1, st);
 }
 
 dk_status block_selfnorm_umma_launch(dk_ctx* ctx, const void* states, int m, int nb, int dp, float* log_norm,
@@ -484,7 +534,8 @@ dk_status block_selfnorm_umma_launch(dk_ctx* ctx, const void* states, int m, int
   GramArgs a{};
   a.status = ctx->status;
   const int grid = int(units < ctx->sm_count ? units : ctx->sm_count);
-  gram_blocks_umma_kernel<128><<<grid, NTHREADS, Cfg<128>::SMEM, st>>>(t, t, a, nb, dp / 16, 1, int(units), g2, m);
+  gram_blocks_umma_kernel<128><<<grid, NTHREADS, Cfg<128>::SMEM, st>>>(t, t, a, nb, dp / 16, 1, int(units), g2, m,
+                                                                      1, nullptr);
   s = launch_status();
   if (s == DK_OK) {
     selfnorm_sum_kernel<<<(m + 255) / 256, 256, 0, st>>>(g2, m, nb, log_norm);

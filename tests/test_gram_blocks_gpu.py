@@ -326,6 +326,41 @@ def test_block_gram_forms_agree_and_persist(dk):
     ctx.sync_status()
 
 
+@pytest.mark.parametrize("case", ["split_n784", "one_block"])
+def test_block_gram_rows_split_and_narrow_tiles(dk, case):
+    """Rectangular blocks: 300 x 1000 at n = 784 in blocks of 10 (24 tiles of 128 x 128, so
+    the 79 blocks are split over 6 work items per tile and the partial log sums added by the
+    finishing kernel) and 300 x 700 with a single block of 10 qubits (no split possible: the
+    128 x 64 tiles); tcgen05 against mma.sync to 2e-5 relative in log K_q, K_c identical, and
+    against the oracle on a sample."""
+    dualk, ctx, torch = dk
+    from oracle import gram as og
+    from paper_2602_01330_gb300 import synthetic
+    n, b, mr, mc = (784, 10, 300, 1000) if case == "split_n784" else (10, 10, 300, 700)
+    d = synthetic.fmnist_like(mc, mr, n)
+    xc, xr = d["x_train"], d["x_test"]
+    fm = dualk.FeatureMap(reps=2, block=b)
+    p = dualk.DK_PREC_BF16X3
+    res = {}
+    for form in FORMS:
+        with _form(dualk, ctx, form):
+            sc = dualk.block_states(ctx, _dev(torch, xc), fm, dualk.DK_ENT_FULL, prec=p)
+            sr = dualk.block_states(ctx, _dev(torch, xr), fm, dualk.DK_ENT_FULL, prec=p)
+            out = dualk.gram_blocks(ctx, sr, sc, w=0.5)
+            torch.cuda.synchronize()
+            res[form] = {k: v.cpu().numpy().astype(np.float64) for k, v in out.items()}
+    a, c = res["tcgen05"], res["mma_sync"]
+    assert np.max(np.abs(a["logkq"] - c["logkq"]) / np.maximum(1.0, np.abs(c["logkq"]))) <= 2e-5
+    assert np.array_equal(a["kc"], c["kc"])
+    ri, cj = np.arange(0, mr, 23), np.arange(0, mc, 41)
+    ref = _ref_log(xr[ri], xc[cj], 2, b, "full")
+    got = a["logkq"][np.ix_(ri, cj)]
+    assert np.max(np.abs(np.exp(got) - np.exp(ref))) <= 1e-4
+    assert np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref))) <= 1e-3
+    assert np.max(np.abs(a["kc"][np.ix_(ri, cj)] - og.rbf(xr[ri], xc[cj], 1.0 / n))) <= 1e-6
+    ctx.sync_status()
+
+
 def _check_call(dualk, status):
     assert status == 0, status
 
