@@ -43,27 +43,36 @@ using u64 = uint64_t;
 
 constexpr int BM = 128;     // tile rows = MMA M = TMEM lanes
 constexpr int ROWB = 128;   // one 16-amplitude chunk of a sample: 4 planes x 16 BF16
-constexpr int NSTAGES = 6;
 constexpr int NEPI = 8;     // epilogue warps
 constexpr int NTHREADS = (2 + NEPI) * 32;
 
-template <int BN>
+// BN columns per tile. Narrow form (WIDE = false): N = BN instructions into [Re | Im]
+// accumulators, two of them (double-buffered). Wide form (BN = 128): the column rows are
+// staged twice, the second copy shifted by one plane (16 BF16), so at byte offset 0 / 64 of
+// a row the 256 rows [copy 1; copy 2] hold [b_re; b_im] of the hi / lo planes; the N = 256
+// instructions D1 = a_re [b_re; b_im]^T and D2 = a_im [b_re; b_im]^T fill one accumulator of
+// 512 columns, and Re = D1[:, re] + D2[:, im], Im = D1[:, im] - D2[:, re] in the epilogue.
+template <int BN, bool WIDE>
 struct Cfg {
   static_assert(BN % 16 == 0 && BN >= 32 && BN <= 128, "MMA N for M = 128");
+  static_assert(!WIDE || BN == 128, "the wide form pairs 128 real and 128 imaginary rows");
   static constexpr int A_BYTES = BM * ROWB;
-  static constexpr int B_BYTES = BN * ROWB;
-  static constexpr int STAGE = A_BYTES + B_BYTES;  // a multiple of 1024: every stage on a swizzle atom
-  static constexpr int ACC = 2 * BN;               // TMEM columns of one accumulator: Re | Im
-  static constexpr u32 TMEM_COLS = 2 * ACC;        // two accumulators (a power of two, >= 32)
-  static constexpr int CPT = BN / 2;               // columns per epilogue thread
-  static constexpr size_t SMEM = 1024 + size_t(NSTAGES) * STAGE + 256;
+  static constexpr int B_BYTES = BN * ROWB;                   // one copy of the column rows
+  static constexpr int STAGE = A_BYTES + (WIDE ? 2 : 1) * B_BYTES;  // multiples of 1024 (swizzle atoms)
+  static constexpr int NST = WIDE ? 4 : 6;                    // stages in the ring
+  static constexpr int NACC = WIDE ? 1 : 2;                   // accumulators
+  static constexpr int ACC = WIDE ? 4 * BN : 2 * BN;          // TMEM columns of one accumulator
+  static constexpr u32 TMEM_COLS = NACC * ACC;                // a power of two, >= 32
+  static constexpr int CPT = BN / 2;                          // columns per epilogue thread
+  static constexpr size_t SMEM = 1024 + size_t(NST) * STAGE + 256;
 };
 
 // Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both K-major,
-// N = BN, M = 128; neg_b negates B.
-template <int BN>
+// M = 128, N = the template argument; neg_b negates B.
+template <int N>
 __host__ __device__ constexpr u32 idesc(bool neg_b) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (neg_b ? (1u << 14) : 0u) | (u32(BN >> 3) << 17) | (u32(BM >> 4) << 24);
+  static_assert(N % 16 == 0 && N >= 16 && N <= 256, "MMA N for M = 128");
+  return (1u << 4) | (1u << 7) | (1u << 10) | (neg_b ? (1u << 14) : 0u) | (u32(N >> 3) << 17) | (u32(BM >> 4) << 24);
 }
 
 // Shared-memory descriptor of a K-major operand in the 128-byte swizzle layout written by
@@ -126,12 +135,13 @@ __device__ __forceinline__ float abs2(float re, float im) { return fmaf(re, re, 
 // log2 sums go to part[split][i - row0][j - col0] for split_finish_kernel. Diagonal mode
 // (diag = 1): n_units = ceil(m_diag / 128) * nb items (diagonal tile, block) over the states
 // of tm_r, |G_B(i, i)|^2 written to g2_out[blk][i].
-template <int BN>
+template <int BN, bool WIDE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gram_blocks_umma_kernel(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_c,
                             const GramArgs p, int nb, int cpb, int diag, int n_units, float* __restrict__ g2_out,
                             int m_diag, int ksplit, float* __restrict__ part) {
-  using C = Cfg<BN>;
+  using C = Cfg<BN, WIDE>;
+  constexpr int NSTAGES = C::NST;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGES * C::STAGE);
@@ -198,7 +208,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     // ---- TMA loader ----
     if (lane == 0) {
-      const u32 tx = diag ? u32(C::A_BYTES) : u32(C::STAGE);
+      const u32 tx = WIDE ? (diag ? u32(2 * C::A_BYTES) : u32(C::STAGE)) : (diag ? u32(C::A_BYTES) : u32(C::STAGE));
       long long it = 0;  // stage fills issued
       bool stop = false;
       for (int w = bid; w < n_items && !stop && !*abort_flag; w += grid) {
@@ -217,6 +227,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_arrive_expect_tx(&full[s], tx);
             tma_load_3d(sa, &tm_r, &full[s], c * 64, r0, blk);
             if (!diag) tma_load_3d(sa + C::A_BYTES, &tm_c, &full[s], c * 64, c0, blk);
+            if (WIDE)  // the column rows again, one plane on (x + 16: 32 bytes, a 16-byte multiple)
+              tma_load_3d(sa + (diag ? C::A_BYTES : C::A_BYTES + C::B_BYTES), diag ? &tm_r : &tm_c, &full[s],
+                          c * 64 + 16, diag ? r0 : c0, blk);
             ++it;
           }
         }
@@ -228,15 +241,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
-      constexpr u32 ID_POS = idesc<BN>(false), ID_NEG = idesc<BN>(true);
+      constexpr u32 ID_POS = idesc<BN>(false), ID_NEG = idesc<BN>(true), ID_W = idesc<2 * BN>(false);
       long long it = 0, k = 0;  // stages consumed, units issued
       bool stop = false;
       for (int w = bid; w < n_items && !stop && !*abort_flag; w += grid) {
         int r0, c0, b0, b1, split;
         item(w, r0, c0, b0, b1, split);
         for (int blk = b0; blk < b1 && !stop; ++blk, ++k) {
-          const int a = int(k & 1);
-          const long long use = k >> 1;
+          const int a = C::NACC == 2 ? int(k & 1) : 0;
+          const long long use = C::NACC == 2 ? (k >> 1) : k;
           if (use > 0 && !mbar_wait_bounded(&acc_empty[a], u32((use - 1) & 1))) {
             give_up();
             stop = true;
@@ -257,9 +270,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // planes: 0 hi(re), 1 hi(im), 2 lo(re), 3 lo(im), 32 bytes apart in a row
             const u64 a0 = sw128_desc(sa), a1 = sw128_desc(sa + 32), a2 = sw128_desc(sa + 64),
                       a3 = sw128_desc(sa + 96);
+            const u32 acc = c > 0 ? 1u : 0u;
+            if (WIDE) {
+              // B = [column rows; the copy one plane on]: [b_re; b_im] at offset 0 (hi), 64 (lo)
+              const u64 bh = sw128_desc(sb), bl = sw128_desc(sb + 64);
+              const u32 d1 = d_re, d2 = d_re + 2 * BN;
+              tc_mma(d1, a2, bh, ID_W, acc);  // D1 += a_re [b_re; b_im]
+              tc_mma(d1, a0, bl, ID_W, 1u);
+              tc_mma(d1, a0, bh, ID_W, 1u);
+              tc_mma(d2, a3, bh, ID_W, acc);  // D2 += a_im [b_re; b_im]
+              tc_mma(d2, a1, bl, ID_W, 1u);
+              tc_mma(d2, a1, bh, ID_W, 1u);
+              tc_commit(&empty[s]);
+              continue;
+            }
             const u64 b0d = sw128_desc(sb), b1d = sw128_desc(sb + 32), b2d = sw128_desc(sb + 64),
                       b3d = sw128_desc(sb + 96);
-            const u32 acc = c > 0 ? 1u : 0u;
             tc_mma(d_re, a2, b0d, ID_POS, acc);  // Re += ar br
             tc_mma(d_re, a0, b2d, ID_POS, 1u);
             tc_mma(d_re, a0, b0d, ID_POS, 1u);
@@ -296,9 +322,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       item(w, r0, c0, b0, b1, split);
       const int i = r0 + r;
       for (int blk = b0; blk < b1; ++blk, ++k) {
-        const int a = int(k & 1);
+        const int a = C::NACC == 2 ? int(k & 1) : 0;
+        const u32 par = C::NACC == 2 ? u32((k >> 1) & 1) : u32(k & 1);
         // one decision per warp: the loads below are warp-collective
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[a], u32((k >> 1) & 1)))) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[a], par))) {
           if (lane == 0) give_up();
           stop = true;
           break;
@@ -309,6 +336,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int cc = 0; cc < C::CPT / 16; ++cc) {
           float re[16], im[16];
           tc_ld16x2(t_row + u32(a * C::ACC + 16 * cc), t_row + u32(a * C::ACC + BN + 16 * cc), re, im);
+          if (WIDE) {  // re, im hold ar br, ar bi; D2 holds ai br, ai bi
+            float x2[16], y2[16];
+            tc_ld16x2(t_row + u32(2 * BN + 16 * cc), t_row + u32(3 * BN + 16 * cc), x2, y2);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              re[e] = re[e] + y2[e];
+              im[e] = im[e] - x2[e];
+            }
+          }
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const float g2 = abs2(re[e], im[e]);
@@ -438,24 +474,24 @@ dk_status encode_states_map(dk_ctx* ctx, CUtensorMap* map, const void* states, i
   return r == CUDA_SUCCESS ? DK_OK : DK_ERR_CUDA;
 }
 
-template <int BN>
+template <int BN, bool WIDE>
 dk_status set_smem() {
   static bool done = false;
   if (done) return DK_OK;
-  if (cudaFuncSetAttribute(gram_blocks_umma_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(Cfg<BN>::SMEM)) != cudaSuccess)
+  if (cudaFuncSetAttribute(gram_blocks_umma_kernel<BN, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(Cfg<BN, WIDE>::SMEM)) != cudaSuccess)
     return DK_ERR_CUDA;
   done = true;
   return DK_OK;
 }
 
-template <int BN>
+template <int BN, bool WIDE>
 dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp, GramArgs a,
                       int ntiles, int ksplit, cudaStream_t st) {
   CUtensorMap tr, tc;
   dk_status s = encode_states_map(ctx, &tr, sr, m_r, nb, dp, BM);
   if (s == DK_OK) s = encode_states_map(ctx, &tc, sc, m_c, nb, dp, BN);
-  if (s == DK_OK) s = set_smem<BN>();
+  if (s == DK_OK) s = set_smem<BN, WIDE>();
   if (s != DK_OK) return s;
   a.ntiles = ntiles;
   const long long items = (long long)ntiles * ksplit;
@@ -480,8 +516,8 @@ dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int 
       cudaMallocAsync(reinterpret_cast<void**>(&part), size_t(ksplit) * np * sizeof(float), st) != cudaSuccess)
     s = DK_ERR_CUDA;
   if (s == DK_OK) {
-    gram_blocks_umma_kernel<BN><<<grid, NTHREADS, Cfg<BN>::SMEM, st>>>(tr, tc, a, nb, dp / 16, 0, 0, nullptr, 0,
-                                                                       ksplit, part);
+    gram_blocks_umma_kernel<BN, WIDE><<<grid, NTHREADS, Cfg<BN, WIDE>::SMEM, st>>>(tr, tc, a, nb, dp / 16, 0, 0,
+                                                                                   nullptr, 0, ksplit, part);
     s = launch_status();
   }
   if (s == DK_OK && part) {
@@ -506,7 +542,7 @@ dk_status gram_blocks_umma_launch(dk_ctx* ctx, const void* sr, int m_r, const vo
   // 128 x 128 one: its N = 64 MMAs are bound by shared-memory reads)
   GramArgs a128 = a, a64 = a;
   const int t128 = count_tiles(a128, gbum::BM, 128);
-  if (a.symmetric) return gbum::launch_gram<128>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, 1, st);
+  if (a.symmetric) return gbum::launch_gram<128, true>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, 1, st);
   const int t64 = count_tiles(a64, gbum::BM, 64);
   const long long sms = ctx->sm_count;
   long long ks = t128 < sms ? sms / t128 : 1;
@@ -515,8 +551,8 @@ dk_status gram_blocks_umma_launch(dk_ctx* ctx, const void* sr, int m_r, const vo
   if (ks < 1) ks = 1;
   const double cost128 = double((t128 * ks + sms - 1) / sms) * double((nb + ks - 1) / ks);
   const double cost64 = double((t64 + sms - 1) / sms) * double(nb) * 0.92;
-  if (cost128 <= cost64) return gbum::launch_gram<128>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, int(ks), st);
-  return gbum::launch_gram<64>(ctx, sr, m_r, sc, m_c, nb, dp, a64, t64, 1, st);
+  if (cost128 <= cost64) return gbum::launch_gram<128, true>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, int(ks), st);
+  return gbum::launch_gram<64, false>(ctx, sr, m_r, sc, m_c, nb, dp, a64, t64, 1, st);
 }
 
 dk_status block_selfnorm_umma_launch(dk_ctx* ctx, const void* states, int m, int nb, int dp, float* log_norm,
@@ -526,7 +562,7 @@ dk_status block_selfnorm_umma_launch(dk_ctx* ctx, const void* states, int m, int
   if (units > 0x7fffffffLL) return DK_ERR_UNSUPPORTED;
   CUtensorMap t;
   dk_status s = encode_states_map(ctx, &t, states, m, nb, dp, BM);
-  if (s == DK_OK) s = set_smem<128>();
+  if (s == DK_OK) s = set_smem<128, true>();
   if (s != DK_OK) return s;
   float* g2 = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&g2), size_t(nb) * size_t(m) * sizeof(float), st) != cudaSuccess)
@@ -534,8 +570,8 @@ dk_status block_selfnorm_umma_launch(dk_ctx* ctx, const void* states, int m, int
   GramArgs a{};
   a.status = ctx->status;
   const int grid = int(units < ctx->sm_count ? units : ctx->sm_count);
-  gram_blocks_umma_kernel<128><<<grid, NTHREADS, Cfg<128>::SMEM, st>>>(t, t, a, nb, dp / 16, 1, int(units), g2, m,
-                                                                      1, nullptr);
+  gram_blocks_umma_kernel<128, true><<<grid, NTHREADS, Cfg<128, true>::SMEM, st>>>(t, t, a, nb, dp / 16, 1, int(units),
+                                                                                  g2, m, 1, nullptr);
   s = launch_status();
   if (s == DK_OK) {
     selfnorm_sum_kernel<<<(m + 255) / 256, 256, 0, st>>>(g2, m, nb, log_norm);
