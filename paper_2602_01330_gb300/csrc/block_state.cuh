@@ -137,66 +137,96 @@ __device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
   return make_float2(hi, e - (hi - s));
 }
 
+constexpr float TWO_PI_HI = 6.28318548202514648438f;    // float(2 pi)
+constexpr float TWO_PI_LO = -1.74845553146951931e-07f;  // 2 pi - TWO_PI_HI
+constexpr float INV_TWO_PI = 0.15915494309189533577f;
+
+// A two-float angle reduced to [-pi, pi] (up to rounding) as a two-float pair: k = round(v / 2 pi),
+// k TWO_PI_HI split exactly into a float and its product error (fmaf), the high part
+// v.x - k TWO_PI_HI exact (the two are within a factor of two: Sterbenz), the rest added to
+// the low part. About 44 bits for |v| up to a few hundred.
+__device__ __forceinline__ float2 ff_reduce_2pi(float2 v) {
+  const float k = rintf(v.x * INV_TWO_PI);
+  const float p = __fmul_rn(k, TWO_PI_HI);  // _rn: no contraction into an FMA
+  const float pe = fmaf(k, TWO_PI_HI, -p);
+  const float s = __fsub_rn(v.x, p);
+  const float lo = (v.y - pe) - k * TWO_PI_LO;
+  const float hi = s + lo;
+  return make_float2(hi, lo - (hi - s));
+}
+
+__device__ __forceinline__ float2 ff_neg(float2 v) { return make_float2(-v.x, -v.y); }
+
 // The same state in FP32 for operands that are rounded to split BF16 afterwards (about 17
-// significant bits). The tables are built in FP64 as above, and each entry is then reduced to
-// [-pi, pi] and kept as a two-float pair; the phase of an amplitude, a sum of hb + 2 reduced
-// entries, is added in two-float arithmetic, reduced once more and passed to sincosf (angle
-// error ~1e-7 rad, as for an FP64 phase rounded to FP32, at a fraction of the FP64 work); the
-// butterflies and the phase multiplications run in FP32 (relative error ~1e-7 per amplitude,
-// far below the split's 2^-18 ~ 4e-6).
+// significant bits). GB300's FP64 rate is a small fraction of its FP32 rate, so only the
+// b + b(b-1)/2 angles of the block (angle_scale x_q / 2 and (pi - x_q)(pi - x_r)) are formed in
+// FP64, each reduced to [-pi, pi] and kept as a two-float pair; the tables are then summed in
+// two-float arithmetic and reduced again, and an amplitude's phase, hb + 2 table entries, is
+// added the same way, reduced once more and passed to sincosf (angle error ~2e-7 rad, the
+// class of an FP64 phase rounded to FP32); the butterflies and the phase multiplications run
+// in FP32 (relative error ~1e-7 per amplitude, far below the split's 2^-18 ~ 4e-6).
 template <class Sync = CtaSync>
 __device__ inline void build_f32(float2* psi, float2* ph, Coeffs& C, const float* xb, int bl, int reps,
                                  double angle_scale, int pairs_kind, int tid, int nt, Sync sync = Sync()) {
   const int dim = 1 << bl;
   const int hb = bl >> 1, lb = bl - hb;
-  if (tid < bl) C.hq[tid] = 0.5 * angle_scale * double(xb[tid]);
-  for (int e = tid; e < MAXB * MAXB; e += nt) {
-    const int q = e / MAXB, r = e % MAXB;
-    const bool on = q < bl && r < bl && q < r &&
-                    (pairs_kind == DK_ENT_FULL || (pairs_kind == DK_ENT_CHAIN && r == q + 1));
-    C.jq[q][r] = on ? (PI_D - double(xb[q])) * (PI_D - double(xb[r])) : 0.0;
-  }
-  sync();
   constexpr double TWO_PI = 6.283185307179586476925;
-  // an FP64 table entry reduced to [-pi, pi] as a two-float pair, stored in its own slot
+  // an FP64 angle reduced to [-pi, pi] as a two-float pair
   auto reduced = [](double v) {
     const double r = v - TWO_PI * rint(v * (1.0 / TWO_PI));
     const float hi = float(r);
     return make_float2(hi, float(r - double(hi)));
   };
+  // each two-float value sits in the 8-byte slot of the FP64 value it replaces
+  float2* h2 = reinterpret_cast<float2*>(C.hq);
+  float2* j2 = reinterpret_cast<float2*>(&C.jq[0][0]);
   float2* ta2 = reinterpret_cast<float2*>(C.ta);
   float2* tb2 = reinterpret_cast<float2*>(C.tb);
   float2* tv2 = reinterpret_cast<float2*>(&C.tv[0][0]);
+  if (tid < bl) h2[tid] = reduced(0.5 * angle_scale * double(xb[tid]));
+  for (int e = tid; e < MAXB * MAXB; e += nt) {
+    const int q = e / MAXB, r = e % MAXB;
+    const bool on = q < bl && r < bl && q < r &&
+                    (pairs_kind == DK_ENT_FULL || (pairs_kind == DK_ENT_CHAIN && r == q + 1));
+    j2[e] = on ? reduced((PI_D - double(xb[q])) * (PI_D - double(xb[r]))) : make_float2(0.0f, 0.0f);
+  }
+  sync();
+  // tables: z of qubit q (q < hb) is bit hb-1-q of zH; of qubit hb+t is bit lb-1-t of zL
   for (int e = tid; e < (1 << hb); e += nt) {
-    double a = 0.0;
+    float2 a = make_float2(0.0f, 0.0f);
     for (int q = 0; q < hb; ++q) {
-      const double zq = ((e >> (hb - 1 - q)) & 1) ? -1.0 : 1.0;
-      double s = C.hq[q];
-      for (int r = q + 1; r < hb; ++r) s += ((e >> (hb - 1 - r)) & 1) ? -C.jq[q][r] : C.jq[q][r];
-      a += zq * s;
+      float2 s = h2[q];
+      for (int r = q + 1; r < hb; ++r) {
+        const float2 j = j2[q * MAXB + r];
+        s = ff_add(s, ((e >> (hb - 1 - r)) & 1) ? ff_neg(j) : j);
+      }
+      a = ff_add(a, ((e >> (hb - 1 - q)) & 1) ? ff_neg(s) : s);
     }
-    ta2[e] = reduced(a);
+    ta2[e] = ff_reduce_2pi(a);
   }
   for (int e = tid; e < (1 << lb); e += nt) {
-    double bsum = 0.0;
+    float2 bsum = make_float2(0.0f, 0.0f);
     for (int t = 0; t < lb; ++t) {
       const int q = hb + t;
-      const double zq = ((e >> (lb - 1 - t)) & 1) ? -1.0 : 1.0;
-      double s = C.hq[q];
-      for (int u = t + 1; u < lb; ++u) s += ((e >> (lb - 1 - u)) & 1) ? -C.jq[q][hb + u] : C.jq[q][hb + u];
-      bsum += zq * s;
+      float2 s = h2[q];
+      for (int u = t + 1; u < lb; ++u) {
+        const float2 j = j2[q * MAXB + hb + u];
+        s = ff_add(s, ((e >> (lb - 1 - u)) & 1) ? ff_neg(j) : j);
+      }
+      bsum = ff_add(bsum, ((e >> (lb - 1 - t)) & 1) ? ff_neg(s) : s);
     }
-    tb2[e] = reduced(bsum);
+    tb2[e] = ff_reduce_2pi(bsum);
     for (int q = 0; q < hb; ++q) {
-      double v = 0.0;
-      for (int t = 0; t < lb; ++t) v += ((e >> (lb - 1 - t)) & 1) ? -C.jq[q][hb + t] : C.jq[q][hb + t];
-      tv2[e * MAXH + q] = reduced(v);
+      float2 v = make_float2(0.0f, 0.0f);
+      for (int t = 0; t < lb; ++t) {
+        const float2 j = j2[q * MAXB + hb + t];
+        v = ff_add(v, ((e >> (lb - 1 - t)) & 1) ? ff_neg(j) : j);
+      }
+      tv2[e * MAXH + q] = ff_reduce_2pi(v);
     }
   }
   sync();
   const float amp = exp2f(-0.5f * float(bl));
-  constexpr float TWO_PI_HI = 6.28318548202514648438f;             // float(2 pi)
-  constexpr float TWO_PI_LO = -1.74845553146951931e-07f;           // 2 pi - TWO_PI_HI
   for (int e = tid; e < dim; e += nt) {
     const int zh = e >> lb, zl = e & ((1 << lb) - 1);
     float2 phi = ff_add(ta2[zh], tb2[zl]);
@@ -205,7 +235,7 @@ __device__ inline void build_f32(float2* psi, float2* ph, Coeffs& C, const float
       phi = ff_add(phi, ((zh >> (hb - 1 - q)) & 1) ? make_float2(-v.x, -v.y) : v);
     }
     // |phi| <= (hb + 2) pi: one more reduction, k = round(phi / 2 pi) <= 4 in magnitude
-    const float k = rintf(phi.x * 0.15915494309189533577f);
+    const float k = rintf(phi.x * INV_TWO_PI);
     const float red = fmaf(-k, TWO_PI_LO, fmaf(-k, TWO_PI_HI, phi.x)) + phi.y;  // in [-pi, pi] up to rounding
     float sn, cs;
     sincosf(-red, &sn, &cs);
