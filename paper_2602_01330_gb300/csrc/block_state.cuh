@@ -126,119 +126,88 @@ __device__ inline void build(double2* psi, double2* ph, Coeffs& C, const float* 
   }
 }
 
-// Two-float sum a + b of unevaluated pairs (hi, lo) (Knuth's two-sum of the high parts, the
-// low parts added to the error, then renormalised): about 44 significant bits.
-__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
-  const float s = a.x + b.x;
-  const float bb = s - a.x;
-  float e = (a.x - (s - bb)) + (b.x - bb);
-  e += a.y + b.y;
-  const float hi = s + e;
-  return make_float2(hi, e - (hi - s));
+// An angle in FP64 as an unsigned 32-bit count of 2^-32 turns (angle / 2 pi modulo 1): sums
+// of such counts with wraparound are sums of angles modulo 2 pi, exact but for the rounding
+// of each term (2^-33 turns, 7e-10 rad).
+__device__ __forceinline__ uint32_t turns32(double angle) {
+  const double t = angle * (1.0 / 6.283185307179586476925);
+  return static_cast<uint32_t>(static_cast<long long>(rint((t - floor(t)) * 4294967296.0)));
 }
-
-constexpr float TWO_PI_HI = 6.28318548202514648438f;    // float(2 pi)
-constexpr float TWO_PI_LO = -1.74845553146951931e-07f;  // 2 pi - TWO_PI_HI
-constexpr float INV_TWO_PI = 0.15915494309189533577f;
-
-// A two-float angle reduced to [-pi, pi] (up to rounding) as a two-float pair: k = round(v / 2 pi),
-// k TWO_PI_HI split exactly into a float and its product error (fmaf), the high part
-// v.x - k TWO_PI_HI exact (the two are within a factor of two: Sterbenz), the rest added to
-// the low part. About 44 bits for |v| up to a few hundred.
-__device__ __forceinline__ float2 ff_reduce_2pi(float2 v) {
-  const float k = rintf(v.x * INV_TWO_PI);
-  const float p = __fmul_rn(k, TWO_PI_HI);  // _rn: no contraction into an FMA
-  const float pe = fmaf(k, TWO_PI_HI, -p);
-  const float s = __fsub_rn(v.x, p);
-  const float lo = (v.y - pe) - k * TWO_PI_LO;
-  const float hi = s + lo;
-  return make_float2(hi, lo - (hi - s));
-}
-
-__device__ __forceinline__ float2 ff_neg(float2 v) { return make_float2(-v.x, -v.y); }
 
 // The same state in FP32 for operands that are rounded to split BF16 afterwards (about 17
 // significant bits). GB300's FP64 rate is a small fraction of its FP32 rate, so only the
 // b + b(b-1)/2 angles of the block (angle_scale x_q / 2 and (pi - x_q)(pi - x_r)) are formed in
-// FP64, each reduced to [-pi, pi] and kept as a two-float pair; the tables are then summed in
-// two-float arithmetic and reduced again, and an amplitude's phase, hb + 2 table entries, is
-// added the same way, reduced once more and passed to sincosf (angle error ~2e-7 rad, the
-// class of an FP64 phase rounded to FP32); the butterflies and the phase multiplications run
-// in FP32 (relative error ~1e-7 per amplitude, far below the split's 2^-18 ~ 4e-6).
+// FP64; each becomes a 32-bit turn count (turns32), the tables are integer sums of counts and
+// an amplitude's phase is hb + 2 integer additions, all modulo 2 pi by wraparound (error
+// under 1e-8 rad); the count, read as a signed fraction of a half turn, goes to sincospif
+// (angle error ~2e-7 rad from its rounding to FP32, the class of an FP64 phase rounded to
+// FP32); the butterflies and the phase multiplications run in FP32 (relative error ~1e-7 per
+// amplitude, far below the split's 2^-18 ~ 4e-6).
 template <class Sync = CtaSync>
 __device__ inline void build_f32(float2* psi, float2* ph, Coeffs& C, const float* xb, int bl, int reps,
                                  double angle_scale, int pairs_kind, int tid, int nt, Sync sync = Sync()) {
   const int dim = 1 << bl;
   const int hb = bl >> 1, lb = bl - hb;
-  constexpr double TWO_PI = 6.283185307179586476925;
-  // an FP64 angle reduced to [-pi, pi] as a two-float pair
-  auto reduced = [](double v) {
-    const double r = v - TWO_PI * rint(v * (1.0 / TWO_PI));
-    const float hi = float(r);
-    return make_float2(hi, float(r - double(hi)));
-  };
-  // each two-float value sits in the 8-byte slot of the FP64 value it replaces
-  float2* h2 = reinterpret_cast<float2*>(C.hq);
-  float2* j2 = reinterpret_cast<float2*>(&C.jq[0][0]);
-  float2* ta2 = reinterpret_cast<float2*>(C.ta);
-  float2* tb2 = reinterpret_cast<float2*>(C.tb);
-  float2* tv2 = reinterpret_cast<float2*>(&C.tv[0][0]);
-  if (tid < bl) h2[tid] = reduced(0.5 * angle_scale * double(xb[tid]));
+  // each count sits in the 8-byte slot of the FP64 value it replaces
+  auto slot = [](double* p, int i) -> uint32_t& { return *reinterpret_cast<uint32_t*>(p + i); };
+  double* hq = C.hq;
+  double* jq = &C.jq[0][0];
+  double* tv = &C.tv[0][0];
+  if (tid < bl) slot(hq, tid) = turns32(0.5 * angle_scale * double(xb[tid]));
   for (int e = tid; e < MAXB * MAXB; e += nt) {
     const int q = e / MAXB, r = e % MAXB;
     const bool on = q < bl && r < bl && q < r &&
                     (pairs_kind == DK_ENT_FULL || (pairs_kind == DK_ENT_CHAIN && r == q + 1));
-    j2[e] = on ? reduced((PI_D - double(xb[q])) * (PI_D - double(xb[r]))) : make_float2(0.0f, 0.0f);
+    slot(jq, e) = on ? turns32((PI_D - double(xb[q])) * (PI_D - double(xb[r]))) : 0u;
   }
   sync();
   // tables: z of qubit q (q < hb) is bit hb-1-q of zH; of qubit hb+t is bit lb-1-t of zL
   for (int e = tid; e < (1 << hb); e += nt) {
-    float2 a = make_float2(0.0f, 0.0f);
+    uint32_t a = 0u;
     for (int q = 0; q < hb; ++q) {
-      float2 s = h2[q];
+      uint32_t s = slot(hq, q);
       for (int r = q + 1; r < hb; ++r) {
-        const float2 j = j2[q * MAXB + r];
-        s = ff_add(s, ((e >> (hb - 1 - r)) & 1) ? ff_neg(j) : j);
+        const uint32_t j = slot(jq, q * MAXB + r);
+        s += ((e >> (hb - 1 - r)) & 1) ? 0u - j : j;
       }
-      a = ff_add(a, ((e >> (hb - 1 - q)) & 1) ? ff_neg(s) : s);
+      a += ((e >> (hb - 1 - q)) & 1) ? 0u - s : s;
     }
-    ta2[e] = ff_reduce_2pi(a);
+    slot(C.ta, e) = a;
   }
   for (int e = tid; e < (1 << lb); e += nt) {
-    float2 bsum = make_float2(0.0f, 0.0f);
+    uint32_t bsum = 0u;
     for (int t = 0; t < lb; ++t) {
       const int q = hb + t;
-      float2 s = h2[q];
+      uint32_t s = slot(hq, q);
       for (int u = t + 1; u < lb; ++u) {
-        const float2 j = j2[q * MAXB + hb + u];
-        s = ff_add(s, ((e >> (lb - 1 - u)) & 1) ? ff_neg(j) : j);
+        const uint32_t j = slot(jq, q * MAXB + hb + u);
+        s += ((e >> (lb - 1 - u)) & 1) ? 0u - j : j;
       }
-      bsum = ff_add(bsum, ((e >> (lb - 1 - t)) & 1) ? ff_neg(s) : s);
+      bsum += ((e >> (lb - 1 - t)) & 1) ? 0u - s : s;
     }
-    tb2[e] = ff_reduce_2pi(bsum);
+    slot(C.tb, e) = bsum;
     for (int q = 0; q < hb; ++q) {
-      float2 v = make_float2(0.0f, 0.0f);
+      uint32_t v = 0u;
       for (int t = 0; t < lb; ++t) {
-        const float2 j = j2[q * MAXB + hb + t];
-        v = ff_add(v, ((e >> (lb - 1 - t)) & 1) ? ff_neg(j) : j);
+        const uint32_t j = slot(jq, q * MAXB + hb + t);
+        v += ((e >> (lb - 1 - t)) & 1) ? 0u - j : j;
       }
-      tv2[e * MAXH + q] = ff_reduce_2pi(v);
+      slot(tv, e * MAXH + q) = v;
     }
   }
   sync();
   const float amp = exp2f(-0.5f * float(bl));
   for (int e = tid; e < dim; e += nt) {
     const int zh = e >> lb, zl = e & ((1 << lb) - 1);
-    float2 phi = ff_add(ta2[zh], tb2[zl]);
+    uint32_t phi = slot(C.ta, zh) + slot(C.tb, zl);
     for (int q = 0; q < hb; ++q) {
-      const float2 v = tv2[zl * MAXH + q];
-      phi = ff_add(phi, ((zh >> (hb - 1 - q)) & 1) ? make_float2(-v.x, -v.y) : v);
+      const uint32_t v = slot(tv, zl * MAXH + q);
+      phi += ((zh >> (hb - 1 - q)) & 1) ? 0u - v : v;
     }
-    // |phi| <= (hb + 2) pi: one more reduction, k = round(phi / 2 pi) <= 4 in magnitude
-    const float k = rintf(phi.x * INV_TWO_PI);
-    const float red = fmaf(-k, TWO_PI_LO, fmaf(-k, TWO_PI_HI, phi.x)) + phi.y;  // in [-pi, pi] up to rounding
+    // phi / 2^32 turns = x half turns, x in [-1, 1)
+    const float x = float(static_cast<int>(phi)) * 4.656612873077392578125e-10f;
     float sn, cs;
-    sincosf(-red, &sn, &cs);
+    sincospif(-x, &sn, &cs);
     ph[e] = make_float2(cs, sn);
     psi[e] = make_float2(amp * cs, amp * sn);
   }
