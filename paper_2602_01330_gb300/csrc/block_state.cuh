@@ -37,9 +37,13 @@ struct Coeffs {
   double tv[1 << MAXH][MAXH];    // V_q(zL) for the high qubits q
 };
 
-// Shared memory a block of bl <= b qubits needs: Coeffs, then psi and the phase factors.
+// Shared memory a block of bl <= b qubits needs: Coeffs, then psi and the phase factors
+// (FP64 for build, FP32 for build_f32).
 __host__ __device__ inline size_t smem_bytes(int b) {
   return ((sizeof(Coeffs) + 15) & ~size_t(15)) + 2 * (size_t(1) << b) * sizeof(double2);
+}
+__host__ __device__ inline size_t smem_bytes_f32(int b) {
+  return ((sizeof(Coeffs) + 15) & ~size_t(15)) + 2 * (size_t(1) << b) * sizeof(float2);
 }
 
 // Barrier of the threads that build one block together: a whole CTA or one warp.

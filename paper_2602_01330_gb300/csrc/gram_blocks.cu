@@ -274,11 +274,12 @@ DK_API dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, cons
   if (size_t(nb) * sizeof(float2) > 48 * 1024) return DK_ERR_UNSUPPORTED;  // self-norm staging
   const int kind = fm->entangle ? entangler : -1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t smem = blockstate::smem_bytes(b);
-  if (cudaFuncSetAttribute(gblk::block_states_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-      cudaSuccess)
-    return DK_ERR_CUDA;
   const int split = prec == DK_PREC_BF16X3 ? 1 : 0;
+  if (cudaFuncSetAttribute(gblk::block_states_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(blockstate::smem_bytes(b))) != cudaSuccess)
+    return DK_ERR_CUDA;
+  // the FP32 build of the split form needs half the state storage: twice the CTAs per SM
+  const size_t smem = split ? blockstate::smem_bytes_f32(b) : blockstate::smem_bytes(b);
   gblk::block_states_kernel<<<dim3(nb, m), gblk::BUILD_NT, smem, st>>>(x, m, n, b, fm->reps, double(fm->angle_scale),
                                                                       kind, split, static_cast<float2*>(states));
   dk_status s = launch_status();
