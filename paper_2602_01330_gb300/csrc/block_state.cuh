@@ -147,13 +147,15 @@ __device__ __forceinline__ uint32_t turns32(double angle) {
 // (angle error ~2e-7 rad from its rounding to FP32, the class of an FP64 phase rounded to
 // FP32); the butterflies and the phase multiplications run in FP32 (relative error ~1e-7 per
 // amplitude, far below the split's 2^-18 ~ 4e-6).
-template <class Sync = CtaSync>
-__device__ inline void build_f32(float2* psi, float2* ph, Coeffs& C, const float* xb, int bl, int reps,
-                                 double angle_scale, int pairs_kind, int tid, int nt, Sync sync = Sync()) {
-  const int dim = 1 << bl;
+// each turn count sits in the 8-byte slot of the FP64 value it replaces
+__device__ __forceinline__ uint32_t& slot32(double* p, int i) { return *reinterpret_cast<uint32_t*>(p + i); }
+
+// The turn-count tables of build_f32 (ends with a barrier).
+template <class Sync>
+__device__ inline void tables_f32(Coeffs& C, const float* xb, int bl, double angle_scale, int pairs_kind, int tid,
+                                  int nt, Sync sync) {
   const int hb = bl >> 1, lb = bl - hb;
-  // each count sits in the 8-byte slot of the FP64 value it replaces
-  auto slot = [](double* p, int i) -> uint32_t& { return *reinterpret_cast<uint32_t*>(p + i); };
+  auto slot = [](double* p, int i) -> uint32_t& { return slot32(p, i); };
   double* hq = C.hq;
   double* jq = &C.jq[0][0];
   double* tv = &C.tv[0][0];
@@ -200,16 +202,29 @@ __device__ inline void build_f32(float2* psi, float2* ph, Coeffs& C, const float
     }
   }
   sync();
+}
+
+// Phase of amplitude e from the tables, as x half turns (x in [-1, 1)): hb + 2 integer
+// additions of turn counts.
+__device__ __forceinline__ float phase_x(Coeffs& C, int e, int bl) {
+  const int hb = bl >> 1, lb = bl - hb;
+  const int zh = e >> lb, zl = e & ((1 << lb) - 1);
+  uint32_t phi = slot32(C.ta, zh) + slot32(C.tb, zl);
+  for (int q = 0; q < hb; ++q) {
+    const uint32_t v = slot32(&C.tv[0][0], zl * MAXH + q);
+    phi += ((zh >> (hb - 1 - q)) & 1) ? 0u - v : v;
+  }
+  return float(static_cast<int>(phi)) * 4.656612873077392578125e-10f;
+}
+
+template <class Sync = CtaSync>
+__device__ inline void build_f32(float2* psi, float2* ph, Coeffs& C, const float* xb, int bl, int reps,
+                                 double angle_scale, int pairs_kind, int tid, int nt, Sync sync = Sync()) {
+  const int dim = 1 << bl;
+  tables_f32(C, xb, bl, angle_scale, pairs_kind, tid, nt, sync);
   const float amp = exp2f(-0.5f * float(bl));
   for (int e = tid; e < dim; e += nt) {
-    const int zh = e >> lb, zl = e & ((1 << lb) - 1);
-    uint32_t phi = slot(C.ta, zh) + slot(C.tb, zl);
-    for (int q = 0; q < hb; ++q) {
-      const uint32_t v = slot(tv, zl * MAXH + q);
-      phi += ((zh >> (hb - 1 - q)) & 1) ? 0u - v : v;
-    }
-    // phi / 2^32 turns = x half turns, x in [-1, 1)
-    const float x = float(static_cast<int>(phi)) * 4.656612873077392578125e-10f;
+    const float x = phase_x(C, e, bl);
     float sn, cs;
     sincospif(-x, &sn, &cs);
     ph[e] = make_float2(cs, sn);
@@ -235,6 +250,78 @@ __device__ inline void build_f32(float2* psi, float2* ph, Coeffs& C, const float
     }
     sync();
   }
+}
+
+// build_f32 for blocks of bl = 7 + log2(R) qubits by a CTA of 128 threads, the amplitudes in
+// registers: thread t holds e = 128 j + t (j < R). A Walsh-Hadamard pass takes bits 0-4 of
+// the index by warp shuffles, bits 7 and up inside the thread, and bits 5-6 together as one
+// radix-4 pass through shared memory: three shared-memory accesses per amplitude per
+// repetition instead of 2 bl. Same state as build_f32 up to rounding; psi receives it.
+template <int R>
+__device__ inline void build_f32_regs(float2* psi, float2* ph, Coeffs& C, const float* xb, int reps, double angle_scale,
+                                      int pairs_kind, int tid) {
+  constexpr int NT = 128, DIM = R * NT;
+  constexpr int BL = 7 + (R >= 2) + (R >= 4) + (R >= 8) + (R >= 16) + (R >= 32);
+  static_assert((1 << BL) == DIM, "R is a power of two up to 32");
+  tables_f32(C, xb, BL, angle_scale, pairs_kind, tid, NT, CtaSync());
+  const int lane = tid & 31;
+  const float amp = exp2f(-0.5f * float(BL));
+  float2 v[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int e = j * NT + tid;
+    float sn, cs;
+    sincospif(-phase_x(C, e, BL), &sn, &cs);
+    ph[e] = make_float2(cs, sn);
+    v[j] = make_float2(amp * cs, amp * sn);
+  }
+  constexpr float R2 = 0.70710678118654752440f;
+  for (int rep = 1; rep < reps; ++rep) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const bool upper = (lane >> k) & 1;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const float px = __shfl_xor_sync(0xffffffffu, v[j].x, 1 << k);
+        const float py = __shfl_xor_sync(0xffffffffu, v[j].y, 1 << k);
+        v[j] = upper ? make_float2((px - v[j].x) * R2, (py - v[j].y) * R2)
+                     : make_float2((v[j].x + px) * R2, (v[j].y + py) * R2);
+      }
+    }
+#pragma unroll
+    for (int s = 1; s < R; s <<= 1)
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (!(j & s)) {
+          const float2 a = v[j], b = v[j | s];
+          v[j] = make_float2((a.x + b.x) * R2, (a.y + b.y) * R2);
+          v[j | s] = make_float2((a.x - b.x) * R2, (a.y - b.y) * R2);
+        }
+#pragma unroll
+    for (int j = 0; j < R; ++j) psi[j * NT + tid] = v[j];
+    __syncthreads();
+    for (int g = tid; g < DIM / 4; g += NT) {
+      const int base = ((g >> 5) << 7) | (g & 31);  // bits 5 and 6 clear
+      const float2 a0 = psi[base], a1 = psi[base | 32], a2 = psi[base | 64], a3 = psi[base | 96];
+      const float2 b0 = make_float2(a0.x + a1.x, a0.y + a1.y), b1 = make_float2(a0.x - a1.x, a0.y - a1.y);
+      const float2 b2 = make_float2(a2.x + a3.x, a2.y + a3.y), b3 = make_float2(a2.x - a3.x, a2.y - a3.y);
+      psi[base] = make_float2((b0.x + b2.x) * 0.5f, (b0.y + b2.y) * 0.5f);
+      psi[base | 32] = make_float2((b1.x + b3.x) * 0.5f, (b1.y + b3.y) * 0.5f);
+      psi[base | 64] = make_float2((b0.x - b2.x) * 0.5f, (b0.y - b2.y) * 0.5f);
+      psi[base | 96] = make_float2((b1.x - b3.x) * 0.5f, (b1.y - b3.y) * 0.5f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int e = j * NT + tid;
+      const float2 a = psi[e], w = ph[e];
+      v[j] = make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+    }
+    __syncthreads();  // psi is written again below or in the next repetition
+  }
+#pragma unroll
+  for (int j = 0; j < R; ++j) psi[j * NT + tid] = v[j];
+  __syncthreads();
 }
 
 }  // namespace blockstate

@@ -64,9 +64,23 @@ __device__ __forceinline__ void lg_add(float& lg, float2 g) { lg += log2f(fmaf(g
 // ln|a| from the log2 sum of |a|^2
 __device__ __forceinline__ float half_log_lg(float lg) { return lg * (0.5f * 0.69314718055994530942f); }
 
-// split = 0: complex64 [dpad]; split = 1: the operand form of the tensor-core Grams, same 8
-// bytes per amplitude: per chunk of 16 amplitudes one 128-byte row of four BF16 planes
-// [hi_re | hi_im | lo_re | lo_im] of 16 values each
+// The operand form of the tensor-core Grams, same 8 bytes per amplitude as complex64: per
+// chunk of 16 amplitudes one 128-byte row of four BF16 planes [hi_re | hi_im | lo_re | lo_im]
+// of 16 values each, v ~ hi + lo; zeros past the dim amplitudes of the state.
+__device__ inline void store_split(float2* out, const float2* psf, int dim, int dp) {
+  __nv_bfloat16* pl = reinterpret_cast<__nv_bfloat16*>(out);
+  for (int k = threadIdx.x; k < dp; k += BUILD_NT) {
+    const float vr = k < dim ? psf[k].x : 0.0f, vi = k < dim ? psf[k].y : 0.0f;
+    const __nv_bfloat16 hr = __float2bfloat16_rn(vr), hi = __float2bfloat16_rn(vi);
+    __nv_bfloat16* row = pl + (k >> 4) * 64 + (k & 15);
+    row[0] = hr;
+    row[16] = hi;
+    row[32] = __float2bfloat16_rn(vr - __bfloat162float(hr));
+    row[48] = __float2bfloat16_rn(vi - __bfloat162float(hi));
+  }
+}
+
+// split = 0: complex64 [dpad]; split = 1: the split-BF16 operand form (store_split)
 __global__ void __launch_bounds__(BUILD_NT) block_states_kernel(const float* __restrict__ x, int m, int n, int b,
                                                                 int reps, double angle_scale, int pairs_kind,
                                                                 int split, float2* __restrict__ states) {
@@ -92,16 +106,31 @@ __global__ void __launch_bounds__(BUILD_NT) block_states_kernel(const float* __r
   float2* phf = psf + (1 << b);
   blockstate::build_f32(psf, phf, C, x + size_t(i) * n + start, bl, reps, angle_scale, pairs_kind, threadIdx.x,
                         BUILD_NT);
-  __nv_bfloat16* pl = reinterpret_cast<__nv_bfloat16*>(out);
-  for (int k = threadIdx.x; k < dp; k += BUILD_NT) {
-    const float vr = k < dim ? psf[k].x : 0.0f, vi = k < dim ? psf[k].y : 0.0f;
-    const __nv_bfloat16 hr = __float2bfloat16_rn(vr), hi = __float2bfloat16_rn(vi);
-    __nv_bfloat16* row = pl + (k >> 4) * 64 + (k & 15);
-    row[0] = hr;
-    row[16] = hi;
-    row[32] = __float2bfloat16_rn(vr - __bfloat162float(hr));
-    row[48] = __float2bfloat16_rn(vi - __bfloat162float(hi));
-  }
+  store_split(out, psf, dim, dp);
+}
+
+// The split-BF16 states of blocks of b = 7 + log2(R) qubits, built with the amplitudes in
+// registers (blockstate::build_f32_regs); a shorter last block takes the shared-memory form.
+template <int R>
+__global__ void __launch_bounds__(BUILD_NT) block_states_split_kernel(const float* __restrict__ x, int m, int n,
+                                                                      int b, int reps, double angle_scale,
+                                                                      int pairs_kind, float2* __restrict__ states) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  blockstate::Coeffs& C = *reinterpret_cast<blockstate::Coeffs*>(raw);
+  float2* psf = reinterpret_cast<float2*>(raw + ((sizeof(blockstate::Coeffs) + 15) & ~size_t(15)));
+  float2* phf = psf + (1 << b);
+  const int blk = blockIdx.x, i = blockIdx.y;
+  const int start = blk * b;
+  const int bl = min(b, n - start);
+  const int dp = dpad_of(b);
+  float2* out = states + (size_t(blk) * m + i) * dp;
+  if (bl == b)
+    blockstate::build_f32_regs<R>(psf, phf, C, x + size_t(i) * n + start, reps, angle_scale, pairs_kind,
+                                  threadIdx.x);
+  else
+    blockstate::build_f32(psf, phf, C, x + size_t(i) * n + start, bl, reps, angle_scale, pairs_kind, threadIdx.x,
+                          BUILD_NT);
+  store_split(out, psf, 1 << bl, dp);
 }
 
 // One CTA per sample: thread B forms <psi_B|psi_B> with the Gram kernel's sequential
@@ -275,14 +304,35 @@ DK_API dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, cons
   const int kind = fm->entangle ? entangler : -1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int split = prec == DK_PREC_BF16X3 ? 1 : 0;
-  if (cudaFuncSetAttribute(gblk::block_states_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(blockstate::smem_bytes(b))) != cudaSuccess)
-    return DK_ERR_CUDA;
-  // the FP32 build of the split form needs half the state storage: twice the CTAs per SM
-  const size_t smem = split ? blockstate::smem_bytes_f32(b) : blockstate::smem_bytes(b);
-  gblk::block_states_kernel<<<dim3(nb, m), gblk::BUILD_NT, smem, st>>>(x, m, n, b, fm->reps, double(fm->angle_scale),
-                                                                      kind, split, static_cast<float2*>(states));
-  dk_status s = launch_status();
+  dk_status s = DK_OK;
+  if (split && b >= 7) {
+    // the FP32 build of the split form needs half the state storage: twice the CTAs per SM
+    const size_t smem = blockstate::smem_bytes_f32(b);
+    auto launch = [&](auto kern) {
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+        return DK_ERR_CUDA;
+      kern<<<dim3(nb, m), gblk::BUILD_NT, smem, st>>>(x, m, n, b, fm->reps, double(fm->angle_scale), kind,
+                                                      static_cast<float2*>(states));
+      return launch_status();
+    };
+    switch (b) {
+      case 7: s = launch(gblk::block_states_split_kernel<1>); break;
+      case 8: s = launch(gblk::block_states_split_kernel<2>); break;
+      case 9: s = launch(gblk::block_states_split_kernel<4>); break;
+      case 10: s = launch(gblk::block_states_split_kernel<8>); break;
+      case 11: s = launch(gblk::block_states_split_kernel<16>); break;
+      default: s = launch(gblk::block_states_split_kernel<32>); break;
+    }
+  } else {
+    if (cudaFuncSetAttribute(gblk::block_states_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(blockstate::smem_bytes(b))) != cudaSuccess)
+      return DK_ERR_CUDA;
+    const size_t smem = split ? blockstate::smem_bytes_f32(b) : blockstate::smem_bytes(b);
+    gblk::block_states_kernel<<<dim3(nb, m), gblk::BUILD_NT, smem, st>>>(x, m, n, b, fm->reps,
+                                                                        double(fm->angle_scale), kind, split,
+                                                                        static_cast<float2*>(states));
+    s = launch_status();
+  }
   if (s != DK_OK || !log_norm) return s;
   if (split)
     return ctx->block_form == DK_BLOCK_MMA_SYNC

@@ -170,13 +170,15 @@ def _check_tol(out, lref, kc_ref, w, tol):
 
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("m,n,b,reps,ent", [(70, 40, 8, 2, "full"), (70, 50, 7, 2, "chain"), (70, 36, 12, 2, "full"),
-                                            (70, 9, 2, 3, "full"), (300, 16, 8, 2, "full"), (2000, 16, 8, 2, "full")])
+                                            (70, 9, 2, 3, "full"), (300, 16, 8, 2, "full"), (2000, 16, 8, 2, "full"),
+                                            (70, 27, 9, 3, "full"), (70, 25, 11, 2, "chain")])
 def test_gram_blocks_bf16x3_tensor_cores(dk, m, n, b, reps, ent, form):
     """Split-BF16 tensor-core forms (tcgen05 and mma.sync) against the oracle with the
     mixed-precision tolerance 1e-4 on K_q and K (K_c stays FP32, 1e-6): one ragged tile (70
     samples), several (300) and a full-size Gram (2000 = 15 x 128 + 80); short last blocks
-    (n = 50, 9); rows; exact unit diagonal from the self-norms of the same MMA sequence;
-    exact symmetry."""
+    (n = 50, 9, 25); blocks of 7 to 12 qubits (every register form of the state build) and
+    of 2; rows; exact unit diagonal from the self-norms of the same MMA sequence; exact
+    symmetry."""
     dualk, ctx, torch = dk
     from oracle import gram as og
     from paper_2602_01330_gb300 import synthetic
