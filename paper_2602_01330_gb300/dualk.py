@@ -329,7 +329,7 @@ class BlockStates:
     block: int
     log_norm: torch.Tensor  # float32, m
     x: torch.Tensor         # float32 m x n features
-    prec: int = 0           # DK_PREC_F32 (complex64) or DK_PREC_BF16X3 (split planes)
+    prec: int = 0           # DK_PREC_F32 (complex64) or DK_PREC_BF16X3 (split-BF16 chunk rows)
 
 
 def block_states(ctx: Context, x: torch.Tensor, fmap: FeatureMap, entangler: int = DK_ENT_FULL,

@@ -79,6 +79,7 @@ def test_error_strings_and_host_validation(lib):
     assert lib.dk_gram_tile(None, None, 1, None, 1, 1, 4, 0, 0, 1, 0, 1, None, None, None, None,
                             ctypes.c_float(1.0), ctypes.c_float(0.5), 0, None, None, None, None,
                             ctypes.c_int64(1), 0, None) == 1
+    assert lib.dk_set_block_gram_form(None, 0) == 1  # DK_BLOCK_TCGEN05 on no context
 
 
 def test_create_without_device_reports_no_device(lib):
