@@ -4,25 +4,29 @@
 // For block B and a tile of 128 row samples x BN column samples the factor of the overlap
 // is the complex GEMM G_B = A^H B over K = 2^b amplitudes, taken with split-BF16 operands
 // (v ~ hi + lo) and FP32 accumulation as lo.hi + hi.lo + hi.hi (bf16x3, the precision of
-// gram_blocks_tc.cu): per 16 amplitudes twelve 128 x BN x 16 MMAs, six into Re G
-// (ar br + ai bi) and six into Im G (ar bi - ai br, the minus through the instruction's
-// negate-B bit).
+// gram_blocks_tc.cu). Two instruction forms (Cfg):
+//   wide (128 x 128 tiles): per 16 amplitudes six 128 x 256 x 16 MMAs, D1 = a_re [b_re; b_im]
+//             and D2 = a_im [b_re; b_im], the 256 B rows being the tile's column rows and a
+//             second copy of them one plane further on; Re = D1_re + D2_im, Im = D1_im - D2_re;
+//   narrow (128 x 64 tiles): twelve 128 x 64 x 16 MMAs, six into Re G (ar br + ai bi) and six
+//             into Im G (ar bi - ai br, the minus through the instruction's negate-B bit).
 //
-// Warp roles of a CTA (one CTA per SM, persistent over its tiles):
-//   warp 0    one thread issues the TMA loads: per (tile, block, 16-amplitude chunk) one
+// Warp roles of a CTA (one CTA per SM, persistent over its work items):
+//   warp 0    one thread issues the TMA loads: per (item, block, 16-amplitude chunk) one
 //             128-byte row per sample (the chunk's four BF16 planes, which dk_block_states
-//             interleaves in HBM) for the 128 row and BN column samples, 128-byte swizzle,
-//             into a ring of NSTAGES stages (full / empty mbarriers);
-//   warp 1    allocates the tensor memory, two accumulators of [Re | Im] (4 BN columns), and
-//             one thread issues the MMAs; tcgen05.commit releases each stage to the loader
-//             and hands a finished block's accumulator to the epilogue;
+//             interleaves in HBM) for the 128 row and BN column samples (twice for the wide
+//             form), 128-byte swizzle, into a ring of stages (full / empty mbarriers);
+//   warp 1    allocates the tensor memory (512 columns wide, 256 narrow) and one thread
+//             issues the MMAs; tcgen05.commit releases each stage to the loader and hands a
+//             finished block's accumulator to the epilogue;
 //   warps 2-9 the epilogue: thread (TMEM lane r, column half h) reads BN/2 columns of Re and
-//             Im of row r, adds log2 |G_B|^2 to its running sums and frees the accumulator,
-//             which the MMA thread refills two blocks later (so block B's epilogue runs under
-//             the MMAs of block B + 1); after the last block it writes the tile through the
-//             common epilogue (write_pair) with the squared distances of the RBF kernel, which
-//             rbf_d2_kernel computed beforehand (feature rows staged through shared memory, the
-//             per-pair Kahan FP32 sum of every Gram kernel).
+//             Im of row r, adds log2 |G_B|^2 to its running sums and frees the accumulator
+//             (narrow: two accumulators, so block B's epilogue runs under the MMAs of block
+//             B + 1); after an item's last block it writes the tile through the common
+//             epilogue (write_pair) with the squared distances of the RBF kernel, which
+//             rbf_d2_kernel computed beforehand (feature rows staged through shared memory,
+//             the per-pair Kahan FP32 sum of every Gram kernel), or, when a rectangular
+//             tile's blocks are split over several items, its partial log2 sums.
 //
 // Self-norms (diagonal mode): a unit is one (diagonal tile, block) pair with A = B in shared
 // memory. The diagonal tile of the symmetric Gram issues the same instructions on the same
