@@ -374,6 +374,32 @@ def test_block_gram_rows_split_and_narrow_tiles(dk, case):
     ctx.sync_status()
 
 
+@pytest.mark.parametrize("form", FORMS)
+def test_block_gram_symmetric_offset_diagonal(dk, form):
+    """A symmetric block starting at sample 50 (not a multiple of the 128-sample tile): each
+    sample's diagonal element sits at another position of its Gram tile than of its
+    self-norm tile, and K_q(x, x) = 1 must still hold exactly; off the diagonal the block
+    equals the same entries of the full Gram to 1e-6 relative in log K_q."""
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    x = _dev(torch, synthetic.fmnist_like(600, 0, 40)["x_train"])
+    fm = dualk.FeatureMap(reps=2, block=10)
+    with _form(dualk, ctx, form):
+        s = dualk.block_states(ctx, x, fm, dualk.DK_ENT_FULL, prec=dualk.DK_PREC_BF16X3)
+        full = dualk.gram_blocks(ctx, s, w=1.0, want=("logkq",))["logkq"]
+        sub = torch.full((300, 300), -7.0, device="cuda")
+        _check_call(dualk, dualk._lib().dk_gram_blocks(
+            ctx.handle, dualk._ptr(s.data), 600, dualk._ptr(s.data), 600, 40, 10, 50, 300, 50, 300,
+            dualk._ptr(s.log_norm), dualk._ptr(s.log_norm), None, None, 0.0, 1.0, dualk.DK_PREC_BF16X3, None,
+            None, None, dualk._ptr(sub), 300, 1, dualk._stream(None)))
+        torch.cuda.synchronize()
+    sub, full = sub.cpu().numpy().astype(np.float64), full.cpu().numpy().astype(np.float64)
+    assert np.all(np.diag(sub) == 0.0)
+    ref = full[50:350, 50:350]
+    assert np.max(np.abs(sub - ref) / np.maximum(1.0, np.abs(ref))) <= 1e-6
+    ctx.sync_status()
+
+
 def _check_call(dualk, status):
     assert status == 0, status
 
