@@ -281,9 +281,15 @@ dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, const dk_fm
  *   k_out, kq_out, kc_out, logkq_out  nrows x ncols float32 (device, any may be NULL, not
  *                              all), row stride ld; symmetric (rows == cols, same range)
  *                              computes each unordered pair once and writes both entries
+ * Scratch: the tcgen05 form of DK_PREC_BF16X3 takes stream-ordered device memory
+ * (cudaMallocAsync / cudaFreeAsync on `stream`, from the device's default pool): nrows *
+ * ncols * 4 bytes for the RBF distances when K_c is needed, and up to 8 * nrows * ncols * 4
+ * for the partial sums of a rectangular block split over its blocks; the other forms and
+ * every chain-path call allocate nothing.
  * Errors: DK_ERR_ARG (NULL inputs, ranges outside the sample counts, ld < ncols, no
  *         output, symmetric with different rows and columns, K_c needed without x),
- *         DK_ERR_UNSUPPORTED (block, prec neither F32 nor BF16X3), DK_ERR_CUDA. */
+ *         DK_ERR_UNSUPPORTED (block, prec neither F32 nor BF16X3), DK_ERR_CUDA (also when
+ *         the scratch cannot be had). */
 dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows, const void* states_cols, int m_cols,
                          int n, int block, int row0, int nrows, int col0, int ncols, const float* lnorm_rows,
                          const float* lnorm_cols, const float* x_rows, const float* x_cols, float gamma, float w,
