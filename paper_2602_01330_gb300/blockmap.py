@@ -78,7 +78,7 @@ def _run_benchmark(ctx, m, m_test, n, block, reps, entangler, w, iters, prec, fo
     achieved = gram_flops(m, m, n, block, True) / (t["gram_ms"] * 1e-3) / 1e12
     if prec == dualk.DK_PREC_BF16X3:
         bf16, src = bf16_peak_tflops()
-        kern = ("gram_blocks_umma_kernel<128> (symmetric Gram, tcgen05 bf16x3)" if form == dualk.DK_BLOCK_TCGEN05
+        kern = ("gram_blocks_umma_kernel<128, wide> (symmetric Gram, tcgen05 bf16x3, N = 256 MMAs)" if form == dualk.DK_BLOCK_TCGEN05
                 else "gram_blocks_tc_kernel (symmetric Gram, mma.sync bf16x3)")
         roof = {"bound": "tensor", "kernel": kern,
                 "achieved": achieved, "peak": bf16 / 3, "unit": "TFLOP/s (FP32-equivalent)",
