@@ -92,6 +92,8 @@ def test_gram_blocks_vs_block_statevectors(dk, n, b, reps, ent):
     kq = g["kq"].cpu().numpy()
     assert np.all(np.diag(kq) == 1.0)
     assert np.array_equal(kq, kq.T)
+    # positive semi-definite to the FP32 bound lambda_min >= -m 1e-6
+    assert np.linalg.eigvalsh(kq.astype(np.float64)).min() >= -kq.shape[0] * 1e-6
     ctx.sync_status()
 
 
@@ -198,6 +200,8 @@ def test_gram_blocks_bf16x3_tensor_cores(dk, m, n, b, reps, ent, form):
     kq = g["kq"].cpu().numpy()
     assert np.all(np.diag(kq) == 1.0)
     assert np.array_equal(kq, kq.T)
+    # positive semi-definite to the mixed-precision bound lambda_min >= -m 1e-4
+    assert np.linalg.eigvalsh(kq.astype(np.float64)).min() >= -m * 1e-4
     ctx.sync_status()
 
 
