@@ -4,7 +4,7 @@
 Workload (one step, all of the hot path): Fashion-MNIST-shaped synthetic data at d = 784
 features (raw pixels, one qubit per feature), 2000 training + 500 test samples, ZZ-chain
 map with reps = 2 (bond chi = 4), complex64 / FP32:
-  MPS build of the 2000 training and the 500 test samples (FP64 QR canonicalisation),
+  MPS build of the 2000 training and the 500 test samples (closed-form sites, FP32 QR sweep),
   the symmetric 2000 x 2000 Gram with the fused RBF kernel and mix (w = 0.5; K, K_q,
   K_c and log K_q written), and the 500 x 2000 dual-kernel rows.
 Unit of work: one entry x qubit (one pair through one site). Entries per step =

@@ -98,6 +98,7 @@ def rbf(x_rows, x_cols, gamma: float):
 
 
 def rbf_pairs(x_rows, x_cols, i_idx, j_idx, gamma: float):
+    """K_c for the listed pairs only: exp(-gamma ||x_rows[i] - x_cols[j]||^2) (Eq. 3)."""
     a = np.asarray(x_rows, dtype=np.float64)[np.asarray(i_idx)]
     b = np.asarray(x_cols, dtype=np.float64)[np.asarray(j_idx)]
     diff = a - b

@@ -121,10 +121,3 @@ def to_statevector(sites, sample: int = 0) -> np.ndarray:
         v = np.einsum("pa,asr->psr", v, t).reshape(-1, t.shape[2])
     return v.reshape(-1)
 
-
-def schmidt_values(sites, sample: int, bond: int) -> np.ndarray:
-    """Singular values across the cut between sites bond-1 and bond of one sample (small n)."""
-    psi = to_statevector(sites, sample)
-    n = len(sites)
-    mat = psi.reshape(2 ** bond, 2 ** (n - bond))
-    return np.linalg.svd(mat, compute_uv=False)

@@ -478,14 +478,13 @@ dk_status encode_states_map(dk_ctx* ctx, CUtensorMap* map, const void* states, i
   return r == CUDA_SUCCESS ? DK_OK : DK_ERR_CUDA;
 }
 
+// The shared-memory opt-in is a per-device, per-function attribute: it is set before every
+// launch (a cheap host call), so no process-wide flag has to track devices or threads.
 template <int BN, bool WIDE>
 dk_status set_smem() {
-  static bool done = false;
-  if (done) return DK_OK;
   if (cudaFuncSetAttribute(gram_blocks_umma_kernel<BN, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(Cfg<BN, WIDE>::SMEM)) != cudaSuccess)
     return DK_ERR_CUDA;
-  done = true;
   return DK_OK;
 }
 

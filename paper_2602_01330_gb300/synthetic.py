@@ -103,3 +103,16 @@ def uniform_angles(m: int, n: int, seed: int = 0, dtype=np.float64) -> np.ndarra
     """m x n features drawn uniformly from [0, pi] (the tiny n=8 check case uses seed 0)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(0.0, np.pi, size=(m, n)).astype(dtype)
+
+
+def near_copies(x: np.ndarray, sigma_lo: float, sigma_hi: float, seed: int) -> np.ndarray:
+    """Perturbed copies of the rows of x: row i plus N(0, sigma_i^2) noise on every feature,
+    clipped to [0, pi], with sigma_i log-uniform in [sigma_lo, sigma_hi] (seeded). Pairs of
+    a row and its copy have quantum kernel values spread from near 0 to near 1 even at
+    hundreds of qubits, where independent samples give values far below 1e-100. Returns
+    the dtype of x."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = x.shape[0]
+    sigma = np.exp(rng.uniform(np.log(sigma_lo), np.log(sigma_hi), size=m))
+    y = x.astype(np.float64) + rng.normal(0.0, 1.0, size=x.shape) * sigma[:, None]
+    return np.clip(y, 0.0, np.pi).astype(x.dtype)

@@ -157,6 +157,22 @@ def rbf_vs_library(seed: int = 16) -> float:
     return float(np.max(np.abs(gram.rbf(a, b, gamma) - ref)))
 
 
+def rbf_pairs_vs_library(seed: int = 19) -> float:
+    """The oracle's pair-list RBF (used by the CPU baseline) against scipy's squared
+    Euclidean cdist on the same pairs: random (i, j) of a rectangular set, i = j, and pairs
+    listed out of order and repeated."""
+    x = synthetic.fmnist_like(30, 12, 64)
+    a, b = x["x_train"].astype(np.float64), x["x_test"].astype(np.float64)
+    gamma = 1.0 / 64
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ii = np.concatenate([rng.integers(0, 30, 50), np.arange(12), [29, 0, 29]])
+    jj = np.concatenate([rng.integers(0, 12, 50), np.arange(12), [11, 0, 11]])
+    ref = np.exp(-gamma * cdist(a, b, "sqeuclidean"))[ii, jj]
+    err = float(np.max(np.abs(gram.rbf_pairs(a, b, ii, jj, gamma) - ref)))
+    same = np.exp(-gamma * cdist(a, a, "sqeuclidean"))[ii, ii[::-1]]
+    return max(err, float(np.max(np.abs(gram.rbf_pairs(a, a, ii, ii[::-1], gamma) - same))))
+
+
 def mix_limits() -> float:
     x = synthetic.uniform_angles(8, 5, 17)
     kq, _ = gram.quantum_gram(x, reps=2)

@@ -51,6 +51,7 @@ PIN_SUITE = [
     ("block mps", lambda: pins.block_mps_vs_products(12, 2, 6), 1e-10),
     ("single cut", pins.single_cut_truncation, 1e-12),
     ("rbf", pins.rbf_vs_library, 1e-12),
+    ("rbf pairs", pins.rbf_pairs_vs_library, 1e-12),
     ("mix", pins.mix_limits, 1e-12),
 ]
 
@@ -119,6 +120,18 @@ def _mut_rbf_no_square(mp):
     mp.setattr(gram, "np", _Proxy(real_np, sum=lambda a, axis=None: real_np.sum(real_np.sqrt(real_np.abs(a)), axis=axis)))
 
 
+_orig_rbf_pairs = gram.rbf_pairs
+
+
+def _mut_rbf_pairs_one_side(mp):
+    # both samples of a pair taken from the row set
+    mp.setattr(gram, "rbf_pairs", lambda xr, xc, i, j, g: _orig_rbf_pairs(xr, xr, i, j, g))
+
+
+def _mut_rbf_pairs_indices_swapped(mp):
+    mp.setattr(gram, "rbf_pairs", lambda xr, xc, i, j, g: _orig_rbf_pairs(xr, xc, j, i, g))
+
+
 def _mut_mix_swapped(mp):
     mp.setattr(gram, "dual_kernel", lambda kq, kc, w: (1 - w) * real_np.asarray(kq) + w * real_np.asarray(kc))
 
@@ -171,6 +184,8 @@ MUTATIONS = {
     "svd split drops singular values": _mut_svd_drops_s,
     "no per-site rescale": _mut_no_rescale,
     "rbf distance not squared": _mut_rbf_no_square,
+    "rbf pairs read both samples from the rows": _mut_rbf_pairs_one_side,
+    "rbf pairs swap the pair indices": _mut_rbf_pairs_indices_swapped,
     "mix weights swapped": _mut_mix_swapped,
     "hadamard transposed": _mut_hadamard_sign,
 }

@@ -161,6 +161,10 @@ def test_rbf_matches_scipy():
     assert pins.rbf_vs_library() < 1e-14
 
 
+def test_rbf_pairs_matches_scipy():
+    assert pins.rbf_pairs_vs_library() < 1e-14
+
+
 def test_rbf_matches_sklearn():
     skl = pytest.importorskip("sklearn.metrics.pairwise")
     x = synthetic.fmnist_like(20, 0, 16)["x_train"].astype(np.float64)

@@ -1,0 +1,209 @@
+"""GPU parity where the kernel values are of order one, at the full qubit counts.
+
+Independent Fashion-MNIST-shaped samples at hundreds of qubits have K_q far below 1e-100
+(exponential concentration, §I), so a |dK| bound checked on them alone says little. These
+tests add near-duplicate pairs (a sample and a perturbed copy, noise scale log-uniform so
+that K_q spreads from about 1e-3 to 0.999) and compare the CUDA path with the FP64 oracle
+element by element (§II-C Eqs. 7-10; §II-B Eq. 3; §II-D Eq. 11):
+
+* the FP32 path (complex64 MPS, bond 4) at n = 784 in the benchmarked launch: the symmetric
+  2000 x 2000 Gram and the 500 x 2000 rows, with tile shapes chosen by the autotuner as the
+  benchmark does, |dK| <= 1e-6;
+* the split-BF16 tensor-core path at bond 32 (reps = 5) at n = 256, |dK| <= 1e-4;
+* the d = 64 workload at its full size (1000 train, 200 test, reps = 2) at every mix weight.
+
+Each test prints one JSON line with the measured largest |dK| and the largest relative
+error over the pairs with K_q > 1e-3 (run pytest with -s to see them).
+"""
+import json
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL_K = 1e-6
+TOL_MIXED = 1e-4
+
+
+def _tol_log(ref):
+    return 1e-3 * np.maximum(1.0, np.abs(ref))
+
+
+@pytest.fixture(scope="module")
+def dk():
+    import torch
+    from paper_2602_01330_gb300 import build, dualk
+    build.build()
+    ctx = dualk.Context(0)
+    yield dualk, ctx, torch
+    ctx.close()
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _pairs_check(name, got, ref, xa, xb, ia, ib, w, gamma, tol):
+    """Compare the listed entries (ia[p], ib[p]) of the GPU blocks `got` with the oracle's
+    (K_q, log K_q) `ref` of the same pairs (xa / xb: their row and column samples)."""
+    from oracle import gram as og
+    kq_ref, lkq_ref = ref
+    p = np.arange(len(ia))
+    kc_ref = og.rbf_pairs(xa, xb, p, p, gamma)
+    k_ref = og.dual_kernel(kq_ref, kc_ref, w)
+    pick = lambda t: t.cpu().numpy().astype(np.float64)[ia, ib]
+    kq, kc, k, lkq = pick(got["kq"]), pick(got["kc"]), pick(got["k"]), pick(got["logkq"])
+    big = kq_ref > 1e-3
+    rel = np.abs(kq - kq_ref)[big] / kq_ref[big]
+    report = {"case": name, "pairs": int(len(ia)), "pairs_kq_gt_1e-3": int(big.sum()),
+              "kq_ref_min": float(kq_ref.min()), "kq_ref_max": float(kq_ref.max()),
+              "max_abs_dkq": float(np.max(np.abs(kq - kq_ref))), "max_abs_dk": float(np.max(np.abs(k - k_ref))),
+              "max_abs_dkc": float(np.max(np.abs(kc - kc_ref))),
+              "max_rel_dkq_kq_gt_1e-3": float(rel.max()) if rel.size else None}
+    print(json.dumps(report))
+    assert report["max_abs_dkq"] <= tol
+    assert report["max_abs_dk"] <= tol
+    assert report["max_abs_dkc"] <= TOL_K
+    sel = lkq_ref > -700
+    assert np.all(np.abs(lkq[sel] - lkq_ref[sel]) <= _tol_log(lkq_ref[sel]))
+    return report
+
+
+def _block_check(got, ref, sub, x, w, gamma, tol):
+    """The symmetric block sub x sub of the GPU Gram against the oracle's (K_q, log K_q)
+    `ref` of x[sub]; returns the number of off-diagonal entries with K_q > 1e-3."""
+    from oracle import gram as og
+    kq_ref, lkq_ref = ref
+    kc_ref = og.rbf(x[sub], x[sub], gamma)
+    g = {k: v.cpu().numpy().astype(np.float64)[np.ix_(sub, sub)] for k, v in got.items()}
+    assert np.max(np.abs(g["kq"] - kq_ref)) <= tol
+    assert np.max(np.abs(g["kc"] - kc_ref)) <= TOL_K
+    assert np.max(np.abs(g["k"] - og.dual_kernel(kq_ref, kc_ref, w))) <= tol
+    sel = lkq_ref > -700
+    assert np.all(np.abs(g["logkq"][sel] - lkq_ref[sel]) <= _tol_log(lkq_ref[sel]))
+    return int((kq_ref[~np.eye(len(sub), dtype=bool)] > 1e-3).sum())
+
+
+def test_fp32_n784_near_duplicates_bench_launch(dk):
+    """d = 784, 2000 train + 500 test, reps = 2, bond 4, w = 0.5, the benchmark's launches.
+    Train samples 1000..1199 are near copies of train 0..199; test samples 0..199 are near
+    copies of train 200..399. Checked: the 200 near pairs of the Gram and the 200 of the
+    rows, and the full 64 x 64 Gram block over train 0..31 and 1000..1031."""
+    import oracle_pool
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    from paper_2602_01330_gb300.sweep import Autotuner
+    d = synthetic.fmnist_like(2000, 500, 784)
+    xtr, xte = d["x_train"].copy(), d["x_test"].copy()
+    xtr[1000:1200] = synthetic.near_copies(xtr[0:200], 3e-4, 3e-2, seed=61)
+    xte[0:200] = synthetic.near_copies(xtr[200:400], 3e-4, 3e-2, seed=62)
+    fm = dualk.FeatureMap(reps=2, chi_max=4)
+    mtr = dualk.mps_build(ctx, _dev(torch, xtr), fm)
+    mte = dualk.mps_build(ctx, _dev(torch, xte), fm)
+    tuner = Autotuner(ctx)
+    cfg_gram = tuner.best(mtr, symmetric=True)
+    cfg_rows = tuner.best(mte, symmetric=False, cols=mtr)
+    try:
+        ctx.set_gram_config(cfg_gram)
+        g = dualk.gram(ctx, mtr, w=0.5)
+        ctx.set_gram_config(cfg_rows)
+        r = dualk.dual_kernel_rows(ctx, mte, mtr, w=0.5)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_gram_config(0)
+    ctx.sync_status()
+    gamma = 1.0 / 784
+    base, near = np.arange(0, 200), np.arange(1000, 1200)
+    ref = oracle_pool.aligned_pairs(xtr[base], xtr[near], 2)
+    rep = _pairs_check("fp32 n784 gram near pairs", g, ref, xtr[base], xtr[near], base, near, 0.5, gamma, TOL_K)
+    assert rep["pairs_kq_gt_1e-3"] >= 150
+    # the mirrored entries of the symmetric Gram hold the same bits
+    kq = g["kq"].cpu().numpy()
+    assert np.array_equal(kq[base, near], kq[near, base])
+    tr_idx, te_idx = np.arange(200, 400), np.arange(0, 200)
+    ref = oracle_pool.aligned_pairs(xte[te_idx], xtr[tr_idx], 2)
+    rep = _pairs_check("fp32 n784 rows near pairs", r, ref, xte[te_idx], xtr[tr_idx], te_idx, tr_idx, 0.5, gamma,
+                       TOL_K)
+    assert rep["pairs_kq_gt_1e-3"] >= 150
+    sub = np.r_[0:32, 1000:1032]
+    ref = oracle_pool.block(xtr[sub], None, 2, symmetric=True)
+    assert _block_check(g, ref, sub, xtr, 0.5, gamma, TOL_K) >= 40
+    assert bool(torch.all(torch.diagonal(g["kq"]) == 1.0))
+
+
+def test_bf16x3_chi32_d256_near_duplicates(dk):
+    """d = 256 (precision-form data), reps = 5 (bond 32), w = 0.5: Gram of 256 train
+    samples where 128..191 are near copies of 0..63, and rows of 64 test samples where
+    0..31 are near copies of train 64..95. The near pairs and the 8 x 8 Gram block over
+    train 0..3 and 128..131 against the oracle: split-BF16 tensor cores at 1e-4, the FP32
+    bond-32 path at 1e-6."""
+    import oracle_pool
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    d = synthetic.fmnist_like(256, 64, 256)
+    xtr, xte = d["x_train"].copy(), d["x_test"].copy()
+    xtr[128:192] = synthetic.near_copies(xtr[0:64], 1e-4, 2.5e-2, seed=63)
+    xte[0:32] = synthetic.near_copies(xtr[64:96], 1e-4, 2.5e-2, seed=64)
+    fm = dualk.FeatureMap(reps=5, chi_max=32)
+    mtr = dualk.mps_build(ctx, _dev(torch, xtr), fm)
+    mte = dualk.mps_build(ctx, _dev(torch, xte), fm)
+    gamma = 1.0 / 256
+    base, near = np.arange(0, 64), np.arange(128, 192)
+    tr_idx, te_idx = np.arange(64, 96), np.arange(0, 32)
+    sub = np.r_[0:4, 128:132]
+    ref_g = oracle_pool.aligned_pairs(xtr[base], xtr[near], 5)
+    ref_r = oracle_pool.aligned_pairs(xte[te_idx], xtr[tr_idx], 5)
+    ref_b = oracle_pool.block(xtr[sub], None, 5, symmetric=True)
+    for name, prec, tol in (("bf16x3", dualk.DK_PREC_BF16X3, TOL_MIXED), ("fp32", dualk.DK_PREC_F32, TOL_K)):
+        g = dualk.gram(ctx, mtr, w=0.5, prec=prec)
+        r = dualk.dual_kernel_rows(ctx, mte, mtr, w=0.5, prec=prec)
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        rep = _pairs_check(f"{name} chi32 d256 gram near pairs", g, ref_g, xtr[base], xtr[near], base, near, 0.5,
+                           gamma, tol)
+        assert rep["pairs_kq_gt_1e-3"] >= 48
+        rep = _pairs_check(f"{name} chi32 d256 rows near pairs", r, ref_r, xte[te_idx], xtr[tr_idx], te_idx, tr_idx,
+                           0.5, gamma, tol)
+        assert rep["pairs_kq_gt_1e-3"] >= 24
+        assert _block_check(g, ref_b, sub, xtr, 0.5, gamma, tol) >= 4
+        assert bool(torch.all(torch.diagonal(g["kq"]) == 1.0))
+
+
+def test_fmnist_d64_full_size_all_mixes(dk):
+    """d = 64, 1000 train and 200 test samples, reps = 2 (bond 4), complex64: the whole
+    1000 x 1000 Gram and 200 x 1000 rows at w in {0, 0.25, 0.5, 0.75, 1}, element by element
+    against the oracle (K, K_q, K_c, log K_q)."""
+    import oracle_pool
+    dualk, ctx, torch = dk
+    from oracle import gram as og
+    from paper_2602_01330_gb300 import synthetic
+    d = synthetic.fmnist_like(1000, 200, 64)
+    xtr, xte = d["x_train"], d["x_test"]
+    kq_tr, lkq_tr = oracle_pool.block(xtr, None, 2, symmetric=True)
+    kq_te, lkq_te = oracle_pool.block(xte, xtr, 2)
+    kc_tr = og.rbf(xtr, xtr, 1 / 64)
+    kc_te = og.rbf(xte, xtr, 1 / 64)
+    fm = dualk.FeatureMap(reps=2, chi_max=4)
+    mtr = dualk.mps_build(ctx, _dev(torch, xtr), fm)
+    mte = dualk.mps_build(ctx, _dev(torch, xte), fm)
+    worst = {}
+    for w in (0.0, 0.25, 0.5, 0.75, 1.0):
+        g = dualk.gram(ctx, mtr, w=w)
+        r = dualk.dual_kernel_rows(ctx, mte, mtr, w=w)
+        torch.cuda.synchronize()
+        for name, got, kq_ref, lkq_ref, kc_ref in (("gram", g, kq_tr, lkq_tr, kc_tr), ("rows", r, kq_te, lkq_te, kc_te)):
+            h = {k: v.cpu().numpy().astype(np.float64) for k, v in got.items()}
+            dk_ = float(np.max(np.abs(h["k"] - og.dual_kernel(kq_ref, kc_ref, w))))
+            dkq = float(np.max(np.abs(h["kq"] - kq_ref)))
+            assert dkq <= TOL_K and dk_ <= TOL_K
+            assert np.max(np.abs(h["kc"] - kc_ref)) <= TOL_K
+            sel = lkq_ref > -700
+            assert np.all(np.abs(h["logkq"][sel] - lkq_ref[sel]) <= _tol_log(lkq_ref[sel]))
+            worst[name] = max(worst.get(name, 0.0), dkq, dk_)
+    kq = g["kq"].cpu().numpy()
+    assert np.array_equal(kq, kq.T) and np.all(np.diag(kq) == 1.0)
+    off = ~np.eye(1000, dtype=bool)
+    print(json.dumps({"case": "fmnist d64 1000/200 all mixes", "max_abs_dK": worst,
+                      "gram_offdiag_kq_max": float(kq_tr[off].max())}))
+    ctx.sync_status()
