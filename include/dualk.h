@@ -129,11 +129,14 @@ dk_status dk_selftest_wait_timeout(dk_ctx* ctx, unsigned long long limit_ns, voi
 /* Bytes of an MPS buffer for m samples, n sites, padded bond chi_max. */
 size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
 
-/* Scratch bytes the build, Gram and rows calls need for (n, chi_max, dtype, prec): always 0.
- * Every kernel keeps its working state in registers and shared memory and writes only the
- * caller's outputs, so these calls take no workspace argument; the query exists for callers
- * that size a workspace per call. Returns (size_t)-1 for a combination no kernel supports
- * (chi_max / dtype / prec as dk_gram_tile), so it also serves as a capability check. */
+/* Scratch bytes the build, Gram and rows calls (dk_mps_build, dk_gram_tile,
+ * dk_dual_kernel_rows, dk_gram_sweep) need for (n, chi_max, dtype, prec): always 0. Every
+ * kernel of these calls keeps its working state in registers and shared memory and writes
+ * only the caller's outputs, so they take no workspace argument; the query exists for
+ * callers that size a workspace per call. Returns (size_t)-1 for a combination no kernel
+ * supports (chi_max / dtype / prec as dk_gram_tile), so it also serves as a capability
+ * check. The block-statevector calls, which do need scratch in one form, have their own
+ * queries (dk_block_states_workspace_bytes, dk_gram_blocks_workspace_bytes). */
 size_t dk_workspace_bytes(int n, int chi_max, dk_dtype dtype, dk_precision prec);
 
 /* |psi(x_i)> = U(x_i)|0>^n as an MPS (§II-C, Eq. 6), for i < m.
@@ -257,14 +260,24 @@ size_t dk_block_states_bytes(int m, int n, int block);
  *             last block
  *   log_norm  m floats (device, written, may be NULL): ln|<psi~_i|psi~_i>| of the rounded
  *             states by the arithmetic of dk_gram_blocks in `prec` (for BF16X3 the diagonal
- *             tiles of that Gram, in the context's dk_set_block_gram_form form; the tcgen05
- *             form takes nb * m * 4 bytes of stream-ordered scratch for it), so that
+ *             tiles of that Gram, in the context's dk_set_block_gram_form form), so that
  *             K_q(x, x) = 1 exactly
+ *   ws        caller-owned device scratch of at least ws_bytes =
+ *             dk_block_states_workspace_bytes(ctx, m, n, fm->block, prec) bytes, 16-byte
+ *             aligned (the tcgen05 form of the BF16X3 self-norms keeps one value per block
+ *             and sample there); may be NULL when that size is 0 or log_norm is NULL. Its
+ *             contents are scratch: nothing is read from it before it is written.
  * Errors: DK_ERR_ARG (NULL pointers, m or n < 1, reps, entangler, misaligned states),
  *         DK_ERR_UNSUPPORTED (block outside 0..12 or above 12 qubits, m > 65535, more than
- *         6144 blocks, prec neither F32 nor BF16X3), DK_ERR_CUDA. */
+ *         6144 blocks, prec neither F32 nor BF16X3), DK_ERR_WORKSPACE (ws NULL, misaligned or
+ *         smaller than the query's size), DK_ERR_CUDA. */
 dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm, int entangler,
-                          dk_precision prec, void* states, float* log_norm, void* stream);
+                          dk_precision prec, void* states, float* log_norm, void* ws, size_t ws_bytes, void* stream);
+
+/* Scratch bytes dk_block_states needs for these arguments on this context (it depends on
+ * dk_set_block_gram_form): nb * m * 4 rounded up to 256 for DK_PREC_BF16X3 in the tcgen05
+ * form, else 0; 0 also for arguments the call would reject. */
+size_t dk_block_states_workspace_bytes(dk_ctx* ctx, int m, int n, int block, dk_precision prec);
 
 /* A block of the Gram matrix of a block-structured map from block statevectors, outputs
  * and epilogue as dk_gram_tile (§II-C Eqs. 8-10 factorised over blocks; §II-B Eq. 3;
@@ -281,20 +294,30 @@ dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, const dk_fm
  *   k_out, kq_out, kc_out, logkq_out  nrows x ncols float32 (device, any may be NULL, not
  *                              all), row stride ld; symmetric (rows == cols, same range)
  *                              computes each unordered pair once and writes both entries
- * Scratch: the tcgen05 form of DK_PREC_BF16X3 takes stream-ordered device memory
- * (cudaMallocAsync / cudaFreeAsync on `stream`, from the device's default pool): nrows *
- * ncols * 4 bytes for the RBF distances when K_c is needed, and up to 8 * nrows * ncols * 4
- * for the partial sums of a rectangular block split over its blocks; the other forms and
- * every chain-path call allocate nothing.
+ *   ws, ws_bytes               caller-owned device scratch, 16-byte aligned, of at least
+ *                              dk_gram_blocks_workspace_bytes(ctx, n, block, nrows, ncols,
+ *                              prec, symmetric, K_c needed) bytes: the tcgen05 form of
+ *                              DK_PREC_BF16X3 keeps the RBF distances there (nrows * ncols * 4
+ *                              bytes when K_c is needed) and, for a rectangular block split
+ *                              over its blocks, the partial sums (up to 8 * nrows * ncols * 4
+ *                              bytes); NULL when that size is 0. Nothing is read from it
+ *                              before it is written. The library allocates nothing.
  * Errors: DK_ERR_ARG (NULL inputs, ranges outside the sample counts, ld < ncols, no
  *         output, symmetric with different rows and columns, K_c needed without x),
- *         DK_ERR_UNSUPPORTED (block, prec neither F32 nor BF16X3), DK_ERR_CUDA (also when
- *         the scratch cannot be had). */
+ *         DK_ERR_UNSUPPORTED (block, prec neither F32 nor BF16X3), DK_ERR_WORKSPACE (ws
+ *         NULL, misaligned or smaller than needed), DK_ERR_CUDA. */
 dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows, const void* states_cols, int m_cols,
                          int n, int block, int row0, int nrows, int col0, int ncols, const float* lnorm_rows,
                          const float* lnorm_cols, const float* x_rows, const float* x_cols, float gamma, float w,
                          dk_precision prec, float* k_out, float* kq_out, float* kc_out, float* logkq_out,
-                         long long ld, int symmetric, void* stream);
+                         long long ld, int symmetric, void* ws, size_t ws_bytes, void* stream);
+
+/* Scratch bytes of a dk_gram_blocks call with these sizes on this context (the plan depends
+ * on the SM count and dk_set_block_gram_form); with_kc: 1 when K_c is needed (kc_out, or
+ * k_out with w != 1). 0 for DK_PREC_F32, for the mma.sync form, and for arguments the call
+ * would reject. */
+size_t dk_gram_blocks_workspace_bytes(dk_ctx* ctx, int n, int block, int nrows, int ncols, dk_precision prec,
+                                      int symmetric, int with_kc);
 
 /* Kernels the context uses for DK_PREC_BF16X3 block states' self-norms and block Grams:
  * DK_BLOCK_TCGEN05 (default; 128 x 128 or 128 x 64 pair tiles, one CTA per SM, tcgen05.mma
@@ -371,11 +394,13 @@ dk_status dk_set_gram_config(dk_ctx* ctx, int id);
  * (symmetric = 1: the strict upper triangle of a square Gram, each pair of distinct samples
  * once), in FP64:
  *   out[0] = entries of kq counted, out[1] = sum K_q, out[2] = sum K_q^2,
- *   out[3] = entries of logkq with a finite value, out[4] = sum log K_q, out[5] = sum (log K_q)^2
- * (mean and variance follow; log K_q stays informative where K_q underflows to 0).
+ *   out[3] = entries of logkq with a finite value, out[4] = sum log K_q, out[5] = sum (log K_q)^2,
+ *   out[6] = mean K_q, out[7] = variance of K_q, out[8] = mean log K_q, out[9] = variance of
+ *   log K_q (population variances from the sums; NaN when no entry was counted)
+ * (log K_q stays informative where K_q underflows to 0).
  *   kq, logkq  float32 blocks with row stride ld >= ncols (device); either may be NULL (its
- *              three sums stay 0)
- *   out        6 doubles (device, written; cleared by the call first)
+ *              three sums stay 0 and its mean and variance are NaN)
+ *   out        10 doubles (device, written; cleared by the call first)
  * Errors: DK_ERR_ARG (NULL ctx / out, both kq and logkq NULL, nrows or ncols < 1, ld < ncols,
  *         symmetric with nrows != ncols), DK_ERR_CUDA. */
 dk_status dk_gram_stats(dk_ctx* ctx, const float* kq, const float* logkq, long long ld, int nrows, int ncols,

@@ -288,8 +288,17 @@ DK_API size_t dk_block_states_bytes(int m, int n, int block) {
   return size_t(nb) * m * dk::gblk::dpad_of(b) * sizeof(float2);
 }
 
+DK_API size_t dk_block_states_workspace_bytes(dk_ctx* ctx, int m, int n, int block, dk_precision prec) {
+  using namespace dk;
+  if (!ctx || m < 1 || n < 1 || dk_block_states_bytes(m, n, block) == 0) return 0;
+  if (prec != DK_PREC_BF16X3 || ctx->block_form == DK_BLOCK_MMA_SYNC) return 0;
+  const int b = block > 0 ? block : n;
+  return block_selfnorm_umma_ws_bytes(m, (n + b - 1) / b);
+}
+
 DK_API dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, const dk_fmap* fm, int entangler,
-                                 dk_precision prec, void* states, float* log_norm, void* stream) {
+                                 dk_precision prec, void* states, float* log_norm, void* ws, size_t ws_bytes,
+                                 void* stream) {
   using namespace dk;
   if (!ctx || !x || !fm || !states || m < 1 || n < 1) return DK_ERR_ARG;
   if (prec != DK_PREC_F32 && prec != DK_PREC_BF16X3) return DK_ERR_UNSUPPORTED;
@@ -337,17 +346,33 @@ DK_API dk_status dk_block_states(dk_ctx* ctx, const float* x, int m, int n, cons
   if (split)
     return ctx->block_form == DK_BLOCK_MMA_SYNC
                ? block_selfnorm_tc_launch(states, m, nb, gblk::dpad_of(b), log_norm, st)
-               : block_selfnorm_umma_launch(ctx, states, m, nb, gblk::dpad_of(b), log_norm, st);
+               : block_selfnorm_umma_launch(ctx, states, m, nb, gblk::dpad_of(b), log_norm, ws, ws_bytes, st);
   gblk::block_selfnorm_kernel<<<m, gblk::NORM_NT, nb * sizeof(float2), st>>>(static_cast<const float2*>(states), m,
                                                                            nb, gblk::dpad_of(b), log_norm);
   return launch_status();
+}
+
+DK_API size_t dk_gram_blocks_workspace_bytes(dk_ctx* ctx, int n, int block, int nrows, int ncols, dk_precision prec,
+                                            int symmetric, int with_kc) {
+  using namespace dk;
+  if (!ctx || n < 1 || nrows < 1 || ncols < 1 || dk_block_states_bytes(1, n, block) == 0) return 0;
+  if (prec != DK_PREC_BF16X3 || ctx->block_form == DK_BLOCK_MMA_SYNC) return 0;
+  const int b = block > 0 ? block : n;
+  GramArgs a{};
+  a.n = n;
+  a.nrows = nrows;
+  a.ncols = ncols;
+  a.symmetric = symmetric ? 1 : 0;
+  a.need_kc = with_kc ? 1 : 0;
+  return gram_blocks_umma_ws_bytes(ctx, a, (n + b - 1) / b);
 }
 
 DK_API dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows, const void* states_cols, int m_cols,
                                 int n, int block, int row0, int nrows, int col0, int ncols, const float* lnorm_rows,
                                 const float* lnorm_cols, const float* x_rows, const float* x_cols, float gamma,
                                 float w, dk_precision prec, float* k_out, float* kq_out, float* kc_out,
-                                float* logkq_out, long long ld, int symmetric, void* stream) {
+                                float* logkq_out, long long ld, int symmetric, void* ws, size_t ws_bytes,
+                                void* stream) {
   using namespace dk;
   if (prec != DK_PREC_F32 && prec != DK_PREC_BF16X3) return DK_ERR_UNSUPPORTED;
   if (!ctx || !states_rows || !states_cols || !lnorm_rows || !lnorm_cols) return DK_ERR_ARG;
@@ -388,7 +413,7 @@ DK_API dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows
       return gram_blocks_tc_launch(ctx, states_rows, m_rows, states_cols, m_cols, (n + b - 1) / b, gblk::dpad_of(b),
                                    a, st);
     return gram_blocks_umma_launch(ctx, states_rows, m_rows, states_cols, m_cols, (n + b - 1) / b, gblk::dpad_of(b),
-                                   a, st);
+                                   a, ws, ws_bytes, st);
   }
   // tile shape: estimated time = waves x tile area / per-pair efficiency (the 128 x 64 tile
   // runs about 15 % more pairs per second than 64 x 64, which fills the GPU better when

@@ -488,9 +488,26 @@ dk_status set_smem() {
   return DK_OK;
 }
 
+// Caller-provided scratch of one Gram launch: the RBF distances (nrows x ncols floats, when
+// K_c is needed) and, for a rectangular block split over ksplit items, the partial log2 sums
+// (ksplit x nrows x ncols floats), each starting on a 256-byte boundary of `ws`.
+struct Scratch {
+  size_t d2_bytes, part_bytes;
+  size_t total() const { return d2_bytes + part_bytes; }
+};
+
+inline size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+inline Scratch scratch_of(const GramArgs& a, int ksplit) {
+  const size_t np = size_t(a.nrows) * size_t(a.ncols);
+  return {a.need_kc ? round256(np * sizeof(float)) : 0, ksplit > 1 ? round256(size_t(ksplit) * np * sizeof(float)) : 0};
+}
+
 template <int BN, bool WIDE>
 dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp, GramArgs a,
-                      int ntiles, int ksplit, cudaStream_t st) {
+                      int ntiles, int ksplit, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const Scratch need = scratch_of(a, ksplit);
+  if (need.total() > 0 && (!ws || ws_bytes < need.total() || !aligned16(ws))) return DK_ERR_WORKSPACE;
   CUtensorMap tr, tc;
   dk_status s = encode_states_map(ctx, &tr, sr, m_r, nb, dp, BM);
   if (s == DK_OK) s = encode_states_map(ctx, &tc, sc, m_c, nb, dp, BN);
@@ -500,12 +517,9 @@ dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int 
   const long long items = (long long)ntiles * ksplit;
   const int grid = int(items < ctx->sm_count ? items : ctx->sm_count);
   if (grid < 1) return DK_OK;
-  // squared distances of the RBF kernel first, into stream-ordered scratch
-  float* d2 = nullptr;
+  // squared distances of the RBF kernel first, into the caller's scratch
+  float* d2 = need.d2_bytes ? static_cast<float*>(ws) : nullptr;
   if (a.need_kc) {
-    if (cudaMallocAsync(reinterpret_cast<void**>(&d2), size_t(a.nrows) * size_t(a.ncols) * sizeof(float), st) !=
-        cudaSuccess)
-      return DK_ERR_CUDA;
     GramArgs ar = a;
     ar.ntiles = count_tiles(ar, RT, RT);
     const int rgrid = ar.ntiles < 8 * ctx->sm_count ? ar.ntiles : 8 * ctx->sm_count;
@@ -513,11 +527,8 @@ dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int 
     s = launch_status();
     a.d2 = d2;
   }
-  float* part = nullptr;
+  float* part = need.part_bytes ? reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + need.d2_bytes) : nullptr;
   const size_t np = size_t(a.nrows) * size_t(a.ncols);
-  if (s == DK_OK && ksplit > 1 &&
-      cudaMallocAsync(reinterpret_cast<void**>(&part), size_t(ksplit) * np * sizeof(float), st) != cudaSuccess)
-    s = DK_ERR_CUDA;
   if (s == DK_OK) {
     gram_blocks_umma_kernel<BN, WIDE><<<grid, NTHREADS, Cfg<BN, WIDE>::SMEM, st>>>(tr, tc, a, nb, dp / 16, 0, 0,
                                                                                    nullptr, 0, ksplit, part);
@@ -529,24 +540,24 @@ dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int 
                                                                                                        ksplit);
     s = launch_status();
   }
-  if (part && cudaFreeAsync(part, st) != cudaSuccess && s == DK_OK) s = DK_ERR_CUDA;
-  if (d2 && cudaFreeAsync(d2, st) != cudaSuccess && s == DK_OK) s = DK_ERR_CUDA;
   return s;
 }
 
-}  // namespace gbum
+// The launch plan of a block Gram: symmetric: 128 x 128 tiles, all blocks in one item (the
+// diagonal tiles are then the self-norm units, bit for bit). Rectangular: 128 x 128 tiles
+// with the blocks split over up to 8 items per tile when there are fewer tiles than SMs, or
+// 128 x 64 tiles, whichever takes less time by waves x blocks per item (a 128 x 64
+// tile-block costs about 0.92 of a 128 x 128 one: its N = 64 MMAs are bound by shared-memory
+// reads).
+struct Plan {
+  bool wide;
+  int ntiles, ksplit;
+};
 
-dk_status gram_blocks_umma_launch(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp,
-                                  GramArgs a, cudaStream_t st) {
-  // symmetric: 128 x 128 tiles, all blocks in one item (the diagonal tiles are then the
-  // self-norm units, bit for bit). Rectangular: 128 x 128 tiles with the blocks split over up
-  // to 8 items per tile when there are fewer tiles than SMs, or 128 x 64 tiles, whichever
-  // takes less time by waves x blocks per item (a 128 x 64 tile-block costs about 0.92 of a
-  // 128 x 128 one: its N = 64 MMAs are bound by shared-memory reads)
-  GramArgs a128 = a, a64 = a;
-  const int t128 = count_tiles(a128, gbum::BM, 128);
-  if (a.symmetric) return gbum::launch_gram<128, true>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, 1, st);
-  const int t64 = count_tiles(a64, gbum::BM, 64);
+inline Plan plan_gram(const dk_ctx* ctx, GramArgs a, int nb) {
+  const int t128 = count_tiles(a, BM, 128);
+  if (a.symmetric) return {true, t128, 1};
+  const int t64 = count_tiles(a, BM, 64);
   const long long sms = ctx->sm_count;
   long long ks = t128 < sms ? sms / t128 : 1;
   if (ks > nb) ks = nb;
@@ -554,22 +565,38 @@ dk_status gram_blocks_umma_launch(dk_ctx* ctx, const void* sr, int m_r, const vo
   if (ks < 1) ks = 1;
   const double cost128 = double((t128 * ks + sms - 1) / sms) * double((nb + ks - 1) / ks);
   const double cost64 = double((t64 + sms - 1) / sms) * double(nb) * 0.92;
-  if (cost128 <= cost64) return gbum::launch_gram<128, true>(ctx, sr, m_r, sc, m_c, nb, dp, a128, t128, int(ks), st);
-  return gbum::launch_gram<64, false>(ctx, sr, m_r, sc, m_c, nb, dp, a64, t64, 1, st);
+  if (cost128 <= cost64) return {true, t128, int(ks)};
+  return {false, t64, 1};
 }
 
+}  // namespace gbum
+
+size_t gram_blocks_umma_ws_bytes(const dk_ctx* ctx, GramArgs a, int nb) {
+  const gbum::Plan pl = gbum::plan_gram(ctx, a, nb);
+  return gbum::scratch_of(a, pl.ksplit).total();
+}
+
+dk_status gram_blocks_umma_launch(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp,
+                                  GramArgs a, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const gbum::Plan pl = gbum::plan_gram(ctx, a, nb);
+  if (pl.wide)
+    return gbum::launch_gram<128, true>(ctx, sr, m_r, sc, m_c, nb, dp, a, pl.ntiles, pl.ksplit, ws, ws_bytes, st);
+  return gbum::launch_gram<64, false>(ctx, sr, m_r, sc, m_c, nb, dp, a, pl.ntiles, 1, ws, ws_bytes, st);
+}
+
+size_t block_selfnorm_umma_ws_bytes(int m, int nb) { return gbum::round256(size_t(nb) * size_t(m) * sizeof(float)); }
+
 dk_status block_selfnorm_umma_launch(dk_ctx* ctx, const void* states, int m, int nb, int dp, float* log_norm,
-                                     cudaStream_t st) {
+                                     void* ws, size_t ws_bytes, cudaStream_t st) {
   using namespace gbum;
   const long long units = (long long)((m + BM - 1) / BM) * nb;
   if (units > 0x7fffffffLL) return DK_ERR_UNSUPPORTED;
+  if (!ws || ws_bytes < block_selfnorm_umma_ws_bytes(m, nb) || !aligned16(ws)) return DK_ERR_WORKSPACE;
   CUtensorMap t;
   dk_status s = encode_states_map(ctx, &t, states, m, nb, dp, BM);
   if (s == DK_OK) s = set_smem<128, true>();
   if (s != DK_OK) return s;
-  float* g2 = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&g2), size_t(nb) * size_t(m) * sizeof(float), st) != cudaSuccess)
-    return DK_ERR_CUDA;
+  float* g2 = static_cast<float*>(ws);
   GramArgs a{};
   a.status = ctx->status;
   const int grid = int(units < ctx->sm_count ? units : ctx->sm_count);
@@ -580,7 +607,6 @@ dk_status block_selfnorm_umma_launch(dk_ctx* ctx, const void* states, int m, int
     selfnorm_sum_kernel<<<(m + 255) / 256, 256, 0, st>>>(g2, m, nb, log_norm);
     s = launch_status();
   }
-  if (cudaFreeAsync(g2, st) != cudaSuccess && s == DK_OK) s = DK_ERR_CUDA;
   return s;
 }
 

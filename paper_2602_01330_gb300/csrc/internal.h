@@ -56,10 +56,14 @@ dk_status gram_blocks_tc_launch(dk_ctx* ctx, const void* sr, int m_r, const void
                                 GramArgs a, cudaStream_t st);
 dk_status block_selfnorm_tc_launch(const void* states, int m, int nb, int dp, float* log_norm, cudaStream_t st);
 // The same on tcgen05 tensor cores (gram_blocks_umma.cu).
+// Both take their scratch from the caller (ws, ws_bytes; DK_ERR_WORKSPACE when too small);
+// the *_ws_bytes functions give the size a launch with the same arguments needs.
+size_t gram_blocks_umma_ws_bytes(const dk_ctx* ctx, GramArgs a, int nb);
 dk_status gram_blocks_umma_launch(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int m_c, int nb, int dp,
-                                  GramArgs a, cudaStream_t st);
+                                  GramArgs a, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t block_selfnorm_umma_ws_bytes(int m, int nb);
 dk_status block_selfnorm_umma_launch(dk_ctx* ctx, const void* states, int m, int nb, int dp, float* log_norm,
-                                     cudaStream_t st);
+                                     void* ws, size_t ws_bytes, cudaStream_t st);
 // Destroys the graphs dk_gram_sweep recorded for this context (sweep.cu).
 void sweep_cache_free(dk_ctx* ctx);
 

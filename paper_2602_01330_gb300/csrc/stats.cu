@@ -6,7 +6,8 @@
 // One grid-stride pass over the entries of a block (for a symmetric Gram: the strict upper
 // triangle, each unordered pair once): count, sum and sum of squares of K_q and of log K_q
 // (finite values only; log K_q stays exact where K_q underflows to 0), accumulated in FP64
-// per thread, reduced per CTA and added atomically into the caller's six doubles.
+// per thread, reduced per CTA and added atomically into the caller's doubles; a one-thread
+// kernel then forms the means and variances from the sums.
 #include <math.h>
 #include <stdint.h>
 
@@ -60,6 +61,20 @@ __global__ void __launch_bounds__(NT) gram_stats_kernel(const float* __restrict_
   }
 }
 
+// Means and population variances from the sums: out[6..9] = mean K_q, var K_q, mean log K_q,
+// var log K_q (NaN when nothing was counted; a variance rounding below 0 is set to 0).
+__global__ void gram_stats_finish_kernel(double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const double c = out[3 * q], s1 = out[3 * q + 1], s2 = out[3 * q + 2];
+    const double mean = c > 0.0 ? s1 / c : nan("");
+    const double var = c > 0.0 ? fmax(s2 / c - mean * mean, 0.0) : nan("");
+    out[6 + 2 * q] = mean;
+    out[7 + 2 * q] = var;
+  }
+}
+
 }  // namespace stats
 }  // namespace dk
 
@@ -70,12 +85,15 @@ DK_API dk_status dk_gram_stats(dk_ctx* ctx, const float* kq, const float* logkq,
   if (!ctx || (!kq && !logkq) || !out || nrows < 1 || ncols < 1 || ld < ncols) return DK_ERR_ARG;
   if (symmetric && nrows != ncols) return DK_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(out, 0, 6 * sizeof(double), st) != cudaSuccess) return DK_ERR_CUDA;
+  if (cudaMemsetAsync(out, 0, 10 * sizeof(double), st) != cudaSuccess) return DK_ERR_CUDA;
   const long long total = (long long)nrows * ncols;
   long long blocks = (total + stats::NT * 8 - 1) / (stats::NT * 8);
   const long long cap = (long long)ctx->sm_count * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   stats::gram_stats_kernel<<<int(blocks), stats::NT, 0, st>>>(kq, logkq, ld, nrows, ncols, symmetric, out);
+  dk_status s = launch_status();
+  if (s != DK_OK) return s;
+  stats::gram_stats_finish_kernel<<<1, 32, 0, st>>>(out);
   return launch_status();
 }

@@ -30,7 +30,7 @@ EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_
             "dk_svm_ovo_train", "dk_svm_ovo_predict", "dk_gram_stats", "dk_pca_workspace_bytes", "dk_pca_fit",
             "dk_pca_transform", "dk_pca_fit_noalloc", "dk_mps_build_blocks", "dk_block_states_bytes",
             "dk_block_states", "dk_gram_blocks", "dk_gram_sweep", "dk_workspace_bytes",
-            "dk_set_block_gram_form")
+            "dk_set_block_gram_form", "dk_block_states_workspace_bytes", "dk_gram_blocks_workspace_bytes")
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 PCA_MAX_FEATURES = 4096  # DK_PCA_MAX_FEATURES
 PCA_NOALLOC_MAX_FEATURES = 256  # DK_PCA_NOALLOC_MAX_FEATURES
@@ -80,11 +80,16 @@ def _lib():
     lib.dk_gram_sweep.restype = i32
     lib.dk_block_states_bytes.argtypes = [i32, i32, i32]
     lib.dk_block_states_bytes.restype = ctypes.c_size_t
-    lib.dk_block_states.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, i32, vp, vp, vp]
+    sz = ctypes.c_size_t
+    lib.dk_block_states.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Fmap), i32, i32, vp, vp, vp, sz, vp]
     lib.dk_block_states.restype = i32
+    lib.dk_block_states_workspace_bytes.argtypes = [vp, i32, i32, i32, i32]
+    lib.dk_block_states_workspace_bytes.restype = sz
     lib.dk_gram_blocks.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, f32, f32,
-                                   i32, vp, vp, vp, vp, i64, i32, vp]
+                                   i32, vp, vp, vp, vp, i64, i32, vp, sz, vp]
     lib.dk_gram_blocks.restype = i32
+    lib.dk_gram_blocks_workspace_bytes.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32]
+    lib.dk_gram_blocks_workspace_bytes.restype = sz
     lib.dk_gram_tile.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, i32,
                                  vp, vp, vp, vp, f32, f32, i32, vp, vp, vp, vp, i64, i32, vp]
     lib.dk_gram_tile.restype = i32
@@ -343,9 +348,11 @@ def block_states(ctx: Context, x: torch.Tensor, fmap: FeatureMap, entangler: int
         raise ValueError(f"block {fmap.block} is outside the supported range for n = {n}")
     out = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
     log_norm = torch.empty(m, dtype=torch.float32, device=x.device)
+    ws_bytes = int(_lib().dk_block_states_workspace_bytes(ctx.handle, m, n, int(fmap.block), int(prec)))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=x.device) if ws_bytes else None
     fm = fmap._c()
     _check(_lib().dk_block_states(ctx.handle, _ptr(x), m, n, ctypes.byref(fm), int(entangler), int(prec), _ptr(out),
-                                  _ptr(log_norm), _stream(stream)), "dk_block_states")
+                                  _ptr(log_norm), _ptr(ws), ws_bytes, _stream(stream)), "dk_block_states")
     return BlockStates(out, m, n, fmap.block, log_norm, x, int(prec))
 
 
@@ -358,12 +365,16 @@ def gram_blocks(ctx: Context, rows: BlockStates, cols: BlockStates | None = None
         raise ValueError("row and column states differ in n, block or precision")
     gamma = 1.0 / rows.n if gamma is None else gamma
     out = _outs((rows.m, cols.m), rows.data.device, want)
+    with_kc = out.get("kc") is not None or (out.get("k") is not None and w != 1.0)
+    ws_bytes = int(_lib().dk_gram_blocks_workspace_bytes(ctx.handle, rows.n, rows.block, rows.m, cols.m, rows.prec,
+                                                         1 if symmetric else 0, 1 if with_kc else 0))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=rows.data.device) if ws_bytes else None
     _check(_lib().dk_gram_blocks(ctx.handle, _ptr(rows.data), rows.m, _ptr(cols.data), cols.m, rows.n, rows.block,
                                  0, rows.m, 0, cols.m, _ptr(rows.log_norm), _ptr(cols.log_norm), _ptr(rows.x),
                                  _ptr(cols.x), float(gamma), float(w), rows.prec, _ptr(out.get("k")),
                                  _ptr(out.get("kq")),
                                  _ptr(out.get("kc")), _ptr(out.get("logkq")), int(cols.m), 1 if symmetric else 0,
-                                 _stream(stream)), "dk_gram_blocks")
+                                 _ptr(ws), ws_bytes, _stream(stream)), "dk_gram_blocks")
     return out
 
 
@@ -502,22 +513,20 @@ def svm_ovo_predict(ctx: Context, kq: torch.Tensor | None, kc: torch.Tensor | No
 def gram_stats(ctx: Context, kq: torch.Tensor | None, logkq: torch.Tensor | None = None,
                symmetric: bool = True, stream=None) -> dict:
     """dk_gram_stats: mean and variance of the off-diagonal K_q and log K_q of a Gram block
-    (the strict upper triangle when symmetric). Reads back six numbers."""
+    (the strict upper triangle when symmetric), formed on the device. Reads back ten numbers."""
     ref = kq if kq is not None else logkq
     _need_cuda(kq, "kq", torch.float32)
     _need_cuda(logkq, "logkq", torch.float32)
-    out = torch.empty(6, dtype=torch.float64, device=ref.device)
+    out = torch.empty(10, dtype=torch.float64, device=ref.device)
     _check(_lib().dk_gram_stats(ctx.handle, _ptr(kq), _ptr(logkq), int(ref.stride(0)), int(ref.shape[0]),
                                 int(ref.shape[1]), 1 if symmetric else 0, _ptr(out), _stream(stream)),
            "dk_gram_stats")
-    c, s1, s2, cl, l1, l2 = out.cpu().tolist()
+    c, _, _, cl, _, _, kq_mean, kq_var, l_mean, l_var = out.cpu().tolist()
     res = {"pairs": int(c), "finite_log_pairs": int(cl)}
     if c > 0:
-        res["kq_mean"] = s1 / c
-        res["kq_var"] = max(s2 / c - (s1 / c) ** 2, 0.0)
+        res["kq_mean"], res["kq_var"] = kq_mean, kq_var
     if cl > 0:
-        res["logkq_mean"] = l1 / cl
-        res["logkq_var"] = max(l2 / cl - (l1 / cl) ** 2, 0.0)
+        res["logkq_mean"], res["logkq_var"] = l_mean, l_var
     return res
 
 

@@ -92,6 +92,70 @@ def compare(m: int = 512, d: int = 256, pool: int = 128, n_uniform: int = 40, n_
     return res
 
 
+def _event_ms(fn):
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    fn()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def sampled_pairs_full_size(pairs, near_base, m: int = 4000, d: int = 256, near_sigma=(1e-4, 2.5e-2),
+                            near_seed: int = 65, ctx: dualk.Context | None = None):
+    """The precision form at full size: the whole m x m Gram of the d-feature Fashion-MNIST-shaped
+    set at reps = 3 (bond 8, FP32) and reps = 5 (bond 32, FP32 and split-BF16 tensor cores),
+    each timed once, and the rows of the near copies of the samples `near_base` against the
+    set. Returns, per path, the timings and the K_q and log K_q of the listed pairs:
+    pairs = [(group, i, j)], group "near_copy" meaning (set sample i, copy j), else the Gram
+    entry (i, j)."""
+    own = ctx is None
+    ctx = ctx or dualk.Context(0)
+    x = synthetic.fmnist_like(m, 0, d)["x_train"]
+    xn = synthetic.near_copies(x[np.asarray(near_base)], near_sigma[0], near_sigma[1], seed=near_seed)
+    xt = torch.from_numpy(x).cuda()
+    xnt = torch.from_numpy(xn).cuda()
+    gi = torch.tensor([i for g, i, j in pairs if g != "near_copy"], device="cuda", dtype=torch.long)
+    gj = torch.tensor([j for g, i, j in pairs if g != "near_copy"], device="cuda", dtype=torch.long)
+    ri = torch.tensor([j for g, i, j in pairs if g == "near_copy"], device="cuda", dtype=torch.long)
+    rj = torch.tensor([i for g, i, j in pairs if g == "near_copy"], device="cuda", dtype=torch.long)
+    is_row = np.array([g == "near_copy" for g, _, _ in pairs])
+    res = {"workload": f"fmnist d={d} m={m}: full symmetric Gram + rows of {len(near_base)} near copies"}
+    out = {"kq": torch.empty((m, m), device="cuda"), "logkq": torch.empty((m, m), device="cuda")}
+    rows = {"kq": torch.empty((len(near_base), m), device="cuda"),
+            "logkq": torch.empty((len(near_base), m), device="cuda")}
+    for reps, chi, precs in ((3, 8, (("fp32", dualk.DK_PREC_F32),)),
+                             (5, 32, (("fp32", dualk.DK_PREC_F32), ("bf16x3", dualk.DK_PREC_BF16X3)))):
+        fm = dualk.FeatureMap(reps=reps, chi_max=chi)
+        mp = dualk.mps_build(ctx, xt, fm)
+        mpn = dualk.mps_build(ctx, xnt, fm)
+        for name, prec in precs:
+            mp.log_norm_for(ctx, prec)
+            mpn.log_norm_for(ctx, prec)
+            torch.cuda.synchronize()
+            g_ms = _event_ms(lambda: dualk.gram_tile(ctx, mp, mp, symmetric=True, out=out, ld=m, w=1.0, prec=prec,
+                                                     want=("kq", "logkq")))
+            r_ms = _event_ms(lambda: dualk.dual_kernel_rows(ctx, mpn, mp, w=1.0, out=rows, prec=prec,
+                                                            want=("kq", "logkq")))
+            kq = np.empty(len(pairs))
+            lkq = np.empty(len(pairs))
+            kq[~is_row] = out["kq"][gi, gj].double().cpu().numpy()
+            lkq[~is_row] = out["logkq"][gi, gj].double().cpu().numpy()
+            kq[is_row] = rows["kq"][ri, rj].double().cpu().numpy()
+            lkq[is_row] = rows["logkq"][ri, rj].double().cpu().numpy()
+            units = workload.gram_entries(m) * d
+            res[f"chi{chi}_{name}"] = {
+                "gram_ms": g_ms, "rows_ms": r_ms, "gram_entry_qubits_per_s": units / (g_ms / 1e3),
+                "gram_tflops_block_count": workload.gram_entries(m) * workload.flops_per_pair(d, reps) / g_ms / 1e9,
+                "kq": kq, "logkq": lkq}
+        del mp, mpn
+    ctx.sync_status()
+    if own:
+        ctx.close()
+    return res
+
+
 def compare_build_qr(m: int = 2000, d: int = 784, block: int = 256, ctx: dualk.Context | None = None):
     """The bond-4 MPS build with its QR sweep in FP32 (default) and in FP64, both stored as
     complex64: build time for m samples at d features, and the largest |dK| and |d log K|

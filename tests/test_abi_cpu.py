@@ -103,3 +103,14 @@ def test_workload_accounting():
     # block count at n = 784: sites 1, 2, 783, 784 cost 32, 192, 192, 64 flops
     assert workload.flops_per_pair(784, 2) == 780 * 512 + 32 + 192 + 192 + 64
     assert workload.gram_entries(4) == 10 and workload.gram_entries(4, False, 3) == 12
+
+
+def test_block_workspace_queries_without_context(lib):
+    # The scratch queries of the block calls need a context (the plan depends on the SM
+    # count); without one they return 0 rather than guess.
+    lib.dk_block_states_workspace_bytes.restype = ctypes.c_size_t
+    lib.dk_block_states_workspace_bytes.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4
+    lib.dk_gram_blocks_workspace_bytes.restype = ctypes.c_size_t
+    lib.dk_gram_blocks_workspace_bytes.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 7
+    assert lib.dk_block_states_workspace_bytes(None, 100, 40, 10, 2) == 0
+    assert lib.dk_gram_blocks_workspace_bytes(None, 40, 10, 100, 100, 2, 1, 1) == 0

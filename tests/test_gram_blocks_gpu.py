@@ -419,3 +419,53 @@ def test_svm_workflow_on_a_block_map(dk):
     assert out["test_accuracy"] > 0.5
     assert 0.0 <= out["cv_accuracy_by_w"]["1.0"] <= 1.0
     ctx.sync_status()
+
+
+def test_tcgen05_block_calls_use_the_callers_workspace(dk):
+    """The tcgen05 form takes its scratch from the caller: the queries give the sizes (the
+    RBF distances, and partial sums of a rectangular block split over its blocks), a call
+    with too small a workspace returns DK_ERR_WORKSPACE without launching, and a call with
+    the queried size matches the binding's result bit for bit."""
+    import ctypes
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    lib = dualk._lib()
+    d = synthetic.fmnist_like(300, 40, 60)
+    fm = dualk.FeatureMap(reps=2, block=10)
+    xtr, xte = _dev(torch, d["x_train"]), _dev(torch, d["x_test"])
+    ws_states = int(lib.dk_block_states_workspace_bytes(ctx.handle, 300, 60, 10, dualk.DK_PREC_BF16X3))
+    assert ws_states >= 6 * 300 * 4 and ws_states % 256 == 0
+    assert int(lib.dk_block_states_workspace_bytes(ctx.handle, 300, 60, 10, dualk.DK_PREC_F32)) == 0
+    s_tr = dualk.block_states(ctx, xtr, fm, dualk.DK_ENT_FULL, prec=dualk.DK_PREC_BF16X3)
+    s_te = dualk.block_states(ctx, xte, fm, dualk.DK_ENT_FULL, prec=dualk.DK_PREC_BF16X3)
+    # states with too small a workspace: rejected on the host
+    out = torch.empty_like(s_tr.data)
+    ln = torch.empty(300, device="cuda")
+    small = torch.empty(ws_states - 256, dtype=torch.uint8, device="cuda")
+    fmc = fm._c()
+    st = dualk._stream(None)
+    assert lib.dk_block_states(ctx.handle, dualk._ptr(xtr), 300, 60, ctypes.byref(fmc), dualk.DK_ENT_FULL,
+                               dualk.DK_PREC_BF16X3, dualk._ptr(out), dualk._ptr(ln), dualk._ptr(small),
+                               ws_states - 256, st) == 5
+    # rows 40 x 300: 1 x 3 tiles of 128 x 128, fewer than the SMs, so the blocks are split
+    ws_rows = int(lib.dk_gram_blocks_workspace_bytes(ctx.handle, 60, 10, 40, 300, dualk.DK_PREC_BF16X3, 0, 1))
+    ws_rows_nokc = int(lib.dk_gram_blocks_workspace_bytes(ctx.handle, 60, 10, 40, 300, dualk.DK_PREC_BF16X3, 0, 0))
+    ws_sym = int(lib.dk_gram_blocks_workspace_bytes(ctx.handle, 60, 10, 300, 300, dualk.DK_PREC_BF16X3, 1, 1))
+    assert ws_rows > ws_rows_nokc > 0
+    assert ws_rows - ws_rows_nokc == (40 * 300 * 4 + 255) // 256 * 256
+    assert ws_sym == (300 * 300 * 4 + 255) // 256 * 256
+    assert int(lib.dk_gram_blocks_workspace_bytes(ctx.handle, 60, 10, 300, 300, dualk.DK_PREC_F32, 1, 1)) == 0
+    ref = dualk.gram_blocks(ctx, s_te, s_tr, w=0.5)
+    k = torch.empty((40, 300), device="cuda")
+    args = lambda ws, nb: (ctx.handle, dualk._ptr(s_te.data), 40, dualk._ptr(s_tr.data), 300, 60, 10, 0, 40, 0, 300,
+                           dualk._ptr(s_te.log_norm), dualk._ptr(s_tr.log_norm), dualk._ptr(xte), dualk._ptr(xtr),
+                           1.0 / 60, 0.5, dualk.DK_PREC_BF16X3, dualk._ptr(k), None, None, None, 300, 0,
+                           dualk._ptr(ws), nb, st)
+    tiny = torch.empty(ws_rows - 256, dtype=torch.uint8, device="cuda")
+    assert lib.dk_gram_blocks(*args(tiny, ws_rows - 256)) == 5
+    assert lib.dk_gram_blocks(*args(None, 0)) == 5
+    ws = torch.full((ws_rows,), 0xAB, dtype=torch.uint8, device="cuda")  # stale contents must not matter
+    assert lib.dk_gram_blocks(*args(ws, ws_rows)) == 0
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert torch.equal(k, ref["k"])
