@@ -13,7 +13,9 @@ Unit of work: one entry x qubit (one pair through one site). Entries per step =
 Default arm: our CUDA library (libdualk.so) through its Python binding. `--impl reference`
 times the FP64 CPU oracle on a bounded sample of the same workload.
 Multi-GPU (torchrun, one rank per GPU): each rank runs its own independent problem of the
-same size (weak scaling, no collective on the data path).
+same size (weak scaling, no collective on the data path). `--split` instead splits one
+8000-sample Gram at n = 784 into balanced row blocks over the ranks (strong scaling; the
+blocks are gathered to the hosts in the end-to-end leg only).
 """
 from __future__ import annotations
 
@@ -385,34 +387,39 @@ def run_ours(args):
         cfg_gram = tuner.best(mtr0, symmetric=True)
         cfg_rows = tuner.best(mte0, symmetric=False, cols=mtr0)
 
-    phase_events = []  # per timed step: events before build, Gram, rows, and after rows
+    phase_events = []  # per timed step: events around build, Gram, its refinement, rows, theirs
 
     def step(record=False):
         # The test-set build runs on a side stream beside the training-set build (each is a
         # latency-bound chain per sample); the Gram and the rows then run one after the other
-        # on the main stream, so each launch's own time is measured.
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
-        if record:
-            ev[0].record(stream)
+        # on the main stream, each followed by its refinement pass, so each launch's own time
+        # is measured.
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)] if record else None
+        rec = (lambda q: ev[q].record(stream)) if record else (lambda q: None)
+        rec(0)
         side.wait_stream(stream)
         mtr = dualk.mps_build(ctx, x_tr, fm, out=mps_tr, bond=bond_tr, log_norm=ln_tr)
         mte = dualk.mps_build(ctx, x_te, fm, out=mps_te, bond=bond_te, log_norm=ln_te, stream=side)
-        if record:
-            ev[1].record(stream)
+        rec(1)
         ctx.set_gram_config(cfg_gram)
-        dualk.gram_tile(ctx, mtr, mtr, symmetric=True, w=w, out=g_out, ld=n_tr)
-        if record:
-            ev[2].record(stream)
+        dualk.gram_tile(ctx, mtr, mtr, symmetric=True, w=w, out=g_out, ld=n_tr, refine=None)
+        rec(2)
+        dualk.gram_refine(ctx, mtr, mtr, 0, n_tr, 0, n_tr, g_out, n_tr, 1.0 / d, w, symmetric=True)
+        rec(3)
         stream.wait_stream(side)
         ctx.set_gram_config(cfg_rows)
-        dualk.dual_kernel_rows(ctx, mte, mtr, w=w, out=r_out)
+        dualk.dual_kernel_rows(ctx, mte, mtr, w=w, out=r_out, refine=None)
+        rec(4)
+        dualk.gram_refine(ctx, mte, mtr, 0, n_te, 0, n_tr, r_out, n_tr, 1.0 / d, w)
+        rec(5)
         if record:
-            ev[3].record(stream)
             phase_events.append(ev)
 
-    # MPS build x 2 (the ln-norms are fused into the build at bond 4), Gram, rows: the ncu launch
-    # list of this command shows exactly these four libdualk kernels per step
-    launches_per_step = 2 + 1 + 1
+    # MPS build x 2 (the ln-norms are fused into the build at bond 4), Gram, rows, and the
+    # refinement pass after each of the two (dk_gram_refine: entries with K_q > 0.02
+    # recomputed in double-word FP32; here a scan of the block, as no off-diagonal K_q of
+    # independent 784-qubit samples comes near it): six libdualk kernels per step
+    launches_per_step = 2 + 1 + 1 + 2
 
     def barrier():
         if world > 1:
@@ -447,7 +454,9 @@ def run_ours(args):
     gram_ms = [ev[1].elapsed_time(ev[2]) for ev in phase_events]
     phases = {"mps_build_ms": statistics.mean(ev[0].elapsed_time(ev[1]) for ev in phase_events),
               "gram_ms": statistics.mean(gram_ms),
-              "rows_ms": statistics.mean(ev[2].elapsed_time(ev[3]) for ev in phase_events)}
+              "gram_refine_ms": statistics.mean(ev[2].elapsed_time(ev[3]) for ev in phase_events),
+              "rows_ms": statistics.mean(ev[3].elapsed_time(ev[4]) for ev in phase_events),
+              "rows_refine_ms": statistics.mean(ev[4].elapsed_time(ev[5]) for ev in phase_events)}
 
     units_step = entries_per_step(n_tr, n_te) * d
     value = world * units_step * args.steps / (ms / 1e3)
@@ -485,14 +494,17 @@ def run_ours(args):
     # at bond 32 on 512 samples (d = 256, where every off-diagonal K_q is tiny, and d = 16,
     # where many are not); the FP32 against the FP64 QR sweep of the bond-4 build; and the
     # continuous-batching server's latency.
-    mixed = serving_stats = svm_stats = block_stats = None
+    mixed = serving_stats = svm_stats = block_stats = sweep_stats = None
     if rank == 0 and world == 1 and not args.no_extras:
         from paper_2602_01330_gb300 import blockmap, precision, serving, svm
+        from paper_2602_01330_gb300 import sweep as gsweep
+        # the feature-dimension sweep: ten 2000-sample Grams, d = 2 .. 784
+        sweep_stats = gsweep.run_benchmark(ctx, m=2000, peak_tflops=peak_tflops)
         mixed = {"cfg3_full_size_vs_oracle": precision_vs_oracle(ctx),
                  "d256": precision.compare(m=512, pool=128, n_uniform=40, n_near=20, n_diag=10, ctx=ctx),
                  "d16": precision.compare(m=512, d=16, pool=128, n_uniform=40, n_near=20, n_diag=10, ctx=ctx),
                  "mps_build_qr": precision.compare_build_qr(ctx=ctx)}
-        serving_stats = serving.run_benchmark(ctx, m=8000, requests=150, rho=0.8, slots=8)
+        serving_stats = serving.run_benchmark(ctx, m=8000, requests=2000, rho=(0.5, 0.8, 0.95), slots=8)
         # the SVM that consumes this step's Gram and rows: 5-fold CV over C x w, fit, test votes
         svm_stats = svm.run_pipeline(ctx, n_tr, n_te, d, reps,
                                      gram=(g_out["kq"], g_out["kc"], r_out["kq"], r_out["kc"]))
@@ -535,6 +547,119 @@ def run_ours(args):
         "serving": serving_stats,
         "svm": svm_stats,
         "block_product_map": block_stats,
+        "feature_dimension_sweep": sweep_stats,
+    }
+    print(json.dumps(line), flush=True)
+
+
+SPLIT_WL = dict(workload="fmnist784_gram8000_rowsplit", d=784, m=8000, reps=2, chi=4, w=0.5)
+
+
+def run_split(args):
+    """Strong scaling over one Gram (§II-D: blocks of one kernel matrix on several GPU workers):
+    the 8000-sample symmetric Gram at n = 784 split into balanced row blocks, one per rank
+    (shard.gram_row_block: no exchange while computing). value = the Gram's unique entries x
+    qubits / the slowest rank's time per step; e2e adds, every step, the host-to-device copy of
+    the features and the gather of every rank's K block into each rank's host memory."""
+    import torch
+    import torch.distributed as tdist
+
+    from paper_2602_01330_gb300 import build as libbuild
+    from paper_2602_01330_gb300 import dualk, shard, synthetic, workload
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not os.path.exists(dualk.LIB_PATH):
+        libbuild.build()
+    m, d, reps, chi, w = SPLIT_WL["m"], SPLIT_WL["d"], SPLIT_WL["reps"], SPLIT_WL["chi"], SPLIT_WL["w"]
+    data = synthetic.fmnist_like(m, 0, d)
+    ctx = dualk.Context(local)
+    fm = dualk.FeatureMap(reps=reps, chi_max=chi)
+    stream = torch.cuda.current_stream()
+    x = torch.from_numpy(data["x_train"]).to(dev)
+    mps_buf = torch.empty(dualk.mps_bytes(m, d, chi), dtype=torch.uint8, device=dev)
+    bond = torch.empty(d + 1, dtype=torch.int32, device=dev)
+    ln = torch.empty(m, dtype=torch.float32, device=dev)
+    lo, hi = shard.balanced_row_blocks(m, world)[rank]
+    block = {k: torch.empty((hi - lo, m - lo), dtype=torch.float32, device=dev) for k in ("k", "kq", "kc", "logkq")}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    def step():
+        mp_ = dualk.mps_build(ctx, x, fm, out=mps_buf, bond=bond, log_norm=ln)
+        shard.gram_row_block(ctx, mp_, rank, world, w=w, out=block)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ctx.sync_status()
+    units_step = workload.gram_entries(m) * d
+    value = units_step * args.steps / (ms / 1e3)
+    # end to end: features in from pinned host memory, K blocks gathered to every rank's host
+    h_x = torch.from_numpy(data["x_train"]).pin_memory()
+    e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(e_steps):
+        x.copy_(h_x, non_blocking=True)
+        step()
+        if world > 1:
+            full = shard.gather_gram({"k": block["k"]}, m, world)
+        else:
+            full = {"k": shard.assemble([block["k"].cpu()], [(lo, hi)], m)}
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = (time.perf_counter() - e0) / e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    assert full["k"].shape == (m, m)
+    if world > 1:
+        tdist.destroy_process_group()
+    ctx.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (Fashion-MNIST-shaped, seeded; the real data set is not available)",
+        "config": {"workload": SPLIT_WL["workload"], "d": d, "m": m, "reps": reps, "chi": chi, "w": w,
+                   "parallelism": f"balanced row blocks of one Gram over {world} GPU(s)",
+                   "l2": "256 MB buffer written before every timed step (inside the timed region)"},
+        "e2e": {"value": units_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h_x.numel() * 4,
+                "d2h_bytes_per_step": (hi - lo) * (m - lo) * 4, "gather": "all ranks' K blocks to every host"},
+        "gpu_launches": (1 + 2 * (1 if hi < m else 0) + 2) * args.steps,
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 
@@ -553,12 +678,16 @@ def main():
     ap.add_argument("--n-train", type=int, default=WL["n_train"],
                     help="training-set size; smaller cases serve ncu captures, not bench lines")
     ap.add_argument("--n-test", type=int, default=WL["n_test"])
+    ap.add_argument("--split", action="store_true",
+                    help="strong scaling: one 8000-sample Gram split into row blocks over the ranks")
     args = ap.parse_args()
     if (args.n_train, args.n_test) != (WL["n_train"], WL["n_test"]):
         WL.update(n_train=args.n_train, n_test=args.n_test,
                   workload=f"fmnist784_gram{args.n_train}_rows{args.n_test}")
     if args.impl == "reference":
         run_reference(args)
+    elif args.split:
+        run_split(args)
     else:
         run_ours(args)
 

@@ -222,7 +222,8 @@ typedef struct {
 /* The symmetric Gram matrices of a feature-dimension sweep (§II-D: a kernel matrix for
  * every qubit count of a study, each filled block by block), each item as
  * dk_gram_tile over all its samples with gamma = 1/n, mix weight w and precision prec,
- * issued in order on `stream`.
+ * followed, for complex64 items in F32 or BF16X3 with kq or logkq, by dk_gram_refine with
+ * tau = DK_REFINE_TAU (declared below), issued in order on `stream`.
  * graph = 0: the launches are issued directly.
  * graph = 1: the launches are recorded once into a CUDA graph that the context keeps
  *   (keyed by the bytes of the item array and the other arguments, pointers included) and
@@ -377,6 +378,39 @@ dk_status dk_dual_kernel_rows(dk_ctx* ctx,
                               dk_precision prec,
                               float* k_out, float* kq_out, float* kc_out, float* logkq_out,
                               void* stream);
+
+/* Threshold the sweep call and the Python binding use for dk_gram_refine. */
+#define DK_REFINE_TAU 0.02f
+
+/* Refinement of the large values of a block written by dk_gram_tile or dk_dual_kernel_rows
+ * (§II-C Eqs. 7-10; §II-D Eq. 11). The FP32 transfer chain rounds E at every site, and the
+ * rounding of its dominant direction adds up over the n sites like a random walk: a K_q of
+ * order one comes out with a relative error of about sqrt(n) * 6 u (7e-6 at n = 784, bond 4;
+ * 1e-5 at bond 32 and n = 256; split-BF16 products, about 16 significant bits: 1e-3), small
+ * values with the same relative error. This call recomputes every entry of the block with
+ * K_q > tau (log K_q > ln tau when kq_out is NULL): the amplitude and both self-overlaps by
+ * the same chain on the same complex64 tensors, with E kept as double-word FP32 sums hi + lo
+ * (error-free products and additions, about 44 bits), and writes K_q, log K_q and K (K_c
+ * read from kc_out or recomputed as the Gram call forms it). Other entries keep their bits;
+ * the diagonal of a symmetric block (exactly 1) is not touched. With tau = 0.02 the FP32
+ * paths stay within |dK| <= 1e-6 and the split-BF16 path within 1e-4 of the exact values.
+ *   The block arguments are those of the Gram call that wrote it: rows [row0, row0 + nrows)
+ *   of mps_rows x columns [col0, col0 + ncols) of mps_cols (dk_mps_build layout, complex64,
+ *   chi_max 4, 8 or 32), outputs with row stride ld; symmetric as for dk_gram_tile (only
+ *   j > i is examined, both entries written). x_rows / x_cols, gamma, w: as for that call
+ *   (x needed only when k_out is given with w != 1 and kc_out is NULL).
+ *   tau in (0, 1).
+ * Bond 4 / 8: one thread per refined entry; bond 32: one warp per entry (three chains of
+ * about 1e9 operations each), so the cost is proportional to the number of entries above
+ * tau: nothing but one read of the block when there are none.
+ * Errors: DK_ERR_ARG (NULL pointers, ranges, ld < ncols, neither kq_out nor logkq_out, tau
+ *         outside (0, 1), symmetric with different rows and columns, x missing when K_c has
+ *         to be recomputed, misaligned MPS), DK_ERR_UNSUPPORTED (complex128, other chi_max),
+ *         DK_ERR_CUDA. */
+dk_status dk_gram_refine(dk_ctx* ctx, const void* mps_rows, int m_rows, const void* mps_cols, int m_cols, int n,
+                         int chi_max, dk_dtype dtype, int row0, int nrows, int col0, int ncols, const float* x_rows,
+                         const float* x_cols, float gamma, float w, float tau, float* k_out, float* kq_out,
+                         float* kc_out, float* logkq_out, long long ld, int symmetric, void* stream);
 
 /* Tile shapes of the Gram kernels (the blocks of §II-D, sized for one GB300 SM).
  * Shape 0 is the built-in choice; shapes 1..dk_gram_config_count(dtype, chi_max) can be

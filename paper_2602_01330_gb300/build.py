@@ -17,7 +17,7 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(HERE, "libdualk.so")
 SOURCES = ["api.cu", "mps_build.cu", "gram.cu", "gram32.cu", "gram32_tc.cu", "svm.cu", "stats.cu", "pca.cu",
            "block_svd.cu", "gram_blocks.cu",
-           "sweep.cu", "gram_blocks_tc.cu", "gram_blocks_umma.cu"]
+           "sweep.cu", "gram_blocks_tc.cu", "gram_blocks_umma.cu", "refine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
               "-Xptxas", "-v", "-I", os.path.join(ROOT, "include")]

@@ -513,7 +513,8 @@ dk_status launch_gram(dk_ctx* ctx, const void* sr, int m_r, const void* sc, int 
   if (s == DK_OK) s = encode_states_map(ctx, &tc, sc, m_c, nb, dp, BN);
   if (s == DK_OK) s = set_smem<BN, WIDE>();
   if (s != DK_OK) return s;
-  a.ntiles = ntiles;
+  a.ntiles = count_tiles(a, BM, BN);  // also sets the tile grid (tiles_r, tiles_c) the kernel decodes
+  if (a.ntiles != ntiles) return DK_ERR_ARG;
   const long long items = (long long)ntiles * ksplit;
   const int grid = int(items < ctx->sm_count ? items : ctx->sm_count);
   if (grid < 1) return DK_OK;

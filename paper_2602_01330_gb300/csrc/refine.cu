@@ -1,0 +1,458 @@
+// Refinement of the large kernel values of a Gram block in double-word FP32 arithmetic.
+//
+// The transfer chain (§II-C, Eqs. 8-10) rounds E at every site. In FP32 the rounding of
+// the chain's dominant direction performs a random walk over the n sites, so a kernel value
+// K_q of order one carries a relative error of about sqrt(n) * 6 u (7e-6 at n = 784 for the
+// bond-4 FP32 kernels; 1e-3 for split-BF16 products at bond 32 and n = 256), while a small
+// K_q has the same relative error and hence a tiny absolute one. This pass scans a block
+// that a Gram call has written and recomputes every entry with K_q > tau: the amplitude
+// a_ij and both self-overlaps N_i, N_j by the same chain with E held as unevaluated sums
+// hi + lo of two floats (double-word numbers, about 44 significant bits). The site tensors
+// are the stored complex64 ones, exact as FP32 inputs, so only the arithmetic changes:
+//   products    x (double-word) * y (float): p = hi y rounded, its exact error
+//               fma(hi, y, -p), plus lo y;
+//   dot products Dot2 accumulation: the rounded sum of the p's with TwoSum's exact error of
+//               every addition and the product errors in a second float; normalised with
+//               Fast2Sum into hi + lo once per output element (Ogita, Rump and Oishi, 2005);
+//   rescaling   hi and lo multiplied by the same power of two (exact).
+// __fadd_rn / __fmul_rn keep the error-free transforms from being contracted into FMAs.
+// log K_q = 2 ln|a_ij| - ln N_i - ln N_j is then formed in FP64 and K_q, K = w K_q +
+// (1 - w) K_c and log K_q are written back (K_c is read from the block, or recomputed with
+// the Gram kernels' compensated feature sum). Entries with K_q <= tau keep their values.
+//
+// Bond 4 and 8: one thread per pair, E in registers. Bond 32: one warp per pair, E, the
+// intermediate F and the two samples' site blocks in shared memory; each warp tests 32
+// entries at once and works through the hits among them.
+#include <math.h>
+
+#include "common.cuh"
+#include "gram_common.cuh"
+#include "internal.h"
+
+namespace dk {
+namespace rf {
+
+struct DW {
+  float hi, lo;
+};
+
+// Dot2 accumulator: s holds the rounded running sum, c the running sum of the errors.
+struct Acc {
+  float s, c;
+};
+
+__device__ __forceinline__ void acc_add(Acc& A, DW x, float y) {
+  const float p = __fmul_rn(x.hi, y);
+  float q = fmaf(x.hi, y, -p);
+  q = fmaf(x.lo, y, q);
+  const float s = __fadd_rn(A.s, p);
+  const float bp = __fsub_rn(s, A.s);
+  const float e = __fadd_rn(__fsub_rn(A.s, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  A.s = s;
+  A.c = __fadd_rn(A.c, __fadd_rn(e, q));
+}
+
+__device__ __forceinline__ DW acc_get(const Acc& A) {
+  const float s = __fadd_rn(A.s, A.c);
+  return {s, __fsub_rn(A.c, __fsub_rn(s, A.s))};
+}
+
+__device__ __forceinline__ int exponent_of(float v) { return int((__float_as_uint(v) >> 23) & 0xffu) - 127; }
+__device__ __forceinline__ float pow2_neg(int e) { return __uint_as_float(uint32_t(127 - e) << 23); }
+
+// Complex element (s, jc, l) of a sample's compact site tensor (chi x chi complex64).
+__device__ __forceinline__ float2 site_elem(const float2* a, int chi, int h, int s, int jc, int l) {
+  return __ldg(a + (s * h + jc) * chi + l);
+}
+
+// ---------------- bond 4 / 8: one thread per chain ----------------
+
+template <int H>
+struct ChainE {
+  DW r[2][H][H], i[2][H][H];
+};
+
+// ln|<psi~_i|psi~_j>| by the double-word chain (FP64 result). mi / mj: the two MPS, with
+// sample counts m_i / m_j (site-major layout).
+template <int H>
+__device__ double chain_half_log(const float2* __restrict__ mi, int m_i, int i, const float2* __restrict__ mj, int m_j,
+                                 int j, int n) {
+  constexpr int CHI = 2 * H;
+  ChainE<H> E;
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int a = 0; a < H; ++a)
+#pragma unroll
+      for (int c = 0; c < H; ++c) E.r[t][a][c] = E.i[t][a][c] = DW{0.0f, 0.0f};
+  E.r[0][0][0] = DW{1.0f, 0.0f};
+  int e2 = 0;
+  for (int k = 0; k < n; ++k) {
+    const float2* ai = mi + (size_t(k) * m_i + i) * (CHI * CHI);
+    const float2* aj = mj + (size_t(k) * m_j + j) * (CHI * CHI);
+    Acc nr[2][H][H], ni[2][H][H];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < H; ++p)
+#pragma unroll
+        for (int c = 0; c < H; ++c) nr[s][p][c] = ni[s][p][c] = Acc{0.0f, 0.0f};
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        // F = E_t B with B[b][c] = A_s[t](x_j)[b][c] = element (s, c, t H + b) of sample j
+        DW fr[H][H], fi[H][H];
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+          float br[H], bi[H];
+#pragma unroll
+          for (int b = 0; b < H; ++b) {
+            const float2 v = site_elem(aj, CHI, H, s, c, t * H + b);
+            br[b] = v.x;
+            bi[b] = v.y;
+          }
+#pragma unroll
+          for (int a = 0; a < H; ++a) {
+            Acc xr{0.0f, 0.0f}, xi{0.0f, 0.0f};
+#pragma unroll
+            for (int b = 0; b < H; ++b) {
+              acc_add(xr, E.r[t][a][b], br[b]);
+              acc_add(xr, E.i[t][a][b], -bi[b]);
+              acc_add(xi, E.r[t][a][b], bi[b]);
+              acc_add(xi, E.i[t][a][b], br[b]);
+            }
+            fr[a][c] = acc_get(xr);
+            fi[a][c] = acc_get(xi);
+          }
+        }
+        // E'_s[p][c] += sum_a conj(C[a][p]) F[a][c], C[a][p] = element (s, p, t H + a) of sample i
+#pragma unroll
+        for (int p = 0; p < H; ++p) {
+          float cr[H], ci[H];
+#pragma unroll
+          for (int a = 0; a < H; ++a) {
+            const float2 v = site_elem(ai, CHI, H, s, p, t * H + a);
+            cr[a] = v.x;
+            ci[a] = v.y;
+          }
+#pragma unroll
+          for (int c = 0; c < H; ++c)
+#pragma unroll
+            for (int a = 0; a < H; ++a) {
+              acc_add(nr[s][p][c], fr[a][c], cr[a]);
+              acc_add(nr[s][p][c], fi[a][c], ci[a]);
+              acc_add(ni[s][p][c], fi[a][c], cr[a]);
+              acc_add(ni[s][p][c], fr[a][c], -ci[a]);
+            }
+        }
+      }
+    }
+    float mx = 0.0f;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < H; ++p)
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+          E.r[s][p][c] = acc_get(nr[s][p][c]);
+          E.i[s][p][c] = acc_get(ni[s][p][c]);
+          mx = fmaxf(mx, fmaxf(fabsf(E.r[s][p][c].hi), fabsf(E.i[s][p][c].hi)));
+        }
+    if (mx > 0.0f && ((k & 3) == 3 || k == n - 1)) {
+      const int e = exponent_of(mx);
+      const float sc = pow2_neg(e);
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int p = 0; p < H; ++p)
+#pragma unroll
+          for (int c = 0; c < H; ++c) {
+            E.r[s][p][c] = DW{E.r[s][p][c].hi * sc, E.r[s][p][c].lo * sc};
+            E.i[s][p][c] = DW{E.i[s][p][c].hi * sc, E.i[s][p][c].lo * sc};
+          }
+      e2 += e;
+    }
+  }
+  const double re = (double(E.r[0][0][0].hi) + double(E.r[0][0][0].lo)) + (double(E.r[1][0][0].hi) + double(E.r[1][0][0].lo));
+  const double im = (double(E.i[0][0][0].hi) + double(E.i[0][0][0].lo)) + (double(E.i[1][0][0].hi) + double(E.i[1][0][0].lo));
+  return 0.5 * log(re * re + im * im) + double(e2) * 0.69314718055994530942;
+}
+
+struct RefineArgs {
+  GramArgs g;            // block, outputs, x, gamma, w (lnorm unused)
+  const float2* mps_r;
+  const float2* mps_c;
+  int m_r, m_c;
+  float tau, log_tau;
+};
+
+__device__ __forceinline__ bool is_hit(const RefineArgs& a, long long at) {
+  if (a.g.kq) return a.g.kq[at] > a.tau;
+  return a.g.lkq[at] > a.log_tau;
+}
+
+// K_c of pair (i, j) as the Gram kernels form it: the compensated FP32 sum of squared
+// feature differences in feature order.
+__device__ __forceinline__ float kc_of(const GramArgs& g, long long at, int i, int j) {
+  if (g.kc) return g.kc[at];
+  if (!g.need_kc) return 0.0f;
+  float d2 = 0.0f, comp = 0.0f;
+  const float* xa = g.x_r + size_t(i) * g.n;
+  const float* xb = g.x_c + size_t(j) * g.n;
+  for (int f = 0; f < g.n; ++f) kahan_add_sq(d2, comp, __ldg(xa + f) - __ldg(xb + f));
+  return expf(-g.gamma * d2);
+}
+
+__device__ __forceinline__ void write_refined(const GramArgs& g, long long at, int i, int j, double lkq_d) {
+  const float kq = float(exp(lkq_d));
+  const float lkq = float(lkq_d);
+  const float kc = kc_of(g, at, i, j);
+  const float k = g.w * kq + (1.0f - g.w) * kc;
+  if (g.k) g.k[at] = k;
+  if (g.kq) g.kq[at] = kq;
+  if (g.lkq) g.lkq[at] = lkq;
+  if (g.symmetric && i != j) {
+    const long long b = (long long)(j - g.row0) * g.ld + (i - g.col0);
+    if (g.k) g.k[b] = k;
+    if (g.kq) g.kq[b] = kq;
+    if (g.kc) g.kc[b] = kc;
+    if (g.lkq) g.lkq[b] = lkq;
+  }
+}
+
+template <int H>
+__global__ void __launch_bounds__(128) refine_small_kernel(const RefineArgs a) {
+  const GramArgs& g = a.g;
+  const long long total = (long long)g.nrows * g.ncols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = int(e / g.ncols), c = int(e - (long long)r * g.ncols);
+    const int i = g.row0 + r, j = g.col0 + c;
+    if (g.symmetric && j <= i) continue;
+    const long long at = (long long)r * g.ld + c;
+    if (!is_hit(a, at)) continue;
+    const double lij = chain_half_log<H>(a.mps_r, a.m_r, i, a.mps_c, a.m_c, j, g.n);
+    const double lii = chain_half_log<H>(a.mps_r, a.m_r, i, a.mps_r, a.m_r, i, g.n);
+    const double ljj = chain_half_log<H>(a.mps_c, a.m_c, j, a.mps_c, a.m_c, j, g.n);
+    write_refined(g, at, i, j, 2.0 * lij - lii - ljj);
+  }
+}
+
+// ---------------- bond 32: one warp per chain ----------------
+
+constexpr int H32 = 16, CHI32 = 32;
+constexpr int WARPS32 = 4;
+// per warp: E (2 blocks) and F as double-word 16 x 16 complex: [blk][re/im][hi/lo][16][16]
+constexpr int EW = 2 * 2 * 2 * 256;  // floats of E
+constexpr int FW = 2 * 2 * 256;      // floats of F
+constexpr int BW = 2 * 256;          // floats of one 16 x 16 complex float block [re/im][16][16]
+constexpr int WARP_FLOATS = EW + FW + 2 * BW;
+
+__device__ __forceinline__ float& dw_ref(float* base, int blk, int ri, int hl, int r, int c) {
+  return base[(((blk * 2 + ri) * 2 + hl) * 16 + r) * 16 + c];
+}
+
+// ln|<psi~_i|psi~_j>| at bond 32 by one warp (result valid in every lane).
+__device__ double chain32_half_log(const float2* __restrict__ mi, int m_i, int i, const float2* __restrict__ mj,
+                                   int m_j, int j, int n, float* wbuf, int lane) {
+  float* E = wbuf;
+  float* F = E + EW;
+  float* B = F + FW;  // column-sample block B[b][c]
+  float* C = B + BW;  // row-sample block C[a][p]
+  for (int q = lane; q < EW; q += 32) E[q] = 0.0f;
+  __syncwarp();
+  if (lane == 0) dw_ref(E, 0, 0, 0, 0, 0) = 1.0f;
+  __syncwarp();
+  int e2 = 0;
+  for (int k = 0; k < n; ++k) {
+    const float2* ai = mi + (size_t(k) * m_i + i) * (CHI32 * CHI32);
+    const float2* aj = mj + (size_t(k) * m_j + j) * (CHI32 * CHI32);
+    // lane owns outputs o = lane + 32 q (q < 8): row o / 16, column o % 16
+    Acc nr[2][8], ni[2][8];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) nr[s][q] = ni[s][q] = Acc{0.0f, 0.0f};
+    for (int t = 0; t < 2; ++t) {
+      for (int s = 0; s < 2; ++s) {
+        __syncwarp();
+        for (int q = lane; q < 256; q += 32) {
+          const int rr = q >> 4, cc = q & 15;
+          const float2 vb = site_elem(aj, CHI32, H32, s, cc, t * H32 + rr);  // B[rr][cc]
+          B[rr * 16 + cc] = vb.x;
+          B[256 + rr * 16 + cc] = vb.y;
+          const float2 vc = site_elem(ai, CHI32, H32, s, cc, t * H32 + rr);  // C[a = rr][p = cc]
+          C[rr * 16 + cc] = vc.x;
+          C[256 + rr * 16 + cc] = vc.y;
+        }
+        __syncwarp();
+        // F[a][c] = sum_b E_t[a][b] B[b][c]
+#pragma unroll 1
+        for (int q = 0; q < 8; ++q) {
+          const int o = lane + 32 * q, a = o >> 4, c = o & 15;
+          Acc xr{0.0f, 0.0f}, xi{0.0f, 0.0f};
+          for (int b = 0; b < 16; ++b) {
+            const DW er{dw_ref(E, t, 0, 0, a, b), dw_ref(E, t, 0, 1, a, b)};
+            const DW ei{dw_ref(E, t, 1, 0, a, b), dw_ref(E, t, 1, 1, a, b)};
+            const float br = B[b * 16 + c], bi = B[256 + b * 16 + c];
+            acc_add(xr, er, br);
+            acc_add(xr, ei, -bi);
+            acc_add(xi, er, bi);
+            acc_add(xi, ei, br);
+          }
+          const DW fr = acc_get(xr), fi = acc_get(xi);
+          dw_ref(F, 0, 0, 0, a, c) = fr.hi;
+          dw_ref(F, 0, 0, 1, a, c) = fr.lo;
+          dw_ref(F, 0, 1, 0, a, c) = fi.hi;
+          dw_ref(F, 0, 1, 1, a, c) = fi.lo;
+        }
+        __syncwarp();
+        // E'_s[p][c] += sum_a conj(C[a][p]) F[a][c]
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int o = lane + 32 * q, p = o >> 4, c = o & 15;
+          for (int a2 = 0; a2 < 16; ++a2) {
+            const DW fr{dw_ref(F, 0, 0, 0, a2, c), dw_ref(F, 0, 0, 1, a2, c)};
+            const DW fi{dw_ref(F, 0, 1, 0, a2, c), dw_ref(F, 0, 1, 1, a2, c)};
+            const float cr = C[a2 * 16 + p], ci = C[256 + a2 * 16 + p];
+            acc_add(nr[s][q], fr, cr);
+            acc_add(nr[s][q], fi, ci);
+            acc_add(ni[s][q], fi, cr);
+            acc_add(ni[s][q], fr, -ci);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    float mx = 0.0f;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int o = lane + 32 * q, p = o >> 4, c = o & 15;
+        const DW vr = acc_get(nr[s][q]), vi = acc_get(ni[s][q]);
+        dw_ref(E, s, 0, 0, p, c) = vr.hi;
+        dw_ref(E, s, 0, 1, p, c) = vr.lo;
+        dw_ref(E, s, 1, 0, p, c) = vi.hi;
+        dw_ref(E, s, 1, 1, p, c) = vi.lo;
+        mx = fmaxf(mx, fmaxf(fabsf(vr.hi), fabsf(vi.hi)));
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __syncwarp();
+    if (mx > 0.0f && ((k & 3) == 3 || k == n - 1)) {
+      const int e = exponent_of(mx);
+      const float sc = pow2_neg(e);
+      for (int q = lane; q < EW; q += 32) E[q] *= sc;
+      e2 += e;
+    }
+    __syncwarp();
+  }
+  const double re = (double(dw_ref(E, 0, 0, 0, 0, 0)) + double(dw_ref(E, 0, 0, 1, 0, 0))) +
+                    (double(dw_ref(E, 1, 0, 0, 0, 0)) + double(dw_ref(E, 1, 0, 1, 0, 0)));
+  const double im = (double(dw_ref(E, 0, 1, 0, 0, 0)) + double(dw_ref(E, 0, 1, 1, 0, 0))) +
+                    (double(dw_ref(E, 1, 1, 0, 0, 0)) + double(dw_ref(E, 1, 1, 1, 0, 0)));
+  __syncwarp();
+  return 0.5 * log(re * re + im * im) + double(e2) * 0.69314718055994530942;
+}
+
+__global__ void __launch_bounds__(WARPS32 * 32) refine32_kernel(const RefineArgs a) {
+  extern __shared__ __align__(16) float smf[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* wbuf = smf + warp * WARP_FLOATS;
+  const GramArgs& g = a.g;
+  const long long total = (long long)g.nrows * g.ncols;
+  const long long nwarps = (long long)gridDim.x * WARPS32;
+  for (long long base = (blockIdx.x * (long long)WARPS32 + warp) * 32; base < total; base += nwarps * 32) {
+    const long long e = base + lane;
+    bool hit = false;
+    long long at = 0;
+    int i = 0, j = 0;
+    if (e < total) {
+      const int r = int(e / g.ncols), c = int(e - (long long)r * g.ncols);
+      i = g.row0 + r;
+      j = g.col0 + c;
+      at = (long long)r * g.ld + c;
+      hit = !(g.symmetric && j <= i) && is_hit(a, at);
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, hit);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int hi_ = __shfl_sync(0xffffffffu, i, src), hj = __shfl_sync(0xffffffffu, j, src);
+      const double lij = chain32_half_log(a.mps_r, a.m_r, hi_, a.mps_c, a.m_c, hj, g.n, wbuf, lane);
+      const double lii = chain32_half_log(a.mps_r, a.m_r, hi_, a.mps_r, a.m_r, hi_, g.n, wbuf, lane);
+      const double ljj = chain32_half_log(a.mps_c, a.m_c, hj, a.mps_c, a.m_c, hj, g.n, wbuf, lane);
+      if (lane == src) write_refined(g, at, i, j, 2.0 * lij - lii - ljj);
+      __syncwarp();
+    }
+  }
+}
+
+}  // namespace rf
+}  // namespace dk
+
+using namespace dk;
+
+DK_API dk_status dk_gram_refine(dk_ctx* ctx, const void* mps_rows, int m_rows, const void* mps_cols, int m_cols, int n,
+                                int chi_max, dk_dtype dtype, int row0, int nrows, int col0, int ncols,
+                                const float* x_rows, const float* x_cols, float gamma, float w, float tau,
+                                float* k_out, float* kq_out, float* kc_out, float* logkq_out, long long ld,
+                                int symmetric, void* stream) {
+  if (!ctx || !mps_rows || !mps_cols || m_rows < 1 || m_cols < 1 || n < 1) return DK_ERR_ARG;
+  if (dtype != DK_C64) return DK_ERR_UNSUPPORTED;
+  if (chi_max != 4 && chi_max != 8 && chi_max != 32) return DK_ERR_UNSUPPORTED;
+  if (nrows < 0 || ncols < 0 || row0 < 0 || col0 < 0 || row0 + nrows > m_rows || col0 + ncols > m_cols)
+    return DK_ERR_ARG;
+  if (!kq_out && !logkq_out) return DK_ERR_ARG;
+  if (ld < ncols) return DK_ERR_ARG;
+  if (!(tau > 0.0f) || !(tau < 1.0f)) return DK_ERR_ARG;
+  if (symmetric && (row0 != col0 || nrows != ncols || mps_rows != mps_cols)) return DK_ERR_ARG;
+  const bool need_kc = k_out && w != 1.0f && !kc_out;
+  if (need_kc && (!x_rows || !x_cols)) return DK_ERR_ARG;
+  if (!aligned16(mps_rows) || !aligned16(mps_cols)) return DK_ERR_ARG;
+  if (nrows == 0 || ncols == 0) return DK_OK;
+  rf::RefineArgs a{};
+  a.g.n = n;
+  a.g.row0 = row0;
+  a.g.nrows = nrows;
+  a.g.col0 = col0;
+  a.g.ncols = ncols;
+  a.g.symmetric = symmetric ? 1 : 0;
+  a.g.x_r = x_rows;
+  a.g.x_c = x_cols;
+  a.g.gamma = gamma;
+  a.g.w = w;
+  a.g.k = k_out;
+  a.g.kq = kq_out;
+  a.g.kc = kc_out;
+  a.g.lkq = logkq_out;
+  a.g.ld = ld;
+  a.g.status = ctx->status;
+  a.g.need_kc = need_kc ? 1 : 0;
+  a.mps_r = static_cast<const float2*>(mps_rows);
+  a.mps_c = static_cast<const float2*>(mps_cols);
+  a.m_r = m_rows;
+  a.m_c = m_cols;
+  a.tau = tau;
+  a.log_tau = logf(tau);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long total = (long long)nrows * ncols;
+  if (chi_max == 32) {
+    const int smem = rf::WARPS32 * rf::WARP_FLOATS * int(sizeof(float));
+    if (cudaFuncSetAttribute(rf::refine32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return DK_ERR_CUDA;
+    long long grid = (total + rf::WARPS32 * 32 * 32 - 1) / (rf::WARPS32 * 32 * 32);
+    const long long cap = 8LL * ctx->sm_count;
+    if (grid > cap) grid = cap;
+    rf::refine32_kernel<<<int(grid), rf::WARPS32 * 32, smem, st>>>(a);
+    return launch_status();
+  }
+  long long grid = (total + 128 * 8 - 1) / (128 * 8);
+  const long long cap = 16LL * ctx->sm_count;
+  if (grid > cap) grid = cap;
+  if (chi_max == 4) rf::refine_small_kernel<2><<<int(grid), 128, 0, st>>>(a);
+  else rf::refine_small_kernel<4><<<int(grid), 128, 0, st>>>(a);
+  return launch_status();
+}

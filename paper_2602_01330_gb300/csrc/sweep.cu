@@ -1,6 +1,7 @@
 // Feature-dimension sweep (§II-D: the kernel matrices for every qubit count n of a study)
-// as one native call: every item's symmetric Gram through dk_gram_tile, in order, on the
-// caller's stream, optionally recorded once into a CUDA graph that the context keeps and
+// as one native call: every item's symmetric Gram through dk_gram_tile and, for complex64
+// FP32 / split-BF16 items, its refinement pass (dk_gram_refine, tau = DK_REFINE_TAU), in
+// order, on the caller's stream, optionally recorded once into a CUDA graph that the context keeps and
 // replays, so a sweep of many Gram launches of uneven size costs one graph launch.
 //
 // Graph cache: keyed by the exact bytes of the item list and the call's parameters (the
@@ -52,6 +53,11 @@ dk_status run_items(dk_ctx* ctx, const dk_sweep_item* items, int n_items, int ch
     s = dk_gram_tile(ctx, it.mps, it.m, it.mps, it.m, it.n, chi_max, dtype, 0, it.m, 0, it.m, it.log_norm,
                      it.log_norm, it.x, it.x, 1.0f / float(it.n), w, prec, it.k, it.kq, it.kc, it.logkq, it.ld, 1,
                      st);
+    const bool refinable = dtype == DK_C64 && (chi_max == 4 || chi_max == 8 || chi_max == 32) &&
+                           (prec == DK_PREC_F32 || prec == DK_PREC_BF16X3) && (it.kq || it.logkq);
+    if (s == DK_OK && refinable)
+      s = dk_gram_refine(ctx, it.mps, it.m, it.mps, it.m, it.n, chi_max, dtype, 0, it.m, 0, it.m, it.x, it.x,
+                         1.0f / float(it.n), w, DK_REFINE_TAU, it.k, it.kq, it.kc, it.logkq, it.ld, 1, st);
   }
   ctx->gram_config = saved;
   return s;

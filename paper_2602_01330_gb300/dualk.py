@@ -30,7 +30,8 @@ EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_
             "dk_svm_ovo_train", "dk_svm_ovo_predict", "dk_gram_stats", "dk_pca_workspace_bytes", "dk_pca_fit",
             "dk_pca_transform", "dk_pca_fit_noalloc", "dk_mps_build_blocks", "dk_block_states_bytes",
             "dk_block_states", "dk_gram_blocks", "dk_gram_sweep", "dk_workspace_bytes",
-            "dk_set_block_gram_form", "dk_block_states_workspace_bytes", "dk_gram_blocks_workspace_bytes")
+            "dk_set_block_gram_form", "dk_block_states_workspace_bytes", "dk_gram_blocks_workspace_bytes",
+            "dk_gram_refine")
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 PCA_MAX_FEATURES = 4096  # DK_PCA_MAX_FEATURES
 PCA_NOALLOC_MAX_FEATURES = 256  # DK_PCA_NOALLOC_MAX_FEATURES
@@ -96,6 +97,9 @@ def _lib():
     lib.dk_dual_kernel_rows.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, i32, i32, i32, i32,
                                         f32, f32, i32, vp, vp, vp, vp, vp]
     lib.dk_dual_kernel_rows.restype = i32
+    lib.dk_gram_refine.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, f32, f32, f32,
+                                   vp, vp, vp, vp, i64, i32, vp]
+    lib.dk_gram_refine.restype = i32
     lib.dk_gram_config_count.argtypes = [i32, i32]
     lib.dk_gram_config_count.restype = i32
     ip = ctypes.POINTER(ctypes.c_int)
@@ -391,6 +395,26 @@ def _default_prec(mps):
     return DK_PREC_F32 if mps.dtype == DK_C64 else DK_PREC_F64
 
 
+# Entries with K_q above this are recomputed in double-word FP32 by dk_gram_refine after
+# every FP32 / split-BF16 Gram and rows call of the binding (refine=None switches it off).
+REFINE_TAU = 0.02
+
+
+def _refinable(mps, prec):
+    return mps.dtype == DK_C64 and mps.chi_max in (4, 8, 32) and prec in (DK_PREC_F32, DK_PREC_BF16X3)
+
+
+def gram_refine(ctx: "Context", rows: "MPS", cols: "MPS", row0: int, nrows: int, col0: int, ncols: int, out: dict,
+                ld: int, gamma: float, w: float, tau: float = REFINE_TAU, symmetric: bool = False, stream=None):
+    """dk_gram_refine: recompute the entries of a written block with K_q > tau in double-word
+    FP32 (see include/dualk.h)."""
+    _check(_lib().dk_gram_refine(ctx.handle, _ptr(rows.data), rows.m, _ptr(cols.data), cols.m, rows.n,
+                                 rows.chi_max, rows.dtype, row0, nrows, col0, ncols, _ptr(rows.x), _ptr(cols.x),
+                                 float(gamma), float(w), float(tau), _ptr(out.get("k")), _ptr(out.get("kq")),
+                                 _ptr(out.get("kc")), _ptr(out.get("logkq")), int(ld), 1 if symmetric else 0,
+                                 _stream(stream)), "dk_gram_refine")
+
+
 def _outs(shape, device, want):
     return {k: (torch.empty(shape, dtype=torch.float32, device=device) if k in want else None)
             for k in ("k", "kq", "kc", "logkq")}
@@ -399,8 +423,9 @@ def _outs(shape, device, want):
 def gram_tile(ctx: Context, rows: MPS, cols: MPS, row0: int = 0, nrows: int | None = None,
               col0: int = 0, ncols: int | None = None, gamma: float | None = None, w: float = 0.5,
               want=("k", "kq", "kc", "logkq"), symmetric: bool = False, out=None, ld: int | None = None,
-              stream=None, prec: int | None = None):
-    """dk_gram_tile: the (nrows x ncols) block of K, K_q, K_c, log K_q (dict of tensors)."""
+              stream=None, prec: int | None = None, refine: float | None = REFINE_TAU):
+    """dk_gram_tile: the (nrows x ncols) block of K, K_q, K_c, log K_q (dict of tensors),
+    then dk_gram_refine with tau = refine for FP32 / split-BF16 blocks (None: no refinement)."""
     nrows = rows.m - row0 if nrows is None else nrows
     ncols = cols.m - col0 if ncols is None else ncols
     if rows.n != cols.n or rows.chi_max != cols.chi_max or rows.dtype != cols.dtype:
@@ -420,18 +445,23 @@ def gram_tile(ctx: Context, rows: MPS, cols: MPS, row0: int = 0, nrows: int | No
                                _ptr(out.get("k")), _ptr(out.get("kq")), _ptr(out.get("kc")),
                                _ptr(out.get("logkq")), int(ld), 1 if symmetric else 0, _stream(stream)),
            "dk_gram_tile")
+    if refine is not None and _refinable(rows, prec) and (out.get("kq") is not None or out.get("logkq") is not None):
+        gram_refine(ctx, rows, cols, row0, nrows, col0, ncols, out, ld, gamma, w, refine, symmetric, stream)
     return out
 
 
 def gram(ctx: Context, mps: MPS, gamma: float | None = None, w: float = 0.5,
-         want=("k", "kq", "kc", "logkq"), stream=None, prec: int | None = None):
+         want=("k", "kq", "kc", "logkq"), stream=None, prec: int | None = None, refine: float | None = REFINE_TAU):
     """Full symmetric m x m Gram of one MPS batch (each unordered pair contracted once)."""
-    return gram_tile(ctx, mps, mps, gamma=gamma, w=w, want=want, symmetric=True, stream=stream, prec=prec)
+    return gram_tile(ctx, mps, mps, gamma=gamma, w=w, want=want, symmetric=True, stream=stream, prec=prec,
+                     refine=refine)
 
 
 def dual_kernel_rows(ctx: Context, test: MPS, train: MPS, gamma: float | None = None, w: float = 0.5,
-                     want=("k", "kq", "kc", "logkq"), out=None, stream=None, prec: int | None = None):
-    """dk_dual_kernel_rows: the b x m block K(test, train)."""
+                     want=("k", "kq", "kc", "logkq"), out=None, stream=None, prec: int | None = None,
+                     refine: float | None = REFINE_TAU):
+    """dk_dual_kernel_rows: the b x m block K(test, train), then dk_gram_refine (tau = refine)
+    for FP32 / split-BF16 blocks."""
     if test.n != train.n or test.chi_max != train.chi_max or test.dtype != train.dtype:
         raise ValueError("test and train MPS differ in n, chi_max or dtype")
     gamma = 1.0 / train.n if gamma is None else gamma
@@ -446,6 +476,8 @@ def dual_kernel_rows(ctx: Context, test: MPS, train: MPS, gamma: float | None = 
                                       _ptr(out.get("k")), _ptr(out.get("kq")), _ptr(out.get("kc")),
                                       _ptr(out.get("logkq")), _stream(stream)),
            "dk_dual_kernel_rows")
+    if refine is not None and _refinable(train, prec) and (out.get("kq") is not None or out.get("logkq") is not None):
+        gram_refine(ctx, test, train, 0, test.m, 0, train.m, out, train.m, gamma, w, refine, False, stream)
     return out
 
 

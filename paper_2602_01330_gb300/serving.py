@@ -6,12 +6,16 @@ set per qubit count resident on the device (its MPS, features and norms) and ans
 requests — batches of test samples of one qubit count — with their b x m row block.
 
 Continuous batching: requests arrive over time; each is admitted into a free slot as
-soon as one is free and the device has room for its buffers (free HBM from
-``torch.cuda.mem_get_info`` minus a reserve), runs on its slot's own stream (test MPS
-build, then dual-kernel rows, then the copy of K to pinned host memory), and overlaps on
-the device with every other admitted request. A request that could never fit is
-rejected. Results do not depend on what else runs: every pair is contracted by the same
-arithmetic in the same order whatever tile or launch it lands in.
+soon as one is free and the device has room for its buffers (free HBM: the driver's free
+bytes plus what torch's caching allocator holds unused, minus a reserve), runs on its
+slot's own stream (test MPS build, then dual-kernel rows and their refinement pass, then
+the copy of K to pinned host memory), and overlaps on the device with every other admitted
+request. Waiting requests of the same qubit count are merged into one launch of up to
+``merge_rows`` test rows (first come first served; a request is never split), so that
+small requests share one pair tile instead of each leaving most of a tile idle. A request
+that could never fit is rejected. Results do not depend on what else runs: every pair is
+contracted by the same arithmetic in the same order whatever tile, launch or merged batch
+it lands in.
 
 All device work runs in libdualk's kernels; this module only schedules it.
 """
@@ -42,10 +46,14 @@ class Request:
 @dataclass
 class _Slot:
     stream: torch.cuda.Stream
-    req: Request | None = None
+    reqs: list = field(default_factory=list)   # requests of the launch in flight (one n)
     event: torch.cuda.Event | None = None
     host_out: torch.Tensor | None = None
     keep: list = field(default_factory=list)
+
+    @property
+    def busy(self) -> bool:
+        return bool(self.reqs)
 
 
 class TrainingSet:
@@ -64,7 +72,7 @@ class KernelServer:
     """Serves K(test, train) row blocks with continuous batching over ``slots`` streams."""
 
     def __init__(self, ctx: dualk.Context, train: dict, fmap: dualk.FeatureMap, w: float = 0.5,
-                 slots: int = 8, reserve_bytes: int = 2 << 30, device=None):
+                 slots: int = 8, reserve_bytes: int = 2 << 30, device=None, merge_rows: int = 256):
         self.ctx = ctx
         self.fmap = fmap
         self.w = w
@@ -73,36 +81,70 @@ class KernelServer:
         torch.cuda.synchronize()
         self.slots = [_Slot(torch.cuda.Stream(device=self.device)) for _ in range(slots)]
         self.reserve = reserve_bytes
+        self.merge_rows = merge_rows
         self.admitted = 0
         self.rejected = 0
+        self.launches = 0
+        self.max_in_flight = 0        # most requests on the device at once
+        self.max_launches_in_flight = 0
 
     def request_bytes(self, b: int, n: int) -> int:
         m = self.train[n].m
         return dualk.mps_bytes(b, n, self.fmap.chi_max) + b * n * 4 + 2 * b * 4 + b * m * 4 + 4096
 
     def _mem(self):
-        """(free, total) device bytes."""
-        return torch.cuda.mem_get_info(self.device)
+        """(free, total) device bytes; free counts memory that torch's caching allocator has
+        reserved but not handed out, which it reuses before asking the driver for more."""
+        free, total = torch.cuda.mem_get_info(self.device)
+        cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+        return free + max(cached, 0), total
 
-    def _fits(self, req: Request) -> bool:
-        return self.request_bytes(req.x.shape[0], req.n) + self.reserve <= self._mem()[0]
+    def _fits(self, reqs) -> bool:
+        b = sum(r.x.shape[0] for r in reqs)
+        return self.request_bytes(b, reqs[0].n) + self.reserve <= self._mem()[0]
 
-    def _launch(self, slot: _Slot, req: Request):
-        ts = self.train[req.n]
-        b = req.x.shape[0]
+    def _launch(self, slot: _Slot, reqs: list):
+        ts = self.train[reqs[0].n]
+        xs = np.concatenate([np.ascontiguousarray(r.x, dtype=np.float32) for r in reqs])
+        b, n = xs.shape
         with torch.cuda.stream(slot.stream):
-            hx = torch.from_numpy(np.ascontiguousarray(req.x, dtype=np.float32)).pin_memory()
-            x = torch.empty((b, req.n), dtype=torch.float32, device=self.device)
+            hx = torch.from_numpy(xs).pin_memory()
+            x = torch.empty((b, n), dtype=torch.float32, device=self.device)
             x.copy_(hx, non_blocking=True)
             test = dualk.mps_build(self.ctx, x, self.fmap, stream=slot.stream)
-            out = {"k": torch.empty((b, ts.m), dtype=torch.float32, device=self.device)}
-            dualk.dual_kernel_rows(self.ctx, test, ts.mps, w=self.w, want=("k",), out=out, stream=slot.stream)
+            out = {"k": torch.empty((b, ts.m), dtype=torch.float32, device=self.device),
+                   "kq": torch.empty((b, ts.m), dtype=torch.float32, device=self.device)}
+            dualk.dual_kernel_rows(self.ctx, test, ts.mps, w=self.w, want=("k", "kq"), out=out, stream=slot.stream)
             host = torch.empty((b, ts.m), dtype=torch.float32).pin_memory()
             host.copy_(out["k"], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(slot.stream)
-        slot.req, slot.event, slot.host_out = req, ev, host
+        slot.reqs, slot.event, slot.host_out = list(reqs), ev, host
         slot.keep = [hx, x, test, out]  # alive until the stream has passed them
+        self.launches += 1
+
+    def _take_batch(self, waiting: deque) -> list:
+        """The first waiting request and, after it, waiting requests of the same qubit count
+        while the merged batch stays within merge_rows rows (queue order otherwise kept)."""
+        first = waiting[0]
+        batch, rows = [first], first.x.shape[0]
+        for r in list(waiting)[1:]:
+            if r.n == first.n and rows + r.x.shape[0] <= self.merge_rows:
+                batch.append(r)
+                rows += r.x.shape[0]
+        return batch
+
+    def _retire(self, slot: _Slot, now: float):
+        out = slot.host_out.numpy()
+        row = 0
+        for r in slot.reqs:
+            b = r.x.shape[0]
+            r.result = out[row:row + b]
+            r.done = now
+            row += b
+        n = len(slot.reqs)
+        slot.reqs, slot.event, slot.host_out, slot.keep = [], None, None, []
+        return n
 
     def run(self, requests: list[Request], clock=time.perf_counter, poll_sleep: float = 0.0):
         """Serve every request; arrivals are honoured relative to the start of the call."""
@@ -115,18 +157,15 @@ class KernelServer:
             now = clock() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
-            # retire finished requests
+            # retire finished launches
             for slot in self.slots:
-                if slot.req is not None and slot.event.query():
-                    slot.req.result = slot.host_out.numpy()
-                    slot.req.done = clock() - t0
-                    slot.req, slot.event, slot.host_out, slot.keep = None, None, None, []
-                    done += 1
+                if slot.busy and slot.event.query():
+                    done += self._retire(slot, clock() - t0)
             # admit into free slots while memory allows
             for slot in self.slots:
                 if not waiting:
                     break
-                if slot.req is not None:
+                if slot.busy:
                     continue
                 req = waiting[0]
                 if self.request_bytes(req.x.shape[0], req.n) + self.reserve > self._mem()[1]:
@@ -135,12 +174,19 @@ class KernelServer:
                     self.rejected += 1
                     done += 1
                     continue
-                if not self._fits(req):
+                batch = self._take_batch(waiting)
+                while len(batch) > 1 and not self._fits(batch):
+                    batch.pop()
+                if not self._fits(batch):
                     break
-                waiting.popleft()
-                req.admitted = clock() - t0
-                self.admitted += 1
-                self._launch(slot, req)
+                for r in batch:
+                    waiting.remove(r)
+                    r.admitted = clock() - t0
+                self.admitted += len(batch)
+                self._launch(slot, batch)
+            busy = [s_ for s_ in self.slots if s_.busy]
+            self.max_in_flight = max(self.max_in_flight, sum(len(s_.reqs) for s_ in busy))
+            self.max_launches_in_flight = max(self.max_launches_in_flight, len(busy))
             if poll_sleep:
                 time.sleep(poll_sleep)
         self.ctx.sync_status()
@@ -150,11 +196,12 @@ class KernelServer:
         """The same request with nothing else on the device (for the determinism check)."""
         torch.cuda.synchronize()
         slot = self.slots[0]
-        assert slot.req is None
-        self._launch(slot, req)
+        assert not slot.busy
+        self._launch(slot, [req])
         slot.event.synchronize()
         out = slot.host_out.numpy().copy()
-        slot.req, slot.event, slot.host_out, slot.keep = None, None, None, []
+        slot.reqs, slot.event, slot.host_out, slot.keep = [], None, None, []
+        self.launches -= 1
         return out
 
 
@@ -187,11 +234,12 @@ def poisson_requests(rng: np.random.Generator, count: int, rate_per_s: float, di
     return reqs
 
 
-def run_benchmark(ctx: dualk.Context, m: int = 8000, requests: int = 300, rho: float = 0.8, slots: int = 8,
+def run_benchmark(ctx: dualk.Context, m: int = 8000, requests: int = 300, rho=(0.8,), slots: int = 8,
                   seed: int = 4, dims=(16, 128, 784), b_max: int = 256) -> dict:
     """Resident training sets of m samples per qubit count, a saturating burst to measure the
-    peak rows/s, then Poisson arrivals at rho times that rate; p50/p99 latency, rows/s,
-    admissions, and whether a few results are bit-identical when run alone."""
+    peak rows/s, then for each offered load rho a Poisson stream at rho times that rate;
+    per load p50/p99 latency, rows/s, admissions, launches, the most requests and launches
+    on the device at once, and whether a few results are bit-identical when run alone."""
     from . import synthetic
 
     fm = dualk.FeatureMap(reps=2, chi_max=4)
@@ -199,18 +247,26 @@ def run_benchmark(ctx: dualk.Context, m: int = 8000, requests: int = 300, rho: f
     test_pool = {n: synthetic.fmnist_like(16, 512, n)["x_test"] for n in dims}
     srv = KernelServer(ctx, train, fm, slots=slots)
     rng = np.random.Generator(np.random.PCG64(seed))
-    burst = poisson_requests(rng, 32, 1e9, dims, test_pool, b_max)
+    burst = poisson_requests(rng, 64, 1e9, dims, test_pool, b_max)
+    srv.run(burst[:8])  # warm-up: first launches of every kernel
     t0 = time.perf_counter()
-    srv.run(burst)
-    sat_rows = sum(r.x.shape[0] for r in burst) / (time.perf_counter() - t0)
-    rate = rho * sat_rows / ((1 + b_max) / 2)
-    reqs = poisson_requests(rng, requests, rate, dims, test_pool, b_max)
-    srv.run(reqs)
-    stats = latency_stats(reqs)
-    same = all(np.array_equal(srv.solve_alone(r), r.result) for r in reqs[:5] if r.result is not None)
-    return {"workload": f"serving m={m} n={tuple(dims)} slots={slots} rho={rho} requests={requests}",
-            "saturated_rows_per_s": sat_rows, "offered_requests_per_s": rate, **stats,
-            "admitted": srv.admitted, "same_alone_and_in_mix": same}
+    srv.run(burst[8:])
+    sat_rows = sum(r.x.shape[0] for r in burst[8:]) / (time.perf_counter() - t0)
+    res = {"workload": f"serving m={m} n={tuple(dims)} slots={slots} requests={requests} per load, "
+                       f"batch U{{1..{b_max}}}, Poisson arrivals",
+           "saturated_rows_per_s": sat_rows, "loads": {}}
+    for r_ in (rho if isinstance(rho, (tuple, list)) else (rho,)):
+        rate = r_ * sat_rows / ((1 + b_max) / 2)
+        reqs = poisson_requests(rng, requests, rate, dims, test_pool, b_max)
+        srv.admitted = srv.rejected = srv.launches = srv.max_in_flight = srv.max_launches_in_flight = 0
+        srv.run(reqs)
+        stats = latency_stats(reqs)
+        same = all(np.array_equal(srv.solve_alone(r), r.result) for r in reqs[:5] if r.result is not None)
+        res["loads"][f"rho={r_}"] = {"offered_requests_per_s": rate, **stats, "admitted": srv.admitted,
+                                     "launches": srv.launches, "max_requests_in_flight": srv.max_in_flight,
+                                     "max_launches_in_flight": srv.max_launches_in_flight,
+                                     "same_alone_and_in_mix": same}
+    return res
 
 
 def main():
@@ -226,7 +282,7 @@ def main():
     ap.add_argument("--seed", type=int, default=4)
     args = ap.parse_args()
     ctx = dualk.Context(0)
-    print(json.dumps(run_benchmark(ctx, args.m, args.requests, args.rho, args.slots, args.seed)))
+    print(json.dumps(run_benchmark(ctx, args.m, args.requests, (args.rho,), args.slots, args.seed)))
     ctx.close()
 
 

@@ -242,11 +242,11 @@ def test_gram_blocks_errors(dk):
     # symmetric with different row and column ranges
     assert lib.dk_gram_blocks(ctx.handle, dualk._ptr(st.data), 8, dualk._ptr(st.data), 8, 30, 6, 0, 4, 2, 4,
                               dualk._ptr(st.log_norm), dualk._ptr(st.log_norm), dualk._ptr(x), dualk._ptr(x),
-                              0.1, 1.0, 0, None, dualk._ptr(out), None, None, 8, 1, dualk._stream(None)) == 1
+                              0.1, 1.0, 0, None, dualk._ptr(out), None, None, 8, 1, None, 0, dualk._stream(None)) == 1
     # ld below ncols
     assert lib.dk_gram_blocks(ctx.handle, dualk._ptr(st.data), 8, dualk._ptr(st.data), 8, 30, 6, 0, 8, 0, 8,
                               dualk._ptr(st.log_norm), dualk._ptr(st.log_norm), dualk._ptr(x), dualk._ptr(x),
-                              0.1, 1.0, 0, None, dualk._ptr(out), None, None, 4, 0, dualk._stream(None)) == 1
+                              0.1, 1.0, 0, None, dualk._ptr(out), None, None, 4, 0, None, 0, dualk._stream(None)) == 1
     ctx.sync_status()
 
 
@@ -282,7 +282,7 @@ def _edge_cases(dualk, ctx, torch, prec):
     assert dualk._lib().dk_gram_blocks(ctx.handle, dualk._ptr(st.data), 1, dualk._ptr(st.data), 1, 7, 3, 0, 0, 0, 1,
                                        dualk._ptr(st.log_norm), dualk._ptr(st.log_norm), dualk._ptr(x1),
                                        dualk._ptr(x1), 0.1, 1.0, p, None, dualk._ptr(out), None, None, 1, 0,
-                                       dualk._stream(None)) == 0
+                                       None, 0, dualk._stream(None)) == 0
     torch.cuda.synchronize()
     assert out.item() == -3.0  # nothing to compute, nothing written
     ctx.sync_status()
@@ -319,10 +319,11 @@ def test_block_gram_forms_agree_and_persist(dk):
             st = dualk.block_states(ctx, _dev(torch, xt), fm, dualk.DK_ENT_FULL, prec=p)
             g = dualk.gram_blocks(ctx, sa, w=1.0, want=("logkq",))
             rect = torch.empty(2000, 1900, device="cuda")
+            ws, nws = _ws(dualk, ctx, n, b, 2000, 1900, p, 0, 0)
             _check_call(dualk, dualk._lib().dk_gram_blocks(
                 ctx.handle, dualk._ptr(sa.data), 4000, dualk._ptr(sa.data), 4000, n, b, 100, 2000, 2100, 1900,
                 dualk._ptr(sa.log_norm), dualk._ptr(sa.log_norm), None, None, 0.0, 1.0, p, None, None, None,
-                dualk._ptr(rect), 1900, 0, dualk._stream(None)))
+                dualk._ptr(rect), 1900, 0, dualk._ptr(ws), nws, dualk._stream(None)))
             r = dualk.gram_blocks(ctx, st, sa, w=1.0, want=("logkq",))
             torch.cuda.synchronize()
             res[form] = (g["logkq"].cpu().numpy().astype(np.float64), rect.cpu().numpy().astype(np.float64),
@@ -392,10 +393,11 @@ def test_block_gram_symmetric_offset_diagonal(dk, form):
         s = dualk.block_states(ctx, x, fm, dualk.DK_ENT_FULL, prec=dualk.DK_PREC_BF16X3)
         full = dualk.gram_blocks(ctx, s, w=1.0, want=("logkq",))["logkq"]
         sub = torch.full((300, 300), -7.0, device="cuda")
+        ws, nws = _ws(dualk, ctx, 40, 10, 300, 300, dualk.DK_PREC_BF16X3, 1, 0)
         _check_call(dualk, dualk._lib().dk_gram_blocks(
             ctx.handle, dualk._ptr(s.data), 600, dualk._ptr(s.data), 600, 40, 10, 50, 300, 50, 300,
             dualk._ptr(s.log_norm), dualk._ptr(s.log_norm), None, None, 0.0, 1.0, dualk.DK_PREC_BF16X3, None,
-            None, None, dualk._ptr(sub), 300, 1, dualk._stream(None)))
+            None, None, dualk._ptr(sub), 300, 1, dualk._ptr(ws), nws, dualk._stream(None)))
         torch.cuda.synchronize()
     sub, full = sub.cpu().numpy().astype(np.float64), full.cpu().numpy().astype(np.float64)
     assert np.all(np.diag(sub) == 0.0)
@@ -406,6 +408,14 @@ def test_block_gram_symmetric_offset_diagonal(dk, form):
 
 def _check_call(dualk, status):
     assert status == 0, status
+
+
+def _ws(dualk, ctx, n, b, nrows, ncols, prec, symmetric, with_kc):
+    """Caller workspace of a direct dk_gram_blocks call: (tensor or None, bytes)."""
+    import torch
+    nbytes = int(dualk._lib().dk_gram_blocks_workspace_bytes(ctx.handle, n, b, nrows, ncols, prec, symmetric,
+                                                             with_kc))
+    return (torch.empty(nbytes, dtype=torch.uint8, device="cuda") if nbytes else None), nbytes
 
 
 def test_svm_workflow_on_a_block_map(dk):

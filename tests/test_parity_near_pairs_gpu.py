@@ -9,7 +9,13 @@ element by element (§II-C Eqs. 7-10; §II-B Eq. 3; §II-D Eq. 11):
 * the FP32 path (complex64 MPS, bond 4) at n = 784 in the benchmarked launch: the symmetric
   2000 x 2000 Gram and the 500 x 2000 rows, with tile shapes chosen by the autotuner as the
   benchmark does, |dK| <= 1e-6;
-* the split-BF16 tensor-core path at bond 32 (reps = 5) at n = 256, |dK| <= 1e-4;
+* the split-BF16 tensor-core path at bond 32 (reps = 5) at n = 256, |dK| <= 1e-4, and the
+  FP32 bond-32 path on the same pairs, |dK| <= 1e-6;
+
+each followed, as every binding call is by default, by the refinement pass
+(dk_gram_refine, tau = 0.02) that recomputes the entries with K_q > tau in double-word FP32:
+plain FP32 rounding over 784 sites leaves about 7e-6 on K_q of order one, split-BF16 about
+1e-3, which the first test also prints;
 * the d = 64 workload at its full size (1000 train, 200 test, reps = 2) at every mix weight.
 
 Each test prints one JSON line with the measured largest |dK| and the largest relative
@@ -107,6 +113,7 @@ def test_fp32_n784_near_duplicates_bench_launch(dk):
     try:
         ctx.set_gram_config(cfg_gram)
         g = dualk.gram(ctx, mtr, w=0.5)
+        g0 = dualk.gram(ctx, mtr, w=0.5, refine=None)
         ctx.set_gram_config(cfg_rows)
         r = dualk.dual_kernel_rows(ctx, mte, mtr, w=0.5)
         torch.cuda.synchronize()
@@ -118,6 +125,17 @@ def test_fp32_n784_near_duplicates_bench_launch(dk):
     ref = oracle_pool.aligned_pairs(xtr[base], xtr[near], 2)
     rep = _pairs_check("fp32 n784 gram near pairs", g, ref, xtr[base], xtr[near], base, near, 0.5, gamma, TOL_K)
     assert rep["pairs_kq_gt_1e-3"] >= 150
+    # the refinement pass changes exactly the entries whose FP32 K_q exceeds tau (off the
+    # diagonal); the plain FP32 values of the near pairs, for the record
+    kq0 = g0["kq"].cpu().numpy()
+    kq1 = g["kq"].cpu().numpy()
+    keep = ~(kq0 > dualk.REFINE_TAU) | np.eye(2000, dtype=bool)
+    for key in ("k", "kq", "kc", "logkq"):
+        assert np.array_equal(g0[key].cpu().numpy()[keep], g[key].cpu().numpy()[keep]), key
+    assert np.array_equal(g0["kc"].cpu().numpy(), g["kc"].cpu().numpy())
+    print(json.dumps({"case": "fp32 n784 gram near pairs without refinement",
+                      "max_abs_dkq": float(np.max(np.abs(kq0[base, near] - ref[0]))),
+                      "entries_refined": int((~keep).sum()), "max_change": float(np.max(np.abs(kq1 - kq0)))}))
     # the mirrored entries of the symmetric Gram hold the same bits
     kq = g["kq"].cpu().numpy()
     assert np.array_equal(kq[base, near], kq[near, base])

@@ -27,12 +27,17 @@ class _Event:
 
 
 class FakeServer(KernelServer):
-    def __init__(self, clock, free_bytes, total_bytes, slots, service_s):
+    def __init__(self, clock, free_bytes, total_bytes, slots, service_s, merge_rows=1):
         self.clock = clock
         self.slots = [_Slot(stream=None) for _ in range(slots)]
         self.reserve = 0
+        self.merge_rows = merge_rows
         self.admitted = 0
         self.rejected = 0
+        self.launches = 0
+        self.max_in_flight = 0
+        self.max_launches_in_flight = 0
+        self.batches = []
         self.train = {8: SimpleNamespace(m=10), 32: SimpleNamespace(m=10)}
         self.free_bytes, self.total_bytes = free_bytes, total_bytes
         self.service_s = service_s
@@ -44,15 +49,17 @@ class FakeServer(KernelServer):
         return 100 * b
 
     def _mem(self):
-        used = sum(self.request_bytes(s.req.x.shape[0], s.req.n) for s in self.slots if s.req is not None)
+        used = sum(self.request_bytes(r.x.shape[0], r.n) for s in self.slots for r in s.reqs)
         return self.free_bytes - used, self.total_bytes
 
-    def _launch(self, slot, req):
-        slot.req = req
+    def _launch(self, slot, reqs):
+        slot.reqs = list(reqs)
         slot.event = _Event(self.clock, self.clock.t + self.service_s)
-        slot.host_out = torch.full((req.x.shape[0], 10), float(req.rid))
-        self.order.append(req.rid)
-        self.max_inflight = max(self.max_inflight, sum(s.req is not None for s in self.slots))
+        slot.host_out = torch.cat([torch.full((r.x.shape[0], 10), float(r.rid)) for r in reqs])
+        self.order.extend(r.rid for r in reqs)
+        self.batches.append([r.rid for r in reqs])
+        self.launches += 1
+        self.max_inflight = max(self.max_inflight, sum(len(s.reqs) for s in self.slots))
 
 
 def _req(rid, b, n=8, t=0.0):
@@ -99,3 +106,37 @@ def test_poisson_requests_shape():
     assert np.all(np.diff(arr) > 0)
     assert 1.0 < arr[-1] < 3.5  # 200 arrivals at 100/s
     assert all(1 <= r.x.shape[0] <= 256 and r.x.shape[1] == r.n for r in reqs)
+
+
+def test_waiting_requests_of_one_qubit_count_merge_into_one_launch():
+    clk = _Clock()
+    srv = FakeServer(clk, free_bytes=1 << 30, total_bytes=1 << 30, slots=1, service_s=0.05, merge_rows=25)
+    # r0 occupies the only slot; r1..r5 wait together and are merged by qubit count up to 25 rows
+    reqs = [_req(0, 5), _req(1, 10, t=0.01), _req(2, 10, n=32, t=0.01), _req(3, 10, t=0.01),
+            _req(4, 10, t=0.01), _req(5, 5, n=32, t=0.01)]
+    srv.run(reqs, clock=clk)
+    assert srv.batches[0] == [0]
+    assert srv.batches[1] == [1, 3]          # n = 8, 20 rows; r4 would make 30
+    assert srv.batches[2] == [2, 5]          # n = 32, queue order
+    assert srv.batches[3] == [4]
+    assert srv.launches == 4 and srv.admitted == 6
+    assert all(np.all(r.result == r.rid) and r.result.shape[0] == r.x.shape[0] for r in reqs)
+
+
+def test_merged_batch_shrinks_to_fit_memory():
+    clk = _Clock()
+    srv = FakeServer(clk, free_bytes=2500, total_bytes=10_000, slots=2, service_s=0.01, merge_rows=256)
+    reqs = [_req(i, 10) for i in range(5)]   # 1000 bytes each: at most two per batch
+    srv.run(reqs, clock=clk)
+    assert max(len(b) for b in srv.batches) == 2
+    assert srv.order == list(range(5))
+    assert all(r.done is not None and not r.rejected for r in reqs)
+
+
+def test_admission_counts_memory_cached_by_the_allocator(monkeypatch):
+    srv = KernelServer.__new__(KernelServer)
+    srv.device = torch.device("cpu")
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda dev: (1000, 5000))
+    monkeypatch.setattr(torch.cuda, "memory_reserved", lambda dev: 800)
+    monkeypatch.setattr(torch.cuda, "memory_allocated", lambda dev: 300)
+    assert srv._mem() == (1500, 5000)

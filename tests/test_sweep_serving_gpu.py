@@ -81,6 +81,14 @@ def test_serving_same_alone_and_in_mix(env):
     assert st["served"] == 24 and st["rejected"] == 0
     for r in reqs[:6]:
         assert np.array_equal(srv.solve_alone(r), r.result)
+    # a burst: every request waits at once, so launches of all three qubit counts (each a
+    # merged batch) are on the device together, on their own streams
+    burst = poisson_requests(rng, 24, 1e9, dims, pool, b_max=20)
+    srv.max_launches_in_flight = srv.max_in_flight = 0
+    srv.run(burst)
+    assert srv.max_launches_in_flight >= 2 and srv.max_in_flight >= 3
+    for r in burst[:6]:
+        assert np.array_equal(srv.solve_alone(r), r.result)
     for r in reqs[:3]:
         xt = train[r.n].astype(np.float64)
         xs = r.x.astype(np.float64)
