@@ -20,9 +20,10 @@
 // (1 - w) K_c and log K_q are written back (K_c is read from the block, or recomputed with
 // the Gram kernels' compensated feature sum). Entries with K_q <= tau keep their values.
 //
-// Bond 4 and 8: one thread per pair, E in registers. Bond 32: one warp per pair, E, the
-// intermediate F and the two samples' site blocks in shared memory; each warp tests 32
-// entries at once and works through the hits among them.
+// Bond 4 and 8: one thread per pair, E in registers, hits queued per warp so that the
+// chains run 32 at a time. Bond 32: one warp per pair, E, the intermediate F and the two
+// samples' site blocks in shared memory; each warp tests 32 entries at once and works
+// through the hits among them.
 #include <math.h>
 
 #include "common.cuh"
@@ -221,22 +222,72 @@ __device__ __forceinline__ void write_refined(const GramArgs& g, long long at, i
   }
 }
 
+// Each warp tests 32 entries at a time and queues the hits in shared memory; whenever 32
+// are queued every lane takes one, so the chains run with full warps even when the hits
+// are sparse (a lone hit per warp would otherwise cost the warp its whole chain time).
+constexpr int SMALL_WARPS = 4;
+
 template <int H>
-__global__ void __launch_bounds__(128) refine_small_kernel(const RefineArgs a) {
+__device__ __forceinline__ void refine_one(const RefineArgs& a, int i, int j, long long at) {
+  const double lij = chain_half_log<H>(a.mps_r, a.m_r, i, a.mps_c, a.m_c, j, a.g.n);
+  const double lii = chain_half_log<H>(a.mps_r, a.m_r, i, a.mps_r, a.m_r, i, a.g.n);
+  const double ljj = chain_half_log<H>(a.mps_c, a.m_c, j, a.mps_c, a.m_c, j, a.g.n);
+  write_refined(a.g, at, i, j, 2.0 * lij - lii - ljj);
+}
+
+template <int H>
+__global__ void __launch_bounds__(SMALL_WARPS * 32) refine_small_kernel(const RefineArgs a) {
+  __shared__ int qi[SMALL_WARPS][64], qj[SMALL_WARPS][64];
+  __shared__ long long qa[SMALL_WARPS][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const GramArgs& g = a.g;
   const long long total = (long long)g.nrows * g.ncols;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int r = int(e / g.ncols), c = int(e - (long long)r * g.ncols);
-    const int i = g.row0 + r, j = g.col0 + c;
-    if (g.symmetric && j <= i) continue;
-    const long long at = (long long)r * g.ld + c;
-    if (!is_hit(a, at)) continue;
-    const double lij = chain_half_log<H>(a.mps_r, a.m_r, i, a.mps_c, a.m_c, j, g.n);
-    const double lii = chain_half_log<H>(a.mps_r, a.m_r, i, a.mps_r, a.m_r, i, g.n);
-    const double ljj = chain_half_log<H>(a.mps_c, a.m_c, j, a.mps_c, a.m_c, j, g.n);
-    write_refined(g, at, i, j, 2.0 * lij - lii - ljj);
+  const long long nwarps = (long long)gridDim.x * SMALL_WARPS;
+  const unsigned below = (1u << lane) - 1u;
+  int count = 0;
+  for (long long base = (blockIdx.x * (long long)SMALL_WARPS + warp) * 32; base < total; base += nwarps * 32) {
+    const long long e = base + lane;
+    bool hit = false;
+    long long at = 0;
+    int i = 0, j = 0;
+    if (e < total) {
+      const int r = int(e / g.ncols), c = int(e - (long long)r * g.ncols);
+      i = g.row0 + r;
+      j = g.col0 + c;
+      at = (long long)r * g.ld + c;
+      hit = !(g.symmetric && j <= i) && is_hit(a, at);
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (hit) {
+      const int pos = count + __popc(mask & below);
+      qi[warp][pos] = i;
+      qj[warp][pos] = j;
+      qa[warp][pos] = at;
+    }
+    count += __popc(mask);
+    __syncwarp();
+    if (count >= 32) {
+      refine_one<H>(a, qi[warp][lane], qj[warp][lane], qa[warp][lane]);
+      __syncwarp();
+      const int rest = count - 32;
+      int ti = 0, tj = 0;
+      long long ta = 0;
+      if (lane < rest) {
+        ti = qi[warp][32 + lane];
+        tj = qj[warp][32 + lane];
+        ta = qa[warp][32 + lane];
+      }
+      __syncwarp();
+      if (lane < rest) {
+        qi[warp][lane] = ti;
+        qj[warp][lane] = tj;
+        qa[warp][lane] = ta;
+      }
+      count = rest;
+      __syncwarp();
+    }
   }
+  if (lane < count) refine_one<H>(a, qi[warp][lane], qj[warp][lane], qa[warp][lane]);
 }
 
 // ---------------- bond 32: one warp per chain ----------------
@@ -449,10 +500,10 @@ DK_API dk_status dk_gram_refine(dk_ctx* ctx, const void* mps_rows, int m_rows, c
     rf::refine32_kernel<<<int(grid), rf::WARPS32 * 32, smem, st>>>(a);
     return launch_status();
   }
-  long long grid = (total + 128 * 8 - 1) / (128 * 8);
+  long long grid = (total + rf::SMALL_WARPS * 32 * 8 - 1) / (rf::SMALL_WARPS * 32 * 8);
   const long long cap = 16LL * ctx->sm_count;
   if (grid > cap) grid = cap;
-  if (chi_max == 4) rf::refine_small_kernel<2><<<int(grid), 128, 0, st>>>(a);
-  else rf::refine_small_kernel<4><<<int(grid), 128, 0, st>>>(a);
+  if (chi_max == 4) rf::refine_small_kernel<2><<<int(grid), rf::SMALL_WARPS * 32, 0, st>>>(a);
+  else rf::refine_small_kernel<4><<<int(grid), rf::SMALL_WARPS * 32, 0, st>>>(a);
   return launch_status();
 }
