@@ -106,9 +106,10 @@ typedef struct {
 /* Create a context on `device` (sets it current on the calling thread). The context
  * holds the device status word and cached launch parameters; it never owns user
  * buffers. Returns DK_ERR_NO_DEVICE if the device is not compute capability 10.x.
- * One device per process: kernels' shared-memory limits and occupancies are set up once
- * per process, on the device of the first launch; a launch on another device of the same
- * process returns DK_ERR_CUDA (multi-GPU runs use one process per GPU). */
+ * Calls on a context must be made with its device current. Every launch sets its kernel's
+ * shared-memory opt-in itself (the setting is per device), so contexts on several devices
+ * of one process are possible; multi-GPU runs here use one process per GPU, and only that
+ * arrangement has been run. */
 dk_status dk_create(dk_ctx** out, int device);
 void dk_destroy(dk_ctx* ctx);
 const char* dk_error_string(dk_status status);

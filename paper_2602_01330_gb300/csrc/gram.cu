@@ -21,6 +21,8 @@
 //    FP32 sum over the features, K = w K_q + (1 - w) K_c.
 #include <math.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "internal.h"
 #include "gram_common.cuh"
@@ -316,14 +318,20 @@ struct GramLauncher {
     s = encode_mps_map(ctx, &tmc, mps_c, m_c, a.n, Cfg::SITE_BYTES, Cfg::TC, Cfg::SPS);
     if (s != DK_OK) return s;
     auto kern = gram_kernel<Cfg>;
-    static int occ = -1;  // resident CTAs per SM, per instantiation
+    // The shared-memory opt-in is per device: set before every launch (a cheap host call).
+    // Resident CTAs per SM depend only on the kernel and the architecture, so the first
+    // query's answer serves every device and thread (a relaxed atomic, computed at most a
+    // few times in a race).
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES) != cudaSuccess)
+      return DK_ERR_CUDA;
+    static std::atomic<int> occ_cache{-1};
+    int occ = occ_cache.load(std::memory_order_relaxed);
     if (occ < 0) {
-      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES) != cudaSuccess)
-        return DK_ERR_CUDA;
       int o = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Cfg::NTHREADS, Cfg::SMEM_BYTES) != cudaSuccess)
         return DK_ERR_CUDA;
       occ = o > 0 ? o : 1;
+      occ_cache.store(occ, std::memory_order_relaxed);
     }
     long long grid = (long long)ctx->sm_count * occ;
     if (grid > a.ntiles) grid = a.ntiles;

@@ -480,13 +480,10 @@ DK_API dk_status dk_svm_ovo_train(dk_ctx* ctx, const float* kq, const float* kc,
   svm::TrainArgs a{kq,  kc,     ld,      n,     ctx->status, w, C, idx, count, m_max, labels, n_class,
                    n_class * (n_class - 1) / 2, double(tol), max_iter, coef, bias, iters};
   const size_t smem = svm::train_smem(m_max);
-  static size_t attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    if (cudaFuncSetAttribute(svm::ovo_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-        cudaSuccess)
-      return DK_ERR_CUDA;
-    attr = smem;
-  }
+  // the shared-memory opt-in is per device: set before every launch that needs it
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(svm::ovo_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+    return DK_ERR_CUDA;
   svm::ovo_train_kernel<<<dim3(a.n_pairs, n_jobs), svm::NT, smem, static_cast<cudaStream_t>(stream)>>>(a);
   return launch_status();
 }
@@ -506,13 +503,10 @@ DK_API dk_status dk_svm_ovo_predict(dk_ctx* ctx, const float* kq, const float* k
   svm::PredictArgs a{kq,    kc,        ld,    n_rows, n_cols, ctx->status, w,       rows,     row_count,
                      r_max, idx,       count, m_max,  coef,   bias,        n_class, n_pairs, decision, pred};
   const size_t smem = size_t(m_max + n_pairs) * sizeof(float);
-  static size_t attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    if (cudaFuncSetAttribute(svm::ovo_predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-        cudaSuccess)
-      return DK_ERR_CUDA;
-    attr = smem;
-  }
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(svm::ovo_predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+          cudaSuccess)
+    return DK_ERR_CUDA;
   svm::ovo_predict_kernel<<<dim3(r_max, n_jobs), svm::NT, smem, static_cast<cudaStream_t>(stream)>>>(a);
   return launch_status();
 }
