@@ -117,8 +117,10 @@ class GramSweep:
     """
 
     def __init__(self, ctx: dualk.Context, features: dict, fmap: dualk.FeatureMap, w: float = 0.5,
-                 autotuner: Autotuner | None = None, want=("k", "kq", "kc", "logkq"), device=None):
+                 autotuner: Autotuner | None = None, want=("k", "kq", "kc", "logkq"), device=None,
+                 refine: float | None = dualk.REFINE_TAU):
         self.ctx = ctx
+        self.refine = refine  # tau of the refinement pass after each Gram (None: none)
         self.fmap = fmap
         self.w = w
         self.device = device or torch.device("cuda", torch.cuda.current_device())
@@ -144,7 +146,7 @@ class GramSweep:
                                   stream=stream)
             self.ctx.set_gram_config(mt.cfg)
             dualk.gram_tile(self.ctx, mps, mps, symmetric=True, w=self.w, out=mt.out, ld=mt.x.shape[0],
-                            stream=stream)
+                            stream=stream, refine=self.refine)
         self.ctx.set_gram_config(0)
 
     def run_eager(self):
@@ -220,23 +222,31 @@ def run_benchmark(ctx: dualk.Context, m: int = 2000, dims=DIMS, reps: int = 3, a
             sw.run_native(graph=True, stream=side)
         torch.cuda.current_stream().wait_stream(side)
     native_ms = _time_ms(native, reps)
+    sw.refine = None  # the same pass without the refinement passes (kernels of the plain FP32 path)
+    plain_ms = _time_ms(sw.run_eager, reps)
+    sw.refine = dualk.REFINE_TAU
     ctx.sync_status()
     units = sw.entries_qubits()
     flops = sum(workload.gram_entries(mt.x.shape[0]) * workload.flops_per_pair(mt.d, 2) for mt in sw.mats)
     best = min(eager, graph, native_ms)
+    gram_only = plain_ms
     res = {
         "workload": f"sweep d={list(dims)} m={m} reps=2 chi=4 (build + Gram + refinement per d)",
         "entry_qubits": units,
         "eager_ms": eager, "graph_ms": graph, "native_sweep_graph_ms": native_ms,
         "eager_entry_qubits_per_s": units / (eager / 1e3), "graph_entry_qubits_per_s": units / (graph / 1e3),
         "native_sweep_entry_qubits_per_s": units / (native_ms / 1e3),
+        "eager_without_refinement_ms": plain_ms,
+        "eager_without_refinement_entry_qubits_per_s": units / (plain_ms / 1e3),
         "gram_tflops_block_count_best": flops / (best / 1e3) / 1e12,
         "tile_shapes": {mt.d: (mt.cfg, dualk.gram_config_info(mt.cfg) if mt.cfg else None) for mt in sw.mats},
         "concentration": {d: {k: s_[k] for k in ("kq_mean", "kq_var", "logkq_mean", "logkq_var") if k in s_}
                           for d, s_ in sw.concentration().items()},
     }
+    res["gram_tflops_block_count_without_refinement"] = flops / (gram_only / 1e3) / 1e12
     if peak_tflops:
         res["fraction_of_fp32_peak_best"] = res["gram_tflops_block_count_best"] / peak_tflops
+        res["fraction_of_fp32_peak_without_refinement"] = res["gram_tflops_block_count_without_refinement"] / peak_tflops
     return res
 
 
