@@ -224,10 +224,12 @@ typedef struct {
  * every qubit count of a study, each filled block by block), each item as
  * dk_gram_tile over all its samples with gamma = 1/n, mix weight w and precision prec,
  * followed, for complex64 items in F32 or BF16X3 with kq or logkq, by dk_gram_refine with
- * tau = DK_REFINE_TAU (declared below), issued in order on `stream`.
+ * tau = DK_REFINE_TAU (declared below) and the workspace ws / ws_bytes (NULL / 0: no
+ * workspace; otherwise dk_gram_refine_workspace_bytes(m, m) bytes for the largest item m,
+ * caller-owned, reused by the items one after the other), issued in order on `stream`.
  * graph = 0: the launches are issued directly.
  * graph = 1: the launches are recorded once into a CUDA graph that the context keeps
- *   (keyed by the bytes of the item array and the other arguments, pointers included) and
+ *   (keyed by the bytes of the item array and the other arguments, pointers and ws included) and
  *   replayed by every later call with the same key: one graph launch for the whole sweep.
  *   The first call with a new key also computes the results (eagerly, before recording).
  *   A replay reads the items' current buffer contents, so inputs may change between calls;
@@ -237,7 +239,7 @@ typedef struct {
  *         n < 1, no output, ld < m, tile_shape out of range; graph with the NULL stream),
  *         and those of dk_gram_tile; DK_ERR_CUDA if recording or instantiation fails. */
 dk_status dk_gram_sweep(dk_ctx* ctx, const dk_sweep_item* items, int n_items, int chi_max, dk_dtype dtype,
-                        dk_precision prec, float w, int graph, void* stream);
+                        dk_precision prec, float w, int graph, void* ws, size_t ws_bytes, void* stream);
 
 /* Block statevectors of a block-structured feature map (§II-C: entanglers only inside
  * blocks of b consecutive qubits, chain or all-to-all as for dk_mps_build_blocks). The state
@@ -401,17 +403,29 @@ dk_status dk_dual_kernel_rows(dk_ctx* ctx,
  *   j > i is examined, both entries written). x_rows / x_cols, gamma, w: as for that call
  *   (x needed only when k_out is given with w != 1 and kc_out is NULL).
  *   tau in (0, 1).
- * Bond 4 / 8: one thread per refined entry; bond 32: one warp per entry (three chains of
- * about 1e9 operations each), so the cost is proportional to the number of entries above
- * tau: nothing but one read of the block when there are none.
+ *   ws, ws_bytes  optional caller-owned device scratch of dk_gram_refine_workspace_bytes(
+ *                 m_rows, m_cols) bytes, 16-byte aligned: with it the pass first marks the
+ *                 samples that entries above tau need and computes each of their ln-norms
+ *                 once (three extra launches: a clear, a scan, the norms), so an entry costs
+ *                 one chain instead of three — the choice when many entries exceed tau; NULL
+ *                 (ws_bytes ignored): each entry computes both of its norms. Both give the
+ *                 same values. Nothing is read from ws before it is written.
+ * Bond 4 / 8: one thread per refined entry (queued per warp); bond 32: one warp per entry
+ * (chains of about 1e9 operations each), so the cost is proportional to the number of
+ * entries above tau: nothing but reads of the block when there are none.
  * Errors: DK_ERR_ARG (NULL pointers, ranges, ld < ncols, neither kq_out nor logkq_out, tau
  *         outside (0, 1), symmetric with different rows and columns, x missing when K_c has
  *         to be recomputed, misaligned MPS), DK_ERR_UNSUPPORTED (complex128, other chi_max),
- *         DK_ERR_CUDA. */
+ *         DK_ERR_WORKSPACE (ws too small or misaligned), DK_ERR_CUDA. */
 dk_status dk_gram_refine(dk_ctx* ctx, const void* mps_rows, int m_rows, const void* mps_cols, int m_cols, int n,
                          int chi_max, dk_dtype dtype, int row0, int nrows, int col0, int ncols, const float* x_rows,
                          const float* x_cols, float gamma, float w, float tau, float* k_out, float* kq_out,
-                         float* kc_out, float* logkq_out, long long ld, int symmetric, void* stream);
+                         float* kc_out, float* logkq_out, long long ld, int symmetric, void* ws, size_t ws_bytes,
+                         void* stream);
+
+/* Scratch bytes of dk_gram_refine's once-per-sample ln-norms: (m_rows + m_cols) flags and
+ * doubles, each array rounded up to 256 bytes; 0 for a size below 1. */
+size_t dk_gram_refine_workspace_bytes(int m_rows, int m_cols);
 
 /* Tile shapes of the Gram kernels (the blocks of §II-D, sized for one GB300 SM).
  * Shape 0 is the built-in choice; shapes 1..dk_gram_config_count(dtype, chi_max) can be

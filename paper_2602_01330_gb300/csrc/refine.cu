@@ -61,6 +61,13 @@ __device__ __forceinline__ DW acc_get(const Acc& A) {
 __device__ __forceinline__ int exponent_of(float v) { return int((__float_as_uint(v) >> 23) & 0xffu) - 127; }
 __device__ __forceinline__ float pow2_neg(int e) { return __uint_as_float(uint32_t(127 - e) << 23); }
 
+// ln|a| for a = (re + i im) 2^e2, with explicitly rounded operations so that every call site
+// gives the same bits for the same amplitude (a pair and a self-overlap of one sample agree).
+__device__ __forceinline__ double half_log_of(double re, double im, int e2) {
+  const double mod2 = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+  return __dadd_rn(__dmul_rn(0.5, log(mod2)), __dmul_rn(double(e2), 0.69314718055994530942));
+}
+
 // Complex element (s, jc, l) of a sample's compact site tensor (chi x chi complex64).
 __device__ __forceinline__ float2 site_elem(const float2* a, int chi, int h, int s, int jc, int l) {
   return __ldg(a + (s * h + jc) * chi + l);
@@ -177,7 +184,7 @@ __device__ double chain_half_log(const float2* __restrict__ mi, int m_i, int i, 
   }
   const double re = (double(E.r[0][0][0].hi) + double(E.r[0][0][0].lo)) + (double(E.r[1][0][0].hi) + double(E.r[1][0][0].lo));
   const double im = (double(E.i[0][0][0].hi) + double(E.i[0][0][0].lo)) + (double(E.i[1][0][0].hi) + double(E.i[1][0][0].lo));
-  return 0.5 * log(re * re + im * im) + double(e2) * 0.69314718055994530942;
+  return half_log_of(re, im, e2);
 }
 
 struct RefineArgs {
@@ -186,6 +193,14 @@ struct RefineArgs {
   const float2* mps_c;
   int m_r, m_c;
   float tau, log_tau;
+  // With a caller workspace: flags of the samples that some entry above tau needs, and their
+  // double-word ln-norms, computed once per sample (rows [0, m_r), columns after them; the
+  // column arrays alias the row arrays for a symmetric block). NULL: each refined entry
+  // computes both of its norms itself.
+  int* flag_r;
+  int* flag_c;
+  double* norm_r;
+  double* norm_c;
 };
 
 __device__ __forceinline__ bool is_hit(const RefineArgs& a, long long at) {
@@ -230,9 +245,60 @@ constexpr int SMALL_WARPS = 4;
 template <int H>
 __device__ __forceinline__ void refine_one(const RefineArgs& a, int i, int j, long long at) {
   const double lij = chain_half_log<H>(a.mps_r, a.m_r, i, a.mps_c, a.m_c, j, a.g.n);
-  const double lii = chain_half_log<H>(a.mps_r, a.m_r, i, a.mps_r, a.m_r, i, a.g.n);
-  const double ljj = chain_half_log<H>(a.mps_c, a.m_c, j, a.mps_c, a.m_c, j, a.g.n);
+  const double lii = a.norm_r ? a.norm_r[i] : chain_half_log<H>(a.mps_r, a.m_r, i, a.mps_r, a.m_r, i, a.g.n);
+  const double ljj = a.norm_c ? a.norm_c[j] : chain_half_log<H>(a.mps_c, a.m_c, j, a.mps_c, a.m_c, j, a.g.n);
   write_refined(a.g, at, i, j, 2.0 * lij - lii - ljj);
+}
+
+// Marks the samples whose ln-norm some entry above tau needs (all entries of the block,
+// same test as the refinement pass). Several threads may store the same 1: benign.
+__global__ void __launch_bounds__(256) mark_kernel(const RefineArgs a) {
+  const GramArgs& g = a.g;
+  const long long total = (long long)g.nrows * g.ncols;
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < total; e += (long long)gridDim.x * 256) {
+    const int r = int(e / g.ncols), c = int(e - (long long)r * g.ncols);
+    const int i = g.row0 + r, j = g.col0 + c;
+    if (g.symmetric && j <= i) continue;
+    if (is_hit(a, (long long)r * g.ld + c)) {
+      a.flag_r[i] = 1;
+      a.flag_c[j] = 1;
+    }
+  }
+}
+
+// ln-norms of the marked samples: entries u < m_r are row samples, the rest column samples
+// (none for a symmetric block). Marked samples are queued per warp as in the pass itself.
+template <int H>
+__device__ __forceinline__ void norm_one(const RefineArgs& a, int u) {
+  if (u < a.m_r) a.norm_r[u] = chain_half_log<H>(a.mps_r, a.m_r, u, a.mps_r, a.m_r, u, a.g.n);
+  else a.norm_c[u - a.m_r] = chain_half_log<H>(a.mps_c, a.m_c, u - a.m_r, a.mps_c, a.m_c, u - a.m_r, a.g.n);
+}
+
+template <int H>
+__global__ void __launch_bounds__(128) norms_small_kernel(const RefineArgs a, int n_units) {
+  __shared__ int q[4][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  int count = 0;
+  for (int base = (blockIdx.x * 4 + warp) * 32; base < n_units; base += gridDim.x * 4 * 32) {
+    const int u = base + lane;
+    const bool hit = u < n_units && (u < a.m_r ? a.flag_r[u] : a.flag_c[u - a.m_r]) != 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (hit) q[warp][count + __popc(mask & below)] = u;
+    count += __popc(mask);
+    __syncwarp();
+    if (count >= 32) {
+      norm_one<H>(a, q[warp][lane]);
+      __syncwarp();
+      const int rest = count - 32;
+      const int t = lane < rest ? q[warp][32 + lane] : 0;
+      __syncwarp();
+      if (lane < rest) q[warp][lane] = t;
+      count = rest;
+      __syncwarp();
+    }
+  }
+  if (lane < count) norm_one<H>(a, q[warp][lane]);
 }
 
 template <int H>
@@ -405,7 +471,7 @@ __device__ double chain32_half_log(const float2* __restrict__ mi, int m_i, int i
   const double im = (double(dw_ref(E, 0, 1, 0, 0, 0)) + double(dw_ref(E, 0, 1, 1, 0, 0))) +
                     (double(dw_ref(E, 1, 1, 0, 0, 0)) + double(dw_ref(E, 1, 1, 1, 0, 0)));
   __syncwarp();
-  return 0.5 * log(re * re + im * im) + double(e2) * 0.69314718055994530942;
+  return half_log_of(re, im, e2);
 }
 
 __global__ void __launch_bounds__(WARPS32 * 32) refine32_kernel(const RefineArgs a) {
@@ -433,24 +499,59 @@ __global__ void __launch_bounds__(WARPS32 * 32) refine32_kernel(const RefineArgs
       mask &= mask - 1;
       const int hi_ = __shfl_sync(0xffffffffu, i, src), hj = __shfl_sync(0xffffffffu, j, src);
       const double lij = chain32_half_log(a.mps_r, a.m_r, hi_, a.mps_c, a.m_c, hj, g.n, wbuf, lane);
-      const double lii = chain32_half_log(a.mps_r, a.m_r, hi_, a.mps_r, a.m_r, hi_, g.n, wbuf, lane);
-      const double ljj = chain32_half_log(a.mps_c, a.m_c, hj, a.mps_c, a.m_c, hj, g.n, wbuf, lane);
+      const double lii = a.norm_r ? a.norm_r[hi_]
+                                  : chain32_half_log(a.mps_r, a.m_r, hi_, a.mps_r, a.m_r, hi_, g.n, wbuf, lane);
+      const double ljj = a.norm_c ? a.norm_c[hj]
+                                  : chain32_half_log(a.mps_c, a.m_c, hj, a.mps_c, a.m_c, hj, g.n, wbuf, lane);
       if (lane == src) write_refined(g, at, i, j, 2.0 * lij - lii - ljj);
       __syncwarp();
     }
   }
 }
 
+// ln-norms of the marked samples at bond 32, one warp per sample.
+__global__ void __launch_bounds__(WARPS32 * 32) norms32_kernel(const RefineArgs a, int n_units) {
+  extern __shared__ __align__(16) float smf[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* wbuf = smf + warp * WARP_FLOATS;
+  for (int base = (blockIdx.x * WARPS32 + warp) * 32; base < n_units; base += gridDim.x * WARPS32 * 32) {
+    const int u = base + lane;
+    const bool hit = u < n_units && (u < a.m_r ? a.flag_r[u] : a.flag_c[u - a.m_r]) != 0;
+    unsigned mask = __ballot_sync(0xffffffffu, hit);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int v = base + src;
+      double l;
+      if (v < a.m_r) l = chain32_half_log(a.mps_r, a.m_r, v, a.mps_r, a.m_r, v, a.g.n, wbuf, lane);
+      else l = chain32_half_log(a.mps_c, a.m_c, v - a.m_r, a.mps_c, a.m_c, v - a.m_r, a.g.n, wbuf, lane);
+      if (lane == 0) {
+        if (v < a.m_r) a.norm_r[v] = l;
+        else a.norm_c[v - a.m_r] = l;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+inline size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
 }  // namespace rf
 }  // namespace dk
 
 using namespace dk;
 
+DK_API size_t dk_gram_refine_workspace_bytes(int m_rows, int m_cols) {
+  if (m_rows < 1 || m_cols < 1) return 0;
+  const size_t u = size_t(m_rows) + size_t(m_cols);
+  return rf::round256(u * sizeof(int)) + rf::round256(u * sizeof(double));
+}
+
 DK_API dk_status dk_gram_refine(dk_ctx* ctx, const void* mps_rows, int m_rows, const void* mps_cols, int m_cols, int n,
                                 int chi_max, dk_dtype dtype, int row0, int nrows, int col0, int ncols,
                                 const float* x_rows, const float* x_cols, float gamma, float w, float tau,
                                 float* k_out, float* kq_out, float* kc_out, float* logkq_out, long long ld,
-                                int symmetric, void* stream) {
+                                int symmetric, void* ws, size_t ws_bytes, void* stream) {
   if (!ctx || !mps_rows || !mps_cols || m_rows < 1 || m_cols < 1 || n < 1) return DK_ERR_ARG;
   if (dtype != DK_C64) return DK_ERR_UNSUPPORTED;
   if (chi_max != 4 && chi_max != 8 && chi_max != 32) return DK_ERR_UNSUPPORTED;
@@ -463,6 +564,7 @@ DK_API dk_status dk_gram_refine(dk_ctx* ctx, const void* mps_rows, int m_rows, c
   const bool need_kc = k_out && w != 1.0f && !kc_out;
   if (need_kc && (!x_rows || !x_cols)) return DK_ERR_ARG;
   if (!aligned16(mps_rows) || !aligned16(mps_cols)) return DK_ERR_ARG;
+  if (ws && (ws_bytes < dk_gram_refine_workspace_bytes(m_rows, m_cols) || !aligned16(ws))) return DK_ERR_WORKSPACE;
   if (nrows == 0 || ncols == 0) return DK_OK;
   rf::RefineArgs a{};
   a.g.n = n;
@@ -490,10 +592,41 @@ DK_API dk_status dk_gram_refine(dk_ctx* ctx, const void* mps_rows, int m_rows, c
   a.log_tau = logf(tau);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long total = (long long)nrows * ncols;
+  const int smem32 = rf::WARPS32 * rf::WARP_FLOATS * int(sizeof(float));
+  if (chi_max == 32 &&
+      (cudaFuncSetAttribute(rf::refine32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem32) != cudaSuccess ||
+       cudaFuncSetAttribute(rf::norms32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem32) != cudaSuccess))
+    return DK_ERR_CUDA;
+  if (ws) {
+    // the ln-norms of every sample an entry above tau needs, once per sample
+    const size_t u = size_t(m_rows) + size_t(m_cols);
+    uint8_t* b = static_cast<uint8_t*>(ws);
+    a.flag_r = reinterpret_cast<int*>(b);
+    a.norm_r = reinterpret_cast<double*>(b + rf::round256(u * sizeof(int)));
+    a.flag_c = symmetric ? a.flag_r : a.flag_r + m_rows;
+    a.norm_c = symmetric ? a.norm_r : a.norm_r + m_rows;
+    const int n_units = symmetric ? m_rows : m_rows + m_cols;
+    if (cudaMemsetAsync(a.flag_r, 0, u * sizeof(int), st) != cudaSuccess) return DK_ERR_CUDA;
+    long long mg = (total + 255) / 256;
+    if (mg > 8LL * ctx->sm_count) mg = 8LL * ctx->sm_count;
+    rf::mark_kernel<<<int(mg), 256, 0, st>>>(a);
+    dk_status s = launch_status();
+    if (s != DK_OK) return s;
+    if (chi_max == 32) {
+      long long ng = (n_units + rf::WARPS32 * 32 - 1) / (rf::WARPS32 * 32);
+      if (ng > 8LL * ctx->sm_count) ng = 8LL * ctx->sm_count;
+      rf::norms32_kernel<<<int(ng), rf::WARPS32 * 32, smem32, st>>>(a, n_units);
+    } else {
+      long long ng = (n_units + 127) / 128;
+      if (ng > 16LL * ctx->sm_count) ng = 16LL * ctx->sm_count;
+      if (chi_max == 4) rf::norms_small_kernel<2><<<int(ng), 128, 0, st>>>(a, n_units);
+      else rf::norms_small_kernel<4><<<int(ng), 128, 0, st>>>(a, n_units);
+    }
+    s = launch_status();
+    if (s != DK_OK) return s;
+  }
   if (chi_max == 32) {
-    const int smem = rf::WARPS32 * rf::WARP_FLOATS * int(sizeof(float));
-    if (cudaFuncSetAttribute(rf::refine32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-      return DK_ERR_CUDA;
+    const int smem = smem32;
     long long grid = (total + rf::WARPS32 * 32 * 32 - 1) / (rf::WARPS32 * 32 * 32);
     const long long cap = 8LL * ctx->sm_count;
     if (grid > cap) grid = cap;

@@ -34,17 +34,20 @@ struct GraphCache {
 };
 
 std::vector<unsigned char> make_key(const dk_sweep_item* items, int n_items, int chi_max, dk_dtype dtype,
-                                    dk_precision prec, float w) {
-  std::vector<unsigned char> key(sizeof(dk_sweep_item) * size_t(n_items) + 4 * sizeof(int));
-  memcpy(key.data(), items, sizeof(dk_sweep_item) * size_t(n_items));
+                                    dk_precision prec, float w, const void* ws, size_t ws_bytes) {
+  const size_t head = sizeof(dk_sweep_item) * size_t(n_items);
+  std::vector<unsigned char> key(head + 4 * sizeof(int) + sizeof(ws) + sizeof(ws_bytes));
+  memcpy(key.data(), items, head);
   int tail[4] = {chi_max, int(dtype), int(prec), 0};
   memcpy(&tail[3], &w, sizeof(float));
-  memcpy(key.data() + sizeof(dk_sweep_item) * size_t(n_items), tail, sizeof(tail));
+  memcpy(key.data() + head, tail, sizeof(tail));
+  memcpy(key.data() + head + sizeof(tail), &ws, sizeof(ws));
+  memcpy(key.data() + head + sizeof(tail) + sizeof(ws), &ws_bytes, sizeof(ws_bytes));
   return key;
 }
 
 dk_status run_items(dk_ctx* ctx, const dk_sweep_item* items, int n_items, int chi_max, dk_dtype dtype,
-                    dk_precision prec, float w, cudaStream_t st) {
+                    dk_precision prec, float w, void* ws, size_t ws_bytes, cudaStream_t st) {
   const int saved = ctx->gram_config;
   dk_status s = DK_OK;
   for (int t = 0; t < n_items && s == DK_OK; ++t) {
@@ -57,7 +60,8 @@ dk_status run_items(dk_ctx* ctx, const dk_sweep_item* items, int n_items, int ch
                            (prec == DK_PREC_F32 || prec == DK_PREC_BF16X3) && (it.kq || it.logkq);
     if (s == DK_OK && refinable)
       s = dk_gram_refine(ctx, it.mps, it.m, it.mps, it.m, it.n, chi_max, dtype, 0, it.m, 0, it.m, it.x, it.x,
-                         1.0f / float(it.n), w, DK_REFINE_TAU, it.k, it.kq, it.kc, it.logkq, it.ld, 1, st);
+                         1.0f / float(it.n), w, DK_REFINE_TAU, it.k, it.kq, it.kc, it.logkq, it.ld, 1, ws, ws_bytes,
+                         st);
   }
   ctx->gram_config = saved;
   return s;
@@ -76,7 +80,7 @@ void sweep_cache_free(dk_ctx* ctx) {
 }  // namespace dk
 
 DK_API dk_status dk_gram_sweep(dk_ctx* ctx, const dk_sweep_item* items, int n_items, int chi_max, dk_dtype dtype,
-                               dk_precision prec, float w, int graph, void* stream) {
+                               dk_precision prec, float w, int graph, void* ws, size_t ws_bytes, void* stream) {
   using namespace dk;
   if (!ctx || !items || n_items < 1) return DK_ERR_ARG;
   for (int t = 0; t < n_items; ++t) {
@@ -87,10 +91,10 @@ DK_API dk_status dk_gram_sweep(dk_ctx* ctx, const dk_sweep_item* items, int n_it
     if (it.tile_shape < 0 || it.tile_shape > dk_gram_config_count(dtype, chi_max)) return DK_ERR_ARG;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (!graph) return run_items(ctx, items, n_items, chi_max, dtype, prec, w, st);
+  if (!graph) return run_items(ctx, items, n_items, chi_max, dtype, prec, w, ws, ws_bytes, st);
   if (st == nullptr) return DK_ERR_ARG;  // the legacy default stream cannot be captured
 
-  std::vector<unsigned char> key = make_key(items, n_items, chi_max, dtype, prec, w);
+  std::vector<unsigned char> key = make_key(items, n_items, chi_max, dtype, prec, w, ws, ws_bytes);
   if (!ctx->graphs) ctx->graphs = new GraphCache();
   GraphCache* cache = static_cast<GraphCache*>(ctx->graphs);
   std::lock_guard<std::mutex> lock(cache->mu);
@@ -98,13 +102,13 @@ DK_API dk_status dk_gram_sweep(dk_ctx* ctx, const dk_sweep_item* items, int n_it
     if (e.key == key) return cudaGraphLaunch(e.exec, st) == cudaSuccess ? DK_OK : DK_ERR_CUDA;
 
   // new key: run eagerly, then record the same launches without executing them
-  dk_status s = run_items(ctx, items, n_items, chi_max, dtype, prec, w, st);
+  dk_status s = run_items(ctx, items, n_items, chi_max, dtype, prec, w, ws, ws_bytes, st);
   if (s != DK_OK) return s;
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return DK_ERR_CUDA;
   }
-  s = run_items(ctx, items, n_items, chi_max, dtype, prec, w, st);
+  s = run_items(ctx, items, n_items, chi_max, dtype, prec, w, ws, ws_bytes, st);
   cudaGraph_t g = nullptr;
   const cudaError_t end = cudaStreamEndCapture(st, &g);
   if (s != DK_OK || end != cudaSuccess || !g) {

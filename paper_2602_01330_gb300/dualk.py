@@ -31,7 +31,7 @@ EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_
             "dk_pca_transform", "dk_pca_fit_noalloc", "dk_mps_build_blocks", "dk_block_states_bytes",
             "dk_block_states", "dk_gram_blocks", "dk_gram_sweep", "dk_workspace_bytes",
             "dk_set_block_gram_form", "dk_block_states_workspace_bytes", "dk_gram_blocks_workspace_bytes",
-            "dk_gram_refine")
+            "dk_gram_refine", "dk_gram_refine_workspace_bytes")
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 PCA_MAX_FEATURES = 4096  # DK_PCA_MAX_FEATURES
 PCA_NOALLOC_MAX_FEATURES = 256  # DK_PCA_NOALLOC_MAX_FEATURES
@@ -77,7 +77,8 @@ def _lib():
     lib.dk_mps_build_blocks.restype = i32
     lib.dk_workspace_bytes.argtypes = [i32, i32, i32, i32]
     lib.dk_workspace_bytes.restype = ctypes.c_size_t
-    lib.dk_gram_sweep.argtypes = [vp, ctypes.POINTER(_SweepItem), i32, i32, i32, i32, f32, i32, vp]
+    lib.dk_gram_sweep.argtypes = [vp, ctypes.POINTER(_SweepItem), i32, i32, i32, i32, f32, i32, vp, ctypes.c_size_t,
+                                  vp]
     lib.dk_gram_sweep.restype = i32
     lib.dk_block_states_bytes.argtypes = [i32, i32, i32]
     lib.dk_block_states_bytes.restype = ctypes.c_size_t
@@ -98,8 +99,10 @@ def _lib():
                                         f32, f32, i32, vp, vp, vp, vp, vp]
     lib.dk_dual_kernel_rows.restype = i32
     lib.dk_gram_refine.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, f32, f32, f32,
-                                   vp, vp, vp, vp, i64, i32, vp]
+                                   vp, vp, vp, vp, i64, i32, vp, ctypes.c_size_t, vp]
     lib.dk_gram_refine.restype = i32
+    lib.dk_gram_refine_workspace_bytes.argtypes = [i32, i32]
+    lib.dk_gram_refine_workspace_bytes.restype = ctypes.c_size_t
     lib.dk_gram_config_count.argtypes = [i32, i32]
     lib.dk_gram_config_count.restype = i32
     ip = ctypes.POINTER(ctypes.c_int)
@@ -292,10 +295,13 @@ class _SweepItem(ctypes.Structure):
                 ("ld", ctypes.c_longlong), ("m", ctypes.c_int), ("n", ctypes.c_int), ("tile_shape", ctypes.c_int)]
 
 
-def gram_sweep(ctx: "Context", items, w: float = 0.5, prec: int | None = None, graph: bool = False, stream=None):
+def gram_sweep(ctx: "Context", items, w: float = 0.5, prec: int | None = None, graph: bool = False, stream=None,
+               ws: torch.Tensor | None = None):
     """dk_gram_sweep over items = [(MPS, out dict of m x m tensors, tile_shape id)], all with
     the same chi_max and dtype. graph=True records the launches once into a CUDA graph kept by
-    the context and replays it on later calls with the same items (needs a non-default stream)."""
+    the context and replays it on later calls with the same items (needs a non-default stream).
+    ws: workspace of the refinement passes (refine_workspace(m, m) for the largest m), kept by
+    the caller across calls (a recorded graph refers to it); None: per-entry norms."""
     first = items[0][0]
     prec = _default_prec(first) if prec is None else prec
     arr = (_SweepItem * len(items))()
@@ -306,7 +312,8 @@ def gram_sweep(ctx: "Context", items, w: float = 0.5, prec: int | None = None, g
         arr[t] = _SweepItem(_ptr(mps.data), _ptr(ln), _ptr(mps.x), _ptr(out.get("k")), _ptr(out.get("kq")),
                             _ptr(out.get("kc")), _ptr(out.get("logkq")), mps.m, mps.m, mps.n, int(tile))
     _check(_lib().dk_gram_sweep(ctx.handle, arr, len(items), first.chi_max, first.dtype, int(prec), float(w),
-                                1 if graph else 0, _stream(stream)), "dk_gram_sweep")
+                                1 if graph else 0, _ptr(ws), 0 if ws is None else int(ws.numel()), _stream(stream)),
+           "dk_gram_sweep")
 
 
 DK_ENT_CHAIN, DK_ENT_FULL = 0, 1
@@ -404,15 +411,25 @@ def _refinable(mps, prec):
     return mps.dtype == DK_C64 and mps.chi_max in (4, 8, 32) and prec in (DK_PREC_F32, DK_PREC_BF16X3)
 
 
+def refine_workspace(rows_m: int, cols_m: int, device) -> torch.Tensor:
+    """Scratch for dk_gram_refine's once-per-sample ln-norms (dk_gram_refine_workspace_bytes)."""
+    return torch.empty(int(_lib().dk_gram_refine_workspace_bytes(int(rows_m), int(cols_m))), dtype=torch.uint8,
+                       device=device)
+
+
 def gram_refine(ctx: "Context", rows: "MPS", cols: "MPS", row0: int, nrows: int, col0: int, ncols: int, out: dict,
-                ld: int, gamma: float, w: float, tau: float = REFINE_TAU, symmetric: bool = False, stream=None):
+                ld: int, gamma: float, w: float, tau: float = REFINE_TAU, symmetric: bool = False, stream=None,
+                ws: torch.Tensor | None = None):
     """dk_gram_refine: recompute the entries of a written block with K_q > tau in double-word
-    FP32 (see include/dualk.h)."""
+    FP32 (see include/dualk.h), with a workspace for once-per-sample ln-norms (allocated here
+    when not given)."""
+    if ws is None:
+        ws = refine_workspace(rows.m, cols.m, rows.data.device)
     _check(_lib().dk_gram_refine(ctx.handle, _ptr(rows.data), rows.m, _ptr(cols.data), cols.m, rows.n,
                                  rows.chi_max, rows.dtype, row0, nrows, col0, ncols, _ptr(rows.x), _ptr(cols.x),
                                  float(gamma), float(w), float(tau), _ptr(out.get("k")), _ptr(out.get("kq")),
                                  _ptr(out.get("kc")), _ptr(out.get("logkq")), int(ld), 1 if symmetric else 0,
-                                 _stream(stream)), "dk_gram_refine")
+                                 _ptr(ws), int(ws.numel()), _stream(stream)), "dk_gram_refine")
 
 
 def _outs(shape, device, want):
@@ -423,9 +440,11 @@ def _outs(shape, device, want):
 def gram_tile(ctx: Context, rows: MPS, cols: MPS, row0: int = 0, nrows: int | None = None,
               col0: int = 0, ncols: int | None = None, gamma: float | None = None, w: float = 0.5,
               want=("k", "kq", "kc", "logkq"), symmetric: bool = False, out=None, ld: int | None = None,
-              stream=None, prec: int | None = None, refine: float | None = REFINE_TAU):
+              stream=None, prec: int | None = None, refine: float | None = REFINE_TAU,
+              refine_ws: torch.Tensor | None = None):
     """dk_gram_tile: the (nrows x ncols) block of K, K_q, K_c, log K_q (dict of tensors),
-    then dk_gram_refine with tau = refine for FP32 / split-BF16 blocks (None: no refinement)."""
+    then dk_gram_refine with tau = refine for FP32 / split-BF16 blocks (None: no refinement;
+    refine_ws: its workspace, allocated when not given)."""
     nrows = rows.m - row0 if nrows is None else nrows
     ncols = cols.m - col0 if ncols is None else ncols
     if rows.n != cols.n or rows.chi_max != cols.chi_max or rows.dtype != cols.dtype:
@@ -446,20 +465,22 @@ def gram_tile(ctx: Context, rows: MPS, cols: MPS, row0: int = 0, nrows: int | No
                                _ptr(out.get("logkq")), int(ld), 1 if symmetric else 0, _stream(stream)),
            "dk_gram_tile")
     if refine is not None and _refinable(rows, prec) and (out.get("kq") is not None or out.get("logkq") is not None):
-        gram_refine(ctx, rows, cols, row0, nrows, col0, ncols, out, ld, gamma, w, refine, symmetric, stream)
+        gram_refine(ctx, rows, cols, row0, nrows, col0, ncols, out, ld, gamma, w, refine, symmetric, stream,
+                    ws=refine_ws)
     return out
 
 
 def gram(ctx: Context, mps: MPS, gamma: float | None = None, w: float = 0.5,
-         want=("k", "kq", "kc", "logkq"), stream=None, prec: int | None = None, refine: float | None = REFINE_TAU):
+         want=("k", "kq", "kc", "logkq"), stream=None, prec: int | None = None, refine: float | None = REFINE_TAU,
+         refine_ws: torch.Tensor | None = None):
     """Full symmetric m x m Gram of one MPS batch (each unordered pair contracted once)."""
     return gram_tile(ctx, mps, mps, gamma=gamma, w=w, want=want, symmetric=True, stream=stream, prec=prec,
-                     refine=refine)
+                     refine=refine, refine_ws=refine_ws)
 
 
 def dual_kernel_rows(ctx: Context, test: MPS, train: MPS, gamma: float | None = None, w: float = 0.5,
                      want=("k", "kq", "kc", "logkq"), out=None, stream=None, prec: int | None = None,
-                     refine: float | None = REFINE_TAU):
+                     refine: float | None = REFINE_TAU, refine_ws: torch.Tensor | None = None):
     """dk_dual_kernel_rows: the b x m block K(test, train), then dk_gram_refine (tau = refine)
     for FP32 / split-BF16 blocks."""
     if test.n != train.n or test.chi_max != train.chi_max or test.dtype != train.dtype:
@@ -477,7 +498,8 @@ def dual_kernel_rows(ctx: Context, test: MPS, train: MPS, gamma: float | None = 
                                       _ptr(out.get("logkq")), _stream(stream)),
            "dk_dual_kernel_rows")
     if refine is not None and _refinable(train, prec) and (out.get("kq") is not None or out.get("logkq") is not None):
-        gram_refine(ctx, test, train, 0, test.m, 0, train.m, out, train.m, gamma, w, refine, False, stream)
+        gram_refine(ctx, test, train, 0, test.m, 0, train.m, out, train.m, gamma, w, refine, False, stream,
+                    ws=refine_ws)
     return out
 
 

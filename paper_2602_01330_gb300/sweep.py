@@ -134,6 +134,8 @@ class GramSweep:
             out = {k: torch.empty((m, m), dtype=torch.float32, device=self.device) for k in want}
             self.mats.append(SweepMatrix(d, xt, buf, bond, ln, out))
         self.graph = None
+        m_max = max(mt.x.shape[0] for mt in self.mats)
+        self.refine_ws = dualk.refine_workspace(m_max, m_max, self.device)  # reused by every item
         if autotuner is not None:
             for mt in self.mats:
                 mps = dualk.mps_build(self.ctx, mt.x, self.fmap, out=mt.mps, bond=mt.bond, log_norm=mt.log_norm)
@@ -146,7 +148,7 @@ class GramSweep:
                                   stream=stream)
             self.ctx.set_gram_config(mt.cfg)
             dualk.gram_tile(self.ctx, mps, mps, symmetric=True, w=self.w, out=mt.out, ld=mt.x.shape[0],
-                            stream=stream, refine=self.refine)
+                            stream=stream, refine=self.refine, refine_ws=self.refine_ws)
         self.ctx.set_gram_config(0)
 
     def run_eager(self):
@@ -180,7 +182,7 @@ class GramSweep:
             mps = dualk.mps_build(self.ctx, mt.x, self.fmap, out=mt.mps, bond=mt.bond, log_norm=mt.log_norm,
                                   stream=stream)
             items.append((mps, mt.out, mt.cfg))
-        dualk.gram_sweep(self.ctx, items, w=self.w, graph=graph, stream=stream)
+        dualk.gram_sweep(self.ctx, items, w=self.w, graph=graph, stream=stream, ws=self.refine_ws)
 
     def concentration(self) -> dict:
         """Per qubit count: mean and variance of the off-diagonal K_q and log K_q of the last

@@ -225,3 +225,49 @@ def test_fmnist_d64_full_size_all_mixes(dk):
     print(json.dumps({"case": "fmnist d64 1000/200 all mixes", "max_abs_dK": worst,
                       "gram_offdiag_kq_max": float(kq_tr[off].max())}))
     ctx.sync_status()
+
+
+@pytest.mark.parametrize("chi,reps,d", [(4, 2, 6), (8, 3, 6), (32, 5, 10)])
+def test_refinement_with_and_without_workspace_agree(dk, chi, reps, d):
+    """Small n with many K_q above tau: the refinement pass with its workspace (each sample's
+    double-word norm computed once) gives the same bits as without it (each entry computing
+    both norms), for the symmetric Gram and for rows; and the refined block is within 1e-6 of
+    the oracle (brute-force statevectors) everywhere."""
+    import ctypes
+    dualk, ctx, torch = dk
+    from oracle import circuit
+    from paper_2602_01330_gb300 import synthetic
+    # bond 32 needs reps = 5, whose states spread fast: features narrowed to [1, 1 + pi / 10]
+    sc, off = (0.1, 1.0) if chi == 32 else (1.0, 0.0)
+    x = synthetic.uniform_angles(70, d, seed=d + chi) * sc + off
+    xt = synthetic.uniform_angles(9, d, seed=d + chi + 1) * sc + off
+    fm = dualk.FeatureMap(reps=reps, chi_max=chi)
+    m = dualk.mps_build(ctx, _dev(torch, x), fm)
+    mt = dualk.mps_build(ctx, _dev(torch, xt), fm)
+    lib = dualk._lib()
+    for rows, cols, sym in ((m, m, True), (mt, m, False)):
+        base = dualk.gram_tile(ctx, rows, cols, symmetric=sym, w=0.5, refine=None)
+        a = {k: v.clone() for k, v in base.items()}
+        b = {k: v.clone() for k, v in base.items()}
+        dualk.gram_refine(ctx, rows, cols, 0, rows.m, 0, cols.m, a, cols.m, 1.0 / d, 0.5, symmetric=sym)
+        st = lib.dk_gram_refine(ctx.handle, dualk._ptr(rows.data), rows.m, dualk._ptr(cols.data), cols.m, d, chi,
+                                dualk.DK_C64, 0, rows.m, 0, cols.m, dualk._ptr(rows.x), dualk._ptr(cols.x),
+                                1.0 / d, 0.5, dualk.REFINE_TAU, dualk._ptr(b["k"]), dualk._ptr(b["kq"]),
+                                dualk._ptr(b["kc"]), dualk._ptr(b["logkq"]), cols.m, 1 if sym else 0, None, 0,
+                                dualk._stream(None))
+        assert st == 0
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        for key in ("k", "kq", "kc", "logkq"):
+            assert torch.equal(a[key], b[key]), (chi, sym, key)
+        refined = (base["kq"] > dualk.REFINE_TAU).sum().item()
+        assert refined > (rows.m * cols.m) // 20
+        ref = circuit.kernel_matrix(rows.x.cpu().numpy().astype(np.float64),
+                                    cols.x.cpu().numpy().astype(np.float64), reps)
+        assert np.max(np.abs(a["kq"].cpu().numpy() - ref)) <= TOL_K
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    out = dualk.gram_tile(ctx, m, m, symmetric=True, w=0.5, refine=None)
+    assert lib.dk_gram_refine(ctx.handle, dualk._ptr(m.data), m.m, dualk._ptr(m.data), m.m, d, chi, dualk.DK_C64,
+                              0, m.m, 0, m.m, dualk._ptr(m.x), dualk._ptr(m.x), 1.0 / d, 0.5, dualk.REFINE_TAU,
+                              None, dualk._ptr(out["kq"]), None, None, m.m, 1, dualk._ptr(small), 16,
+                              dualk._stream(None)) == 5
