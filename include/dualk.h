@@ -323,6 +323,25 @@ dk_status dk_gram_blocks(dk_ctx* ctx, const void* states_rows, int m_rows, const
 size_t dk_gram_blocks_workspace_bytes(dk_ctx* ctx, int n, int block, int nrows, int ncols, dk_precision prec,
                                       int symmetric, int with_kc);
 
+/* Refinement of the large values of a block written by dk_gram_blocks (§II-C Eqs. 7-10,
+ * factorised over the blocks; §II-D Eq. 11). The Gram kernels form each block's overlap as
+ * an FP32 (or split-BF16) dot product of 2^b amplitudes and sum the logs over the blocks;
+ * on K_q of order one at n = 784 in blocks of 10 that leaves about 5e-5 (FP32) and 4e-4
+ * (split BF16). This call recomputes every entry with K_q > tau (log K_q > ln tau when
+ * kq_out is NULL; not the symmetric diagonal): for every block the overlap and both
+ * self-overlaps of the stored amplitudes with exact products and compensated (Dot2)
+ * sums, the lanes of a warp added in FP64, log K_q = sum_B [log |<a_B|b_B>|^2 - log
+ * <a_B|a_B> - log <b_B|b_B>] in FP64; then K_q, log K_q and K as dk_gram_refine does. One
+ * warp per refined entry: the cost is proportional to the entries above tau.
+ *   Arguments as for the dk_gram_blocks call that wrote the block (states, sizes, n, block,
+ *   prec, range, x, gamma, w, outputs, ld, symmetric); tau in (0, 1).
+ * Errors: DK_ERR_ARG (as dk_gram_refine), DK_ERR_UNSUPPORTED (block, prec), DK_ERR_CUDA. */
+dk_status dk_gram_blocks_refine(dk_ctx* ctx, const void* states_rows, int m_rows, const void* states_cols, int m_cols,
+                                int n, int block, dk_precision prec, int row0, int nrows, int col0, int ncols,
+                                const float* x_rows, const float* x_cols, float gamma, float w, float tau,
+                                float* k_out, float* kq_out, float* kc_out, float* logkq_out, long long ld,
+                                int symmetric, void* stream);
+
 /* Kernels the context uses for DK_PREC_BF16X3 block states' self-norms and block Grams:
  * DK_BLOCK_TCGEN05 (default; 128 x 128 or 128 x 64 pair tiles, one CTA per SM, tcgen05.mma
  * from TMA-loaded shared memory into tensor-memory accumulators) or DK_BLOCK_MMA_SYNC. Both

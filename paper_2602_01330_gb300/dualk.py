@@ -31,7 +31,10 @@ EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_
             "dk_pca_transform", "dk_pca_fit_noalloc", "dk_mps_build_blocks", "dk_block_states_bytes",
             "dk_block_states", "dk_gram_blocks", "dk_gram_sweep", "dk_workspace_bytes",
             "dk_set_block_gram_form", "dk_block_states_workspace_bytes", "dk_gram_blocks_workspace_bytes",
-            "dk_gram_refine", "dk_gram_refine_workspace_bytes")
+            "dk_gram_refine", "dk_gram_refine_workspace_bytes", "dk_gram_blocks_refine")
+# Entries with K_q above this are recomputed after every FP32 / split-BF16 Gram, rows and
+# block-Gram call of the binding (dk_gram_refine, dk_gram_blocks_refine; refine=None: not).
+REFINE_TAU = 0.02  # DK_REFINE_TAU
 SVM_MAX_SAMPLES = 4096  # DK_SVM_MAX_SAMPLES
 PCA_MAX_FEATURES = 4096  # DK_PCA_MAX_FEATURES
 PCA_NOALLOC_MAX_FEATURES = 256  # DK_PCA_NOALLOC_MAX_FEATURES
@@ -101,6 +104,9 @@ def _lib():
     lib.dk_gram_refine.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, f32, f32, f32,
                                    vp, vp, vp, vp, i64, i32, vp, ctypes.c_size_t, vp]
     lib.dk_gram_refine.restype = i32
+    lib.dk_gram_blocks_refine.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, f32, f32,
+                                          f32, vp, vp, vp, vp, i64, i32, vp]
+    lib.dk_gram_blocks_refine.restype = i32
     lib.dk_gram_refine_workspace_bytes.argtypes = [i32, i32]
     lib.dk_gram_refine_workspace_bytes.restype = ctypes.c_size_t
     lib.dk_gram_config_count.argtypes = [i32, i32]
@@ -368,8 +374,10 @@ def block_states(ctx: Context, x: torch.Tensor, fmap: FeatureMap, entangler: int
 
 
 def gram_blocks(ctx: Context, rows: BlockStates, cols: BlockStates | None = None, gamma: float | None = None,
-                w: float = 0.5, want=("k", "kq", "kc", "logkq"), stream=None) -> dict:
-    """dk_gram_blocks: K, K_q, K_c, log K_q of rows x cols (symmetric when cols is None)."""
+                w: float = 0.5, want=("k", "kq", "kc", "logkq"), stream=None,
+                refine: float | None = REFINE_TAU) -> dict:
+    """dk_gram_blocks: K, K_q, K_c, log K_q of rows x cols (symmetric when cols is None), then
+    dk_gram_blocks_refine with tau = refine (None: no refinement)."""
     symmetric = cols is None
     cols = rows if cols is None else cols
     if rows.n != cols.n or rows.block != cols.block or rows.prec != cols.prec:
@@ -386,6 +394,13 @@ def gram_blocks(ctx: Context, rows: BlockStates, cols: BlockStates | None = None
                                  _ptr(out.get("kq")),
                                  _ptr(out.get("kc")), _ptr(out.get("logkq")), int(cols.m), 1 if symmetric else 0,
                                  _ptr(ws), ws_bytes, _stream(stream)), "dk_gram_blocks")
+    if refine is not None and (out.get("kq") is not None or out.get("logkq") is not None):
+        _check(_lib().dk_gram_blocks_refine(ctx.handle, _ptr(rows.data), rows.m, _ptr(cols.data), cols.m, rows.n,
+                                            rows.block, rows.prec, 0, rows.m, 0, cols.m, _ptr(rows.x),
+                                            _ptr(cols.x), float(gamma), float(w), float(refine),
+                                            _ptr(out.get("k")), _ptr(out.get("kq")), _ptr(out.get("kc")),
+                                            _ptr(out.get("logkq")), int(cols.m), 1 if symmetric else 0,
+                                            _stream(stream)), "dk_gram_blocks_refine")
     return out
 
 
@@ -400,11 +415,6 @@ def self_overlap(ctx: Context, mps: "MPS", prec: int, out: torch.Tensor | None =
 
 def _default_prec(mps):
     return DK_PREC_F32 if mps.dtype == DK_C64 else DK_PREC_F64
-
-
-# Entries with K_q above this are recomputed in double-word FP32 by dk_gram_refine after
-# every FP32 / split-BF16 Gram and rows call of the binding (refine=None switches it off).
-REFINE_TAU = 0.02
 
 
 def _refinable(mps, prec):

@@ -391,7 +391,8 @@ def test_block_gram_symmetric_offset_diagonal(dk, form):
     fm = dualk.FeatureMap(reps=2, block=10)
     with _form(dualk, ctx, form):
         s = dualk.block_states(ctx, x, fm, dualk.DK_ENT_FULL, prec=dualk.DK_PREC_BF16X3)
-        full = dualk.gram_blocks(ctx, s, w=1.0, want=("logkq",))["logkq"]
+        # both blocks straight from the Gram kernels (no refinement pass on either side)
+        full = dualk.gram_blocks(ctx, s, w=1.0, want=("logkq",), refine=None)["logkq"]
         sub = torch.full((300, 300), -7.0, device="cuda")
         ws, nws = _ws(dualk, ctx, 40, 10, 300, 300, dualk.DK_PREC_BF16X3, 1, 0)
         _check_call(dualk, dualk._lib().dk_gram_blocks(
@@ -479,3 +480,54 @@ def test_tcgen05_block_calls_use_the_callers_workspace(dk):
     torch.cuda.synchronize()
     ctx.sync_status()
     assert torch.equal(k, ref["k"])
+
+
+def _block_pair_logs(xa, xb, reps, b, entangler):
+    """Oracle log K_q of the aligned pairs (xa[p], xb[p]): the sum over blocks of
+    log |<psi_B(a)|psi_B(b)>|^2 from the oracle's dense block statevectors."""
+    from oracle import circuit
+    n = xa.shape[1]
+    out = np.zeros(xa.shape[0])
+    for s in range(0, n, b):
+        e = min(s + b, n)
+        for p in range(xa.shape[0]):
+            u = circuit.statevector(xa[p, s:e].astype(np.float64), reps, entangler=entangler)
+            v = circuit.statevector(xb[p, s:e].astype(np.float64), reps, entangler=entangler)
+            out[p] += np.log(abs(np.vdot(u, v)) ** 2)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16x3"])
+def test_block_gram_near_duplicates_n784(dk, prec):
+    """n = 784 in all-to-all blocks of 10 (79 blocks), 300 samples of which 200..263 are near
+    copies of 0..63 (K_q spread over about 1e-3 .. 1): the near pairs of the symmetric Gram
+    against the oracle, 1e-6 on K_q in FP32 and 1e-4 in split BF16 (tcgen05 form), after the
+    refinement pass (dk_gram_blocks_refine) the binding runs; without it the Gram kernels'
+    sums of 79 block logs leave about 5e-5 (FP32) and 4e-4 (split BF16), printed too."""
+    import json
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    x = synthetic.fmnist_like(300, 0, 784)["x_train"].copy()
+    x[200:264] = synthetic.near_copies(x[0:64], 3e-4, 3e-2, seed=71)
+    p = dualk.DK_PREC_F32 if prec == "f32" else dualk.DK_PREC_BF16X3
+    fm = dualk.FeatureMap(reps=2, block=10)
+    s = dualk.block_states(ctx, _dev(torch, x), fm, dualk.DK_ENT_FULL, prec=p)
+    g = dualk.gram_blocks(ctx, s, w=1.0, want=("kq", "logkq"))
+    g0 = dualk.gram_blocks(ctx, s, w=1.0, want=("kq", "logkq"), refine=None)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    ref = np.exp(_block_pair_logs(x[0:64], x[200:264], 2, 10, "full"))
+    pick = lambda t: t.cpu().numpy().astype(np.float64)[np.arange(64), np.arange(200, 264)]
+    got, got0 = pick(g["kq"]), pick(g0["kq"])
+    err = np.abs(got - ref)
+    big = ref > 1e-3
+    print(json.dumps({"case": f"block gram n784 near pairs {prec}", "pairs_kq_gt_1e-3": int(big.sum()),
+                      "max_abs_dkq": float(err.max()), "max_rel_dkq": float((err[big] / ref[big]).max()),
+                      "max_abs_dkq_without_refinement": float(np.abs(got0 - ref).max())}))
+    # entries at or below tau keep the Gram kernels' bits
+    kq0 = g0["kq"].cpu().numpy()
+    keep = ~(kq0 > dualk.REFINE_TAU) | np.eye(300, dtype=bool)
+    assert np.array_equal(kq0[keep], g["kq"].cpu().numpy()[keep])
+    assert np.all(np.diag(g["logkq"].cpu().numpy()) == 0.0)
+    assert big.sum() >= 40
+    assert err.max() <= (1e-6 if prec == "f32" else 1e-4)

@@ -271,3 +271,24 @@ def test_refinement_with_and_without_workspace_agree(dk, chi, reps, d):
                               0, m.m, 0, m.m, dualk._ptr(m.x), dualk._ptr(m.x), 1.0 / d, 0.5, dualk.REFINE_TAU,
                               None, dualk._ptr(out["kq"]), None, None, m.m, 1, dualk._ptr(small), 16,
                               dualk._stream(None)) == 5
+
+
+def test_refinement_of_a_log_only_block(dk):
+    """A call that asks for log K_q alone is refined by log K_q > ln tau: the result equals
+    the log K_q of a call with every output, bit for bit, and is within 1e-3 relative of the
+    oracle; K_q(x, x) stays exactly 0 in log form."""
+    dualk, ctx, torch = dk
+    from oracle import circuit
+    from paper_2602_01330_gb300 import synthetic
+    x = synthetic.uniform_angles(50, 6, seed=77)
+    m = dualk.mps_build(ctx, _dev(torch, x), dualk.FeatureMap(reps=2, chi_max=4))
+    full = dualk.gram(ctx, m, w=0.5)
+    only = dualk.gram(ctx, m, w=0.5, want=("logkq",))
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert only["kq"] is None
+    assert torch.equal(only["logkq"], full["logkq"])
+    assert bool(torch.all(torch.diagonal(only["logkq"]) == 0.0))
+    ref = np.log(circuit.kernel_matrix(x, x, 2))
+    got = only["logkq"].cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(np.exp(got) - np.exp(ref))) <= TOL_K
