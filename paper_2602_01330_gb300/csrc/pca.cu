@@ -109,12 +109,10 @@ __global__ void eye_kernel(float* __restrict__ Vt, int p) {
 // index of round-robin position t in round r (positions 0..pe-1, pe even; 0 stays put)
 __device__ __forceinline__ int rr_pos(int t, int r, int pe) { return t == 0 ? 0 : 1 + (t - 1 + r) % (pe - 1); }
 
-// rotation angles of every pair of round r: (i, j, c, s) with i < j; a pair holding the
+// rotation angles of pair k of round r: (i, j, c, s) with i < j; a pair holding the
 // padding index p (odd p) is the identity
-__global__ void jacobi_params_kernel(const float* __restrict__ A, int p, int pe, int r, int2* __restrict__ ij,
-                                     float4* __restrict__ cs) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= pe / 2) return;
+__device__ __forceinline__ void jacobi_pair_params(const float* A, int p, int pe, int r, int k, int2* ij,
+                                                   float4* cs) {
   int i = rr_pos(k, r, pe), j = rr_pos(pe - 1 - k, r, pe);
   if (i > j) {
     const int t = i;
@@ -136,12 +134,24 @@ __global__ void jacobi_params_kernel(const float* __restrict__ A, int p, int pe,
   cs[k] = make_float4(c, s, t, 0.0f);
 }
 
+// the rotation angles of round r (the first round of a fit)
+__global__ void jacobi_params_kernel(const float* __restrict__ A, int p, int pe, int r, int2* __restrict__ ij,
+                                     float4* __restrict__ cs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < pe / 2) jacobi_pair_params(A, p, pe, r, k, ij, cs);
+}
+
 // one round: block (k1) handles the rows of pair k1; thread k2 the 2 x 2 block with the
 // columns of pair k2: B' = J1^T B J2 (J = [[c, s], [-s, c]]); the block's pair also rotates
 // rows i1, j1 of V^T
+//
+// One launch per round: the CTA that finishes the round last (a counter each CTA bumps after
+// a fence) computes the next round's angles from the finished matrix, so no launch of its
+// own and no CTA waits for another; it also resets the counter. r_next < 0: last round.
 __global__ void __launch_bounds__(256) jacobi_rotate_kernel(float* __restrict__ A, float* __restrict__ Vt, int p,
-                                                            int npairs, const int2* __restrict__ ij,
-                                                            const float4* __restrict__ cs) {
+                                                            int npairs, int2* __restrict__ ij,
+                                                            float4* __restrict__ cs, unsigned* __restrict__ done,
+                                                            int pe, int r_next) {
   const int k1 = blockIdx.x;
   const int2 a = ij[k1];
   const float4 r1 = cs[k1];
@@ -182,6 +192,16 @@ __global__ void __launch_bounds__(256) jacobi_rotate_kernel(float* __restrict__ 
       Vt[(long long)j1 * p + col] = r1.y * u + r1.x * v;
     }
   }
+  if (r_next < 0) return;
+  __shared__ bool last;
+  __threadfence();  // this CTA's writes of A are visible before it counts itself done
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == unsigned(npairs - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();  // every other CTA's writes are visible to this one
+  for (int k = threadIdx.x; k < npairs; k += blockDim.x) jacobi_pair_params(A, p, pe, r_next, k, ij, cs);
+  if (threadIdx.x == 0) *done = 0u;
 }
 
 // sqrt(off-diagonal sum of squares / total sum of squares) of A
@@ -323,6 +343,7 @@ struct Workspace {
   float* Vt;
   int2* ij;
   float4* cs;
+  unsigned* done;  // CTAs finished in the current Jacobi round
 };
 
 inline size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -330,7 +351,7 @@ inline size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 inline size_t workspace_bytes(int p) {
   const size_t pe = size_t(p + (p & 1));
   return 2 * round256(size_t(p) * p * sizeof(float)) + round256(pe / 2 * sizeof(int2)) +
-         round256(pe / 2 * sizeof(float4));
+         round256(pe / 2 * sizeof(float4)) + 256;
 }
 
 inline Workspace carve(void* ws, int p) {
@@ -344,6 +365,8 @@ inline Workspace carve(void* ws, int p) {
   w.ij = reinterpret_cast<int2*>(b);
   b += round256(pe / 2 * sizeof(int2));
   w.cs = reinterpret_cast<float4*>(b);
+  b += round256(pe / 2 * sizeof(float4));
+  w.done = reinterpret_cast<unsigned*>(b);
   return w;
 }
 
@@ -355,11 +378,13 @@ dk_status fit(dk_ctx* ctx, const float* x, int m, int p, int k, int sweeps, cons
   const int fill_blocks = int(((long long)p * p + 255) / 256 < 4096 ? ((long long)p * p + 255) / 256 : 4096);
   eye_kernel<<<fill_blocks, 256, 0, st>>>(w.Vt, p);
   const int pe = p + (p & 1), np = pe / 2;
-  for (int sw = 0; sw < sweeps; ++sw)
-    for (int r = 0; r < pe - 1; ++r) {
-      jacobi_params_kernel<<<(np + 255) / 256, 256, 0, st>>>(w.A, p, pe, r, w.ij, w.cs);
-      jacobi_rotate_kernel<<<np, 256, 0, st>>>(w.A, w.Vt, p, np, w.ij, w.cs);
-    }
+  if (cudaMemsetAsync(w.done, 0, sizeof(unsigned), st) != cudaSuccess) return DK_ERR_CUDA;
+  jacobi_params_kernel<<<(np + 255) / 256, 256, 0, st>>>(w.A, p, pe, 0, w.ij, w.cs);
+  const int rounds = sweeps * (pe - 1);
+  for (int q = 0; q < rounds; ++q) {
+    const int r_next = q + 1 < rounds ? (q + 1) % (pe - 1) : -1;
+    jacobi_rotate_kernel<<<np, 256, 0, st>>>(w.A, w.Vt, p, np, w.ij, w.cs, w.done, pe, r_next);
+  }
   if (off_norm) off_norm_kernel<<<1, 256, 0, st>>>(w.A, p, off_norm);
   select_kernel<<<p, 256, 0, st>>>(w.A, w.Vt, p, k, comps, eig);
   return launch_status();
@@ -418,7 +443,7 @@ constexpr size_t round256_c(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t noalloc_bytes() {
   return 2 * round256_c(size_t(DK_PCA_NOALLOC_MAX_FEATURES) * DK_PCA_NOALLOC_MAX_FEATURES * sizeof(float)) +
          round256_c(DK_PCA_NOALLOC_MAX_FEATURES / 2 * sizeof(int2)) +
-         round256_c(DK_PCA_NOALLOC_MAX_FEATURES / 2 * sizeof(float4));
+         round256_c(DK_PCA_NOALLOC_MAX_FEATURES / 2 * sizeof(float4)) + 256;
 }
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[noalloc_bytes()];
@@ -458,7 +483,8 @@ DK_API dk_status dk_pca_fit_noalloc(dk_ctx* ctx, const float* x, int m, int p, i
   const dk_status s = pca::noalloc_scratch(ctx->device, &scratch);
   if (s != DK_OK) return s;
   // every part of the scratch that the fit reads is written earlier in the same call (the
-  // covariance, the identity, each round's rotation table), so nothing needs clearing
+  // covariance, the identity, each round's rotation table, the round counter, which the fit
+  // clears), so nothing else needs clearing
   return pca::fit(ctx, x, m, p, k, sweeps, pca::carve(scratch, p), mean, scale, components, eigenvalues, off_norm,
                   static_cast<cudaStream_t>(stream));
 }
