@@ -537,7 +537,8 @@ def run_ours(args):
                      "kernel": f"gram_kernel<float,chi=4> (symmetric {n_tr}x{n_tr} Gram), "
                                f"{tile_gram[0]}x{tile_gram[1]} tiles, {tile_gram[2]} threads",
                      "tile_shape_ids": {"gram": cfg_gram, "rows": cfg_rows},
-                     "peak_source": f"FP32 FMA peak {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
+                     "peak_source": (f"FP32 FMA peak {props.multi_processor_count} SMs x 128 lanes x 2 x "
+                                     f"{sm_max:.0f} MHz"),
                      "avg_launch_ms": gram_avg_ms},
         "e2e": e2e,
         "phases_ms": phases,

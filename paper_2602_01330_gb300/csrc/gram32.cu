@@ -327,7 +327,9 @@ dk_status gram32_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps
   a.ntiles = count_tiles(a, TR, TC);
   auto kern = c32::gram32_f32_kernel<TR, TC>;
   // set before every launch: the attribute is per device and cheap to set
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess) return DK_ERR_CUDA;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+      cudaSuccess)
+    return DK_ERR_CUDA;
   long long grid = ctx->sm_count;
   if (grid > a.ntiles) grid = a.ntiles;
   if (grid < 1) return DK_OK;
@@ -339,7 +341,9 @@ dk_status gram32_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps
 dk_status self_overlap32_launch(const void* mps, int m, int n, float* log_norm, cudaStream_t st) {
   const int smem = (c32::ABUF + c32::BBUF + 3 * c32::EBLK) * 4;
   // set before every launch: the attribute is per device and cheap to set
-  if (cudaFuncSetAttribute(c32::self_overlap32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return DK_ERR_CUDA;
+  if (cudaFuncSetAttribute(c32::self_overlap32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
+    return DK_ERR_CUDA;
   c32::self_overlap32_kernel<<<m, 32, smem, st>>>(static_cast<const float*>(mps), m, n, log_norm);
   return launch_status();
 }

@@ -344,7 +344,9 @@ dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* 
   a.ntiles = count_tiles(a, TR, TC);
   auto kern = tc32::gram32_tc_kernel<TR, TC>;
   // set before every launch: the attribute is per device and cheap to set
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess) return DK_ERR_CUDA;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+      cudaSuccess)
+    return DK_ERR_CUDA;
   long long grid = ctx->sm_count;
   if (grid > a.ntiles) grid = a.ntiles;
   if (grid < 1) return DK_OK;
@@ -356,7 +358,9 @@ dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* 
 dk_status self_overlap32_tc_launch(const void* mps, int m, int n, float* log_norm, cudaStream_t st) {
   const int smem = 2 * tc32::SBUF * 2;
   // set before every launch: the attribute is per device and cheap to set
-  if (cudaFuncSetAttribute(tc32::self_overlap32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return DK_ERR_CUDA;
+  if (cudaFuncSetAttribute(tc32::self_overlap32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
+    return DK_ERR_CUDA;
   tc32::self_overlap32_tc_kernel<<<m, 32, smem, st>>>(static_cast<const float*>(mps), m, n, log_norm);
   return launch_status();
 }

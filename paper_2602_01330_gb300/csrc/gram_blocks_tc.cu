@@ -323,7 +323,9 @@ static dk_status launch_tc(dk_ctx* ctx, const void* sr, int m_r, const void* sc,
   using T = gbtc::TileCfg<WM>;
   auto kern = gbtc::gram_blocks_tc_kernel<WM>;
   // set before every launch: the attribute is per device and cheap to set
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(T::SMEM)) != cudaSuccess) return DK_ERR_CUDA;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(T::SMEM)) !=
+      cudaSuccess)
+    return DK_ERR_CUDA;
   a.ntiles = ntiles;
   long long grid = (long long)(8 / WM) * ctx->sm_count;
   if (grid > ntiles) grid = ntiles;

@@ -182,8 +182,10 @@ __device__ double chain_half_log(const float2* __restrict__ mi, int m_i, int i, 
       e2 += e;
     }
   }
-  const double re = (double(E.r[0][0][0].hi) + double(E.r[0][0][0].lo)) + (double(E.r[1][0][0].hi) + double(E.r[1][0][0].lo));
-  const double im = (double(E.i[0][0][0].hi) + double(E.i[0][0][0].lo)) + (double(E.i[1][0][0].hi) + double(E.i[1][0][0].lo));
+  const double re =
+      (double(E.r[0][0][0].hi) + double(E.r[0][0][0].lo)) + (double(E.r[1][0][0].hi) + double(E.r[1][0][0].lo));
+  const double im =
+      (double(E.i[0][0][0].hi) + double(E.i[0][0][0].lo)) + (double(E.i[1][0][0].hi) + double(E.i[1][0][0].lo));
   return half_log_of(re, im, e2);
 }
 

@@ -12,7 +12,8 @@
 // decrease picks j, one thread solves the two-variable problem, and the gradient is updated
 // with rows i and j. Multipliers and gradient are FP64 in shared memory, the working-set
 // choice compares FP32 copies (the kernel values are the FP32 Gram outputs); nothing else is
-// written until the end, so no global scratch is used. The loop ends when the largest KKT violation is below tol, or after max_iter steps.
+// written until the end, so no global scratch is used. The loop ends when the largest KKT
+// violation is below tol, or after max_iter steps.
 //
 // Prediction: one CTA per (job, row): the row's kernel values against the job's training
 // samples are staged in shared memory, each class pair's decision value is one warp-wide dot
@@ -482,7 +483,8 @@ DK_API dk_status dk_svm_ovo_train(dk_ctx* ctx, const float* kq, const float* kc,
   const size_t smem = svm::train_smem(m_max);
   // the shared-memory opt-in is per device: set before every launch that needs it
   if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(svm::ovo_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+      cudaFuncSetAttribute(svm::ovo_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+          cudaSuccess)
     return DK_ERR_CUDA;
   svm::ovo_train_kernel<<<dim3(a.n_pairs, n_jobs), svm::NT, smem, static_cast<cudaStream_t>(stream)>>>(a);
   return launch_status();

@@ -248,7 +248,8 @@ def run_benchmark(ctx: dualk.Context, m: int = 2000, dims=DIMS, reps: int = 3, a
     res["gram_tflops_block_count_without_refinement"] = flops / (gram_only / 1e3) / 1e12
     if peak_tflops:
         res["fraction_of_fp32_peak_best"] = res["gram_tflops_block_count_best"] / peak_tflops
-        res["fraction_of_fp32_peak_without_refinement"] = res["gram_tflops_block_count_without_refinement"] / peak_tflops
+        res["fraction_of_fp32_peak_without_refinement"] = (res["gram_tflops_block_count_without_refinement"]
+                                                           / peak_tflops)
     return res
 
 

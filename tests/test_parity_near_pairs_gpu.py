@@ -210,7 +210,8 @@ def test_fmnist_d64_full_size_all_mixes(dk):
         g = dualk.gram(ctx, mtr, w=w)
         r = dualk.dual_kernel_rows(ctx, mte, mtr, w=w)
         torch.cuda.synchronize()
-        for name, got, kq_ref, lkq_ref, kc_ref in (("gram", g, kq_tr, lkq_tr, kc_tr), ("rows", r, kq_te, lkq_te, kc_te)):
+        for name, got, kq_ref, lkq_ref, kc_ref in (("gram", g, kq_tr, lkq_tr, kc_tr),
+                                                   ("rows", r, kq_te, lkq_te, kc_te)):
             h = {k: v.cpu().numpy().astype(np.float64) for k, v in got.items()}
             dk_ = float(np.max(np.abs(h["k"] - og.dual_kernel(kq_ref, kc_ref, w))))
             dkq = float(np.max(np.abs(h["kq"] - kq_ref)))
