@@ -18,9 +18,11 @@
 //   step 2:  E'_s += C G          (A operand C from shared memory, B operand from G^T's
 //                                  accumulators),
 // and E'_s is again in accumulator form for the next site. No intermediate goes through
-// shared memory. The CTA stages, per site and double buffered, its row samples as C
-// operands and its column samples as B^T operands (the same 16 x 32 layout, without the
-// conjugation), split into BF16 hi / lo.
+// shared memory. Four staging warps, separate from the pair warps, fill a three-stage ring in
+// shared memory, one site per stage: the CTA's row samples as C operands and its column
+// samples as B^T operands (the same 16 x 32 layout, without the conjugation), split into
+// BF16 hi / lo. Their HBM loads and conversions run under the pair warps' MMAs, and the pair
+// warps hold no prefetch registers.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -153,7 +155,14 @@ __device__ __forceinline__ void mma_block(float (&acc)[4][4], const u16* xh, con
 }
 
 // One site of one pair (warp). rbuf: row-sample C operands; cbuf: column-sample B^T
-// operands. E is replaced by diag(acc_0, acc_1).
+// operands. E is replaced by diag(acc_0, acc_1). Two schedules of the same MMAs:
+//   IL = false: per (t, s) step 1, conversion of G, step 2 (fewest live registers);
+//   IL = true:  per t both step-1 products (s = 0, 1) back to back, so converting one G into
+//               B-operand words overlaps the other's MMAs, and the first step-2 product
+//               overlaps the second conversion.
+// Every accumulator receives its MMAs in the same order in both (acc_s: t = 0, then t = 1),
+// so the result does not depend on the schedule.
+template <bool IL>
 __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* cbuf, int lane) {
   float acc[2][4][4];
 #pragma unroll
@@ -162,23 +171,47 @@ __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* c
     for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[s][nt][c] = 0.0f;
+  if (IL) {
+    BFrag fe[2];
+    to_bfrag(E.v[0], fe[0]);  // B operands of E_t^T
+    to_bfrag(E.v[1], fe[1]);
 #pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    BFrag fe;
-    to_bfrag(E.v[t], fe);  // B operand of E_t^T
+    for (int t = 0; t < 2; ++t) {
+      // step 1: G_s^T = B_{s,t}^T . E_t^T for s = 0, 1
+      float g[2][4][4];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      // step 1: G^T = B^T . E_t^T
-      float g[4][4];
+      for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
+        for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) g[nt][c] = 0.0f;
-      mma_block(g, cbuf + (s * 2 + t) * 2 * COP, fe, lane);
-      // step 2: acc_s += C . G (B operand of G = (G^T)^T from G^T's accumulators)
-      BFrag fg;
-      to_bfrag(g, fg);
-      mma_block(acc[s], rbuf + (s * 2 + t) * 2 * COP, fg, lane);
+          for (int c = 0; c < 4; ++c) g[s][nt][c] = 0.0f;
+      mma_block(g[0], cbuf + (0 * 2 + t) * 2 * COP, fe[t], lane);
+      mma_block(g[1], cbuf + (1 * 2 + t) * 2 * COP, fe[t], lane);
+      // step 2: acc_s += C_{s,t} . G_s (B operand of G_s from G_s^T's accumulators)
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        BFrag fg;
+        to_bfrag(g[s], fg);
+        mma_block(acc[s], rbuf + (s * 2 + t) * 2 * COP, fg, lane);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      BFrag fe;
+      to_bfrag(E.v[t], fe);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        float g[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) g[nt][c] = 0.0f;
+        mma_block(g, cbuf + (s * 2 + t) * 2 * COP, fe, lane);
+        BFrag fg;
+        to_bfrag(g, fg);
+        mma_block(acc[s], rbuf + (s * 2 + t) * 2 * COP, fg, lane);
+      }
     }
   }
 #pragma unroll
@@ -229,84 +262,147 @@ __device__ __forceinline__ float half_log_mod(const Frag& E, int e2) {
   return fmaf(0.5f, logf(mod2), float(e2) * 0.69314718055994530942f);
 }
 
-template <int TR, int TC>
+// CTA of TR x TC pair warps (one pair each) and NPROD staging warps over a ring of NSTG
+// stages; a stage holds one site of the tile's TR row samples (C operands) and TC column
+// samples (B^T operands).
+constexpr int NPROD = 4;
+template <int TR, int TC, int NSTG, int BATCH_, bool IL_>
 struct CfgTc {
-  static constexpr int NW = TR * TC, NT = NW * 32;
-  static constexpr int STAGE = (TR + TC) * SBUF;  // u16 per stage
-  static constexpr int CH = (TR + TC) * CHUNKS;
-  static constexpr int PER_THREAD = (CH + NT - 1) / NT;
-  static constexpr int SMEM = 2 * STAGE * 2;
+  static constexpr int TR_ = TR, TC_ = TC, NSTG_ = NSTG;
+  static constexpr int NW = TR * TC;               // pair warps
+  static constexpr int PT = NPROD * 32;            // staging threads
+  static constexpr int NT = NW * 32 + PT;
+  static constexpr int STAGE = (TR + TC) * SBUF;   // u16 per stage
+  static constexpr int CH = (TR + TC) * CHUNKS;    // 16-byte chunks of a stage's site tensors
+  static_assert(CH % PT == 0, "whole chunks per staging thread");
+  static constexpr int PER_THREAD = CH / PT;
+  static constexpr int BATCH = BATCH_;             // loads in flight per staging thread
+  static constexpr bool IL = IL_;
+  static_assert(PER_THREAD % BATCH == 0, "whole batches");
+  static constexpr size_t BAR_OFF = size_t(NSTG) * STAGE * sizeof(u16);
+  static constexpr size_t SMEM = BAR_OFF + 2 * NSTG * sizeof(uint64_t) + 16;
 };
 
-template <int TR, int TC>
-__global__ void __launch_bounds__(TR * TC * 32, 1)
+// Warp roles. Staging warps: for every (tile, site) of the CTA, in order, wait until the ring
+// slot is free (empty barrier: one arrival per pair warp), read the site tensors of the
+// tile's samples from HBM (16-byte chunks, BATCH loads in flight per thread), split them into
+// BF16 hi / lo operands in shared memory and arrive on the slot's full barrier (one arrival
+// per staging thread, which releases its stores). Pair warps: wait for the slot, run one site
+// of their pair, release the slot. Every wait is bounded; on a timeout the CTA records
+// DEV_TIMEOUT in the status word, raises its abort flag and every role leaves its loop.
+template <class C>
+__global__ void __launch_bounds__(C::NT, 1)
     gram32_tc_kernel(const float* __restrict__ mps_r, int m_r, const float* __restrict__ mps_c, int m_c,
                      const GramArgs p) {
-  using C = CfgTc<TR, TC>;
+  constexpr int TR = C::TR_, TC = C::TC_, NSTG = C::NSTG_;
   extern __shared__ __align__(16) u16 smu[];
-  u16* stage[2] = {smu, smu + C::STAGE};
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(smu) + C::BAR_OFF);
+  uint64_t* empty = full + NSTG;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NSTG);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wr = warp / TC, wc = warp % TC;
-
-  float4 pre[C::PER_THREAD];
-  auto fetch = [&](int r0, int c0, int k) {
-#pragma unroll
-    for (int q = 0; q < C::PER_THREAD; ++q) {
-      const int ch = threadIdx.x + q * C::NT;
-      if (ch < C::CH) {
-        const int smp = ch / CHUNKS, w = chunk_of(ch % CHUNKS);
-        const bool is_row = smp < TR;
-        const int idx = is_row ? min(r0 + smp, m_r - 1) : min(c0 + smp - TR, m_c - 1);
-        const float* src = (is_row ? mps_r + (size_t(k) * m_r + idx) * SAMPLE_FLOATS
-                                   : mps_c + (size_t(k) * m_c + idx) * SAMPLE_FLOATS) + w * 4;
-        pre[q] = __ldg(reinterpret_cast<const float4*>(src));
-      }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTG; ++s) {
+      mbar_init(&full[s], C::PT);
+      mbar_init(&empty[s], C::NW);
     }
-  };
-  auto commit = [&](u16* st) {
-#pragma unroll
-    for (int q = 0; q < C::PER_THREAD; ++q) {
-      const int ch = threadIdx.x + q * C::NT;
-      if (ch < C::CH) {
-        const int smp = ch / CHUNKS, w = chunk_of(ch % CHUNKS);
-        if (smp < TR) put_chunk<true>(st + smp * SBUF, w, pre[q]);
-        else put_chunk<false>(st + smp * SBUF, w, pre[q]);
-      }
-    }
-  };
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
 
   const int my_tiles = (p.ntiles > int(blockIdx.x)) ? (p.ntiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
-  for (int lt = 0; lt < my_tiles; ++lt) {
+  auto tile_origin = [&](int lt, int& r0, int& c0) {
     int ti, tj;
     decode_tile(p, TR, TC, int(blockIdx.x) + lt * int(gridDim.x), ti, tj);
-    const int r0 = p.row0 + ti * TR, c0 = p.col0 + tj * TC;
-    Frag E;
-    init_e(E, lane);
-    int e2 = 0;
-    fetch(r0, c0, 0);
-    __syncthreads();
-    commit(stage[0]);
-    __syncthreads();
-    for (int k = 0; k < p.n; ++k) {
-      u16* cur = stage[k & 1];
-      if (k + 1 < p.n) fetch(r0, c0, k + 1);
-      pair_site(E, cur + wr * SBUF, cur + (TR + wc) * SBUF, lane);
-      if (k == p.n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1)) e2 += renorm(E);
-      if (k + 1 < p.n) commit(stage[(k + 1) & 1]);
-      __syncthreads();
-    }
-    if (lane == 0) {
-      const int i = r0 + wr, j = c0 + wc;
-      float d2 = 0.0f, comp = 0.0f;
-      if (p.need_kc && i < p.row0 + p.nrows && j < p.col0 + p.ncols) {
-        const float* xa = p.x_r + size_t(i) * p.n;
-        const float* xb = p.x_c + size_t(j) * p.n;
-        for (int f = 0; f < p.n; ++f) kahan_add_sq(d2, comp, __ldg(xa + f) - __ldg(xb + f));
+    r0 = p.row0 + ti * TR;
+    c0 = p.col0 + tj * TC;
+  };
+  auto give_up = [&]() {
+    record_status(p.status, DEV_TIMEOUT);
+    *abort_flag = 1;
+  };
+
+  if (warp >= C::NW) {
+    // ---- staging ----
+    const int pt = threadIdx.x - C::NW * 32;
+    long long g = 0;  // stage fills issued
+    bool stop = false;
+    for (int lt = 0; lt < my_tiles && !stop; ++lt) {
+      int r0, c0;
+      tile_origin(lt, r0, c0);
+      for (int k = 0; k < p.n; ++k, ++g) {
+        const int s = int(g % NSTG);
+        const long long use = g / NSTG;
+        if (*abort_flag || (use > 0 && !mbar_wait_bounded(&empty[s], u32((use - 1) & 1)))) {
+          give_up();
+          stop = true;
+          break;
+        }
+        u16* st = smu + s * C::STAGE;
+#pragma unroll
+        for (int b0 = 0; b0 < C::PER_THREAD; b0 += C::BATCH) {
+          float4 v[C::BATCH];
+#pragma unroll
+          for (int q = 0; q < C::BATCH; ++q) {
+            const int ch = pt + (b0 + q) * C::PT;
+            const int smp = ch / CHUNKS, w = chunk_of(ch % CHUNKS);
+            const bool is_row = smp < TR;
+            const int idx = is_row ? min(r0 + smp, m_r - 1) : min(c0 + smp - TR, m_c - 1);
+            const float* src = (is_row ? mps_r + (size_t(k) * m_r + idx) * SAMPLE_FLOATS
+                                       : mps_c + (size_t(k) * m_c + idx) * SAMPLE_FLOATS) + w * 4;
+            v[q] = __ldg(reinterpret_cast<const float4*>(src));
+          }
+#pragma unroll
+          for (int q = 0; q < C::BATCH; ++q) {
+            const int ch = pt + (b0 + q) * C::PT;
+            const int smp = ch / CHUNKS, w = chunk_of(ch % CHUNKS);
+            if (smp < TR) put_chunk<true>(st + smp * SBUF, w, v[q]);
+            else put_chunk<false>(st + smp * SBUF, w, v[q]);
+          }
+        }
+        mbar_arrive(&full[s]);
       }
-      write_pair(p, half_log_mod(E, e2), d2, i, j);
     }
-    __syncwarp();
+  } else {
+    // ---- pair warps ----
+    const int wr = warp / TC, wc = warp % TC;
+    long long g = 0;  // stages consumed
+    bool stop = false;
+    for (int lt = 0; lt < my_tiles && !stop; ++lt) {
+      int r0, c0;
+      tile_origin(lt, r0, c0);
+      Frag E;
+      init_e(E, lane);
+      int e2 = 0;
+      for (int k = 0; k < p.n; ++k, ++g) {
+        const int s = int(g % NSTG);
+        // one decision per warp: the MMAs below are warp-collective
+        if (!__all_sync(0xffffffffu, !*abort_flag && mbar_wait_bounded(&full[s], u32((g / NSTG) & 1)))) {
+          if (lane == 0) give_up();
+          stop = true;
+          break;
+        }
+        const u16* cur = smu + s * C::STAGE;
+        pair_site<C::IL>(E, cur + wr * SBUF, cur + (TR + wc) * SBUF, lane);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (k == p.n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1)) e2 += renorm(E);
+      }
+      if (stop) break;
+      if (lane == 0) {
+        const int i = r0 + wr, j = c0 + wc;
+        float d2 = 0.0f, comp = 0.0f;
+        if (p.need_kc && i < p.row0 + p.nrows && j < p.col0 + p.ncols) {
+          const float* xa = p.x_r + size_t(i) * p.n;
+          const float* xb = p.x_c + size_t(j) * p.n;
+          for (int f = 0; f < p.n; ++f) kahan_add_sq(d2, comp, __ldg(xa + f) - __ldg(xb + f));
+        }
+        write_pair(p, half_log_mod(E, e2), d2, i, j);
+      }
+      __syncwarp();
+    }
   }
+  __syncthreads();
 }
 
 // ln|<psi~_i|psi~_i>| with the same split-BF16 arithmetic (one warp per sample).
@@ -328,7 +424,7 @@ __global__ void __launch_bounds__(32) self_overlap32_tc_kernel(const float* __re
       put_chunk<false>(cbuf, w, v);
     }
     __syncwarp();
-    pair_site(E, rbuf, cbuf, lane);
+    pair_site<false>(E, rbuf, cbuf, lane);
     if (k == n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1)) e2 += renorm(E);
     __syncwarp();
   }
@@ -339,12 +435,13 @@ __global__ void __launch_bounds__(32) self_overlap32_tc_kernel(const float* __re
 
 dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
                            cudaStream_t st) {
-  constexpr int TR = 4, TC = 2;
-  using C = tc32::CfgTc<TR, TC>;
-  a.ntiles = count_tiles(a, TR, TC);
-  auto kern = tc32::gram32_tc_kernel<TR, TC>;
+  // 4 x 2 pairs per CTA, three stages, 12 loads in flight per staging thread, interleaved
+  // step-1 products (measured fastest of the tile shapes and schedules that fit 168 registers)
+  using C = tc32::CfgTc<4, 2, 3, 12, true>;
+  a.ntiles = count_tiles(a, C::TR_, C::TC_);
+  auto kern = tc32::gram32_tc_kernel<C>;
   // set before every launch: the attribute is per device and cheap to set
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM)) !=
       cudaSuccess)
     return DK_ERR_CUDA;
   long long grid = ctx->sm_count;
