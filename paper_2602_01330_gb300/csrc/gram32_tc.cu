@@ -23,7 +23,6 @@
 // samples as B^T operands (the same 16 x 32 layout, without the conjugation), split into
 // BF16 hi / lo. Their HBM loads and conversions run under the pair warps' MMAs, and the pair
 // warps hold no prefetch registers.
-#include <cuda_bf16.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -59,13 +58,21 @@ __device__ __forceinline__ void ldsm_x4(u32 (&r)[4], const u16* p) {
                : "r"(smem_u32(p)));
 }
 
-// (x, y) -> packed BF16 pairs hi and lo with x ~ hi + lo (low half = x).
+// (x, y) -> packed BF16 pairs hi and lo with x ~ hi + lo (low half = x): hi = round(x, y)
+// to BF16, the residuals x - hi and y - hi (exact in FP32: the upper half of hi's word, and
+// the lower half shifted up, are hi's values as FP32) rounded to BF16 again. Six instructions
+// in inline PTX, so that the compiler keeps them where the schedule places them.
 __device__ __forceinline__ void split2(float x, float y, u32& hi, u32& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
-  const float2 hf = __bfloat1622float2(h);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
-  hi = *reinterpret_cast<const u32*>(&h);
-  lo = *reinterpret_cast<const u32*>(&l);
+  asm volatile(
+      "{\n\t.reg .b32 hx, hy;\n\t.reg .f32 rx, ry;\n\t"
+      "cvt.rn.bf16x2.f32 %0, %3, %2;\n\t"
+      "shl.b32 hx, %0, 16;\n\t"
+      "and.b32 hy, %0, 0xffff0000;\n\t"
+      "sub.f32 rx, %2, hx;\n\t"
+      "sub.f32 ry, %3, hy;\n\t"
+      "cvt.rn.bf16x2.f32 %1, ry, rx;\n\t}"
+      : "=r"(hi), "=r"(lo)
+      : "f"(x), "f"(y));
 }
 constexpr u32 NEG2 = 0x80008000u;  // flips the sign of both BF16 halves
 
@@ -124,11 +131,22 @@ __device__ __forceinline__ void to_bfrag(const float (&x)[4][4], BFrag& f) {
         split2(x[2 * c + tile][2 * h], x[2 * c + tile][2 * h + 1], f.hi[c][h][tile], f.lo[c][h][tile]);
 }
 
+// Step q (0..7) of to_bfrag, in the same (c, h, tile) order: the same words, one split2.
+__device__ __forceinline__ void to_bfrag_step(const float (&x)[4][4], BFrag& f, int q) {
+  const int c = q >> 2, h = (q >> 1) & 1, tile = q & 1;
+  split2(x[2 * c + tile][2 * h], x[2 * c + tile][2 * h + 1], f.hi[c][h][tile], f.lo[c][h][tile]);
+}
+
 // acc += [Xr | Xi] . [[Yr, Yi], [-Yi, Yr]] for X (16 x 16 complex) from shared memory
 // (xh: hi operand, lo operand COP further) and Y given by f (Y = the transpose of the matrix
 // whose accumulators made f). k-step kk = 0 takes the rows [Yr | Yi], kk = 1 [-Yi | Yr]; the
-// MMAs are issued term-major over the four independent n-tile accumulators.
-__device__ __forceinline__ void mma_block(float (&acc)[4][4], const u16* xh, const BFrag& f, int lane) {
+// MMAs are issued term-major over the four independent n-tile accumulators. With SIDE, the
+// conversion sf = to_bfrag(sx) of an independent matrix is spread over the block, one split2
+// after every third MMA, so that the warp issues it between MMAs instead of in a burst of its own.
+template <bool SIDE>
+__device__ __forceinline__ void mma_block_side(float (&acc)[4][4], const u16* xh, const BFrag& f, int lane,
+                                               const float (&sx)[4][4], BFrag& sf) {
+  int n = 0;
 #pragma unroll
   for (int kk = 0; kk < 2; ++kk) {
     u32 ahi[4], alo[4];
@@ -146,23 +164,33 @@ __device__ __forceinline__ void mma_block(float (&acc)[4][4], const u16* xh, con
       bl[nt][1] = f.lo[c][h][1] ^ sg;
     }
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], alo, bh[nt][0], bh[nt][1]);
+    for (int term = 0; term < 3; ++term)
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], ahi, bl[nt][0], bl[nt][1]);
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) mma16816(acc[nt], ahi, bh[nt][0], bh[nt][1]);
+      for (int nt = 0; nt < 4; ++nt, ++n) {
+        if (term == 0) mma16816(acc[nt], alo, bh[nt][0], bh[nt][1]);
+        else if (term == 1) mma16816(acc[nt], ahi, bl[nt][0], bl[nt][1]);
+        else mma16816(acc[nt], ahi, bh[nt][0], bh[nt][1]);
+        if (SIDE && n % 3 == 2) to_bfrag_step(sx, sf, n / 3);
+      }
   }
 }
 
+__device__ __forceinline__ void mma_block(float (&acc)[4][4], const u16* xh, const BFrag& f, int lane) {
+  BFrag unused;
+  mma_block_side<false>(acc, xh, f, lane, acc, unused);
+}
+
 // One site of one pair (warp). rbuf: row-sample C operands; cbuf: column-sample B^T
-// operands. E is replaced by diag(acc_0, acc_1). Two schedules of the same MMAs:
-//   IL = false: per (t, s) step 1, conversion of G, step 2 (fewest live registers);
-//   IL = true:  per t both step-1 products (s = 0, 1) back to back, so converting one G into
-//               B-operand words overlaps the other's MMAs, and the first step-2 product
-//               overlaps the second conversion.
-// Every accumulator receives its MMAs in the same order in both (acc_s: t = 0, then t = 1),
-// so the result does not depend on the schedule.
-template <bool IL>
+// operands. E is replaced by diag(acc_0, acc_1). Schedules of the same MMAs and conversions:
+//   SCHED 0: per (t, s) step 1, conversion of G, step 2 (fewest live registers);
+//   SCHED 1: per t both step-1 products (s = 0, 1) back to back, then per s the conversion of
+//            G_s and step 2;
+//   SCHED 2: as 1, with every conversion that has an independent MMA block beside it spread
+//            over that block's MMAs (E_1 over the first step-1 block, G_0 over the second,
+//            G_1 over the first step-2 block); only E_0's conversion runs on its own.
+// Every accumulator receives its MMAs in the same order in all three (acc_s: t = 0, then
+// t = 1) and every conversion is the same split2, so the result does not depend on the schedule.
+template <int SCHED>
 __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* cbuf, int lane) {
   float acc[2][4][4];
 #pragma unroll
@@ -171,31 +199,7 @@ __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* c
     for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[s][nt][c] = 0.0f;
-  if (IL) {
-    BFrag fe[2];
-    to_bfrag(E.v[0], fe[0]);  // B operands of E_t^T
-    to_bfrag(E.v[1], fe[1]);
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      // step 1: G_s^T = B_{s,t}^T . E_t^T for s = 0, 1
-      float g[2][4][4];
-#pragma unroll
-      for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) g[s][nt][c] = 0.0f;
-      mma_block(g[0], cbuf + (0 * 2 + t) * 2 * COP, fe[t], lane);
-      mma_block(g[1], cbuf + (1 * 2 + t) * 2 * COP, fe[t], lane);
-      // step 2: acc_s += C_{s,t} . G_s (B operand of G_s from G_s^T's accumulators)
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        BFrag fg;
-        to_bfrag(g[s], fg);
-        mma_block(acc[s], rbuf + (s * 2 + t) * 2 * COP, fg, lane);
-      }
-    }
-  } else {
+  if (SCHED == 0) {
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       BFrag fe;
@@ -212,6 +216,31 @@ __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* c
         to_bfrag(g, fg);
         mma_block(acc[s], rbuf + (s * 2 + t) * 2 * COP, fg, lane);
       }
+    }
+  } else {
+    constexpr bool SIDE = SCHED == 2;
+    BFrag fe[2];
+    to_bfrag(E.v[0], fe[0]);  // B operands of E_t^T
+    if (!SIDE) to_bfrag(E.v[1], fe[1]);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      // step 1: G_s^T = B_{s,t}^T . E_t^T for s = 0, 1
+      float g[2][4][4];
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) g[s][nt][c] = 0.0f;
+      BFrag fg[2];
+      if (t == 0) mma_block_side<SIDE>(g[0], cbuf + (0 * 2 + t) * 2 * COP, fe[t], lane, E.v[1], fe[1]);
+      else mma_block(g[0], cbuf + (0 * 2 + t) * 2 * COP, fe[t], lane);
+      mma_block_side<SIDE>(g[1], cbuf + (1 * 2 + t) * 2 * COP, fe[t], lane, g[0], fg[0]);
+      // step 2: acc_s += C_{s,t} . G_s (B operand of G_s from G_s^T's accumulators)
+      if (!SIDE) to_bfrag(g[0], fg[0]);
+      mma_block_side<SIDE>(acc[0], rbuf + (0 * 2 + t) * 2 * COP, fg[0], lane, g[1], fg[1]);
+      if (!SIDE) to_bfrag(g[1], fg[1]);
+      mma_block(acc[1], rbuf + (1 * 2 + t) * 2 * COP, fg[1], lane);
     }
   }
 #pragma unroll
@@ -266,7 +295,7 @@ __device__ __forceinline__ float half_log_mod(const Frag& E, int e2) {
 // stages; a stage holds one site of the tile's TR row samples (C operands) and TC column
 // samples (B^T operands).
 constexpr int NPROD = 4;
-template <int TR, int TC, int NSTG, int BATCH_, bool IL_>
+template <int TR, int TC, int NSTG, int BATCH_, int SCHED_>
 struct CfgTc {
   static constexpr int TR_ = TR, TC_ = TC, NSTG_ = NSTG;
   static constexpr int NW = TR * TC;               // pair warps
@@ -277,7 +306,7 @@ struct CfgTc {
   static_assert(CH % PT == 0, "whole chunks per staging thread");
   static constexpr int PER_THREAD = CH / PT;
   static constexpr int BATCH = BATCH_;             // loads in flight per staging thread
-  static constexpr bool IL = IL_;
+  static constexpr int SCHED = SCHED_;
   static_assert(PER_THREAD % BATCH == 0, "whole batches");
   static constexpr size_t BAR_OFF = size_t(NSTG) * STAGE * sizeof(u16);
   static constexpr size_t SMEM = BAR_OFF + 2 * NSTG * sizeof(uint64_t) + 16;
@@ -383,7 +412,7 @@ __global__ void __launch_bounds__(C::NT, 1)
           break;
         }
         const u16* cur = smu + s * C::STAGE;
-        pair_site<C::IL>(E, cur + wr * SBUF, cur + (TR + wc) * SBUF, lane);
+        pair_site<C::SCHED>(E, cur + wr * SBUF, cur + (TR + wc) * SBUF, lane);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         if (k == p.n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1)) e2 += renorm(E);
@@ -424,7 +453,7 @@ __global__ void __launch_bounds__(32) self_overlap32_tc_kernel(const float* __re
       put_chunk<false>(cbuf, w, v);
     }
     __syncwarp();
-    pair_site<false>(E, rbuf, cbuf, lane);
+    pair_site<0>(E, rbuf, cbuf, lane);
     if (k == n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1)) e2 += renorm(E);
     __syncwarp();
   }
@@ -435,9 +464,10 @@ __global__ void __launch_bounds__(32) self_overlap32_tc_kernel(const float* __re
 
 dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
                            cudaStream_t st) {
-  // 4 x 2 pairs per CTA, three stages, 12 loads in flight per staging thread, interleaved
-  // step-1 products (measured fastest of the tile shapes and schedules that fit 168 registers)
-  using C = tc32::CfgTc<4, 2, 3, 12, true>;
+  // 4 x 2 pairs per CTA, three stages, 12 loads in flight per staging thread, schedule 2
+  // (measured fastest of the tile shapes and schedules that fit the 168 registers of a
+  // 384-thread CTA; 4 x 3 tiles spill at 128)
+  using C = tc32::CfgTc<4, 2, 3, 12, 2>;
   a.ntiles = count_tiles(a, C::TR_, C::TC_);
   auto kern = tc32::gram32_tc_kernel<C>;
   // set before every launch: the attribute is per device and cheap to set
