@@ -295,7 +295,7 @@ __device__ __forceinline__ float half_log_mod(const Frag& E, int e2) {
 // stages; a stage holds one site of the tile's TR row samples (C operands) and TC column
 // samples (B^T operands).
 constexpr int NPROD = 4;
-template <int TR, int TC, int NSTG, int BATCH_, int SCHED_>
+template <int TR, int TC, int NSTG, int SCHED_>
 struct CfgTc {
   static constexpr int TR_ = TR, TC_ = TC, NSTG_ = NSTG;
   static constexpr int NW = TR * TC;               // pair warps
@@ -305,16 +305,14 @@ struct CfgTc {
   static constexpr int CH = (TR + TC) * CHUNKS;    // 16-byte chunks of a stage's site tensors
   static_assert(CH % PT == 0, "whole chunks per staging thread");
   static constexpr int PER_THREAD = CH / PT;
-  static constexpr int BATCH = BATCH_;             // loads in flight per staging thread
   static constexpr int SCHED = SCHED_;
-  static_assert(PER_THREAD % BATCH == 0, "whole batches");
   static constexpr size_t BAR_OFF = size_t(NSTG) * STAGE * sizeof(u16);
   static constexpr size_t SMEM = BAR_OFF + 2 * NSTG * sizeof(uint64_t) + 16;
 };
 
 // Warp roles. Staging warps: for every (tile, site) of the CTA, in order, wait until the ring
 // slot is free (empty barrier: one arrival per pair warp), read the site tensors of the
-// tile's samples from HBM (16-byte chunks, BATCH loads in flight per thread), split them into
+// tile's samples from HBM (16-byte chunks, one site ahead in registers), split them into
 // BF16 hi / lo operands in shared memory and arrive on the slot's full barrier (one arrival
 // per staging thread, which releases its stores). Pair warps: wait for the slot, run one site
 // of their pair, release the slot. Every wait is bounded; on a timeout the CTA records
@@ -353,44 +351,63 @@ __global__ void __launch_bounds__(C::NT, 1)
 
   if (warp >= C::NW) {
     // ---- staging ----
+    // Each thread owns chunks pt + q * PT (q < PER_THREAD) of every stage and keeps the next
+    // site's copies of them in registers: while it converts chunk q of site g it loads chunk q
+    // of site g + 1 into the register just freed, so every load has a whole conversion pass to
+    // arrive.
     const int pt = threadIdx.x - C::NW * 32;
-    long long g = 0;  // stage fills issued
-    bool stop = false;
-    for (int lt = 0; lt < my_tiles && !stop; ++lt) {
-      int r0, c0;
-      tile_origin(lt, r0, c0);
-      for (int k = 0; k < p.n; ++k, ++g) {
-        const int s = int(g % NSTG);
-        const long long use = g / NSTG;
-        if (*abort_flag || (use > 0 && !mbar_wait_bounded(&empty[s], u32((use - 1) & 1)))) {
-          give_up();
-          stop = true;
-          break;
-        }
-        u16* st = smu + s * C::STAGE;
+    const long long total = (long long)my_tiles * p.n;
+    // chunk pt + q PT of a stage is chunk w[q % QS] of sample q / QS (QS = CHUNKS / PT)
+    constexpr int QS = CHUNKS / C::PT;
+    static_assert(CHUNKS % C::PT == 0, "a staging thread's chunks of a sample are the same for every sample");
+    int w4[QS];
 #pragma unroll
-        for (int b0 = 0; b0 < C::PER_THREAD; b0 += C::BATCH) {
-          float4 v[C::BATCH];
+    for (int u = 0; u < QS; ++u) w4[u] = 4 * chunk_of(pt + u * C::PT);
+    const float* base[TR + TC];  // the samples of the site being loaded
+    auto bases = [&](int k, int r0, int c0) {
 #pragma unroll
-          for (int q = 0; q < C::BATCH; ++q) {
-            const int ch = pt + (b0 + q) * C::PT;
-            const int smp = ch / CHUNKS, w = chunk_of(ch % CHUNKS);
-            const bool is_row = smp < TR;
-            const int idx = is_row ? min(r0 + smp, m_r - 1) : min(c0 + smp - TR, m_c - 1);
-            const float* src = (is_row ? mps_r + (size_t(k) * m_r + idx) * SAMPLE_FLOATS
-                                       : mps_c + (size_t(k) * m_c + idx) * SAMPLE_FLOATS) + w * 4;
-            v[q] = __ldg(reinterpret_cast<const float4*>(src));
-          }
+      for (int smp = 0; smp < TR + TC; ++smp)
+        base[smp] = smp < TR ? mps_r + (size_t(k) * m_r + min(r0 + smp, m_r - 1)) * SAMPLE_FLOATS
+                             : mps_c + (size_t(k) * m_c + min(c0 + smp - TR, m_c - 1)) * SAMPLE_FLOATS;
+    };
+    auto load = [&](int q) { return __ldg(reinterpret_cast<const float4*>(base[q / QS] + w4[q % QS])); };
+    float4 v[C::PER_THREAD];
+    int lt = 0, k = 0, r0 = 0, c0 = 0;  // the site whose chunks v holds
+    if (total > 0) {
+      tile_origin(0, r0, c0);
+      bases(0, r0, c0);
 #pragma unroll
-          for (int q = 0; q < C::BATCH; ++q) {
-            const int ch = pt + (b0 + q) * C::PT;
-            const int smp = ch / CHUNKS, w = chunk_of(ch % CHUNKS);
-            if (smp < TR) put_chunk<true>(st + smp * SBUF, w, v[q]);
-            else put_chunk<false>(st + smp * SBUF, w, v[q]);
-          }
-        }
-        mbar_arrive(&full[s]);
+      for (int q = 0; q < C::PER_THREAD; ++q) v[q] = load(q);
+    }
+    for (long long g = 0; g < total; ++g) {
+      int nlt = lt, nk = k + 1, nr0 = r0, nc0 = c0;
+      const bool more = g + 1 < total;
+      if (nk == p.n) {
+        nk = 0;
+        ++nlt;
+        if (more) tile_origin(nlt, nr0, nc0);
       }
+      const int s = int(g % NSTG);
+      const long long use = g / NSTG;
+      if (*abort_flag || (use > 0 && !mbar_wait_bounded(&empty[s], u32((use - 1) & 1)))) {
+        give_up();
+        break;
+      }
+      u16* st = smu + s * C::STAGE;
+      if (more) bases(nk, nr0, nc0);
+#pragma unroll
+      for (int q = 0; q < C::PER_THREAD; ++q) {
+        const float4 x = v[q];
+        if (more) v[q] = load(q);
+        const int smp = q / QS, w = w4[q % QS] >> 2;
+        if (smp < TR) put_chunk<true>(st + smp * SBUF, w, x);
+        else put_chunk<false>(st + smp * SBUF, w, x);
+      }
+      mbar_arrive(&full[s]);
+      lt = nlt;
+      k = nk;
+      r0 = nr0;
+      c0 = nc0;
     }
   } else {
     // ---- pair warps ----
@@ -464,10 +481,9 @@ __global__ void __launch_bounds__(32) self_overlap32_tc_kernel(const float* __re
 
 dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
                            cudaStream_t st) {
-  // 4 x 2 pairs per CTA, three stages, 12 loads in flight per staging thread, schedule 2
-  // (measured fastest of the tile shapes and schedules that fit the 168 registers of a
-  // 384-thread CTA; 4 x 3 tiles spill at 128)
-  using C = tc32::CfgTc<4, 2, 3, 12, 2>;
+  // 4 x 2 pairs per CTA, three stages, schedule 2 (measured fastest of the tile shapes and
+  // schedules that fit the 168 registers of a 384-thread CTA; 4 x 3 tiles spill at 128)
+  using C = tc32::CfgTc<4, 2, 3, 2>;
   a.ntiles = count_tiles(a, C::TR_, C::TC_);
   auto kern = tc32::gram32_tc_kernel<C>;
   // set before every launch: the attribute is per device and cheap to set
