@@ -62,13 +62,17 @@ typedef enum {
   DK_ERR_NO_DEVICE = 6     /* no usable sm_100-family device */
 } dk_status;
 
-typedef enum { DK_C64 = 0, DK_C128 = 1 } dk_dtype;
+/* Buffer formats of an MPS. DK_C64 / DK_C128: the site tensors (layout above) in complex64 /
+ * complex128. DK_SPLIT_BF16: the split-BF16 tensor-core operands of a bond-32 complex64 MPS,
+ * written by dk_mps_split32 and read by the DK_PREC_BF16X3 Gram calls (layout there). */
+typedef enum { DK_C64 = 0, DK_C128 = 1, DK_SPLIT_BF16 = 2 } dk_dtype;
 
 /* Arithmetic of the transfer contraction. F32: complex64 tensors, FP32 FMA on CUDA
  * cores (chi_max 4, 8, 32). F64: complex128 tensors, FP64 (chi_max 4). BF16X3: complex64
  * tensors at chi_max 32 on tensor cores, each FP32 operand split into two BF16 halves
  * (hi + lo) and each product formed as hi.hi + hi.lo + lo.hi with FP32 accumulation
- * (about 16 significant bits per product). */
+ * (about 16 significant bits per product); the Gram calls also take the operands already
+ * split (dtype DK_SPLIT_BF16, dk_mps_split32), which is the faster form. */
 typedef enum {
   DK_PREC_F32 = 0,
   DK_PREC_F64 = 1,
@@ -127,8 +131,28 @@ dk_status dk_sync_status(dk_ctx* ctx, void* stream);
  * Errors: DK_ERR_ARG for NULL ctx or limit_ns outside 1 .. 2e9; DK_ERR_CUDA. */
 dk_status dk_selftest_wait_timeout(dk_ctx* ctx, unsigned long long limit_ns, void* stream);
 
-/* Bytes of an MPS buffer for m samples, n sites, padded bond chi_max. */
+/* Bytes of an MPS buffer for m samples, n sites, padded bond chi_max (DK_SPLIT_BF16:
+ * chi_max 32 only, 10240 bytes per sample and site; 0 for other bonds). */
 size_t dk_mps_bytes(int m, int n, int chi_max, dk_dtype dtype);
+
+/* Split-BF16 operands of a bond-32 complex64 MPS for the DK_PREC_BF16X3 Gram calls
+ * (§II-C, Eqs. 8-10 on tensor cores). For every site k and sample i the four 16 x 16
+ * blocks A_s[t] (s, t in {0, 1}) are written as the real operand X = [Re A^T | Im A^T]
+ * (16 rows of 32 values; row p holds Re A[l][p] for l < 16, then Im A[l][p]), each value v
+ * split into BF16 hi = round(v) and lo = round(v - hi), so that the Gram kernels copy them
+ * to shared memory as they are instead of splitting them again for every tile:
+ *   ops[((k*m + i)*4 + 2*s + t)*2 + plane][p][c],  plane 0 = hi, 1 = lo, p < 16, c < 40,
+ * BF16 values, c >= 32 zero (row padding that spreads the tensor-core operand reads over
+ * the shared-memory banks): 10240 bytes per sample and site, dk_mps_bytes(m, n, 32,
+ * DK_SPLIT_BF16) in all. The Gram calls take `ops` in place of the MPS with dtype
+ * DK_SPLIT_BF16, prec DK_PREC_BF16X3 and chi_max 32, and give bit for bit the results of
+ * the same call on the complex64 MPS; the self-norms (dk_self_overlap, prec BF16X3) and
+ * the refinement (dk_gram_refine) keep reading the complex64 MPS.
+ *   mps: device, dk_mps_build layout, complex64, chi_max 32, m samples, n sites;
+ *   ops: device, ops_bytes >= dk_mps_bytes(m, n, 32, DK_SPLIT_BF16), 16-byte aligned.
+ * Errors: DK_ERR_ARG (NULL or misaligned pointers, m or n < 1), DK_ERR_WORKSPACE (ops_bytes
+ *         too small), DK_ERR_CUDA. */
+dk_status dk_mps_split32(dk_ctx* ctx, const void* mps, int m, int n, void* ops, size_t ops_bytes, void* stream);
 
 /* Scratch bytes the build, Gram and rows calls (dk_mps_build, dk_gram_tile,
  * dk_dual_kernel_rows, dk_gram_sweep) need for (n, chi_max, dtype, prec): always 0. Every
@@ -237,7 +261,8 @@ typedef struct {
  *   kept (the oldest is destroyed); dk_destroy releases them. Needs a non-NULL stream.
  * Errors: DK_ERR_ARG (NULL ctx/items, n_items < 1, an item with NULL mps or log_norm, m or
  *         n < 1, no output, ld < m, tile_shape out of range; graph with the NULL stream),
- *         and those of dk_gram_tile; DK_ERR_CUDA if recording or instantiation fails. */
+ *         DK_ERR_UNSUPPORTED for dtype DK_SPLIT_BF16 (the refinement reads complex64 site
+ *         tensors), and those of dk_gram_tile; DK_ERR_CUDA if recording or instantiation fails. */
 dk_status dk_gram_sweep(dk_ctx* ctx, const dk_sweep_item* items, int n_items, int chi_max, dk_dtype dtype,
                         dk_precision prec, float w, int graph, void* ws, size_t ws_bytes, void* stream);
 
@@ -377,6 +402,9 @@ dk_status dk_self_overlap(dk_ctx* ctx, const void* mps, int m, int n, int chi_ma
  * unordered pair is then contracted once and written to both (i,j) and (j,i).
  *   x_rows / x_cols: the m_rows x n / m_cols x n features the MPS were built from;
  *   needed only when k_out or kc_out is requested.
+ * dtype DK_SPLIT_BF16 (prec DK_PREC_BF16X3, chi_max 32): mps_rows / mps_cols are the
+ * split operands dk_mps_split32 wrote from the MPS; log_norm_* still come from the MPS
+ * (dk_self_overlap with prec BF16X3).
  * Errors: DK_ERR_ARG (ranges outside the MPS, ld < ncols, bad symmetric request,
  *         NULL x when k/kc requested), DK_ERR_UNSUPPORTED (precision/dtype/chi). */
 dk_status dk_gram_tile(dk_ctx* ctx,

@@ -92,6 +92,7 @@ DK_API size_t dk_workspace_bytes(int n, int chi_max, dk_dtype dtype, dk_precisio
   const size_t none = ~size_t(0);
   if (n < 1) return none;
   if (dtype == DK_C128) return (chi_max == 4 && prec == DK_PREC_F64) ? 0 : none;
+  if (dtype == DK_SPLIT_BF16) return (chi_max == 32 && prec == DK_PREC_BF16X3) ? 0 : none;
   if (dtype != DK_C64) return none;
   if (prec == DK_PREC_F32) return (chi_max == 4 || chi_max == 8 || chi_max == 32) ? 0 : none;
   if (prec == DK_PREC_BF16X3) return chi_max == 32 ? 0 : none;

@@ -439,7 +439,9 @@ static dk_status gram_dispatch(dk_ctx* ctx, const void* mps_r, int m_r, const vo
   }
   if (dtype == DK_C64 && prec == DK_PREC_F32 && chi == 32) return gram32_launch(ctx, mps_r, m_r, mps_c, m_c, a, st);
   if (dtype == DK_C64 && prec == DK_PREC_BF16X3 && chi == 32)
-    return gram32_tc_launch(ctx, mps_r, m_r, mps_c, m_c, a, st);
+    return gram32_tc_launch(ctx, mps_r, m_r, mps_c, m_c, a, false, st);
+  if (dtype == DK_SPLIT_BF16 && prec == DK_PREC_BF16X3 && chi == 32)
+    return gram32_tc_launch(ctx, mps_r, m_r, mps_c, m_c, a, true, st);
   return DK_ERR_UNSUPPORTED;
 }
 

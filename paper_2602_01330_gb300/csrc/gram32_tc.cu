@@ -76,11 +76,11 @@ __device__ __forceinline__ void split2(float x, float y, u32& hi, u32& lo) {
 }
 constexpr u32 NEG2 = 0x80008000u;  // flips the sign of both BF16 halves
 
-// Operand of block (s, t) of a sample: X[p][k] = Re A[k][p] (k < 16), sign Im A[k-16][p]
-// (k >= 16), A[a][p] the compact element (s, j = p, l = 16 t + a). CONJ (sign -1): the C
-// operand of a row sample (conjugate transpose); otherwise the B^T operand of a column
-// sample (transpose). A 16-byte chunk holds elements l, l+1 of compact row r = 16 s + p.
-template <bool CONJ>
+// Operand of block (s, t) of a sample: X[p][k] = Re A[k][p] (k < 16), Im A[k-16][p]
+// (k >= 16), A[a][p] the compact element (s, j = p, l = 16 t + a): the B^T operand of a
+// column sample (transpose) as it is, and the C operand of a row sample (conjugate transpose)
+// with its k >= 16 half negated, which mma_block applies to the other factor instead (CONJ).
+// A 16-byte chunk holds elements l, l+1 of compact row r = 16 s + p.
 __device__ __forceinline__ void put_chunk(u16* buf, int chunk, float4 v) {
   const int r = chunk >> 4, q = chunk & 15;
   const int s = r >> 4, p = r & 15;
@@ -92,9 +92,8 @@ __device__ __forceinline__ void put_chunk(u16* buf, int chunk, float4 v) {
   *reinterpret_cast<u32*>(hi + p * ROW + a) = h;
   *reinterpret_cast<u32*>(lo + p * ROW + a) = w;
   split2(v.y, v.w, h, w);  // Im at a, a+1
-  const u32 sg = CONJ ? NEG2 : 0u;
-  *reinterpret_cast<u32*>(hi + p * ROW + 16 + a) = h ^ sg;
-  *reinterpret_cast<u32*>(lo + p * ROW + 16 + a) = w ^ sg;
+  *reinterpret_cast<u32*>(hi + p * ROW + 16 + a) = h;
+  *reinterpret_cast<u32*>(lo + p * ROW + 16 + a) = w;
 }
 
 // Thread u (0..511 over a sample's chunks) -> chunk 16 r + q, r = 16 s + p, q = 8 t + q'.
@@ -139,11 +138,13 @@ __device__ __forceinline__ void to_bfrag_step(const float (&x)[4][4], BFrag& f, 
 
 // acc += [Xr | Xi] . [[Yr, Yi], [-Yi, Yr]] for X (16 x 16 complex) from shared memory
 // (xh: hi operand, lo operand COP further) and Y given by f (Y = the transpose of the matrix
-// whose accumulators made f). k-step kk = 0 takes the rows [Yr | Yi], kk = 1 [-Yi | Yr]; the
-// MMAs are issued term-major over the four independent n-tile accumulators. With SIDE, the
-// conversion sf = to_bfrag(sx) of an independent matrix is spread over the block, one split2
-// after every third MMA, so that the warp issues it between MMAs instead of in a burst of its own.
-template <bool SIDE>
+// whose accumulators made f). k-step kk = 0 takes the rows [Yr | Yi], kk = 1 [-Yi | Yr]; with
+// CONJ, X is used as [Xr | -Xi] (the conjugate of the stored matrix) by negating the kk = 1
+// rows instead, [Yi | -Yr]: the same products, so the same sums. The MMAs are issued
+// term-major over the four independent n-tile accumulators. With SIDE, the conversion
+// sf = to_bfrag(sx) of an independent matrix is spread over the block, one split2 after every
+// third MMA, so that the warp issues it between MMAs instead of in a burst of its own.
+template <bool CONJ, bool SIDE>
 __device__ __forceinline__ void mma_block_side(float (&acc)[4][4], const u16* xh, const BFrag& f, int lane,
                                                const float (&sx)[4][4], BFrag& sf) {
   int n = 0;
@@ -157,7 +158,7 @@ __device__ __forceinline__ void mma_block_side(float (&acc)[4][4], const u16* xh
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
       const int c = (nt >> 1) ^ kk, h = nt & 1;
-      const u32 sg = (kk == 1 && nt < 2) ? NEG2 : 0u;
+      const u32 sg = (kk == 1 && ((nt < 2) != CONJ)) ? NEG2 : 0u;
       bh[nt][0] = f.hi[c][h][0] ^ sg;
       bh[nt][1] = f.hi[c][h][1] ^ sg;
       bl[nt][0] = f.lo[c][h][0] ^ sg;
@@ -175,9 +176,10 @@ __device__ __forceinline__ void mma_block_side(float (&acc)[4][4], const u16* xh
   }
 }
 
+template <bool CONJ>
 __device__ __forceinline__ void mma_block(float (&acc)[4][4], const u16* xh, const BFrag& f, int lane) {
   BFrag unused;
-  mma_block_side<false>(acc, xh, f, lane, acc, unused);
+  mma_block_side<CONJ, false>(acc, xh, f, lane, acc, unused);
 }
 
 // One site of one pair (warp). rbuf: row-sample C operands; cbuf: column-sample B^T
@@ -211,10 +213,10 @@ __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* c
         for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
           for (int c = 0; c < 4; ++c) g[nt][c] = 0.0f;
-        mma_block(g, cbuf + (s * 2 + t) * 2 * COP, fe, lane);
+        mma_block<false>(g, cbuf + (s * 2 + t) * 2 * COP, fe, lane);
         BFrag fg;
         to_bfrag(g, fg);
-        mma_block(acc[s], rbuf + (s * 2 + t) * 2 * COP, fg, lane);
+        mma_block<true>(acc[s], rbuf + (s * 2 + t) * 2 * COP, fg, lane);
       }
     }
   } else {
@@ -233,14 +235,14 @@ __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* c
 #pragma unroll
           for (int c = 0; c < 4; ++c) g[s][nt][c] = 0.0f;
       BFrag fg[2];
-      if (t == 0) mma_block_side<SIDE>(g[0], cbuf + (0 * 2 + t) * 2 * COP, fe[t], lane, E.v[1], fe[1]);
-      else mma_block(g[0], cbuf + (0 * 2 + t) * 2 * COP, fe[t], lane);
-      mma_block_side<SIDE>(g[1], cbuf + (1 * 2 + t) * 2 * COP, fe[t], lane, g[0], fg[0]);
+      if (t == 0) mma_block_side<false, SIDE>(g[0], cbuf + (0 * 2 + t) * 2 * COP, fe[t], lane, E.v[1], fe[1]);
+      else mma_block<false>(g[0], cbuf + (0 * 2 + t) * 2 * COP, fe[t], lane);
+      mma_block_side<false, SIDE>(g[1], cbuf + (1 * 2 + t) * 2 * COP, fe[t], lane, g[0], fg[0]);
       // step 2: acc_s += C_{s,t} . G_s (B operand of G_s from G_s^T's accumulators)
       if (!SIDE) to_bfrag(g[0], fg[0]);
-      mma_block_side<SIDE>(acc[0], rbuf + (0 * 2 + t) * 2 * COP, fg[0], lane, g[1], fg[1]);
+      mma_block_side<true, SIDE>(acc[0], rbuf + (0 * 2 + t) * 2 * COP, fg[0], lane, g[1], fg[1]);
       if (!SIDE) to_bfrag(g[1], fg[1]);
-      mma_block(acc[1], rbuf + (1 * 2 + t) * 2 * COP, fg[1], lane);
+      mma_block<true>(acc[1], rbuf + (1 * 2 + t) * 2 * COP, fg[1], lane);
     }
   }
 #pragma unroll
@@ -294,29 +296,33 @@ __device__ __forceinline__ float half_log_mod(const Frag& E, int e2) {
 // CTA of TR x TC pair warps (one pair each) and NPROD staging warps over a ring of NSTG
 // stages; a stage holds one site of the tile's TR row samples (C operands) and TC column
 // samples (B^T operands).
-constexpr int NPROD = 4;
-template <int TR, int TC, int NSTG, int SCHED_>
+template <int TR, int TC, int NSTG, int SCHED_, bool PRESPLIT_>
 struct CfgTc {
   static constexpr int TR_ = TR, TC_ = TC, NSTG_ = NSTG;
+  static constexpr bool PRESPLIT = PRESPLIT_;      // operands from dk_mps_split32: copied, not split
   static constexpr int NW = TR * TC;               // pair warps
-  static constexpr int PT = NPROD * 32;            // staging threads
+  static constexpr int PT = (PRESPLIT ? 1 : 4) * 32;  // staging threads (presplit: one copy warp)
   static constexpr int NT = NW * 32 + PT;
   static constexpr int STAGE = (TR + TC) * SBUF;   // u16 per stage
   static constexpr int CH = (TR + TC) * CHUNKS;    // 16-byte chunks of a stage's site tensors
-  static_assert(CH % PT == 0, "whole chunks per staging thread");
+  static_assert(PRESPLIT || CH % PT == 0, "whole chunks per staging thread");
   static constexpr int PER_THREAD = CH / PT;
   static constexpr int SCHED = SCHED_;
+  static constexpr u32 OPS_BYTES = SBUF * sizeof(u16);  // one sample-site of dk_mps_split32 operands
   static constexpr size_t BAR_OFF = size_t(NSTG) * STAGE * sizeof(u16);
   static constexpr size_t SMEM = BAR_OFF + 2 * NSTG * sizeof(uint64_t) + 16;
 };
 
-// Warp roles. Staging warps: for every (tile, site) of the CTA, in order, wait until the ring
-// slot is free (empty barrier: one arrival per pair warp), read the site tensors of the
-// tile's samples from HBM (16-byte chunks, one site ahead in registers), split them into
-// BF16 hi / lo operands in shared memory and arrive on the slot's full barrier (one arrival
-// per staging thread, which releases its stores). Pair warps: wait for the slot, run one site
-// of their pair, release the slot. Every wait is bounded; on a timeout the CTA records
-// DEV_TIMEOUT in the status word, raises its abort flag and every role leaves its loop.
+// Warp roles. Staging warps (complex64 input): for every (tile, site) of the CTA, in order,
+// wait until the ring slot is free (empty barrier: one arrival per pair warp), read the site
+// tensors of the tile's samples from HBM (16-byte chunks, one site ahead in registers), split
+// them into BF16 hi / lo operands in shared memory and arrive on the slot's full barrier (one
+// arrival per staging thread, which releases its stores). Copy warp (PRESPLIT, operands from
+// dk_mps_split32): one thread waits for the slot and fills it with one 10 KB bulk copy per
+// sample, the slot's full barrier counting the bytes. Pair warps: wait for the slot, run one
+// site of their pair, release the slot. Every wait is bounded; on a timeout the CTA records
+// DEV_TIMEOUT in the status word, raises its abort flag and every role leaves its loop, the
+// copy thread after waiting for its copies in flight.
 template <class C>
 __global__ void __launch_bounds__(C::NT, 1)
     gram32_tc_kernel(const float* __restrict__ mps_r, int m_r, const float* __restrict__ mps_c, int m_c,
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(C::NT, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTG; ++s) {
-      mbar_init(&full[s], C::PT);
+      mbar_init(&full[s], C::PRESPLIT ? 1 : C::PT);
       mbar_init(&empty[s], C::NW);
     }
     *abort_flag = 0;
@@ -349,7 +355,42 @@ __global__ void __launch_bounds__(C::NT, 1)
     *abort_flag = 1;
   };
 
-  if (warp >= C::NW) {
+  if (warp >= C::NW && C::PRESPLIT) {
+    // ---- copy warp: one thread moves each sample's split operands with one bulk copy ----
+    if (lane == 0) {
+      const uint8_t* ops_r = reinterpret_cast<const uint8_t*>(mps_r);
+      const uint8_t* ops_c = reinterpret_cast<const uint8_t*>(mps_c);
+      const long long total = (long long)my_tiles * p.n;
+      long long g = 0;  // stage fills issued
+      int lt = 0, k = 0, r0 = 0, c0 = 0;
+      if (total > 0) tile_origin(0, r0, c0);
+      for (; g < total; ++g) {
+        const int s = int(g % NSTG);
+        const long long use = g / NSTG;
+        if (*abort_flag || (use > 0 && !mbar_wait_bounded(&empty[s], u32((use - 1) & 1)))) {
+          give_up();
+          break;
+        }
+        u16* st = smu + s * C::STAGE;
+        mbar_arrive_expect_tx(&full[s], u32(TR + TC) * C::OPS_BYTES);
+#pragma unroll 1
+        for (int smp = 0; smp < TR + TC; ++smp) {
+          const uint8_t* src = smp < TR ? ops_r + (size_t(k) * m_r + min(r0 + smp, m_r - 1)) * C::OPS_BYTES
+                                        : ops_c + (size_t(k) * m_c + min(c0 + smp - TR, m_c - 1)) * C::OPS_BYTES;
+          bulk_load(st + smp * SBUF, src, C::OPS_BYTES, &full[s]);
+        }
+        if (++k == p.n) {
+          k = 0;
+          ++lt;
+          if (g + 1 < total) tile_origin(lt, r0, c0);
+        }
+      }
+      // the copies of the last fills of every slot land before the CTA exits (each is the
+      // slot's newest phase, so its parity cannot alias)
+      for (long long q = g - 1; q >= 0 && q >= g - NSTG; --q)
+        if (!mbar_wait_bounded(&full[int(q % NSTG)], u32((q / NSTG) & 1))) record_status(p.status, DEV_TIMEOUT);
+    }
+  } else if (warp >= C::NW) {
     // ---- staging ----
     // Each thread owns chunks pt + q * PT (q < PER_THREAD) of every stage and keeps the next
     // site's copies of them in registers: while it converts chunk q of site g it loads chunk q
@@ -400,8 +441,7 @@ __global__ void __launch_bounds__(C::NT, 1)
         const float4 x = v[q];
         if (more) v[q] = load(q);
         const int smp = q / QS, w = w4[q % QS] >> 2;
-        if (smp < TR) put_chunk<true>(st + smp * SBUF, w, x);
-        else put_chunk<false>(st + smp * SBUF, w, x);
+        put_chunk(st + smp * SBUF, w, x);
       }
       mbar_arrive(&full[s]);
       lt = nlt;
@@ -454,9 +494,7 @@ __global__ void __launch_bounds__(C::NT, 1)
 // ln|<psi~_i|psi~_i>| with the same split-BF16 arithmetic (one warp per sample).
 __global__ void __launch_bounds__(32) self_overlap32_tc_kernel(const float* __restrict__ mps, int m, int n,
                                                                float* __restrict__ log_norm) {
-  extern __shared__ __align__(16) u16 smu[];
-  u16* rbuf = smu;
-  u16* cbuf = rbuf + SBUF;
+  extern __shared__ __align__(16) u16 smu[];  // the sample's operands, row and column side alike
   const int lane = threadIdx.x;
   const int i = blockIdx.x;
   Frag E;
@@ -466,24 +504,40 @@ __global__ void __launch_bounds__(32) self_overlap32_tc_kernel(const float* __re
     const float* src = mps + (size_t(k) * m + i) * SAMPLE_FLOATS;
     for (int w = lane; w < CHUNKS; w += 32) {
       const float4 v = __ldg(reinterpret_cast<const float4*>(src) + w);
-      put_chunk<true>(rbuf, w, v);
-      put_chunk<false>(cbuf, w, v);
+      put_chunk(smu, w, v);
     }
     __syncwarp();
-    pair_site<0>(E, rbuf, cbuf, lane);
+    pair_site<0>(E, smu, smu, lane);
     if (k == n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1)) e2 += renorm(E);
     __syncwarp();
   }
   if (lane == 0) log_norm[i] = half_log_mod(E, e2);
 }
 
+// dk_mps_split32: the operands of sample-site u = k m + i (u < m n), one CTA of 128 threads
+// per sample-site at a time (grid-stride): the 512 chunks split into a shared-memory copy
+// of the operand layout with zeroed row padding, then written out in 16-byte pieces.
+__global__ void __launch_bounds__(128) split32_kernel(const float* __restrict__ mps, long long units,
+                                                      uint4* __restrict__ ops) {
+  __shared__ __align__(16) u16 buf[SBUF];
+  constexpr int PIECES = SBUF * int(sizeof(u16)) / 16;
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    for (int r = threadIdx.x; r < SBUF / ROW; r += blockDim.x)  // padding of every operand row
+      *reinterpret_cast<uint4*>(buf + r * ROW + 32) = make_uint4(0u, 0u, 0u, 0u);
+    const float4* src = reinterpret_cast<const float4*>(mps + size_t(u) * SAMPLE_FLOATS);
+    for (int w = threadIdx.x; w < CHUNKS; w += blockDim.x) put_chunk(buf, w, __ldg(src + w));
+    __syncthreads();
+    const uint4* b4 = reinterpret_cast<const uint4*>(buf);
+    for (int q = threadIdx.x; q < PIECES; q += blockDim.x) ops[size_t(u) * PIECES + q] = b4[q];
+    __syncthreads();
+  }
+}
+
 }  // namespace tc32
 
-dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
-                           cudaStream_t st) {
-  // 4 x 2 pairs per CTA, three stages, schedule 2 (measured fastest of the tile shapes and
-  // schedules that fit the 168 registers of a 384-thread CTA; 4 x 3 tiles spill at 128)
-  using C = tc32::CfgTc<4, 2, 3, 2>;
+template <class C>
+static dk_status gram32_tc_run(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
+                               cudaStream_t st) {
   a.ntiles = count_tiles(a, C::TR_, C::TC_);
   auto kern = tc32::gram32_tc_kernel<C>;
   // set before every launch: the attribute is per device and cheap to set
@@ -498,8 +552,16 @@ dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* 
   return launch_status();
 }
 
+dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
+                           bool presplit, cudaStream_t st) {
+  // 4 x 2 pairs per CTA, three stages, schedule 2 (measured fastest of the tile shapes and
+  // schedules that fit the 168 registers of a 384-thread CTA; 4 x 3 tiles spill at 128)
+  if (presplit) return gram32_tc_run<tc32::CfgTc<4, 2, 3, 2, true>>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+  return gram32_tc_run<tc32::CfgTc<4, 2, 3, 2, false>>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+}
+
 dk_status self_overlap32_tc_launch(const void* mps, int m, int n, float* log_norm, cudaStream_t st) {
-  const int smem = 2 * tc32::SBUF * 2;
+  const int smem = tc32::SBUF * 2;
   // set before every launch: the attribute is per device and cheap to set
   if (cudaFuncSetAttribute(tc32::self_overlap32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess)
@@ -509,3 +571,17 @@ dk_status self_overlap32_tc_launch(const void* mps, int m, int n, float* log_nor
 }
 
 }  // namespace dk
+
+DK_API dk_status dk_mps_split32(dk_ctx* ctx, const void* mps, int m, int n, void* ops, size_t ops_bytes,
+                                void* stream) {
+  using namespace dk;
+  if (!ctx || !mps || !ops || m < 1 || n < 1) return DK_ERR_ARG;
+  if (!aligned16(mps) || !aligned16(ops)) return DK_ERR_ARG;
+  if (ops_bytes < size_t(m) * size_t(n) * site_bytes(32, DK_SPLIT_BF16)) return DK_ERR_WORKSPACE;
+  const long long units = (long long)m * n;
+  long long grid = (long long)ctx->sm_count * 16;
+  if (grid > units) grid = units;
+  tc32::split32_kernel<<<int(grid), 128, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float*>(mps),
+                                                                                   units, static_cast<uint4*>(ops));
+  return launch_status();
+}

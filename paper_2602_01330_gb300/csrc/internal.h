@@ -30,6 +30,7 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 // Compact site tensor of one sample: chi^2 complex numbers (see include/dualk.h).
 inline size_t site_bytes(int chi_max, dk_dtype dtype) {
+  if (dtype == DK_SPLIT_BF16) return chi_max == 32 ? 10240 : 0;  // dk_mps_split32's operands
   return size_t(chi_max) * chi_max * (dtype == DK_C64 ? 8 : 16);
 }
 
@@ -44,8 +45,9 @@ dk_status gram32_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps
                         cudaStream_t st);
 dk_status self_overlap32_launch(const void* mps, int m, int n, float* log_norm, cudaStream_t st);
 // Bond-32 tensor-core kernels (gram32_tc.cu): split-BF16 Gram and self-overlap.
+// presplit: mps_r / mps_c hold dk_mps_split32 operands instead of complex64 site tensors
 dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
-                           cudaStream_t st);
+                           bool presplit, cudaStream_t st);
 dk_status self_overlap32_tc_launch(const void* mps, int m, int n, float* log_norm, cudaStream_t st);
 // Self-overlap normalisers of the chi_max 4 / 8 kernels (mps_build.cu).
 dk_status self_overlap_launch(const void* mps, int m, int n, int chi, dk_dtype dtype, float* log_norm,

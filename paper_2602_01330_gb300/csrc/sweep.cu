@@ -83,6 +83,7 @@ DK_API dk_status dk_gram_sweep(dk_ctx* ctx, const dk_sweep_item* items, int n_it
                                dk_precision prec, float w, int graph, void* ws, size_t ws_bytes, void* stream) {
   using namespace dk;
   if (!ctx || !items || n_items < 1) return DK_ERR_ARG;
+  if (dtype == DK_SPLIT_BF16) return DK_ERR_UNSUPPORTED;  // the refinement needs the complex64 tensors
   for (int t = 0; t < n_items; ++t) {
     const dk_sweep_item& it = items[t];
     if (!it.mps || !it.log_norm || it.m < 1 || it.n < 1) return DK_ERR_ARG;

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdualk.so")
 
 DK_OK = 0
-DK_C64, DK_C128 = 0, 1
+DK_C64, DK_C128, DK_SPLIT_BF16 = 0, 1, 2
 DK_PREC_F32, DK_PREC_F64, DK_PREC_BF16X3 = 0, 1, 2
 DK_BLOCK_TCGEN05, DK_BLOCK_MMA_SYNC = 0, 1
 
@@ -31,7 +31,7 @@ EXPORTED = ("dk_create", "dk_destroy", "dk_error_string", "dk_sync_status", "dk_
             "dk_pca_transform", "dk_pca_fit_noalloc", "dk_mps_build_blocks", "dk_block_states_bytes",
             "dk_block_states", "dk_gram_blocks", "dk_gram_sweep", "dk_workspace_bytes",
             "dk_set_block_gram_form", "dk_block_states_workspace_bytes", "dk_gram_blocks_workspace_bytes",
-            "dk_gram_refine", "dk_gram_refine_workspace_bytes", "dk_gram_blocks_refine")
+            "dk_gram_refine", "dk_gram_refine_workspace_bytes", "dk_gram_blocks_refine", "dk_mps_split32")
 # Entries with K_q above this are recomputed after every FP32 / split-BF16 Gram, rows and
 # block-Gram call of the binding (dk_gram_refine, dk_gram_blocks_refine; refine=None: not).
 REFINE_TAU = 0.02  # DK_REFINE_TAU
@@ -107,6 +107,8 @@ def _lib():
     lib.dk_gram_blocks_refine.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, f32, f32,
                                           f32, vp, vp, vp, vp, i64, i32, vp]
     lib.dk_gram_blocks_refine.restype = i32
+    lib.dk_mps_split32.argtypes = [vp, vp, i32, i32, vp, ctypes.c_size_t, vp]
+    lib.dk_mps_split32.restype = i32
     lib.dk_gram_refine_workspace_bytes.argtypes = [i32, i32]
     lib.dk_gram_refine_workspace_bytes.restype = ctypes.c_size_t
     lib.dk_gram_config_count.argtypes = [i32, i32]
@@ -197,6 +199,7 @@ class MPS:
     x: torch.Tensor           # float32 m x n features it was built from
     norms: dict | None = None  # precision -> log_norm computed with that arithmetic
     fmap: "FeatureMap | None" = None  # the feature map it was built with
+    split: torch.Tensor | None = None  # dk_mps_split32 operands (bond 32), made on first use
 
     def log_norm_for(self, ctx: "Context", prec: int, stream=None) -> torch.Tensor:
         """ln-norms matching the Gram precision `prec` (dk_self_overlap when not built in)."""
@@ -208,6 +211,19 @@ class MPS:
         if prec not in self.norms:
             self.norms[prec] = self_overlap(ctx, self, prec, stream=stream)
         return self.norms[prec]
+
+    def split_for(self, ctx: "Context", stream=None) -> torch.Tensor:
+        """The split-BF16 operands of this bond-32 complex64 MPS (dk_mps_split32), which the
+        BF16X3 Gram calls read instead of the site tensors; made once and kept."""
+        if self.chi_max != 32 or self.dtype != DK_C64:
+            raise ValueError("split operands exist for bond-32 complex64 MPS only")
+        if self.split is None:
+            nbytes = int(_lib().dk_mps_bytes(self.m, self.n, 32, DK_SPLIT_BF16))
+            split = torch.empty(nbytes, dtype=torch.uint8, device=self.data.device)
+            _check(_lib().dk_mps_split32(ctx.handle, _ptr(self.data), self.m, self.n, _ptr(split), nbytes,
+                                         _stream(stream)), "dk_mps_split32")
+            self.split = split
+        return self.split
 
     def complex_view(self):
         """[site][sample][s][j][l] view of the compact block layout (see include/dualk.h)."""
@@ -447,6 +463,14 @@ def _outs(shape, device, want):
             for k in ("k", "kq", "kc", "logkq")}
 
 
+def _gram_operands(ctx: "Context", mps: MPS, prec: int, stream=None):
+    """(buffer, dtype) a Gram call reads: the split operands for bond-32 split-BF16 Grams,
+    the site tensors otherwise."""
+    if prec == DK_PREC_BF16X3 and mps.chi_max == 32 and mps.dtype == DK_C64:
+        return mps.split_for(ctx, stream), DK_SPLIT_BF16
+    return mps.data, mps.dtype
+
+
 def gram_tile(ctx: Context, rows: MPS, cols: MPS, row0: int = 0, nrows: int | None = None,
               col0: int = 0, ncols: int | None = None, gamma: float | None = None, w: float = 0.5,
               want=("k", "kq", "kc", "logkq"), symmetric: bool = False, out=None, ld: int | None = None,
@@ -468,8 +492,10 @@ def gram_tile(ctx: Context, rows: MPS, cols: MPS, row0: int = 0, nrows: int | No
     prec = _default_prec(rows) if prec is None else prec
     ln_r = rows.log_norm_for(ctx, prec, stream)
     ln_c = ln_r if cols is rows else cols.log_norm_for(ctx, prec, stream)
-    _check(_lib().dk_gram_tile(ctx.handle, _ptr(rows.data), rows.m, _ptr(cols.data), cols.m, rows.n,
-                               rows.chi_max, rows.dtype, row0, nrows, col0, ncols, _ptr(ln_r),
+    buf_r, dt = _gram_operands(ctx, rows, prec, stream)
+    buf_c = buf_r if cols is rows else _gram_operands(ctx, cols, prec, stream)[0]
+    _check(_lib().dk_gram_tile(ctx.handle, _ptr(buf_r), rows.m, _ptr(buf_c), cols.m, rows.n,
+                               rows.chi_max, dt, row0, nrows, col0, ncols, _ptr(ln_r),
                                _ptr(ln_c), _ptr(rows.x), _ptr(cols.x), float(gamma), float(w), prec,
                                _ptr(out.get("k")), _ptr(out.get("kq")), _ptr(out.get("kc")),
                                _ptr(out.get("logkq")), int(ld), 1 if symmetric else 0, _stream(stream)),
@@ -501,9 +527,11 @@ def dual_kernel_rows(ctx: Context, test: MPS, train: MPS, gamma: float | None = 
     prec = _default_prec(train) if prec is None else prec
     ln_te = test.log_norm_for(ctx, prec, stream)
     ln_tr = train.log_norm_for(ctx, prec, stream)
-    _check(_lib().dk_dual_kernel_rows(ctx.handle, _ptr(test.data), _ptr(test.x), _ptr(ln_te), test.m,
-                                      _ptr(train.data), _ptr(train.x), _ptr(ln_tr), train.m, train.n,
-                                      train.chi_max, train.dtype, float(gamma), float(w), prec,
+    buf_te, dt = _gram_operands(ctx, test, prec, stream)
+    buf_tr = _gram_operands(ctx, train, prec, stream)[0]
+    _check(_lib().dk_dual_kernel_rows(ctx.handle, _ptr(buf_te), _ptr(test.x), _ptr(ln_te), test.m,
+                                      _ptr(buf_tr), _ptr(train.x), _ptr(ln_tr), train.m, train.n,
+                                      train.chi_max, dt, float(gamma), float(w), prec,
                                       _ptr(out.get("k")), _ptr(out.get("kq")), _ptr(out.get("kc")),
                                       _ptr(out.get("logkq")), _stream(stream)),
            "dk_dual_kernel_rows")

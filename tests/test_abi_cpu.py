@@ -17,7 +17,7 @@ HEADER = os.path.join(ROOT, "include", "dualk.h")
 def declared_symbols():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(dk_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(dk_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -61,12 +61,15 @@ def test_error_strings_and_host_validation(lib):
     assert lib.dk_mps_bytes(10, 7, 4, 0) == 10 * 7 * 4 * 4 * 8     # chi^2 complex64 per sample-site
     assert lib.dk_mps_bytes(10, 7, 8, 1) == 10 * 7 * 8 * 8 * 16
     assert lib.dk_mps_bytes(0, 7, 4, 0) == 0
+    # split-BF16 operands (DK_SPLIT_BF16 = 2): bond 32 only, 4 blocks x hi/lo x 16 rows of 40 BF16
+    assert lib.dk_mps_bytes(10, 7, 32, 2) == 10 * 7 * 4 * 2 * 16 * 40 * 2
+    assert lib.dk_mps_bytes(10, 7, 4, 2) == 0
     # no Gram-path call needs a workspace; unsupported combinations read as (size_t)-1
     lib.dk_workspace_bytes.restype = ctypes.c_size_t
     none = ctypes.c_size_t(-1).value
-    for chi, dt, prec in ((4, 0, 0), (8, 0, 0), (32, 0, 0), (32, 0, 2), (4, 1, 1)):
+    for chi, dt, prec in ((4, 0, 0), (8, 0, 0), (32, 0, 0), (32, 0, 2), (4, 1, 1), (32, 2, 2)):
         assert lib.dk_workspace_bytes(784, chi, dt, prec) == 0
-    for chi, dt, prec in ((16, 0, 0), (4, 0, 2), (8, 1, 1), (4, 1, 0), (32, 0, 1)):
+    for chi, dt, prec in ((16, 0, 0), (4, 0, 2), (8, 1, 1), (4, 1, 0), (32, 0, 1), (32, 2, 0), (8, 2, 2)):
         assert lib.dk_workspace_bytes(784, chi, dt, prec) == none
     assert lib.dk_workspace_bytes(0, 4, 0, 0) == none
     # block-state and PCA sizes
@@ -80,6 +83,7 @@ def test_error_strings_and_host_validation(lib):
                             ctypes.c_float(1.0), ctypes.c_float(0.5), 0, None, None, None, None,
                             ctypes.c_int64(1), 0, None) == 1
     assert lib.dk_set_block_gram_form(None, 0) == 1  # DK_BLOCK_TCGEN05 on no context
+    assert lib.dk_mps_split32(None, None, 1, 1, None, ctypes.c_size_t(0), None) == 1
 
 
 def test_create_without_device_reports_no_device(lib):
