@@ -554,9 +554,11 @@ static dk_status gram32_tc_run(dk_ctx* ctx, const void* mps_r, int m_r, const vo
 
 dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
                            bool presplit, cudaStream_t st) {
-  // 4 x 2 pairs per CTA, three stages, schedule 2 (measured fastest of the tile shapes and
-  // schedules that fit the 168 registers of a 384-thread CTA; 4 x 3 tiles spill at 128)
-  if (presplit) return gram32_tc_run<tc32::CfgTc<4, 2, 3, 2, true>>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+  // Measured fastest of the shapes and schedules that fit the registers (512 samples, d = 256):
+  // split operands: 4 x 4 pairs, two stages, schedule 0 (16 pair warps at 96 registers;
+  // 56.6 ms against 58.4 for 4 x 2); complex64 input: 4 x 2 pairs, three stages, schedule 2
+  // (the staging warps leave 168 registers for 8 pair warps; 4 x 3 tiles spill at 128).
+  if (presplit) return gram32_tc_run<tc32::CfgTc<4, 4, 2, 0, true>>(ctx, mps_r, m_r, mps_c, m_c, a, st);
   return gram32_tc_run<tc32::CfgTc<4, 2, 3, 2, false>>(ctx, mps_r, m_r, mps_c, m_c, a, st);
 }
 
