@@ -71,6 +71,11 @@ def compare(m: int = 512, d: int = 256, pool: int = 128, n_uniform: int = 40, n_
         mps = dualk.mps_build(ctx, xt, fm)
         out = {"kq": torch.empty((m, m), device="cuda")}
         for name, prec in precs:
+            split_ms = None
+            if prec == dualk.DK_PREC_BF16X3:  # the split operands, made once per MPS (not in the Gram time)
+                mps.log_norm_for(ctx, prec)
+                torch.cuda.synchronize()
+                split_ms = _event_ms(lambda: mps.split_for(ctx))
             ms = _time(lambda: dualk.gram_tile(ctx, mps, mps, symmetric=True, out=out, ld=m, w=1.0, prec=prec))
             kq = out["kq"].cpu().numpy().astype(np.float64)
             kq_block[(chi, name)] = kq
@@ -79,6 +84,8 @@ def compare(m: int = 512, d: int = 256, pool: int = 128, n_uniform: int = 40, n_
                 "gram_ms": ms, "entry_qubits_per_s": units / (ms / 1e3),
                 "tflops_block_count": workload.gram_entries(m) * workload.flops_per_pair(d, reps) / ms / 1e9,
             }
+            if split_ms is not None:
+                res[f"chi{chi}_{name}"]["split_operands_ms"] = split_ms
     diff = np.abs(kq_block[(32, "fp32")] - kq_block[(32, "bf16x3")])
     res["chi32_max_abs_dK_bf16x3_vs_fp32_block"] = float(diff.max())
     res["chi32_max_abs_dK_bf16x3_vs_fp32_sampled"] = float(max(diff[i, j] for i, j in pairs))
@@ -134,6 +141,9 @@ def sampled_pairs_full_size(pairs, near_base, m: int = 4000, d: int = 256, near_
             mp.log_norm_for(ctx, prec)
             mpn.log_norm_for(ctx, prec)
             torch.cuda.synchronize()
+            split_ms = None
+            if prec == dualk.DK_PREC_BF16X3:  # the split operands, made once per MPS
+                split_ms = _event_ms(lambda: (mp.split_for(ctx), mpn.split_for(ctx)))
             g_ms = _event_ms(lambda: dualk.gram_tile(ctx, mp, mp, symmetric=True, out=out, ld=m, w=1.0, prec=prec,
                                                      want=("kq", "logkq")))
             r_ms = _event_ms(lambda: dualk.dual_kernel_rows(ctx, mpn, mp, w=1.0, out=rows, prec=prec,
@@ -149,6 +159,8 @@ def sampled_pairs_full_size(pairs, near_base, m: int = 4000, d: int = 256, near_
                 "gram_ms": g_ms, "rows_ms": r_ms, "gram_entry_qubits_per_s": units / (g_ms / 1e3),
                 "gram_tflops_block_count": workload.gram_entries(m) * workload.flops_per_pair(d, reps) / g_ms / 1e9,
                 "kq": kq, "logkq": lkq}
+            if split_ms is not None:
+                res[f"chi{chi}_{name}"]["split_operands_ms"] = split_ms
         del mp, mpn
     ctx.sync_status()
     if own:
