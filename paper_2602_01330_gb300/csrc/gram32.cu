@@ -4,9 +4,9 @@
 // pair, E'_s = sum_t A_s[t](x_i)^dagger E_t A_s[t](x_j) with h = 16, i.e. for each of the
 // four (s, t) terms two complex 16 x 16 x 16 products
 //     F = E_t B,  B = A_s[t](x_j);      E'_s += A_s[t](x_i)^dagger F.
-// E (two 16 x 16 blocks) and F live in shared memory per warp; lane (rp, cq) owns output
-// rows {rp, rp + 8} and columns {4cq .. 4cq + 3}, so every operand read is a 16-byte load
-// that 4 or 8 lanes share. Per site the CTA stages the site tensors of its TR row samples
+// E (two 16 x 16 blocks) and F (one per s) live in shared memory per warp; the warp works on
+// both s at once, each lane on a 4 x 4 complex tile of one block, so that every float read
+// from shared memory feeds four FMAs (see pair_site). Per site the CTA stages the site tensors of its TR row samples
 // (compact layout, rows padded to 272 B) and TC column samples (each 16 x 16 block
 // transposed to row-major, rows padded to 144 B) into shared memory, double buffered: the
 // next site's tensors are loaded into registers while the current site is contracted.
@@ -21,7 +21,7 @@
 namespace dk {
 namespace c32 {
 
-constexpr int H = 16, CHI = 32;
+constexpr int CHI = 32;
 constexpr int SAMPLE_FLOATS = CHI * CHI * 2;        // compact site tensor, complex64
 // Row-sample buffer: compact rows r = s*16 + j (32 of them), each 32 complex = 256 B, padded
 // to 272 B (68 floats): consecutive rows start 4 banks apart, so the 8 rows a warp reads at
@@ -55,138 +55,135 @@ __device__ __forceinline__ void put_col_chunk(float* bbuf, int chunk, float4 v) 
   *reinterpret_cast<float2*>(blk + (b0 + 1) * BROW + 2 * c) = make_float2(v.z, v.w);
 }
 
-// One site of one pair by one warp. ebuf: 2 blocks E_t (row-major, padded); fbuf: F.
+// One site of one pair by one warp. ebuf: 2 blocks E_t (row-major, padded); fbuf: F_0, F_1.
 // abuf: row sample (compact, padded rows); bbuf: column sample (transposed blocks).
-// Returns nothing; E is updated in place (block s of the result replaces E_s).
-__device__ __forceinline__ void pair_site(float* ebuf, float* fbuf, const float* abuf, const float* bbuf, int lane,
-                                          float (&accr)[2][2][4], float (&acci)[2][2][4]) {
-  const int rp = lane >> 2, cq = lane & 3;
+// Lane L works on block s = L / 16 (both s at once: they read the same E_t) and owns rows
+// rg, rg + 4, rg + 8, rg + 12 (the 16 lanes of a half read 4 consecutive rows at a time, in
+// different banks), columns 4 cg .. 4 cg + 3 of it (rg = (L % 16) / 4, cg = L % 4): per k-step
+// it reads 4 complex of E_t (or of the row sample) and 4 of B (or of F) for 16 complex
+// multiply-adds, four FMAs per float read from shared memory, the rate at which the shared-
+// memory pipe keeps the FMA pipe busy. acc receives E'_s = block s of the result; every
+// entry sees the same additions in the same order as with any other split of the outputs.
+__device__ __forceinline__ void pair_site(const float* ebuf, float* fbuf, const float* abuf, const float* bbuf,
+                                          int lane, float (&accr)[4][4], float (&acci)[4][4]) {
+  const int s = lane >> 4, rg = (lane >> 2) & 3, cg = lane & 3;
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        accr[s][u][v] = 0.0f;
-        acci[s][u][v] = 0.0f;
-      }
-#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      accr[u][v] = 0.0f;
+      acci[u][v] = 0.0f;
+    }
+  float* fs = fbuf + s * EBLK;
+#pragma unroll 1
   for (int t = 0; t < 2; ++t) {
     const float* et = ebuf + t * EBLK;
+    const float* bb = bbuf + (s * 2 + t) * BBLK;
+    // F_s[a][c] = sum_b E_t[a][b] B[b][c], a = rg + 4u, c in 4cg .. 4cg+3
+    float fr[4][4], fi[4][4];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      // F[a][c] = sum_b E_t[a][b] B[b][c], a in {rp, rp+8}, c in 4cq..4cq+3
-      const float* bb = bbuf + (s * 2 + t) * BBLK;
-      float fr[2][4], fi[2][4];
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
+      for (int v = 0; v < 4; ++v) {
+        fr[u][v] = 0.0f;
+        fi[u][v] = 0.0f;
+      }
+#pragma unroll 2
+    for (int b2 = 0; b2 < 8; ++b2) {  // two b per step
+      float4 e[4];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          fr[u][v] = 0.0f;
-          fi[u][v] = 0.0f;
-        }
-#pragma unroll 4
-      for (int b2 = 0; b2 < 8; ++b2) {  // two b per step
-        float4 e[2];
-        e[0] = ld4(et + rp * BROW + 4 * b2);
-        e[1] = ld4(et + (rp + 8) * BROW + 4 * b2);
+      for (int u = 0; u < 4; ++u) e[u] = ld4(et + (rg + 4 * u) * BROW + 4 * b2);
 #pragma unroll
-        for (int bb_ = 0; bb_ < 2; ++bb_) {
-          const int b = 2 * b2 + bb_;
-          const float4 x0 = ld4(bb + b * BROW + 8 * cq);
-          const float4 x1 = ld4(bb + b * BROW + 8 * cq + 4);
-          const float br[4] = {x0.x, x0.z, x1.x, x1.z};
-          const float bi[4] = {x0.y, x0.w, x1.y, x1.w};
+      for (int bb_ = 0; bb_ < 2; ++bb_) {
+        const int b = 2 * b2 + bb_;
+        const float4 x0 = ld4(bb + b * BROW + 8 * cg);
+        const float4 x1 = ld4(bb + b * BROW + 8 * cg + 4);
+        const float br[4] = {x0.x, x0.z, x1.x, x1.z};
+        const float bi[4] = {x0.y, x0.w, x1.y, x1.w};
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const float er = bb_ == 0 ? e[u].x : e[u].z;
-            const float ei = bb_ == 0 ? e[u].y : e[u].w;
+        for (int u = 0; u < 4; ++u) {
+          const float er = bb_ == 0 ? e[u].x : e[u].z;
+          const float ei = bb_ == 0 ? e[u].y : e[u].w;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              fr[u][v] = fmaf(er, br[v], fr[u][v]);
-              fi[u][v] = fmaf(er, bi[v], fi[u][v]);
-              fr[u][v] = fmaf(-ei, bi[v], fr[u][v]);
-              fi[u][v] = fmaf(ei, br[v], fi[u][v]);
-            }
+          for (int v = 0; v < 4; ++v) {
+            fr[u][v] = fmaf(er, br[v], fr[u][v]);
+            fi[u][v] = fmaf(er, bi[v], fi[u][v]);
+            fr[u][v] = fmaf(-ei, bi[v], fr[u][v]);
+            fi[u][v] = fmaf(ei, br[v], fi[u][v]);
           }
         }
       }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        float* fp = fbuf + (rp + 8 * u) * BROW + 8 * cq;
-        *reinterpret_cast<float4*>(fp) = make_float4(fr[u][0], fi[u][0], fr[u][1], fi[u][1]);
-        *reinterpret_cast<float4*>(fp + 4) = make_float4(fr[u][2], fi[u][2], fr[u][3], fi[u][3]);
-      }
-      __syncwarp();
-      // E'_s[p][c] += sum_a conj(A_s[t][a][p]) F[a][c], p in {rp, rp+8}: row p of the compact
-      // tensor at block s, positions t*16 + a.
-      const float* ar0 = abuf + (s * 16 + rp) * AROW + t * 32;
-      const float* ar1 = abuf + (s * 16 + rp + 8) * AROW + t * 32;
-#pragma unroll 4
-      for (int a2 = 0; a2 < 8; ++a2) {
-        const float4 y[2] = {ld4(ar0 + 4 * a2), ld4(ar1 + 4 * a2)};
-#pragma unroll
-        for (int aa = 0; aa < 2; ++aa) {
-          const int a = 2 * a2 + aa;
-          const float4 f0 = ld4(fbuf + a * BROW + 8 * cq);
-          const float4 f1 = ld4(fbuf + a * BROW + 8 * cq + 4);
-          const float gr[4] = {f0.x, f0.z, f1.x, f1.z};
-          const float gi[4] = {f0.y, f0.w, f1.y, f1.w};
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const float cr = aa == 0 ? y[u].x : y[u].z;
-            const float ci = aa == 0 ? y[u].y : y[u].w;
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              accr[s][u][v] = fmaf(cr, gr[v], accr[s][u][v]);
-              acci[s][u][v] = fmaf(cr, gi[v], acci[s][u][v]);
-              accr[s][u][v] = fmaf(ci, gi[v], accr[s][u][v]);
-              acci[s][u][v] = fmaf(-ci, gr[v], acci[s][u][v]);
-            }
-          }
-        }
-      }
-      __syncwarp();
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float* fp = fs + (rg + 4 * u) * BROW + 8 * cg;
+      *reinterpret_cast<float4*>(fp) = make_float4(fr[u][0], fi[u][0], fr[u][1], fi[u][1]);
+      *reinterpret_cast<float4*>(fp + 4) = make_float4(fr[u][2], fi[u][2], fr[u][3], fi[u][3]);
+    }
+    __syncwarp();
+    // E'_s[p][c] += sum_a conj(A_s[t][a][p]) F_s[a][c], p = rg + 4u: row p of the
+    // compact tensor at block s, positions t*16 + a.
+    const float* ar = abuf + (s * 16 + rg) * AROW + t * 32;
+#pragma unroll 2
+    for (int a2 = 0; a2 < 8; ++a2) {
+      float4 y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) y[u] = ld4(ar + 4 * u * AROW + 4 * a2);
+#pragma unroll
+      for (int aa = 0; aa < 2; ++aa) {
+        const int a = 2 * a2 + aa;
+        const float4 f0 = ld4(fs + a * BROW + 8 * cg);
+        const float4 f1 = ld4(fs + a * BROW + 8 * cg + 4);
+        const float gr[4] = {f0.x, f0.z, f1.x, f1.z};
+        const float gi[4] = {f0.y, f0.w, f1.y, f1.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float cr = aa == 0 ? y[u].x : y[u].z;
+          const float ci = aa == 0 ? y[u].y : y[u].w;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            accr[u][v] = fmaf(cr, gr[v], accr[u][v]);
+            acci[u][v] = fmaf(cr, gi[v], acci[u][v]);
+            accr[u][v] = fmaf(ci, gi[v], accr[u][v]);
+            acci[u][v] = fmaf(-ci, gr[v], acci[u][v]);
+          }
+        }
+      }
+    }
+    __syncwarp();
   }
 }
 
-// Write E := diag(acc_0, acc_1), rescaling by a power of two when asked; returns the
-// exponent taken out (warp-uniform).
-__device__ __forceinline__ int store_e(float* ebuf, int lane, float (&accr)[2][2][4], float (&acci)[2][2][4],
+// Write E := diag(acc_0, acc_1) (block s from the lanes of half s), rescaling by a power of
+// two when asked; returns the exponent taken out (warp-uniform).
+__device__ __forceinline__ int store_e(float* ebuf, int lane, float (&accr)[4][4], float (&acci)[4][4],
                                        bool renorm) {
-  const int rp = lane >> 2, cq = lane & 3;
+  const int s = lane >> 4, rg = (lane >> 2) & 3, cg = lane & 3;
   int e = 0;
   if (renorm) {
     float mx = 0.0f;
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) mx = fmaxf(mx, fmaxf(fabsf(accr[s][u][v]), fabsf(acci[s][u][v])));
+      for (int v = 0; v < 4; ++v) mx = fmaxf(mx, fmaxf(fabsf(accr[u][v]), fabsf(acci[u][v])));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     e = RealBits<float>::exponent(mx);
     const float sc = RealBits<float>::pow2_neg(e);
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          accr[s][u][v] *= sc;
-          acci[s][u][v] *= sc;
-        }
+      for (int v = 0; v < 4; ++v) {
+        accr[u][v] *= sc;
+        acci[u][v] *= sc;
+      }
   }
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      float* ep = ebuf + s * EBLK + (rp + 8 * u) * BROW + 8 * cq;
-      *reinterpret_cast<float4*>(ep) = make_float4(accr[s][u][0], acci[s][u][0], accr[s][u][1], acci[s][u][1]);
-      *reinterpret_cast<float4*>(ep + 4) = make_float4(accr[s][u][2], acci[s][u][2], accr[s][u][3], acci[s][u][3]);
-    }
+  for (int u = 0; u < 4; ++u) {
+    float* ep = ebuf + s * EBLK + (rg + 4 * u) * BROW + 8 * cg;
+    *reinterpret_cast<float4*>(ep) = make_float4(accr[u][0], acci[u][0], accr[u][1], acci[u][1]);
+    *reinterpret_cast<float4*>(ep + 4) = make_float4(accr[u][2], acci[u][2], accr[u][3], acci[u][3]);
+  }
   __syncwarp();
   return e;
 }
@@ -212,7 +209,7 @@ struct Cfg32 {
   static constexpr int STAGE = TR * ABUF + TC * BBUF;                 // floats per stage
   static constexpr int CHUNKS = (TR + TC) * (SAMPLE_FLOATS / 4);        // 16-byte chunks per stage
   static constexpr int PER_THREAD = (CHUNKS + NT - 1) / NT;
-  static constexpr int SMEM = (2 * STAGE + NW * (2 * EBLK + EBLK)) * 4;
+  static constexpr int SMEM = (2 * STAGE + NW * 4 * EBLK) * 4;  // + per warp E (2 blocks), F (2 blocks)
 };
 
 template <int TR, int TC>
@@ -223,7 +220,7 @@ __global__ void __launch_bounds__(TR * TC * 32, 1)
   extern __shared__ __align__(16) float sm[];
   float* stage[2] = {sm, sm + C::STAGE};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* ebuf = sm + 2 * C::STAGE + warp * 3 * EBLK;
+  float* ebuf = sm + 2 * C::STAGE + warp * 4 * EBLK;
   float* fbuf = ebuf + 2 * EBLK;
   const int wr = warp / TC, wc = warp % TC;
 
@@ -268,7 +265,7 @@ __global__ void __launch_bounds__(TR * TC * 32, 1)
     for (int k = 0; k < p.n; ++k) {
       float* cur = stage[k & 1];
       if (k + 1 < p.n) fetch(r0, c0, k + 1);
-      float accr[2][2][4], acci[2][2][4];
+      float accr[4][4], acci[4][4];
       pair_site(ebuf, fbuf, cur + wr * ABUF, cur + TR * ABUF + wc * BBUF, lane, accr, acci);
       const bool rn = (k == p.n - 1) || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1);
       e2 += store_e(ebuf, lane, accr, acci, rn);
@@ -310,7 +307,7 @@ __global__ void __launch_bounds__(32) self_overlap32_kernel(const float* __restr
       put_col_chunk(bbuf, ch, v);
     }
     __syncwarp();
-    float accr[2][2][4], acci[2][2][4];
+    float accr[4][4], acci[4][4];
     pair_site(ebuf, fbuf, abuf, bbuf, lane, accr, acci);
     const bool rn = (k == n - 1) || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1);
     e2 += store_e(ebuf, lane, accr, acci, rn);
@@ -339,7 +336,7 @@ dk_status gram32_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps
 }
 
 dk_status self_overlap32_launch(const void* mps, int m, int n, float* log_norm, cudaStream_t st) {
-  const int smem = (c32::ABUF + c32::BBUF + 3 * c32::EBLK) * 4;
+  const int smem = (c32::ABUF + c32::BBUF + 4 * c32::EBLK) * 4;
   // set before every launch: the attribute is per device and cheap to set
   if (cudaFuncSetAttribute(c32::self_overlap32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess)
