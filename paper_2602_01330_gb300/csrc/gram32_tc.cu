@@ -18,11 +18,16 @@
 //   step 2:  E'_s += C G          (A operand C from shared memory, B operand from G^T's
 //                                  accumulators),
 // and E'_s is again in accumulator form for the next site. No intermediate goes through
-// shared memory. Four staging warps, separate from the pair warps, fill a three-stage ring in
-// shared memory, one site per stage: the CTA's row samples as C operands and its column
-// samples as B^T operands (the same 16 x 32 layout, without the conjugation), split into
-// BF16 hi / lo. Their HBM loads and conversions run under the pair warps' MMAs, and the pair
-// warps hold no prefetch registers.
+// shared memory. A sample's operand is stored once, X = [Re A^T | Im A^T] split into BF16
+// hi / lo: step 1 uses it as B^T, step 2 as C = conj(A)^T by negating the other factor's
+// matching rows (put_chunk, mma_block_side).
+//
+// Operand staging, one site per stage of a shared-memory ring, by warps separate from the
+// pair warps so that it runs under their MMAs:
+//   split operands (dk_mps_split32, the faster form): one copy warp moves each sample's
+//     10 KB image with one bulk copy;
+//   complex64 site tensors: four staging warps load them from HBM (one site ahead, in
+//     registers) and split them.
 #include <math.h>
 
 #include "common.cuh"
@@ -183,16 +188,15 @@ __device__ __forceinline__ void mma_block(float (&acc)[4][4], const u16* xh, con
 }
 
 // One site of one pair (warp). rbuf: row-sample C operands; cbuf: column-sample B^T
-// operands. E is replaced by diag(acc_0, acc_1). Schedules of the same MMAs and conversions:
-//   SCHED 0: per (t, s) step 1, conversion of G, step 2 (fewest live registers);
-//   SCHED 1: per t both step-1 products (s = 0, 1) back to back, then per s the conversion of
-//            G_s and step 2;
-//   SCHED 2: as 1, with every conversion that has an independent MMA block beside it spread
-//            over that block's MMAs (E_1 over the first step-1 block, G_0 over the second,
-//            G_1 over the first step-2 block); only E_0's conversion runs on its own.
-// Every accumulator receives its MMAs in the same order in all three (acc_s: t = 0, then
-// t = 1) and every conversion is the same split2, so the result does not depend on the schedule.
-template <int SCHED>
+// operands. E is replaced by diag(acc_0, acc_1). Two schedules of the same MMAs:
+//   IL = false: per (t, s) step 1, conversion of G, step 2 (fewest live registers);
+//   IL = true:  per t both step-1 products (s = 0, 1) back to back, and every conversion that
+//               has an independent MMA block beside it spread over that block's MMAs (E_1
+//               over the first step-1 block, G_0 over the second, G_1 over the first step-2
+//               block); only E_0's conversion runs on its own.
+// Every accumulator receives its MMAs in the same order in both (acc_s: t = 0, then t = 1)
+// and every conversion is the same split2, so the result does not depend on the schedule.
+template <bool IL>
 __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* cbuf, int lane) {
   float acc[2][4][4];
 #pragma unroll
@@ -201,7 +205,7 @@ __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* c
     for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[s][nt][c] = 0.0f;
-  if (SCHED == 0) {
+  if (!IL) {
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       BFrag fe;
@@ -220,10 +224,8 @@ __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* c
       }
     }
   } else {
-    constexpr bool SIDE = SCHED == 2;
     BFrag fe[2];
-    to_bfrag(E.v[0], fe[0]);  // B operands of E_t^T
-    if (!SIDE) to_bfrag(E.v[1], fe[1]);
+    to_bfrag(E.v[0], fe[0]);  // B operands of E_0^T; E_1's are formed during the first block
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       // step 1: G_s^T = B_{s,t}^T . E_t^T for s = 0, 1
@@ -235,13 +237,11 @@ __device__ __forceinline__ void pair_site(Frag& E, const u16* rbuf, const u16* c
 #pragma unroll
           for (int c = 0; c < 4; ++c) g[s][nt][c] = 0.0f;
       BFrag fg[2];
-      if (t == 0) mma_block_side<false, SIDE>(g[0], cbuf + (0 * 2 + t) * 2 * COP, fe[t], lane, E.v[1], fe[1]);
+      if (t == 0) mma_block_side<false, true>(g[0], cbuf + (0 * 2 + t) * 2 * COP, fe[t], lane, E.v[1], fe[1]);
       else mma_block<false>(g[0], cbuf + (0 * 2 + t) * 2 * COP, fe[t], lane);
-      mma_block_side<false, SIDE>(g[1], cbuf + (1 * 2 + t) * 2 * COP, fe[t], lane, g[0], fg[0]);
+      mma_block_side<false, true>(g[1], cbuf + (1 * 2 + t) * 2 * COP, fe[t], lane, g[0], fg[0]);
       // step 2: acc_s += C_{s,t} . G_s (B operand of G_s from G_s^T's accumulators)
-      if (!SIDE) to_bfrag(g[0], fg[0]);
-      mma_block_side<true, SIDE>(acc[0], rbuf + (0 * 2 + t) * 2 * COP, fg[0], lane, g[1], fg[1]);
-      if (!SIDE) to_bfrag(g[1], fg[1]);
+      mma_block_side<true, true>(acc[0], rbuf + (0 * 2 + t) * 2 * COP, fg[0], lane, g[1], fg[1]);
       mma_block<true>(acc[1], rbuf + (1 * 2 + t) * 2 * COP, fg[1], lane);
     }
   }
@@ -296,7 +296,7 @@ __device__ __forceinline__ float half_log_mod(const Frag& E, int e2) {
 // CTA of TR x TC pair warps (one pair each) and NPROD staging warps over a ring of NSTG
 // stages; a stage holds one site of the tile's TR row samples (C operands) and TC column
 // samples (B^T operands).
-template <int TR, int TC, int NSTG, int SCHED_, bool PRESPLIT_>
+template <int TR, int TC, int NSTG, bool IL_, bool PRESPLIT_>
 struct CfgTc {
   static constexpr int TR_ = TR, TC_ = TC, NSTG_ = NSTG;
   static constexpr bool PRESPLIT = PRESPLIT_;      // operands from dk_mps_split32: copied, not split
@@ -307,7 +307,7 @@ struct CfgTc {
   static constexpr int CH = (TR + TC) * CHUNKS;    // 16-byte chunks of a stage's site tensors
   static_assert(PRESPLIT || CH % PT == 0, "whole chunks per staging thread");
   static constexpr int PER_THREAD = CH / PT;
-  static constexpr int SCHED = SCHED_;
+  static constexpr bool IL = IL_;                  // pair_site schedule
   static constexpr u32 OPS_BYTES = SBUF * sizeof(u16);  // one sample-site of dk_mps_split32 operands
   static constexpr size_t BAR_OFF = size_t(NSTG) * STAGE * sizeof(u16);
   static constexpr size_t SMEM = BAR_OFF + 2 * NSTG * sizeof(uint64_t) + 16;
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(C::NT, 1)
           break;
         }
         const u16* cur = smu + s * C::STAGE;
-        pair_site<C::SCHED>(E, cur + wr * SBUF, cur + (TR + wc) * SBUF, lane);
+        pair_site<C::IL>(E, cur + wr * SBUF, cur + (TR + wc) * SBUF, lane);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         if (k == p.n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1)) e2 += renorm(E);
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(32) self_overlap32_tc_kernel(const float* __re
       put_chunk(smu, w, v);
     }
     __syncwarp();
-    pair_site<0>(E, smu, smu, lane);
+    pair_site<false>(E, smu, smu, lane);
     if (k == n - 1 || ((k & (RENORM_EVERY - 1)) == RENORM_EVERY - 1)) e2 += renorm(E);
     __syncwarp();
   }
@@ -555,11 +555,11 @@ static dk_status gram32_tc_run(dk_ctx* ctx, const void* mps_r, int m_r, const vo
 dk_status gram32_tc_launch(dk_ctx* ctx, const void* mps_r, int m_r, const void* mps_c, int m_c, GramArgs a,
                            bool presplit, cudaStream_t st) {
   // Measured fastest of the shapes and schedules that fit the registers (512 samples, d = 256):
-  // split operands: 4 x 4 pairs, two stages, schedule 0 (16 pair warps at 96 registers;
-  // 56.6 ms against 58.4 for 4 x 2); complex64 input: 4 x 2 pairs, three stages, schedule 2
+  // split operands: 4 x 4 pairs, two stages, IL = false (16 pair warps at 96 registers;
+  // 56.6 ms against 58.4 for 4 x 2); complex64 input: 4 x 2 pairs, three stages, IL = true
   // (the staging warps leave 168 registers for 8 pair warps; 4 x 3 tiles spill at 128).
-  if (presplit) return gram32_tc_run<tc32::CfgTc<4, 4, 2, 0, true>>(ctx, mps_r, m_r, mps_c, m_c, a, st);
-  return gram32_tc_run<tc32::CfgTc<4, 2, 3, 2, false>>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+  if (presplit) return gram32_tc_run<tc32::CfgTc<4, 4, 2, false, true>>(ctx, mps_r, m_r, mps_c, m_c, a, st);
+  return gram32_tc_run<tc32::CfgTc<4, 2, 3, true, false>>(ctx, mps_r, m_r, mps_c, m_c, a, st);
 }
 
 dk_status self_overlap32_tc_launch(const void* mps, int m, int n, float* log_norm, cudaStream_t st) {
