@@ -87,6 +87,31 @@ def test_gram_on_split_operands_is_bit_identical(dk, m_rows, m_cols, d):
     ctx.sync_status()
 
 
+@pytest.mark.parametrize("m,d,row0,nrows,col0,ncols", [(23, 3, 5, 11, 3, 17), (9, 2, 0, 9, 2, 5), (41, 7, 37, 4, 0, 41)])
+def test_split_operands_on_sub_blocks(dk, m, d, row0, nrows, col0, ncols):
+    """Rectangular sub-blocks at offsets, ragged against the 4 x 4 pair tiles, short chains:
+    the split-operand Gram gives the bits of the complex64 one."""
+    dualk, ctx, torch = dk
+    from paper_2602_01330_gb300 import synthetic
+    x = synthetic.uniform_angles(m, d, seed=m + d)
+    mps = dualk.mps_build(ctx, torch.from_numpy(x.astype(np.float32)).cuda(), dualk.FeatureMap(reps=5, chi_max=32))
+    prec = dualk.DK_PREC_BF16X3
+    kw = dict(row0=row0, nrows=nrows, col0=col0, ncols=ncols, w=0.25, prec=prec, refine=None)
+    split = dualk.gram_tile(ctx, mps, mps, **kw)
+    direct = dualk._gram_operands
+    try:
+        dualk._gram_operands = lambda c, mp, p, s=None: (mp.data, mp.dtype)
+        whole = dualk.gram_tile(ctx, mps, mps, **kw)
+    finally:
+        dualk._gram_operands = direct
+    torch.cuda.synchronize()
+    for key in ("k", "kq", "kc", "logkq"):
+        assert torch.equal(split[key], whole[key]), key
+    kq = split["kq"].cpu().numpy()
+    assert np.all(np.isfinite(kq)) and np.all(kq >= 0.0) and np.all(kq <= 1.0 + 1e-4)
+    ctx.sync_status()
+
+
 def test_split_rejections(dk):
     dualk, ctx, torch = dk
     from paper_2602_01330_gb300 import synthetic
