@@ -293,9 +293,9 @@ __device__ __forceinline__ float half_log_mod(const Frag& E, int e2) {
   return fmaf(0.5f, logf(mod2), float(e2) * 0.69314718055994530942f);
 }
 
-// CTA of TR x TC pair warps (one pair each) and NPROD staging warps over a ring of NSTG
-// stages; a stage holds one site of the tile's TR row samples (C operands) and TC column
-// samples (B^T operands).
+// CTA of TR x TC pair warps (one pair each) and the staging warps (four, or one copy warp
+// for split operands) over a ring of NSTG stages; a stage holds one site of the operands of
+// the tile's TR row samples and TC column samples.
 template <int TR, int TC, int NSTG, bool IL_, bool PRESPLIT_>
 struct CfgTc {
   static constexpr int TR_ = TR, TC_ = TC, NSTG_ = NSTG;
