@@ -383,7 +383,7 @@ template <class Cfg>
 constexpr CfgInfo info_of() {
   return CfgInfo{Cfg::TR, Cfg::TC, Cfg::NTHREADS};
 }
-// Shapes selectable for complex64 / chi 4, in id order 1..11; the built-in choice is id 8.
+// Shapes selectable for complex64 / chi 4, in id order 1..19; the built-in choice is kF32Chi4Default.
 static const CfgInfo kF32Chi4[] = {info_of<F32_P11>(),  info_of<F32_P21>(),  info_of<F32_P22>(), info_of<F32_P12>(),
                                    info_of<F32_P22w>(), info_of<F32_P21w>(), info_of<F32_P14>(),
                                    info_of<F32_P22wS2>(), info_of<F32_P22S2>(), info_of<F32_P22wS4>(),
